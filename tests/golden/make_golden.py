@@ -1,0 +1,47 @@
+"""Write the stored expected values under tests/golden/ by calling the CPU oracle only.
+
+    python tests/golden/make_golden.py [cubic] [dimer]
+
+cubic_dense_eigs.txt   lowest 8 eigenvalues above the gap of the dense shifted H'
+                       for the cubic workload (zheevd, FP64).
+dimer_lobpcgf_eigs.txt lowest 32 eigenvalues of the dimer workload from the oracle's
+                       Algorithm 1 (FP64, tol 1e-7, Teter, N_init = 3).
+"""
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import workloads as W  # noqa: E402
+from oracle import basis, lobpcgf as lb, operator as op  # noqa: E402
+
+
+def cubic():
+    wl = W.make("cubic")
+    m, q = basis.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
+    lam, _, _ = lb.dense_eigs(op.dense_hamiltonian(wl, m, q), wl.c, 8)
+    np.savetxt(os.path.join(HERE, "cubic_dense_eigs.txt"), lam, fmt="%.15e",
+               header="cubic workload: lowest 8 eigenvalues (Ha, shifted by -c^2) of dense H', zheevd")
+
+
+def dimer():
+    wl = W.make("dimer")
+    m, q = basis.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
+    hop = op.MatrixFreeH(wl, m, q)
+    cs, om = op.filter_constants(wl, q)
+    x0 = W.start_block(len(q), 32, wl.seed)
+    r = lb.lobpcgf(hop, q, x0, 32, cs, om, tol=1e-7,
+                   callback=lambda it, lam, n: print(it, n.max(), flush=True))
+    assert r.converged
+    np.savetxt(os.path.join(HERE, "dimer_lobpcgf_eigs.txt"), r.lam, fmt="%.15e",
+               header=f"dimer workload: lowest 32 eigenvalues (Ha, shifted) from the oracle's "
+                      f"Algorithm 1, tol 1e-7, {r.iterations} iterations")
+
+
+if __name__ == "__main__":
+    which = sys.argv[1:] or ["cubic"]
+    for w in which:
+        globals()[w]()
