@@ -1,0 +1,216 @@
+/*
+ * dks.h -- C ABI of the GB300 LOBPCG-F solver for the four-component
+ * Dirac-Kohn-Sham (DKS) operator in a planewave basis.
+ *
+ * Method: Lin, Shao and E, "Efficient iterative method for solving the
+ * Dirac-Kohn-Sham density functional theory", Algorithm 1 (LOBPCG-F) with the
+ * filter f(E) = (E - C)^2 / Omega^2 of Eq. (filter), applied to the valence DKS
+ * operator of Eq. (vDKS): the free Dirac operator of Eq. (2), a local potential
+ * V(r) I4 and the spin-orbit projectors of Eq. (HGH), discretised by planewaves
+ * (Sec. 2.3).  All energies are shifted by -mc^2 (Sec. 4): the library works
+ * with H' = H - c^2, the positive band starts near 0 and the gap midpoint is
+ * -c^2.
+ *
+ * Conventions shared by every entry point
+ *  - Units: atomic units (bohr, Hartree), m = 1.
+ *  - Basis of k-point ik: G = m1 b1 + m2 b2 + m3 b3 with |k+G|^2/2 <= ecut_k,
+ *    in canonical order (Miller triples sorted lexicographically, signed).
+ *    dks_basis() returns the Miller triples in that order.
+ *  - Vector blocks: X[band][comp][pw], complex interleaved (re, im), contiguous,
+ *    comp 0,1 the large two-spinor (spin up, down), comp 2,3 the small one.
+ *    complex128 for DKS_PREC_FP64, complex64 for DKS_PREC_FP32.
+ *  - Device pointers are CUDA device memory owned by the caller; host pointers
+ *    are read during the call only.  `stream` is a cudaStream_t (NULL = legacy
+ *    default stream).  Calls are asynchronous on `stream` unless stated.
+ *  - Errors: every function returns DKS_OK (0) or a negative DKS_ERR_* code;
+ *    dks_strerror() describes it and dks_last_error() gives detail for the
+ *    calling thread.  Nothing is thrown across the ABI; no kernel traps.
+ */
+#ifndef DKS_H
+#define DKS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DKS_OK 0
+#define DKS_ERR_INVALID_ARG (-1)   /* bad pointer, size, index or option          */
+#define DKS_ERR_CUDA (-2)          /* a CUDA runtime call failed                   */
+#define DKS_ERR_OOM (-3)           /* device or host allocation failed             */
+#define DKS_ERR_NOT_CONVERGED (-4) /* n_iter exhausted; partial results returned   */
+#define DKS_ERR_NEG_STATE (-5)     /* a selected Ritz value is below the gap midpoint */
+#define DKS_ERR_RANK (-6)          /* SVQB left fewer directions than the block    */
+#define DKS_ERR_TIMEOUT (-7)       /* a bounded device wait gave up               */
+#define DKS_ERR_GRID (-8)          /* a planewave sphere does not fit the FFT grid */
+#define DKS_ERR_UNSUPPORTED (-9)   /* size outside the compiled limits             */
+
+#define DKS_PREC_FP64 0  /* complex128 storage, FP64 arithmetic                      */
+#define DKS_PREC_FP32 1  /* complex64 storage, FP32 arithmetic (FP64 Dirac 4x4 term) */
+
+typedef struct dks_ctx dks_ctx; /* opaque; owns basis tables and workspace */
+
+/* Cell, grid and k-points (Sec. 2.3, Sec. 4).  lattice rows are a1, a2, a3 in
+ * bohr; grid = FFT grid (N1, N2, N3) used for wavefunctions and potential;
+ * c = speed of light; kfrac = nk x 3 fractional k-points (host); ecut_k = nk
+ * cutoffs in Ha (host) or NULL to use the `ecut` argument of dks_create. */
+typedef struct {
+  double lattice[9];
+  int grid[3];
+  double c;
+  int nk;
+  const double* kfrac;
+  const double* ecut_k;
+} dks_cell;
+
+/* Local potential V(r) (Eq. vDKS: V_hxc + local pseudopotential) on the grid,
+ * host FP64 array v_r[(i1*N2 + i2)*N3 + i3] = V(sum_i (i_i/N_i) a_i) in Ha.
+ * v_r = NULL means V = 0. */
+typedef struct {
+  const double* v_r;
+} dks_potentials;
+
+/* Spin-orbit projectors of Eq. (HGH) (host arrays, nsite may be 0):
+ *   beta_{s,l,j,mj}(q) = p_l(|q|) Omega_{j l mj}(qhat) exp(-i q.R_s) / sqrt(vol)
+ *   p_l(q) = A_l q^l exp(-q^2 rl^2 / 2),  A_l = sqrt(2 (2 pi)^3 rl^(2l+3) / Gamma(l+3/2))
+ * with Omega the spinor spherical harmonics (Condon-Shortley Y_lm coupled to
+ * spin 1/2), l = 0..lmax[s] <= 2, j = l +- 1/2.  The operator is
+ * I2 (x) sum D beta beta^H (identical on large and small two-spinors, since
+ * the spin operator of Eq. (HGH) is diag(sigma, sigma)/2).
+ *   pos[nsite*3]   cartesian positions (bohr)
+ *   lmax[nsite]    highest l (-1 = no projector on this site)
+ *   rl[nsite*3]    Gaussian width per l (bohr)
+ *   d[nsite*3*2]   strength D per (l, jj) in Ha; jj = 0: j = l+1/2, jj = 1: j = l-1/2 */
+typedef struct {
+  int nsite;
+  const double* pos;
+  const int* lmax;
+  const double* rl;
+  const double* d;
+} dks_projectors;
+
+/* dks_create: build the planewave spheres, grid maps and projector tables for
+ * every k-point and upload them with V(r) to the current CUDA device.
+ * Synchronous.  Errors: INVALID_ARG, GRID (sphere touches the Nyquist plane
+ * or leaves the grid), UNSUPPORTED (grid axis > 256 or plane too large),
+ * OOM, CUDA.  *out is NULL on error. */
+int dks_create(const dks_cell* cell, double ecut, const dks_potentials* pot,
+               const dks_projectors* proj, dks_ctx** out);
+void dks_destroy(dks_ctx* ctx);
+
+/* Basis size of k-point ik, and its Miller triples (host int[npw*3]). */
+int dks_npw(const dks_ctx* ctx, int ik, int* npw);
+int dks_basis(const dks_ctx* ctx, int ik, int* miller);
+/* Number of projector channels (sum over sites of 2(2 lmax + 1)^... = 18 per s,p,d site). */
+int dks_nproj(const dks_ctx* ctx, int* nproj);
+
+/* Default filter constants for k-point ik (readings of Sec. 3.1, shifted units):
+ *   C     = -(3c^2 + sqrt(c^2 qmax^2 + c^4)) / 2  (midpoint of the free negative band)
+ *   Omega = E_upper - C,  E_upper = sqrt(c^2 qmax^2 + c^4) - c^2 + max|V| + sum|D|. */
+int dks_filter_constants(const dks_ctx* ctx, int ik, double* C, double* Omega);
+
+/* dks_apply_H: HX = H' X for nb bands of k-point ik (Eq. vDKS, Sec. 3.1
+ * "matrix-free" Hx).  X, HX: device, [nb][4][npw], precision `prec`; X and HX
+ * must not overlap.  Uses ctx workspace (not reentrant per ctx).  Errors:
+ * INVALID_ARG, CUDA. */
+int dks_apply_H(dks_ctx* ctx, int ik, const void* X, void* HX, int nb, int prec, void* stream);
+
+/* dks_filter: FY = f(H') Y = (H' - C)^2 Y / Omega^2 (Eq. filter), applied as
+ * two passes of (H' - C)/Omega.  C and Omega in shifted units (see
+ * dks_filter_constants).  Same layout and rules as dks_apply_H. */
+int dks_filter(dks_ctx* ctx, int ik, const void* Y, void* FY, int nb, double C, double Omega,
+               int prec, void* stream);
+
+/* ---------------------------------------------------------------- solver */
+
+#define DKS_MODE_FP64 0  /* plain FP64 LOBPCG-F                                        */
+#define DKS_MODE_MIXED 1 /* FP32 H, Gram and rotations + FP64 small RR and residual
+                            norms, then FP64 refinement iterations                     */
+#define DKS_PRECOND_TETER 0
+#define DKS_PRECOND_IDENTITY 1
+
+typedef struct {
+  int n_init;          /* initial filter steps N_init (Alg. 1 lines 1-3), default 3 */
+  int n_iter;          /* maximum iterations N_iter, default 200                       */
+  int nbuf;            /* extra columns iterated but not convergence-checked           */
+  double C, Omega;     /* filter constants; NaN = dks_filter_constants                 */
+  int mode;            /* DKS_MODE_*                                                   */
+  double refine_tol;   /* MIXED: switch to FP64 once max residual < refine_tol         */
+  int precond;         /* DKS_PRECOND_*                                                */
+  int use_filter;      /* 1 = LOBPCG-F; 0 = standard LOBPCG (Alg. 1 without F lines)  */
+  const int* nev_k;    /* per-k wanted pairs (host, nk) or NULL = the nev argument     */
+  void* stream;        /* cudaStream_t for all work                                    */
+} dks_solve_opts;
+
+typedef struct {
+  int iterations[64];        /* per k (first 64 k-points)                         */
+  int fp64_iterations[64];   /* iterations run in FP64 (MIXED: refinement only)   */
+  double max_residual[64];   /* final max ||H'x - lambda x|| over checked columns */
+  long long h_applications;  /* single-band H' applications, all k               */
+  double shift;              /* c^2 removed from every eigenvalue                  */
+  double seconds;            /* wall time of the call (host clock)                 */
+  int status;                /* DKS_OK or the first error                          */
+} dks_solve_report;
+
+void dks_solve_opts_default(dks_solve_opts* opts);
+
+/* dks_lobpcgf_solve: Algorithm 1 for every k-point of ctx.
+ *  nev      wanted eigenpairs per k (unless opts->nev_k)
+ *  tol      convergence test: every checked column has ||H'x - lambda x||_2 < tol
+ *           with ||x||_2 = 1 (FP64 norms)
+ *  eig      host double[sum_k nev_k], ascending per k, shifted by -c^2
+ *  X        host array of nk device pointers; X[ik] is complex128
+ *           [nev_k + nbuf][4][npw_k]: the start block X0 on entry (N_init filter
+ *           steps are applied to it), the eigenvectors on exit
+ *  report   may be NULL
+ * Synchronous (returns after the eigenvalues reach the host).  Returns
+ * NOT_CONVERGED (results of the last iteration are still written), NEG_STATE,
+ * RANK, INVALID_ARG, OOM or CUDA. */
+int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* opts,
+                      double* eig, void* const* X, dks_solve_report* report);
+
+/* ------------------------------------------- single steps of Algorithm 1
+ * Exposed so that each step can be checked on its own.  Column blocks are
+ * [ncol][rows] complex (rows = 4 npw for DKS vectors), device memory. */
+
+/* Alg. 1 line 9 with the residual of line 16 fused: for i < nact, column
+ * j = act[i] (device int[nact]):  Y[i] = K(x_G) (HX[j] - lam[j] X[j]) with the
+ * Teter-Payne-Allan factor K(x) = P/(P + 16x^4), P = 27+18x+12x^2+8x^3,
+ * x_G = (|k+G|^2/2)/T_j, T_j = sum |k+G|^2/2 |X[j]|^2 / sum |X[j]|^2 over all four
+ * components (precond = IDENTITY: K = 1).  lam: device double[ncols of X]. */
+int dks_precond(dks_ctx* ctx, int ik, const void* X, const void* HX, const double* lam,
+                const int* act, int nact, void* Y, int precond, int prec, void* stream);
+
+/* Alg. 1 lines 12-13 (the projected pencil): A = Z^H HZ and S = Z^H Z for
+ * Z, HZ [nz][rows]; A, S device double2 (complex128) nz x nz, column-major,
+ * both full (Hermitian).  FP64 accumulation for prec FP64; FP32 for FP32. */
+int dks_gram(const void* Z, const void* HZ, int rows, int nz, void* A, void* S, int prec,
+             void* stream);
+
+/* Alg. 1 lines 12-14 on the device in FP64: the n lowest pairs of A v = lam S v
+ * (after diagonal scaling; Cholesky of S, or SVQB with drop tolerance
+ * 1e-12 * max eig when the smallest Cholesky pivot^2 < 1e-12).  A, S device
+ * complex128 nz x nz column-major; V device complex128 nz x n column-major;
+ * lam device double[n] ascending; info device int[2] = {used SVQB, rank}.
+ * nz <= 512.  Returns INVALID_ARG, UNSUPPORTED, CUDA. */
+int dks_rayleigh_ritz(const void* A, const void* S, int nz, int n, void* V, double* lam,
+                      int* info, void* stream);
+
+/* Alg. 1 line 15 / 22: OUT[j] = sum_i Z[i] W[i + ldw*j] (+ beta OUT[j]) for
+ * j < n, i < nz; Z [nz][rows], OUT [n][rows] (precision prec), W device
+ * complex128 column-major with leading dimension ldw (converted to prec). */
+int dks_rotate(const void* Z, int rows, int nz, const void* W, int ldw, int n, void* OUT,
+               double beta, int prec, void* stream);
+
+/* Alg. 1 line 16-17: norms[j] = ||HX[j] - lam[j] X[j]||_2 accumulated in FP64. */
+int dks_residual_norms(const void* X, const void* HX, const double* lam, int rows, int n,
+                       double* norms, int prec, void* stream);
+
+const char* dks_strerror(int code);
+const char* dks_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DKS_H */

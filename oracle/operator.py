@@ -20,7 +20,15 @@ from __future__ import annotations
 import math
 
 import numpy as np
-from scipy.special import eval_legendre, gamma, sph_harm_y
+from scipy.special import eval_legendre, gamma
+
+try:                                   # scipy >= 1.15
+    from scipy.special import sph_harm_y
+except ImportError:                    # older scipy: sph_harm(m, l, azimuth, polar)
+    from scipy.special import sph_harm as _sph_harm_old
+
+    def sph_harm_y(l, m, theta, phi):
+        return _sph_harm_old(m, l, phi, theta)
 
 from .basis import grid_index
 

@@ -1,0 +1,287 @@
+"""Python binding of libdks.so (GB300 LOBPCG-F for the Dirac-Kohn-Sham operator).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI declared in include/dks.h.  PyTorch provides device
+memory and streams.  If the shared library is missing or fails to load, every
+entry point raises -- there is no CPU fallback.
+
+Layouts follow include/dks.h: vector blocks are complex tensors of shape
+[nb, 4, npw] (complex128 for FP64, complex64 for FP32), planewaves in the
+canonical (lexicographic Miller) order returned by Context.basis(ik).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdks.so")
+
+PREC_FP64, PREC_FP32 = 0, 1
+MODE_FP64, MODE_MIXED = 0, 1
+PRECOND_TETER, PRECOND_IDENTITY = 0, 1
+
+ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "NOT_CONVERGED", -5: "NEG_STATE",
+          -6: "RANK", -7: "TIMEOUT", -8: "GRID", -9: "UNSUPPORTED"}
+
+
+class DKSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Cell(C.Structure):
+    _fields_ = [("lattice", C.c_double * 9), ("grid", C.c_int * 3), ("c", C.c_double), ("nk", C.c_int),
+                ("kfrac", C.POINTER(C.c_double)), ("ecut_k", C.POINTER(C.c_double))]
+
+
+class _Pot(C.Structure):
+    _fields_ = [("v_r", C.POINTER(C.c_double))]
+
+
+class _Proj(C.Structure):
+    _fields_ = [("nsite", C.c_int), ("pos", C.POINTER(C.c_double)), ("lmax", C.POINTER(C.c_int)),
+                ("rl", C.POINTER(C.c_double)), ("d", C.POINTER(C.c_double))]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("n_init", C.c_int), ("n_iter", C.c_int), ("nbuf", C.c_int), ("C", C.c_double),
+                ("Omega", C.c_double), ("mode", C.c_int), ("refine_tol", C.c_double), ("precond", C.c_int),
+                ("use_filter", C.c_int), ("nev_k", C.POINTER(C.c_int)), ("stream", C.c_void_p)]
+
+
+class SolveReport(C.Structure):
+    _fields_ = [("iterations", C.c_int * 64), ("fp64_iterations", C.c_int * 64),
+                ("max_residual", C.c_double * 64), ("h_applications", C.c_longlong), ("shift", C.c_double),
+                ("seconds", C.c_double), ("status", C.c_int)]
+
+
+EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dks_filter_constants",
+           "dks_apply_H", "dks_filter", "dks_solve_opts_default", "dks_lobpcgf_solve", "dks_precond",
+           "dks_gram", "dks_rayleigh_ritz", "dks_rotate", "dks_residual_norms", "dks_strerror",
+           "dks_last_error"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdks.so (raises if it is missing: build it with paper_1211_1446_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libdks.so not found at {path}; run `python -m paper_1211_1446_gb300.build`")
+    lib = C.CDLL(path)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    lib.dks_create.argtypes = [C.POINTER(_Cell), d, C.POINTER(_Pot), C.POINTER(_Proj), C.POINTER(vp)]
+    lib.dks_destroy.argtypes = [vp]
+    lib.dks_destroy.restype = None
+    lib.dks_npw.argtypes = [vp, i, C.POINTER(i)]
+    lib.dks_basis.argtypes = [vp, i, C.POINTER(i)]
+    lib.dks_nproj.argtypes = [vp, C.POINTER(i)]
+    lib.dks_filter_constants.argtypes = [vp, i, C.POINTER(d), C.POINTER(d)]
+    lib.dks_apply_H.argtypes = [vp, i, vp, vp, i, i, vp]
+    lib.dks_filter.argtypes = [vp, i, vp, vp, i, d, d, i, vp]
+    lib.dks_solve_opts_default.argtypes = [C.POINTER(SolveOpts)]
+    lib.dks_solve_opts_default.restype = None
+    lib.dks_lobpcgf_solve.argtypes = [vp, i, d, C.POINTER(SolveOpts), C.POINTER(d), C.POINTER(vp),
+                                      C.POINTER(SolveReport)]
+    lib.dks_precond.argtypes = [vp, i, vp, vp, vp, vp, i, vp, i, i, vp]
+    lib.dks_gram.argtypes = [vp, vp, i, i, vp, vp, i, vp]
+    lib.dks_rayleigh_ritz.argtypes = [vp, vp, i, i, vp, vp, vp, vp]
+    lib.dks_rotate.argtypes = [vp, i, i, vp, i, i, vp, d, i, vp]
+    lib.dks_residual_norms.argtypes = [vp, vp, vp, i, i, vp, i, vp]
+    lib.dks_strerror.argtypes = [i]
+    lib.dks_strerror.restype = C.c_char_p
+    lib.dks_last_error.argtypes = []
+    lib.dks_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise DKSError(rc, _lib.dks_last_error().decode())
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _prec_of(t):
+    import torch
+    if t.dtype == torch.complex128:
+        return PREC_FP64
+    if t.dtype == torch.complex64:
+        return PREC_FP32
+    raise TypeError("blocks must be complex128 or complex64")
+
+
+class Context:
+    """Owns a dks_ctx: planewave spheres, FFT plans, V(r) and projector tables on the GPU."""
+
+    def __init__(self, lattice, grid, c, kfrac, ecut, v_r=None, pos=None, lmax=None, rl=None, d=None,
+                 ecut_k=None):
+        lib = load_library()
+        self._keep = []
+        cell = _Cell()
+        cell.lattice[:] = [float(x) for x in np.asarray(lattice, dtype=np.float64).reshape(9)]
+        cell.grid[:] = [int(x) for x in grid]
+        cell.c = float(c)
+        kf = np.ascontiguousarray(np.asarray(kfrac, dtype=np.float64).reshape(-1, 3))
+        cell.nk = kf.shape[0]
+        cell.kfrac = self._arr(kf, C.c_double)
+        if ecut_k is not None:
+            cell.ecut_k = self._arr(np.ascontiguousarray(ecut_k, dtype=np.float64), C.c_double)
+        pot = _Pot()
+        if v_r is not None:
+            pot.v_r = self._arr(np.ascontiguousarray(v_r, dtype=np.float64).reshape(-1), C.c_double)
+        proj = _Proj()
+        if pos is not None and len(pos) and lmax is not None and int(np.max(lmax)) >= 0:
+            proj.nsite = len(pos)
+            proj.pos = self._arr(np.ascontiguousarray(pos, dtype=np.float64).reshape(-1), C.c_double)
+            proj.lmax = self._arr(np.ascontiguousarray(lmax, dtype=np.int32).reshape(-1), C.c_int)
+            proj.rl = self._arr(np.ascontiguousarray(rl, dtype=np.float64).reshape(-1), C.c_double)
+            proj.d = self._arr(np.ascontiguousarray(d, dtype=np.float64).reshape(-1), C.c_double)
+        self._h = C.c_void_p()
+        _check(lib.dks_create(C.byref(cell), float(ecut if ecut is not None else 0.0), C.byref(pot),
+                              C.byref(proj), C.byref(self._h)))
+        self.nk = cell.nk
+        self.c = float(c)
+        self._keep = []
+
+    def _arr(self, a, ctype):
+        self._keep.append(a)
+        return a.ctypes.data_as(C.POINTER(ctype))
+
+    @classmethod
+    def from_workload(cls, wl):
+        """Build from any object with the attributes of workloads.Workload (duck-typed)."""
+        return cls(wl.lattice, wl.grid, wl.c, wl.kfrac, None, v_r=wl.v_r, pos=wl.pos, lmax=wl.lmax,
+                   rl=wl.rl, d=wl.d, ecut_k=wl.ecut_k)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dks_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- queries
+    def npw(self, ik=0):
+        n = C.c_int()
+        _check(_lib.dks_npw(self._h, ik, C.byref(n)))
+        return n.value
+
+    def basis(self, ik=0):
+        m = np.zeros((self.npw(ik), 3), dtype=np.int32)
+        _check(_lib.dks_basis(self._h, ik, m.ctypes.data_as(C.POINTER(C.c_int))))
+        return m
+
+    def nproj(self):
+        n = C.c_int()
+        _check(_lib.dks_nproj(self._h, C.byref(n)))
+        return n.value
+
+    def filter_constants(self, ik=0):
+        cs, om = C.c_double(), C.c_double()
+        _check(_lib.dks_filter_constants(self._h, ik, C.byref(cs), C.byref(om)))
+        return cs.value, om.value
+
+    # ---- operator
+    def apply_H(self, ik, x, hx, stream=None):
+        _check(_lib.dks_apply_H(self._h, ik, _dptr(x), _dptr(hx), x.shape[0], _prec_of(x), _stream(stream)))
+        return hx
+
+    def filter(self, ik, y, fy, cshift, omega, stream=None):
+        _check(_lib.dks_filter(self._h, ik, _dptr(y), _dptr(fy), y.shape[0], float(cshift), float(omega),
+                               _prec_of(y), _stream(stream)))
+        return fy
+
+    def precond(self, ik, x, hx, lam, act, y, precond=PRECOND_TETER, stream=None):
+        _check(_lib.dks_precond(self._h, ik, _dptr(x), _dptr(hx), _dptr(lam), _dptr(act), act.shape[0],
+                                _dptr(y), precond, _prec_of(x), _stream(stream)))
+        return y
+
+    # ---- solver
+    def solve(self, x_list, nev, tol=1e-6, n_init=3, n_iter=200, mode=MODE_FP64, refine_tol=1e-3,
+              precond=PRECOND_TETER, use_filter=True, cshift=None, omega=None, nev_k=None, nbuf=0,
+              stream=None, check=True):
+        """Algorithm 1 on every k-point.  x_list[ik]: complex128 [nev_k+nbuf, 4, npw] (X0 in, X out).
+        Returns (eigenvalues per k as numpy arrays, report dict, status code)."""
+        opts = SolveOpts()
+        _lib.dks_solve_opts_default(C.byref(opts))
+        opts.n_init, opts.n_iter, opts.nbuf = int(n_init), int(n_iter), int(nbuf)
+        opts.C = float("nan") if cshift is None else float(cshift)
+        opts.Omega = float("nan") if omega is None else float(omega)
+        opts.mode, opts.refine_tol, opts.precond = int(mode), float(refine_tol), int(precond)
+        opts.use_filter = 1 if use_filter else 0
+        nevs = [int(nev)] * self.nk if nev_k is None else [int(v) for v in nev_k]
+        if nev_k is not None:
+            arr = np.ascontiguousarray(nevs, dtype=np.int32)
+            self._keep.append(arr)
+            opts.nev_k = arr.ctypes.data_as(C.POINTER(C.c_int))
+        opts.stream = _stream(stream)
+        eig = np.zeros(sum(nevs), dtype=np.float64)
+        ptrs = (C.c_void_p * self.nk)(*[t.data_ptr() for t in x_list])
+        rep = SolveReport()
+        rc = _lib.dks_lobpcgf_solve(self._h, int(nev), float(tol), C.byref(opts),
+                                    eig.ctypes.data_as(C.POINTER(C.c_double)), ptrs, C.byref(rep))
+        self._keep = []
+        if check and rc not in (0,):
+            _check(rc)
+        out, o = [], 0
+        for v in nevs:
+            out.append(eig[o:o + v].copy())
+            o += v
+        nk = min(self.nk, 64)
+        report = dict(iterations=list(rep.iterations[:nk]), fp64_iterations=list(rep.fp64_iterations[:nk]),
+                      max_residual=list(rep.max_residual[:nk]), h_applications=int(rep.h_applications),
+                      shift=rep.shift, seconds=rep.seconds, status=rep.status)
+        return out, report, rc
+
+
+# ---- single steps of Algorithm 1 (blocks are [ncol, rows] complex tensors)
+
+def gram(z, hz, a_out, s_out, stream=None):
+    load_library()
+    nz, rows = z.shape[0], z[0].numel()
+    _check(_lib.dks_gram(_dptr(z), _dptr(hz), rows, nz, _dptr(a_out), _dptr(s_out), _prec_of(z),
+                         _stream(stream)))
+
+
+def rayleigh_ritz(a, s, n, v_out, lam_out, info_out, stream=None):
+    load_library()
+    _check(_lib.dks_rayleigh_ritz(_dptr(a), _dptr(s), a.shape[0], int(n), _dptr(v_out), _dptr(lam_out),
+                                  _dptr(info_out), _stream(stream)))
+
+
+def rotate(z, w, n, out, beta=0.0, stream=None):
+    """out[j] = sum_i z[i] w[i, j] (+ beta out[j]); w complex128 (nz x n) stored column-major."""
+    load_library()
+    nz, rows = z.shape[0], z[0].numel()
+    ldw = w.shape[-1] if w.dim() == 2 else nz
+    _check(_lib.dks_rotate(_dptr(z), rows, nz, _dptr(w), ldw, int(n), _dptr(out), float(beta), _prec_of(z),
+                           _stream(stream)))
+
+
+def residual_norms(x, hx, lam, norms_out, stream=None):
+    load_library()
+    n, rows = x.shape[0], x[0].numel()
+    _check(_lib.dks_residual_norms(_dptr(x), _dptr(hx), _dptr(lam), rows, n, _dptr(norms_out), _prec_of(x),
+                                   _stream(stream)))

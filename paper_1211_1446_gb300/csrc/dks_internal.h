@@ -1,0 +1,140 @@
+// Internal declarations of the GB300 DKS / LOBPCG-F library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dks.h"
+
+namespace dks {
+
+constexpr int kMaxFftLen = 256;    // largest FFT axis length
+constexpr int kMaxRadix = 8;       // radices 2, 3, 4, 5, 7, 8
+constexpr int kMaxStages = 8;
+constexpr int kMaxRR = 512;        // largest Rayleigh-Ritz pencil
+
+// --------------------------------------------------------------- error state
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+#define DKS_CUDA_TRY(...)                                                                      \
+  do {                                                                                         \
+    cudaError_t e_ = (__VA_ARGS__);                                                            \
+    if (e_ != cudaSuccess)                                                                     \
+      return ::dks::fail(DKS_ERR_CUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define DKS_TRY(...)                 \
+  do {                               \
+    int r_ = (__VA_ARGS__);          \
+    if (r_ != DKS_OK) return r_;     \
+  } while (0)
+
+// --------------------------------------------------------------- FFT plans
+// Mixed-radix in-place plan of one axis.  DIF stages run s = 0..nst-1 on blocks
+// of length L_s (L_0 = N, L_{s+1} = L_s / R_s); DIT runs them in reverse.
+struct AxisPlan {
+  int n;
+  int nst;
+  int radix[kMaxStages];
+  int blk[kMaxStages];   // L_s
+};
+bool make_axis_plan(int n, AxisPlan* p);
+// position of frequency index k after the DIF stages (mixed-radix digit reversal)
+std::vector<int> dif_positions(const AxisPlan& p);
+
+// --------------------------------------------------------------- per-k basis
+struct KPoint {
+  int npw = 0;
+  int nsticks = 0;
+  double kcart[3] = {0, 0, 0};
+  double ecut = 0;
+  double qmax = 0;
+  std::vector<int> miller;      // host npw*3, canonical order
+  // device tables
+  int* stick_start = nullptr;   // nsticks+1, pw offsets
+  int* stick_plane = nullptr;   // nsticks, i1*N2 + i2 (natural frequency position)
+  int* pw_stick = nullptr;      // npw
+  int* pw_iz = nullptr;         // npw, i3 (natural)
+  double* q = nullptr;          // npw*3 cartesian k+G (FP64)
+  double* ek = nullptr;         // npw, |k+G|^2/2
+  double2* bt64 = nullptr;      // nproj x (2 npw) projector rows (beta, spin-major)
+  float2* bt32 = nullptr;
+  double cshift = 0, omega = 1; // default filter constants
+};
+
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace dks
+
+struct dks_ctx {
+  int grid[3] = {0, 0, 0};
+  int ng = 0;
+  double c = 137.036;
+  double lattice[9];
+  double recip[9];
+  double volume = 0;
+  int nk = 0;
+  dks::AxisPlan plan[3];
+  // device: twiddles exp(+2 pi i t / N_axis), t < N_axis
+  double2* tw64[3] = {nullptr, nullptr, nullptr};
+  float2* tw32[3] = {nullptr, nullptr, nullptr};
+  // device: V / Ng in DIF-permuted layout [p3][p1*N2 + p2]
+  double* vperm64 = nullptr;
+  float* vperm32 = nullptr;
+  double vmax = 0;
+  bool has_v = false;
+  // projectors
+  int nproj = 0;
+  double dsum = 0;
+  std::vector<double> dvec;     // host, per channel
+  double* dvec_dev = nullptr;
+  std::vector<dks::KPoint> k;
+  // scratch owned by the context (grown on demand)
+  dks::Workspace ws_h;          // apply_H grid intermediates + projector coefficients
+  dks::Workspace ws_solve;      // solver blocks
+  size_t chunk_budget = 64u << 20;   // bytes of FFT intermediates per chunk (L2-resident)
+  int device = 0;
+  int num_sms = 0;
+};
+
+namespace dks {
+
+int grow(Workspace& w, size_t bytes);
+void release(Workspace& w);
+
+// H' application on nb columns of k-point ik:
+//   out = scale * (H' x - shift * x)          (beta == 0)
+// x and out [nb][4][npw]; precision by template (double2 / float2).
+template <typename V>
+int apply_h(dks_ctx* ctx, int ik, const V* x, V* out, int nb, double shift, double scale,
+            cudaStream_t st);
+
+// kernels shared by the solver and the single-step entry points
+template <typename V>
+int gemm_hn(const V* a, int lda, const V* b, int ldb, int k, int m, int n, double2* c,
+            cudaStream_t st);  // c (m x n, col-major, ld m) = a^H b, accumulated in FP64 atomics
+template <typename V>
+int gemm_nn(const V* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
+            int n, V* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0);
+// out (k x n) = alpha * a (k x m) * (diag(wscale) w) + beta * out; wscale may be NULL
+template <typename V>
+int col_stats(const V* x, const V* hx, const double* lam, const double* ek, int npw, int n,
+              double* stats, cudaStream_t st);  // stats[3j..]: |hx - lam x|^2, |x|^2, sum ek|x|^2
+template <typename V>
+int precond_apply(const V* x, const V* hx, const double* lam, const double* stats, const int* act,
+                  int nact, const double* ek, int npw, int precond, V* y, cudaStream_t st);
+int rayleigh_ritz(const double2* a, const double2* s, int nz, int n, double2* v, double* lam,
+                  int* info, double2* scratch, cudaStream_t st);
+size_t rr_scratch_elems(int nz);
+template <typename Vi, typename Vo>
+int convert(const Vi* in, Vo* out, size_t n, cudaStream_t st);
+int gather_cols(const double2* v, int ldv, int row0, int rows, const int* act, int nact,
+                double2* out, cudaStream_t st);
+
+}  // namespace dks

@@ -1,0 +1,333 @@
+// H' x for the shifted valence DKS operator (Eq. vDKS, Sec. 3.1 "matrix-free Hx").
+//
+//   H' x = [[0, c s.q], [c s.q, -2c^2]] x          free Dirac term per planewave (Eq. 2)
+//        + FFT^-1 . V(r) . FFT x                     local potential, one grid per component
+//        + (I2 (x) B D B^H) x                         spin-orbit projectors (Eq. HGH)
+//
+// GPU layout.  x[band][comp][pw] with planewaves in canonical order, so each
+// (m1, m2) "stick" along the third axis is a contiguous run of planewaves.  The
+// 3D transform of one field (band, comp) runs in three passes that keep all
+// intermediates in a stick-compressed buffer T[field][p3][stick] sized to stay
+// resident in the 129 MB L2:
+//   pass A  scatter the stick into a zeroed length-N3 line in shared memory,
+//           inverse FFT along axis 3 (DIF, natural in -> digit-reversed out)
+//   pass B  one (field, plane) per CTA: scatter the sticks into an N1 x N2 plane
+//           in shared memory, inverse 2D FFT (DIF), multiply by V/Ng stored in
+//           the same digit-reversed order, forward 2D FFT (DIT, digit-reversed in
+//           -> natural out), gather the sticks back (in place in T)
+//   pass C  four components of one band per CTA: forward FFT along axis 3 (DIT),
+//           gather to the sphere, add the Dirac 4x4 term computed in FP64 and the
+//           optional filter shift, scale, store
+// Pairing DIF for the inverse with DIT for the forward transform removes every
+// digit-reversal permutation: the real-space planes simply live in permuted
+// order, and V is uploaded in that order.
+// The projector term is two tall-skinny contractions over 2*npw rows with
+// x viewed as [2*nb][2*npw] (large and small two-spinors as separate columns).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "dks_internal.h"
+#include "dks_kernels.cuh"
+
+namespace dks {
+
+// ---------------------------------------------------------------------------
+// one radix-R pass over a batch of lines held in shared memory (in place)
+// ---------------------------------------------------------------------------
+template <typename V, int R, bool DIT>
+__device__ __forceinline__ void fft_pass(V* buf, int nlines, int lstride, int estride, int n,
+                                         int L, const V* __restrict__ tw, bool fwd) {
+  const int S = L / R;
+  const int per_line = n / R;
+  const int total = nlines * per_line;
+  const int tstep = n / L;
+  const int rstep = n / R;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int line = t / per_line;
+    const int u = t - line * per_line;
+    const int blk = u / S;
+    const int j = u - blk * S;
+    V* base = buf + line * lstride + (blk * L + j) * estride;
+    V x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = base[r * S * estride];
+    if (DIT) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle(tw, j * r * tstep, fwd));
+    }
+    V y[R];
+    if (R == 2) {
+      y[0] = cadd(x[0], x[1]);
+      y[1] = csub(x[0], x[1]);
+    } else if (R == 4) {
+      // w4 = +i (inverse) or -i (forward)
+      V a = cadd(x[0], x[2]), b = csub(x[0], x[2]);
+      V c = cadd(x[1], x[3]), d = csub(x[1], x[3]);
+      V di = fwd ? mul_mi(d) : mul_i(d);
+      y[0] = cadd(a, c);
+      y[2] = csub(a, c);
+      y[1] = cadd(b, di);
+      y[3] = csub(b, di);
+    } else {
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        V acc = x[0];
+#pragma unroll
+        for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(x[r], twiddle(tw, ((r * m) % R) * rstep, fwd)));
+        y[m] = acc;
+      }
+    }
+    if (!DIT) {
+#pragma unroll
+      for (int m = 1; m < R; ++m) y[m] = cmul(y[m], twiddle(tw, j * m * tstep, fwd));
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) base[m * S * estride] = y[m];
+  }
+}
+
+template <typename V, bool DIT>
+__device__ void fft_lines(V* buf, int nlines, int lstride, int estride, const AxisPlan& p,
+                          const V* __restrict__ tw, bool fwd) {
+  for (int i = 0; i < p.nst; ++i) {
+    const int s = DIT ? (p.nst - 1 - i) : i;
+    const int R = p.radix[s];
+    const int L = p.blk[s];
+    switch (R) {
+      case 2: fft_pass<V, 2, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
+      case 3: fft_pass<V, 3, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
+      case 4: fft_pass<V, 4, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
+      case 5: fft_pass<V, 5, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
+      case 7: fft_pass<V, 7, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
+      default: fft_pass<V, 8, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass A: sphere -> stick lines, inverse FFT along axis 3
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void __launch_bounds__(256) k_stick_inverse(
+    const V* __restrict__ x, V* __restrict__ t, int npw, int nsticks, const int* __restrict__ stick_start,
+    const int* __restrict__ pw_stick, const int* __restrict__ pw_iz, AxisPlan p3,
+    const V* __restrict__ tw3, int spb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* line = reinterpret_cast<V*>(smem_raw);
+  const int n3 = p3.n;
+  const int s0 = blockIdx.x * spb;
+  const int ns = min(spb, nsticks - s0);
+  const int f = blockIdx.y;
+  for (int e = threadIdx.x; e < spb * n3; e += blockDim.x) line[e] = V{0, 0};
+  __syncthreads();
+  const V* xf = x + (size_t)f * npw;
+  const int q0 = stick_start[s0], q1 = stick_start[s0 + ns];
+  for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x)
+    line[(pw_stick[q] - s0) * n3 + pw_iz[q]] = xf[q];
+  __syncthreads();
+  fft_lines<V, false>(line, ns, n3, 1, p3, tw3, false);
+  V* tf = t + (size_t)f * n3 * nsticks;
+  for (int e = threadIdx.x; e < ns * n3; e += blockDim.x) {
+    const int z = e / ns, s = e - z * ns;
+    tf[(size_t)z * nsticks + s0 + s] = line[s * n3 + z];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass B: one plane of one field: 2D inverse FFT, x V/Ng, 2D forward FFT
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void __launch_bounds__(512) k_plane(V* __restrict__ t, int nsticks,
+                                               const int* __restrict__ stick_plane, AxisPlan p1,
+                                               AxisPlan p2, int n3, const V* __restrict__ tw1,
+                                               const V* __restrict__ tw2,
+                                               const typename RealOf<V>::T* __restrict__ vperm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* plane = reinterpret_cast<V*>(smem_raw);
+  const int n1 = p1.n, n2 = p2.n, nn = n1 * n2;
+  const int z = blockIdx.x, f = blockIdx.y;
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) plane[e] = V{0, 0};
+  __syncthreads();
+  V* row = t + ((size_t)f * n3 + z) * nsticks;
+  for (int s = threadIdx.x; s < nsticks; s += blockDim.x) plane[stick_plane[s]] = row[s];
+  __syncthreads();
+  fft_lines<V, false>(plane, n1, n2, 1, p2, tw2, false);   // along axis 2 (contiguous)
+  fft_lines<V, false>(plane, n2, 1, n2, p1, tw1, false);   // along axis 1
+  const typename RealOf<V>::T* vz = vperm + (size_t)z * nn;
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) plane[e] = cscale(plane[e], vz[e]);
+  __syncthreads();
+  fft_lines<V, true>(plane, n2, 1, n2, p1, tw1, true);
+  fft_lines<V, true>(plane, n1, n2, 1, p2, tw2, true);
+  for (int s = threadIdx.x; s < nsticks; s += blockDim.x) row[s] = plane[stick_plane[s]];
+}
+
+// ---------------------------------------------------------------------------
+// pass C: forward FFT along axis 3, gather, Dirac term (FP64), shift, scale
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void dirac4(const double2 xv[4], double qx, double qy, double qz, double c,
+                                       double diag_small, double shift, double2 h[4]) {
+  // [[0, c s.q], [c s.q, -2c^2]] x - shift x ;  s.q = [[qz, qx - i qy], [qx + i qy, -qz]]
+  const double2 qm = {c * qx, -c * qy};   // c (qx - i qy)
+  const double2 qp = {c * qx, c * qy};    // c (qx + i qy)
+  const double cz = c * qz;
+  double2 a = cmul(qm, xv[3]);
+  h[0] = {cz * xv[2].x + a.x - shift * xv[0].x, cz * xv[2].y + a.y - shift * xv[0].y};
+  a = cmul(qp, xv[2]);
+  h[1] = {a.x - cz * xv[3].x - shift * xv[1].x, a.y - cz * xv[3].y - shift * xv[1].y};
+  a = cmul(qm, xv[1]);
+  h[2] = {cz * xv[0].x + a.x + (diag_small - shift) * xv[2].x,
+          cz * xv[0].y + a.y + (diag_small - shift) * xv[2].y};
+  a = cmul(qp, xv[0]);
+  h[3] = {a.x - cz * xv[1].x + (diag_small - shift) * xv[3].x,
+          a.y - cz * xv[1].y + (diag_small - shift) * xv[3].y};
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_stick_forward(
+    const V* __restrict__ t, const V* __restrict__ x, V* __restrict__ out, int npw, int nsticks,
+    const int* __restrict__ stick_start, const int* __restrict__ pw_stick, const int* __restrict__ pw_iz,
+    AxisPlan p3, const V* __restrict__ tw3, const double* __restrict__ q, double c, double shift,
+    double scale, int spb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* line = reinterpret_cast<V*>(smem_raw);
+  const int n3 = p3.n;
+  const int s0 = blockIdx.x * spb;
+  const int ns = min(spb, nsticks - s0);
+  const int b = blockIdx.y;
+  for (int e = threadIdx.x; e < 4 * ns * n3; e += blockDim.x) {
+    const int a = e / (ns * n3);
+    const int rem = e - a * ns * n3;
+    const int z = rem / ns, s = rem - z * ns;
+    line[(a * spb + s) * n3 + z] = t[((size_t)(b * 4 + a) * n3 + z) * nsticks + s0 + s];
+  }
+  __syncthreads();
+  fft_lines<V, true>(line, 4 * spb, n3, 1, p3, tw3, true);
+  const size_t fo = (size_t)b * 4 * npw;
+  const int q0 = stick_start[s0], q1 = stick_start[s0 + ns];
+  const double diag_small = -2.0 * c * c;
+  for (int p = q0 + threadIdx.x; p < q1; p += blockDim.x) {
+    const int s = pw_stick[p] - s0, iz = pw_iz[p];
+    double2 xv[4], h[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) xv[a] = to_d2(x[fo + (size_t)a * npw + p]);
+    dirac4(xv, q[3 * p], q[3 * p + 1], q[3 * p + 2], c, diag_small, shift, h);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const double2 loc = to_d2(line[(a * spb + s) * n3 + iz]);
+      out[fo + (size_t)a * npw + p] = from_d2<V>({scale * (h[a].x + loc.x), scale * (h[a].y + loc.y)});
+    }
+  }
+}
+
+// Dirac term alone (no local potential on the grid)
+template <typename V>
+__global__ void k_dirac_only(const V* __restrict__ x, V* __restrict__ out, int npw, int nb,
+                             const double* __restrict__ q, double c, double shift, double scale) {
+  const size_t total = (size_t)nb * npw;
+  const double diag_small = -2.0 * c * c;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = e / npw;
+    const int p = (int)(e - b * npw);
+    const size_t fo = b * 4 * npw;
+    double2 xv[4], h[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) xv[a] = to_d2(x[fo + (size_t)a * npw + p]);
+    dirac4(xv, q[3 * p], q[3 * p + 1], q[3 * p + 2], c, diag_small, shift, h);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+      out[fo + (size_t)a * npw + p] = from_d2<V>({scale * h[a].x, scale * h[a].y});
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <typename V>
+static int set_smem(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return fail(DKS_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
+  }
+  return DKS_OK;
+}
+
+static int pick_spb(int n3, size_t elem, int lines_per_stick, size_t target) {
+  int spb = 32;
+  while (spb > 1 && (size_t)spb * n3 * elem * lines_per_stick > target) spb >>= 1;
+  return spb;
+}
+
+template <typename V>
+int apply_h(dks_ctx* ctx, int ik, const V* x, V* out, int nb, double shift, double scale,
+            cudaStream_t st) {
+  if (nb <= 0) return DKS_OK;
+  KPoint& kp = ctx->k[ik];
+  const int npw = kp.npw;
+  const bool fp64 = sizeof(V) == sizeof(double2);
+  const int n3 = ctx->grid[2];
+  const size_t zp_elems = (size_t)ctx->nproj * 2 * nb;
+  const size_t field_elems = (size_t)kp.nsticks * n3;
+  // chunk of bands whose intermediates stay within the L2-resident budget
+  int chunk = (int)std::max<size_t>(1, ctx->chunk_budget / (4 * field_elems * sizeof(V)));
+  chunk = std::min(chunk, nb);
+  const size_t need = zp_elems * sizeof(double2) + 256 + (ctx->has_v ? 4 * chunk * field_elems * sizeof(V) : 0);
+  DKS_TRY(grow(ctx->ws_h, need));
+  double2* zp = reinterpret_cast<double2*>(ctx->ws_h.ptr);
+  V* tbuf = reinterpret_cast<V*>(reinterpret_cast<char*>(ctx->ws_h.ptr) +
+                                 ((zp_elems * sizeof(double2) + 255) / 256) * 256);
+  const V* bt = nullptr;
+  if (ctx->nproj) {
+    bt = fp64 ? reinterpret_cast<const V*>(kp.bt64) : reinterpret_cast<const V*>(kp.bt32);
+    DKS_CUDA_TRY(cudaMemsetAsync(zp, 0, zp_elems * sizeof(double2), st));
+    // Z = B^H x~ : (nproj x 2npw) (2npw x 2nb)
+    DKS_TRY(gemm_hn<V>(bt, 2 * npw, x, 2 * npw, 2 * npw, ctx->nproj, 2 * nb, zp, st));
+  }
+  const V* tw1 = fp64 ? (const V*)ctx->tw64[0] : (const V*)ctx->tw32[0];
+  const V* tw2 = fp64 ? (const V*)ctx->tw64[1] : (const V*)ctx->tw32[1];
+  const V* tw3 = fp64 ? (const V*)ctx->tw64[2] : (const V*)ctx->tw32[2];
+  if (ctx->has_v) {
+    const int spb_a = pick_spb(n3, sizeof(V), 1, 32 * 1024);
+    const int spb_c = pick_spb(n3, sizeof(V), 4, 64 * 1024);
+    const size_t sm_a = (size_t)spb_a * n3 * sizeof(V);
+    const size_t sm_b = (size_t)ctx->grid[0] * ctx->grid[1] * sizeof(V);
+    const size_t sm_c = (size_t)4 * spb_c * n3 * sizeof(V);
+    DKS_TRY(set_smem<V>((const void*)k_stick_inverse<V>, sm_a));
+    DKS_TRY(set_smem<V>((const void*)k_plane<V>, sm_b));
+    DKS_TRY(set_smem<V>((const void*)k_stick_forward<V>, sm_c));
+    const typename RealOf<V>::T* vp =
+        fp64 ? (const typename RealOf<V>::T*)ctx->vperm64 : (const typename RealOf<V>::T*)ctx->vperm32;
+    for (int b0 = 0; b0 < nb; b0 += chunk) {
+      const int nbc = std::min(chunk, nb - b0);
+      const V* xb = x + (size_t)b0 * 4 * npw;
+      dim3 ga((kp.nsticks + spb_a - 1) / spb_a, 4 * nbc);
+      k_stick_inverse<V><<<ga, 256, sm_a, st>>>(xb, tbuf, npw, kp.nsticks, kp.stick_start, kp.pw_stick,
+                                                kp.pw_iz, ctx->plan[2], tw3, spb_a);
+      dim3 gb(n3, 4 * nbc);
+      k_plane<V><<<gb, 512, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0], ctx->plan[1], n3,
+                                        tw1, tw2, vp);
+      dim3 gc((kp.nsticks + spb_c - 1) / spb_c, nbc);
+      k_stick_forward<V><<<gc, 256, sm_c, st>>>(tbuf, xb, out + (size_t)b0 * 4 * npw, npw, kp.nsticks,
+                                                kp.stick_start, kp.pw_stick, kp.pw_iz, ctx->plan[2], tw3,
+                                                kp.q, ctx->c, shift, scale, spb_c);
+    }
+  } else {
+    const int blocks = std::max(1, std::min(ctx->num_sms * 8, (int)(((size_t)nb * npw + 255) / 256)));
+    k_dirac_only<V><<<blocks, 256, 0, st>>>(x, out, npw, nb, kp.q, ctx->c, shift, scale);
+  }
+  DKS_CUDA_TRY(cudaGetLastError());
+  if (ctx->nproj) {
+    // out~ += B (scale D Z)
+    DKS_TRY(gemm_nn<V>(bt, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, 2 * nb, out,
+                       2 * npw, 1.0, st, scale));
+  }
+  return DKS_OK;
+}
+
+template int apply_h<double2>(dks_ctx*, int, const double2*, double2*, int, double, double, cudaStream_t);
+template int apply_h<float2>(dks_ctx*, int, const float2*, float2*, int, double, double, cudaStream_t);
+
+}  // namespace dks

@@ -1,0 +1,333 @@
+// Block linear algebra of Algorithm 1 on tall-skinny complex blocks.
+//
+//  gemm_hn   C (m x n) += A^H B   A: k x m, B: k x n (k = 4 npw or 2 npw, huge; m, n small)
+//            Gram matrices of lines 12-13 and the projector coefficients B^H x~.
+//            Split over k across the grid; each CTA reduces a 32x32 tile of C over its
+//            k-range in registers and adds it to C with FP64 atomics.
+//  gemm_nn   OUT (k x n) = alpha A (k x m) diag(ws) W (m x n) + beta OUT
+//            Rotations X <- Z V, P <- [0,Y,P] V (lines 15, 22) and the projector
+//            update x~ += B (D Z).  W (FP64, from the small solve) is staged in shared
+//            memory in the working precision.
+//  col_stats per column: ||hx - lam x||^2, ||x||^2 and sum_G |k+G|^2/2 |x|^2 (FP64)
+//  precond   Y = K(x_G) (HX - lam X) on the active columns (lines 9 and 16 fused)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "dks_internal.h"
+#include "dks_kernels.cuh"
+
+namespace dks {
+
+template <typename V> struct Acc;
+template <> struct Acc<double2> { using T = double2; };
+template <> struct Acc<float2> { using T = float2; };
+
+// ---------------------------------------------------------------- gemm_hn
+constexpr int HN_T = 32;
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_gemm_hn(const V* __restrict__ a, int lda, const V* __restrict__ b,
+                                                 int ldb, int k, int m, int n, int mt, int kchunk,
+                                                 double2* __restrict__ c) {
+  __shared__ V as[HN_T][HN_T + 1];
+  __shared__ V bs[HN_T][HN_T + 1];
+  const int tile = blockIdx.x;
+  const int m0 = (tile % mt) * HN_T, n0 = (tile / mt) * HN_T;
+  const int kb = blockIdx.y * kchunk;
+  const int ke = min(k, kb + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  using A = typename Acc<V>::T;
+  A acc[2][2] = {{A{0, 0}, A{0, 0}}, {A{0, 0}, A{0, 0}}};
+  for (int k0 = kb; k0 < ke; k0 += HN_T) {
+    for (int e = threadIdx.x; e < HN_T * HN_T; e += 256) {
+      const int kq = e & (HN_T - 1), q = e >> 5;
+      const int gk = k0 + kq;
+      V va{0, 0}, vb{0, 0};
+      if (gk < ke) {
+        if (m0 + q < m) va = a[(size_t)(m0 + q) * lda + gk];
+        if (n0 + q < n) vb = b[(size_t)(n0 + q) * ldb + gk];
+      }
+      as[kq][q] = va;
+      bs[kq][q] = vb;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kq = 0; kq < HN_T; ++kq) {
+      const V a0 = as[kq][ty], a1 = as[kq][ty + 16];
+      const V b0 = bs[kq][tx], b1 = bs[kq][tx + 16];
+      acc[0][0] = cadd(acc[0][0], cmulc(a0, b0));
+      acc[0][1] = cadd(acc[0][1], cmulc(a0, b1));
+      acc[1][0] = cadd(acc[1][0], cmulc(a1, b0));
+      acc[1][1] = cadd(acc[1][1], cmulc(a1, b1));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int mm = m0 + ty + 16 * i, nn = n0 + tx + 16 * j;
+      if (mm < m && nn < n) {
+        atomicAdd(&c[(size_t)nn * m + mm].x, (double)acc[i][j].x);
+        atomicAdd(&c[(size_t)nn * m + mm].y, (double)acc[i][j].y);
+      }
+    }
+}
+
+static int g_num_sms = 0;
+static int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+template <typename V>
+int gemm_hn(const V* a, int lda, const V* b, int ldb, int k, int m, int n, double2* c, cudaStream_t st) {
+  if (m <= 0 || n <= 0 || k <= 0) return DKS_OK;
+  const int mt = (m + HN_T - 1) / HN_T, nt = (n + HN_T - 1) / HN_T;
+  const int ktiles = (k + HN_T - 1) / HN_T;
+  int splits = std::max(1, (4 * num_sms()) / (mt * nt));
+  splits = std::min(splits, ktiles);
+  const int kchunk = ((ktiles + splits - 1) / splits) * HN_T;
+  splits = (k + kchunk - 1) / kchunk;
+  dim3 grid(mt * nt, splits);
+  k_gemm_hn<V><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c);
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
+}
+
+// ---------------------------------------------------------------- gemm_nn
+constexpr int NN_R = 64, NN_C = 32, NN_M = 16;
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_gemm_nn(const V* __restrict__ a, int lda, int k, int m,
+                                                 const double2* __restrict__ w, int ldw,
+                                                 const double* __restrict__ ws, int n, V* __restrict__ out,
+                                                 int ldo, double alpha, double beta) {
+  __shared__ V as[NN_M][NN_R];
+  __shared__ V wsm[NN_M][NN_C];
+  const int r0 = blockIdx.x * NN_R, c0 = blockIdx.y * NN_C;
+  const int row = threadIdx.x & (NN_R - 1), cg = threadIdx.x >> 6;
+  using A = typename Acc<V>::T;
+  A acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = A{0, 0};
+  for (int m0 = 0; m0 < m; m0 += NN_M) {
+    for (int e = threadIdx.x; e < NN_M * NN_R; e += 256) {
+      const int rr = e & (NN_R - 1), mm = e >> 6;
+      V v{0, 0};
+      if (m0 + mm < m && r0 + rr < k) v = a[(size_t)(m0 + mm) * lda + r0 + rr];
+      as[mm][rr] = v;
+    }
+    for (int e = threadIdx.x; e < NN_M * NN_C; e += 256) {
+      const int cc = e & (NN_C - 1), mm = e >> 5;
+      double2 v{0, 0};
+      if (m0 + mm < m && c0 + cc < n) {
+        v = w[(size_t)(c0 + cc) * ldw + m0 + mm];
+        const double s = (ws ? ws[m0 + mm] : 1.0) * alpha;
+        v.x *= s;
+        v.y *= s;
+      }
+      wsm[mm][cc] = from_d2<V>(v);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int mm = 0; mm < NN_M; ++mm) {
+      const V av = as[mm][row];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = cadd(acc[j], cmul(av, wsm[mm][cg * 8 + j]));
+    }
+    __syncthreads();
+  }
+  if (r0 + row < k) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int cc = c0 + cg * 8 + j;
+      if (cc < n) {
+        V* o = out + (size_t)cc * ldo + r0 + row;
+        V r = acc[j];
+        if (beta != 0.0) {
+          const V old = *o;
+          r.x += (typename RealOf<V>::T)beta * old.x;
+          r.y += (typename RealOf<V>::T)beta * old.y;
+        }
+        *o = r;
+      }
+    }
+  }
+}
+
+template <typename V>
+int gemm_nn(const V* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
+            V* out, int ldo, double beta, cudaStream_t st, double alpha) {
+  if (k <= 0 || n <= 0) return DKS_OK;
+  dim3 grid((k + NN_R - 1) / NN_R, (n + NN_C - 1) / NN_C);
+  k_gemm_nn<V><<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
+}
+
+// ---------------------------------------------------------------- column statistics
+template <typename V>
+__global__ void __launch_bounds__(256) k_col_stats(const V* __restrict__ x, const V* __restrict__ hx,
+                                                   const double* __restrict__ lam,
+                                                   const double* __restrict__ ek, int npw,
+                                                   double* __restrict__ stats) {
+  const int j = blockIdx.x;
+  const size_t rows = (size_t)4 * npw;
+  const V* xj = x + (size_t)j * rows;
+  const V* hj = hx ? hx + (size_t)j * rows : nullptr;
+  const double l = lam ? lam[j] : 0.0;
+  double s0 = 0, s1 = 0, s2 = 0;
+  for (size_t e = threadIdx.x; e < rows; e += blockDim.x) {
+    const double2 xv = to_d2(xj[e]);
+    const double ax = xv.x * xv.x + xv.y * xv.y;
+    if (hj) {
+      const double2 hv = to_d2(hj[e]);
+      const double rx = hv.x - l * xv.x, ry = hv.y - l * xv.y;
+      s0 += rx * rx + ry * ry;
+    }
+    s1 += ax;
+    s2 += ek[e % npw] * ax;
+  }
+  __shared__ double red[3][32];
+  for (int off = 16; off; off >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, off);
+    s1 += __shfl_down_sync(0xffffffffu, s1, off);
+    s2 += __shfl_down_sync(0xffffffffu, s2, off);
+  }
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  if (ln == 0) {
+    red[0][w] = s0;
+    red[1][w] = s1;
+    red[2][w] = s2;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    s0 = ln < nw ? red[0][ln] : 0;
+    s1 = ln < nw ? red[1][ln] : 0;
+    s2 = ln < nw ? red[2][ln] : 0;
+    for (int off = 16; off; off >>= 1) {
+      s0 += __shfl_down_sync(0xffffffffu, s0, off);
+      s1 += __shfl_down_sync(0xffffffffu, s1, off);
+      s2 += __shfl_down_sync(0xffffffffu, s2, off);
+    }
+    if (ln == 0) {
+      stats[3 * j] = s0;
+      stats[3 * j + 1] = s1;
+      stats[3 * j + 2] = s2;
+    }
+  }
+}
+
+template <typename V>
+int col_stats(const V* x, const V* hx, const double* lam, const double* ek, int npw, int n, double* stats,
+              cudaStream_t st) {
+  if (n <= 0) return DKS_OK;
+  k_col_stats<V><<<n, 256, 0, st>>>(x, hx, lam, ek, npw, stats);
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
+}
+
+// ---------------------------------------------------------------- Teter preconditioner
+template <typename V>
+__global__ void k_precond(const V* __restrict__ x, const V* __restrict__ hx, const double* __restrict__ lam,
+                          const double* __restrict__ stats, const int* __restrict__ act, int nact,
+                          const double* __restrict__ ek, int npw, int precond, V* __restrict__ y) {
+  using T = typename RealOf<V>::T;
+  const size_t rows = (size_t)4 * npw;
+  const size_t total = rows * nact;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / rows);
+    const size_t rr = e - (size_t)i * rows;
+    const int j = act[i];
+    const size_t src = (size_t)j * rows + rr;
+    const T l = (T)lam[j];
+    const V xv = x[src], hv = hx[src];
+    V r{hv.x - l * xv.x, hv.y - l * xv.y};
+    if (precond == DKS_PRECOND_TETER) {
+      double tb = stats[3 * j + 2] / fmax(stats[3 * j + 1], 1e-300);
+      tb = fmax(tb, 1e-12);
+      const T xx = (T)(ek[rr % npw] / tb);
+      const T p = (T)27 + xx * ((T)18 + xx * ((T)12 + xx * (T)8));
+      const T x2 = xx * xx;
+      const T kf = p / (p + (T)16 * x2 * x2);
+      r.x *= kf;
+      r.y *= kf;
+    }
+    y[(size_t)i * rows + rr] = r;
+  }
+}
+
+template <typename V>
+int precond_apply(const V* x, const V* hx, const double* lam, const double* stats, const int* act, int nact,
+                  const double* ek, int npw, int precond, V* y, cudaStream_t st) {
+  if (nact <= 0) return DKS_OK;
+  const size_t total = (size_t)4 * npw * nact;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)num_sms() * 16);
+  k_precond<V><<<blocks, 256, 0, st>>>(x, hx, lam, stats, act, nact, ek, npw, precond, y);
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
+}
+
+// ---------------------------------------------------------------- conversions and gathers
+template <typename Vi, typename Vo>
+__global__ void k_convert(const Vi* __restrict__ in, Vo* __restrict__ out, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = from_d2<Vo>(to_d2(in[e]));
+}
+
+template <typename Vi, typename Vo>
+int convert(const Vi* in, Vo* out, size_t n, cudaStream_t st) {
+  if (!n) return DKS_OK;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 16);
+  k_convert<Vi, Vo><<<blocks, 256, 0, st>>>(in, out, n);
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
+}
+
+__global__ void k_gather_cols(const double2* __restrict__ v, int ldv, int row0, int rows,
+                              const int* __restrict__ act, int nact, double2* __restrict__ out) {
+  const int total = rows * nact;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int i = e / rows, r = e - i * rows;
+    out[e] = v[(size_t)act[i] * ldv + row0 + r];
+  }
+}
+
+int gather_cols(const double2* v, int ldv, int row0, int rows, const int* act, int nact, double2* out,
+                cudaStream_t st) {
+  if (rows <= 0 || nact <= 0) return DKS_OK;
+  const int total = rows * nact;
+  k_gather_cols<<<std::min((total + 255) / 256, 1024), 256, 0, st>>>(v, ldv, row0, rows, act, nact, out);
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
+}
+
+// explicit instantiations
+template int gemm_hn<double2>(const double2*, int, const double2*, int, int, int, int, double2*, cudaStream_t);
+template int gemm_hn<float2>(const float2*, int, const float2*, int, int, int, int, double2*, cudaStream_t);
+template int gemm_nn<double2>(const double2*, int, int, int, const double2*, int, const double*, int, double2*,
+                              int, double, cudaStream_t, double);
+template int gemm_nn<float2>(const float2*, int, int, int, const double2*, int, const double*, int, float2*, int,
+                             double, cudaStream_t, double);
+template int col_stats<double2>(const double2*, const double2*, const double*, const double*, int, int, double*,
+                                cudaStream_t);
+template int col_stats<float2>(const float2*, const float2*, const double*, const double*, int, int, double*,
+                               cudaStream_t);
+template int precond_apply<double2>(const double2*, const double2*, const double*, const double*, const int*, int,
+                                    const double*, int, int, double2*, cudaStream_t);
+template int precond_apply<float2>(const float2*, const float2*, const double*, const double*, const int*, int,
+                                   const double*, int, int, float2*, cudaStream_t);
+template int convert<double2, float2>(const double2*, float2*, size_t, cudaStream_t);
+template int convert<float2, double2>(const float2*, double2*, size_t, cudaStream_t);
+template int convert<double2, double2>(const double2*, double2*, size_t, cudaStream_t);
+
+}  // namespace dks

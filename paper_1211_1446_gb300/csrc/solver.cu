@@ -1,0 +1,352 @@
+// Algorithm 1 (LOBPCG-F) driver on the device.
+//
+// Per k-point the blocks Z = [X | Y | P] and HZ = [HX | HY | HP] live in two
+// ping-pong column buffers of capacity 3n columns (n = nev + nbuf), each column
+// 4 npw complex values.  One iteration:
+//   Y  = K(x_G) (HX - X Lambda) on the active columns           (lines 9, 16)
+//   Y  = f(H) Y      two H' passes with shift C and scale 1/Omega (line 10)
+//   HY = H' Y                                                     (one H' pass)
+//   A = Z^H HZ, S = Z^H Z, FP64 Rayleigh-Ritz, first n pairs      (lines 11-14)
+//   X, HX <- Z V, HZ V into the other buffer                       (line 15)
+//   column norms of HX - X Lambda (FP64), host reads them          (lines 16-19)
+//   P, HP <- [0, Y, P] V_active, HZ likewise                        (lines 20-22)
+// so H' is applied 3 times per active column per iteration (Sec. 3.2).
+//
+// DKS_MODE_MIXED runs the same loop with complex64 blocks (FP32 H', Gram and
+// rotations; FP64 small problem and norms) until the largest residual drops
+// below refine_tol or stops improving, then restarts Algorithm 1 in FP64 from
+// that X with N_init = 1 -- the paper's warm start (Sec. 3.1: N_init = 1 when X0
+// is a previous solution), which also removes the negative-band noise that FP32
+// rounding leaves in X.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "dks_internal.h"
+
+namespace dks {
+
+template <typename V>
+struct Blocks {
+  V* z[2];
+  V* hz[2];
+  V* tmp;
+};
+
+struct Small {
+  double2* a;
+  double2* s;
+  double2* vm;
+  double2* vp;
+  double* lam;
+  double* stats;
+  int* act;
+  int* info;
+  double2* rrs;
+};
+
+struct PhaseOut {
+  int iterations = 0;
+  bool converged = false;
+  double max_res = 0;
+  long long happ = 0;
+  bool neg = false;
+  int cur = 0;
+};
+
+struct Pinned {
+  double* lam = nullptr;
+  double* stats = nullptr;
+  int* act = nullptr;
+  int* info = nullptr;
+  int n = 0;
+  ~Pinned() {
+    if (lam) cudaFreeHost(lam);
+    if (stats) cudaFreeHost(stats);
+    if (act) cudaFreeHost(act);
+    if (info) cudaFreeHost(info);
+  }
+  int alloc(int nn) {
+    n = nn;
+    DKS_CUDA_TRY(cudaMallocHost((void**)&lam, nn * sizeof(double)));
+    DKS_CUDA_TRY(cudaMallocHost((void**)&stats, 3 * nn * sizeof(double)));
+    DKS_CUDA_TRY(cudaMallocHost((void**)&act, nn * sizeof(int)));
+    DKS_CUDA_TRY(cudaMallocHost((void**)&info, 4 * sizeof(int)));
+    return DKS_OK;
+  }
+};
+
+template <typename V>
+static int filter_inplace(dks_ctx* ctx, int ik, V* y, V* tmp, int nb, double C, double om, cudaStream_t st) {
+  DKS_TRY(apply_h<V>(ctx, ik, y, tmp, nb, C, 1.0 / om, st));
+  return apply_h<V>(ctx, ik, tmp, y, nb, C, 1.0 / om, st);
+}
+
+template <typename V>
+static int gram(const V* z, const V* hz, int rows, int nz, Small& sm, cudaStream_t st) {
+  DKS_CUDA_TRY(cudaMemsetAsync(sm.a, 0, (size_t)nz * nz * sizeof(double2), st));
+  DKS_CUDA_TRY(cudaMemsetAsync(sm.s, 0, (size_t)nz * nz * sizeof(double2), st));
+  DKS_TRY(gemm_hn<V>(z, rows, hz, rows, rows, nz, nz, sm.a, st));
+  return gemm_hn<V>(z, rows, z, rows, rows, nz, nz, sm.s, st);
+}
+
+// reads lam and residual statistics of the n columns; returns the host residual norms
+static int fetch(Small& sm, Pinned& pin, int n, std::vector<double>& res, cudaStream_t st) {
+  DKS_CUDA_TRY(cudaMemcpyAsync(pin.lam, sm.lam, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DKS_CUDA_TRY(cudaMemcpyAsync(pin.stats, sm.stats, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DKS_CUDA_TRY(cudaMemcpyAsync(pin.info, sm.info, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  DKS_CUDA_TRY(cudaStreamSynchronize(st));
+  res.resize(n);
+  for (int j = 0; j < n; ++j) res[j] = std::sqrt(pin.stats[3 * j] / std::max(pin.stats[3 * j + 1], 1e-300));
+  return DKS_OK;
+}
+
+template <typename V>
+static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int n, int nconv, double tol,
+                 int n_init, int n_iter, double C, double om, int precond, int use_filter, bool stop_on_stall,
+                 PhaseOut& out, cudaStream_t st) {
+  const KPoint& kp = ctx->k[ik];
+  const int rows = 4 * kp.npw;
+  const size_t colsz = (size_t)rows;
+  int cur = out.cur;
+  long long happ = 0;
+  // lines 1-3: initial filtering
+  if (use_filter)
+    for (int i = 0; i < n_init; ++i) {
+      DKS_TRY(filter_inplace<V>(ctx, ik, b.z[cur], b.tmp, n, C, om, st));
+      happ += 2LL * n;
+    }
+  // line 4-6: Rayleigh-Ritz on X0
+  DKS_TRY(apply_h<V>(ctx, ik, b.z[cur], b.hz[cur], n, 0.0, 1.0, st));
+  happ += n;
+  DKS_TRY(gram<V>(b.z[cur], b.hz[cur], rows, n, sm, st));
+  DKS_TRY(rayleigh_ritz(sm.a, sm.s, n, n, sm.vm, sm.lam, sm.info, sm.rrs, st));
+  int nx = cur ^ 1;
+  DKS_TRY(gemm_nn<V>(b.z[cur], rows, rows, n, sm.vm, n, nullptr, n, b.z[nx], rows, 0.0, st));
+  DKS_TRY(gemm_nn<V>(b.hz[cur], rows, rows, n, sm.vm, n, nullptr, n, b.hz[nx], rows, 0.0, st));
+  cur = nx;
+  DKS_TRY(col_stats<V>(b.z[cur], b.hz[cur], sm.lam, kp.ek, kp.npw, n, sm.stats, st));
+  std::vector<double> res;
+  DKS_TRY(fetch(sm, pin, n, res, st));
+  if (pin.info[1] < n) return fail(DKS_ERR_RANK, "initial block is rank deficient");
+  std::vector<int> act;
+  for (int j = 0; j < n; ++j) act.push_back(j);   // line 9 uses every column of R first
+  int p = 0;
+  double best = INFINITY;
+  int since_best = 0;
+  bool converged = false;
+  int it = 0;
+  double maxres = 0;
+  // device copy of the active list; refreshed after every soft-locking step below
+  std::memcpy(pin.act, act.data(), act.size() * sizeof(int));
+  DKS_CUDA_TRY(cudaMemcpyAsync(sm.act, pin.act, act.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  for (it = 1; it <= n_iter; ++it) {
+    const int a = (int)act.size();
+    V* y = b.z[cur] + (size_t)n * colsz;
+    V* hy = b.hz[cur] + (size_t)n * colsz;
+    DKS_TRY(precond_apply<V>(b.z[cur], b.hz[cur], sm.lam, sm.stats, sm.act, a, kp.ek, kp.npw, precond, y, st));
+    if (use_filter) {
+      DKS_TRY(filter_inplace<V>(ctx, ik, y, b.tmp, a, C, om, st));
+      happ += 2LL * a;
+    }
+    DKS_TRY(apply_h<V>(ctx, ik, y, hy, a, 0.0, 1.0, st));
+    happ += a;
+    const int nz = n + a + p;
+    DKS_TRY(gram<V>(b.z[cur], b.hz[cur], rows, nz, sm, st));
+    DKS_TRY(rayleigh_ritz(sm.a, sm.s, nz, n, sm.vm, sm.lam, sm.info, sm.rrs, st));
+    nx = cur ^ 1;
+    DKS_TRY(gemm_nn<V>(b.z[cur], rows, rows, nz, sm.vm, nz, nullptr, n, b.z[nx], rows, 0.0, st));
+    DKS_TRY(gemm_nn<V>(b.hz[cur], rows, rows, nz, sm.vm, nz, nullptr, n, b.hz[nx], rows, 0.0, st));
+    DKS_TRY(col_stats<V>(b.z[nx], b.hz[nx], sm.lam, kp.ek, kp.npw, n, sm.stats, st));
+    DKS_TRY(fetch(sm, pin, n, res, st));
+    if (pin.info[1] < n) return fail(DKS_ERR_RANK, "Rayleigh-Ritz subspace rank below the block size");
+    maxres = 0;
+    for (int j = 0; j < nconv; ++j) maxres = std::max(maxres, res[j]);
+    if (!std::isfinite(maxres)) return fail(DKS_ERR_NOT_CONVERGED, "non-finite residual norm");
+    if (maxres < tol) {
+      cur = nx;
+      converged = true;
+      break;
+    }
+    if (stop_on_stall) {
+      if (maxres < 0.7 * best) {
+        best = maxres;
+        since_best = 0;
+      } else if (++since_best >= 4) {
+        cur = nx;
+        break;
+      }
+    }
+    // lines 20-22: soft locking, P <- [0, Y, P] V_active
+    std::vector<int> act2;
+    for (int j = 0; j < n; ++j)
+      if (res[j] > tol) act2.push_back(j);
+    const int a2 = (int)act2.size();
+    std::memcpy(pin.act, act2.data(), a2 * sizeof(int));
+    DKS_CUDA_TRY(cudaMemcpyAsync(sm.act, pin.act, a2 * sizeof(int), cudaMemcpyHostToDevice, st));
+    DKS_TRY(gather_cols(sm.vm, nz, n, nz - n, sm.act, a2, sm.vp, st));
+    V* pz = b.z[nx] + (size_t)(n + a2) * colsz;
+    V* phz = b.hz[nx] + (size_t)(n + a2) * colsz;
+    DKS_TRY(gemm_nn<V>(b.z[cur] + (size_t)n * colsz, rows, rows, nz - n, sm.vp, nz - n, nullptr, a2, pz, rows, 0.0, st));
+    DKS_TRY(gemm_nn<V>(b.hz[cur] + (size_t)n * colsz, rows, rows, nz - n, sm.vp, nz - n, nullptr, a2, phz, rows, 0.0,
+                       st));
+    // the Teter factor of the next iteration needs statistics of the new X (already in sm.stats)
+    cur = nx;
+    act.swap(act2);
+    p = a2;
+  }
+  out.iterations = std::min(it, n_iter);
+  out.converged = converged;
+  out.max_res = maxres;
+  out.happ = happ;
+  out.cur = cur;
+  out.neg = pin.lam[0] < -ctx->c * ctx->c;
+  return DKS_OK;
+}
+
+}  // namespace dks
+
+using namespace dks;
+
+extern "C" {
+
+void dks_solve_opts_default(dks_solve_opts* o) {
+  if (!o) return;
+  o->n_init = 3;
+  o->n_iter = 200;
+  o->nbuf = 0;
+  o->C = NAN;
+  o->Omega = NAN;
+  o->mode = DKS_MODE_FP64;
+  o->refine_tol = 1e-3;
+  o->precond = DKS_PRECOND_TETER;
+  o->use_filter = 1;
+  o->nev_k = nullptr;
+  o->stream = nullptr;
+}
+
+int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* opts_in, double* eig, void* const* X,
+                      dks_solve_report* report) {
+  auto t0 = std::chrono::steady_clock::now();
+  dks_solve_opts opts;
+  if (opts_in) opts = *opts_in;
+  else dks_solve_opts_default(&opts);
+  if (!ctx || !eig || !X || !(tol > 0) || opts.n_init < 0 || opts.n_iter < 0 || opts.nbuf < 0 ||
+      (opts.mode != DKS_MODE_FP64 && opts.mode != DKS_MODE_MIXED))
+    return fail(DKS_ERR_INVALID_ARG, "dks_lobpcgf_solve: bad argument");
+  cudaStream_t st = (cudaStream_t)opts.stream;
+  if (report) {
+    std::memset(report, 0, sizeof(*report));
+    report->shift = ctx->c * ctx->c;
+  }
+  // sizes
+  int nmax = 0, rowsmax = 0;
+  for (int ik = 0; ik < ctx->nk; ++ik) {
+    const int nv = opts.nev_k ? opts.nev_k[ik] : nev;
+    if (nv <= 0 || !X[ik]) return fail(DKS_ERR_INVALID_ARG, "dks_lobpcgf_solve: nev_k and X[ik] required");
+    const int n = nv + opts.nbuf;
+    if (3 * n > kMaxRR) return fail(DKS_ERR_UNSUPPORTED, "block wider than the Rayleigh-Ritz limit (3n <= 512)");
+    if (n > ctx->k[ik].npw * 4) return fail(DKS_ERR_INVALID_ARG, "block wider than the basis");
+    nmax = std::max(nmax, n);
+    rowsmax = std::max(rowsmax, 4 * ctx->k[ik].npw);
+  }
+  const bool mixed = opts.mode == DKS_MODE_MIXED;
+  const size_t cols = (size_t)3 * nmax;
+  const size_t big64 = cols * rowsmax * sizeof(double2);
+  const size_t big32 = mixed ? cols * rowsmax * sizeof(float2) : 0;
+  const size_t tmp64 = (size_t)nmax * rowsmax * sizeof(double2);
+  const size_t tmp32 = mixed ? (size_t)nmax * rowsmax * sizeof(float2) : 0;
+  const size_t nz = 3 * nmax;
+  const size_t small = (2 * nz * nz + 2 * nz * nmax + rr_scratch_elems((int)nz)) * sizeof(double2) +
+                       (nmax + 3 * nmax) * sizeof(double) + (nmax + 4) * sizeof(int) + 16 * 256;
+  const size_t total = 4 * big64 + tmp64 + 4 * big32 + tmp32 + small + 16 * 256;
+  DKS_TRY(grow(ctx->ws_solve, total));
+  char* base = reinterpret_cast<char*>(ctx->ws_solve.ptr);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    void* p = base + off;
+    off += (bytes + 255) / 256 * 256;
+    return p;
+  };
+  Blocks<double2> b64;
+  b64.z[0] = (double2*)take(big64);
+  b64.z[1] = (double2*)take(big64);
+  b64.hz[0] = (double2*)take(big64);
+  b64.hz[1] = (double2*)take(big64);
+  b64.tmp = (double2*)take(tmp64);
+  Blocks<float2> b32{};
+  if (mixed) {
+    b32.z[0] = (float2*)take(big32);
+    b32.z[1] = (float2*)take(big32);
+    b32.hz[0] = (float2*)take(big32);
+    b32.hz[1] = (float2*)take(big32);
+    b32.tmp = (float2*)take(tmp32);
+  }
+  Small sm;
+  sm.a = (double2*)take(nz * nz * sizeof(double2));
+  sm.s = (double2*)take(nz * nz * sizeof(double2));
+  sm.vm = (double2*)take(nz * nmax * sizeof(double2));
+  sm.vp = (double2*)take(nz * nmax * sizeof(double2));
+  sm.rrs = (double2*)take(rr_scratch_elems((int)nz) * sizeof(double2));
+  sm.lam = (double*)take(nmax * sizeof(double));
+  sm.stats = (double*)take(3 * nmax * sizeof(double));
+  sm.act = (int*)take(nmax * sizeof(int));
+  sm.info = (int*)take(4 * sizeof(int));
+  Pinned pin;
+  DKS_TRY(pin.alloc(nmax));
+
+  int status = DKS_OK;
+  size_t eoff = 0;
+  for (int ik = 0; ik < ctx->nk; ++ik) {
+    const KPoint& kp = ctx->k[ik];
+    const int nv = opts.nev_k ? opts.nev_k[ik] : nev;
+    const int n = nv + opts.nbuf;
+    const size_t elems = (size_t)n * 4 * kp.npw;
+    const double C = std::isnan(opts.C) ? kp.cshift : opts.C;
+    const double om = std::isnan(opts.Omega) ? kp.omega : opts.Omega;
+    PhaseOut o32, o64;
+    if (mixed) {
+      DKS_TRY(convert<double2, float2>((const double2*)X[ik], b32.z[0], elems, st));
+      o32.cur = 0;
+      DKS_TRY(phase<float2>(ctx, ik, b32, sm, pin, n, nv, std::max(opts.refine_tol, tol), opts.n_init, opts.n_iter,
+                            C, om, opts.precond, opts.use_filter, true, o32, st));
+      DKS_TRY(convert<float2, double2>(b32.z[o32.cur], b64.z[0], elems, st));
+      o64.cur = 0;
+      const int left = std::max(0, opts.n_iter - o32.iterations);
+      DKS_TRY(phase<double2>(ctx, ik, b64, sm, pin, n, nv, tol, opts.use_filter ? 1 : 0, left, C, om, opts.precond,
+                             opts.use_filter, false, o64, st));
+    } else {
+      DKS_CUDA_TRY(cudaMemcpyAsync(b64.z[0], X[ik], elems * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      o64.cur = 0;
+      DKS_TRY(phase<double2>(ctx, ik, b64, sm, pin, n, nv, tol, opts.n_init, opts.n_iter, C, om, opts.precond,
+                             opts.use_filter, false, o64, st));
+    }
+    DKS_CUDA_TRY(cudaMemcpyAsync(X[ik], b64.z[o64.cur], elems * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    DKS_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int j = 0; j < nv; ++j) eig[eoff + j] = pin.lam[j];
+    eoff += nv;
+    if (report) {
+      if (ik < 64) {
+        report->iterations[ik] = o32.iterations + o64.iterations;
+        report->fp64_iterations[ik] = o64.iterations;
+        report->max_residual[ik] = o64.max_res;
+      }
+      report->h_applications += o32.happ + o64.happ;
+    }
+    if (status == DKS_OK) {
+      if (o64.neg) status = fail(DKS_ERR_NEG_STATE, "a returned eigenvalue lies below the gap midpoint");
+      else if (!o64.converged) status = fail(DKS_ERR_NOT_CONVERGED, "n_iter exhausted");
+    }
+  }
+  if (report) {
+    report->status = status;
+    report->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+}  // extern "C"
