@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Benchmark: time to the nev lowest positive-energy DKS eigenpairs with LOBPCG-F on one GB300.
+
+One step = one full solve of Algorithm 1 (N_init = 3 filter steps on a seed-fixed start
+block, then iterations until every residual norm ||H'x - lambda x|| < 1e-6, eigenvalues
+copied to the host) on the dimer workload: 20x20x24 bohr box, 48x48x56 FFT grid,
+Ecut 25 Ha (57,419 planewaves, dimension 229,676), two Gaussian-smeared sites 4.5 bohr
+apart with 36 spin-orbit projector channels, Gamma point, nev = 32, c = 137.036.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode mixed|fp64] [--impl ours|reference]
+
+value  = converged eigenpairs per second over all ranks (nev * ranks / step time);
+e2e    = the same through the public C ABI with the start block in pinned host memory and
+         the eigenvectors returned to host memory inside the timed region;
+roofline = the kernel category with the largest device time inside the timed region, its
+         algorithmic bytes (or flops) per launch divided by its mean CUDA-event duration.
+Multi-GPU (torchrun): every rank solves its own replica of the single-k-point dimer (weak
+scaling, no collective in the solve); the only collectives are the timing barrier and max.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "time to nev DKS eigenpairs at 1e-8 Ha (mixed+batched vs FP64); H·X GB/s vs peak"
+WORKLOAD = ("dimer: 20x20x24 bohr, 48x48x56 grid, Ecut 25 Ha (npw 57419, dim 229676), 2 sites Z=18 "
+            "sigma 0.8, 36 SO projector channels, Gamma, nev 32 (+8 buffer columns), c 137.036, "
+            "residual tol 1e-6, N_init 3")
+NEV = 32
+NBUF = 8
+TOL = 1e-6
+
+
+def _peaks():
+    path = os.path.join(HERE, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names[1:], p[5:9]):
+                if val.lower() in ("active", "1", "0x1"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(wl, nev, n_iter_ref, budget_s=20.0):
+    """Time the FP64 CPU oracle (as it stands) on a bounded sample of the workload: N_init filter
+    steps + the first Rayleigh-Ritz + as many Algorithm 1 iterations as fit in about budget_s;
+    scaled to a full solve of n_iter_ref iterations.  Returns (eigenpairs/s, cores, sample text)."""
+    import numpy as np
+
+    from oracle import basis, lobpcgf, operator
+    m, q = basis.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
+    hop = operator.MatrixFreeH(wl, m, q)
+    cs, om = operator.filter_constants(wl, q)
+    import workloads as W
+    x0 = W.start_block(len(q), nev + NBUF, wl.seed)
+    t_it = []
+    t0 = time.perf_counter()
+    marks = [t0]
+
+    class Stop(Exception):
+        pass
+
+    def cb(it, lam, norms):
+        marks.append(time.perf_counter())
+        if marks[-1] - t0 > budget_s:
+            raise Stop()
+
+    try:
+        lobpcgf.lobpcgf(hop, q, x0, nev + NBUF, cs, om, tol=TOL, n_iter=1000, nconv=nev, callback=cb)
+    except Stop:
+        pass
+    t_init = marks[1] - marks[0] - ((marks[2] - marks[1]) if len(marks) > 2 else 0.0)
+    t_it = np.diff(marks[1:]) if len(marks) > 2 else np.array([marks[1] - marks[0]])
+    per_it = float(np.mean(t_it))
+    full = max(t_init, 0.0) + per_it * n_iter_ref
+    cores = len(os.sched_getaffinity(0))
+    sample = (f"oracle Algorithm 1 on the same dimer: initial filtering + {len(marks) - 2} iterations "
+              f"({marks[-1] - t0:.1f} s), scaled to {n_iter_ref} iterations")
+    return nev / full, cores, sample, full
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    import workloads as W
+    wl = W.make("dimer")
+    n_iter_ref = args.ref_iterations
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, cores, sample, full = cpu_oracle_sample(wl, NEV, n_iter_ref, budget_s=args.ref_budget)
+        if i >= args.warmup:
+            vals.append(v)
+    value = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * NEV / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "mode": "fp64 oracle (numpy/scipy)"},
+            "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-iterations", type=int, default=60)
+    ap.add_argument("--ref-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_1211_1446_gb300 as P
+    import workloads as W
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = W.make("dimer")
+    ctx = P.Context.from_workload(wl)
+    npw = ctx.npw(0)
+    mode = P.MODE_MIXED if args.mode == "mixed" else P.MODE_FP64
+    x0 = torch.from_numpy(W.start_block(npw, NEV + NBUF, wl.seed)).cuda()
+    x = torch.empty_like(x0)
+    stream = torch.cuda.current_stream()
+
+    def step(m=mode):
+        x.copy_(x0)
+        lam, rep, rc = ctx.solve([x], NEV, tol=TOL, mode=m, nbuf=NBUF, check=False)
+        if rc != 0:
+            raise RuntimeError(f"solve failed: {P.ERRORS.get(rc, rc)} {rep}")
+        return lam[0], rep
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    P.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = []
+    for _ in range(args.steps):
+        lam, rep = step()
+        reps.append(rep)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = P.profile_read()
+    P.profile_enable(False)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = NEV * ws / (ms / 1e3)
+
+    # end to end through the public ABI: start block from pinned host memory, vectors back to host
+    xh = x0.cpu().pin_memory()
+    xo = torch.empty_like(xh).pin_memory()
+    step()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        x.copy_(xh, non_blocking=True)
+        lam_e, rep_e, rc = ctx.solve([x], NEV, tol=TOL, mode=mode, nbuf=NBUF, check=False)
+        xo.copy_(x, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    bytes_vec = x0.numel() * x0.element_size()
+
+    # the plain FP64 GPU form of the same solve (speedup denominator)
+    fp64 = None
+    if mode == P.MODE_MIXED and args.fp64_steps > 0:
+        step(P.MODE_FP64)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            lam64, rep64 = step(P.MODE_FP64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        fp64 = {"ms_per_step": ms64, "iterations": rep64["iterations"][0], "speedup_mixed_vs_fp64": ms64 / ms,
+                "max_eig_diff_vs_mixed": float(np.abs(lam64 - lam).max())}
+
+    # accuracy against the oracle's stored eigenvalues (written by tests/golden/make_golden.py)
+    acc = {"max_residual": max(r["max_residual"][0] for r in reps), "iterations": reps[-1]["iterations"][0],
+           "fp64_iterations": reps[-1]["fp64_iterations"][0], "h_applications": reps[-1]["h_applications"]}
+    gold = os.path.join(HERE, "tests", "golden", "dimer_lobpcgf_eigs.txt")
+    if os.path.exists(gold):
+        acc["max_eig_err_vs_oracle"] = float(np.abs(lam - np.loadtxt(gold)).max())
+
+    # roofline of the dominant kernel category
+    hbm, bf16, src = _peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    per_launch_ms = d["ms"] / max(d["launches"], 1)
+    launches = int(sum(v["launches"] for v in prof.values()))
+    ach_gbs = d["bytes"] / max(d["launches"], 1) / (per_launch_ms / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    roof = {"kernel": dom, "bound": "hbm", "achieved": ach_gbs, "peak": hbm, "unit": "GB/s",
+            "frac": ach_gbs / hbm, "traffic": None, "peak_source": src,
+            "share_of_step": d["ms"] / (ms * args.steps),
+            "per_category_ms": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items() if v["launches"]}}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, cores, sample, full = cpu_oracle_sample(wl, NEV, acc["iterations"])
+        cpu = {"value": v, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    line = {"metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if mode == P.MODE_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mode": args.mode, "parallelism": f"replicas x{ws}",
+                       "l2": "working set (>1 GB of blocks per solve) exceeds the 129 MB L2"},
+            "e2e": {"value": NEV * ws / (ms_e2e / 1e3), "unit": "eigenpairs/s",
+                    "h2d_bytes_per_step": bytes_vec, "d2h_bytes_per_step": bytes_vec + 8 * NEV},
+            "gpu_launches": launches // args.steps * args.steps, "clocks": clk, "roofline": roof,
+            "cpu_baseline": cpu, "fp64_form": fp64, "accuracy": acc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

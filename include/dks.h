@@ -102,7 +102,7 @@ void dks_destroy(dks_ctx* ctx);
 /* Basis size of k-point ik, and its Miller triples (host int[npw*3]). */
 int dks_npw(const dks_ctx* ctx, int ik, int* npw);
 int dks_basis(const dks_ctx* ctx, int ik, int* miller);
-/* Number of projector channels (sum over sites of 2(2 lmax + 1)^... = 18 per s,p,d site). */
+/* Number of projector channels: 2(l+1) + 2l per l on each site (18 for an s, p, d site). */
 int dks_nproj(const dks_ctx* ctx, int* nproj);
 
 /* Default filter constants for k-point ik (readings of Sec. 3.1, shifted units):
@@ -136,11 +136,13 @@ typedef struct {
   int nbuf;            /* extra columns iterated but not convergence-checked           */
   double C, Omega;     /* filter constants; NaN = dks_filter_constants                 */
   int mode;            /* DKS_MODE_*                                                   */
-  double refine_tol;   /* MIXED: switch to FP64 once max residual < refine_tol         */
+  double refine_tol;   /* MIXED: FP64 once max residual < refine_tol (1e-5) or stalls   */
   int precond;         /* DKS_PRECOND_*                                                */
   int use_filter;      /* 1 = LOBPCG-F; 0 = standard LOBPCG (Alg. 1 without F lines)  */
   const int* nev_k;    /* per-k wanted pairs (host, nk) or NULL = the nev argument     */
   void* stream;        /* cudaStream_t for all work                                    */
+  double chol_tol;     /* Rayleigh-Ritz: SVQB when a Cholesky pivot^2 < chol_tol (1e-12) */
+  double drop_tol;     /* SVQB drops directions below drop_tol * max eig (1e-12)        */
 } dks_solve_opts;
 
 typedef struct {
@@ -151,6 +153,8 @@ typedef struct {
   double shift;              /* c^2 removed from every eigenvalue                  */
   double seconds;            /* wall time of the call (host clock)                 */
   int status;                /* DKS_OK or the first error                          */
+  int hist_len;              /* entries of res_history                             */
+  double res_history[512];   /* k-point 0: max checked residual after each RR      */
 } dks_solve_report;
 
 void dks_solve_opts_default(dks_solve_opts* opts);
@@ -206,6 +210,19 @@ int dks_rotate(const void* Z, int rows, int nz, const void* W, int ldw, int n, v
 /* Alg. 1 line 16-17: norms[j] = ||HX[j] - lam[j] X[j]||_2 accumulated in FP64. */
 int dks_residual_norms(const void* X, const void* HX, const double* lam, int rows, int n,
                        double* norms, int prec, void* stream);
+
+/* ------------------------------------------------ instrumentation (no counterpart in the paper;
+ * the solve report's phase timers of a production code).  Every kernel launch of the library is
+ * counted per category; while profiling is enabled each launch is also bracketed by a CUDA event
+ * pair on its own stream and tagged with its algorithmic bytes and flops (the minimum traffic and
+ * work the launch must do, see the kernel comments).  Process-wide, thread-safe. */
+int dks_profile_ncat(void);
+const char* dks_profile_name(int cat);
+/* enable (1) or disable (0) event recording; clears all counters and records */
+int dks_profile_enable(int on);
+/* synchronises the device, then per category c < ncat: ms[c] = summed event time,
+ * launches[c], bytes[c], flops[c]; clears.  ncat must be >= dks_profile_ncat(). */
+int dks_profile_read(int ncat, double* ms, long long* launches, double* bytes, double* flops);
 
 const char* dks_strerror(int code);
 const char* dks_last_error(void);

@@ -51,19 +51,21 @@ class _Proj(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("n_init", C.c_int), ("n_iter", C.c_int), ("nbuf", C.c_int), ("C", C.c_double),
                 ("Omega", C.c_double), ("mode", C.c_int), ("refine_tol", C.c_double), ("precond", C.c_int),
-                ("use_filter", C.c_int), ("nev_k", C.POINTER(C.c_int)), ("stream", C.c_void_p)]
+                ("use_filter", C.c_int), ("nev_k", C.POINTER(C.c_int)), ("stream", C.c_void_p),
+                ("chol_tol", C.c_double), ("drop_tol", C.c_double)]
 
 
 class SolveReport(C.Structure):
     _fields_ = [("iterations", C.c_int * 64), ("fp64_iterations", C.c_int * 64),
                 ("max_residual", C.c_double * 64), ("h_applications", C.c_longlong), ("shift", C.c_double),
-                ("seconds", C.c_double), ("status", C.c_int)]
+                ("seconds", C.c_double), ("status", C.c_int), ("hist_len", C.c_int),
+                ("res_history", C.c_double * 512)]
 
 
 EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dks_filter_constants",
            "dks_apply_H", "dks_filter", "dks_solve_opts_default", "dks_lobpcgf_solve", "dks_precond",
            "dks_gram", "dks_rayleigh_ritz", "dks_rotate", "dks_residual_norms", "dks_strerror",
-           "dks_last_error"]
+           "dks_last_error", "dks_profile_ncat", "dks_profile_name", "dks_profile_enable", "dks_profile_read"]
 
 _lib = None
 
@@ -99,6 +101,11 @@ def load_library(path: str = LIB_PATH):
     lib.dks_strerror.restype = C.c_char_p
     lib.dks_last_error.argtypes = []
     lib.dks_last_error.restype = C.c_char_p
+    lib.dks_profile_ncat.argtypes = []
+    lib.dks_profile_name.argtypes = [i]
+    lib.dks_profile_name.restype = C.c_char_p
+    lib.dks_profile_enable.argtypes = [i]
+    lib.dks_profile_read.argtypes = [i, vp, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -219,9 +226,9 @@ class Context:
         return y
 
     # ---- solver
-    def solve(self, x_list, nev, tol=1e-6, n_init=3, n_iter=200, mode=MODE_FP64, refine_tol=1e-3,
+    def solve(self, x_list, nev, tol=1e-6, n_init=3, n_iter=200, mode=MODE_FP64, refine_tol=1e-5,
               precond=PRECOND_TETER, use_filter=True, cshift=None, omega=None, nev_k=None, nbuf=0,
-              stream=None, check=True):
+              stream=None, check=True, chol_tol=None, drop_tol=None):
         """Algorithm 1 on every k-point.  x_list[ik]: complex128 [nev_k+nbuf, 4, npw] (X0 in, X out).
         Returns (eigenvalues per k as numpy arrays, report dict, status code)."""
         opts = SolveOpts()
@@ -231,6 +238,10 @@ class Context:
         opts.Omega = float("nan") if omega is None else float(omega)
         opts.mode, opts.refine_tol, opts.precond = int(mode), float(refine_tol), int(precond)
         opts.use_filter = 1 if use_filter else 0
+        if chol_tol is not None:
+            opts.chol_tol = float(chol_tol)
+        if drop_tol is not None:
+            opts.drop_tol = float(drop_tol)
         nevs = [int(nev)] * self.nk if nev_k is None else [int(v) for v in nev_k]
         if nev_k is not None:
             arr = np.ascontiguousarray(nevs, dtype=np.int32)
@@ -252,8 +263,28 @@ class Context:
         nk = min(self.nk, 64)
         report = dict(iterations=list(rep.iterations[:nk]), fp64_iterations=list(rep.fp64_iterations[:nk]),
                       max_residual=list(rep.max_residual[:nk]), h_applications=int(rep.h_applications),
-                      shift=rep.shift, seconds=rep.seconds, status=rep.status)
+                      shift=rep.shift, seconds=rep.seconds, status=rep.status,
+                      history=list(rep.res_history[:rep.hist_len]))
         return out, report, rc
+
+
+def profile_enable(on=True):
+    """Start (or stop) per-launch CUDA-event timing inside the library; clears counters."""
+    _check(load_library().dks_profile_enable(1 if on else 0))
+
+
+def profile_read():
+    """Synchronise and return {category: dict(ms, launches, bytes, flops)}; clears the records."""
+    lib = load_library()
+    n = lib.dks_profile_ncat()
+    ms = np.zeros(n)
+    la = np.zeros(n, dtype=np.int64)
+    by = np.zeros(n)
+    fl = np.zeros(n)
+    _check(lib.dks_profile_read(n, ms.ctypes.data_as(C.c_void_p), la.ctypes.data_as(C.c_void_p),
+                                by.ctypes.data_as(C.c_void_p), fl.ctypes.data_as(C.c_void_p)))
+    return {lib.dks_profile_name(c).decode(): dict(ms=float(ms[c]), launches=int(la[c]), bytes=float(by[c]),
+                                                   flops=float(fl[c])) for c in range(n)}
 
 
 # ---- single steps of Algorithm 1 (blocks are [ncol, rows] complex tensors)

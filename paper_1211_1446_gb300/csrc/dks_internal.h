@@ -105,6 +105,22 @@ struct dks_ctx {
 
 namespace dks {
 
+// ---------------------------------------------------------------- profiling
+enum ProfCat {
+  P_STICK_INV, P_PLANE, P_STICK_FWD, P_DIRAC, P_PROJ_HN, P_PROJ_NN, P_GRAM, P_ROTATE, P_RR, P_STATS,
+  P_PRECOND, P_MISC, P_NCAT
+};
+// RAII scope around one kernel launch: counts it, and while profiling is on records a
+// CUDA event pair on the launching stream with the launch's algorithmic bytes and flops.
+class Prof {
+ public:
+  Prof(int cat, cudaStream_t st, double bytes, double flops);
+  ~Prof();
+ private:
+  cudaStream_t st_;
+  long long idx_;
+};
+
 int grow(Workspace& w, size_t bytes);
 void release(Workspace& w);
 
@@ -118,10 +134,11 @@ int apply_h(dks_ctx* ctx, int ik, const V* x, V* out, int nb, double shift, doub
 // kernels shared by the solver and the single-step entry points
 template <typename V>
 int gemm_hn(const V* a, int lda, const V* b, int ldb, int k, int m, int n, double2* c,
-            cudaStream_t st);  // c (m x n, col-major, ld m) = a^H b, accumulated in FP64 atomics
+            cudaStream_t st, int cat = P_GRAM);  // c (m x n, col-major, ld m) += a^H b, FP64 atomics
 template <typename V>
 int gemm_nn(const V* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
-            int n, V* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0);
+            int n, V* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0,
+            int cat = P_ROTATE);
 // out (k x n) = alpha * a (k x m) * (diag(wscale) w) + beta * out; wscale may be NULL
 template <typename V>
 int col_stats(const V* x, const V* hx, const double* lam, const double* ek, int npw, int n,
@@ -130,7 +147,8 @@ template <typename V>
 int precond_apply(const V* x, const V* hx, const double* lam, const double* stats, const int* act,
                   int nact, const double* ek, int npw, int precond, V* y, cudaStream_t st);
 int rayleigh_ritz(const double2* a, const double2* s, int nz, int n, double2* v, double* lam,
-                  int* info, double2* scratch, cudaStream_t st);
+                  int* info, double2* scratch, cudaStream_t st, double chol_tol = 1e-12,
+                  double drop_tol = 1e-12);
 size_t rr_scratch_elems(int nz);
 template <typename Vi, typename Vo>
 int convert(const Vi* in, Vo* out, size_t n, cudaStream_t st);

@@ -87,7 +87,8 @@ static int num_sms() {
 }
 
 template <typename V>
-int gemm_hn(const V* a, int lda, const V* b, int ldb, int k, int m, int n, double2* c, cudaStream_t st) {
+int gemm_hn(const V* a, int lda, const V* b, int ldb, int k, int m, int n, double2* c, cudaStream_t st,
+            int cat) {
   if (m <= 0 || n <= 0 || k <= 0) return DKS_OK;
   const int mt = (m + HN_T - 1) / HN_T, nt = (n + HN_T - 1) / HN_T;
   const int ktiles = (k + HN_T - 1) / HN_T;
@@ -96,6 +97,8 @@ int gemm_hn(const V* a, int lda, const V* b, int ldb, int k, int m, int n, doubl
   const int kchunk = ((ktiles + splits - 1) / splits) * HN_T;
   splits = (k + kchunk - 1) / kchunk;
   dim3 grid(mt * nt, splits);
+  const double es = (double)sizeof(V);
+  Prof pr(cat, st, ((a == b) ? (double)m : (double)(m + n)) * k * es + 16.0 * m * n, 8.0 * m * n * (double)k);
   k_gemm_hn<V><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
@@ -164,9 +167,11 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const V* __restrict__ a, int ld
 
 template <typename V>
 int gemm_nn(const V* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
-            V* out, int ldo, double beta, cudaStream_t st, double alpha) {
+            V* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
   if (k <= 0 || n <= 0) return DKS_OK;
   dim3 grid((k + NN_R - 1) / NN_R, (n + NN_C - 1) / NN_C);
+  const double es = (double)sizeof(V);
+  Prof pr(cat, st, ((double)m + (beta != 0.0 ? 2.0 : 1.0) * n) * k * es + 16.0 * m * n, 8.0 * (double)k * m * n);
   k_gemm_nn<V><<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
@@ -230,6 +235,7 @@ template <typename V>
 int col_stats(const V* x, const V* hx, const double* lam, const double* ek, int npw, int n, double* stats,
               cudaStream_t st) {
   if (n <= 0) return DKS_OK;
+  Prof pr(P_STATS, st, (hx ? 2.0 : 1.0) * n * 4.0 * npw * sizeof(V) + 8.0 * npw, 12.0 * n * 4.0 * npw);
   k_col_stats<V><<<n, 256, 0, st>>>(x, hx, lam, ek, npw, stats);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
@@ -272,6 +278,7 @@ int precond_apply(const V* x, const V* hx, const double* lam, const double* stat
   if (nact <= 0) return DKS_OK;
   const size_t total = (size_t)4 * npw * nact;
   const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)num_sms() * 16);
+  Prof pr(P_PRECOND, st, 3.0 * total * sizeof(V) + 8.0 * npw, 20.0 * total);
   k_precond<V><<<blocks, 256, 0, st>>>(x, hx, lam, stats, act, nact, ek, npw, precond, y);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
@@ -288,6 +295,7 @@ template <typename Vi, typename Vo>
 int convert(const Vi* in, Vo* out, size_t n, cudaStream_t st) {
   if (!n) return DKS_OK;
   const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 16);
+  Prof pr(P_MISC, st, (double)n * (sizeof(Vi) + sizeof(Vo)), 0.0);
   k_convert<Vi, Vo><<<blocks, 256, 0, st>>>(in, out, n);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
@@ -306,18 +314,20 @@ int gather_cols(const double2* v, int ldv, int row0, int rows, const int* act, i
                 cudaStream_t st) {
   if (rows <= 0 || nact <= 0) return DKS_OK;
   const int total = rows * nact;
+  Prof pr(P_MISC, st, 32.0 * total, 0.0);
   k_gather_cols<<<std::min((total + 255) / 256, 1024), 256, 0, st>>>(v, ldv, row0, rows, act, nact, out);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
 
 // explicit instantiations
-template int gemm_hn<double2>(const double2*, int, const double2*, int, int, int, int, double2*, cudaStream_t);
-template int gemm_hn<float2>(const float2*, int, const float2*, int, int, int, int, double2*, cudaStream_t);
+template int gemm_hn<double2>(const double2*, int, const double2*, int, int, int, int, double2*, cudaStream_t,
+                              int);
+template int gemm_hn<float2>(const float2*, int, const float2*, int, int, int, int, double2*, cudaStream_t, int);
 template int gemm_nn<double2>(const double2*, int, int, int, const double2*, int, const double*, int, double2*,
-                              int, double, cudaStream_t, double);
+                              int, double, cudaStream_t, double, int);
 template int gemm_nn<float2>(const float2*, int, int, int, const double2*, int, const double*, int, float2*, int,
-                             double, cudaStream_t, double);
+                             double, cudaStream_t, double, int);
 template int col_stats<double2>(const double2*, const double2*, const double*, const double*, int, int, double*,
                                 cudaStream_t);
 template int col_stats<float2>(const float2*, const float2*, const double*, const double*, int, int, double*,

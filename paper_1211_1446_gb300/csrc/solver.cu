@@ -108,7 +108,7 @@ static int fetch(Small& sm, Pinned& pin, int n, std::vector<double>& res, cudaSt
 template <typename V>
 static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int n, int nconv, double tol,
                  int n_init, int n_iter, double C, double om, int precond, int use_filter, bool stop_on_stall,
-                 PhaseOut& out, cudaStream_t st) {
+                 double chol_tol, double drop_tol, std::vector<double>* hist, PhaseOut& out, cudaStream_t st) {
   const KPoint& kp = ctx->k[ik];
   const int rows = 4 * kp.npw;
   const size_t colsz = (size_t)rows;
@@ -124,7 +124,7 @@ static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int
   DKS_TRY(apply_h<V>(ctx, ik, b.z[cur], b.hz[cur], n, 0.0, 1.0, st));
   happ += n;
   DKS_TRY(gram<V>(b.z[cur], b.hz[cur], rows, n, sm, st));
-  DKS_TRY(rayleigh_ritz(sm.a, sm.s, n, n, sm.vm, sm.lam, sm.info, sm.rrs, st));
+  DKS_TRY(rayleigh_ritz(sm.a, sm.s, n, n, sm.vm, sm.lam, sm.info, sm.rrs, st, chol_tol, drop_tol));
   int nx = cur ^ 1;
   DKS_TRY(gemm_nn<V>(b.z[cur], rows, rows, n, sm.vm, n, nullptr, n, b.z[nx], rows, 0.0, st));
   DKS_TRY(gemm_nn<V>(b.hz[cur], rows, rows, n, sm.vm, n, nullptr, n, b.hz[nx], rows, 0.0, st));
@@ -157,7 +157,7 @@ static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int
     happ += a;
     const int nz = n + a + p;
     DKS_TRY(gram<V>(b.z[cur], b.hz[cur], rows, nz, sm, st));
-    DKS_TRY(rayleigh_ritz(sm.a, sm.s, nz, n, sm.vm, sm.lam, sm.info, sm.rrs, st));
+    DKS_TRY(rayleigh_ritz(sm.a, sm.s, nz, n, sm.vm, sm.lam, sm.info, sm.rrs, st, chol_tol, drop_tol));
     nx = cur ^ 1;
     DKS_TRY(gemm_nn<V>(b.z[cur], rows, rows, nz, sm.vm, nz, nullptr, n, b.z[nx], rows, 0.0, st));
     DKS_TRY(gemm_nn<V>(b.hz[cur], rows, rows, nz, sm.vm, nz, nullptr, n, b.hz[nx], rows, 0.0, st));
@@ -166,6 +166,7 @@ static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int
     if (pin.info[1] < n) return fail(DKS_ERR_RANK, "Rayleigh-Ritz subspace rank below the block size");
     maxres = 0;
     for (int j = 0; j < nconv; ++j) maxres = std::max(maxres, res[j]);
+    if (hist) hist->push_back(maxres);
     if (!std::isfinite(maxres)) return fail(DKS_ERR_NOT_CONVERGED, "non-finite residual norm");
     if (maxres < tol) {
       cur = nx;
@@ -222,11 +223,13 @@ void dks_solve_opts_default(dks_solve_opts* o) {
   o->C = NAN;
   o->Omega = NAN;
   o->mode = DKS_MODE_FP64;
-  o->refine_tol = 1e-3;
+  o->refine_tol = 1e-5;
   o->precond = DKS_PRECOND_TETER;
   o->use_filter = 1;
   o->nev_k = nullptr;
   o->stream = nullptr;
+  o->chol_tol = 1e-12;
+  o->drop_tol = 1e-12;
 }
 
 int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* opts_in, double* eig, void* const* X,
@@ -301,6 +304,7 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
 
   int status = DKS_OK;
   size_t eoff = 0;
+  std::vector<double> hist;
   for (int ik = 0; ik < ctx->nk; ++ik) {
     const KPoint& kp = ctx->k[ik];
     const int nv = opts.nev_k ? opts.nev_k[ik] : nev;
@@ -313,17 +317,20 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
       DKS_TRY(convert<double2, float2>((const double2*)X[ik], b32.z[0], elems, st));
       o32.cur = 0;
       DKS_TRY(phase<float2>(ctx, ik, b32, sm, pin, n, nv, std::max(opts.refine_tol, tol), opts.n_init, opts.n_iter,
-                            C, om, opts.precond, opts.use_filter, true, o32, st));
+                            C, om, opts.precond, opts.use_filter, true, opts.chol_tol, opts.drop_tol,
+                            ik == 0 ? &hist : nullptr, o32, st));
       DKS_TRY(convert<float2, double2>(b32.z[o32.cur], b64.z[0], elems, st));
       o64.cur = 0;
       const int left = std::max(0, opts.n_iter - o32.iterations);
       DKS_TRY(phase<double2>(ctx, ik, b64, sm, pin, n, nv, tol, opts.use_filter ? 1 : 0, left, C, om, opts.precond,
-                             opts.use_filter, false, o64, st));
+                             opts.use_filter, false, opts.chol_tol, opts.drop_tol, ik == 0 ? &hist : nullptr, o64,
+                             st));
     } else {
       DKS_CUDA_TRY(cudaMemcpyAsync(b64.z[0], X[ik], elems * sizeof(double2), cudaMemcpyDeviceToDevice, st));
       o64.cur = 0;
       DKS_TRY(phase<double2>(ctx, ik, b64, sm, pin, n, nv, tol, opts.n_init, opts.n_iter, C, om, opts.precond,
-                             opts.use_filter, false, o64, st));
+                             opts.use_filter, false, opts.chol_tol, opts.drop_tol, ik == 0 ? &hist : nullptr, o64,
+                             st));
     }
     DKS_CUDA_TRY(cudaMemcpyAsync(X[ik], b64.z[o64.cur], elems * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     DKS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -343,6 +350,8 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
     }
   }
   if (report) {
+    report->hist_len = (int)std::min<size_t>(hist.size(), 512);
+    for (int i = 0; i < report->hist_len; ++i) report->res_history[i] = hist[i];
     report->status = status;
     report->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
