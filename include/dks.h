@@ -201,6 +201,21 @@ int dks_gram(const void* Z, const void* HZ, int rows, int nz, void* A, void* S, 
 int dks_rayleigh_ritz(const void* A, const void* S, int nz, int n, void* V, double* lam,
                       int* info, void* stream);
 
+/* Allocation-free variant of dks_rayleigh_ritz (the paper has no counterpart: it exists for
+ * callers that may not allocate device memory when they need the solve, e.g. a service whose
+ * device memory all belongs to its own arena after start-up, or a host thread that must not
+ * risk the device-wide synchronisation a cudaMalloc/cudaFree can cause).  Same arguments,
+ * layout and results as dks_rayleigh_ritz; its scratch space is one file-scope device array of
+ * about 1.6 MB per device, held from library load until process exit.  Limit:
+ * nz <= DKS_RR_STATIC_MAX_NZ, larger pencils return DKS_ERR_UNSUPPORTED.  The first call on
+ * each device caches the array's device address, so make it before any stream capture.  Every
+ * call on a device shares the array (each call overwrites it completely before use); calls
+ * whose executions overlap on the GPU race on it and must be ordered by the caller.  Calls no
+ * cudaMalloc, cudaFree or other allocating routine. */
+#define DKS_RR_STATIC_MAX_NZ 128
+int dks_rayleigh_ritz_static(const void* A, const void* S, int nz, int n, void* V, double* lam,
+                             int* info, void* stream);
+
 /* Alg. 1 line 15 / 22: OUT[j] = sum_i Z[i] W[i + ldw*j] (+ beta OUT[j]) for
  * j < n, i < nz; Z [nz][rows], OUT [n][rows] (precision prec), W device
  * complex128 column-major with leading dimension ldw (converted to prec). */

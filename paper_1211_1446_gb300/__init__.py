@@ -65,7 +65,8 @@ class SolveReport(C.Structure):
 EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dks_filter_constants",
            "dks_apply_H", "dks_filter", "dks_solve_opts_default", "dks_lobpcgf_solve", "dks_precond",
            "dks_gram", "dks_rayleigh_ritz", "dks_rotate", "dks_residual_norms", "dks_strerror",
-           "dks_last_error", "dks_profile_ncat", "dks_profile_name", "dks_profile_enable", "dks_profile_read"]
+           "dks_last_error", "dks_profile_ncat", "dks_profile_name", "dks_profile_enable", "dks_profile_read",
+           "dks_rayleigh_ritz_static"]
 
 _lib = None
 
@@ -95,6 +96,7 @@ def load_library(path: str = LIB_PATH):
     lib.dks_precond.argtypes = [vp, i, vp, vp, vp, vp, i, vp, i, i, vp]
     lib.dks_gram.argtypes = [vp, vp, i, i, vp, vp, i, vp]
     lib.dks_rayleigh_ritz.argtypes = [vp, vp, i, i, vp, vp, vp, vp]
+    lib.dks_rayleigh_ritz_static.argtypes = [vp, vp, i, i, vp, vp, vp, vp]
     lib.dks_rotate.argtypes = [vp, i, i, vp, i, i, vp, d, i, vp]
     lib.dks_residual_norms.argtypes = [vp, vp, vp, i, i, vp, i, vp]
     lib.dks_strerror.argtypes = [i]
@@ -300,6 +302,14 @@ def rayleigh_ritz(a, s, n, v_out, lam_out, info_out, stream=None):
     load_library()
     _check(_lib.dks_rayleigh_ritz(_dptr(a), _dptr(s), a.shape[0], int(n), _dptr(v_out), _dptr(lam_out),
                                   _dptr(info_out), _stream(stream)))
+
+
+def rayleigh_ritz_static(a, s, n, v_out, lam_out, info_out, stream=None):
+    """dks_rayleigh_ritz_static: same solve with the library's fixed device scratch array (no
+    allocation; nz <= 128; calls that overlap on the GPU race on the shared array)."""
+    load_library()
+    _check(_lib.dks_rayleigh_ritz_static(_dptr(a), _dptr(s), a.shape[0], int(n), _dptr(v_out), _dptr(lam_out),
+                                         _dptr(info_out), _stream(stream)))
 
 
 def rotate(z, w, n, out, beta=0.0, stream=None):
