@@ -74,3 +74,24 @@ def test_h_application_count():
     assert rc == 0
     assert rep["h_applications"] >= 8 * 7 + 3 * 8
     assert (rep["h_applications"] - 8 * 7) % 3 == 0
+
+
+@pytest.mark.parametrize("mode", [1, 0])
+def test_dimer_full_size_vs_oracle(mode):
+    """Bench configuration (dimer, npw 57419, nev 32 + 8 buffer columns, tol 1e-6): eigenvalues
+    within 1e-8 Ha of the oracle's Algorithm 1 (tests/golden/dimer_lobpcgf_eigs.txt), and the
+    residuals of sampled returned vectors recomputed one by one by the oracle's FP64 H'."""
+    gpu()
+    import torch
+    wl, ctx, hop, q = make_pair("dimer")
+    ref = np.loadtxt(os.path.join(GOLDEN, "dimer_lobpcgf_eigs.txt"))
+    x0 = torch.from_numpy(W.start_block(len(q), 40, wl.seed)).cuda()
+    lam, rep, rc = ctx.solve([x0], 32, nbuf=8, tol=1e-6, mode=mode, check=False)
+    assert rc == 0, rep
+    lam = lam[0]
+    assert np.abs(lam - ref).max() < 1e-8
+    assert np.all(lam > -wl.c ** 2)
+    x = x0.cpu().numpy()
+    pick = np.array([0, 7, 18, 31])
+    res = _residuals(hop, x[pick], lam[pick])
+    assert res.max() < 1e-6, res
