@@ -1,0 +1,530 @@
+// FP64 Rayleigh-Ritz on a thread-block cluster (Cholesky path of Algorithm 1 lines 4 and 12-14).
+//
+// FP64 throughput on GB300 is about two FMAs per clock per SM, so the O(m^3) work of the
+// small pencil is spread over the SMs of one cluster (16 CTAs when the device allows
+// non-portable clusters, else 8).  Matrices stay in a global scratch area (L2-resident);
+// the cluster barrier (release/acquire at cluster scope) orders the dependent steps.
+//
+//  1. A' = D A D, S' = D S D, D = diag(S)^-1/2                     (element-parallel)
+//  2. S' = L L^H, right-looking, one barrier per column; if a pivot^2 falls below
+//     chol_tol the kernel records it and returns -- the single-CTA kernel then runs
+//     the SVQB path
+//  3. W = L^-1 A' and C = L^-1 W^H = L^-1 A' L^-H                  (warp per column)
+//  4. Householder reduction of C to a complex tridiagonal: every warp recomputes the
+//     column norm and reflector itself (no barrier), rows of p = tau C v are split over
+//     the warps, then the rank-2 update; two barriers per column
+//  5. real tridiagonal by a diagonal phase; the n lowest eigenvalues by 32-way
+//     multisection of the Sturm count (warp per eigenvalue)
+//  6. eigenvectors by inverse iteration on the tridiagonal (LU with partial pivoting in
+//     shared memory, one lane per vector); vectors of a cluster of close eigenvalues are
+//     computed by one lane in turn and orthogonalised against each other
+//  7. y = Phi z, Householder back-transformation, V = D L^-H U    (warp per column)
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cstdio>
+
+#include "dks_internal.h"
+#include "dks_kernels.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace dks {
+
+constexpr int RRC_THREADS = 512;
+constexpr int RRC_WARPS = RRC_THREADS / 32;
+
+// Phase timer for development builds (-DDKS_RR_TIMING): CTA 0, thread 0 prints the
+// nanoseconds spent between the marks of the algorithm steps.
+#ifdef DKS_RR_TIMING
+#define RR_MARK(i) \
+  if (gtid == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tmark[i]))
+#else
+#define RR_MARK(i)
+#endif
+
+__device__ __forceinline__ double2 warp_csum(double2 v) {
+  for (int o = 16; o; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// number of eigenvalues of the real symmetric tridiagonal (d, e) below x (Sturm count)
+__device__ int sturm_count(const double* d, const double* e2, int m, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0;
+  for (int j = 1; j < m; ++j) {
+    q = d[j] - x - e2[j - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0;
+  }
+  return cnt;
+}
+
+// deterministic start vector in (-1, 1)
+__device__ __forceinline__ double start_val(int i, int v) {
+  unsigned h = (unsigned)(i * 2654435761u) ^ (unsigned)(v * 40503u + 12345u);
+  h ^= h >> 13;
+  h *= 0x5bd1e995u;
+  h ^= h >> 15;
+  return ((double)(h & 0xffffff) / (double)0x800000) - 1.0;
+}
+
+// Solve (T - lam I) x = b in place (x holds b on entry) with the factors of
+// tridiagonal Gaussian elimination with partial pivoting; f: 5m doubles of workspace.
+// Factor: rows are processed top-down; at step i the pivot is the larger of the current
+// diagonal and the subdiagonal below it.
+__device__ void tri_factor(const double* d, const double* e, int m, double lam, double tiny, double* f) {
+  double* u0 = f;            // diagonal of U
+  double* u1 = f + m;        // first superdiagonal
+  double* u2 = f + 2 * m;    // second superdiagonal (fill-in from pivoting)
+  double* l = f + 3 * m;     // multipliers
+  double* piv = f + 4 * m;   // 1 if rows i, i+1 were swapped
+  double a = d[0] - lam;     // current diagonal
+  double b = m > 1 ? e[0] : 0.0;  // current superdiagonal
+  for (int i = 0; i < m - 1; ++i) {
+    const double c = e[i];               // subdiagonal (row i+1, col i)
+    const double dn = d[i + 1] - lam;    // next diagonal
+    const double bn = i + 1 < m - 1 ? e[i + 1] : 0.0;
+    if (fabs(a) >= fabs(c)) {
+      piv[i] = 0;
+      if (a == 0.0) a = tiny;
+      const double mult = c / a;
+      l[i] = mult;
+      u0[i] = a;
+      u1[i] = b;
+      u2[i] = 0.0;
+      a = dn - mult * b;
+      b = bn;
+    } else {
+      piv[i] = 1;
+      const double mult = a / c;
+      l[i] = mult;
+      u0[i] = c;
+      u1[i] = dn;
+      u2[i] = bn;
+      a = b - mult * dn;
+      b = -mult * bn;
+    }
+  }
+  if (a == 0.0) a = tiny;
+  u0[m - 1] = a;
+  u1[m - 1] = 0.0;
+  u2[m - 1] = 0.0;
+}
+
+__device__ void tri_solve(int m, const double* f, double* x) {
+  const double* u0 = f;
+  const double* u1 = f + m;
+  const double* u2 = f + 2 * m;
+  const double* l = f + 3 * m;
+  const double* piv = f + 4 * m;
+  for (int i = 0; i < m - 1; ++i) {
+    if (piv[i] != 0.0) {
+      const double t = x[i];
+      x[i] = x[i + 1];
+      x[i + 1] = t - l[i] * x[i];
+    } else {
+      x[i + 1] -= l[i] * x[i];
+    }
+  }
+  x[m - 1] /= u0[m - 1];
+  if (m > 1) x[m - 2] = (x[m - 2] - u1[m - 2] * x[m - 1]) / u0[m - 2];
+  for (int i = m - 3; i >= 0; --i) x[i] = (x[i] - u1[i] * x[i + 1] - u2[i] * x[i + 2]) / u0[i];
+}
+
+__global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __restrict__ A,
+                                                            const double2* __restrict__ S, int m, int n,
+                                                            double2* __restrict__ V, double* __restrict__ lam,
+                                                            int* __restrict__ info, double2* __restrict__ scr,
+                                                            double chol_tol) {
+  extern __shared__ __align__(16) unsigned char rrc_smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank(), csize = (int)cl.num_blocks();
+  const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
+  const int gtid = crank * RRC_THREADS + tid, gnt = csize * RRC_THREADS;
+  const int gw = crank * RRC_WARPS + wl, gnw = csize * RRC_WARPS;
+  const size_t mm = (size_t)m * m;
+#ifdef DKS_RR_TIMING
+  unsigned long long tmark[10] = {0};
+#endif
+  RR_MARK(0);
+  double2* am = scr;           // A' (full Hermitian)
+  double2* lm = am + mm;       // working copy for the Cholesky trailing updates
+  double2* lf = lm + mm;       // L, column-major
+  double2* lt = lf + mm;       // L, row-major (rows contiguous)
+  double2* cm = lt + mm;       // W, then C (full), then Householder vectors
+  double* dsc = reinterpret_cast<double*>(cm + mm);
+  double* dd = dsc + m;
+  double* ee = dd + m;
+  double* e2 = ee + m;
+  double* lamw = e2 + m;       // wanted eigenvalues
+  // six m-length double arrays (one spare) keep the complex arrays below 16-byte aligned for odd m
+  double2* tau = reinterpret_cast<double2*>(lamw + 2 * m);
+  double2* ph = tau + m;
+  double2* pv = ph + m;
+  int* flag = reinterpret_cast<int*>(pv + m);
+  double* zt = reinterpret_cast<double*>(lm);   // m x n real eigenvectors of T (after Cholesky)
+
+  // 1. scaling
+  for (int i = gtid; i < m; i += gnt) dsc[i] = 1.0 / sqrt(fmax(S[(size_t)i * m + i].x, 1e-300));
+  for (size_t e = gtid; e < mm; e += gnt) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    const double s = (1.0 / sqrt(fmax(S[(size_t)i * m + i].x, 1e-300))) * (1.0 / sqrt(fmax(S[(size_t)j * m + j].x, 1e-300)));
+    const double2 a = A[e], at = A[(size_t)i * m + j];
+    am[e] = double2{0.5 * s * (a.x + at.x), 0.5 * s * (a.y - at.y)};
+    const double2 b = S[e], bt = S[(size_t)i * m + j];
+    lm[e] = double2{0.5 * s * (b.x + bt.x), 0.5 * s * (b.y - bt.y)};
+  }
+  cl.sync();
+  // 2. Cholesky: column j of L from the (final) column j of lm; trailing update in lm.
+  // Every thread reads the same pivot, so the failure decision is uniform over the cluster.
+  bool failed = false;
+  for (int j = 0; j < m; ++j) {
+    const double piv = lm[(size_t)j * m + j].x;
+    if (!(piv > chol_tol)) {
+      failed = true;
+      break;
+    }
+    const double ljj = sqrt(piv), inv = 1.0 / ljj;
+    for (int i = j + gtid; i < m; i += gnt) {
+      const double2 v = i == j ? double2{ljj, 0} : double2{lm[(size_t)j * m + i].x * inv, lm[(size_t)j * m + i].y * inv};
+      lf[(size_t)j * m + i] = v;
+      lt[(size_t)i * m + j] = v;
+    }
+    const int len = m - j - 1;
+    for (int e = gtid; e < len * len; e += gnt) {
+      const int i = j + 1 + e % len, k = j + 1 + e / len;
+      if (k <= i) {
+        const double2 lij = lm[(size_t)j * m + i], lkj = lm[(size_t)j * m + k];
+        const double2 u = cmulc(lkj, lij);      // conj(l_kj) l_ij, times inv^2
+        lm[(size_t)k * m + i].x -= u.x * inv * inv;
+        lm[(size_t)k * m + i].y -= u.y * inv * inv;
+      }
+    }
+    cl.sync();
+  }
+  if (failed) {
+    if (gtid == 0) *flag = 1;
+    return;   // every CTA leaves here; the single-CTA SVQB kernel that follows takes over
+  }
+  if (gtid == 0) *flag = 0;
+  RR_MARK(1);
+  double2* wvec = reinterpret_cast<double2*>(rrc_smem) + (size_t)wl * m;   // per-warp vector
+  // 3a. W = L^-1 A'  (column c of A' -> column c of W, stored in cm)
+  for (int c = gw; c < m; c += gnw) {
+    for (int i = 0; i < m; ++i) {
+      double2 s{0, 0};
+      for (int k = lane; k < i; k += 32) s = cadd(s, cmul(lt[(size_t)i * m + k], wvec[k]));
+      s = warp_csum(s);
+      const double lii = lt[(size_t)i * m + i].x;
+      const double2 a = am[(size_t)c * m + i];
+      const double2 w = double2{(a.x - s.x) / lii, (a.y - s.y) / lii};
+      if (lane == 0) wvec[i] = w;
+      __syncwarp();
+    }
+    for (int i = lane; i < m; i += 32) cm[(size_t)c * m + i] = wvec[i];
+    __syncwarp();
+  }
+  cl.sync();
+  // 3b. C = L^-1 W^H: right-hand side column c of W^H is conj(row c of W); result into lm (free)
+  double2* cc = lm;
+  for (int c = gw; c < m; c += gnw) {
+    for (int i = 0; i < m; ++i) {
+      double2 s{0, 0};
+      for (int k = lane; k < i; k += 32) s = cadd(s, cmul(lt[(size_t)i * m + k], wvec[k]));
+      s = warp_csum(s);
+      const double lii = lt[(size_t)i * m + i].x;
+      const double2 b = cm[(size_t)i * m + c];      // W[c, i]
+      const double2 w = double2{(b.x - s.x) / lii, (-b.y - s.y) / lii};
+      if (lane == 0) wvec[i] = w;
+      __syncwarp();
+    }
+    for (int i = lane; i < m; i += 32) cc[(size_t)c * m + i] = wvec[i];
+    __syncwarp();
+  }
+  cl.sync();
+  RR_MARK(2);
+  // Hermitian average into cm (full storage)
+  for (size_t e = gtid; e < mm; e += gnt) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    const double2 a = cc[e], b = cc[(size_t)i * m + j];
+    cm[e] = i == j ? double2{a.x, 0.0} : double2{0.5 * (a.x + b.x), 0.5 * (a.y - b.y)};
+  }
+  cl.sync();
+  // 4. Householder reduction of cm
+  for (int k = 0; k + 2 < m; ++k) {
+    const int len = m - k - 1;
+    double2* x = cm + (size_t)k * m + k + 1;
+    double a2 = 0;
+    for (int i = lane; i < len; i += 32) a2 += x[i].x * x[i].x + x[i].y * x[i].y;
+    a2 = warp_sum(a2);
+    const double2 x0 = x[0];
+    const double ax0 = hypot(x0.x, x0.y);
+    const double alpha = sqrt(a2);
+    double t = 0.0;
+    double2 beta = x0, v0 = x0;
+    if (alpha > 1e-300 && a2 - ax0 * ax0 > 1e-30 * a2) {
+      const double2 phs = ax0 > 0 ? double2{x0.x / ax0, x0.y / ax0} : double2{1, 0};
+      beta = double2{-phs.x * alpha, -phs.y * alpha};
+      v0 = double2{x0.x - beta.x, x0.y - beta.y};
+      t = 2.0 / (a2 - ax0 * ax0 + v0.x * v0.x + v0.y * v0.y);
+    }
+    if (t != 0.0) {
+      double2* a22 = cm + (size_t)(k + 1) * m + (k + 1);
+      // p_i = t sum_j A22[i, j] v_j = t sum_j conj(A22[j, i]) v_j (read column i)
+      for (int i = gw; i < len; i += gnw) {
+        double2 s{0, 0};
+        for (int j = lane; j < len; j += 32) {
+          const double2 vj = j == 0 ? v0 : x[j];
+          s = cadd(s, cmulc(a22[(size_t)i * m + j], vj));
+        }
+        s = warp_csum(s);
+        if (lane == 0) pv[i] = double2{t * s.x, t * s.y};
+      }
+    }
+    cl.sync();
+    if (t != 0.0) {
+      double2* a22 = cm + (size_t)(k + 1) * m + (k + 1);
+      double2 kv{0, 0};
+      for (int i = lane; i < len; i += 32) kv = cadd(kv, cmulc(i == 0 ? v0 : x[i], pv[i]));
+      kv = warp_csum(kv);
+      kv = double2{0.5 * t * kv.x, 0.5 * t * kv.y};
+      for (int e = gtid; e < len * len; e += gnt) {
+        const int i = e % len, j = e / len;
+        const double2 vi = i == 0 ? v0 : x[i], vj = j == 0 ? v0 : x[j];
+        const double2 wi = csub(pv[i], cmul(kv, vi)), wj = csub(pv[j], cmul(kv, vj));
+        const double2 u1 = cmul(vi, double2{wj.x, -wj.y});
+        const double2 u2 = cmul(wi, double2{vj.x, -vj.y});
+        a22[(size_t)j * m + i] = csub(a22[(size_t)j * m + i], cadd(u1, u2));
+      }
+    }
+    if (gtid == 0) {
+      tau[k] = double2{t, 0};
+      ph[k] = beta;
+    }
+    cl.sync();
+    if (gtid == 0 && t != 0.0) x[0] = v0;    // reflector stored after every warp has read x[0]
+    // (no barrier needed: x[0] of column k is not read again until the back-transformation)
+  }
+  cl.sync();
+  RR_MARK(3);
+  // 5. real tridiagonal (every CTA keeps its own copy in shared memory for the multisection)
+  if (gtid == 0) {
+    if (m >= 2) {
+      tau[m - 2] = double2{0, 0};
+      ph[m - 2] = cm[(size_t)(m - 2) * m + (m - 1)];
+    }
+    double2 phi{1, 0};
+    for (int k = 0; k < m; ++k) dd[k] = cm[(size_t)k * m + k].x;
+    for (int k = 0; k + 1 < m; ++k) {
+      const double2 e = ph[k];
+      const double ae = hypot(e.x, e.y);
+      ee[k] = ae;
+      e2[k] = ae * ae;
+      ph[k] = phi;
+      if (ae > 0) phi = cmul(phi, double2{e.x / ae, e.y / ae});
+    }
+    ph[m - 1] = phi;
+    ee[m - 1] = 0;
+    e2[m - 1] = 0;
+  }
+  cl.sync();
+  double tnorm = 0, lo0 = INFINITY, hi0 = -INFINITY;
+  for (int k = 0; k < m; ++k) {
+    const double r = (k > 0 ? ee[k - 1] : 0.0) + (k + 1 < m ? ee[k] : 0.0);
+    lo0 = fmin(lo0, dd[k] - r);
+    hi0 = fmax(hi0, dd[k] + r);
+  }
+  tnorm = fmax(fabs(lo0), fabs(hi0));
+  const double pivmin = fmax(1e-290, DBL_MIN * 4.0) + 1e-300;
+  // multisection: warp gw finds eigenvalue index gw (ascending)
+  for (int idx = gw; idx < n; idx += gnw) {
+    double lo = lo0 - 1e-14 * tnorm - 1e-300, hi = hi0 + 1e-14 * tnorm + 1e-300;
+    for (int it = 0; it < 40 && hi - lo > 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300; ++it) {
+      const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+      const int cnt = sturm_count(dd, e2, m, x, pivmin);
+      const unsigned above = __ballot_sync(0xffffffffu, cnt > idx);
+      const int first = above ? __ffs(above) - 1 : 32;    // first point with count > idx
+      const double nhi = first < 32 ? lo + (hi - lo) * (double)(first + 1) / 33.0 : hi;
+      const double nlo = first > 0 ? lo + (hi - lo) * (double)first / 33.0 : lo;
+      lo = nlo;
+      hi = nhi;
+    }
+    if (lane == 0) lamw[idx] = 0.5 * (lo + hi);
+  }
+  cl.sync();
+  RR_MARK(4);
+  // 6. inverse iteration; clusters of close eigenvalues go to one lane in order
+  const double ortol = 1e-7 * fmax(tnorm, 1e-300);
+  const int nslots = min(RRC_WARPS, (int)(48 * 1024 / (sizeof(double) * 6 * (size_t)m)));
+  double* fws = reinterpret_cast<double*>(rrc_smem);   // per-slot 5m factors + m vector
+  for (int start = gw; start < n; start += gnw) {
+    // one lane (lane 0) of this warp handles the cluster that begins at `start`
+    const bool begins = start == 0 || lamw[start] - lamw[start - 1] > ortol;
+    if (!begins || lane != 0 || wl >= nslots) continue;
+    int end = start + 1;
+    while (end < n && lamw[end] - lamw[end - 1] <= ortol) ++end;
+    double* f = fws + (size_t)wl * 6 * m;
+    double* xv = f + 5 * m;
+    for (int v = start; v < end; ++v) {
+      const double shift = lamw[v] + (double)(v - start) * 10.0 * DBL_EPSILON * tnorm;
+      tri_factor(dd, ee, m, shift, DBL_EPSILON * tnorm + 1e-300, f);
+      for (int i = 0; i < m; ++i) xv[i] = start_val(i, v);
+      for (int itr = 0; itr < 4; ++itr) {
+        tri_solve(m, f, xv);
+        for (int u = start; u < v; ++u) {        // orthogonalise against the cluster's earlier vectors
+          double dot = 0;
+          for (int i = 0; i < m; ++i) dot += zt[(size_t)u * m + i] * xv[i];
+          for (int i = 0; i < m; ++i) xv[i] -= dot * zt[(size_t)u * m + i];
+        }
+        double nrm = 0;
+        for (int i = 0; i < m; ++i) nrm += xv[i] * xv[i];
+        nrm = 1.0 / sqrt(fmax(nrm, 1e-300));
+        for (int i = 0; i < m; ++i) xv[i] *= nrm;
+      }
+      for (int i = 0; i < m; ++i) zt[(size_t)v * m + i] = xv[i];
+    }
+  }
+  // slots beyond nslots (very large m) are handled by the first warp of CTA 0 afterwards
+  cl.sync();
+  if (nslots < RRC_WARPS) {
+    for (int start = 0; start < n; ++start) {
+      const int owner_w = start % gnw;
+      if ((owner_w % RRC_WARPS) < nslots) continue;
+      const bool begins = start == 0 || lamw[start] - lamw[start - 1] > ortol;
+      if (!begins || gtid != 0) continue;
+      int end = start + 1;
+      while (end < n && lamw[end] - lamw[end - 1] <= ortol) ++end;
+      double* f = fws;
+      double* xv = f + 5 * m;
+      for (int v = start; v < end; ++v) {
+        const double shift = lamw[v] + (double)(v - start) * 10.0 * DBL_EPSILON * tnorm;
+        tri_factor(dd, ee, m, shift, DBL_EPSILON * tnorm + 1e-300, f);
+        for (int i = 0; i < m; ++i) xv[i] = start_val(i, v);
+        for (int itr = 0; itr < 4; ++itr) {
+          tri_solve(m, f, xv);
+          for (int u = start; u < v; ++u) {
+            double dot = 0;
+            for (int i = 0; i < m; ++i) dot += zt[(size_t)u * m + i] * xv[i];
+            for (int i = 0; i < m; ++i) xv[i] -= dot * zt[(size_t)u * m + i];
+          }
+          double nrm = 0;
+          for (int i = 0; i < m; ++i) nrm += xv[i] * xv[i];
+          nrm = 1.0 / sqrt(fmax(nrm, 1e-300));
+          for (int i = 0; i < m; ++i) xv[i] *= nrm;
+        }
+        for (int i = 0; i < m; ++i) zt[(size_t)v * m + i] = xv[i];
+      }
+    }
+    cl.sync();
+  }
+  RR_MARK(5);
+  // 7. u = H_0 ... H_{m-3} (Phi z); V = D L^-H u
+  for (int j = gw; j < n; j += gnw) {
+    for (int i = lane; i < m; i += 32) {
+      const double z = zt[(size_t)j * m + i];
+      wvec[i] = double2{ph[i].x * z, ph[i].y * z};
+    }
+    __syncwarp();
+    for (int k = m - 3; k >= 0; --k) {
+      const double t = tau[k].x;
+      if (t == 0.0) continue;
+      const double2* v = cm + (size_t)k * m + k + 1;
+      const int len = m - k - 1;
+      double2 s{0, 0};
+      for (int i = lane; i < len; i += 32) s = cadd(s, cmulc(v[i], wvec[k + 1 + i]));
+      s = warp_csum(s);
+      s = double2{t * s.x, t * s.y};
+      for (int i = lane; i < len; i += 32) wvec[k + 1 + i] = csub(wvec[k + 1 + i], cmul(s, v[i]));
+      __syncwarp();
+    }
+    // L^H y = u (upper triangular, back substitution); L^H[i, k] = conj(L[k, i]) = conj(lf[i*m + k])
+    for (int i = m - 1; i >= 0; --i) {
+      double2 s{0, 0};
+      for (int k = i + 1 + lane; k < m; k += 32) s = cadd(s, cmulc(lf[(size_t)i * m + k], wvec[k]));
+      s = warp_csum(s);
+      const double lii = lf[(size_t)i * m + i].x;
+      const double2 u = wvec[i];
+      if (lane == 0) wvec[i] = double2{(u.x - s.x) / lii, (u.y - s.y) / lii};
+      __syncwarp();
+    }
+    for (int i = lane; i < m; i += 32) {
+      const double2 y = wvec[i];
+      V[(size_t)j * m + i] = double2{dsc[i] * y.x, dsc[i] * y.y};
+    }
+    if (lane == 0) lam[j] = lamw[j];
+    __syncwarp();
+  }
+  if (gtid == 0) {
+    info[0] = 0;
+    info[1] = m;
+    info[2] = 0;
+  }
+#ifdef DKS_RR_TIMING
+  RR_MARK(6);
+  if (gtid == 0)
+    printf("rr_cluster m=%d n=%d csize=%d: chol %.1f trsm %.1f householder %.1f multisect %.1f invit %.1f backtr %.1f us\n",
+           m, n, csize, (tmark[1] - tmark[0]) * 1e-3, (tmark[2] - tmark[1]) * 1e-3, (tmark[3] - tmark[2]) * 1e-3,
+           (tmark[4] - tmark[3]) * 1e-3, (tmark[5] - tmark[4]) * 1e-3, (tmark[6] - tmark[5]) * 1e-3);
+#endif
+}
+
+// byte offset of the hand-off flag inside the scratch layout above
+size_t rr_cluster_flag_offset(int m) {
+  const size_t mm = (size_t)m * m;
+  return 5 * mm * sizeof(double2) + 6 * (size_t)m * sizeof(double) + 3 * (size_t)m * sizeof(double2);
+}
+
+static int g_cluster = 0;   // 0 = unknown, else cluster size that launched successfully
+
+int rayleigh_ritz_cluster(const double2* a, const double2* s, int nz, int n, double2* v, double* lam, int* info,
+                          double2* scratch, cudaStream_t st, double chol_tol, bool* launched) {
+  *launched = false;
+  const size_t smem = std::max<size_t>((size_t)RRC_WARPS * nz * sizeof(double2), 48 * 1024 + 64);
+  if (smem > 200 * 1024) return DKS_OK;     // too large for the per-warp vectors: caller falls back
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute((const void*)k_rr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute((const void*)k_rr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_done = true;
+  }
+  const int tries[2] = {16, 8};
+  for (int t = 0; t < 2; ++t) {
+    const int csz = g_cluster ? g_cluster : tries[t];
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csz, 1, 1);
+    cfg.blockDim = dim3(RRC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csz;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    Prof pr(P_RR, st, 2.0 * nz * nz * 16.0 + 16.0 * nz * n, 0.0);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_rr_cluster, a, s, nz, n, v, lam, info, scratch, chol_tol);
+    if (e == cudaSuccess) {
+      g_cluster = csz;
+      *launched = true;
+      return DKS_OK;
+    }
+    cudaGetLastError();   // clear the launch error and try the portable size
+    if (g_cluster) break;
+  }
+  return DKS_OK;
+}
+
+}  // namespace dks

@@ -174,10 +174,12 @@ static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int
       break;
     }
     if (stop_on_stall) {
+      // FP32 phase: stop at its rounding floor -- no 30% gain in 3 iterations, or a jump above
+      // twice the best residual (FP32 noise reaching the negative band)
       if (maxres < 0.7 * best) {
         best = maxres;
         since_best = 0;
-      } else if (++since_best >= 4) {
+      } else if (++since_best >= 3 || maxres > 2.0 * best) {
         cur = nx;
         break;
       }

@@ -55,7 +55,7 @@ def _pencil(nz, seed, rank_def=False, degenerate=False):
     if degenerate:
         # pencil with exactly repeated generalized eigenvalues: A = Z^H W Z, S = Z^H Z (Z square)
         zq = zz[:nz]
-        w = np.repeat(np.arange(nz // 2, dtype=float), 2)[:nz] - 3.0
+        w = np.repeat(np.arange((nz + 1) // 2, dtype=float), 2)[:nz] - 3.0
         return zq.conj().T @ (w[:, None] * zq), zq.conj().T @ zq
     hm = rng.standard_normal((nn, nn)) + 1j * rng.standard_normal((nn, nn))
     hm = hm + hm.conj().T
@@ -63,7 +63,8 @@ def _pencil(nz, seed, rank_def=False, degenerate=False):
 
 
 @pytest.mark.parametrize("nz,n,kind", [(96, 32, "plain"), (40, 12, "rankdef"), (24, 24, "plain"),
-                                       (60, 20, "degenerate"), (1, 1, "plain"), (200, 64, "plain")])
+                                       (60, 20, "degenerate"), (1, 1, "plain"), (200, 64, "plain"),
+                                       (37, 9, "plain"), (2, 1, "plain"), (3, 2, "degenerate")])
 def test_rayleigh_ritz(nz, n, kind):
     torch = gpu()
     import paper_1211_1446_gb300 as P
