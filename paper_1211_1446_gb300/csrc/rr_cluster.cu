@@ -71,6 +71,19 @@ __device__ int sturm_count(const double* d, const double* e2, int m, double x, d
   return cnt;
 }
 
+__device__ int sturm_count_f(const float* d, const float* e2, int m, float x, float pivmin) {
+  int cnt = 0;
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  cnt += q < 0.f;
+  for (int j = 1; j < m; ++j) {
+    q = d[j] - x - e2[j - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += q < 0.f;
+  }
+  return cnt;
+}
+
 // deterministic start vector in (-1, 1)
 __device__ __forceinline__ double start_val(int i, int v) {
   unsigned h = (unsigned)(i * 2654435761u) ^ (unsigned)(v * 40503u + 12345u);
@@ -121,6 +134,7 @@ __device__ void tri_factor(const double* d, const double* e, int m, double lam, 
   u0[m - 1] = a;
   u1[m - 1] = 0.0;
   u2[m - 1] = 0.0;
+  for (int i = 0; i < m; ++i) u0[i] = 1.0 / u0[i];   // the solves multiply by reciprocals
 }
 
 __device__ void tri_solve(int m, const double* f, double* x) {
@@ -138,9 +152,18 @@ __device__ void tri_solve(int m, const double* f, double* x) {
       x[i + 1] -= l[i] * x[i];
     }
   }
-  x[m - 1] /= u0[m - 1];
-  if (m > 1) x[m - 2] = (x[m - 2] - u1[m - 2] * x[m - 1]) / u0[m - 2];
-  for (int i = m - 3; i >= 0; --i) x[i] = (x[i] - u1[i] * x[i + 1] - u2[i] * x[i + 2]) / u0[i];
+  x[m - 1] *= u0[m - 1];
+  if (m > 1) x[m - 2] = (x[m - 2] - u1[m - 2] * x[m - 1]) * u0[m - 2];
+  for (int i = m - 3; i >= 0; --i) x[i] = (x[i] - u1[i] * x[i + 1] - u2[i] * x[i + 2]) * u0[i];
+}
+
+// shared memory: per-warp complex vectors (or inverse-iteration slots), then the tridiagonal
+__host__ __device__ inline size_t rr_tri_smem_offset(int m) {
+  const size_t vec = (size_t)RRC_WARPS * m * sizeof(double2);
+  return vec > 48 * 1024 ? vec : 48 * 1024;
+}
+__host__ __device__ inline size_t rr_cluster_smem(int m) {
+  return rr_tri_smem_offset(m) + (size_t)m * (3 * sizeof(double) + 2 * sizeof(float)) + 64;
 }
 
 __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __restrict__ A,
@@ -219,6 +242,9 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
     return;   // every CTA leaves here; the single-CTA SVQB kernel that follows takes over
   }
   if (gtid == 0) *flag = 0;
+  double* linv = lamw + m;     // 1 / L_ii (the spare m-array)
+  for (int i = gtid; i < m; i += gnt) linv[i] = 1.0 / lt[(size_t)i * m + i].x;
+  cl.sync();
   RR_MARK(1);
   double2* wvec = reinterpret_cast<double2*>(rrc_smem) + (size_t)wl * m;   // per-warp vector
   // 3a. W = L^-1 A'  (column c of A' -> column c of W, stored in cm)
@@ -227,9 +253,9 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
       double2 s{0, 0};
       for (int k = lane; k < i; k += 32) s = cadd(s, cmul(lt[(size_t)i * m + k], wvec[k]));
       s = warp_csum(s);
-      const double lii = lt[(size_t)i * m + i].x;
+      const double li = linv[i];
       const double2 a = am[(size_t)c * m + i];
-      const double2 w = double2{(a.x - s.x) / lii, (a.y - s.y) / lii};
+      const double2 w = double2{(a.x - s.x) * li, (a.y - s.y) * li};
       if (lane == 0) wvec[i] = w;
       __syncwarp();
     }
@@ -244,9 +270,9 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
       double2 s{0, 0};
       for (int k = lane; k < i; k += 32) s = cadd(s, cmul(lt[(size_t)i * m + k], wvec[k]));
       s = warp_csum(s);
-      const double lii = lt[(size_t)i * m + i].x;
+      const double li = linv[i];
       const double2 b = cm[(size_t)i * m + c];      // W[c, i]
-      const double2 w = double2{(b.x - s.x) / lii, (-b.y - s.y) / lii};
+      const double2 w = double2{(b.x - s.x) * li, (-b.y - s.y) * li};
       if (lane == 0) wvec[i] = w;
       __syncwarp();
     }
@@ -340,20 +366,51 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
     e2[m - 1] = 0;
   }
   cl.sync();
+  // copy the tridiagonal into this CTA's shared memory (behind the per-warp vectors)
+  double* sd = reinterpret_cast<double*>(rrc_smem + rr_tri_smem_offset(m));
+  double* se = sd + m;
+  double* se2 = se + m;
+  float* fd = reinterpret_cast<float*>(se2 + m);
+  float* fe2 = fd + m;
+  for (int k = tid; k < m; k += RRC_THREADS) {
+    sd[k] = dd[k];
+    se[k] = ee[k];
+    se2[k] = e2[k];
+    fd[k] = (float)dd[k];
+    fe2[k] = (float)e2[k];
+  }
+  __syncthreads();
   double tnorm = 0, lo0 = INFINITY, hi0 = -INFINITY;
   for (int k = 0; k < m; ++k) {
-    const double r = (k > 0 ? ee[k - 1] : 0.0) + (k + 1 < m ? ee[k] : 0.0);
-    lo0 = fmin(lo0, dd[k] - r);
-    hi0 = fmax(hi0, dd[k] + r);
+    const double r = (k > 0 ? se[k - 1] : 0.0) + (k + 1 < m ? se[k] : 0.0);
+    lo0 = fmin(lo0, sd[k] - r);
+    hi0 = fmax(hi0, sd[k] + r);
   }
   tnorm = fmax(fabs(lo0), fabs(hi0));
   const double pivmin = fmax(1e-290, DBL_MIN * 4.0) + 1e-300;
-  // multisection: warp gw finds eigenvalue index gw (ascending)
+  // multisection: warp gw finds eigenvalue index gw (ascending); four 33-way FP32 steps first,
+  // then the bracket is widened by the FP32 rounding level and refined in FP64
   for (int idx = gw; idx < n; idx += gnw) {
     double lo = lo0 - 1e-14 * tnorm - 1e-300, hi = hi0 + 1e-14 * tnorm + 1e-300;
+    {
+      float flo = (float)lo, fhi = (float)hi;
+      for (int it = 0; it < 4; ++it) {
+        const float x = flo + (fhi - flo) * (float)(lane + 1) / 33.0f;
+        const int cnt = sturm_count_f(fd, fe2, m, x, 1e-30f);
+        const unsigned above = __ballot_sync(0xffffffffu, cnt > idx);
+        const int first = above ? __ffs(above) - 1 : 32;
+        const float nhi = first < 32 ? flo + (fhi - flo) * (float)(first + 1) / 33.0f : fhi;
+        const float nlo = first > 0 ? flo + (fhi - flo) * (float)first / 33.0f : flo;
+        flo = nlo;
+        fhi = nhi;
+      }
+      const double pad = 1e-5 * tnorm + 1e-300;
+      lo = fmax(lo, (double)flo - pad);
+      hi = fmin(hi, (double)fhi + pad);
+    }
     for (int it = 0; it < 40 && hi - lo > 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300; ++it) {
       const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-      const int cnt = sturm_count(dd, e2, m, x, pivmin);
+      const int cnt = sturm_count(sd, se2, m, x, pivmin);
       const unsigned above = __ballot_sync(0xffffffffu, cnt > idx);
       const int first = above ? __ffs(above) - 1 : 32;    // first point with count > idx
       const double nhi = first < 32 ? lo + (hi - lo) * (double)(first + 1) / 33.0 : hi;
@@ -367,7 +424,7 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
   RR_MARK(4);
   // 6. inverse iteration; clusters of close eigenvalues go to one lane in order
   const double ortol = 1e-7 * fmax(tnorm, 1e-300);
-  const int nslots = min(RRC_WARPS, (int)(48 * 1024 / (sizeof(double) * 6 * (size_t)m)));
+  const int nslots = min(RRC_WARPS, (int)(rr_tri_smem_offset(m) / (sizeof(double) * 6 * (size_t)m)));
   double* fws = reinterpret_cast<double*>(rrc_smem);   // per-slot 5m factors + m vector
   for (int start = gw; start < n; start += gnw) {
     // one lane (lane 0) of this warp handles the cluster that begins at `start`
@@ -379,9 +436,9 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
     double* xv = f + 5 * m;
     for (int v = start; v < end; ++v) {
       const double shift = lamw[v] + (double)(v - start) * 10.0 * DBL_EPSILON * tnorm;
-      tri_factor(dd, ee, m, shift, DBL_EPSILON * tnorm + 1e-300, f);
+      tri_factor(sd, se, m, shift, DBL_EPSILON * tnorm + 1e-300, f);
       for (int i = 0; i < m; ++i) xv[i] = start_val(i, v);
-      for (int itr = 0; itr < 4; ++itr) {
+      for (int itr = 0; itr < 3; ++itr) {
         tri_solve(m, f, xv);
         for (int u = start; u < v; ++u) {        // orthogonalise against the cluster's earlier vectors
           double dot = 0;
@@ -410,9 +467,9 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
       double* xv = f + 5 * m;
       for (int v = start; v < end; ++v) {
         const double shift = lamw[v] + (double)(v - start) * 10.0 * DBL_EPSILON * tnorm;
-        tri_factor(dd, ee, m, shift, DBL_EPSILON * tnorm + 1e-300, f);
+        tri_factor(sd, se, m, shift, DBL_EPSILON * tnorm + 1e-300, f);
         for (int i = 0; i < m; ++i) xv[i] = start_val(i, v);
-        for (int itr = 0; itr < 4; ++itr) {
+        for (int itr = 0; itr < 3; ++itr) {
           tri_solve(m, f, xv);
           for (int u = start; u < v; ++u) {
             double dot = 0;
@@ -454,9 +511,9 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
       double2 s{0, 0};
       for (int k = i + 1 + lane; k < m; k += 32) s = cadd(s, cmulc(lf[(size_t)i * m + k], wvec[k]));
       s = warp_csum(s);
-      const double lii = lf[(size_t)i * m + i].x;
+      const double li = linv[i];
       const double2 u = wvec[i];
-      if (lane == 0) wvec[i] = double2{(u.x - s.x) / lii, (u.y - s.y) / lii};
+      if (lane == 0) wvec[i] = double2{(u.x - s.x) * li, (u.y - s.y) * li};
       __syncwarp();
     }
     for (int i = lane; i < m; i += 32) {
@@ -491,7 +548,7 @@ static int g_cluster = 0;   // 0 = unknown, else cluster size that launched succ
 int rayleigh_ritz_cluster(const double2* a, const double2* s, int nz, int n, double2* v, double* lam, int* info,
                           double2* scratch, cudaStream_t st, double chol_tol, bool* launched) {
   *launched = false;
-  const size_t smem = std::max<size_t>((size_t)RRC_WARPS * nz * sizeof(double2), 48 * 1024 + 64);
+  const size_t smem = rr_cluster_smem(nz);
   if (smem > 200 * 1024) return DKS_OK;     // too large for the per-warp vectors: caller falls back
   static bool attr_done = false;
   if (!attr_done) {
