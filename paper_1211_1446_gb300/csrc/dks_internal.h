@@ -132,20 +132,24 @@ int apply_h(dks_ctx* ctx, int ik, const V* x, V* out, int nb, double shift, doub
             cudaStream_t st);
 
 // kernels shared by the solver and the single-step entry points
-template <typename V>
-int gemm_hn(const V* a, int lda, const V* b, int ldb, int k, int m, int n, double2* c,
-            cudaStream_t st, int cat = P_GRAM);  // c (m x n, col-major, ld m) += a^H b, FP64 atomics
-template <typename V>
-int gemm_nn(const V* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
-            int n, V* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0,
+template <typename Va, typename Vb = Va, bool Acc64 = false>
+int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, double2* c,
+            cudaStream_t st, int cat = P_GRAM, int ldc = 0, bool lower = false);
+// c (m x n, col-major, leading dimension ldc or m) += a^H b, FP64 atomics; FP64 arithmetic when
+// either operand is complex128 or Acc64; lower: only the block lower triangle (square results)
+int mirror_lower(double2* c, int m, cudaStream_t st);   // upper triangle = conj of the lower
+template <typename Va, typename Vo = Va>
+int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
+            int n, Vo* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0,
             int cat = P_ROTATE);
-// out (k x n) = alpha * a (k x m) * (diag(wscale) w) + beta * out; wscale may be NULL
+// out (k x n) = alpha * a (k x m) * (diag(wscale) w) + beta * out; wscale may be NULL;
+// FP64 arithmetic when a or out is complex128
 template <typename V>
 int col_stats(const V* x, const V* hx, const double* lam, const double* ek, int npw, int n,
               double* stats, cudaStream_t st);  // stats[3j..]: |hx - lam x|^2, |x|^2, sum ek|x|^2
-template <typename V>
+template <typename V, typename Vo = V>
 int precond_apply(const V* x, const V* hx, const double* lam, const double* stats, const int* act,
-                  int nact, const double* ek, int npw, int precond, V* y, cudaStream_t st);
+                  int nact, const double* ek, int npw, int precond, Vo* y, cudaStream_t st);
 int rayleigh_ritz(const double2* a, const double2* s, int nz, int n, double2* v, double* lam,
                   int* info, double2* scratch, cudaStream_t st, double chol_tol = 1e-12,
                   double drop_tol = 1e-12);

@@ -13,40 +13,56 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "dks_internal.h"
 #include "dks_kernels.cuh"
 
 namespace dks {
 
-template <typename V> struct Acc;
-template <> struct Acc<double2> { using T = double2; };
-template <> struct Acc<float2> { using T = float2; };
+// accumulation type: FP64 as soon as one operand is FP64
+template <typename A, typename B> struct AccOf { using T = double2; };
+template <> struct AccOf<float2, float2> { using T = float2; };
+template <typename T> __device__ __forceinline__ T cvt(double2 v);
+template <> __device__ __forceinline__ double2 cvt<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 cvt<float2>(double2 v) { return float2{(float)v.x, (float)v.y}; }
+template <typename T> __device__ __forceinline__ T cvt(float2 v);
+template <> __device__ __forceinline__ double2 cvt<double2>(float2 v) { return double2{v.x, v.y}; }
+template <> __device__ __forceinline__ float2 cvt<float2>(float2 v) { return v; }
 
 // ---------------------------------------------------------------- gemm_hn
 constexpr int HN_T = 32;
 
-template <typename V>
-__global__ void __launch_bounds__(256) k_gemm_hn(const V* __restrict__ a, int lda, const V* __restrict__ b,
+template <typename Va, typename Vb, typename A>
+__global__ void __launch_bounds__(256) k_gemm_hn(const Va* __restrict__ a, int lda, const Vb* __restrict__ b,
                                                  int ldb, int k, int m, int n, int mt, int kchunk,
-                                                 double2* __restrict__ c) {
-  __shared__ V as[HN_T][HN_T + 1];
-  __shared__ V bs[HN_T][HN_T + 1];
-  const int tile = blockIdx.x;
-  const int m0 = (tile % mt) * HN_T, n0 = (tile / mt) * HN_T;
+                                                 double2* __restrict__ c, int ldc, int lower) {
+  __shared__ A as[HN_T][HN_T + 1];
+  __shared__ A bs[HN_T][HN_T + 1];
+  int tm, tn;
+  if (lower) {   // only tiles with tn <= tm (the block lower triangle of a Hermitian result)
+    const int t = blockIdx.x;
+    tm = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
+    while (tm * (tm + 1) / 2 > t) --tm;
+    tn = t - tm * (tm + 1) / 2;
+  } else {
+    tm = blockIdx.x % mt;
+    tn = blockIdx.x / mt;
+  }
+  const int m0 = tm * HN_T, n0 = tn * HN_T;
   const int kb = blockIdx.y * kchunk;
   const int ke = min(k, kb + kchunk);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  using A = typename Acc<V>::T;
   A acc[2][2] = {{A{0, 0}, A{0, 0}}, {A{0, 0}, A{0, 0}}};
   for (int k0 = kb; k0 < ke; k0 += HN_T) {
     for (int e = threadIdx.x; e < HN_T * HN_T; e += 256) {
       const int kq = e & (HN_T - 1), q = e >> 5;
       const int gk = k0 + kq;
-      V va{0, 0}, vb{0, 0};
+      A va{0, 0}, vb{0, 0};
       if (gk < ke) {
-        if (m0 + q < m) va = a[(size_t)(m0 + q) * lda + gk];
-        if (n0 + q < n) vb = b[(size_t)(n0 + q) * ldb + gk];
+        if (m0 + q < m) va = cvt<A>(a[(size_t)(m0 + q) * lda + gk]);
+        if (n0 + q < n) vb = cvt<A>(b[(size_t)(n0 + q) * ldb + gk]);
       }
       as[kq][q] = va;
       bs[kq][q] = vb;
@@ -54,8 +70,8 @@ __global__ void __launch_bounds__(256) k_gemm_hn(const V* __restrict__ a, int ld
     __syncthreads();
 #pragma unroll 8
     for (int kq = 0; kq < HN_T; ++kq) {
-      const V a0 = as[kq][ty], a1 = as[kq][ty + 16];
-      const V b0 = bs[kq][tx], b1 = bs[kq][tx + 16];
+      const A a0 = as[kq][ty], a1 = as[kq][ty + 16];
+      const A b0 = bs[kq][tx], b1 = bs[kq][tx + 16];
       acc[0][0] = cadd(acc[0][0], cmulc(a0, b0));
       acc[0][1] = cadd(acc[0][1], cmulc(a0, b1));
       acc[1][0] = cadd(acc[1][0], cmulc(a1, b0));
@@ -69,8 +85,8 @@ __global__ void __launch_bounds__(256) k_gemm_hn(const V* __restrict__ a, int ld
     for (int j = 0; j < 2; ++j) {
       const int mm = m0 + ty + 16 * i, nn = n0 + tx + 16 * j;
       if (mm < m && nn < n) {
-        atomicAdd(&c[(size_t)nn * m + mm].x, (double)acc[i][j].x);
-        atomicAdd(&c[(size_t)nn * m + mm].y, (double)acc[i][j].y);
+        atomicAdd(&c[(size_t)nn * ldc + mm].x, (double)acc[i][j].x);
+        atomicAdd(&c[(size_t)nn * ldc + mm].y, (double)acc[i][j].y);
       }
     }
 }
@@ -86,20 +102,46 @@ static int num_sms() {
   return g_num_sms;
 }
 
-template <typename V>
-int gemm_hn(const V* a, int lda, const V* b, int ldb, int k, int m, int n, double2* c, cudaStream_t st,
-            int cat) {
+template <typename Va, typename Vb, bool Acc64>
+int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, double2* c, cudaStream_t st,
+            int cat, int ldc, bool lower) {
   if (m <= 0 || n <= 0 || k <= 0) return DKS_OK;
+  if (ldc <= 0) ldc = m;
+  if (lower && m != n) return fail(DKS_ERR_INVALID_ARG, "gemm_hn: lower-triangle mode needs a square result");
   const int mt = (m + HN_T - 1) / HN_T, nt = (n + HN_T - 1) / HN_T;
+  const int tiles = lower ? mt * (mt + 1) / 2 : mt * nt;
   const int ktiles = (k + HN_T - 1) / HN_T;
-  int splits = std::max(1, (4 * num_sms()) / (mt * nt));
+  int splits = std::max(1, (4 * num_sms()) / tiles);
   splits = std::min(splits, ktiles);
   const int kchunk = ((ktiles + splits - 1) / splits) * HN_T;
   splits = (k + kchunk - 1) / kchunk;
-  dim3 grid(mt * nt, splits);
-  const double es = (double)sizeof(V);
-  Prof pr(cat, st, ((a == b) ? (double)m : (double)(m + n)) * k * es + 16.0 * m * n, 8.0 * m * n * (double)k);
-  k_gemm_hn<V><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c);
+  dim3 grid(tiles, splits);
+  const bool same = (const void*)a == (const void*)b;
+  Prof pr(cat, st, (same ? (double)m * sizeof(Va) : (double)m * sizeof(Va) + (double)n * sizeof(Vb)) * k +
+                       16.0 * m * n,
+          (lower ? 4.0 * m * (m + 1.0) : 8.0 * m * n) * (double)k);
+  using A = typename std::conditional<Acc64, double2, typename AccOf<Va, Vb>::T>::type;
+  k_gemm_hn<Va, Vb, A><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
+}
+
+// upper triangle of a Hermitian m x m matrix from its lower triangle
+__global__ void k_mirror_lower(double2* __restrict__ c, int m) {
+  const int total = m * m;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int i = e % m, j = e / m;
+    if (i < j) {
+      const double2 v = c[(size_t)i * m + j];
+      c[e] = double2{v.x, -v.y};
+    }
+  }
+}
+
+int mirror_lower(double2* c, int m, cudaStream_t st) {
+  if (m <= 1) return DKS_OK;
+  Prof pr(P_MISC, st, 16.0 * m * m, 0.0);
+  k_mirror_lower<<<std::min(1024, (m * m + 255) / 256), 256, 0, st>>>(c, m);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
@@ -107,24 +149,24 @@ int gemm_hn(const V* a, int lda, const V* b, int ldb, int k, int m, int n, doubl
 // ---------------------------------------------------------------- gemm_nn
 constexpr int NN_R = 64, NN_C = 32, NN_M = 16;
 
-template <typename V>
-__global__ void __launch_bounds__(256) k_gemm_nn(const V* __restrict__ a, int lda, int k, int m,
+template <typename Va, typename Vo>
+__global__ void __launch_bounds__(256) k_gemm_nn(const Va* __restrict__ a, int lda, int k, int m,
                                                  const double2* __restrict__ w, int ldw,
-                                                 const double* __restrict__ ws, int n, V* __restrict__ out,
+                                                 const double* __restrict__ ws, int n, Vo* __restrict__ out,
                                                  int ldo, double alpha, double beta) {
-  __shared__ V as[NN_M][NN_R];
-  __shared__ V wsm[NN_M][NN_C];
+  using A = typename AccOf<Va, Vo>::T;
+  __shared__ A as[NN_M][NN_R];
+  __shared__ A wsm[NN_M][NN_C];
   const int r0 = blockIdx.x * NN_R, c0 = blockIdx.y * NN_C;
   const int row = threadIdx.x & (NN_R - 1), cg = threadIdx.x >> 6;
-  using A = typename Acc<V>::T;
   A acc[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) acc[j] = A{0, 0};
   for (int m0 = 0; m0 < m; m0 += NN_M) {
     for (int e = threadIdx.x; e < NN_M * NN_R; e += 256) {
       const int rr = e & (NN_R - 1), mm = e >> 6;
-      V v{0, 0};
-      if (m0 + mm < m && r0 + rr < k) v = a[(size_t)(m0 + mm) * lda + r0 + rr];
+      A v{0, 0};
+      if (m0 + mm < m && r0 + rr < k) v = cvt<A>(a[(size_t)(m0 + mm) * lda + r0 + rr]);
       as[mm][rr] = v;
     }
     for (int e = threadIdx.x; e < NN_M * NN_C; e += 256) {
@@ -136,12 +178,12 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const V* __restrict__ a, int ld
         v.x *= s;
         v.y *= s;
       }
-      wsm[mm][cc] = from_d2<V>(v);
+      wsm[mm][cc] = cvt<A>(v);
     }
     __syncthreads();
 #pragma unroll 4
     for (int mm = 0; mm < NN_M; ++mm) {
-      const V av = as[mm][row];
+      const A av = as[mm][row];
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[j] = cadd(acc[j], cmul(av, wsm[mm][cg * 8 + j]));
     }
@@ -152,27 +194,27 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const V* __restrict__ a, int ld
     for (int j = 0; j < 8; ++j) {
       const int cc = c0 + cg * 8 + j;
       if (cc < n) {
-        V* o = out + (size_t)cc * ldo + r0 + row;
-        V r = acc[j];
+        Vo* o = out + (size_t)cc * ldo + r0 + row;
+        A r = acc[j];
         if (beta != 0.0) {
-          const V old = *o;
-          r.x += (typename RealOf<V>::T)beta * old.x;
-          r.y += (typename RealOf<V>::T)beta * old.y;
+          const A old = cvt<A>(*o);
+          r.x += (typename RealOf<A>::T)beta * old.x;
+          r.y += (typename RealOf<A>::T)beta * old.y;
         }
-        *o = r;
+        *o = from_d2<Vo>(to_d2(r));
       }
     }
   }
 }
 
-template <typename V>
-int gemm_nn(const V* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
-            V* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
+template <typename Va, typename Vo>
+int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
+            Vo* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
   if (k <= 0 || n <= 0) return DKS_OK;
   dim3 grid((k + NN_R - 1) / NN_R, (n + NN_C - 1) / NN_C);
-  const double es = (double)sizeof(V);
-  Prof pr(cat, st, ((double)m + (beta != 0.0 ? 2.0 : 1.0) * n) * k * es + 16.0 * m * n, 8.0 * (double)k * m * n);
-  k_gemm_nn<V><<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
+  Prof pr(cat, st, (double)m * k * sizeof(Va) + (beta != 0.0 ? 2.0 : 1.0) * n * k * sizeof(Vo) + 16.0 * m * n,
+          8.0 * (double)k * m * n);
+  k_gemm_nn<Va, Vo><<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
@@ -242,10 +284,10 @@ int col_stats(const V* x, const V* hx, const double* lam, const double* ek, int 
 }
 
 // ---------------------------------------------------------------- Teter preconditioner
-template <typename V>
+template <typename V, typename Vo>
 __global__ void k_precond(const V* __restrict__ x, const V* __restrict__ hx, const double* __restrict__ lam,
                           const double* __restrict__ stats, const int* __restrict__ act, int nact,
-                          const double* __restrict__ ek, int npw, int precond, V* __restrict__ y) {
+                          const double* __restrict__ ek, int npw, int precond, Vo* __restrict__ y) {
   using T = typename RealOf<V>::T;
   const size_t rows = (size_t)4 * npw;
   const size_t total = rows * nact;
@@ -268,18 +310,18 @@ __global__ void k_precond(const V* __restrict__ x, const V* __restrict__ hx, con
       r.x *= kf;
       r.y *= kf;
     }
-    y[(size_t)i * rows + rr] = r;
+    y[(size_t)i * rows + rr] = from_d2<Vo>(to_d2(r));
   }
 }
 
-template <typename V>
+template <typename V, typename Vo>
 int precond_apply(const V* x, const V* hx, const double* lam, const double* stats, const int* act, int nact,
-                  const double* ek, int npw, int precond, V* y, cudaStream_t st) {
+                  const double* ek, int npw, int precond, Vo* y, cudaStream_t st) {
   if (nact <= 0) return DKS_OK;
   const size_t total = (size_t)4 * npw * nact;
   const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)num_sms() * 16);
   Prof pr(P_PRECOND, st, 3.0 * total * sizeof(V) + 8.0 * npw, 20.0 * total);
-  k_precond<V><<<blocks, 256, 0, st>>>(x, hx, lam, stats, act, nact, ek, npw, precond, y);
+  k_precond<V, Vo><<<blocks, 256, 0, st>>>(x, hx, lam, stats, act, nact, ek, npw, precond, y);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
@@ -321,21 +363,30 @@ int gather_cols(const double2* v, int ldv, int row0, int rows, const int* act, i
 }
 
 // explicit instantiations
-template int gemm_hn<double2>(const double2*, int, const double2*, int, int, int, int, double2*, cudaStream_t,
-                              int);
-template int gemm_hn<float2>(const float2*, int, const float2*, int, int, int, int, double2*, cudaStream_t, int);
-template int gemm_nn<double2>(const double2*, int, int, int, const double2*, int, const double*, int, double2*,
-                              int, double, cudaStream_t, double, int);
-template int gemm_nn<float2>(const float2*, int, int, int, const double2*, int, const double*, int, float2*, int,
-                             double, cudaStream_t, double, int);
+#define DKS_INST_HN(TA, TB, ACC)                                                                        \
+  template int gemm_hn<TA, TB, ACC>(const TA*, int, const TB*, int, int, int, int, double2*, cudaStream_t, int, \
+                                    int, bool);
+DKS_INST_HN(double2, double2, false)
+DKS_INST_HN(float2, float2, false)
+DKS_INST_HN(float2, float2, true)
+DKS_INST_HN(double2, float2, false)
+DKS_INST_HN(float2, double2, false)
+template int gemm_nn<double2, double2>(const double2*, int, int, int, const double2*, int, const double*, int,
+                                       double2*, int, double, cudaStream_t, double, int);
+template int gemm_nn<float2, float2>(const float2*, int, int, int, const double2*, int, const double*, int,
+                                     float2*, int, double, cudaStream_t, double, int);
+template int gemm_nn<float2, double2>(const float2*, int, int, int, const double2*, int, const double*, int,
+                                      double2*, int, double, cudaStream_t, double, int);
 template int col_stats<double2>(const double2*, const double2*, const double*, const double*, int, int, double*,
                                 cudaStream_t);
 template int col_stats<float2>(const float2*, const float2*, const double*, const double*, int, int, double*,
                                cudaStream_t);
-template int precond_apply<double2>(const double2*, const double2*, const double*, const double*, const int*, int,
-                                    const double*, int, int, double2*, cudaStream_t);
-template int precond_apply<float2>(const float2*, const float2*, const double*, const double*, const int*, int,
-                                   const double*, int, int, float2*, cudaStream_t);
+template int precond_apply<double2, double2>(const double2*, const double2*, const double*, const double*,
+                                             const int*, int, const double*, int, int, double2*, cudaStream_t);
+template int precond_apply<float2, float2>(const float2*, const float2*, const double*, const double*, const int*,
+                                           int, const double*, int, int, float2*, cudaStream_t);
+template int precond_apply<double2, float2>(const double2*, const double2*, const double*, const double*,
+                                            const int*, int, const double*, int, int, float2*, cudaStream_t);
 template int convert<double2, float2>(const double2*, float2*, size_t, cudaStream_t);
 template int convert<float2, double2>(const float2*, double2*, size_t, cudaStream_t);
 template int convert<double2, double2>(const double2*, double2*, size_t, cudaStream_t);

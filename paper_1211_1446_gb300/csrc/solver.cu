@@ -90,8 +90,10 @@ template <typename V>
 static int gram(const V* z, const V* hz, int rows, int nz, Small& sm, cudaStream_t st) {
   DKS_CUDA_TRY(cudaMemsetAsync(sm.a, 0, (size_t)nz * nz * sizeof(double2), st));
   DKS_CUDA_TRY(cudaMemsetAsync(sm.s, 0, (size_t)nz * nz * sizeof(double2), st));
-  DKS_TRY(gemm_hn<V>(z, rows, hz, rows, rows, nz, nz, sm.a, st));
-  return gemm_hn<V>(z, rows, z, rows, rows, nz, nz, sm.s, st);
+  DKS_TRY(gemm_hn<V>(z, rows, hz, rows, rows, nz, nz, sm.a, st, P_GRAM, 0, true));
+  DKS_TRY(gemm_hn<V>(z, rows, z, rows, rows, nz, nz, sm.s, st, P_GRAM, 0, true));
+  DKS_TRY(mirror_lower(sm.a, nz, st));
+  return mirror_lower(sm.s, nz, st);
 }
 
 // reads lam and residual statistics of the n columns; returns the host residual norms
@@ -211,6 +213,7 @@ static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int
   return DKS_OK;
 }
 
+
 }  // namespace dks
 
 using namespace dks;
@@ -277,13 +280,13 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
     off += (bytes + 255) / 256 * 256;
     return p;
   };
-  Blocks<double2> b64;
+  Blocks<double2> b64{};
+  Blocks<float2> b32{};
   b64.z[0] = (double2*)take(big64);
   b64.z[1] = (double2*)take(big64);
   b64.hz[0] = (double2*)take(big64);
   b64.hz[1] = (double2*)take(big64);
   b64.tmp = (double2*)take(tmp64);
-  Blocks<float2> b32{};
   if (mixed) {
     b32.z[0] = (float2*)take(big32);
     b32.z[1] = (float2*)take(big32);
