@@ -48,6 +48,9 @@ extern "C" {
 
 #define DKS_PREC_FP64 0  /* complex128 storage, FP64 arithmetic                      */
 #define DKS_PREC_FP32 1  /* complex64 storage, FP32 arithmetic (FP64 Dirac 4x4 term) */
+#define DKS_PREC_FP64_EMULATED 2 /* complex128 storage; the tall-skinny contractions (Gram,
+                                    rotations, projectors) in double-float arithmetic on the
+                                    FP32 units (~48-bit significand), everything else FP64   */
 
 typedef struct dks_ctx dks_ctx; /* opaque; owns basis tables and workspace */
 
@@ -143,6 +146,8 @@ typedef struct {
   void* stream;        /* cudaStream_t for all work                                    */
   double chol_tol;     /* Rayleigh-Ritz: SVQB when a Cholesky pivot^2 < chol_tol (1e-12) */
   double drop_tol;     /* SVQB drops directions below drop_tol * max eig (1e-12)        */
+  int emulate_fp64;    /* MIXED: refinement contractions in double-float arithmetic on
+                          the FP32 units (1, default) or native FP64 (0)                */
 } dks_solve_opts;
 
 typedef struct {

@@ -20,7 +20,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdks.so")
 
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_FP64_EMULATED = 0, 1, 2
 MODE_FP64, MODE_MIXED = 0, 1
 PRECOND_TETER, PRECOND_IDENTITY = 0, 1
 
@@ -52,7 +52,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("n_init", C.c_int), ("n_iter", C.c_int), ("nbuf", C.c_int), ("C", C.c_double),
                 ("Omega", C.c_double), ("mode", C.c_int), ("refine_tol", C.c_double), ("precond", C.c_int),
                 ("use_filter", C.c_int), ("nev_k", C.POINTER(C.c_int)), ("stream", C.c_void_p),
-                ("chol_tol", C.c_double), ("drop_tol", C.c_double)]
+                ("chol_tol", C.c_double), ("drop_tol", C.c_double), ("emulate_fp64", C.c_int)]
 
 
 class SolveReport(C.Structure):
@@ -213,8 +213,9 @@ class Context:
         return cs.value, om.value
 
     # ---- operator
-    def apply_H(self, ik, x, hx, stream=None):
-        _check(_lib.dks_apply_H(self._h, ik, _dptr(x), _dptr(hx), x.shape[0], _prec_of(x), _stream(stream)))
+    def apply_H(self, ik, x, hx, stream=None, emulated=False):
+        prec = PREC_FP64_EMULATED if (emulated and _prec_of(x) == PREC_FP64) else _prec_of(x)
+        _check(_lib.dks_apply_H(self._h, ik, _dptr(x), _dptr(hx), x.shape[0], prec, _stream(stream)))
         return hx
 
     def filter(self, ik, y, fy, cshift, omega, stream=None):
@@ -230,7 +231,7 @@ class Context:
     # ---- solver
     def solve(self, x_list, nev, tol=1e-6, n_init=3, n_iter=200, mode=MODE_FP64, refine_tol=1e-5,
               precond=PRECOND_TETER, use_filter=True, cshift=None, omega=None, nev_k=None, nbuf=0,
-              stream=None, check=True, chol_tol=None, drop_tol=None):
+              stream=None, check=True, chol_tol=None, drop_tol=None, emulate_fp64=True):
         """Algorithm 1 on every k-point.  x_list[ik]: complex128 [nev_k+nbuf, 4, npw] (X0 in, X out).
         Returns (eigenvalues per k as numpy arrays, report dict, status code)."""
         opts = SolveOpts()
@@ -244,6 +245,7 @@ class Context:
             opts.chol_tol = float(chol_tol)
         if drop_tol is not None:
             opts.drop_tol = float(drop_tol)
+        opts.emulate_fp64 = 1 if emulate_fp64 else 0
         nevs = [int(nev)] * self.nk if nev_k is None else [int(v) for v in nev_k]
         if nev_k is not None:
             arr = np.ascontiguousarray(nevs, dtype=np.int32)
@@ -291,11 +293,11 @@ def profile_read():
 
 # ---- single steps of Algorithm 1 (blocks are [ncol, rows] complex tensors)
 
-def gram(z, hz, a_out, s_out, stream=None):
+def gram(z, hz, a_out, s_out, stream=None, emulated=False):
     load_library()
     nz, rows = z.shape[0], z[0].numel()
-    _check(_lib.dks_gram(_dptr(z), _dptr(hz), rows, nz, _dptr(a_out), _dptr(s_out), _prec_of(z),
-                         _stream(stream)))
+    prec = PREC_FP64_EMULATED if (emulated and _prec_of(z) == PREC_FP64) else _prec_of(z)
+    _check(_lib.dks_gram(_dptr(z), _dptr(hz), rows, nz, _dptr(a_out), _dptr(s_out), prec, _stream(stream)))
 
 
 def rayleigh_ritz(a, s, n, v_out, lam_out, info_out, stream=None):
@@ -312,12 +314,13 @@ def rayleigh_ritz_static(a, s, n, v_out, lam_out, info_out, stream=None):
                                          _dptr(info_out), _stream(stream)))
 
 
-def rotate(z, w, n, out, beta=0.0, stream=None):
-    """out[j] = sum_i z[i] w[i, j] (+ beta out[j]); w complex128 (nz x n) stored column-major."""
+def rotate(z, w, n, out, beta=0.0, stream=None, emulated=False):
+    """out[j] = sum_i z[i] w[i, j] (+ beta out[j]); w: complex128 tensor [n, nz] holding the columns of W."""
     load_library()
     nz, rows = z.shape[0], z[0].numel()
     ldw = w.shape[-1] if w.dim() == 2 else nz
-    _check(_lib.dks_rotate(_dptr(z), rows, nz, _dptr(w), ldw, int(n), _dptr(out), float(beta), _prec_of(z),
+    prec = PREC_FP64_EMULATED if (emulated and _prec_of(z) == PREC_FP64) else _prec_of(z)
+    _check(_lib.dks_rotate(_dptr(z), rows, nz, _dptr(w), ldw, int(n), _dptr(out), float(beta), prec,
                            _stream(stream)))
 
 

@@ -1,0 +1,236 @@
+// Double-float ("float-float") versions of the two tall-skinny complex contractions, for the
+// FP64 refinement phase of the mixed mode.
+//
+// GB300 issues FP64 at about 1/60 of its FP32 rate, and the FP64 Gram and rotation kernels run
+// with the FP64 pipe ~88% busy while the FP32 FMA pipe is idle.  Here every FP64 operand is
+// split on load into hi = fl32(x) and lo = fl32(x - hi) (48 significant bits), products use the
+// error-free transformation p = hi_a*hi_b, e = fma(hi_a, hi_b, -p) plus the two cross terms, and
+// sums are kept as unevaluated pairs with Knuth's two-sum followed by a fast renormalisation
+// (Dekker / Knuth error-free transformations).  Each real multiply-add costs ~15 FP32
+// instructions, about 4x the FP64 rate on this part, with ~2^-48 relative rounding per step
+// (FP64: 2^-53).  Inputs and outputs stay complex128.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "dks_internal.h"
+#include "dks_kernels.cuh"
+
+namespace dks {
+
+struct df {   // unevaluated sum hi + lo
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_split(double x) {
+  const float h = (float)x;
+  return df{h, (float)(x - (double)h)};
+}
+
+// s += a * b (all double-float); renormalised after the update
+__device__ __forceinline__ void df_mac(df& s, const df a, const df b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);          // exact error of the leading product
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float t = s.hi + p;                // two-sum of the leading parts
+  const float bb = t - s.hi;
+  const float err = (s.hi - (t - bb)) + (p - bb);
+  const float lo = err + (s.lo + e);
+  const float hi = t + lo;                 // fast two-sum renormalisation (|t| >= |lo|)
+  s.lo = lo - (hi - t);
+  s.hi = hi;
+}
+
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ double df_to_d(df a) { return (double)a.hi + (double)a.lo; }
+
+struct cdf {   // complex double-float
+  df re, im;
+};
+
+__device__ __forceinline__ cdf cdf_split(double2 v) { return cdf{df_split(v.x), df_split(v.y)}; }
+
+// acc += conj(a) * b
+__device__ __forceinline__ void cdf_macc(cdf& acc, const cdf& a, const cdf& b) {
+  df_mac(acc.re, a.re, b.re);
+  df_mac(acc.re, a.im, b.im);
+  df_mac(acc.im, a.re, b.im);
+  df_mac(acc.im, df_neg(a.im), b.re);
+}
+// acc += a * b
+__device__ __forceinline__ void cdf_mac(cdf& acc, const cdf& a, const cdf& b) {
+  df_mac(acc.re, a.re, b.re);
+  df_mac(acc.re, df_neg(a.im), b.im);
+  df_mac(acc.im, a.re, b.im);
+  df_mac(acc.im, a.im, b.re);
+}
+
+// ---------------------------------------------------------------- C += A^H B
+constexpr int DHN_T = 32;
+
+__global__ void __launch_bounds__(256) k_gemm_hn_df(const double2* __restrict__ a, int lda,
+                                                    const double2* __restrict__ b, int ldb, int k, int m, int n,
+                                                    int mt, int kchunk, double2* __restrict__ c, int ldc,
+                                                    int lower) {
+  __shared__ cdf as[DHN_T][DHN_T + 1];
+  __shared__ cdf bs[DHN_T][DHN_T + 1];
+  int tm, tn;
+  if (lower) {
+    const int t = blockIdx.x;
+    tm = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
+    while (tm * (tm + 1) / 2 > t) --tm;
+    tn = t - tm * (tm + 1) / 2;
+  } else {
+    tm = blockIdx.x % mt;
+    tn = blockIdx.x / mt;
+  }
+  const int m0 = tm * DHN_T, n0 = tn * DHN_T;
+  const int kb = blockIdx.y * kchunk;
+  const int ke = min(k, kb + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  cdf acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = cdf{{0.f, 0.f}, {0.f, 0.f}};
+  for (int k0 = kb; k0 < ke; k0 += DHN_T) {
+    for (int e = threadIdx.x; e < DHN_T * DHN_T; e += 256) {
+      const int kq = e & (DHN_T - 1), q = e >> 5;
+      const int gk = k0 + kq;
+      double2 va{0, 0}, vb{0, 0};
+      if (gk < ke) {
+        if (m0 + q < m) va = a[(size_t)(m0 + q) * lda + gk];
+        if (n0 + q < n) vb = b[(size_t)(n0 + q) * ldb + gk];
+      }
+      as[kq][q] = cdf_split(va);
+      bs[kq][q] = cdf_split(vb);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kq = 0; kq < DHN_T; ++kq) {
+      const cdf a0 = as[kq][ty], a1 = as[kq][ty + 16];
+      const cdf b0 = bs[kq][tx], b1 = bs[kq][tx + 16];
+      cdf_macc(acc[0][0], a0, b0);
+      cdf_macc(acc[0][1], a0, b1);
+      cdf_macc(acc[1][0], a1, b0);
+      cdf_macc(acc[1][1], a1, b1);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int mm = m0 + ty + 16 * i, nn = n0 + tx + 16 * j;
+      if (mm < m && nn < n) {
+        atomicAdd(&c[(size_t)nn * ldc + mm].x, df_to_d(acc[i][j].re));
+        atomicAdd(&c[(size_t)nn * ldc + mm].y, df_to_d(acc[i][j].im));
+      }
+    }
+}
+
+static int df_num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+int gemm_hn_df(const double2* a, int lda, const double2* b, int ldb, int k, int m, int n, double2* c,
+               cudaStream_t st, int cat, int ldc, bool lower) {
+  if (m <= 0 || n <= 0 || k <= 0) return DKS_OK;
+  if (ldc <= 0) ldc = m;
+  if (lower && m != n) return fail(DKS_ERR_INVALID_ARG, "gemm_hn_df: lower-triangle mode needs a square result");
+  const int mt = (m + DHN_T - 1) / DHN_T, nt = (n + DHN_T - 1) / DHN_T;
+  const int tiles = lower ? mt * (mt + 1) / 2 : mt * nt;
+  const int ktiles = (k + DHN_T - 1) / DHN_T;
+  int splits = std::max(1, (4 * df_num_sms()) / tiles);
+  splits = std::min(splits, ktiles);
+  const int kchunk = ((ktiles + splits - 1) / splits) * DHN_T;
+  splits = (k + kchunk - 1) / kchunk;
+  dim3 grid(tiles, splits);
+  const bool same = (const void*)a == (const void*)b;
+  Prof pr(cat, st, (same ? (double)m : (double)(m + n)) * k * 16.0 + 16.0 * m * n,
+          (lower ? 4.0 * m * (m + 1.0) : 8.0 * m * n) * (double)k);
+  k_gemm_hn_df<<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
+}
+
+// ---------------------------------------------------------------- OUT = alpha A diag(ws) W + beta OUT
+constexpr int DNN_R = 64, DNN_C = 32, DNN_M = 16;
+
+__global__ void __launch_bounds__(256) k_gemm_nn_df(const double2* __restrict__ a, int lda, int k, int m,
+                                                    const double2* __restrict__ w, int ldw,
+                                                    const double* __restrict__ ws, int n,
+                                                    double2* __restrict__ out, int ldo, double alpha, double beta) {
+  __shared__ cdf as[DNN_M][DNN_R];
+  __shared__ cdf wsm[DNN_M][DNN_C];
+  const int r0 = blockIdx.x * DNN_R, c0 = blockIdx.y * DNN_C;
+  const int row = threadIdx.x & (DNN_R - 1), cg = threadIdx.x >> 6;
+  cdf acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = cdf{{0.f, 0.f}, {0.f, 0.f}};
+  for (int m0 = 0; m0 < m; m0 += DNN_M) {
+    for (int e = threadIdx.x; e < DNN_M * DNN_R; e += 256) {
+      const int rr = e & (DNN_R - 1), mm = e >> 6;
+      double2 v{0, 0};
+      if (m0 + mm < m && r0 + rr < k) v = a[(size_t)(m0 + mm) * lda + r0 + rr];
+      as[mm][rr] = cdf_split(v);
+    }
+    for (int e = threadIdx.x; e < DNN_M * DNN_C; e += 256) {
+      const int cc = e & (DNN_C - 1), mm = e >> 5;
+      double2 v{0, 0};
+      if (m0 + mm < m && c0 + cc < n) {
+        v = w[(size_t)(c0 + cc) * ldw + m0 + mm];
+        const double s = (ws ? ws[m0 + mm] : 1.0) * alpha;
+        v.x *= s;
+        v.y *= s;
+      }
+      wsm[mm][cc] = cdf_split(v);
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int mm = 0; mm < DNN_M; ++mm) {
+      const cdf av = as[mm][row];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) cdf_mac(acc[j], av, wsm[mm][cg * 8 + j]);
+    }
+    __syncthreads();
+  }
+  if (r0 + row < k) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int cc = c0 + cg * 8 + j;
+      if (cc < n) {
+        double2* o = out + (size_t)cc * ldo + r0 + row;
+        double2 r{df_to_d(acc[j].re), df_to_d(acc[j].im)};
+        if (beta != 0.0) {
+          const double2 old = *o;
+          r.x += beta * old.x;
+          r.y += beta * old.y;
+        }
+        *o = r;
+      }
+    }
+  }
+}
+
+int gemm_nn_df(const double2* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
+               double2* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
+  if (k <= 0 || n <= 0) return DKS_OK;
+  dim3 grid((k + DNN_R - 1) / DNN_R, (n + DNN_C - 1) / DNN_C);
+  Prof pr(cat, st, (double)m * k * 16.0 + (beta != 0.0 ? 2.0 : 1.0) * n * k * 16.0 + 16.0 * m * n,
+          8.0 * (double)k * m * n);
+  k_gemm_nn_df<<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
+}
+
+}  // namespace dks

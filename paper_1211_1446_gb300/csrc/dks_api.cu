@@ -430,11 +430,15 @@ int dks_filter_constants(const dks_ctx* ctx, int ik, double* C, double* Omega) {
 }
 
 int dks_apply_H(dks_ctx* ctx, int ik, const void* X, void* HX, int nb, int prec, void* stream) {
-  if (!ctx || ik < 0 || ik >= ctx->nk || nb < 0 || (nb && (!X || !HX)) || (prec != 0 && prec != 1))
+  if (!ctx || ik < 0 || ik >= ctx->nk || nb < 0 || (nb && (!X || !HX)) || prec < 0 || prec > 2)
     return fail(DKS_ERR_INVALID_ARG, "dks_apply_H: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
-  if (prec == DKS_PREC_FP64)
-    return apply_h<double2>(ctx, ik, (const double2*)X, (double2*)HX, nb, 0.0, 1.0, st);
+  if (prec != DKS_PREC_FP32) {
+    ctx->df_gemm = prec == DKS_PREC_FP64_EMULATED;
+    const int rc = apply_h<double2>(ctx, ik, (const double2*)X, (double2*)HX, nb, 0.0, 1.0, st);
+    ctx->df_gemm = false;
+    return rc;
+  }
   return apply_h<float2>(ctx, ik, (const float2*)X, (float2*)HX, nb, 0.0, 1.0, st);
 }
 
@@ -500,7 +504,10 @@ int dks_gram(const void* Z, const void* HZ, int rows, int nz, void* A, void* S, 
   cudaStream_t st = (cudaStream_t)stream;
   DKS_CUDA_TRY(cudaMemsetAsync(A, 0, (size_t)nz * nz * sizeof(double2), st));
   DKS_CUDA_TRY(cudaMemsetAsync(S, 0, (size_t)nz * nz * sizeof(double2), st));
-  if (prec == DKS_PREC_FP64) {
+  if (prec == DKS_PREC_FP64_EMULATED) {
+    DKS_TRY(gemm_hn_df((const double2*)Z, rows, (const double2*)HZ, rows, rows, nz, nz, (double2*)A, st));
+    DKS_TRY(gemm_hn_df((const double2*)Z, rows, (const double2*)Z, rows, rows, nz, nz, (double2*)S, st));
+  } else if (prec == DKS_PREC_FP64) {
     DKS_TRY(gemm_hn<double2>((const double2*)Z, rows, (const double2*)HZ, rows, rows, nz, nz, (double2*)A, st));
     DKS_TRY(gemm_hn<double2>((const double2*)Z, rows, (const double2*)Z, rows, rows, nz, nz, (double2*)S, st));
   } else {
@@ -527,6 +534,9 @@ int dks_rotate(const void* Z, int rows, int nz, const void* W, int ldw, int n, v
   if (rows <= 0 || nz <= 0 || n <= 0 || ldw < nz || !Z || !W || !OUT)
     return fail(DKS_ERR_INVALID_ARG, "dks_rotate: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
+  if (prec == DKS_PREC_FP64_EMULATED)
+    return gemm_nn_df((const double2*)Z, rows, rows, nz, (const double2*)W, ldw, nullptr, n, (double2*)OUT, rows,
+                      beta, st);
   if (prec == DKS_PREC_FP64)
     return gemm_nn<double2>((const double2*)Z, rows, rows, nz, (const double2*)W, ldw, nullptr, n, (double2*)OUT,
                             rows, beta, st);

@@ -101,6 +101,7 @@ struct dks_ctx {
   size_t chunk_budget = 64u << 20;   // bytes of FFT intermediates per chunk (L2-resident)
   int device = 0;
   int num_sms = 0;
+  bool df_gemm = false;         // complex128 projector contractions in double-float arithmetic
 };
 
 namespace dks {
@@ -108,8 +109,12 @@ namespace dks {
 // ---------------------------------------------------------------- profiling
 enum ProfCat {
   P_STICK_INV, P_PLANE, P_STICK_FWD, P_DIRAC, P_PROJ_HN, P_PROJ_NN, P_GRAM, P_ROTATE, P_RR, P_STATS,
-  P_PRECOND, P_MISC, P_NCAT
+  P_PRECOND, P_MISC,
+  // the same kernels launched on complex64 data (FP32 arithmetic)
+  P_STICK_INV32, P_PLANE32, P_STICK_FWD32, P_DIRAC32, P_PROJ_HN32, P_PROJ_NN32, P_GRAM32, P_ROTATE32,
+  P_NCAT
 };
+constexpr int kProf32 = P_STICK_INV32 - P_STICK_INV;   // offset of the complex64 variant
 // RAII scope around one kernel launch: counts it, and while profiling is on records a
 // CUDA event pair on the launching stream with the launch's algorithmic bytes and flops.
 class Prof {
@@ -138,6 +143,12 @@ int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, dou
 // c (m x n, col-major, leading dimension ldc or m) += a^H b, FP64 atomics; FP64 arithmetic when
 // either operand is complex128 or Acc64; lower: only the block lower triangle (square results)
 int mirror_lower(double2* c, int m, cudaStream_t st);   // upper triangle = conj of the lower
+// double-float (FP32-pair) versions of the two contractions for complex128 data
+int gemm_hn_df(const double2* a, int lda, const double2* b, int ldb, int k, int m, int n, double2* c,
+               cudaStream_t st, int cat = P_GRAM, int ldc = 0, bool lower = false);
+int gemm_nn_df(const double2* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
+               int n, double2* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0,
+               int cat = P_ROTATE);
 template <typename Va, typename Vo = Va>
 int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
             int n, Vo* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0,

@@ -20,10 +20,13 @@ std::vector<cudaEvent_t> g_pool;
 std::vector<Rec> g_recs;
 bool g_on = false;
 long long g_launch[P_NCAT] = {0};
-const char* g_names[P_NCAT] = {"stick_inverse_fft", "plane_fft_v",   "stick_forward_fft_dirac",
-                               "dirac_only",        "proj_bh_x",     "proj_b_dz",
-                               "gram",              "rotate",        "rayleigh_ritz",
-                               "col_stats",         "precond_teter", "convert_gather"};
+const char* g_names[P_NCAT] = {"stick_inverse_fft",      "plane_fft_v",        "stick_forward_fft_dirac",
+                               "dirac_only",             "proj_bh_x",          "proj_b_dz",
+                               "gram",                   "rotate",             "rayleigh_ritz",
+                               "col_stats",              "precond_teter",      "convert_gather",
+                               "stick_inverse_fft_fp32", "plane_fft_v_fp32",   "stick_forward_fft_dirac_fp32",
+                               "dirac_only_fp32",        "proj_bh_x_fp32",     "proj_b_dz_fp32",
+                               "gram_fp32",              "rotate_fp32"};
 cudaEvent_t take() {
   if (!g_pool.empty()) {
     cudaEvent_t e = g_pool.back();

@@ -285,7 +285,11 @@ int apply_h(dks_ctx* ctx, int ik, const V* x, V* out, int nb, double shift, doub
     bt = fp64 ? reinterpret_cast<const V*>(kp.bt64) : reinterpret_cast<const V*>(kp.bt32);
     DKS_CUDA_TRY(cudaMemsetAsync(zp, 0, zp_elems * sizeof(double2), st));
     // Z = B^H x~ : (nproj x 2npw) (2npw x 2nb)
-    DKS_TRY(gemm_hn<V>(bt, 2 * npw, x, 2 * npw, 2 * npw, ctx->nproj, 2 * nb, zp, st, P_PROJ_HN));
+    if (fp64 && ctx->df_gemm)
+      DKS_TRY(gemm_hn_df((const double2*)bt, 2 * npw, (const double2*)x, 2 * npw, 2 * npw, ctx->nproj, 2 * nb, zp,
+                         st, P_PROJ_HN));
+    else
+      DKS_TRY(gemm_hn<V>(bt, 2 * npw, x, 2 * npw, 2 * npw, ctx->nproj, 2 * nb, zp, st, P_PROJ_HN));
   }
   const V* tw1 = fp64 ? (const V*)ctx->tw64[0] : (const V*)ctx->tw32[0];
   const V* tw2 = fp64 ? (const V*)ctx->tw64[1] : (const V*)ctx->tw32[1];
@@ -308,21 +312,21 @@ int apply_h(dks_ctx* ctx, int ik, const V* x, V* out, int nb, double shift, doub
       const double tb = nf * (double)field_elems * es;          // one pass over the stick buffer
       const double f3 = 5.0 * n3 * std::log2((double)n3) * kp.nsticks * nf;
       {
-        Prof pr(P_STICK_INV, st, nf * npw * es + tb, f3);
+        Prof pr(P_STICK_INV + (fp64 ? 0 : kProf32), st, nf * npw * es + tb, f3);
         dim3 ga((kp.nsticks + spb_a - 1) / spb_a, 4 * nbc);
         k_stick_inverse<V><<<ga, 256, sm_a, st>>>(xb, tbuf, npw, kp.nsticks, kp.stick_start, kp.pw_stick,
                                                   kp.pw_iz, ctx->plan[2], tw3, spb_a);
       }
       {
         const double nn = (double)ctx->grid[0] * ctx->grid[1];
-        Prof pr(P_PLANE, st, 2.0 * tb + (double)ctx->ng * es / 2,
+        Prof pr(P_PLANE + (fp64 ? 0 : kProf32), st, 2.0 * tb + (double)ctx->ng * es / 2,
                 nf * n3 * (10.0 * nn * std::log2(nn) + 2.0 * nn));
         dim3 gb(n3, 4 * nbc);
         k_plane<V><<<gb, 512, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0], ctx->plan[1], n3,
                                           tw1, tw2, vp);
       }
       {
-        Prof pr(P_STICK_FWD, st, tb + 2.0 * nf * npw * es + 24.0 * npw, f3 + 64.0 * nbc * npw);
+        Prof pr(P_STICK_FWD + (fp64 ? 0 : kProf32), st, tb + 2.0 * nf * npw * es + 24.0 * npw, f3 + 64.0 * nbc * npw);
         dim3 gc((kp.nsticks + spb_c - 1) / spb_c, nbc);
         k_stick_forward<V><<<gc, 256, sm_c, st>>>(tbuf, xb, out + (size_t)b0 * 4 * npw, npw, kp.nsticks,
                                                   kp.stick_start, kp.pw_stick, kp.pw_iz, ctx->plan[2], tw3,
@@ -331,14 +335,18 @@ int apply_h(dks_ctx* ctx, int ik, const V* x, V* out, int nb, double shift, doub
     }
   } else {
     const int blocks = std::max(1, std::min(ctx->num_sms * 8, (int)(((size_t)nb * npw + 255) / 256)));
-    Prof pr(P_DIRAC, st, 8.0 * nb * npw * sizeof(V) + 24.0 * npw, 64.0 * nb * npw);
+    Prof pr(P_DIRAC + (fp64 ? 0 : kProf32), st, 8.0 * nb * npw * sizeof(V) + 24.0 * npw, 64.0 * nb * npw);
     k_dirac_only<V><<<blocks, 256, 0, st>>>(x, out, npw, nb, kp.q, ctx->c, shift, scale);
   }
   DKS_CUDA_TRY(cudaGetLastError());
   if (ctx->nproj) {
     // out~ += B (scale D Z)
-    DKS_TRY(gemm_nn<V>(bt, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, 2 * nb, out,
-                       2 * npw, 1.0, st, scale, P_PROJ_NN));
+    if (fp64 && ctx->df_gemm)
+      DKS_TRY(gemm_nn_df((const double2*)bt, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, 2 * nb,
+                         (double2*)out, 2 * npw, 1.0, st, scale, P_PROJ_NN));
+    else
+      DKS_TRY(gemm_nn<V>(bt, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, 2 * nb, out, 2 * npw,
+                         1.0, st, scale, P_PROJ_NN));
   }
   return DKS_OK;
 }

@@ -117,10 +117,12 @@ int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, dou
   splits = (k + kchunk - 1) / kchunk;
   dim3 grid(tiles, splits);
   const bool same = (const void*)a == (const void*)b;
-  Prof pr(cat, st, (same ? (double)m * sizeof(Va) : (double)m * sizeof(Va) + (double)n * sizeof(Vb)) * k +
+  const bool f32 = sizeof(Va) == sizeof(float2) && sizeof(Vb) == sizeof(float2) && !Acc64;
+  Prof pr(f32 && cat < P_RR ? cat + kProf32 : cat, st, (same ? (double)m * sizeof(Va) : (double)m * sizeof(Va) + (double)n * sizeof(Vb)) * k +
                        16.0 * m * n,
           (lower ? 4.0 * m * (m + 1.0) : 8.0 * m * n) * (double)k);
   using A = typename std::conditional<Acc64, double2, typename AccOf<Va, Vb>::T>::type;
+  (void)0;
   k_gemm_hn<Va, Vb, A><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
@@ -212,7 +214,8 @@ int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const
             Vo* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
   if (k <= 0 || n <= 0) return DKS_OK;
   dim3 grid((k + NN_R - 1) / NN_R, (n + NN_C - 1) / NN_C);
-  Prof pr(cat, st, (double)m * k * sizeof(Va) + (beta != 0.0 ? 2.0 : 1.0) * n * k * sizeof(Vo) + 16.0 * m * n,
+  const bool f32 = sizeof(Va) == sizeof(float2) && sizeof(Vo) == sizeof(float2);
+  Prof pr(f32 && cat < P_RR ? cat + kProf32 : cat, st, (double)m * k * sizeof(Va) + (beta != 0.0 ? 2.0 : 1.0) * n * k * sizeof(Vo) + 16.0 * m * n,
           8.0 * (double)k * m * n);
   k_gemm_nn<Va, Vo><<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
   DKS_CUDA_TRY(cudaGetLastError());

@@ -86,12 +86,26 @@ static int filter_inplace(dks_ctx* ctx, int ik, V* y, V* tmp, int nb, double C, 
   return apply_h<V>(ctx, ik, tmp, y, nb, C, 1.0 / om, st);
 }
 
+// contractions of one phase: native arithmetic of V, or double-float for complex128 blocks
 template <typename V>
-static int gram(const V* z, const V* hz, int rows, int nz, Small& sm, cudaStream_t st) {
+static int hn(bool df, const V* a, int lda, const V* b, int ldb, int k, int m, int n, double2* c, cudaStream_t st,
+              bool lower) {
+  if (df) return gemm_hn_df((const double2*)a, lda, (const double2*)b, ldb, k, m, n, c, st, P_GRAM, 0, lower);
+  return gemm_hn<V>(a, lda, b, ldb, k, m, n, c, st, P_GRAM, 0, lower);
+}
+template <typename V>
+static int nn(bool df, const V* a, int lda, int k, int m, const double2* w, int ldw, int n, V* out, int ldo,
+              cudaStream_t st) {
+  if (df) return gemm_nn_df((const double2*)a, lda, k, m, w, ldw, nullptr, n, (double2*)out, ldo, 0.0, st);
+  return gemm_nn<V>(a, lda, k, m, w, ldw, nullptr, n, out, ldo, 0.0, st);
+}
+
+template <typename V>
+static int gram(const V* z, const V* hz, int rows, int nz, Small& sm, cudaStream_t st, bool df = false) {
   DKS_CUDA_TRY(cudaMemsetAsync(sm.a, 0, (size_t)nz * nz * sizeof(double2), st));
   DKS_CUDA_TRY(cudaMemsetAsync(sm.s, 0, (size_t)nz * nz * sizeof(double2), st));
-  DKS_TRY(gemm_hn<V>(z, rows, hz, rows, rows, nz, nz, sm.a, st, P_GRAM, 0, true));
-  DKS_TRY(gemm_hn<V>(z, rows, z, rows, rows, nz, nz, sm.s, st, P_GRAM, 0, true));
+  DKS_TRY(hn<V>(df, z, rows, hz, rows, rows, nz, nz, sm.a, st, true));
+  DKS_TRY(hn<V>(df, z, rows, z, rows, rows, nz, nz, sm.s, st, true));
   DKS_TRY(mirror_lower(sm.a, nz, st));
   return mirror_lower(sm.s, nz, st);
 }
@@ -110,7 +124,10 @@ static int fetch(Small& sm, Pinned& pin, int n, std::vector<double>& res, cudaSt
 template <typename V>
 static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int n, int nconv, double tol,
                  int n_init, int n_iter, double C, double om, int precond, int use_filter, bool stop_on_stall,
-                 double chol_tol, double drop_tol, std::vector<double>* hist, PhaseOut& out, cudaStream_t st) {
+                 double chol_tol, double drop_tol, std::vector<double>* hist, PhaseOut& out, cudaStream_t st,
+                 bool df = false) {
+  df = df && sizeof(V) == sizeof(double2);
+  ctx->df_gemm = df;   // projector contractions inside apply_h follow the phase's arithmetic
   const KPoint& kp = ctx->k[ik];
   const int rows = 4 * kp.npw;
   const size_t colsz = (size_t)rows;
@@ -125,11 +142,11 @@ static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int
   // line 4-6: Rayleigh-Ritz on X0
   DKS_TRY(apply_h<V>(ctx, ik, b.z[cur], b.hz[cur], n, 0.0, 1.0, st));
   happ += n;
-  DKS_TRY(gram<V>(b.z[cur], b.hz[cur], rows, n, sm, st));
+  DKS_TRY(gram<V>(b.z[cur], b.hz[cur], rows, n, sm, st, df));
   DKS_TRY(rayleigh_ritz(sm.a, sm.s, n, n, sm.vm, sm.lam, sm.info, sm.rrs, st, chol_tol, drop_tol));
   int nx = cur ^ 1;
-  DKS_TRY(gemm_nn<V>(b.z[cur], rows, rows, n, sm.vm, n, nullptr, n, b.z[nx], rows, 0.0, st));
-  DKS_TRY(gemm_nn<V>(b.hz[cur], rows, rows, n, sm.vm, n, nullptr, n, b.hz[nx], rows, 0.0, st));
+  DKS_TRY(nn<V>(df, b.z[cur], rows, rows, n, sm.vm, n, n, b.z[nx], rows, st));
+  DKS_TRY(nn<V>(df, b.hz[cur], rows, rows, n, sm.vm, n, n, b.hz[nx], rows, st));
   cur = nx;
   DKS_TRY(col_stats<V>(b.z[cur], b.hz[cur], sm.lam, kp.ek, kp.npw, n, sm.stats, st));
   std::vector<double> res;
@@ -158,11 +175,11 @@ static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int
     DKS_TRY(apply_h<V>(ctx, ik, y, hy, a, 0.0, 1.0, st));
     happ += a;
     const int nz = n + a + p;
-    DKS_TRY(gram<V>(b.z[cur], b.hz[cur], rows, nz, sm, st));
+    DKS_TRY(gram<V>(b.z[cur], b.hz[cur], rows, nz, sm, st, df));
     DKS_TRY(rayleigh_ritz(sm.a, sm.s, nz, n, sm.vm, sm.lam, sm.info, sm.rrs, st, chol_tol, drop_tol));
     nx = cur ^ 1;
-    DKS_TRY(gemm_nn<V>(b.z[cur], rows, rows, nz, sm.vm, nz, nullptr, n, b.z[nx], rows, 0.0, st));
-    DKS_TRY(gemm_nn<V>(b.hz[cur], rows, rows, nz, sm.vm, nz, nullptr, n, b.hz[nx], rows, 0.0, st));
+    DKS_TRY(nn<V>(df, b.z[cur], rows, rows, nz, sm.vm, nz, n, b.z[nx], rows, st));
+    DKS_TRY(nn<V>(df, b.hz[cur], rows, rows, nz, sm.vm, nz, n, b.hz[nx], rows, st));
     DKS_TRY(col_stats<V>(b.z[nx], b.hz[nx], sm.lam, kp.ek, kp.npw, n, sm.stats, st));
     DKS_TRY(fetch(sm, pin, n, res, st));
     if (pin.info[1] < n) return fail(DKS_ERR_RANK, "Rayleigh-Ritz subspace rank below the block size");
@@ -196,9 +213,8 @@ static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int
     DKS_TRY(gather_cols(sm.vm, nz, n, nz - n, sm.act, a2, sm.vp, st));
     V* pz = b.z[nx] + (size_t)(n + a2) * colsz;
     V* phz = b.hz[nx] + (size_t)(n + a2) * colsz;
-    DKS_TRY(gemm_nn<V>(b.z[cur] + (size_t)n * colsz, rows, rows, nz - n, sm.vp, nz - n, nullptr, a2, pz, rows, 0.0, st));
-    DKS_TRY(gemm_nn<V>(b.hz[cur] + (size_t)n * colsz, rows, rows, nz - n, sm.vp, nz - n, nullptr, a2, phz, rows, 0.0,
-                       st));
+    DKS_TRY(nn<V>(df, b.z[cur] + (size_t)n * colsz, rows, rows, nz - n, sm.vp, nz - n, a2, pz, rows, st));
+    DKS_TRY(nn<V>(df, b.hz[cur] + (size_t)n * colsz, rows, rows, nz - n, sm.vp, nz - n, a2, phz, rows, st));
     // the Teter factor of the next iteration needs statistics of the new X (already in sm.stats)
     cur = nx;
     act.swap(act2);
@@ -210,6 +226,7 @@ static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int
   out.happ = happ;
   out.cur = cur;
   out.neg = pin.lam[0] < -ctx->c * ctx->c;
+  ctx->df_gemm = false;
   return DKS_OK;
 }
 
@@ -235,6 +252,7 @@ void dks_solve_opts_default(dks_solve_opts* o) {
   o->stream = nullptr;
   o->chol_tol = 1e-12;
   o->drop_tol = 1e-12;
+  o->emulate_fp64 = 1;
 }
 
 int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* opts_in, double* eig, void* const* X,
@@ -329,7 +347,7 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
       const int left = std::max(0, opts.n_iter - o32.iterations);
       DKS_TRY(phase<double2>(ctx, ik, b64, sm, pin, n, nv, tol, opts.use_filter ? 1 : 0, left, C, om, opts.precond,
                              opts.use_filter, false, opts.chol_tol, opts.drop_tol, ik == 0 ? &hist : nullptr, o64,
-                             st));
+                             st, opts.emulate_fp64 != 0));
     } else {
       DKS_CUDA_TRY(cudaMemcpyAsync(b64.z[0], X[ik], elems * sizeof(double2), cudaMemcpyDeviceToDevice, st));
       o64.cur = 0;

@@ -107,3 +107,30 @@ def test_rotate_and_residual_norms():
     torch.cuda.synchronize()
     ref = np.linalg.norm(hx - lam[:, None] * x, axis=1)
     assert rel_err(nr.cpu().numpy(), ref) < 1e-13
+
+
+@pytest.mark.parametrize("rows,nz", [(4 * 57419, 120), (1000, 33), (4 * 5, 1)])
+def test_gram_double_float(rows, nz):
+    """Double-float (FP32-pair) Gram on complex128 data: FP64-level accuracy (2^-48 per step)."""
+    torch = gpu()
+    import paper_1211_1446_gb300 as P
+    z = _rand((nz, rows), 11)
+    hz = _rand((nz, rows), 12)
+    a = torch.empty((nz, nz), dtype=torch.complex128, device="cuda")
+    s = torch.empty_like(a)
+    P.gram(to_dev(z, torch.complex128), to_dev(hz, torch.complex128), a, s, emulated=True)
+    torch.cuda.synchronize()
+    assert rel_err(a.cpu().numpy().T, z.conj() @ hz.T) < 1e-12
+    assert rel_err(s.cpu().numpy().T, z.conj() @ z.T) < 1e-12
+
+
+def test_rotate_double_float():
+    torch = gpu()
+    import paper_1211_1446_gb300 as P
+    rows, nz, n = 4 * 3001, 120, 40
+    z = _rand((nz, rows), 13)
+    w = _rand((nz, n), 14)
+    out = torch.empty((n, rows), dtype=torch.complex128, device="cuda")
+    P.rotate(to_dev(z, torch.complex128), to_dev(w.T.copy(), torch.complex128), n, out, emulated=True)
+    torch.cuda.synchronize()
+    assert rel_err(out.cpu().numpy(), (z.T @ w).T) < 1e-13

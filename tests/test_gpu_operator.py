@@ -65,6 +65,19 @@ def test_apply_h_full_dimer():
         assert rel_err(hx.cpu().numpy(), ref) < tol
 
 
+def test_apply_h_double_float_projectors():
+    """complex128 H' with the projector contractions in double-float arithmetic."""
+    torch = gpu()
+    wl, ctx, hop, q = make_pair("dimer", ecut=4.0)
+    x = W.random_block(len(q), 5, 31)
+    ref = hop(x)
+    xd = to_dev(x, torch.complex128)
+    hx = torch.empty_like(xd)
+    ctx.apply_H(0, xd, hx, emulated=True)
+    torch.cuda.synchronize()
+    assert rel_err(hx.cpu().numpy(), ref) < 1e-11
+
+
 def test_filter_parity():
     torch = gpu()
     wl, ctx, hop, q = make_pair("small")
