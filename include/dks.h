@@ -148,6 +148,9 @@ typedef struct {
   double drop_tol;     /* SVQB drops directions below drop_tol * max eig (1e-12)        */
   int emulate_fp64;    /* MIXED: refinement contractions in double-float arithmetic on
                           the FP32 units (1, default) or native FP64 (0)                */
+  int concurrency;     /* k-points solved at the same time, each on its own internal stream
+                          and host thread (0 = min(nk, 4), bounded by free device memory);
+                          with more than one, `stream` is synchronised first             */
 } dks_solve_opts;
 
 typedef struct {

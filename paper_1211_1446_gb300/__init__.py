@@ -52,7 +52,8 @@ class SolveOpts(C.Structure):
     _fields_ = [("n_init", C.c_int), ("n_iter", C.c_int), ("nbuf", C.c_int), ("C", C.c_double),
                 ("Omega", C.c_double), ("mode", C.c_int), ("refine_tol", C.c_double), ("precond", C.c_int),
                 ("use_filter", C.c_int), ("nev_k", C.POINTER(C.c_int)), ("stream", C.c_void_p),
-                ("chol_tol", C.c_double), ("drop_tol", C.c_double), ("emulate_fp64", C.c_int)]
+                ("chol_tol", C.c_double), ("drop_tol", C.c_double), ("emulate_fp64", C.c_int),
+                ("concurrency", C.c_int)]
 
 
 class SolveReport(C.Structure):
@@ -231,7 +232,7 @@ class Context:
     # ---- solver
     def solve(self, x_list, nev, tol=1e-6, n_init=3, n_iter=200, mode=MODE_FP64, refine_tol=1e-5,
               precond=PRECOND_TETER, use_filter=True, cshift=None, omega=None, nev_k=None, nbuf=0,
-              stream=None, check=True, chol_tol=None, drop_tol=None, emulate_fp64=True):
+              stream=None, check=True, chol_tol=None, drop_tol=None, emulate_fp64=True, concurrency=0):
         """Algorithm 1 on every k-point.  x_list[ik]: complex128 [nev_k+nbuf, 4, npw] (X0 in, X out).
         Returns (eigenvalues per k as numpy arrays, report dict, status code)."""
         opts = SolveOpts()
@@ -246,6 +247,7 @@ class Context:
         if drop_tol is not None:
             opts.drop_tol = float(drop_tol)
         opts.emulate_fp64 = 1 if emulate_fp64 else 0
+        opts.concurrency = int(concurrency)
         nevs = [int(nev)] * self.nk if nev_k is None else [int(v) for v in nev_k]
         if nev_k is not None:
             arr = np.ascontiguousarray(nevs, dtype=np.int32)

@@ -37,6 +37,11 @@ int grow(Workspace& w, size_t bytes) {
   return DKS_OK;
 }
 
+Exec& exec0(dks_ctx* ctx) {
+  if (ctx->exec.empty()) ctx->exec.push_back(new Exec());
+  return *ctx->exec[0];
+}
+
 void release(Workspace& w) {
   if (w.ptr) cudaFree(w.ptr);
   w.ptr = nullptr;
@@ -257,8 +262,12 @@ static void free_ctx(dks_ctx* ctx) {
     cudaFree(kp.bt64);
     cudaFree(kp.bt32);
   }
-  release(ctx->ws_h);
-  release(ctx->ws_solve);
+  for (Exec* e : ctx->exec) {
+    release(e->ws_h);
+    release(e->ws_solve);
+    if (e->own) cudaStreamDestroy(e->own);
+    delete e;
+  }
   delete ctx;
 }
 
@@ -433,13 +442,14 @@ int dks_apply_H(dks_ctx* ctx, int ik, const void* X, void* HX, int nb, int prec,
   if (!ctx || ik < 0 || ik >= ctx->nk || nb < 0 || (nb && (!X || !HX)) || prec < 0 || prec > 2)
     return fail(DKS_ERR_INVALID_ARG, "dks_apply_H: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
+  Exec& ex = exec0(ctx);
   if (prec != DKS_PREC_FP32) {
-    ctx->df_gemm = prec == DKS_PREC_FP64_EMULATED;
-    const int rc = apply_h<double2>(ctx, ik, (const double2*)X, (double2*)HX, nb, 0.0, 1.0, st);
-    ctx->df_gemm = false;
+    ex.df_gemm = prec == DKS_PREC_FP64_EMULATED;
+    const int rc = apply_h<double2>(ctx, ex, ik, (const double2*)X, (double2*)HX, nb, 0.0, 1.0, st);
+    ex.df_gemm = false;
     return rc;
   }
-  return apply_h<float2>(ctx, ik, (const float2*)X, (float2*)HX, nb, 0.0, 1.0, st);
+  return apply_h<float2>(ctx, ex, ik, (const float2*)X, (float2*)HX, nb, 0.0, 1.0, st);
 }
 
 int dks_filter(dks_ctx* ctx, int ik, const void* Y, void* FY, int nb, double C, double Omega, int prec,
@@ -454,12 +464,13 @@ int dks_filter(dks_ctx* ctx, int ik, const void* Y, void* FY, int nb, double C, 
   void* tmp = nullptr;
   DKS_CUDA_TRY(cudaMallocAsync(&tmp, elems * es, st));
   int rc;
+  Exec& ex = exec0(ctx);
   if (prec == DKS_PREC_FP64) {
-    rc = apply_h<double2>(ctx, ik, (const double2*)Y, (double2*)tmp, nb, C, 1.0 / Omega, st);
-    if (!rc) rc = apply_h<double2>(ctx, ik, (const double2*)tmp, (double2*)FY, nb, C, 1.0 / Omega, st);
+    rc = apply_h<double2>(ctx, ex, ik, (const double2*)Y, (double2*)tmp, nb, C, 1.0 / Omega, st);
+    if (!rc) rc = apply_h<double2>(ctx, ex, ik, (const double2*)tmp, (double2*)FY, nb, C, 1.0 / Omega, st);
   } else {
-    rc = apply_h<float2>(ctx, ik, (const float2*)Y, (float2*)tmp, nb, C, 1.0 / Omega, st);
-    if (!rc) rc = apply_h<float2>(ctx, ik, (const float2*)tmp, (float2*)FY, nb, C, 1.0 / Omega, st);
+    rc = apply_h<float2>(ctx, ex, ik, (const float2*)Y, (float2*)tmp, nb, C, 1.0 / Omega, st);
+    if (!rc) rc = apply_h<float2>(ctx, ex, ik, (const float2*)tmp, (float2*)FY, nb, C, 1.0 / Omega, st);
   }
   cudaFreeAsync(tmp, st);
   return rc;

@@ -70,6 +70,15 @@ struct Workspace {
   size_t bytes = 0;
 };
 
+// Execution state of one stream of work (one solve worker, or the context's own stream for the
+// single-step entry points).  Never shared by two host threads at the same time.
+struct Exec {
+  Workspace ws_h;               // H' intermediates + projector coefficients
+  Workspace ws_solve;           // solver blocks
+  bool df_gemm = false;         // complex128 projector contractions in double-float arithmetic
+  cudaStream_t own = nullptr;   // stream created for a concurrent solve worker
+};
+
 }  // namespace dks
 
 struct dks_ctx {
@@ -95,13 +104,12 @@ struct dks_ctx {
   std::vector<double> dvec;     // host, per channel
   double* dvec_dev = nullptr;
   std::vector<dks::KPoint> k;
-  // scratch owned by the context (grown on demand)
-  dks::Workspace ws_h;          // apply_H grid intermediates + projector coefficients
-  dks::Workspace ws_solve;      // solver blocks
+  // execution states owned by the context (grown on demand): exec[0] serves the single-step
+  // entry points and serial solves, exec[1..] the concurrent k-point workers
+  std::vector<dks::Exec*> exec;
   size_t chunk_budget = 64u << 20;   // bytes of FFT intermediates per chunk (L2-resident)
   int device = 0;
   int num_sms = 0;
-  bool df_gemm = false;         // complex128 projector contractions in double-float arithmetic
 };
 
 namespace dks {
@@ -133,8 +141,9 @@ void release(Workspace& w);
 //   out = scale * (H' x - shift * x)          (beta == 0)
 // x and out [nb][4][npw]; precision by template (double2 / float2).
 template <typename V>
-int apply_h(dks_ctx* ctx, int ik, const V* x, V* out, int nb, double shift, double scale,
+int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double shift, double scale,
             cudaStream_t st);
+Exec& exec0(dks_ctx* ctx);
 
 // kernels shared by the solver and the single-step entry points
 template <typename Va, typename Vb = Va, bool Acc64 = false>

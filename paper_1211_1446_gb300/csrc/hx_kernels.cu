@@ -263,7 +263,7 @@ static int pick_spb(int n3, size_t elem, int lines_per_stick, size_t target) {
 }
 
 template <typename V>
-int apply_h(dks_ctx* ctx, int ik, const V* x, V* out, int nb, double shift, double scale,
+int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double shift, double scale,
             cudaStream_t st) {
   if (nb <= 0) return DKS_OK;
   KPoint& kp = ctx->k[ik];
@@ -276,16 +276,16 @@ int apply_h(dks_ctx* ctx, int ik, const V* x, V* out, int nb, double shift, doub
   int chunk = (int)std::max<size_t>(1, ctx->chunk_budget / (4 * field_elems * sizeof(V)));
   chunk = std::min(chunk, nb);
   const size_t need = zp_elems * sizeof(double2) + 256 + (ctx->has_v ? 4 * chunk * field_elems * sizeof(V) : 0);
-  DKS_TRY(grow(ctx->ws_h, need));
-  double2* zp = reinterpret_cast<double2*>(ctx->ws_h.ptr);
-  V* tbuf = reinterpret_cast<V*>(reinterpret_cast<char*>(ctx->ws_h.ptr) +
+  DKS_TRY(grow(ex.ws_h, need));
+  double2* zp = reinterpret_cast<double2*>(ex.ws_h.ptr);
+  V* tbuf = reinterpret_cast<V*>(reinterpret_cast<char*>(ex.ws_h.ptr) +
                                  ((zp_elems * sizeof(double2) + 255) / 256) * 256);
   const V* bt = nullptr;
   if (ctx->nproj) {
     bt = fp64 ? reinterpret_cast<const V*>(kp.bt64) : reinterpret_cast<const V*>(kp.bt32);
     DKS_CUDA_TRY(cudaMemsetAsync(zp, 0, zp_elems * sizeof(double2), st));
     // Z = B^H x~ : (nproj x 2npw) (2npw x 2nb)
-    if (fp64 && ctx->df_gemm)
+    if (fp64 && ex.df_gemm)
       DKS_TRY(gemm_hn_df((const double2*)bt, 2 * npw, (const double2*)x, 2 * npw, 2 * npw, ctx->nproj, 2 * nb, zp,
                          st, P_PROJ_HN));
     else
@@ -341,7 +341,7 @@ int apply_h(dks_ctx* ctx, int ik, const V* x, V* out, int nb, double shift, doub
   DKS_CUDA_TRY(cudaGetLastError());
   if (ctx->nproj) {
     // out~ += B (scale D Z)
-    if (fp64 && ctx->df_gemm)
+    if (fp64 && ex.df_gemm)
       DKS_TRY(gemm_nn_df((const double2*)bt, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, 2 * nb,
                          (double2*)out, 2 * npw, 1.0, st, scale, P_PROJ_NN));
     else
@@ -351,7 +351,7 @@ int apply_h(dks_ctx* ctx, int ik, const V* x, V* out, int nb, double shift, doub
   return DKS_OK;
 }
 
-template int apply_h<double2>(dks_ctx*, int, const double2*, double2*, int, double, double, cudaStream_t);
-template int apply_h<float2>(dks_ctx*, int, const float2*, float2*, int, double, double, cudaStream_t);
+template int apply_h<double2>(dks_ctx*, Exec&, int, const double2*, double2*, int, double, double, cudaStream_t);
+template int apply_h<float2>(dks_ctx*, Exec&, int, const float2*, float2*, int, double, double, cudaStream_t);
 
 }  // namespace dks

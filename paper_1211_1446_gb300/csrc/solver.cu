@@ -21,9 +21,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "dks_internal.h"
@@ -81,9 +84,10 @@ struct Pinned {
 };
 
 template <typename V>
-static int filter_inplace(dks_ctx* ctx, int ik, V* y, V* tmp, int nb, double C, double om, cudaStream_t st) {
-  DKS_TRY(apply_h<V>(ctx, ik, y, tmp, nb, C, 1.0 / om, st));
-  return apply_h<V>(ctx, ik, tmp, y, nb, C, 1.0 / om, st);
+static int filter_inplace(dks_ctx* ctx, Exec& ex, int ik, V* y, V* tmp, int nb, double C, double om,
+                          cudaStream_t st) {
+  DKS_TRY(apply_h<V>(ctx, ex, ik, y, tmp, nb, C, 1.0 / om, st));
+  return apply_h<V>(ctx, ex, ik, tmp, y, nb, C, 1.0 / om, st);
 }
 
 // contractions of one phase: native arithmetic of V, or double-float for complex128 blocks
@@ -122,12 +126,12 @@ static int fetch(Small& sm, Pinned& pin, int n, std::vector<double>& res, cudaSt
 }
 
 template <typename V>
-static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int n, int nconv, double tol,
+static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int n, int nconv, double tol,
                  int n_init, int n_iter, double C, double om, int precond, int use_filter, bool stop_on_stall,
                  double chol_tol, double drop_tol, std::vector<double>* hist, PhaseOut& out, cudaStream_t st,
                  bool df = false) {
   df = df && sizeof(V) == sizeof(double2);
-  ctx->df_gemm = df;   // projector contractions inside apply_h follow the phase's arithmetic
+  ex.df_gemm = df;   // projector contractions inside apply_h follow the phase's arithmetic
   const KPoint& kp = ctx->k[ik];
   const int rows = 4 * kp.npw;
   const size_t colsz = (size_t)rows;
@@ -136,11 +140,11 @@ static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int
   // lines 1-3: initial filtering
   if (use_filter)
     for (int i = 0; i < n_init; ++i) {
-      DKS_TRY(filter_inplace<V>(ctx, ik, b.z[cur], b.tmp, n, C, om, st));
+      DKS_TRY(filter_inplace<V>(ctx, ex, ik, b.z[cur], b.tmp, n, C, om, st));
       happ += 2LL * n;
     }
   // line 4-6: Rayleigh-Ritz on X0
-  DKS_TRY(apply_h<V>(ctx, ik, b.z[cur], b.hz[cur], n, 0.0, 1.0, st));
+  DKS_TRY(apply_h<V>(ctx, ex, ik, b.z[cur], b.hz[cur], n, 0.0, 1.0, st));
   happ += n;
   DKS_TRY(gram<V>(b.z[cur], b.hz[cur], rows, n, sm, st, df));
   DKS_TRY(rayleigh_ritz(sm.a, sm.s, n, n, sm.vm, sm.lam, sm.info, sm.rrs, st, chol_tol, drop_tol));
@@ -169,10 +173,10 @@ static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int
     V* hy = b.hz[cur] + (size_t)n * colsz;
     DKS_TRY(precond_apply<V>(b.z[cur], b.hz[cur], sm.lam, sm.stats, sm.act, a, kp.ek, kp.npw, precond, y, st));
     if (use_filter) {
-      DKS_TRY(filter_inplace<V>(ctx, ik, y, b.tmp, a, C, om, st));
+      DKS_TRY(filter_inplace<V>(ctx, ex, ik, y, b.tmp, a, C, om, st));
       happ += 2LL * a;
     }
-    DKS_TRY(apply_h<V>(ctx, ik, y, hy, a, 0.0, 1.0, st));
+    DKS_TRY(apply_h<V>(ctx, ex, ik, y, hy, a, 0.0, 1.0, st));
     happ += a;
     const int nz = n + a + p;
     DKS_TRY(gram<V>(b.z[cur], b.hz[cur], rows, nz, sm, st, df));
@@ -226,7 +230,7 @@ static int phase(dks_ctx* ctx, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int
   out.happ = happ;
   out.cur = cur;
   out.neg = pin.lam[0] < -ctx->c * ctx->c;
-  ctx->df_gemm = false;
+  ex.df_gemm = false;
   return DKS_OK;
 }
 
@@ -253,6 +257,7 @@ void dks_solve_opts_default(dks_solve_opts* o) {
   o->chol_tol = 1e-12;
   o->drop_tol = 1e-12;
   o->emulate_fp64 = 1;
+  o->concurrency = 0;
 }
 
 int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* opts_in, double* eig, void* const* X,
@@ -262,15 +267,15 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
   if (opts_in) opts = *opts_in;
   else dks_solve_opts_default(&opts);
   if (!ctx || !eig || !X || !(tol > 0) || opts.n_init < 0 || opts.n_iter < 0 || opts.nbuf < 0 ||
-      (opts.mode != DKS_MODE_FP64 && opts.mode != DKS_MODE_MIXED))
+      opts.concurrency < 0 || (opts.mode != DKS_MODE_FP64 && opts.mode != DKS_MODE_MIXED))
     return fail(DKS_ERR_INVALID_ARG, "dks_lobpcgf_solve: bad argument");
   cudaStream_t st = (cudaStream_t)opts.stream;
   if (report) {
     std::memset(report, 0, sizeof(*report));
     report->shift = ctx->c * ctx->c;
   }
-  // sizes
   int nmax = 0, rowsmax = 0;
+  std::vector<size_t> eoff(ctx->nk + 1, 0);
   for (int ik = 0; ik < ctx->nk; ++ik) {
     const int nv = opts.nev_k ? opts.nev_k[ik] : nev;
     if (nv <= 0 || !X[ik]) return fail(DKS_ERR_INVALID_ARG, "dks_lobpcgf_solve: nev_k and X[ik] required");
@@ -279,6 +284,7 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
     if (n > ctx->k[ik].npw * 4) return fail(DKS_ERR_INVALID_ARG, "block wider than the basis");
     nmax = std::max(nmax, n);
     rowsmax = std::max(rowsmax, 4 * ctx->k[ik].npw);
+    eoff[ik + 1] = eoff[ik] + nv;
   }
   const bool mixed = opts.mode == DKS_MODE_MIXED;
   const size_t cols = (size_t)3 * nmax;
@@ -290,89 +296,146 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
   const size_t small = (2 * nz * nz + 2 * nz * nmax + rr_scratch_elems((int)nz)) * sizeof(double2) +
                        (nmax + 3 * nmax) * sizeof(double) + (nmax + 4) * sizeof(int) + 16 * 256;
   const size_t total = 4 * big64 + tmp64 + 4 * big32 + tmp32 + small + 16 * 256;
-  DKS_TRY(grow(ctx->ws_solve, total));
-  char* base = reinterpret_cast<char*>(ctx->ws_solve.ptr);
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    void* p = base + off;
-    off += (bytes + 255) / 256 * 256;
-    return p;
-  };
-  Blocks<double2> b64{};
-  Blocks<float2> b32{};
-  b64.z[0] = (double2*)take(big64);
-  b64.z[1] = (double2*)take(big64);
-  b64.hz[0] = (double2*)take(big64);
-  b64.hz[1] = (double2*)take(big64);
-  b64.tmp = (double2*)take(tmp64);
-  if (mixed) {
-    b32.z[0] = (float2*)take(big32);
-    b32.z[1] = (float2*)take(big32);
-    b32.hz[0] = (float2*)take(big32);
-    b32.hz[1] = (float2*)take(big32);
-    b32.tmp = (float2*)take(tmp32);
+  // concurrent k-point workers, each with its own stream and workspace (bounded by free memory)
+  int nworkers = opts.concurrency > 0 ? opts.concurrency : std::min(ctx->nk, 4);
+  nworkers = std::max(1, std::min(nworkers, ctx->nk));
+  {
+    size_t freeb = 0, totalb = 0;
+    if (cudaMemGetInfo(&freeb, &totalb) == cudaSuccess) {
+      const size_t per = total + (size_t)6 * 64 * 1024 * 1024;   // + H' intermediates
+      while (nworkers > 1 && (size_t)nworkers * per > freeb * 8 / 10) --nworkers;
+    }
   }
-  Small sm;
-  sm.a = (double2*)take(nz * nz * sizeof(double2));
-  sm.s = (double2*)take(nz * nz * sizeof(double2));
-  sm.vm = (double2*)take(nz * nmax * sizeof(double2));
-  sm.vp = (double2*)take(nz * nmax * sizeof(double2));
-  sm.rrs = (double2*)take(rr_scratch_elems((int)nz) * sizeof(double2));
-  sm.lam = (double*)take(nmax * sizeof(double));
-  sm.stats = (double*)take(3 * nmax * sizeof(double));
-  sm.act = (int*)take(nmax * sizeof(int));
-  sm.info = (int*)take(4 * sizeof(int));
-  Pinned pin;
-  DKS_TRY(pin.alloc(nmax));
-
-  int status = DKS_OK;
-  size_t eoff = 0;
+  if (nworkers > 1) DKS_CUDA_TRY(cudaStreamSynchronize(st));   // caller's pending work before ours
+  while ((int)ctx->exec.size() < nworkers) ctx->exec.push_back(new Exec());
+  for (int w = 0; w < nworkers; ++w) {
+    DKS_TRY(grow(ctx->exec[w]->ws_solve, total));
+    if (nworkers > 1 && !ctx->exec[w]->own)
+      DKS_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->exec[w]->own, cudaStreamNonBlocking));
+  }
+  // k-points largest first (cost ~ block width x basis size)
+  std::vector<int> order(ctx->nk);
+  for (int ik = 0; ik < ctx->nk; ++ik) order[ik] = ik;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const double ca = (double)(opts.nev_k ? opts.nev_k[a] : nev) * ctx->k[a].npw;
+    const double cb = (double)(opts.nev_k ? opts.nev_k[b] : nev) * ctx->k[b].npw;
+    return ca > cb;
+  });
+  std::atomic<int> next{0};
+  std::atomic<long long> happ{0};
+  std::vector<int> krc(ctx->nk, DKS_OK);
+  std::vector<std::string> kmsg(ctx->nk);
   std::vector<double> hist;
-  for (int ik = 0; ik < ctx->nk; ++ik) {
-    const KPoint& kp = ctx->k[ik];
-    const int nv = opts.nev_k ? opts.nev_k[ik] : nev;
-    const int n = nv + opts.nbuf;
-    const size_t elems = (size_t)n * 4 * kp.npw;
-    const double C = std::isnan(opts.C) ? kp.cshift : opts.C;
-    const double om = std::isnan(opts.Omega) ? kp.omega : opts.Omega;
-    PhaseOut o32, o64;
+  std::vector<PhaseOut> o32s(ctx->nk), o64s(ctx->nk);
+  auto worker = [&](int w) {
+    cudaSetDevice(ctx->device);
+    Exec& ex = *ctx->exec[w];
+    cudaStream_t ws = nworkers > 1 ? ex.own : st;
+    char* base = reinterpret_cast<char*>(ex.ws_solve.ptr);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+      void* p = base + off;
+      off += (bytes + 255) / 256 * 256;
+      return p;
+    };
+    Blocks<double2> b64{};
+    Blocks<float2> b32{};
+    b64.z[0] = (double2*)take(big64);
+    b64.z[1] = (double2*)take(big64);
+    b64.hz[0] = (double2*)take(big64);
+    b64.hz[1] = (double2*)take(big64);
+    b64.tmp = (double2*)take(tmp64);
     if (mixed) {
-      DKS_TRY(convert<double2, float2>((const double2*)X[ik], b32.z[0], elems, st));
-      o32.cur = 0;
-      DKS_TRY(phase<float2>(ctx, ik, b32, sm, pin, n, nv, std::max(opts.refine_tol, tol), opts.n_init, opts.n_iter,
-                            C, om, opts.precond, opts.use_filter, true, opts.chol_tol, opts.drop_tol,
-                            ik == 0 ? &hist : nullptr, o32, st));
-      DKS_TRY(convert<float2, double2>(b32.z[o32.cur], b64.z[0], elems, st));
-      o64.cur = 0;
-      const int left = std::max(0, opts.n_iter - o32.iterations);
-      DKS_TRY(phase<double2>(ctx, ik, b64, sm, pin, n, nv, tol, opts.use_filter ? 1 : 0, left, C, om, opts.precond,
-                             opts.use_filter, false, opts.chol_tol, opts.drop_tol, ik == 0 ? &hist : nullptr, o64,
-                             st, opts.emulate_fp64 != 0));
-    } else {
-      DKS_CUDA_TRY(cudaMemcpyAsync(b64.z[0], X[ik], elems * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-      o64.cur = 0;
-      DKS_TRY(phase<double2>(ctx, ik, b64, sm, pin, n, nv, tol, opts.n_init, opts.n_iter, C, om, opts.precond,
-                             opts.use_filter, false, opts.chol_tol, opts.drop_tol, ik == 0 ? &hist : nullptr, o64,
-                             st));
+      b32.z[0] = (float2*)take(big32);
+      b32.z[1] = (float2*)take(big32);
+      b32.hz[0] = (float2*)take(big32);
+      b32.hz[1] = (float2*)take(big32);
+      b32.tmp = (float2*)take(tmp32);
     }
-    DKS_CUDA_TRY(cudaMemcpyAsync(X[ik], b64.z[o64.cur], elems * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    DKS_CUDA_TRY(cudaStreamSynchronize(st));
-    for (int j = 0; j < nv; ++j) eig[eoff + j] = pin.lam[j];
-    eoff += nv;
-    if (report) {
-      if (ik < 64) {
-        report->iterations[ik] = o32.iterations + o64.iterations;
-        report->fp64_iterations[ik] = o64.iterations;
-        report->max_residual[ik] = o64.max_res;
+    Small sm;
+    sm.a = (double2*)take(nz * nz * sizeof(double2));
+    sm.s = (double2*)take(nz * nz * sizeof(double2));
+    sm.vm = (double2*)take(nz * nmax * sizeof(double2));
+    sm.vp = (double2*)take(nz * nmax * sizeof(double2));
+    sm.rrs = (double2*)take(rr_scratch_elems((int)nz) * sizeof(double2));
+    sm.lam = (double*)take(nmax * sizeof(double));
+    sm.stats = (double*)take(3 * nmax * sizeof(double));
+    sm.act = (int*)take(nmax * sizeof(int));
+    sm.info = (int*)take(4 * sizeof(int));
+    Pinned pin;
+    if (pin.alloc(nmax) != DKS_OK) {
+      const int t = next.fetch_add(ctx->nk);   // stop handing out work
+      if (t < ctx->nk) {
+        krc[order[t]] = DKS_ERR_OOM;
+        kmsg[order[t]] = "pinned host buffer";
       }
-      report->h_applications += o32.happ + o64.happ;
+      return;
     }
-    if (status == DKS_OK) {
-      if (o64.neg) status = fail(DKS_ERR_NEG_STATE, "a returned eigenvalue lies below the gap midpoint");
-      else if (!o64.converged) status = fail(DKS_ERR_NOT_CONVERGED, "n_iter exhausted");
+    for (int t = next.fetch_add(1); t < ctx->nk; t = next.fetch_add(1)) {
+      const int ik = order[t];
+      auto run = [&]() -> int {
+        const KPoint& kp = ctx->k[ik];
+        const int nv = opts.nev_k ? opts.nev_k[ik] : nev;
+        const int n = nv + opts.nbuf;
+        const size_t elems = (size_t)n * 4 * kp.npw;
+        const double C = std::isnan(opts.C) ? kp.cshift : opts.C;
+        const double om = std::isnan(opts.Omega) ? kp.omega : opts.Omega;
+        std::vector<double>* h = ik == 0 ? &hist : nullptr;
+        PhaseOut& o32 = o32s[ik];
+        PhaseOut& o64 = o64s[ik];
+        if (mixed) {
+          DKS_TRY(convert<double2, float2>((const double2*)X[ik], b32.z[0], elems, ws));
+          o32.cur = 0;
+          DKS_TRY(phase<float2>(ctx, ex, ik, b32, sm, pin, n, nv, std::max(opts.refine_tol, tol), opts.n_init,
+                                opts.n_iter, C, om, opts.precond, opts.use_filter, true, opts.chol_tol,
+                                opts.drop_tol, h, o32, ws));
+          DKS_TRY(convert<float2, double2>(b32.z[o32.cur], b64.z[0], elems, ws));
+          o64.cur = 0;
+          const int left = std::max(0, opts.n_iter - o32.iterations);
+          DKS_TRY(phase<double2>(ctx, ex, ik, b64, sm, pin, n, nv, tol, opts.use_filter ? 1 : 0, left, C, om,
+                                 opts.precond, opts.use_filter, false, opts.chol_tol, opts.drop_tol, h, o64, ws,
+                                 opts.emulate_fp64 != 0));
+        } else {
+          DKS_CUDA_TRY(cudaMemcpyAsync(b64.z[0], X[ik], elems * sizeof(double2), cudaMemcpyDeviceToDevice, ws));
+          o64.cur = 0;
+          DKS_TRY(phase<double2>(ctx, ex, ik, b64, sm, pin, n, nv, tol, opts.n_init, opts.n_iter, C, om,
+                                 opts.precond, opts.use_filter, false, opts.chol_tol, opts.drop_tol, h, o64, ws));
+        }
+        DKS_CUDA_TRY(cudaMemcpyAsync(X[ik], b64.z[o64.cur], elems * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                     ws));
+        DKS_CUDA_TRY(cudaStreamSynchronize(ws));
+        for (int j = 0; j < nv; ++j) eig[eoff[ik] + j] = pin.lam[j];
+        happ += o32.happ + o64.happ;
+        return DKS_OK;
+      };
+      const int rc = run();
+      if (rc != DKS_OK) {
+        krc[ik] = rc;
+        kmsg[ik] = dks_last_error();
+      }
     }
+  };
+  if (nworkers == 1) {
+    worker(0);
+  } else {
+    std::vector<std::thread> threads;
+    for (int w = 0; w < nworkers; ++w) threads.emplace_back(worker, w);
+    for (std::thread& t : threads) t.join();
+  }
+  int status = DKS_OK;
+  for (int ik = 0; ik < ctx->nk && status == DKS_OK; ++ik)
+    if (krc[ik] != DKS_OK) status = fail(krc[ik], "k-point " + std::to_string(ik) + ": " + kmsg[ik]);
+  for (int ik = 0; ik < ctx->nk && status == DKS_OK; ++ik) {
+    if (o64s[ik].neg) status = fail(DKS_ERR_NEG_STATE, "a returned eigenvalue lies below the gap midpoint");
+    else if (!o64s[ik].converged) status = fail(DKS_ERR_NOT_CONVERGED, "n_iter exhausted");
   }
   if (report) {
+    for (int ik = 0; ik < std::min(ctx->nk, 64); ++ik) {
+      report->iterations[ik] = o32s[ik].iterations + o64s[ik].iterations;
+      report->fp64_iterations[ik] = o64s[ik].iterations;
+      report->max_residual[ik] = o64s[ik].max_res;
+    }
+    report->h_applications = happ.load();
     report->hist_len = (int)std::min<size_t>(hist.size(), 512);
     for (int i = 0; i < report->hist_len; ++i) report->res_history[i] = hist[i];
     report->status = status;

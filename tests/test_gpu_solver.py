@@ -95,3 +95,32 @@ def test_dimer_full_size_vs_oracle(mode):
     pick = np.array([0, 7, 18, 31])
     res = _residuals(hop, x[pick], lam[pick])
     assert res.max() < 1e-6, res
+
+
+def test_multi_k_concurrent_matches_serial_and_dense():
+    """Several k-points (a k/-k pair and time-reversal-invariant points) solved by concurrent
+    workers: identical to the serial solve, each k within 1e-8 Ha of dense zheevd, E(k) = E(-k)
+    and Kramers pairs at the invariant points."""
+    gpu()
+    import torch
+    import paper_1211_1446_gb300 as P
+    import oracle.basis as ob
+    kf = [[0.0, 0.0, 0.0], [0.25, -0.125, 0.0], [-0.25, 0.125, 0.0], [0.5, 0.5, 0.0]]
+    wl = W.make("small", kfrac=kf)
+    ctx = P.Context.from_workload(wl)
+    nev = 6
+    runs = []
+    for conc in (4, 1):
+        xs = [torch.from_numpy(W.start_block(ctx.npw(ik), nev, wl.seed, ik)).cuda() for ik in range(4)]
+        lam, rep, rc = ctx.solve(xs, nev, mode=1, concurrency=conc, check=False)
+        assert rc == 0, rep
+        runs.append(lam)
+    for ik in range(4):
+        assert np.abs(runs[0][ik] - runs[1][ik]).max() < 1e-9
+        m, q = ob.sphere(wl.lattice, wl.grid, wl.kfrac[ik], wl.ecut_k[ik])
+        ref, _, _ = olb.dense_eigs(oop.dense_hamiltonian(wl, m, q), wl.c, nev)
+        assert np.abs(runs[0][ik] - ref).max() < 1e-8
+    assert np.abs(runs[0][1] - runs[0][2]).max() < 1e-8          # E(k) = E(-k)
+    for ik in (0, 3):                                            # Kramers pairs at TRIM
+        lam = runs[0][ik]
+        assert np.abs(lam[0::2] - lam[1::2]).max() < 1e-7
