@@ -45,6 +45,38 @@ constexpr int RRC_WARPS = RRC_THREADS / 32;
 #define RR_MARK(i)
 #endif
 
+// Reciprocal and square root for the serial chains: FP64 division and square root are long
+// instruction sequences on this part, so they are replaced by Newton-Raphson iterations
+// (x <- x + x (1 - a x) for 1/a, y <- y (3 - a y^2)/2 for 1/sqrt(a)) in FP64 FMAs, seeded by the
+// FP32 approximations; each iteration squares the relative error, so two take the ~1e-7 seed
+// below FP64 rounding.  Outside the FP32 normal range the exact operations are used.
+__device__ __forceinline__ bool f32_range(double a) {
+  const double m = fabs(a);
+  return m > 1e-37 && m < 1e37;
+}
+__device__ __forceinline__ double nr_rcp(double a) {
+  if (!f32_range(a)) return 1.0 / a;
+  double x = (double)__frcp_rn((float)a);
+  x = fma(x, fma(-a, x, 1.0), x);
+  x = fma(x, fma(-a, x, 1.0), x);
+  return x;
+}
+__device__ __forceinline__ double nr_rsqrt(double a) {
+  if (!f32_range(a) || a < 0) return 1.0 / sqrt(a);
+  double y = (double)rsqrtf((float)a);
+  const double h = 0.5 * a;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+__device__ __forceinline__ double nr_sqrt(double a) { return a == 0.0 ? 0.0 : a * nr_rsqrt(a); }
+__device__ __forceinline__ double nr_hypot(double x, double y) {
+  const double s = fmax(fabs(x), fabs(y));
+  if (s == 0.0) return 0.0;
+  const double r = nr_rcp(s), xs = x * r, ys = y * r;
+  return s * nr_sqrt(xs * xs + ys * ys);
+}
+
 __device__ __forceinline__ double2 warp_csum(double2 v) {
   for (int o = 16; o; o >>= 1) {
     v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
@@ -64,7 +96,7 @@ __device__ int sturm_count(const double* d, const double* e2, int m, double x, d
   if (fabs(q) < pivmin) q = -pivmin;
   cnt += q < 0;
   for (int j = 1; j < m; ++j) {
-    q = d[j] - x - e2[j - 1] / q;
+    q = d[j] - x - e2[j - 1] * nr_rcp(q);
     if (fabs(q) < pivmin) q = -pivmin;
     cnt += q < 0;
   }
@@ -112,7 +144,7 @@ __device__ void tri_factor(const double* d, const double* e, int m, double lam, 
     if (fabs(a) >= fabs(c)) {
       piv[i] = 0;
       if (a == 0.0) a = tiny;
-      const double mult = c / a;
+      const double mult = c * nr_rcp(a);
       l[i] = mult;
       u0[i] = a;
       u1[i] = b;
@@ -121,7 +153,7 @@ __device__ void tri_factor(const double* d, const double* e, int m, double lam, 
       b = bn;
     } else {
       piv[i] = 1;
-      const double mult = a / c;
+      const double mult = a * nr_rcp(c);
       l[i] = mult;
       u0[i] = c;
       u1[i] = dn;
@@ -134,7 +166,7 @@ __device__ void tri_factor(const double* d, const double* e, int m, double lam, 
   u0[m - 1] = a;
   u1[m - 1] = 0.0;
   u2[m - 1] = 0.0;
-  for (int i = 0; i < m; ++i) u0[i] = 1.0 / u0[i];   // the solves multiply by reciprocals
+  for (int i = 0; i < m; ++i) u0[i] = nr_rcp(u0[i]);   // the solves multiply by reciprocals
 }
 
 __device__ void tri_solve(int m, const double* f, double* x) {
@@ -219,7 +251,7 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
       failed = true;
       break;
     }
-    const double ljj = sqrt(piv), inv = 1.0 / ljj;
+    const double inv = nr_rsqrt(piv), ljj = piv * inv;
     for (int i = j + gtid; i < m; i += gnt) {
       const double2 v = i == j ? double2{ljj, 0} : double2{lm[(size_t)j * m + i].x * inv, lm[(size_t)j * m + i].y * inv};
       lf[(size_t)j * m + i] = v;
@@ -243,7 +275,7 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
   }
   if (gtid == 0) *flag = 0;
   double* linv = lamw + m;     // 1 / L_ii (the spare m-array)
-  for (int i = gtid; i < m; i += gnt) linv[i] = 1.0 / lt[(size_t)i * m + i].x;
+  for (int i = gtid; i < m; i += gnt) linv[i] = nr_rcp(lt[(size_t)i * m + i].x);
   cl.sync();
   RR_MARK(1);
   double2* wvec = reinterpret_cast<double2*>(rrc_smem) + (size_t)wl * m;   // per-warp vector
@@ -288,44 +320,61 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
     cm[e] = i == j ? double2{a.x, 0.0} : double2{0.5 * (a.x + b.x), 0.5 * (a.y - b.y)};
   }
   cl.sync();
-  // 4. Householder reduction of cm
+  // 4. Householder reduction of cm.  Warp 0 of every CTA forms the reflector (norm, phase, tau)
+  // and the scalar K and hands them to its CTA through shared memory.
+  __shared__ double2 hh[4];   // {tau, 0}, beta, v0, K
   for (int k = 0; k + 2 < m; ++k) {
     const int len = m - k - 1;
     double2* x = cm + (size_t)k * m + k + 1;
-    double a2 = 0;
-    for (int i = lane; i < len; i += 32) a2 += x[i].x * x[i].x + x[i].y * x[i].y;
-    a2 = warp_sum(a2);
-    const double2 x0 = x[0];
-    const double ax0 = hypot(x0.x, x0.y);
-    const double alpha = sqrt(a2);
-    double t = 0.0;
-    double2 beta = x0, v0 = x0;
-    if (alpha > 1e-300 && a2 - ax0 * ax0 > 1e-30 * a2) {
-      const double2 phs = ax0 > 0 ? double2{x0.x / ax0, x0.y / ax0} : double2{1, 0};
-      beta = double2{-phs.x * alpha, -phs.y * alpha};
-      v0 = double2{x0.x - beta.x, x0.y - beta.y};
-      t = 2.0 / (a2 - ax0 * ax0 + v0.x * v0.x + v0.y * v0.y);
+    if (wl == 0) {
+      double a2 = 0;
+      for (int i = lane; i < len; i += 32) a2 += x[i].x * x[i].x + x[i].y * x[i].y;
+      a2 = warp_sum(a2);
+      const double2 x0 = x[0];
+      const double ax0 = nr_hypot(x0.x, x0.y);
+      const double alpha = nr_sqrt(a2);
+      double t = 0.0;
+      double2 beta = x0, v0 = x0;
+      if (alpha > 1e-300 && a2 - ax0 * ax0 > 1e-30 * a2) {
+        const double ri = ax0 > 0 ? nr_rcp(ax0) : 0.0;
+        const double2 phs = ax0 > 0 ? double2{x0.x * ri, x0.y * ri} : double2{1, 0};
+        beta = double2{-phs.x * alpha, -phs.y * alpha};
+        v0 = double2{x0.x - beta.x, x0.y - beta.y};
+        t = 2.0 * nr_rcp(a2 - ax0 * ax0 + v0.x * v0.x + v0.y * v0.y);
+      }
+      if (lane == 0) {
+        hh[0] = double2{t, 0.0};
+        hh[1] = beta;
+        hh[2] = v0;
+      }
     }
+    __syncthreads();
+    const double t = hh[0].x;
+    const double2 beta = hh[1], v0 = hh[2];
     if (t != 0.0) {
       double2* a22 = cm + (size_t)(k + 1) * m + (k + 1);
       // p_i = t sum_j A22[i, j] v_j = t sum_j conj(A22[j, i]) v_j (read column i)
       for (int i = gw; i < len; i += gnw) {
-        double2 s{0, 0};
+        double2 sacc{0, 0};
         for (int j = lane; j < len; j += 32) {
           const double2 vj = j == 0 ? v0 : x[j];
-          s = cadd(s, cmulc(a22[(size_t)i * m + j], vj));
+          sacc = cadd(sacc, cmulc(a22[(size_t)i * m + j], vj));
         }
-        s = warp_csum(s);
-        if (lane == 0) pv[i] = double2{t * s.x, t * s.y};
+        sacc = warp_csum(sacc);
+        if (lane == 0) pv[i] = double2{t * sacc.x, t * sacc.y};
       }
     }
     cl.sync();
     if (t != 0.0) {
       double2* a22 = cm + (size_t)(k + 1) * m + (k + 1);
-      double2 kv{0, 0};
-      for (int i = lane; i < len; i += 32) kv = cadd(kv, cmulc(i == 0 ? v0 : x[i], pv[i]));
-      kv = warp_csum(kv);
-      kv = double2{0.5 * t * kv.x, 0.5 * t * kv.y};
+      if (wl == 0) {
+        double2 kv{0, 0};
+        for (int i = lane; i < len; i += 32) kv = cadd(kv, cmulc(i == 0 ? v0 : x[i], pv[i]));
+        kv = warp_csum(kv);
+        if (lane == 0) hh[3] = double2{0.5 * t * kv.x, 0.5 * t * kv.y};
+      }
+      __syncthreads();
+      const double2 kv = hh[3];
       for (int e = gtid; e < len * len; e += gnt) {
         const int i = e % len, j = e / len;
         const double2 vi = i == 0 ? v0 : x[i], vj = j == 0 ? v0 : x[j];
@@ -355,11 +404,14 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
     for (int k = 0; k < m; ++k) dd[k] = cm[(size_t)k * m + k].x;
     for (int k = 0; k + 1 < m; ++k) {
       const double2 e = ph[k];
-      const double ae = hypot(e.x, e.y);
+      const double ae = nr_hypot(e.x, e.y);
       ee[k] = ae;
       e2[k] = ae * ae;
       ph[k] = phi;
-      if (ae > 0) phi = cmul(phi, double2{e.x / ae, e.y / ae});
+      if (ae > 0) {
+        const double ri = nr_rcp(ae);
+        phi = cmul(phi, double2{e.x * ri, e.y * ri});
+      }
     }
     ph[m - 1] = phi;
     ee[m - 1] = 0;
@@ -388,82 +440,45 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
   }
   tnorm = fmax(fabs(lo0), fabs(hi0));
   const double pivmin = fmax(1e-290, DBL_MIN * 4.0) + 1e-300;
-  // multisection: warp gw finds eigenvalue index gw (ascending); four 33-way FP32 steps first,
-  // then the bracket is widened by the FP32 rounding level and refined in FP64
-  for (int idx = gw; idx < n; idx += gnw) {
+  // bisection of the Sturm count, one eigenvalue per thread (FP64 issue slots are the scarce
+  // resource, so no lane evaluates a count that does not narrow its own bracket): FP32 steps to
+  // ~1e-6 of the Gershgorin width, then the bracket is widened by the FP32 rounding level and
+  // refined in FP64 to a few ulps
+  for (int idx = gtid; idx < n; idx += gnt) {
     double lo = lo0 - 1e-14 * tnorm - 1e-300, hi = hi0 + 1e-14 * tnorm + 1e-300;
     {
       float flo = (float)lo, fhi = (float)hi;
-      for (int it = 0; it < 4; ++it) {
-        const float x = flo + (fhi - flo) * (float)(lane + 1) / 33.0f;
-        const int cnt = sturm_count_f(fd, fe2, m, x, 1e-30f);
-        const unsigned above = __ballot_sync(0xffffffffu, cnt > idx);
-        const int first = above ? __ffs(above) - 1 : 32;
-        const float nhi = first < 32 ? flo + (fhi - flo) * (float)(first + 1) / 33.0f : fhi;
-        const float nlo = first > 0 ? flo + (fhi - flo) * (float)first / 33.0f : flo;
-        flo = nlo;
-        fhi = nhi;
+      for (int it = 0; it < 24 && fhi - flo > 4e-7f * fmaxf(fabsf(flo), fabsf(fhi)); ++it) {
+        const float mid = 0.5f * (flo + fhi);
+        if (sturm_count_f(fd, fe2, m, mid, 1e-30f) > idx) fhi = mid;
+        else flo = mid;
       }
-      const double pad = 1e-5 * tnorm + 1e-300;
+      const double pad = 4e-6 * tnorm + 1e-300;
       lo = fmax(lo, (double)flo - pad);
       hi = fmin(hi, (double)fhi + pad);
     }
-    for (int it = 0; it < 40 && hi - lo > 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300; ++it) {
-      const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-      const int cnt = sturm_count(sd, se2, m, x, pivmin);
-      const unsigned above = __ballot_sync(0xffffffffu, cnt > idx);
-      const int first = above ? __ffs(above) - 1 : 32;    // first point with count > idx
-      const double nhi = first < 32 ? lo + (hi - lo) * (double)(first + 1) / 33.0 : hi;
-      const double nlo = first > 0 ? lo + (hi - lo) * (double)first / 33.0 : lo;
-      lo = nlo;
-      hi = nhi;
+    for (int it = 0; it < 60 && hi - lo > 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (sturm_count(sd, se2, m, mid, pivmin) > idx) hi = mid;
+      else lo = mid;
     }
-    if (lane == 0) lamw[idx] = 0.5 * (lo + hi);
+    lamw[idx] = 0.5 * (lo + hi);
   }
   cl.sync();
   RR_MARK(4);
-  // 6. inverse iteration; clusters of close eigenvalues go to one lane in order
+  // 6. inverse iteration; clusters of close eigenvalues go to one lane in order.  Warps that own
+  // a shared-memory slot (nslots per CTA) take the cluster starts round-robin.
   const double ortol = 1e-7 * fmax(tnorm, 1e-300);
   const int nslots = min(RRC_WARPS, (int)(rr_tri_smem_offset(m) / (sizeof(double) * 6 * (size_t)m)));
   double* fws = reinterpret_cast<double*>(rrc_smem);   // per-slot 5m factors + m vector
-  for (int start = gw; start < n; start += gnw) {
-    // one lane (lane 0) of this warp handles the cluster that begins at `start`
-    const bool begins = start == 0 || lamw[start] - lamw[start - 1] > ortol;
-    if (!begins || lane != 0 || wl >= nslots) continue;
-    int end = start + 1;
-    while (end < n && lamw[end] - lamw[end - 1] <= ortol) ++end;
-    double* f = fws + (size_t)wl * 6 * m;
-    double* xv = f + 5 * m;
-    for (int v = start; v < end; ++v) {
-      const double shift = lamw[v] + (double)(v - start) * 10.0 * DBL_EPSILON * tnorm;
-      tri_factor(sd, se, m, shift, DBL_EPSILON * tnorm + 1e-300, f);
-      for (int i = 0; i < m; ++i) xv[i] = start_val(i, v);
-      for (int itr = 0; itr < 3; ++itr) {
-        tri_solve(m, f, xv);
-        for (int u = start; u < v; ++u) {        // orthogonalise against the cluster's earlier vectors
-          double dot = 0;
-          for (int i = 0; i < m; ++i) dot += zt[(size_t)u * m + i] * xv[i];
-          for (int i = 0; i < m; ++i) xv[i] -= dot * zt[(size_t)u * m + i];
-        }
-        double nrm = 0;
-        for (int i = 0; i < m; ++i) nrm += xv[i] * xv[i];
-        nrm = 1.0 / sqrt(fmax(nrm, 1e-300));
-        for (int i = 0; i < m; ++i) xv[i] *= nrm;
-      }
-      for (int i = 0; i < m; ++i) zt[(size_t)v * m + i] = xv[i];
-    }
-  }
-  // slots beyond nslots (very large m) are handled by the first warp of CTA 0 afterwards
-  cl.sync();
-  if (nslots < RRC_WARPS) {
-    for (int start = 0; start < n; ++start) {
-      const int owner_w = start % gnw;
-      if ((owner_w % RRC_WARPS) < nslots) continue;
+  if (wl < nslots && lane == 0) {
+    const int gslot = crank * nslots + wl, nslot_all = csize * nslots;
+    for (int start = gslot; start < n; start += nslot_all) {
       const bool begins = start == 0 || lamw[start] - lamw[start - 1] > ortol;
-      if (!begins || gtid != 0) continue;
+      if (!begins) continue;
       int end = start + 1;
       while (end < n && lamw[end] - lamw[end - 1] <= ortol) ++end;
-      double* f = fws;
+      double* f = fws + (size_t)wl * 6 * m;
       double* xv = f + 5 * m;
       for (int v = start; v < end; ++v) {
         const double shift = lamw[v] + (double)(v - start) * 10.0 * DBL_EPSILON * tnorm;
@@ -471,21 +486,21 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
         for (int i = 0; i < m; ++i) xv[i] = start_val(i, v);
         for (int itr = 0; itr < 3; ++itr) {
           tri_solve(m, f, xv);
-          for (int u = start; u < v; ++u) {
+          for (int u = start; u < v; ++u) {        // orthogonalise against the cluster's earlier vectors
             double dot = 0;
             for (int i = 0; i < m; ++i) dot += zt[(size_t)u * m + i] * xv[i];
             for (int i = 0; i < m; ++i) xv[i] -= dot * zt[(size_t)u * m + i];
           }
           double nrm = 0;
           for (int i = 0; i < m; ++i) nrm += xv[i] * xv[i];
-          nrm = 1.0 / sqrt(fmax(nrm, 1e-300));
+          nrm = nr_rsqrt(fmax(nrm, 1e-300));
           for (int i = 0; i < m; ++i) xv[i] *= nrm;
         }
         for (int i = 0; i < m; ++i) zt[(size_t)v * m + i] = xv[i];
       }
     }
-    cl.sync();
   }
+  cl.sync();
   RR_MARK(5);
   // 7. u = H_0 ... H_{m-3} (Phi z); V = D L^-H u
   for (int j = gw; j < n; j += gnw) {
