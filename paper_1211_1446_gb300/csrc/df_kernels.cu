@@ -18,17 +18,17 @@
 
 namespace dks {
 
-struct df {   // unevaluated sum hi + lo
+struct gdf {   // unevaluated sum hi + lo
   float hi, lo;
 };
 
-__device__ __forceinline__ df df_split(double x) {
+__device__ __forceinline__ gdf df_split(double x) {
   const float h = (float)x;
-  return df{h, (float)(x - (double)h)};
+  return gdf{h, (float)(x - (double)h)};
 }
 
 // s += a * b (all double-float); renormalised after the update
-__device__ __forceinline__ void df_mac(df& s, const df a, const df b) {
+__device__ __forceinline__ void df_mac(gdf& s, const gdf a, const gdf b) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);          // exact error of the leading product
   e = fmaf(a.hi, b.lo, e);
@@ -42,24 +42,24 @@ __device__ __forceinline__ void df_mac(df& s, const df a, const df b) {
   s.hi = hi;
 }
 
-__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
-__device__ __forceinline__ double df_to_d(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ gdf df_neg(gdf a) { return gdf{-a.hi, -a.lo}; }
+__device__ __forceinline__ double df_to_d(gdf a) { return (double)a.hi + (double)a.lo; }
 
-struct cdf {   // complex double-float
-  df re, im;
+struct gcdf {   // complex double-float
+  gdf re, im;
 };
 
-__device__ __forceinline__ cdf cdf_split(double2 v) { return cdf{df_split(v.x), df_split(v.y)}; }
+__device__ __forceinline__ gcdf gcdf_split(double2 v) { return gcdf{df_split(v.x), df_split(v.y)}; }
 
 // acc += conj(a) * b
-__device__ __forceinline__ void cdf_macc(cdf& acc, const cdf& a, const cdf& b) {
+__device__ __forceinline__ void cdf_macc(gcdf& acc, const gcdf& a, const gcdf& b) {
   df_mac(acc.re, a.re, b.re);
   df_mac(acc.re, a.im, b.im);
   df_mac(acc.im, a.re, b.im);
   df_mac(acc.im, df_neg(a.im), b.re);
 }
 // acc += a * b
-__device__ __forceinline__ void cdf_mac(cdf& acc, const cdf& a, const cdf& b) {
+__device__ __forceinline__ void cdf_mac(gcdf& acc, const gcdf& a, const gcdf& b) {
   df_mac(acc.re, a.re, b.re);
   df_mac(acc.re, df_neg(a.im), b.im);
   df_mac(acc.im, a.re, b.im);
@@ -73,8 +73,8 @@ __global__ void __launch_bounds__(256) k_gemm_hn_df(const double2* __restrict__ 
                                                     const double2* __restrict__ b, int ldb, int k, int m, int n,
                                                     int mt, int kchunk, double2* __restrict__ c, int ldc,
                                                     int lower) {
-  __shared__ cdf as[DHN_T][DHN_T + 1];
-  __shared__ cdf bs[DHN_T][DHN_T + 1];
+  __shared__ gcdf as[DHN_T][DHN_T + 1];
+  __shared__ gcdf bs[DHN_T][DHN_T + 1];
   int tm, tn;
   if (lower) {
     const int t = blockIdx.x;
@@ -90,11 +90,11 @@ __global__ void __launch_bounds__(256) k_gemm_hn_df(const double2* __restrict__ 
   const int kb = blockIdx.y * kchunk;
   const int ke = min(k, kb + kchunk);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  cdf acc[2][2];
+  gcdf acc[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) acc[i][j] = cdf{{0.f, 0.f}, {0.f, 0.f}};
+    for (int j = 0; j < 2; ++j) acc[i][j] = gcdf{{0.f, 0.f}, {0.f, 0.f}};
   for (int k0 = kb; k0 < ke; k0 += DHN_T) {
     for (int e = threadIdx.x; e < DHN_T * DHN_T; e += 256) {
       const int kq = e & (DHN_T - 1), q = e >> 5;
@@ -104,14 +104,14 @@ __global__ void __launch_bounds__(256) k_gemm_hn_df(const double2* __restrict__ 
         if (m0 + q < m) va = a[(size_t)(m0 + q) * lda + gk];
         if (n0 + q < n) vb = b[(size_t)(n0 + q) * ldb + gk];
       }
-      as[kq][q] = cdf_split(va);
-      bs[kq][q] = cdf_split(vb);
+      as[kq][q] = gcdf_split(va);
+      bs[kq][q] = gcdf_split(vb);
     }
     __syncthreads();
 #pragma unroll 4
     for (int kq = 0; kq < DHN_T; ++kq) {
-      const cdf a0 = as[kq][ty], a1 = as[kq][ty + 16];
-      const cdf b0 = bs[kq][tx], b1 = bs[kq][tx + 16];
+      const gcdf a0 = as[kq][ty], a1 = as[kq][ty + 16];
+      const gcdf b0 = bs[kq][tx], b1 = bs[kq][tx + 16];
       cdf_macc(acc[0][0], a0, b0);
       cdf_macc(acc[0][1], a0, b1);
       cdf_macc(acc[1][0], a1, b0);
@@ -170,19 +170,19 @@ __global__ void __launch_bounds__(256) k_gemm_nn_df(const double2* __restrict__ 
                                                     const double2* __restrict__ w, int ldw,
                                                     const double* __restrict__ ws, int n,
                                                     double2* __restrict__ out, int ldo, double alpha, double beta) {
-  __shared__ cdf as[DNN_M][DNN_R];
-  __shared__ cdf wsm[DNN_M][DNN_C];
+  __shared__ gcdf as[DNN_M][DNN_R];
+  __shared__ gcdf wsm[DNN_M][DNN_C];
   const int r0 = blockIdx.x * DNN_R, c0 = blockIdx.y * DNN_C;
   const int row = threadIdx.x & (DNN_R - 1), cg = threadIdx.x >> 6;
-  cdf acc[8];
+  gcdf acc[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) acc[j] = cdf{{0.f, 0.f}, {0.f, 0.f}};
+  for (int j = 0; j < 8; ++j) acc[j] = gcdf{{0.f, 0.f}, {0.f, 0.f}};
   for (int m0 = 0; m0 < m; m0 += DNN_M) {
     for (int e = threadIdx.x; e < DNN_M * DNN_R; e += 256) {
       const int rr = e & (DNN_R - 1), mm = e >> 6;
       double2 v{0, 0};
       if (m0 + mm < m && r0 + rr < k) v = a[(size_t)(m0 + mm) * lda + r0 + rr];
-      as[mm][rr] = cdf_split(v);
+      as[mm][rr] = gcdf_split(v);
     }
     for (int e = threadIdx.x; e < DNN_M * DNN_C; e += 256) {
       const int cc = e & (DNN_C - 1), mm = e >> 5;
@@ -193,12 +193,12 @@ __global__ void __launch_bounds__(256) k_gemm_nn_df(const double2* __restrict__ 
         v.x *= s;
         v.y *= s;
       }
-      wsm[mm][cc] = cdf_split(v);
+      wsm[mm][cc] = gcdf_split(v);
     }
     __syncthreads();
 #pragma unroll 2
     for (int mm = 0; mm < DNN_M; ++mm) {
-      const cdf av = as[mm][row];
+      const gcdf av = as[mm][row];
 #pragma unroll
       for (int j = 0; j < 8; ++j) cdf_mac(acc[j], av, wsm[mm][cg * 8 + j]);
     }

@@ -248,9 +248,11 @@ static void free_ctx(dks_ctx* ctx) {
   for (int a = 0; a < 3; ++a) {
     cudaFree(ctx->tw64[a]);
     cudaFree(ctx->tw32[a]);
+    cudaFree(ctx->twdf[a]);
   }
   cudaFree(ctx->vperm64);
   cudaFree(ctx->vperm32);
+  cudaFree(ctx->vpermdf);
   cudaFree(ctx->dvec_dev);
   for (KPoint& kp : ctx->k) {
     cudaFree(kp.stick_start);
@@ -353,8 +355,14 @@ int dks_create(const dks_cell* cell, double ecut, const dks_potentials* pot, con
       tw[t] = double2{std::cos(ang), std::sin(ang)};
       tw32[t] = float2{(float)tw[t].x, (float)tw[t].y};
     }
+    std::vector<float4> twd(n);
+    for (int t = 0; t < n; ++t) {
+      const float rh = (float)tw[t].x, ih = (float)tw[t].y;
+      twd[t] = float4{rh, (float)(tw[t].x - (double)rh), ih, (float)(tw[t].y - (double)ih)};
+    }
     if ((rc = upload(&ctx->tw64[a], tw.data(), n))) return bail(rc);
     if ((rc = upload(&ctx->tw32[a], tw32.data(), n))) return bail(rc);
+    if ((rc = upload(&ctx->twdf[a], twd.data(), n))) return bail(rc);
   }
   // potential in DIF order, scaled by 1/Ng
   ctx->has_v = pot && pot->v_r;
@@ -364,6 +372,7 @@ int dks_create(const dks_cell* cell, double ecut, const dks_potentials* pot, con
                            p3 = dif_positions(ctx->plan[2]);
     std::vector<double> vp((size_t)ctx->ng);
     std::vector<float> vp32((size_t)ctx->ng);
+    std::vector<float2> vpdf((size_t)ctx->ng);
     for (int i1 = 0; i1 < n1; ++i1)
       for (int i2 = 0; i2 < n2; ++i2)
         for (int i3 = 0; i3 < n3; ++i3) {
@@ -372,9 +381,12 @@ int dks_create(const dks_cell* cell, double ecut, const dks_potentials* pot, con
           const size_t at = (size_t)p3[i3] * n1 * n2 + (size_t)p1[i1] * n2 + p2[i2];
           vp[at] = v / ctx->ng;
           vp32[at] = (float)(v / ctx->ng);
+          const float h = (float)vp[at];
+          vpdf[at] = float2{h, (float)(vp[at] - (double)h)};
         }
     if ((rc = upload(&ctx->vperm64, vp.data(), vp.size()))) return bail(rc);
     if ((rc = upload(&ctx->vperm32, vp32.data(), vp32.size()))) return bail(rc);
+    if ((rc = upload(&ctx->vpermdf, vpdf.data(), vpdf.size()))) return bail(rc);
   }
   // projector channels
   std::vector<Channel> chans;

@@ -93,9 +93,11 @@ struct dks_ctx {
   // device: twiddles exp(+2 pi i t / N_axis), t < N_axis
   double2* tw64[3] = {nullptr, nullptr, nullptr};
   float2* tw32[3] = {nullptr, nullptr, nullptr};
+  float4* twdf[3] = {nullptr, nullptr, nullptr};   // double-float twiddles (re hi, re lo, im hi, im lo)
   // device: V / Ng in DIF-permuted layout [p3][p1*N2 + p2]
   double* vperm64 = nullptr;
   float* vperm32 = nullptr;
+  float2* vpermdf = nullptr;    // double-float (hi, lo) copy
   double vmax = 0;
   bool has_v = false;
   // projectors

@@ -45,3 +45,67 @@ template <> __device__ __forceinline__ float2 from_d2<float2>(double2 v) {
 }
 
 }  // namespace dks
+
+namespace dks {
+
+// ---------------------------------------------------------------- double-float arithmetic
+// A value is the unevaluated sum h + l of two floats (about 48 significant bits).  Sums use
+// Knuth's two-sum and products Dekker's exact product via fma, each followed by a fast
+// renormalisation; all of it runs on the FP32 units.
+struct dfl {
+  float h, l;
+};
+__device__ __forceinline__ dfl df_from(double x) {
+  const float h = (float)x;
+  return dfl{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_val(dfl a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  float e = (a.h - (s - bb)) + (b.h - bb);
+  e += a.l + b.l;
+  const float h = s + e;
+  return dfl{h, e - (h - s)};
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.h, -a.l}; }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float h = p + e;
+  return dfl{h, e - (h - p)};
+}
+
+// complex double-float (16 bytes, the size of a double2)
+struct cdf {
+  dfl re, im;
+};
+__device__ __forceinline__ cdf cadd(cdf a, cdf b) { return cdf{df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ cdf csub(cdf a, cdf b) {
+  return cdf{df_add(a.re, df_neg(b.re)), df_add(a.im, df_neg(b.im))};
+}
+__device__ __forceinline__ cdf cmul(cdf a, cdf b) {
+  return cdf{df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ cdf mul_i(cdf a) { return cdf{df_neg(a.im), a.re}; }
+__device__ __forceinline__ cdf mul_mi(cdf a) { return cdf{a.im, df_neg(a.re)}; }
+__device__ __forceinline__ cdf cscale(cdf a, dfl s) { return cdf{df_mul(a.re, s), df_mul(a.im, s)}; }
+__device__ __forceinline__ cdf twiddle(const cdf* __restrict__ tw, int t, bool fwd) {
+  cdf w = tw[t];
+  if (fwd) w.im = df_neg(w.im);
+  return w;
+}
+__device__ __forceinline__ double2 to_d2(cdf v) { return double2{df_val(v.re), df_val(v.im)}; }
+template <> __device__ __forceinline__ cdf from_d2<cdf>(double2 v) { return cdf{df_from(v.x), df_from(v.y)}; }
+template <> struct RealOf<cdf> { using T = dfl; };
+
+// conversions between the storage type in global memory and the compute type in shared memory
+template <typename Vs> __device__ __forceinline__ Vs to_s(double2 v) { return from_d2<Vs>(v); }
+template <typename Vs> __device__ __forceinline__ Vs to_s(float2 v) { return v; }
+__device__ __forceinline__ double2 to_g(double2 v) { return v; }
+__device__ __forceinline__ float2 to_g(float2 v) { return v; }
+__device__ __forceinline__ double2 to_g(cdf v) { return to_d2(v); }
+
+}  // namespace dks

@@ -28,11 +28,15 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "dks_internal.h"
 #include "dks_kernels.cuh"
 
 namespace dks {
+
+template <typename V> __device__ __forceinline__ V vzero() { return V{0, 0}; }
+template <> __device__ __forceinline__ cdf vzero<cdf>() { return cdf{{0.f, 0.f}, {0.f, 0.f}}; }
 
 // ---------------------------------------------------------------------------
 // one radix-R pass over a batch of lines held in shared memory (in place)
@@ -111,9 +115,9 @@ __device__ void fft_lines(V* buf, int nlines, int lstride, int estride, const Ax
 // ---------------------------------------------------------------------------
 // pass A: sphere -> stick lines, inverse FFT along axis 3
 // ---------------------------------------------------------------------------
-template <typename V>
+template <typename Vg, typename V>
 __global__ void __launch_bounds__(256) k_stick_inverse(
-    const V* __restrict__ x, V* __restrict__ t, int npw, int nsticks, const int* __restrict__ stick_start,
+    const Vg* __restrict__ x, Vg* __restrict__ t, int npw, int nsticks, const int* __restrict__ stick_start,
     const int* __restrict__ pw_stick, const int* __restrict__ pw_iz, AxisPlan p3,
     const V* __restrict__ tw3, int spb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -122,26 +126,26 @@ __global__ void __launch_bounds__(256) k_stick_inverse(
   const int s0 = blockIdx.x * spb;
   const int ns = min(spb, nsticks - s0);
   const int f = blockIdx.y;
-  for (int e = threadIdx.x; e < spb * n3; e += blockDim.x) line[e] = V{0, 0};
+  for (int e = threadIdx.x; e < spb * n3; e += blockDim.x) line[e] = vzero<V>();
   __syncthreads();
-  const V* xf = x + (size_t)f * npw;
+  const Vg* xf = x + (size_t)f * npw;
   const int q0 = stick_start[s0], q1 = stick_start[s0 + ns];
   for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x)
-    line[(pw_stick[q] - s0) * n3 + pw_iz[q]] = xf[q];
+    line[(pw_stick[q] - s0) * n3 + pw_iz[q]] = to_s<V>(xf[q]);
   __syncthreads();
   fft_lines<V, false>(line, ns, n3, 1, p3, tw3, false);
-  V* tf = t + (size_t)f * n3 * nsticks;
+  Vg* tf = t + (size_t)f * n3 * nsticks;
   for (int e = threadIdx.x; e < ns * n3; e += blockDim.x) {
     const int z = e / ns, s = e - z * ns;
-    tf[(size_t)z * nsticks + s0 + s] = line[s * n3 + z];
+    tf[(size_t)z * nsticks + s0 + s] = to_g(line[s * n3 + z]);
   }
 }
 
 // ---------------------------------------------------------------------------
 // pass B: one plane of one field: 2D inverse FFT, x V/Ng, 2D forward FFT
 // ---------------------------------------------------------------------------
-template <typename V>
-__global__ void __launch_bounds__(512) k_plane(V* __restrict__ t, int nsticks,
+template <typename Vg, typename V>
+__global__ void __launch_bounds__(512) k_plane(Vg* __restrict__ t, int nsticks,
                                                const int* __restrict__ stick_plane, AxisPlan p1,
                                                AxisPlan p2, int n3, const V* __restrict__ tw1,
                                                const V* __restrict__ tw2,
@@ -150,10 +154,10 @@ __global__ void __launch_bounds__(512) k_plane(V* __restrict__ t, int nsticks,
   V* plane = reinterpret_cast<V*>(smem_raw);
   const int n1 = p1.n, n2 = p2.n, nn = n1 * n2;
   const int z = blockIdx.x, f = blockIdx.y;
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) plane[e] = V{0, 0};
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) plane[e] = vzero<V>();
   __syncthreads();
-  V* row = t + ((size_t)f * n3 + z) * nsticks;
-  for (int s = threadIdx.x; s < nsticks; s += blockDim.x) plane[stick_plane[s]] = row[s];
+  Vg* row = t + ((size_t)f * n3 + z) * nsticks;
+  for (int s = threadIdx.x; s < nsticks; s += blockDim.x) plane[stick_plane[s]] = to_s<V>(row[s]);
   __syncthreads();
   fft_lines<V, false>(plane, n1, n2, 1, p2, tw2, false);   // along axis 2 (contiguous)
   fft_lines<V, false>(plane, n2, 1, n2, p1, tw1, false);   // along axis 1
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(512) k_plane(V* __restrict__ t, int nsticks,
   __syncthreads();
   fft_lines<V, true>(plane, n2, 1, n2, p1, tw1, true);
   fft_lines<V, true>(plane, n1, n2, 1, p2, tw2, true);
-  for (int s = threadIdx.x; s < nsticks; s += blockDim.x) row[s] = plane[stick_plane[s]];
+  for (int s = threadIdx.x; s < nsticks; s += blockDim.x) row[s] = to_g(plane[stick_plane[s]]);
 }
 
 // ---------------------------------------------------------------------------
@@ -186,9 +190,9 @@ __device__ __forceinline__ void dirac4(const double2 xv[4], double qx, double qy
           a.y - cz * xv[1].y + (diag_small - shift) * xv[3].y};
 }
 
-template <typename V>
+template <typename Vg, typename V>
 __global__ void __launch_bounds__(256) k_stick_forward(
-    const V* __restrict__ t, const V* __restrict__ x, V* __restrict__ out, int npw, int nsticks,
+    const Vg* __restrict__ t, const Vg* __restrict__ x, Vg* __restrict__ out, int npw, int nsticks,
     const int* __restrict__ stick_start, const int* __restrict__ pw_stick, const int* __restrict__ pw_iz,
     AxisPlan p3, const V* __restrict__ tw3, const double* __restrict__ q, double c, double shift,
     double scale, int spb) {
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(256) k_stick_forward(
     const int a = e / (ns * n3);
     const int rem = e - a * ns * n3;
     const int z = rem / ns, s = rem - z * ns;
-    line[(a * spb + s) * n3 + z] = t[((size_t)(b * 4 + a) * n3 + z) * nsticks + s0 + s];
+    line[(a * spb + s) * n3 + z] = to_s<V>(t[((size_t)(b * 4 + a) * n3 + z) * nsticks + s0 + s]);
   }
   __syncthreads();
   fft_lines<V, true>(line, 4 * spb, n3, 1, p3, tw3, true);
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(256) k_stick_forward(
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const double2 loc = to_d2(line[(a * spb + s) * n3 + iz]);
-      out[fo + (size_t)a * npw + p] = from_d2<V>({scale * (h[a].x + loc.x), scale * (h[a].y + loc.y)});
+      out[fo + (size_t)a * npw + p] = from_d2<Vg>({scale * (h[a].x + loc.x), scale * (h[a].y + loc.y)});
     }
   }
 }
@@ -262,6 +266,62 @@ static int pick_spb(int n3, size_t elem, int lines_per_stick, size_t target) {
   return spb;
 }
 
+// The three FFT passes over chunks of bands.  Vg is the storage type (global memory), Vs the
+// arithmetic type of the transforms in shared memory: the same type, or double-float (cdf) for
+// complex128 data in the emulated-FP64 mode.
+template <typename Vg, typename Vs>
+static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int nb, int chunk, Vg* tbuf,
+                     double shift, double scale, cudaStream_t st) {
+  const bool fp64 = sizeof(Vg) == sizeof(double2);
+  const bool df = !std::is_same<Vg, Vs>::value;
+  const int npw = kp.npw, n3 = ctx->grid[2];
+  const size_t field_elems = (size_t)kp.nsticks * n3;
+  const Vs* tw1 = df ? (const Vs*)ctx->twdf[0] : fp64 ? (const Vs*)ctx->tw64[0] : (const Vs*)ctx->tw32[0];
+  const Vs* tw2 = df ? (const Vs*)ctx->twdf[1] : fp64 ? (const Vs*)ctx->tw64[1] : (const Vs*)ctx->tw32[1];
+  const Vs* tw3 = df ? (const Vs*)ctx->twdf[2] : fp64 ? (const Vs*)ctx->tw64[2] : (const Vs*)ctx->tw32[2];
+  using VR = typename RealOf<Vs>::T;
+  const VR* vp = df ? (const VR*)ctx->vpermdf : fp64 ? (const VR*)ctx->vperm64 : (const VR*)ctx->vperm32;
+  const int spb_a = pick_spb(n3, sizeof(Vs), 1, 32 * 1024);
+  const int spb_c = pick_spb(n3, sizeof(Vs), 4, 64 * 1024);
+  const size_t sm_a = (size_t)spb_a * n3 * sizeof(Vs);
+  const size_t sm_b = (size_t)ctx->grid[0] * ctx->grid[1] * sizeof(Vs);
+  const size_t sm_c = (size_t)4 * spb_c * n3 * sizeof(Vs);
+  DKS_TRY(set_smem<Vs>((const void*)k_stick_inverse<Vg, Vs>, sm_a));
+  DKS_TRY(set_smem<Vs>((const void*)k_plane<Vg, Vs>, sm_b));
+  DKS_TRY(set_smem<Vs>((const void*)k_stick_forward<Vg, Vs>, sm_c));
+  const int cat32 = fp64 ? 0 : kProf32;
+  for (int b0 = 0; b0 < nb; b0 += chunk) {
+    const int nbc = std::min(chunk, nb - b0);
+    const Vg* xb = x + (size_t)b0 * 4 * npw;
+    const double nf = 4.0 * nbc, es = (double)sizeof(Vg);
+    const double tb = nf * (double)field_elems * es;          // one pass over the stick buffer
+    const double f3 = 5.0 * n3 * std::log2((double)n3) * kp.nsticks * nf;
+    {
+      Prof pr(P_STICK_INV + cat32, st, nf * npw * es + tb, f3);
+      dim3 ga((kp.nsticks + spb_a - 1) / spb_a, 4 * nbc);
+      k_stick_inverse<Vg, Vs><<<ga, 256, sm_a, st>>>(xb, tbuf, npw, kp.nsticks, kp.stick_start, kp.pw_stick,
+                                                     kp.pw_iz, ctx->plan[2], tw3, spb_a);
+    }
+    {
+      const double nn = (double)ctx->grid[0] * ctx->grid[1];
+      Prof pr(P_PLANE + cat32, st, 2.0 * tb + (double)ctx->ng * es / 2,
+              nf * n3 * (10.0 * nn * std::log2(nn) + 2.0 * nn));
+      dim3 gb(n3, 4 * nbc);
+      k_plane<Vg, Vs><<<gb, 512, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0], ctx->plan[1], n3,
+                                             tw1, tw2, vp);
+    }
+    {
+      Prof pr(P_STICK_FWD + cat32, st, tb + 2.0 * nf * npw * es + 24.0 * npw, f3 + 64.0 * nbc * npw);
+      dim3 gc((kp.nsticks + spb_c - 1) / spb_c, nbc);
+      k_stick_forward<Vg, Vs><<<gc, 256, sm_c, st>>>(tbuf, xb, out + (size_t)b0 * 4 * npw, npw, kp.nsticks,
+                                                     kp.stick_start, kp.pw_stick, kp.pw_iz, ctx->plan[2], tw3,
+                                                     kp.q, ctx->c, shift, scale, spb_c);
+    }
+  }
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
+}
+
 template <typename V>
 int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double shift, double scale,
             cudaStream_t st) {
@@ -291,48 +351,15 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
     else
       DKS_TRY(gemm_hn<V>(bt, 2 * npw, x, 2 * npw, 2 * npw, ctx->nproj, 2 * nb, zp, st, P_PROJ_HN));
   }
-  const V* tw1 = fp64 ? (const V*)ctx->tw64[0] : (const V*)ctx->tw32[0];
-  const V* tw2 = fp64 ? (const V*)ctx->tw64[1] : (const V*)ctx->tw32[1];
-  const V* tw3 = fp64 ? (const V*)ctx->tw64[2] : (const V*)ctx->tw32[2];
   if (ctx->has_v) {
-    const int spb_a = pick_spb(n3, sizeof(V), 1, 32 * 1024);
-    const int spb_c = pick_spb(n3, sizeof(V), 4, 64 * 1024);
-    const size_t sm_a = (size_t)spb_a * n3 * sizeof(V);
-    const size_t sm_b = (size_t)ctx->grid[0] * ctx->grid[1] * sizeof(V);
-    const size_t sm_c = (size_t)4 * spb_c * n3 * sizeof(V);
-    DKS_TRY(set_smem<V>((const void*)k_stick_inverse<V>, sm_a));
-    DKS_TRY(set_smem<V>((const void*)k_plane<V>, sm_b));
-    DKS_TRY(set_smem<V>((const void*)k_stick_forward<V>, sm_c));
-    const typename RealOf<V>::T* vp =
-        fp64 ? (const typename RealOf<V>::T*)ctx->vperm64 : (const typename RealOf<V>::T*)ctx->vperm32;
-    for (int b0 = 0; b0 < nb; b0 += chunk) {
-      const int nbc = std::min(chunk, nb - b0);
-      const V* xb = x + (size_t)b0 * 4 * npw;
-      const double nf = 4.0 * nbc, es = (double)sizeof(V);
-      const double tb = nf * (double)field_elems * es;          // one pass over the stick buffer
-      const double f3 = 5.0 * n3 * std::log2((double)n3) * kp.nsticks * nf;
-      {
-        Prof pr(P_STICK_INV + (fp64 ? 0 : kProf32), st, nf * npw * es + tb, f3);
-        dim3 ga((kp.nsticks + spb_a - 1) / spb_a, 4 * nbc);
-        k_stick_inverse<V><<<ga, 256, sm_a, st>>>(xb, tbuf, npw, kp.nsticks, kp.stick_start, kp.pw_stick,
-                                                  kp.pw_iz, ctx->plan[2], tw3, spb_a);
-      }
-      {
-        const double nn = (double)ctx->grid[0] * ctx->grid[1];
-        Prof pr(P_PLANE + (fp64 ? 0 : kProf32), st, 2.0 * tb + (double)ctx->ng * es / 2,
-                nf * n3 * (10.0 * nn * std::log2(nn) + 2.0 * nn));
-        dim3 gb(n3, 4 * nbc);
-        k_plane<V><<<gb, 512, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0], ctx->plan[1], n3,
-                                          tw1, tw2, vp);
-      }
-      {
-        Prof pr(P_STICK_FWD + (fp64 ? 0 : kProf32), st, tb + 2.0 * nf * npw * es + 24.0 * npw, f3 + 64.0 * nbc * npw);
-        dim3 gc((kp.nsticks + spb_c - 1) / spb_c, nbc);
-        k_stick_forward<V><<<gc, 256, sm_c, st>>>(tbuf, xb, out + (size_t)b0 * 4 * npw, npw, kp.nsticks,
-                                                  kp.stick_start, kp.pw_stick, kp.pw_iz, ctx->plan[2], tw3,
-                                                  kp.q, ctx->c, shift, scale, spb_c);
+    bool done = false;
+    if constexpr (std::is_same<V, double2>::value) {
+      if (ex.df_gemm) {
+        DKS_TRY((fft_local<double2, cdf>(ctx, kp, x, out, nb, chunk, tbuf, shift, scale, st)));
+        done = true;
       }
     }
+    if (!done) DKS_TRY((fft_local<V, V>(ctx, kp, x, out, nb, chunk, tbuf, shift, scale, st)));
   } else {
     const int blocks = std::max(1, std::min(ctx->num_sms * 8, (int)(((size_t)nb * npw + 255) / 256)));
     Prof pr(P_DIRAC + (fp64 ? 0 : kProf32), st, 8.0 * nb * npw * sizeof(V) + 24.0 * npw, 64.0 * nb * npw);
