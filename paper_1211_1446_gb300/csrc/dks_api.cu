@@ -48,20 +48,32 @@ void release(Workspace& w) {
   w.bytes = 0;
 }
 
+// fewest passes over the radices {8, 7, 6, 5, 4, 3, 2}; among equal counts the larger radix first
+static int plan_passes(int n, int* best_first) {
+  if (n == 1) return 0;
+  const int radices[] = {8, 7, 6, 5, 4, 3, 2};
+  int best = 1 << 20;
+  *best_first = 0;
+  for (int r : radices) {
+    if (n % r) continue;
+    int dummy = 0;
+    const int c = 1 + plan_passes(n / r, &dummy);
+    if (c < best) {
+      best = c;
+      *best_first = r;
+    }
+  }
+  return best;
+}
+
 bool make_axis_plan(int n, AxisPlan* p) {
   if (n < 1 || n > kMaxFftLen) return false;
   p->n = n;
   p->nst = 0;
   int rest = n, len = n;
-  const int order[] = {8, 7, 5, 4, 3, 2};
   while (rest > 1) {
     int r = 0;
-    for (int c : order)
-      if (rest % c == 0) {
-        r = c;
-        break;
-      }
-    if (!r || p->nst >= kMaxStages) return false;
+    if (plan_passes(rest, &r) >= (1 << 20) || !r || p->nst >= kMaxStages) return false;
     p->radix[p->nst] = r;
     p->blk[p->nst] = len;
     ++p->nst;
@@ -186,7 +198,7 @@ static int build_k(dks_ctx* ctx, const double kfrac[3], double ecut, const dks_p
       sstart.push_back(p);
       const int i1 = ((mil[3 * p] % ctx->grid[0]) + ctx->grid[0]) % ctx->grid[0];
       const int i2 = ((mil[3 * p + 1] % ctx->grid[1]) + ctx->grid[1]) % ctx->grid[1];
-      splane.push_back(i1 * ctx->grid[1] + i2);
+      splane.push_back(i1 * ctx->plane_ld + i2);
     }
     pstick[p] = (int)sstart.size() - 1;
     piz[p] = ((mil[3 * p + 2] % ctx->grid[2]) + ctx->grid[2]) % ctx->grid[2];
@@ -322,7 +334,8 @@ int dks_create(const dks_cell* cell, double ecut, const dks_potentials* pot, con
       return bail(fail(DKS_ERR_UNSUPPORTED, "grid axis must be <= 256 with factors 2, 3, 5, 7"));
   }
   ctx->ng = ctx->grid[0] * ctx->grid[1] * ctx->grid[2];
-  if ((size_t)ctx->grid[0] * ctx->grid[1] * sizeof(double2) > 227 * 1024)
+  ctx->plane_ld = ctx->grid[1] | 1;
+  if ((size_t)ctx->grid[0] * ctx->plane_ld * sizeof(double2) > 227 * 1024)
     return bail(fail(DKS_ERR_UNSUPPORTED, "N1*N2 plane exceeds the shared-memory limit"));
   // reciprocal rows: b_i = 2 pi (A^-1)^T rows
   const double* A = ctx->lattice;
@@ -370,15 +383,17 @@ int dks_create(const dks_cell* cell, double ecut, const dks_potentials* pot, con
     const int n1 = ctx->grid[0], n2 = ctx->grid[1], n3 = ctx->grid[2];
     const std::vector<int> p1 = dif_positions(ctx->plan[0]), p2 = dif_positions(ctx->plan[1]),
                            p3 = dif_positions(ctx->plan[2]);
-    std::vector<double> vp((size_t)ctx->ng);
-    std::vector<float> vp32((size_t)ctx->ng);
-    std::vector<float2> vpdf((size_t)ctx->ng);
+    const int ld = ctx->plane_ld;
+    const size_t nvp = (size_t)n3 * n1 * ld;
+    std::vector<double> vp(nvp, 0.0);
+    std::vector<float> vp32(nvp, 0.0f);
+    std::vector<float2> vpdf(nvp, float2{0.0f, 0.0f});
     for (int i1 = 0; i1 < n1; ++i1)
       for (int i2 = 0; i2 < n2; ++i2)
         for (int i3 = 0; i3 < n3; ++i3) {
           const double v = pot->v_r[((size_t)i1 * n2 + i2) * n3 + i3];
           ctx->vmax = std::max(ctx->vmax, std::fabs(v));
-          const size_t at = (size_t)p3[i3] * n1 * n2 + (size_t)p1[i1] * n2 + p2[i2];
+          const size_t at = ((size_t)p3[i3] * n1 + p1[i1]) * ld + p2[i2];
           vp[at] = v / ctx->ng;
           vp32[at] = (float)(v / ctx->ng);
           const float h = (float)vp[at];

@@ -55,7 +55,7 @@ struct KPoint {
   std::vector<int> miller;      // host npw*3, canonical order
   // device tables
   int* stick_start = nullptr;   // nsticks+1, pw offsets
-  int* stick_plane = nullptr;   // nsticks, i1*N2 + i2 (natural frequency position)
+  int* stick_plane = nullptr;   // nsticks, i1*LD + i2 (natural frequency position, padded rows)
   int* pw_stick = nullptr;      // npw
   int* pw_iz = nullptr;         // npw, i3 (natural)
   double* q = nullptr;          // npw*3 cartesian k+G (FP64)
@@ -90,11 +90,12 @@ struct dks_ctx {
   double volume = 0;
   int nk = 0;
   dks::AxisPlan plan[3];
+  int plane_ld = 0;              // row stride of an N1 x N2 plane in shared memory (N2 rounded up to odd)
   // device: twiddles exp(+2 pi i t / N_axis), t < N_axis
   double2* tw64[3] = {nullptr, nullptr, nullptr};
   float2* tw32[3] = {nullptr, nullptr, nullptr};
   float4* twdf[3] = {nullptr, nullptr, nullptr};   // double-float twiddles (re hi, re lo, im hi, im lo)
-  // device: V / Ng in DIF-permuted layout [p3][p1*N2 + p2]
+  // device: V / Ng in DIF-permuted layout [p3][p1*LD + p2], zero in the padding column
   double* vperm64 = nullptr;
   float* vperm32 = nullptr;
   float2* vpermdf = nullptr;    // double-float (hi, lo) copy
@@ -135,6 +136,15 @@ class Prof {
   cudaStream_t st_;
   long long idx_;
 };
+
+// Algorithmic real flops of one Rayleigh-Ritz step on an m x m Hermitian pencil for n Ritz
+// pairs (Cholesky m^3/6, two triangular solves m^3/2 each, Householder tridiagonalisation
+// 2m^3/3 complex multiply-adds; back-transformation m^2 n and the L^-H solve m^2 n / 2;
+// 8 real flops per complex multiply-add).  The tridiagonal eigensolver is O(m n) and omitted.
+inline double rr_flops(int m, int n) {
+  const double md = m, nd = n;
+  return 8.0 * (md * md * md * (1.0 / 6.0 + 1.0 + 2.0 / 3.0) + 1.5 * md * md * nd);
+}
 
 int grow(Workspace& w, size_t bytes);
 void release(Workspace& w);

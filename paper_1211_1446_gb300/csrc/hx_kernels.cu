@@ -32,85 +32,12 @@
 
 #include "dks_internal.h"
 #include "dks_kernels.cuh"
+#include "fft_device.cuh"
 
 namespace dks {
 
 template <typename V> __device__ __forceinline__ V vzero() { return V{0, 0}; }
 template <> __device__ __forceinline__ cdf vzero<cdf>() { return cdf{{0.f, 0.f}, {0.f, 0.f}}; }
-
-// ---------------------------------------------------------------------------
-// one radix-R pass over a batch of lines held in shared memory (in place)
-// ---------------------------------------------------------------------------
-template <typename V, int R, bool DIT>
-__device__ __forceinline__ void fft_pass(V* buf, int nlines, int lstride, int estride, int n,
-                                         int L, const V* __restrict__ tw, bool fwd) {
-  const int S = L / R;
-  const int per_line = n / R;
-  const int total = nlines * per_line;
-  const int tstep = n / L;
-  const int rstep = n / R;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int line = t / per_line;
-    const int u = t - line * per_line;
-    const int blk = u / S;
-    const int j = u - blk * S;
-    V* base = buf + line * lstride + (blk * L + j) * estride;
-    V x[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = base[r * S * estride];
-    if (DIT) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle(tw, j * r * tstep, fwd));
-    }
-    V y[R];
-    if (R == 2) {
-      y[0] = cadd(x[0], x[1]);
-      y[1] = csub(x[0], x[1]);
-    } else if (R == 4) {
-      // w4 = +i (inverse) or -i (forward)
-      V a = cadd(x[0], x[2]), b = csub(x[0], x[2]);
-      V c = cadd(x[1], x[3]), d = csub(x[1], x[3]);
-      V di = fwd ? mul_mi(d) : mul_i(d);
-      y[0] = cadd(a, c);
-      y[2] = csub(a, c);
-      y[1] = cadd(b, di);
-      y[3] = csub(b, di);
-    } else {
-#pragma unroll
-      for (int m = 0; m < R; ++m) {
-        V acc = x[0];
-#pragma unroll
-        for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(x[r], twiddle(tw, ((r * m) % R) * rstep, fwd)));
-        y[m] = acc;
-      }
-    }
-    if (!DIT) {
-#pragma unroll
-      for (int m = 1; m < R; ++m) y[m] = cmul(y[m], twiddle(tw, j * m * tstep, fwd));
-    }
-#pragma unroll
-    for (int m = 0; m < R; ++m) base[m * S * estride] = y[m];
-  }
-}
-
-template <typename V, bool DIT>
-__device__ void fft_lines(V* buf, int nlines, int lstride, int estride, const AxisPlan& p,
-                          const V* __restrict__ tw, bool fwd) {
-  for (int i = 0; i < p.nst; ++i) {
-    const int s = DIT ? (p.nst - 1 - i) : i;
-    const int R = p.radix[s];
-    const int L = p.blk[s];
-    switch (R) {
-      case 2: fft_pass<V, 2, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
-      case 3: fft_pass<V, 3, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
-      case 4: fft_pass<V, 4, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
-      case 5: fft_pass<V, 5, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
-      case 7: fft_pass<V, 7, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
-      default: fft_pass<V, 8, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
-    }
-    __syncthreads();
-  }
-}
 
 // ---------------------------------------------------------------------------
 // pass A: sphere -> stick lines, inverse FFT along axis 3
@@ -119,25 +46,26 @@ template <typename Vg, typename V>
 __global__ void __launch_bounds__(256) k_stick_inverse(
     const Vg* __restrict__ x, Vg* __restrict__ t, int npw, int nsticks, const int* __restrict__ stick_start,
     const int* __restrict__ pw_stick, const int* __restrict__ pw_iz, AxisPlan p3,
-    const V* __restrict__ tw3, int spb) {
+    const V* __restrict__ tw3, int spb, int ls) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* line = reinterpret_cast<V*>(smem_raw);
+  V* line = reinterpret_cast<V*>(smem_raw);   // spb lines of stride ls (odd)
   const int n3 = p3.n;
   const int s0 = blockIdx.x * spb;
   const int ns = min(spb, nsticks - s0);
   const int f = blockIdx.y;
-  for (int e = threadIdx.x; e < spb * n3; e += blockDim.x) line[e] = vzero<V>();
+  for (int e = threadIdx.x; e < spb * ls; e += blockDim.x) line[e] = vzero<V>();
   __syncthreads();
   const Vg* xf = x + (size_t)f * npw;
   const int q0 = stick_start[s0], q1 = stick_start[s0 + ns];
   for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x)
-    line[(pw_stick[q] - s0) * n3 + pw_iz[q]] = to_s<V>(xf[q]);
+    line[(pw_stick[q] - s0) * ls + pw_iz[q]] = to_s<V>(xf[q]);
   __syncthreads();
-  fft_lines<V, false>(line, ns, n3, 1, p3, tw3, false);
+  fft_lines<V, false>(line, ns, ls, 1, p3, tw3, false);
   Vg* tf = t + (size_t)f * n3 * nsticks;
+  const float rns = __fdividef(1.0f, (float)ns);
   for (int e = threadIdx.x; e < ns * n3; e += blockDim.x) {
-    const int z = e / ns, s = e - z * ns;
-    tf[(size_t)z * nsticks + s0 + s] = to_g(line[s * n3 + z]);
+    const int z = qdiv(e, ns, rns), s = e - z * ns;
+    tf[(size_t)z * nsticks + s0 + s] = to_g(line[s * ls + z]);
   }
 }
 
@@ -147,25 +75,25 @@ __global__ void __launch_bounds__(256) k_stick_inverse(
 template <typename Vg, typename V>
 __global__ void __launch_bounds__(512) k_plane(Vg* __restrict__ t, int nsticks,
                                                const int* __restrict__ stick_plane, AxisPlan p1,
-                                               AxisPlan p2, int n3, const V* __restrict__ tw1,
+                                               AxisPlan p2, int ld, int n3, const V* __restrict__ tw1,
                                                const V* __restrict__ tw2,
                                                const typename RealOf<V>::T* __restrict__ vperm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* plane = reinterpret_cast<V*>(smem_raw);
-  const int n1 = p1.n, n2 = p2.n, nn = n1 * n2;
+  V* plane = reinterpret_cast<V*>(smem_raw);   // n1 rows of stride ld (odd), position i1*ld + i2
+  const int n1 = p1.n, n2 = p2.n, np = n1 * ld;
   const int z = blockIdx.x, f = blockIdx.y;
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) plane[e] = vzero<V>();
+  for (int e = threadIdx.x; e < np; e += blockDim.x) plane[e] = vzero<V>();
   __syncthreads();
   Vg* row = t + ((size_t)f * n3 + z) * nsticks;
   for (int s = threadIdx.x; s < nsticks; s += blockDim.x) plane[stick_plane[s]] = to_s<V>(row[s]);
   __syncthreads();
-  fft_lines<V, false>(plane, n1, n2, 1, p2, tw2, false);   // along axis 2 (contiguous)
-  fft_lines<V, false>(plane, n2, 1, n2, p1, tw1, false);   // along axis 1
-  const typename RealOf<V>::T* vz = vperm + (size_t)z * nn;
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) plane[e] = cscale(plane[e], vz[e]);
+  fft_lines<V, false>(plane, n1, ld, 1, p2, tw2, false);   // along axis 2 (contiguous)
+  fft_lines<V, false>(plane, n2, 1, ld, p1, tw1, false);   // along axis 1
+  const typename RealOf<V>::T* vz = vperm + (size_t)z * np;   // zero in the padding column
+  for (int e = threadIdx.x; e < np; e += blockDim.x) plane[e] = cscale(plane[e], vz[e]);
   __syncthreads();
-  fft_lines<V, true>(plane, n2, 1, n2, p1, tw1, true);
-  fft_lines<V, true>(plane, n1, n2, 1, p2, tw2, true);
+  fft_lines<V, true>(plane, n2, 1, ld, p1, tw1, true);
+  fft_lines<V, true>(plane, n1, ld, 1, p2, tw2, true);
   for (int s = threadIdx.x; s < nsticks; s += blockDim.x) row[s] = to_g(plane[stick_plane[s]]);
 }
 
@@ -195,21 +123,23 @@ __global__ void __launch_bounds__(256) k_stick_forward(
     const Vg* __restrict__ t, const Vg* __restrict__ x, Vg* __restrict__ out, int npw, int nsticks,
     const int* __restrict__ stick_start, const int* __restrict__ pw_stick, const int* __restrict__ pw_iz,
     AxisPlan p3, const V* __restrict__ tw3, const double* __restrict__ q, double c, double shift,
-    double scale, int spb) {
+    double scale, int spb, int ls) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* line = reinterpret_cast<V*>(smem_raw);
+  V* line = reinterpret_cast<V*>(smem_raw);   // 4*spb lines of stride ls (odd)
   const int n3 = p3.n;
   const int s0 = blockIdx.x * spb;
   const int ns = min(spb, nsticks - s0);
   const int b = blockIdx.y;
-  for (int e = threadIdx.x; e < 4 * ns * n3; e += blockDim.x) {
-    const int a = e / (ns * n3);
-    const int rem = e - a * ns * n3;
-    const int z = rem / ns, s = rem - z * ns;
-    line[(a * spb + s) * n3 + z] = to_s<V>(t[((size_t)(b * 4 + a) * n3 + z) * nsticks + s0 + s]);
+  const float rns = __fdividef(1.0f, (float)ns);
+  for (int a = 0; a < 4; ++a) {
+    const Vg* ta = t + (size_t)(b * 4 + a) * n3 * nsticks + s0;
+    for (int e = threadIdx.x; e < ns * n3; e += blockDim.x) {
+      const int z = qdiv(e, ns, rns), s = e - z * ns;
+      line[(a * spb + s) * ls + z] = to_s<V>(ta[(size_t)z * nsticks + s]);
+    }
   }
   __syncthreads();
-  fft_lines<V, true>(line, 4 * spb, n3, 1, p3, tw3, true);
+  fft_lines<V, true>(line, 4 * spb, ls, 1, p3, tw3, true);
   const size_t fo = (size_t)b * 4 * npw;
   const int q0 = stick_start[s0], q1 = stick_start[s0 + ns];
   const double diag_small = -2.0 * c * c;
@@ -221,7 +151,7 @@ __global__ void __launch_bounds__(256) k_stick_forward(
     dirac4(xv, q[3 * p], q[3 * p + 1], q[3 * p + 2], c, diag_small, shift, h);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const double2 loc = to_d2(line[(a * spb + s) * n3 + iz]);
+      const double2 loc = to_d2(line[(a * spb + s) * ls + iz]);
       out[fo + (size_t)a * npw + p] = from_d2<Vg>({scale * (h[a].x + loc.x), scale * (h[a].y + loc.y)});
     }
   }
@@ -281,11 +211,19 @@ static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int n
   const Vs* tw3 = df ? (const Vs*)ctx->twdf[2] : fp64 ? (const Vs*)ctx->tw64[2] : (const Vs*)ctx->tw32[2];
   using VR = typename RealOf<Vs>::T;
   const VR* vp = df ? (const VR*)ctx->vpermdf : fp64 ? (const VR*)ctx->vperm64 : (const VR*)ctx->vperm32;
-  const int spb_a = pick_spb(n3, sizeof(Vs), 1, 32 * 1024);
-  const int spb_c = pick_spb(n3, sizeof(Vs), 4, 64 * 1024);
-  const size_t sm_a = (size_t)spb_a * n3 * sizeof(Vs);
-  const size_t sm_b = (size_t)ctx->grid[0] * ctx->grid[1] * sizeof(Vs);
-  const size_t sm_c = (size_t)4 * spb_c * n3 * sizeof(Vs);
+  const int ls = n3 | 1;                      // odd line stride: conflict-free shared memory
+  const int ld = ctx->plane_ld;
+  const int spb_a = pick_spb(ls, sizeof(Vs), 1, 32 * 1024);
+  const int spb_c = pick_spb(ls, sizeof(Vs), 4, 64 * 1024);
+  const size_t sm_a = (size_t)spb_a * ls * sizeof(Vs);
+  const size_t sm_b = (size_t)ctx->grid[0] * ld * sizeof(Vs);
+  const size_t sm_c = (size_t)4 * spb_c * ls * sizeof(Vs);
+  // threads of the plane kernel: the largest pass has N1 N2 / (smallest radix) butterflies
+  int rmin = 8;
+  for (int a = 0; a < 2; ++a)
+    for (int i = 0; i < ctx->plan[a].nst; ++i) rmin = std::min(rmin, ctx->plan[a].radix[i]);
+  const int nbf = ctx->grid[0] * ctx->grid[1] / rmin;
+  const int tb_plane = std::min(512, std::max(128, (nbf + 31) / 32 * 32));
   DKS_TRY(set_smem<Vs>((const void*)k_stick_inverse<Vg, Vs>, sm_a));
   DKS_TRY(set_smem<Vs>((const void*)k_plane<Vg, Vs>, sm_b));
   DKS_TRY(set_smem<Vs>((const void*)k_stick_forward<Vg, Vs>, sm_c));
@@ -300,22 +238,22 @@ static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int n
       Prof pr(P_STICK_INV + cat32, st, nf * npw * es + tb, f3);
       dim3 ga((kp.nsticks + spb_a - 1) / spb_a, 4 * nbc);
       k_stick_inverse<Vg, Vs><<<ga, 256, sm_a, st>>>(xb, tbuf, npw, kp.nsticks, kp.stick_start, kp.pw_stick,
-                                                     kp.pw_iz, ctx->plan[2], tw3, spb_a);
+                                                     kp.pw_iz, ctx->plan[2], tw3, spb_a, ls);
     }
     {
       const double nn = (double)ctx->grid[0] * ctx->grid[1];
       Prof pr(P_PLANE + cat32, st, 2.0 * tb + (double)ctx->ng * es / 2,
               nf * n3 * (10.0 * nn * std::log2(nn) + 2.0 * nn));
       dim3 gb(n3, 4 * nbc);
-      k_plane<Vg, Vs><<<gb, 512, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0], ctx->plan[1], n3,
-                                             tw1, tw2, vp);
+      k_plane<Vg, Vs><<<gb, tb_plane, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0], ctx->plan[1],
+                                                  ld, n3, tw1, tw2, vp);
     }
     {
       Prof pr(P_STICK_FWD + cat32, st, tb + 2.0 * nf * npw * es + 24.0 * npw, f3 + 64.0 * nbc * npw);
       dim3 gc((kp.nsticks + spb_c - 1) / spb_c, nbc);
       k_stick_forward<Vg, Vs><<<gc, 256, sm_c, st>>>(tbuf, xb, out + (size_t)b0 * 4 * npw, npw, kp.nsticks,
                                                      kp.stick_start, kp.pw_stick, kp.pw_iz, ctx->plan[2], tw3,
-                                                     kp.q, ctx->c, shift, scale, spb_c);
+                                                     kp.q, ctx->c, shift, scale, spb_c, ls);
     }
   }
   DKS_CUDA_TRY(cudaGetLastError());

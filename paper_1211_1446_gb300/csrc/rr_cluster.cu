@@ -586,7 +586,7 @@ int rayleigh_ritz_cluster(const double2* a, const double2* s, int nz, int n, dou
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    Prof pr(P_RR, st, 2.0 * nz * nz * 16.0 + 16.0 * nz * n, 0.0);
+    Prof pr(P_RR, st, 2.0 * nz * nz * 16.0 + 16.0 * nz * n, rr_flops(nz, n));
     const cudaError_t e = cudaLaunchKernelEx(&cfg, k_rr_cluster, a, s, nz, n, v, lam, info, scratch, chol_tol);
     if (e == cudaSuccess) {
       g_cluster = csz;

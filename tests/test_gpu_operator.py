@@ -20,6 +20,8 @@ CASES = [
     ("small", {"kfrac": [[0.25, -0.125, 0.5]]}),          # general k
     ("dimer", {"ecut": 4.0}),                             # full 48x48x56 grid, reduced sphere
     ("cubic", {"potential": False}),                      # free Dirac term alone
+    ("small", {"grid": (20, 21, 14)}),                    # radices 5x4, 7x3, 7x2; odd plane row length
+    ("cubic", {"grid": (16, 12, 27)}),                    # radices 8x2, 6x2, 3x3x3
 ]
 
 
@@ -65,10 +67,11 @@ def test_apply_h_full_dimer():
         assert rel_err(hx.cpu().numpy(), ref) < tol
 
 
-def test_apply_h_double_float_projectors():
-    """complex128 H' with the projector contractions in double-float arithmetic."""
+@pytest.mark.parametrize("name,kw", [("dimer", {"ecut": 4.0}), CASES[5], CASES[6]])
+def test_apply_h_double_float(name, kw):
+    """complex128 H' with the FFTs and projector contractions in double-float arithmetic."""
     torch = gpu()
-    wl, ctx, hop, q = make_pair("dimer", ecut=4.0)
+    wl, ctx, hop, q = make_pair(name, **kw)
     x = W.random_block(len(q), 5, 31)
     ref = hop(x)
     xd = to_dev(x, torch.complex128)
