@@ -3,18 +3,22 @@
 // FP64 throughput on GB300 is about two FMAs per clock per SM, so the O(m^3) work of the
 // small pencil is spread over the SMs of one cluster (16 CTAs when the device allows
 // non-portable clusters, else 8).  Matrices stay in a global scratch area (L2-resident);
-// the cluster barrier (release/acquire at cluster scope) orders the dependent steps.
+// the cluster barrier (release/acquire at cluster scope) orders the dependent steps.  Serial
+// chains read their operands from shared memory: blocks of L and of the reflectors are staged
+// there, since every dependent global load after a cluster barrier costs an L2 round trip.
 //
 //  1. A' = D A D, S' = D S D, D = diag(S)^-1/2                     (element-parallel)
 //  2. S' = L L^H, right-looking, one barrier per column; if a pivot^2 falls below
 //     chol_tol the kernel records it and returns -- the single-CTA kernel then runs
 //     the SVQB path
-//  3. W = L^-1 A' and C = L^-1 W^H = L^-1 A' L^-H                  (warp per column)
+//  3. W = L^-1 A' and C = L^-1 W^H = L^-1 A' L^-H: column-oriented forward substitution,
+//     warp per right-hand side, no reductions
 //  4. Householder reduction of C to a complex tridiagonal: every warp recomputes the
 //     column norm and reflector itself (no barrier), rows of p = tau C v are split over
 //     the warps, then the rank-2 update; two barriers per column
-//  5. real tridiagonal by a diagonal phase; the n lowest eigenvalues by 32-way
-//     multisection of the Sturm count (warp per eigenvalue)
+//  5. real tridiagonal by a diagonal phase; the n lowest eigenvalues by 33-way
+//     multisection of the Sturm count (warp per eigenvalue): FP32 counts, then
+//     double-float counts
 //  6. eigenvectors by inverse iteration on the tridiagonal (LU with partial pivoting in
 //     shared memory, one lane per vector); vectors of a cluster of close eigenvalues are
 //     computed by one lane in turn and orthogonalised against each other
@@ -89,29 +93,45 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// number of eigenvalues of the real symmetric tridiagonal (d, e) below x (Sturm count)
-__device__ int sturm_count(const double* d, const double* e2, int m, double x, double pivmin) {
-  int cnt = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  cnt += q < 0;
-  for (int j = 1; j < m; ++j) {
-    q = d[j] - x - e2[j - 1] * nr_rcp(q);
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += q < 0;
-  }
-  return cnt;
-}
-
+// number of eigenvalues of the real symmetric tridiagonal (d, e) below x (Sturm count): the
+// negative pivots of the LDL^T factorisation of T - x I, each pivot kept away from zero
 __device__ int sturm_count_f(const float* d, const float* e2, int m, float x, float pivmin) {
   int cnt = 0;
   float q = d[0] - x;
   if (fabsf(q) < pivmin) q = -pivmin;
   cnt += q < 0.f;
   for (int j = 1; j < m; ++j) {
-    q = d[j] - x - e2[j - 1] / q;
+    q = d[j] - x - __fdividef(e2[j - 1], q);
     if (fabsf(q) < pivmin) q = -pivmin;
     cnt += q < 0.f;
+  }
+  return cnt;
+}
+
+// a / b in double-float: quotient of the leading parts, one correction from the exact
+// remainder a - q1 b (Dekker)
+__device__ __forceinline__ dfl df_div(dfl a, dfl b) {
+  const float rb = __frcp_rn(b.h);
+  const float q1 = a.h * rb;
+  const float p = q1 * b.h;
+  const float pe = fmaf(q1, b.h, -p);
+  const float r = ((a.h - p) - pe) + (a.l - q1 * b.l);
+  const float q2 = r * rb;
+  const float h = q1 + q2;
+  return dfl{h, q2 - (h - q1)};
+}
+
+// Sturm count in double-float arithmetic (same recurrence as above)
+__device__ int sturm_count_df(const dfl* d, const dfl* e2, int m, dfl x, float pivmin) {
+  const dfl nx = df_neg(x);
+  int cnt = 0;
+  dfl q = df_add(d[0], nx);
+  if (fabsf(q.h) < pivmin) q = dfl{-pivmin, 0.f};
+  cnt += q.h < 0.f;
+  for (int j = 1; j < m; ++j) {
+    q = df_add(df_add(d[j], nx), df_neg(df_div(e2[j - 1], q)));
+    if (fabsf(q.h) < pivmin) q = dfl{-pivmin, 0.f};
+    cnt += q.h < 0.f;
   }
   return cnt;
 }
@@ -189,20 +209,27 @@ __device__ void tri_solve(int m, const double* f, double* x) {
   for (int i = m - 3; i >= 0; --i) x[i] = (x[i] - u1[i] * x[i + 1] - u2[i] * x[i + 2]) * u0[i];
 }
 
-// shared memory: per-warp complex vectors (or inverse-iteration slots), then the tridiagonal
+// shared memory: per-warp complex vectors (or inverse-iteration slots), the tridiagonal
+// (FP64, FP32 and double-float copies), then a staging area for blocks of L / reflector columns
+// and per-index scalars (1/L_ii, tau, D, the diagonal phases)
 __host__ __device__ inline size_t rr_tri_smem_offset(int m) {
   const size_t vec = (size_t)RRC_WARPS * m * sizeof(double2);
   return vec > 48 * 1024 ? vec : 48 * 1024;
 }
-__host__ __device__ inline size_t rr_cluster_smem(int m) {
-  return rr_tri_smem_offset(m) + (size_t)m * (3 * sizeof(double) + 2 * sizeof(float)) + 64;
+__host__ __device__ inline size_t rr_stage_offset(int m) {
+  const size_t tri = rr_tri_smem_offset(m) + (size_t)m * (3 * sizeof(double) + 2 * sizeof(float) + 2 * sizeof(dfl)) + 64;
+  return (tri + 15) / 16 * 16;
 }
+__host__ __device__ inline size_t rr_cluster_smem(int m, int scols) {
+  return rr_stage_offset(m) + (size_t)scols * m * sizeof(double2) + (size_t)m * (3 * sizeof(double) + sizeof(double2));
+}
+constexpr size_t kRrSmemMax = 200 * 1024;
 
-__global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __restrict__ A,
+__global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __restrict__ A,
                                                             const double2* __restrict__ S, int m, int n,
                                                             double2* __restrict__ V, double* __restrict__ lam,
                                                             int* __restrict__ info, double2* __restrict__ scr,
-                                                            double chol_tol) {
+                                                            double chol_tol, int scols) {
   extern __shared__ __align__(16) unsigned char rrc_smem[];
   cg::cluster_group cl = cg::this_cluster();
   const int crank = (int)cl.block_rank(), csize = (int)cl.num_blocks();
@@ -231,11 +258,23 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
   int* flag = reinterpret_cast<int*>(pv + m);
   double* zt = reinterpret_cast<double*>(lm);   // m x n real eigenvectors of T (after Cholesky)
 
-  // 1. scaling
-  for (int i = gtid; i < m; i += gnt) dsc[i] = 1.0 / sqrt(fmax(S[(size_t)i * m + i].x, 1e-300));
+  // staging area and per-index scalars in shared memory
+  double2* stg = reinterpret_cast<double2*>(rrc_smem + rr_stage_offset(m));   // scols x m
+  double2* sph = stg + (size_t)scols * m;              // complex arrays first: 16-byte aligned
+  double* slinv = reinterpret_cast<double*>(sph + m);
+  double* stau = slinv + m;
+  double* sdsc = stau + m;
+
+  // 1. scaling (every CTA keeps D in shared memory)
+  for (int i = tid; i < m; i += RRC_THREADS) {
+    const double di = nr_rsqrt(fmax(S[(size_t)i * m + i].x, 1e-300));
+    sdsc[i] = di;
+    if (crank == 0) dsc[i] = di;
+  }
+  __syncthreads();
   for (size_t e = gtid; e < mm; e += gnt) {
     const int i = (int)(e % m), j = (int)(e / m);
-    const double s = (1.0 / sqrt(fmax(S[(size_t)i * m + i].x, 1e-300))) * (1.0 / sqrt(fmax(S[(size_t)j * m + j].x, 1e-300)));
+    const double s = sdsc[i] * sdsc[j];
     const double2 a = A[e], at = A[(size_t)i * m + j];
     am[e] = double2{0.5 * s * (a.x + at.x), 0.5 * s * (a.y - at.y)};
     const double2 b = S[e], bt = S[(size_t)i * m + j];
@@ -279,39 +318,55 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
   cl.sync();
   RR_MARK(1);
   double2* wvec = reinterpret_cast<double2*>(rrc_smem) + (size_t)wl * m;   // per-warp vector
-  // 3a. W = L^-1 A'  (column c of A' -> column c of W, stored in cm)
-  for (int c = gw; c < m; c += gnw) {
-    for (int i = 0; i < m; ++i) {
-      double2 s{0, 0};
-      for (int k = lane; k < i; k += 32) s = cadd(s, cmul(lt[(size_t)i * m + k], wvec[k]));
-      s = warp_csum(s);
-      const double li = linv[i];
-      const double2 a = am[(size_t)c * m + i];
-      const double2 w = double2{(a.x - s.x) * li, (a.y - s.y) * li};
-      if (lane == 0) wvec[i] = w;
-      __syncwarp();
-    }
-    for (int i = lane; i < m; i += 32) cm[(size_t)c * m + i] = wvec[i];
-    __syncwarp();
-  }
-  cl.sync();
-  // 3b. C = L^-1 W^H: right-hand side column c of W^H is conj(row c of W); result into lm (free)
+  for (int i = tid; i < m; i += RRC_THREADS) slinv[i] = linv[i];
+  // 3. two forward substitutions with L, column-oriented: lanes own rows k of the right-hand
+  // side b; at step i every lane forms w_i = b_i / L_ii from shared memory and updates its
+  // b_k -= L_ki w_i (k > i), so a step needs no reduction.  Columns of L come through the
+  // staging area in blocks; right-hand sides are spread round-robin over the CTAs.
+  //   pass 0: W = L^-1 A'   (column c of A')          -> cm
+  //   pass 1: C = L^-1 W^H  (column c = conj(row c of W)) -> cc (= lm, free after the Cholesky)
   double2* cc = lm;
-  for (int c = gw; c < m; c += gnw) {
-    for (int i = 0; i < m; ++i) {
-      double2 s{0, 0};
-      for (int k = lane; k < i; k += 32) s = cadd(s, cmul(lt[(size_t)i * m + k], wvec[k]));
-      s = warp_csum(s);
-      const double li = linv[i];
-      const double2 b = cm[(size_t)i * m + c];      // W[c, i]
-      const double2 w = double2{(b.x - s.x) * li, (-b.y - s.y) * li};
-      if (lane == 0) wvec[i] = w;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int r0 = 0; r0 < m; r0 += gnw) {                 // same trip count in every CTA
+      const int c = r0 + wl * csize + crank;
+      const bool act = c < m;
+      if (act) {
+        if (pass == 0)
+          for (int k = lane; k < m; k += 32) wvec[k] = am[(size_t)c * m + k];
+        else
+          for (int k = lane; k < m; k += 32) {
+            const double2 w = cm[(size_t)k * m + c];
+            wvec[k] = double2{w.x, -w.y};
+          }
+      }
+      __syncwarp();
+      for (int i0 = 0; i0 < m; i0 += scols) {
+        const int nb = min(scols, m - i0);
+        __syncthreads();
+        for (int e = tid; e < nb * m; e += RRC_THREADS) stg[e] = lf[(size_t)i0 * m + e];
+        __syncthreads();
+        if (act) {
+          for (int i = i0; i < i0 + nb; ++i) {
+            const double2 b = wvec[i];
+            const double li = slinv[i];
+            const double2 w = double2{b.x * li, b.y * li};
+            const double2* lc = stg + (size_t)(i - i0) * m;
+            for (int k = i + 1 + lane; k < m; k += 32) wvec[k] = csub(wvec[k], cmul(lc[k], w));
+            __syncwarp();
+          }
+        }
+      }
+      if (act) {
+        double2* out = pass == 0 ? cm : cc;
+        for (int k = lane; k < m; k += 32) {
+          const double2 b = wvec[k];
+          out[(size_t)c * m + k] = double2{b.x * slinv[k], b.y * slinv[k]};
+        }
+      }
       __syncwarp();
     }
-    for (int i = lane; i < m; i += 32) cc[(size_t)c * m + i] = wvec[i];
-    __syncwarp();
+    cl.sync();
   }
-  cl.sync();
   RR_MARK(2);
   // Hermitian average into cm (full storage)
   for (size_t e = gtid; e < mm; e += gnt) {
@@ -424,45 +479,79 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
   double* se2 = se + m;
   float* fd = reinterpret_cast<float*>(se2 + m);
   float* fe2 = fd + m;
+  dfl* gd = reinterpret_cast<dfl*>(fe2 + m);
+  dfl* ge2 = gd + m;
   for (int k = tid; k < m; k += RRC_THREADS) {
     sd[k] = dd[k];
     se[k] = ee[k];
     se2[k] = e2[k];
     fd[k] = (float)dd[k];
     fe2[k] = (float)e2[k];
+    gd[k] = df_from(dd[k]);
+    ge2[k] = df_from(e2[k]);
+  }
+  // Gershgorin interval and the largest e^2, by warp 0
+  __shared__ double gersh[3];
+  if (wl == 0) {
+    double lo_ = INFINITY, hi_ = -INFINITY, me = 0.0;
+    for (int k = lane; k < m; k += 32) {
+      const double r = (k > 0 ? ee[k - 1] : 0.0) + (k + 1 < m ? ee[k] : 0.0);
+      lo_ = fmin(lo_, dd[k] - r);
+      hi_ = fmax(hi_, dd[k] + r);
+      me = fmax(me, e2[k]);
+    }
+    for (int o = 16; o; o >>= 1) {
+      lo_ = fmin(lo_, __shfl_xor_sync(0xffffffffu, lo_, o));
+      hi_ = fmax(hi_, __shfl_xor_sync(0xffffffffu, hi_, o));
+      me = fmax(me, __shfl_xor_sync(0xffffffffu, me, o));
+    }
+    if (lane == 0) {
+      gersh[0] = lo_;
+      gersh[1] = hi_;
+      gersh[2] = me;
+    }
   }
   __syncthreads();
-  double tnorm = 0, lo0 = INFINITY, hi0 = -INFINITY;
-  for (int k = 0; k < m; ++k) {
-    const double r = (k > 0 ? se[k - 1] : 0.0) + (k + 1 < m ? se[k] : 0.0);
-    lo0 = fmin(lo0, sd[k] - r);
-    hi0 = fmax(hi0, sd[k] + r);
-  }
-  tnorm = fmax(fabs(lo0), fabs(hi0));
-  const double pivmin = fmax(1e-290, DBL_MIN * 4.0) + 1e-300;
-  // bisection of the Sturm count, one eigenvalue per thread (FP64 issue slots are the scarce
-  // resource, so no lane evaluates a count that does not narrow its own bracket): FP32 steps to
-  // ~1e-6 of the Gershgorin width, then the bracket is widened by the FP32 rounding level and
-  // refined in FP64 to a few ulps
-  for (int idx = gtid; idx < n; idx += gnt) {
+  const double lo0 = gersh[0], hi0 = gersh[1];
+  const double tnorm = fmax(fabs(lo0), fabs(hi0));
+  // pivot guard of the FP32 and double-float counts: e^2 / q stays below the FP32 overflow level
+  const float fpiv = 1.2e-38f * fmaxf(1.0f, (float)fmin(gersh[2], 1e30));
+  // 5. eigenvalue idx by one warp (eigenvalues spread round-robin over the CTAs): 33-way
+  // multisection of the Sturm count, lane l counting at lo + (l+1)(hi-lo)/33, the bracket then
+  // narrowed to the first section whose count exceeds idx.  FP32 counts take the bracket to
+  // ~2e-7 relative; it is widened by the FP32 error level and refined with double-float counts
+  // (~2^-47 per operation) to ~3e-14 relative.
+  for (int r0 = 0; r0 < n; r0 += gnw) {
+    const int idx = r0 + wl * csize + crank;
+    if (idx >= n) continue;
     double lo = lo0 - 1e-14 * tnorm - 1e-300, hi = hi0 + 1e-14 * tnorm + 1e-300;
-    {
-      float flo = (float)lo, fhi = (float)hi;
-      for (int it = 0; it < 24 && fhi - flo > 4e-7f * fmaxf(fabsf(flo), fabsf(fhi)); ++it) {
-        const float mid = 0.5f * (flo + fhi);
-        if (sturm_count_f(fd, fe2, m, mid, 1e-30f) > idx) fhi = mid;
-        else flo = mid;
-      }
-      const double pad = 4e-6 * tnorm + 1e-300;
-      lo = fmax(lo, (double)flo - pad);
-      hi = fmin(hi, (double)fhi + pad);
+    float flo = (float)lo, fhi = (float)hi;
+    for (int it = 0; it < 10; ++it) {
+      if (!(fhi - flo > 2e-7f * fmaxf(fabsf(flo), fabsf(fhi)))) break;
+      const float step = (fhi - flo) * (1.0f / 33.0f);
+      const float x = flo + step * (float)(lane + 1);
+      const unsigned bal = __ballot_sync(0xffffffffu, sturm_count_f(fd, fe2, m, x, fpiv) > idx);
+      const int l = bal ? __ffs(bal) - 1 : 32;
+      const float nlo = l == 0 ? flo : flo + step * (float)l;
+      const float nhi = l == 32 ? fhi : flo + step * (float)(l + 1);
+      flo = nlo;
+      fhi = nhi;
     }
-    for (int it = 0; it < 60 && hi - lo > 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (sturm_count(sd, se2, m, mid, pivmin) > idx) hi = mid;
-      else lo = mid;
+    const double pad = 4e-6 * tnorm + 1e-300;
+    lo = fmax(lo, (double)flo - pad);
+    hi = fmin(hi, (double)fhi + pad);
+    for (int it = 0; it < 12; ++it) {
+      if (!(hi - lo > 3e-14 * fmax(fabs(lo), fabs(hi)) + 1e-300)) break;
+      const double step = (hi - lo) * (1.0 / 33.0);
+      const double x = lo + step * (double)(lane + 1);
+      const unsigned bal = __ballot_sync(0xffffffffu, sturm_count_df(gd, ge2, m, df_from(x), fpiv) > idx);
+      const int l = bal ? __ffs(bal) - 1 : 32;
+      const double nlo = l == 0 ? lo : lo + step * (double)l;
+      const double nhi = l == 32 ? hi : lo + step * (double)(l + 1);
+      lo = nlo;
+      hi = nhi;
     }
-    lamw[idx] = 0.5 * (lo + hi);
+    if (lane == 0) lamw[idx] = 0.5 * (lo + hi);
   }
   cl.sync();
   RR_MARK(4);
@@ -502,40 +591,68 @@ __global__ void __launch_bounds__(RRC_THREADS) k_rr_cluster(const double2* __res
   }
   cl.sync();
   RR_MARK(5);
-  // 7. u = H_0 ... H_{m-3} (Phi z); V = D L^-H u
-  for (int j = gw; j < n; j += gnw) {
-    for (int i = lane; i < m; i += 32) {
-      const double z = zt[(size_t)j * m + i];
-      wvec[i] = double2{ph[i].x * z, ph[i].y * z};
-    }
+  // 7. u = H_0 ... H_{m-3} (Phi z); V = D L^-H u.  Warp per eigenvector, spread round-robin over
+  // the CTAs; reflectors and rows of L come through the staging area in blocks.
+  for (int k = tid; k < m; k += RRC_THREADS) {
+    stau[k] = tau[k].x;
+    sph[k] = ph[k];
+  }
+  for (int r0 = 0; r0 < n; r0 += gnw) {                    // same trip count in every CTA
+    const int j = r0 + wl * csize + crank;
+    const bool act = j < n;
+    __syncthreads();
+    if (act)
+      for (int i = lane; i < m; i += 32) {
+        const double z = zt[(size_t)j * m + i];
+        wvec[i] = double2{sph[i].x * z, sph[i].y * z};
+      }
     __syncwarp();
-    for (int k = m - 3; k >= 0; --k) {
-      const double t = tau[k].x;
-      if (t == 0.0) continue;
-      const double2* v = cm + (size_t)k * m + k + 1;
-      const int len = m - k - 1;
-      double2 s{0, 0};
-      for (int i = lane; i < len; i += 32) s = cadd(s, cmulc(v[i], wvec[k + 1 + i]));
-      s = warp_csum(s);
-      s = double2{t * s.x, t * s.y};
-      for (int i = lane; i < len; i += 32) wvec[k + 1 + i] = csub(wvec[k + 1 + i], cmul(s, v[i]));
-      __syncwarp();
+    for (int k1 = m - 3; k1 >= 0; k1 -= scols) {
+      const int k0 = max(0, k1 - scols + 1);
+      __syncthreads();
+      for (int e = tid; e < (k1 - k0 + 1) * m; e += RRC_THREADS) stg[e] = cm[(size_t)k0 * m + e];
+      __syncthreads();
+      if (act) {
+        for (int k = k1; k >= k0; --k) {
+          const double t = stau[k];
+          if (t == 0.0) continue;
+          const double2* v = stg + (size_t)(k - k0) * m + k + 1;
+          const int len = m - k - 1;
+          double2 s{0, 0};
+          for (int i = lane; i < len; i += 32) s = cadd(s, cmulc(v[i], wvec[k + 1 + i]));
+          s = warp_csum(s);
+          s = double2{t * s.x, t * s.y};
+          for (int i = lane; i < len; i += 32) wvec[k + 1 + i] = csub(wvec[k + 1 + i], cmul(s, v[i]));
+          __syncwarp();
+        }
+      }
     }
-    // L^H y = u (upper triangular, back substitution); L^H[i, k] = conj(L[k, i]) = conj(lf[i*m + k])
-    for (int i = m - 1; i >= 0; --i) {
-      double2 s{0, 0};
-      for (int k = i + 1 + lane; k < m; k += 32) s = cadd(s, cmulc(lf[(size_t)i * m + k], wvec[k]));
-      s = warp_csum(s);
-      const double li = linv[i];
-      const double2 u = wvec[i];
-      if (lane == 0) wvec[i] = double2{(u.x - s.x) * li, (u.y - s.y) * li};
-      __syncwarp();
+    // L^H y = u, column-oriented: at step i (descending) y_i = u_i / L_ii and every lane updates
+    // its u_k -= conj(L[i, k]) y_i for k < i (row i of L from the staging area)
+    for (int i1 = m - 1; i1 >= 0; i1 -= scols) {
+      const int i0 = max(0, i1 - scols + 1);
+      __syncthreads();
+      for (int e = tid; e < (i1 - i0 + 1) * m; e += RRC_THREADS) stg[e] = lt[(size_t)i0 * m + e];
+      __syncthreads();
+      if (act) {
+        for (int i = i1; i >= i0; --i) {
+          const double2 u = wvec[i];
+          const double li = slinv[i];
+          const double2 y = double2{u.x * li, u.y * li};
+          const double2* lr = stg + (size_t)(i - i0) * m;
+          for (int k = lane; k < i; k += 32) wvec[k] = csub(wvec[k], cmulc(lr[k], y));
+          __syncwarp();
+        }
+      }
     }
-    for (int i = lane; i < m; i += 32) {
-      const double2 y = wvec[i];
-      V[(size_t)j * m + i] = double2{dsc[i] * y.x, dsc[i] * y.y};
+    if (act) {
+      for (int i = lane; i < m; i += 32) {
+        const double2 u = wvec[i];
+        const double f = sdsc[i] * slinv[i];
+        V[(size_t)j * m + i] = double2{f * u.x, f * u.y};
+      }
+      if (lane == 0) lam[j] = lamw[j];
     }
-    if (lane == 0) lam[j] = lamw[j];
     __syncwarp();
   }
   if (gtid == 0) {
@@ -563,12 +680,15 @@ static int g_cluster = 0;   // 0 = unknown, else cluster size that launched succ
 int rayleigh_ritz_cluster(const double2* a, const double2* s, int nz, int n, double2* v, double* lam, int* info,
                           double2* scratch, cudaStream_t st, double chol_tol, bool* launched) {
   *launched = false;
-  const size_t smem = rr_cluster_smem(nz);
-  if (smem > 200 * 1024) return DKS_OK;     // too large for the per-warp vectors: caller falls back
+  // staging columns: as many as fit (at most 64); too few and the single-CTA kernel takes over
+  const size_t base = rr_cluster_smem(nz, 0);
+  if (base + 8 * (size_t)nz * sizeof(double2) > kRrSmemMax) return DKS_OK;
+  const int scols = (int)std::min<size_t>({(size_t)64, (size_t)nz, (kRrSmemMax - base) / ((size_t)nz * sizeof(double2))});
+  const size_t smem = rr_cluster_smem(nz, scols);
   static bool attr_done = false;
   if (!attr_done) {
     cudaFuncSetAttribute((const void*)k_rr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute((const void*)k_rr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute((const void*)k_rr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRrSmemMax);
     attr_done = true;
   }
   const int tries[2] = {16, 8};
@@ -587,7 +707,7 @@ int rayleigh_ritz_cluster(const double2* a, const double2* s, int nz, int n, dou
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     Prof pr(P_RR, st, 2.0 * nz * nz * 16.0 + 16.0 * nz * n, rr_flops(nz, n));
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_rr_cluster, a, s, nz, n, v, lam, info, scratch, chol_tol);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_rr_cluster, a, s, nz, n, v, lam, info, scratch, chol_tol, scols);
     if (e == cudaSuccess) {
       g_cluster = csz;
       *launched = true;
