@@ -230,7 +230,9 @@ int dks_rayleigh_ritz_static(const void* A, const void* S, int nz, int n, void* 
 int dks_rotate(const void* Z, int rows, int nz, const void* W, int ldw, int n, void* OUT,
                double beta, int prec, void* stream);
 
-/* Alg. 1 line 16-17: norms[j] = ||HX[j] - lam[j] X[j]||_2 accumulated in FP64. */
+/* Alg. 1 line 16-17: norms[j] = ||HX[j] - lam[j] X[j]||_2.  The residual and the sum over the
+ * four components of a planewave are formed in the storage precision (DKS_PREC_FP32: FP32,
+ * otherwise FP64); the sum over planewaves is accumulated in FP64.  rows % 4 == 0. */
 int dks_residual_norms(const void* X, const void* HX, const double* lam, int rows, int n,
                        double* norms, int prec, void* stream);
 

@@ -505,7 +505,8 @@ int dks_filter(dks_ctx* ctx, int ik, const void* Y, void* FY, int nb, double C, 
 
 int dks_precond(dks_ctx* ctx, int ik, const void* X, const void* HX, const double* lam, const int* act, int nact,
                 void* Y, int precond, int prec, void* stream) {
-  if (!ctx || ik < 0 || ik >= ctx->nk || nact < 0 || (nact && (!X || !HX || !lam || !act || !Y)))
+  if (!ctx || ik < 0 || ik >= ctx->nk || nact < 0 || (nact && (!X || !HX || !lam || !act || !Y)) || prec < 0 ||
+      prec > 2)
     return fail(DKS_ERR_INVALID_ARG, "dks_precond: bad argument");
   if (!nact) return DKS_OK;
   cudaStream_t st = (cudaStream_t)stream;
@@ -524,7 +525,7 @@ int dks_precond(dks_ctx* ctx, int ik, const void* X, const void* HX, const doubl
   double* stats = nullptr;
   DKS_CUDA_TRY(cudaMallocAsync((void**)&stats, (size_t)3 * ncol * sizeof(double), st));
   int rc;
-  if (prec == DKS_PREC_FP64) {
+  if (prec != DKS_PREC_FP32) {
     rc = col_stats<double2>((const double2*)X, nullptr, nullptr, kp.ek, kp.npw, ncol, stats, st);
     if (!rc) rc = precond_apply<double2>((const double2*)X, (const double2*)HX, lam, stats, act, nact, kp.ek, kp.npw,
                                          precond, (double2*)Y, st);
@@ -584,7 +585,7 @@ int dks_rotate(const void* Z, int rows, int nz, const void* W, int ldw, int n, v
 
 int dks_residual_norms(const void* X, const void* HX, const double* lam, int rows, int n, double* norms, int prec,
                        void* stream) {
-  if (rows <= 0 || rows % 4 || n <= 0 || !X || !HX || !lam || !norms)
+  if (rows <= 0 || rows % 4 || n <= 0 || !X || !HX || !lam || !norms || prec < 0 || prec > 2)
     return fail(DKS_ERR_INVALID_ARG, "dks_residual_norms: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
   double* stats = nullptr;
@@ -592,7 +593,7 @@ int dks_residual_norms(const void* X, const void* HX, const double* lam, int row
   DKS_CUDA_TRY(cudaMallocAsync((void**)&stats, (size_t)3 * n * sizeof(double), st));
   DKS_CUDA_TRY(cudaMallocAsync((void**)&ek, (size_t)(rows / 4) * sizeof(double), st));
   DKS_CUDA_TRY(cudaMemsetAsync(ek, 0, (size_t)(rows / 4) * sizeof(double), st));
-  int rc = prec == DKS_PREC_FP64
+  int rc = prec != DKS_PREC_FP32
                ? col_stats<double2>((const double2*)X, (const double2*)HX, lam, ek, rows / 4, n, stats, st)
                : col_stats<float2>((const float2*)X, (const float2*)HX, lam, ek, rows / 4, n, stats, st);
   if (!rc) {

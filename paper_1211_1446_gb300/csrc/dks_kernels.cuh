@@ -69,6 +69,14 @@ __device__ __forceinline__ dfl df_add(dfl a, dfl b) {
   return dfl{h, e - (h - s)};
 }
 __device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.h, -a.l}; }
+// a + x for a float x (two-sum of the leading parts, then a fast renormalisation)
+__device__ __forceinline__ dfl df_add_f(dfl a, float x) {
+  const float s = a.h + x;
+  const float bb = s - a.h;
+  const float e = ((a.h - (s - bb)) + (x - bb)) + a.l;
+  const float h = s + e;
+  return dfl{h, e - (h - s)};
+}
 __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
   const float p = a.h * b.h;
   float e = fmaf(a.h, b.h, -p);

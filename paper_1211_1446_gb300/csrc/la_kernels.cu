@@ -3,13 +3,15 @@
 //  gemm_hn   C (m x n) += A^H B   A: k x m, B: k x n (k = 4 npw or 2 npw, huge; m, n small)
 //            Gram matrices of lines 12-13 and the projector coefficients B^H x~.
 //            Split over k across the grid; each CTA reduces a 32x32 tile of C over its
-//            k-range in registers and adds it to C with FP64 atomics.
+//            k-range in registers and adds it to C with FP64 atomics.  With FP32 operands
+//            each 32-deep k-tile is summed in FP32 and folded into a double-float total.
 //  gemm_nn   OUT (k x n) = alpha A (k x m) diag(ws) W (m x n) + beta OUT
 //            Rotations X <- Z V, P <- [0,Y,P] V (lines 15, 22) and the projector
 //            update x~ += B (D Z).  W (FP64, from the small solve) is staged in shared
 //            memory in the working precision.
-//  col_stats per column: ||hx - lam x||^2, ||x||^2 and sum_G |k+G|^2/2 |x|^2 (FP64)
+//  col_stats per column: ||hx - lam x||^2, ||x||^2 and sum_G |k+G|^2/2 |x|^2 (FP64 column sums)
 //  precond   Y = K(x_G) (HX - lam X) on the active columns (lines 9 and 16 fused)
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +21,8 @@
 #include "dks_kernels.cuh"
 
 namespace dks {
+
+namespace cg = cooperative_groups;
 
 // accumulation type: FP64 as soon as one operand is FP64
 template <typename A, typename B> struct AccOf { using T = double2; };
@@ -55,6 +59,10 @@ __global__ void __launch_bounds__(256) k_gemm_hn(const Va* __restrict__ a, int l
   const int ke = min(k, kb + kchunk);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   A acc[2][2] = {{A{0, 0}, A{0, 0}}, {A{0, 0}, A{0, 0}}};
+  // FP32 arithmetic: each k-tile is summed in FP32 and folded into a double-float total, so
+  // FP32 rounding accumulates over 32 terms instead of the whole k-range of the CTA
+  constexpr bool fold = std::is_same<A, float2>::value;
+  dfl tot[2][2][2] = {};
   for (int k0 = kb; k0 < ke; k0 += HN_T) {
     for (int e = threadIdx.x; e < HN_T * HN_T; e += 256) {
       const int kq = e & (HN_T - 1), q = e >> 5;
@@ -77,6 +85,16 @@ __global__ void __launch_bounds__(256) k_gemm_hn(const Va* __restrict__ a, int l
       acc[1][0] = cadd(acc[1][0], cmulc(a1, b0));
       acc[1][1] = cadd(acc[1][1], cmulc(a1, b1));
     }
+    if constexpr (fold) {
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          tot[i][j][0] = df_add_f(tot[i][j][0], acc[i][j].x);
+          tot[i][j][1] = df_add_f(tot[i][j][1], acc[i][j].y);
+          acc[i][j] = A{0, 0};
+        }
+    }
     __syncthreads();
   }
 #pragma unroll
@@ -85,8 +103,10 @@ __global__ void __launch_bounds__(256) k_gemm_hn(const Va* __restrict__ a, int l
     for (int j = 0; j < 2; ++j) {
       const int mm = m0 + ty + 16 * i, nn = n0 + tx + 16 * j;
       if (mm < m && nn < n) {
-        atomicAdd(&c[(size_t)nn * ldc + mm].x, (double)acc[i][j].x);
-        atomicAdd(&c[(size_t)nn * ldc + mm].y, (double)acc[i][j].y);
+        const double vx = fold ? df_val(tot[i][j][0]) : (double)acc[i][j].x;
+        const double vy = fold ? df_val(tot[i][j][1]) : (double)acc[i][j].y;
+        atomicAdd(&c[(size_t)nn * ldc + mm].x, vx);
+        atomicAdd(&c[(size_t)nn * ldc + mm].y, vy);
       }
     }
 }
@@ -223,29 +243,46 @@ int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const
 }
 
 // ---------------------------------------------------------------- column statistics
+// One 8-CTA cluster per column: each CTA sums an eighth of the planewaves (all four
+// components, so |k+G|^2/2 is read once per planewave), and CTA 0 of the cluster adds the
+// eight partial sums from distributed shared memory in rank order (deterministic result).
+constexpr int STATS_SPLIT = 8;
+
 template <typename V>
-__global__ void __launch_bounds__(256) k_col_stats(const V* __restrict__ x, const V* __restrict__ hx,
-                                                   const double* __restrict__ lam,
-                                                   const double* __restrict__ ek, int npw,
-                                                   double* __restrict__ stats) {
-  const int j = blockIdx.x;
+__global__ void __cluster_dims__(STATS_SPLIT, 1, 1) __launch_bounds__(256)
+    k_col_stats(const V* __restrict__ x, const V* __restrict__ hx, const double* __restrict__ lam,
+                const double* __restrict__ ek, int npw, double* __restrict__ stats) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int part = (int)cl.block_rank();
+  const int j = blockIdx.y;
   const size_t rows = (size_t)4 * npw;
   const V* xj = x + (size_t)j * rows;
   const V* hj = hx ? hx + (size_t)j * rows : nullptr;
   const double l = lam ? lam[j] : 0.0;
+  const int per = (npw + STATS_SPLIT - 1) / STATS_SPLIT;
+  const int p0 = part * per, p1 = min(npw, p0 + per);
+  // per-planewave sums in the working precision (the residual is formed in it), column sums in FP64
+  using T = typename RealOf<V>::T;
+  const T lt = (T)l;
   double s0 = 0, s1 = 0, s2 = 0;
-  for (size_t e = threadIdx.x; e < rows; e += blockDim.x) {
-    const double2 xv = to_d2(xj[e]);
-    const double ax = xv.x * xv.x + xv.y * xv.y;
-    if (hj) {
-      const double2 hv = to_d2(hj[e]);
-      const double rx = hv.x - l * xv.x, ry = hv.y - l * xv.y;
-      s0 += rx * rx + ry * ry;
+  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    T ax = 0, rr = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const V xv = xj[(size_t)a * npw + p];
+      ax = fma(xv.x, xv.x, fma(xv.y, xv.y, ax));
+      if (hj) {
+        const V hv = hj[(size_t)a * npw + p];
+        const T rx = fma(-lt, xv.x, hv.x), ry = fma(-lt, xv.y, hv.y);
+        rr = fma(rx, rx, fma(ry, ry, rr));
+      }
     }
-    s1 += ax;
-    s2 += ek[e % npw] * ax;
+    s0 += (double)rr;
+    s1 += (double)ax;
+    s2 = fma(ek[p], (double)ax, s2);
   }
-  __shared__ double red[3][32];
+  __shared__ double red[3][8];
+  __shared__ double part_sum[3];
   for (int off = 16; off; off >>= 1) {
     s0 += __shfl_down_sync(0xffffffffu, s0, off);
     s1 += __shfl_down_sync(0xffffffffu, s1, off);
@@ -258,30 +295,27 @@ __global__ void __launch_bounds__(256) k_col_stats(const V* __restrict__ x, cons
     red[2][w] = s2;
   }
   __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    s0 = ln < nw ? red[0][ln] : 0;
-    s1 = ln < nw ? red[1][ln] : 0;
-    s2 = ln < nw ? red[2][ln] : 0;
-    for (int off = 16; off; off >>= 1) {
-      s0 += __shfl_down_sync(0xffffffffu, s0, off);
-      s1 += __shfl_down_sync(0xffffffffu, s1, off);
-      s2 += __shfl_down_sync(0xffffffffu, s2, off);
-    }
-    if (ln == 0) {
-      stats[3 * j] = s0;
-      stats[3 * j + 1] = s1;
-      stats[3 * j + 2] = s2;
-    }
+  if (threadIdx.x < 3) {
+    double t = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[threadIdx.x][i];
+    part_sum[threadIdx.x] = t;
   }
+  cl.sync();
+  if (part == 0 && threadIdx.x < 3) {
+    double t = 0;
+    for (int r = 0; r < STATS_SPLIT; ++r) t += *cl.map_shared_rank(&part_sum[threadIdx.x], r);
+    stats[3 * j + threadIdx.x] = t;
+  }
+  cl.sync();   // the other CTAs keep their shared memory until rank 0 has read it
 }
 
 template <typename V>
 int col_stats(const V* x, const V* hx, const double* lam, const double* ek, int npw, int n, double* stats,
               cudaStream_t st) {
   if (n <= 0) return DKS_OK;
+  if (n > 65535) return fail(DKS_ERR_INVALID_ARG, "col_stats: too many columns");
   Prof pr(P_STATS, st, (hx ? 2.0 : 1.0) * n * 4.0 * npw * sizeof(V) + 8.0 * npw, 12.0 * n * 4.0 * npw);
-  k_col_stats<V><<<n, 256, 0, st>>>(x, hx, lam, ek, npw, stats);
+  k_col_stats<V><<<dim3(STATS_SPLIT, n), 256, 0, st>>>(x, hx, lam, ek, npw, stats);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
