@@ -13,9 +13,9 @@
 //     the SVQB path
 //  3. W = L^-1 A' and C = L^-1 W^H = L^-1 A' L^-H: column-oriented forward substitution,
 //     warp per right-hand side, no reductions
-//  4. Householder reduction of C to a complex tridiagonal: every warp recomputes the
-//     column norm and reflector itself (no barrier), rows of p = tau C v are split over
-//     the warps, then the rank-2 update; two barriers per column
+//  4. Householder reduction of C to a complex tridiagonal with the columns of C distributed
+//     over the shared memories of the cluster (column j in CTA j % csize); reflectors and
+//     p = tau C v travel through distributed shared memory; two barriers per column
 //  5. real tridiagonal by a diagonal phase; the n lowest eigenvalues by 33-way
 //     multisection of the Sturm count (warp per eigenvalue): FP32 counts, then
 //     double-float counts
@@ -375,6 +375,130 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
     cm[e] = i == j ? double2{a.x, 0.0} : double2{0.5 * (a.x + b.x), 0.5 * (a.y - b.y)};
   }
   cl.sync();
+  // 4. Householder reduction of cm to a complex tridiagonal.
+  // Distributed form (when the staging area holds this CTA's share of the columns): column j
+  // lives in the shared memory of CTA j % csize.  Step k (reflector v of column k, rows > k):
+  //   A  every CTA copies v and tau from the owner of column k (DSMEM)
+  //   B  p_i = tau C[:, i]^H v for the owned columns i > k (Hermitian C: p = tau C v) and the
+  //      partial sum of conj(v_i) p_i
+  //   -- cluster barrier --
+  //   C  K = tau/2 sum of the partials, w = p - K v (p gathered from the owners)
+  //   D  owned columns j > k: C[:, j] -= v conj(w_j) + w conj(v_j)
+  //   E  the owner of column k+1 forms the next reflector
+  //   -- cluster barrier --
+  // The reflectors stay in their columns (first element replaced by v0), as in the global form.
+  const int ncol_own = (m + csize - 1) / csize;
+  if (m >= 3 && scols >= ncol_own) {
+    double2* cb = stg;                                       // owned columns, column j at (j / csize) * m
+    double2* vl = reinterpret_cast<double2*>(rrc_smem);      // v of the current step, by row
+    double2* wf = vl + m;                                    // w, by row
+    double2* pb = wf + m;                                    // p at the owned indices (read by the cluster)
+    double2* bc = pb + m;                                    // 2 x (m + 1): reflector + tau, by parity
+    double2* kp = bc + 2 * (m + 1);                          // this CTA's partial of v^H p
+    double2* kw = kp + 1;                                    // per-warp partials
+    __shared__ double2 hk;                                   // K of the current step
+    for (int e = tid; e < ncol_own * m; e += RRC_THREADS) {
+      const int lj = e / m, r = e - lj * m, j = lj * csize + crank;
+      if (j < m) cb[e] = cm[(size_t)j * m + r];
+    }
+    __syncthreads();
+    // reflector of column k by warp 0 of its owner: broadcast buffer, v0 into the column, tau/ph
+    auto make_reflector = [&](int k) {
+      double2* x = cb + (size_t)(k / csize) * m + k + 1;
+      const int len = m - k - 1;
+      double a2 = 0;
+      for (int i = lane; i < len; i += 32) a2 += x[i].x * x[i].x + x[i].y * x[i].y;
+      a2 = warp_sum(a2);
+      const double2 x0 = x[0];
+      const double ax0 = nr_hypot(x0.x, x0.y);
+      const double alpha = nr_sqrt(a2);
+      double t = 0.0;
+      double2 beta = x0, v0 = x0;
+      if (alpha > 1e-300 && a2 - ax0 * ax0 > 1e-30 * a2) {
+        const double ri = ax0 > 0 ? nr_rcp(ax0) : 0.0;
+        const double2 phs = ax0 > 0 ? double2{x0.x * ri, x0.y * ri} : double2{1, 0};
+        beta = double2{-phs.x * alpha, -phs.y * alpha};
+        v0 = double2{x0.x - beta.x, x0.y - beta.y};
+        t = 2.0 * nr_rcp(a2 - ax0 * ax0 + v0.x * v0.x + v0.y * v0.y);
+      }
+      double2* out = bc + (size_t)(k & 1) * (m + 1);
+      for (int i = lane; i < len; i += 32) out[k + 1 + i] = i == 0 ? v0 : x[i];
+      __syncwarp();
+      if (lane == 0) {
+        out[m] = double2{t, 0.0};
+        if (t != 0.0) x[0] = v0;
+        tau[k] = double2{t, 0.0};
+        ph[k] = beta;
+      }
+    };
+    if (crank == 0 && wl == 0) make_reflector(0);
+    cl.sync();
+    for (int k = 0; k + 2 < m; ++k) {
+      const int len = m - k - 1;
+      // A
+      const double2* src = cl.map_shared_rank(bc + (size_t)(k & 1) * (m + 1), (unsigned)(k % csize));
+      for (int r = k + 1 + tid; r <= m; r += RRC_THREADS) vl[r == m ? 0 : r] = src[r];   // vl[0] <- tau
+      __syncthreads();
+      const double t = vl[0].x;
+      // B
+      const int lj0 = (k + 1 - crank + csize - 1) / csize;   // first owned column > k
+      double2 kacc{0, 0};
+      for (int lj = lj0 + wl; lj < ncol_own; lj += RRC_WARPS) {
+        const int i = lj * csize + crank;
+        if (i >= m) break;
+        const double2* ci = cb + (size_t)lj * m;
+        double2 sacc{0, 0};
+        for (int r = k + 1 + lane; r < m; r += 32) sacc = cadd(sacc, cmulc(ci[r], vl[r]));
+        sacc = warp_csum(sacc);
+        const double2 p = double2{t * sacc.x, t * sacc.y};
+        if (lane == 0) pb[i] = p;
+        kacc = cadd(kacc, cmulc(vl[i], p));
+      }
+      if (lane == 0) kw[wl] = kacc;
+      __syncthreads();
+      if (tid == 0) {
+        double2 ks{0, 0};
+        for (int w = 0; w < RRC_WARPS; ++w) ks = cadd(ks, kw[w]);
+        kp[0] = ks;
+      }
+      cl.sync();
+      // C
+      if (wl == 0) {
+        double2 ks{0, 0};
+        if (lane < csize) ks = *cl.map_shared_rank(kp, (unsigned)lane);
+        ks = warp_csum(ks);
+        if (lane == 0) hk = double2{0.5 * t * ks.x, 0.5 * t * ks.y};
+      }
+      __syncthreads();
+      const double2 kv = hk;
+      for (int r = k + 1 + tid; r < m; r += RRC_THREADS) {
+        const double2 p = *cl.map_shared_rank(pb + r, (unsigned)(r % csize));
+        wf[r] = csub(p, cmul(kv, vl[r]));
+      }
+      __syncthreads();
+      // D
+      const int nown = ncol_own - lj0;
+      for (int e = tid; e < nown * len; e += RRC_THREADS) {
+        const int q = e / len, r = k + 1 + (e - q * len);
+        const int lj = lj0 + q, j = lj * csize + crank;
+        if (j >= m) continue;
+        const double2 vr = vl[r], wr = wf[r], vj = vl[j], wj = wf[j];
+        const double2 u1 = cmul(vr, double2{wj.x, -wj.y});
+        const double2 u2 = cmul(wr, double2{vj.x, -vj.y});
+        double2* cjr = cb + (size_t)lj * m + r;
+        *cjr = csub(*cjr, cadd(u1, u2));
+      }
+      __syncthreads();
+      // E
+      if (k + 3 < m && crank == (k + 1) % csize && wl == 0) make_reflector(k + 1);
+      cl.sync();
+    }
+    for (int e = tid; e < ncol_own * m; e += RRC_THREADS) {
+      const int lj = e / m, r = e - lj * m, j = lj * csize + crank;
+      if (j < m) cm[(size_t)j * m + r] = cb[e];
+    }
+    cl.sync();
+  } else {
   // 4. Householder reduction of cm.  Warp 0 of every CTA forms the reflector (norm, phase, tau)
   // and the scalar K and hands them to its CTA through shared memory.
   __shared__ double2 hh[4];   // {tau, 0}, beta, v0, K
@@ -448,6 +572,7 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
     // (no barrier needed: x[0] of column k is not read again until the back-transformation)
   }
   cl.sync();
+  }
   RR_MARK(3);
   // 5. real tridiagonal (every CTA keeps its own copy in shared memory for the multisection)
   if (gtid == 0) {
