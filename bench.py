@@ -175,7 +175,7 @@ def run_reference(args):
 def kernel_case(case):
     """One hot step of the solve at the bench's dimer size, three launches (ncu --set full target).
     hx64/hx32/hxdf: H' on 40 columns; gram64/gram32/gramdf: A = Z^H HZ, S = Z^H Z with 120 columns;
-    rotate64/rotatedf: X = Z V with Z of 120 columns and V 120 x 40; rr: the 120 x 120 pencil.
+    rotate64/rotate32/rotatedf: X = Z V with Z of 120 columns and V 120 x 40; rr: the 120 x 120 pencil.
     The *df cases run the complex128 arithmetic in double-float form."""
     import numpy as np
     import torch
@@ -236,7 +236,8 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=60)
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--kernel-case", default=None,
-                    choices=["hx64", "hx32", "hxdf", "gram64", "gram32", "gramdf", "rotate64", "rotatedf", "rr"],
+                    choices=["hx64", "hx32", "hxdf", "gram64", "gram32", "gramdf", "rotate64", "rotate32", "rotatedf",
+                             "rr"],
                     help="run one hot step a few times at the dimer's bench size (for ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -164,22 +164,26 @@ int gemm_hn_df(const double2* a, int lda, const double2* b, int ldb, int k, int 
 }
 
 // ---------------------------------------------------------------- OUT = alpha A diag(ws) W + beta OUT
-constexpr int DNN_R = 64, DNN_C = 32, DNN_M = 16;
+// 128 x 32 output tile per CTA, 2 rows x 8 columns per thread (rows t and t+64): the split of W
+// into double-float pairs is amortised over 128 rows.
+constexpr int DNN_R = 128, DNN_C = 32, DNN_M = 16;
 
-__global__ void __launch_bounds__(256) k_gemm_nn_df(const double2* __restrict__ a, int lda, int k, int m,
+__global__ void __launch_bounds__(256, 1) k_gemm_nn_df(const double2* __restrict__ a, int lda, int k, int m,
                                                     const double2* __restrict__ w, int ldw,
                                                     const double* __restrict__ ws, int n,
                                                     double2* __restrict__ out, int ldo, double alpha, double beta) {
   __shared__ gcdf as[DNN_M][DNN_R];
   __shared__ gcdf wsm[DNN_M][DNN_C];
   const int r0 = blockIdx.x * DNN_R, c0 = blockIdx.y * DNN_C;
-  const int row = threadIdx.x & (DNN_R - 1), cg = threadIdx.x >> 6;
-  gcdf acc[8];
+  const int rg = threadIdx.x & 63, cg = threadIdx.x >> 6;
+  gcdf acc[2][8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) acc[j] = gcdf{{0.f, 0.f}, {0.f, 0.f}};
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = gcdf{{0.f, 0.f}, {0.f, 0.f}};
   for (int m0 = 0; m0 < m; m0 += DNN_M) {
     for (int e = threadIdx.x; e < DNN_M * DNN_R; e += 256) {
-      const int rr = e & (DNN_R - 1), mm = e >> 6;
+      const int rr = e & (DNN_R - 1), mm = e >> 7;
       double2 v{0, 0};
       if (m0 + mm < m && r0 + rr < k) v = a[(size_t)(m0 + mm) * lda + r0 + rr];
       as[mm][rr] = gcdf_split(v);
@@ -198,19 +202,26 @@ __global__ void __launch_bounds__(256) k_gemm_nn_df(const double2* __restrict__ 
     __syncthreads();
 #pragma unroll 2
     for (int mm = 0; mm < DNN_M; ++mm) {
-      const gcdf av = as[mm][row];
+      const gcdf a0 = as[mm][rg], a1 = as[mm][rg + 64];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) cdf_mac(acc[j], av, wsm[mm][cg * 8 + j]);
+      for (int j = 0; j < 8; ++j) {
+        const gcdf wv = wsm[mm][cg * 8 + j];
+        cdf_mac(acc[0][j], a0, wv);
+        cdf_mac(acc[1][j], a1, wv);
+      }
     }
     __syncthreads();
   }
-  if (r0 + row < k) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int row = r0 + rg + 64 * i;
+    if (row >= k) continue;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int cc = c0 + cg * 8 + j;
       if (cc < n) {
-        double2* o = out + (size_t)cc * ldo + r0 + row;
-        double2 r{df_to_d(acc[j].re), df_to_d(acc[j].im)};
+        double2* o = out + (size_t)cc * ldo + row;
+        double2 r{df_to_d(acc[i][j].re), df_to_d(acc[i][j].im)};
         if (beta != 0.0) {
           const double2 old = *o;
           r.x += beta * old.x;

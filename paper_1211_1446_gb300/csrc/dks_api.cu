@@ -214,6 +214,14 @@ static int build_k(dks_ctx* ctx, const double kfrac[3], double ecut, const dks_p
   DKS_TRY(upload(&kp.pw_stick, pstick.data(), pstick.size()));
   DKS_TRY(upload(&kp.pw_iz, piz.data(), piz.size()));
   DKS_TRY(upload(&kp.q, q.data(), q.size()));
+  std::vector<float> cq(6 * (size_t)npw);
+  for (size_t e = 0; e < 3 * (size_t)npw; ++e) {
+    const double v = ctx->c * q[e];
+    const float h = (float)v;
+    cq[2 * e] = h;
+    cq[2 * e + 1] = (float)(v - (double)h);
+  }
+  DKS_TRY(upload(&kp.cq32, cq.data(), cq.size()));
   DKS_TRY(upload(&kp.ek, ek.data(), ek.size()));
   // projector rows beta_c[(spin*npw + p)]
   if (!chans.empty()) {
@@ -272,6 +280,7 @@ static void free_ctx(dks_ctx* ctx) {
     cudaFree(kp.pw_stick);
     cudaFree(kp.pw_iz);
     cudaFree(kp.q);
+    cudaFree(kp.cq32);
     cudaFree(kp.ek);
     cudaFree(kp.bt64);
     cudaFree(kp.bt32);

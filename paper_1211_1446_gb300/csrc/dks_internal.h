@@ -59,6 +59,7 @@ struct KPoint {
   int* pw_stick = nullptr;      // npw
   int* pw_iz = nullptr;         // npw, i3 (natural)
   double* q = nullptr;          // npw*3 cartesian k+G (FP64)
+  float* cq32 = nullptr;        // npw*6: c (k+G)_x, c (k+G)_y, c (k+G)_z as double-float (hi, lo) pairs
   double* ek = nullptr;         // npw, |k+G|^2/2
   double2* bt64 = nullptr;      // nproj x (2 npw) projector rows (beta, spin-major)
   float2* bt32 = nullptr;

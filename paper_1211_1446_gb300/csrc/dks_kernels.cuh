@@ -21,6 +21,19 @@ template <typename V>
 __device__ __host__ __forceinline__ V cmulc(V a, V b) {
   return V{a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x};
 }
+// c + a b and c + conj(a) b as four fused multiply-adds
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  return float2{fmaf(-a.y, b.y, fmaf(a.x, b.x, c.x)), fmaf(a.y, b.x, fmaf(a.x, b.y, c.y))};
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  return double2{fma(-a.y, b.y, fma(a.x, b.x, c.x)), fma(a.y, b.x, fma(a.x, b.y, c.y))};
+}
+__device__ __forceinline__ float2 cfmac(float2 a, float2 b, float2 c) {
+  return float2{fmaf(a.y, b.y, fmaf(a.x, b.x, c.x)), fmaf(-a.y, b.x, fmaf(a.x, b.y, c.y))};
+}
+__device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {
+  return double2{fma(a.y, b.y, fma(a.x, b.x, c.x)), fma(-a.y, b.x, fma(a.x, b.y, c.y))};
+}
 template <typename V>
 __device__ __forceinline__ V mul_i(V a) { return V{-a.y, a.x}; }
 template <typename V>

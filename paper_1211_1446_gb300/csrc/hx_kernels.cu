@@ -118,12 +118,32 @@ __device__ __forceinline__ void dirac4(const double2 xv[4], double qx, double qy
           a.y - cz * xv[1].y + (diag_small - shift) * xv[3].y};
 }
 
+// sum_k c_k x_k for four double-float constants c_k = (h, l) and FP32 values x_k: exact FP32
+// products with their rounding errors, two-sum of the leading parts; result as (hi, lo)
+__device__ __forceinline__ dfl dsum4(float c1h, float c1l, float x1, float c2h, float c2l, float x2, float c3h,
+                                     float c3l, float x3, float c4h, float c4l, float x4) {
+  float s = c1h * x1;
+  float r = fmaf(c1l, x1, fmaf(c1h, x1, -s));
+  auto add = [&](float ch, float cl, float x) {
+    const float p = ch * x;
+    const float e = fmaf(cl, x, fmaf(ch, x, -p));
+    const float t = s + p;
+    const float bb = t - s;
+    r += ((s - (t - bb)) + (p - bb)) + e;
+    s = t;
+  };
+  add(c2h, c2l, x2);
+  add(c3h, c3l, x3);
+  add(c4h, c4l, x4);
+  return dfl{s, r};
+}
+
 template <typename Vg, typename V>
 __global__ void __launch_bounds__(256) k_stick_forward(
     const Vg* __restrict__ t, const Vg* __restrict__ x, Vg* __restrict__ out, int npw, int nsticks,
     const int* __restrict__ stick_start, const int* __restrict__ pw_stick, const int* __restrict__ pw_iz,
-    AxisPlan p3, const V* __restrict__ tw3, const double* __restrict__ q, double c, double shift,
-    double scale, int spb, int ls) {
+    AxisPlan p3, const V* __restrict__ tw3, const double* __restrict__ q, const float* __restrict__ cq32,
+    double c, double shift, double scale, int spb, int ls) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* line = reinterpret_cast<V*>(smem_raw);   // 4*spb lines of stride ls (odd)
   const int n3 = p3.n;
@@ -142,6 +162,37 @@ __global__ void __launch_bounds__(256) k_stick_forward(
   fft_lines<V, true>(line, 4 * spb, ls, 1, p3, tw3, true);
   const size_t fo = (size_t)b * 4 * npw;
   const int q0 = stick_start[s0], q1 = stick_start[s0 + ns];
+  if constexpr (std::is_same<Vg, float2>::value && std::is_same<V, float2>::value) {
+    // FP32 blocks: the large components in FP32; the small components, where c s.q x_L and
+    // (2c^2 + shift) x_S nearly cancel, as double-float sums of exact products
+    const double kd = 2.0 * c * c + shift;
+    const float kh = (float)kd, kl = (float)(kd - (double)kh), sh = (float)shift, sc = (float)scale;
+    for (int p = q0 + threadIdx.x; p < q1; p += blockDim.x) {
+      const int s = pw_stick[p] - s0, iz = pw_iz[p];
+      const float2 x0 = x[fo + p], x1 = x[fo + (size_t)npw + p], x2 = x[fo + 2 * (size_t)npw + p],
+                   x3 = x[fo + 3 * (size_t)npw + p];
+      const float* cq = cq32 + 6 * (size_t)p;
+      const float cxh = cq[0], cxl = cq[1], cyh = cq[2], cyl = cq[3], czh = cq[4], czl = cq[5];
+      float2 h[4];
+      h[0] = float2{czh * x2.x + cxh * x3.x + cyh * x3.y - sh * x0.x, czh * x2.y + cxh * x3.y - cyh * x3.x - sh * x0.y};
+      h[1] = float2{cxh * x2.x - cyh * x2.y - czh * x3.x - sh * x1.x, cxh * x2.y + cyh * x2.x - czh * x3.y - sh * x1.y};
+      const dfl h2r = dsum4(czh, czl, x0.x, cxh, cxl, x1.x, cyh, cyl, x1.y, -kh, -kl, x2.x);
+      const dfl h2i = dsum4(czh, czl, x0.y, cxh, cxl, x1.y, -cyh, -cyl, x1.x, -kh, -kl, x2.y);
+      const dfl h3r = dsum4(cxh, cxl, x0.x, -cyh, -cyl, x0.y, -czh, -czl, x1.x, -kh, -kl, x3.x);
+      const dfl h3i = dsum4(cxh, cxl, x0.y, cyh, cyl, x0.x, -czh, -czl, x1.y, -kh, -kl, x3.y);
+      const float2 l2 = line[(2 * spb + s) * ls + iz], l3 = line[(3 * spb + s) * ls + iz];
+      h[2] = float2{h2r.h + (h2r.l + l2.x), h2i.h + (h2i.l + l2.y)};
+      h[3] = float2{h3r.h + (h3r.l + l3.x), h3i.h + (h3i.l + l3.y)};
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const float2 loc = line[(a * spb + s) * ls + iz];
+        h[a] = float2{h[a].x + loc.x, h[a].y + loc.y};
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) out[fo + (size_t)a * npw + p] = float2{sc * h[a].x, sc * h[a].y};
+    }
+    return;
+  }
   const double diag_small = -2.0 * c * c;
   for (int p = q0 + threadIdx.x; p < q1; p += blockDim.x) {
     const int s = pw_stick[p] - s0, iz = pw_iz[p];
@@ -253,7 +304,7 @@ static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int n
       dim3 gc((kp.nsticks + spb_c - 1) / spb_c, nbc);
       k_stick_forward<Vg, Vs><<<gc, 256, sm_c, st>>>(tbuf, xb, out + (size_t)b0 * 4 * npw, npw, kp.nsticks,
                                                      kp.stick_start, kp.pw_stick, kp.pw_iz, ctx->plan[2], tw3,
-                                                     kp.q, ctx->c, shift, scale, spb_c, ls);
+                                                     kp.q, kp.cq32, ctx->c, shift, scale, spb_c, ls);
     }
   }
   DKS_CUDA_TRY(cudaGetLastError());

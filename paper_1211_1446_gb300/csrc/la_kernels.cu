@@ -80,10 +80,10 @@ __global__ void __launch_bounds__(256) k_gemm_hn(const Va* __restrict__ a, int l
     for (int kq = 0; kq < HN_T; ++kq) {
       const A a0 = as[kq][ty], a1 = as[kq][ty + 16];
       const A b0 = bs[kq][tx], b1 = bs[kq][tx + 16];
-      acc[0][0] = cadd(acc[0][0], cmulc(a0, b0));
-      acc[0][1] = cadd(acc[0][1], cmulc(a0, b1));
-      acc[1][0] = cadd(acc[1][0], cmulc(a1, b0));
-      acc[1][1] = cadd(acc[1][1], cmulc(a1, b1));
+      acc[0][0] = cfmac(a0, b0, acc[0][0]);
+      acc[0][1] = cfmac(a0, b1, acc[0][1]);
+      acc[1][0] = cfmac(a1, b0, acc[1][0]);
+      acc[1][1] = cfmac(a1, b1, acc[1][1]);
     }
     if constexpr (fold) {
 #pragma unroll
@@ -142,7 +142,6 @@ int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, dou
                        16.0 * m * n,
           (lower ? 4.0 * m * (m + 1.0) : 8.0 * m * n) * (double)k);
   using A = typename std::conditional<Acc64, double2, typename AccOf<Va, Vb>::T>::type;
-  (void)0;
   k_gemm_hn<Va, Vb, A><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
@@ -207,7 +206,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const Va* __restrict__ a, int l
     for (int mm = 0; mm < NN_M; ++mm) {
       const A av = as[mm][row];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[j] = cadd(acc[j], cmul(av, wsm[mm][cg * 8 + j]));
+      for (int j = 0; j < 8; ++j) acc[j] = cfma(av, wsm[mm][cg * 8 + j], acc[j]);
     }
     __syncthreads();
   }
@@ -229,15 +228,91 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const Va* __restrict__ a, int l
   }
 }
 
+// FP32 operands and output: 256 x 32 output tile per CTA, 4 rows x 8 columns per thread (rows
+// t, t+64, t+128, t+192), so the FP64 -> FP32 conversion of W is amortised over 256 rows and
+// every shared-memory load of W feeds four complex multiply-adds.
+constexpr int NF_R = 256, NF_C = 32, NF_M = 16;
+
+__global__ void __launch_bounds__(256) k_gemm_nn_f32(const float2* __restrict__ a, int lda, int k, int m,
+                                                     const double2* __restrict__ w, int ldw,
+                                                     const double* __restrict__ ws, int n,
+                                                     float2* __restrict__ out, int ldo, double alpha, float beta) {
+  __shared__ float2 as[NF_M][NF_R];
+  __shared__ float2 wsm[NF_M][NF_C];
+  const int r0 = blockIdx.x * NF_R, c0 = blockIdx.y * NF_C;
+  const int rg = threadIdx.x & 63, cg = threadIdx.x >> 6;
+  float2 acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = float2{0.f, 0.f};
+  for (int m0 = 0; m0 < m; m0 += NF_M) {
+    for (int e = threadIdx.x; e < NF_M * NF_R; e += 256) {
+      const int rr = e & (NF_R - 1), mm = e >> 8;
+      float2 v{0.f, 0.f};
+      if (m0 + mm < m && r0 + rr < k) v = a[(size_t)(m0 + mm) * lda + r0 + rr];
+      as[mm][rr] = v;
+    }
+    for (int e = threadIdx.x; e < NF_M * NF_C; e += 256) {
+      const int cc = e & (NF_C - 1), mm = e >> 5;
+      float2 v{0.f, 0.f};
+      if (m0 + mm < m && c0 + cc < n) {
+        const double2 wv = w[(size_t)(c0 + cc) * ldw + m0 + mm];
+        const float s = (float)((ws ? ws[m0 + mm] : 1.0) * alpha);
+        v = float2{(float)wv.x * s, (float)wv.y * s};
+      }
+      wsm[mm][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int mm = 0; mm < NF_M; ++mm) {
+      float2 av[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = as[mm][rg + 64 * i];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float2 wv = wsm[mm][cg * 8 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i][j] = cfma(av[i], wv, acc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = r0 + rg + 64 * i;
+    if (row >= k) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int cc = c0 + cg * 8 + j;
+      if (cc < n) {
+        float2* o = out + (size_t)cc * ldo + row;
+        float2 r = acc[i][j];
+        if (beta != 0.f) {
+          const float2 old = *o;
+          r.x += beta * old.x;
+          r.y += beta * old.y;
+        }
+        *o = r;
+      }
+    }
+  }
+}
+
 template <typename Va, typename Vo>
 int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
             Vo* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
   if (k <= 0 || n <= 0) return DKS_OK;
-  dim3 grid((k + NN_R - 1) / NN_R, (n + NN_C - 1) / NN_C);
   const bool f32 = sizeof(Va) == sizeof(float2) && sizeof(Vo) == sizeof(float2);
   Prof pr(f32 && cat < P_RR ? cat + kProf32 : cat, st, (double)m * k * sizeof(Va) + (beta != 0.0 ? 2.0 : 1.0) * n * k * sizeof(Vo) + 16.0 * m * n,
           8.0 * (double)k * m * n);
-  k_gemm_nn<Va, Vo><<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
+  if constexpr (std::is_same<Va, float2>::value && std::is_same<Vo, float2>::value) {
+    dim3 grid((k + NF_R - 1) / NF_R, (n + NF_C - 1) / NF_C);
+    k_gemm_nn_f32<<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, (float)beta);
+  } else {
+    dim3 grid((k + NN_R - 1) / NN_R, (n + NN_C - 1) / NN_C);
+    k_gemm_nn<Va, Vo><<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
+  }
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
