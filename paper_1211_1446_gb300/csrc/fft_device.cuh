@@ -61,8 +61,8 @@ __device__ __forceinline__ double2 cneg(double2 a) { return double2{-a.x, -a.y};
 __device__ __forceinline__ cdf cneg(cdf a) { return cdf{df_neg(a.re), df_neg(a.im)}; }
 
 // a * exp(i sg 2 pi k / R), sg = -1 for the forward direction
-template <int R, int K, typename V>
-__device__ __forceinline__ V mul_root(V a, bool fwd) {
+template <int R, int K, bool fwd, typename V>
+__device__ __forceinline__ V mul_root(V a) {
   if constexpr (K == 0) {
     return a;
   } else if constexpr (4 * K == R) {
@@ -84,13 +84,13 @@ __device__ __forceinline__ void sfor(F&& f) {
 }
 
 // ------------------------------------------------------------------ small DFTs, y = DFT_R(x)
-template <typename V, int R>
-__device__ __forceinline__ void dft(const V* x, V* y, bool fwd);
+template <typename V, int R, bool fwd>
+__device__ __forceinline__ void dft(const V* x, V* y);
 
 // odd R: pairs a_r = x_r + x_{R-r}, b_r = x_r - x_{R-r};
 // y_m, y_{R-m} = x_0 + sum_r a_r cos(2 pi r m / R) +- i sg sum_r b_r sin(2 pi r m / R)
-template <typename V, int R>
-__device__ __forceinline__ void dft_odd(const V* x, V* y, bool fwd) {
+template <typename V, int R, bool fwd>
+__device__ __forceinline__ void dft_odd(const V* x, V* y) {
   constexpr int H = (R - 1) / 2;
   V a[H], b[H];
   V y0 = x[0];
@@ -125,31 +125,31 @@ __device__ __forceinline__ void dft_odd(const V* x, V* y, bool fwd) {
 
 // R = P Q, n = Q n1 + n2, k = k1 + P k2:
 // y[k1 + P k2] = sum_n2 w_Q^(n2 k2) [ w_R^(n2 k1) sum_n1 x[Q n1 + n2] w_P^(n1 k1) ]
-template <typename V, int P, int Q>
-__device__ __forceinline__ void dft_split(const V* x, V* y, bool fwd) {
+template <typename V, int P, int Q, bool fwd>
+__device__ __forceinline__ void dft_split(const V* x, V* y) {
   constexpr int R = P * Q;
   V a[Q][P];
   sfor<0, Q>([&](auto n2c) {
     constexpr int n2 = decltype(n2c)::value;
     V in[P];
     sfor<0, P>([&](auto n1c) { in[decltype(n1c)::value] = x[Q * decltype(n1c)::value + n2]; });
-    dft<V, P>(in, a[n2], fwd);
+    dft<V, P, fwd>(in, a[n2]);
     sfor<1, P>([&](auto k1c) {
       constexpr int k1 = decltype(k1c)::value;
-      a[n2][k1] = mul_root<R, n2 * k1>(a[n2][k1], fwd);
+      a[n2][k1] = mul_root<R, n2 * k1, fwd>(a[n2][k1]);
     });
   });
   sfor<0, P>([&](auto k1c) {
     constexpr int k1 = decltype(k1c)::value;
     V in[Q], out[Q];
     sfor<0, Q>([&](auto n2c) { in[decltype(n2c)::value] = a[decltype(n2c)::value][k1]; });
-    dft<V, Q>(in, out, fwd);
+    dft<V, Q, fwd>(in, out);
     sfor<0, Q>([&](auto k2c) { y[k1 + P * decltype(k2c)::value] = out[decltype(k2c)::value]; });
   });
 }
 
-template <typename V, int R>
-__device__ __forceinline__ void dft(const V* x, V* y, bool fwd) {
+template <typename V, int R, bool fwd>
+__device__ __forceinline__ void dft(const V* x, V* y) {
   if constexpr (R == 1) {
     y[0] = x[0];
   } else if constexpr (R == 2) {
@@ -164,12 +164,12 @@ __device__ __forceinline__ void dft(const V* x, V* y, bool fwd) {
     y[1] = cadd(b, di);
     y[3] = csub(b, di);
   } else if constexpr (R == 6) {
-    dft_split<V, 2, 3>(x, y, fwd);
+    dft_split<V, 2, 3, fwd>(x, y);
   } else if constexpr (R == 8) {
-    dft_split<V, 2, 4>(x, y, fwd);
+    dft_split<V, 2, 4, fwd>(x, y);
   } else {
     static_assert(R == 3 || R == 5 || R == 7, "unsupported radix");
-    dft_odd<V, R>(x, y, fwd);
+    dft_odd<V, R, fwd>(x, y);
   }
 }
 
@@ -182,9 +182,9 @@ __device__ __forceinline__ int qdiv(int a, int b, float rb) {
   return q;
 }
 
-template <typename V, int R, bool DIT>
+template <typename V, int R, bool DIT, bool fwd>
 __device__ __forceinline__ void fft_pass(V* buf, int nlines, int lstride, int estride, int n, int L,
-                                         const V* __restrict__ tw, bool fwd) {
+                                         const V* __restrict__ tw) {
   const int S = L / R;
   const int per_line = n / R;
   const int total = nlines * per_line;
@@ -204,7 +204,7 @@ __device__ __forceinline__ void fft_pass(V* buf, int nlines, int lstride, int es
 #pragma unroll
       for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle(tw, j * r * tstep, fwd));
     }
-    dft<V, R>(x, y, fwd);
+    dft<V, R, fwd>(x, y);
     if (!DIT && j) {
 #pragma unroll
       for (int m = 1; m < R; ++m) y[m] = cmul(y[m], twiddle(tw, j * m * tstep, fwd));
@@ -216,20 +216,20 @@ __device__ __forceinline__ void fft_pass(V* buf, int nlines, int lstride, int es
 
 // all passes of one axis over nlines lines (element i of line l at buf[l*lstride + i*estride]);
 // DIF passes in plan order, DIT passes in reverse order
-template <typename V, bool DIT>
+template <typename V, bool DIT, bool fwd>
 __device__ void fft_lines(V* buf, int nlines, int lstride, int estride, const AxisPlan& p,
-                          const V* __restrict__ tw, bool fwd) {
+                          const V* __restrict__ tw) {
   for (int i = 0; i < p.nst; ++i) {
     const int s = DIT ? (p.nst - 1 - i) : i;
     const int L = p.blk[s];
     switch (p.radix[s]) {
-      case 2: fft_pass<V, 2, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
-      case 3: fft_pass<V, 3, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
-      case 4: fft_pass<V, 4, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
-      case 5: fft_pass<V, 5, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
-      case 6: fft_pass<V, 6, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
-      case 7: fft_pass<V, 7, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
-      default: fft_pass<V, 8, DIT>(buf, nlines, lstride, estride, p.n, L, tw, fwd); break;
+      case 2: fft_pass<V, 2, DIT, fwd>(buf, nlines, lstride, estride, p.n, L, tw); break;
+      case 3: fft_pass<V, 3, DIT, fwd>(buf, nlines, lstride, estride, p.n, L, tw); break;
+      case 4: fft_pass<V, 4, DIT, fwd>(buf, nlines, lstride, estride, p.n, L, tw); break;
+      case 5: fft_pass<V, 5, DIT, fwd>(buf, nlines, lstride, estride, p.n, L, tw); break;
+      case 6: fft_pass<V, 6, DIT, fwd>(buf, nlines, lstride, estride, p.n, L, tw); break;
+      case 7: fft_pass<V, 7, DIT, fwd>(buf, nlines, lstride, estride, p.n, L, tw); break;
+      default: fft_pass<V, 8, DIT, fwd>(buf, nlines, lstride, estride, p.n, L, tw); break;
     }
     __syncthreads();
   }

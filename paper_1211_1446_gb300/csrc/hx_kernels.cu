@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) k_stick_inverse(
   for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x)
     line[(pw_stick[q] - s0) * ls + pw_iz[q]] = to_s<V>(xf[q]);
   __syncthreads();
-  fft_lines<V, false>(line, ns, ls, 1, p3, tw3, false);
+  fft_lines<V, false, false>(line, ns, ls, 1, p3, tw3);
   Vg* tf = t + (size_t)f * n3 * nsticks;
   const float rns = __fdividef(1.0f, (float)ns);
   for (int e = threadIdx.x; e < ns * n3; e += blockDim.x) {
@@ -87,13 +87,13 @@ __global__ void __launch_bounds__(512) k_plane(Vg* __restrict__ t, int nsticks,
   Vg* row = t + ((size_t)f * n3 + z) * nsticks;
   for (int s = threadIdx.x; s < nsticks; s += blockDim.x) plane[stick_plane[s]] = to_s<V>(row[s]);
   __syncthreads();
-  fft_lines<V, false>(plane, n1, ld, 1, p2, tw2, false);   // along axis 2 (contiguous)
-  fft_lines<V, false>(plane, n2, 1, ld, p1, tw1, false);   // along axis 1
+  fft_lines<V, false, false>(plane, n1, ld, 1, p2, tw2);   // along axis 2 (contiguous)
+  fft_lines<V, false, false>(plane, n2, 1, ld, p1, tw1);   // along axis 1
   const typename RealOf<V>::T* vz = vperm + (size_t)z * np;   // zero in the padding column
   for (int e = threadIdx.x; e < np; e += blockDim.x) plane[e] = cscale(plane[e], vz[e]);
   __syncthreads();
-  fft_lines<V, true>(plane, n2, 1, ld, p1, tw1, true);
-  fft_lines<V, true>(plane, n1, ld, 1, p2, tw2, true);
+  fft_lines<V, true, true>(plane, n2, 1, ld, p1, tw1);
+  fft_lines<V, true, true>(plane, n1, ld, 1, p2, tw2);
   for (int s = threadIdx.x; s < nsticks; s += blockDim.x) row[s] = to_g(plane[stick_plane[s]]);
 }
 
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(256) k_stick_forward(
     }
   }
   __syncthreads();
-  fft_lines<V, true>(line, 4 * spb, ls, 1, p3, tw3, true);
+  fft_lines<V, true, true>(line, 4 * spb, ls, 1, p3, tw3);
   const size_t fo = (size_t)b * 4 * npw;
   const int q0 = stick_start[s0], q1 = stick_start[s0 + ns];
   if constexpr (std::is_same<Vg, float2>::value && std::is_same<V, float2>::value) {
@@ -269,12 +269,13 @@ static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int n
   const size_t sm_a = (size_t)spb_a * ls * sizeof(Vs);
   const size_t sm_b = (size_t)ctx->grid[0] * ld * sizeof(Vs);
   const size_t sm_c = (size_t)4 * spb_c * ls * sizeof(Vs);
-  // threads of the plane kernel: the largest pass has N1 N2 / (smallest radix) butterflies
+  // threads of the plane kernel: the largest pass has N1 N2 / (smallest radix) butterflies;
   int rmin = 8;
   for (int a = 0; a < 2; ++a)
     for (int i = 0; i < ctx->plan[a].nst; ++i) rmin = std::min(rmin, ctx->plan[a].radix[i]);
+  // two butterflies per thread and pass (independent work for latency hiding, more CTAs per SM)
   const int nbf = ctx->grid[0] * ctx->grid[1] / rmin;
-  const int tb_plane = std::min(512, std::max(128, (nbf + 31) / 32 * 32));
+  const int tb_plane = std::min(512, std::max(128, (nbf / 2 + 31) / 32 * 32));
   DKS_TRY(set_smem<Vs>((const void*)k_stick_inverse<Vg, Vs>, sm_a));
   DKS_TRY(set_smem<Vs>((const void*)k_plane<Vg, Vs>, sm_b));
   DKS_TRY(set_smem<Vs>((const void*)k_stick_forward<Vg, Vs>, sm_c));
