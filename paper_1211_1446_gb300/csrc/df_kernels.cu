@@ -6,9 +6,10 @@
 // split on load into hi = fl32(x) and lo = fl32(x - hi) (48 significant bits), products use the
 // error-free transformation p = hi_a*hi_b, e = fma(hi_a, hi_b, -p) plus the two cross terms, and
 // sums are kept as unevaluated pairs with Knuth's two-sum followed by a fast renormalisation
-// (Dekker / Knuth error-free transformations).  Each real multiply-add costs ~15 FP32
-// instructions, about 4x the FP64 rate on this part, with ~2^-48 relative rounding per step
-// (FP64: 2^-53).  Inputs and outputs stay complex128.
+// (Dekker / Knuth error-free transformations).  The fast renormalisation of an accumulator runs
+// after every 8 of its updates instead of after each: a real multiply-add costs 12 FP32
+// instructions plus 3/8, about 5x the FP64 rate on this part, with rounding at the 2^-46..2^-48
+// level relative to the accumulated sums (FP64: 2^-53).  Inputs and outputs stay complex128.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,19 +28,23 @@ __device__ __forceinline__ gdf df_split(double x) {
   return gdf{h, (float)(x - (double)h)};
 }
 
-// s += a * b (all double-float); renormalised after the update
-__device__ __forceinline__ void df_mac(gdf& s, const gdf a, const gdf b) {
+// s += a * b without the final renormalisation: the leading part takes the exact two-sum, the
+// error terms collect in s.lo; callers renormalise every few updates (df_renorm), which keeps
+// |s.lo| within a few ulps of s.hi
+__device__ __forceinline__ void df_mac_nr(gdf& s, const gdf a, const gdf b) {
   const float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);          // exact error of the leading product
+  float e = fmaf(a.hi, b.hi, -p);
   e = fmaf(a.hi, b.lo, e);
   e = fmaf(a.lo, b.hi, e);
-  const float t = s.hi + p;                // two-sum of the leading parts
+  const float t = s.hi + p;
   const float bb = t - s.hi;
-  const float err = (s.hi - (t - bb)) + (p - bb);
-  const float lo = err + (s.lo + e);
-  const float hi = t + lo;                 // fast two-sum renormalisation (|t| >= |lo|)
-  s.lo = lo - (hi - t);
-  s.hi = hi;
+  s.lo += ((s.hi - (t - bb)) + (p - bb)) + e;
+  s.hi = t;
+}
+__device__ __forceinline__ void df_renorm(gdf& s) {
+  const float h = s.hi + s.lo;
+  s.lo = s.lo - (h - s.hi);
+  s.hi = h;
 }
 
 __device__ __forceinline__ gdf df_neg(gdf a) { return gdf{-a.hi, -a.lo}; }
@@ -50,27 +55,40 @@ struct gcdf {   // complex double-float
 };
 
 __device__ __forceinline__ gcdf gcdf_split(double2 v) { return gcdf{df_split(v.x), df_split(v.y)}; }
-
-// acc += conj(a) * b
-__device__ __forceinline__ void cdf_macc(gcdf& acc, const gcdf& a, const gcdf& b) {
-  df_mac(acc.re, a.re, b.re);
-  df_mac(acc.re, a.im, b.im);
-  df_mac(acc.im, a.re, b.im);
-  df_mac(acc.im, df_neg(a.im), b.re);
+// operand element as double-float: split a complex128 value, or take a pre-split (re hi, re lo,
+// im hi, im lo) quadruple as it is
+__device__ __forceinline__ gcdf ld_df(const double2* p, size_t i) { return gcdf_split(p[i]); }
+__device__ __forceinline__ gcdf ld_df(const float4* p, size_t i) {
+  const float4 v = p[i];
+  return gcdf{{v.x, v.y}, {v.z, v.w}};
 }
-// acc += a * b
+template <typename T> __device__ __forceinline__ gcdf zero_df() { return gcdf{{0.f, 0.f}, {0.f, 0.f}}; }
+
+// acc += conj(a) * b  (unnormalised, see df_mac_nr)
+__device__ __forceinline__ void cdf_macc(gcdf& acc, const gcdf& a, const gcdf& b) {
+  df_mac_nr(acc.re, a.re, b.re);
+  df_mac_nr(acc.re, a.im, b.im);
+  df_mac_nr(acc.im, a.re, b.im);
+  df_mac_nr(acc.im, df_neg(a.im), b.re);
+}
+// acc += a * b  (unnormalised)
 __device__ __forceinline__ void cdf_mac(gcdf& acc, const gcdf& a, const gcdf& b) {
-  df_mac(acc.re, a.re, b.re);
-  df_mac(acc.re, df_neg(a.im), b.im);
-  df_mac(acc.im, a.re, b.im);
-  df_mac(acc.im, a.im, b.re);
+  df_mac_nr(acc.re, a.re, b.re);
+  df_mac_nr(acc.re, df_neg(a.im), b.im);
+  df_mac_nr(acc.im, a.re, b.im);
+  df_mac_nr(acc.im, a.im, b.re);
+}
+__device__ __forceinline__ void cdf_renorm(gcdf& acc) {
+  df_renorm(acc.re);
+  df_renorm(acc.im);
 }
 
 // ---------------------------------------------------------------- C += A^H B
 constexpr int DHN_T = 32;
 
-__global__ void __launch_bounds__(256) k_gemm_hn_df(const double2* __restrict__ a, int lda,
-                                                    const double2* __restrict__ b, int ldb, int k, int m, int n,
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(256) k_gemm_hn_df(const TA* __restrict__ a, int lda,
+                                                    const TB* __restrict__ b, int ldb, int k, int m, int n,
                                                     int mt, int kchunk, double2* __restrict__ c, int ldc,
                                                     int lower) {
   __shared__ gcdf as[DHN_T][DHN_T + 1];
@@ -99,23 +117,29 @@ __global__ void __launch_bounds__(256) k_gemm_hn_df(const double2* __restrict__ 
     for (int e = threadIdx.x; e < DHN_T * DHN_T; e += 256) {
       const int kq = e & (DHN_T - 1), q = e >> 5;
       const int gk = k0 + kq;
-      double2 va{0, 0}, vb{0, 0};
+      gcdf va = zero_df<TA>(), vb = zero_df<TB>();
       if (gk < ke) {
-        if (m0 + q < m) va = a[(size_t)(m0 + q) * lda + gk];
-        if (n0 + q < n) vb = b[(size_t)(n0 + q) * ldb + gk];
+        if (m0 + q < m) va = ld_df(a, (size_t)(m0 + q) * lda + gk);
+        if (n0 + q < n) vb = ld_df(b, (size_t)(n0 + q) * ldb + gk);
       }
-      as[kq][q] = gcdf_split(va);
-      bs[kq][q] = gcdf_split(vb);
+      as[kq][q] = va;
+      bs[kq][q] = vb;
     }
     __syncthreads();
-#pragma unroll 4
-    for (int kq = 0; kq < DHN_T; ++kq) {
-      const gcdf a0 = as[kq][ty], a1 = as[kq][ty + 16];
-      const gcdf b0 = bs[kq][tx], b1 = bs[kq][tx + 16];
-      cdf_macc(acc[0][0], a0, b0);
-      cdf_macc(acc[0][1], a0, b1);
-      cdf_macc(acc[1][0], a1, b0);
-      cdf_macc(acc[1][1], a1, b1);
+    for (int kq0 = 0; kq0 < DHN_T; kq0 += 4) {
+#pragma unroll
+      for (int kq = kq0; kq < kq0 + 4; ++kq) {
+        const gcdf a0 = as[kq][ty], a1 = as[kq][ty + 16];
+        const gcdf b0 = bs[kq][tx], b1 = bs[kq][tx + 16];
+        cdf_macc(acc[0][0], a0, b0);
+        cdf_macc(acc[0][1], a0, b1);
+        cdf_macc(acc[1][0], a1, b0);
+        cdf_macc(acc[1][1], a1, b1);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) cdf_renorm(acc[i][j]);   // every 8 updates of each part
     }
     __syncthreads();
   }
@@ -142,8 +166,9 @@ static int df_num_sms() {
   return n;
 }
 
-int gemm_hn_df(const double2* a, int lda, const double2* b, int ldb, int k, int m, int n, double2* c,
-               cudaStream_t st, int cat, int ldc, bool lower) {
+template <typename TA, typename TB>
+static int gemm_hn_df_t(const TA* a, int lda, const TB* b, int ldb, int k, int m, int n, double2* c,
+                        cudaStream_t st, int cat, int ldc, bool lower) {
   if (m <= 0 || n <= 0 || k <= 0) return DKS_OK;
   if (ldc <= 0) ldc = m;
   if (lower && m != n) return fail(DKS_ERR_INVALID_ARG, "gemm_hn_df: lower-triangle mode needs a square result");
@@ -158,9 +183,18 @@ int gemm_hn_df(const double2* a, int lda, const double2* b, int ldb, int k, int 
   const bool same = (const void*)a == (const void*)b;
   Prof pr(cat, st, (same ? (double)m : (double)(m + n)) * k * 16.0 + 16.0 * m * n,
           (lower ? 4.0 * m * (m + 1.0) : 8.0 * m * n) * (double)k);
-  k_gemm_hn_df<<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
+  k_gemm_hn_df<TA, TB><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
+}
+
+int gemm_hn_df(const double2* a, int lda, const double2* b, int ldb, int k, int m, int n, double2* c,
+               cudaStream_t st, int cat, int ldc, bool lower) {
+  return gemm_hn_df_t(a, lda, b, ldb, k, m, n, c, st, cat, ldc, lower);
+}
+int gemm_hn_df(const float4* a, int lda, const float4* b, int ldb, int k, int m, int n, double2* c,
+               cudaStream_t st, int cat, int ldc, bool lower) {
+  return gemm_hn_df_t(a, lda, b, ldb, k, m, n, c, st, cat, ldc, lower);
 }
 
 // ---------------------------------------------------------------- OUT = alpha A diag(ws) W + beta OUT
@@ -168,7 +202,8 @@ int gemm_hn_df(const double2* a, int lda, const double2* b, int ldb, int k, int 
 // into double-float pairs is amortised over 128 rows.
 constexpr int DNN_R = 128, DNN_C = 32, DNN_M = 16;
 
-__global__ void __launch_bounds__(256, 1) k_gemm_nn_df(const double2* __restrict__ a, int lda, int k, int m,
+template <typename TA>
+__global__ void __launch_bounds__(256, 1) k_gemm_nn_df(const TA* __restrict__ a, int lda, int k, int m,
                                                     const double2* __restrict__ w, int ldw,
                                                     const double* __restrict__ ws, int n,
                                                     double2* __restrict__ out, int ldo, double alpha, double beta) {
@@ -184,9 +219,9 @@ __global__ void __launch_bounds__(256, 1) k_gemm_nn_df(const double2* __restrict
   for (int m0 = 0; m0 < m; m0 += DNN_M) {
     for (int e = threadIdx.x; e < DNN_M * DNN_R; e += 256) {
       const int rr = e & (DNN_R - 1), mm = e >> 7;
-      double2 v{0, 0};
-      if (m0 + mm < m && r0 + rr < k) v = a[(size_t)(m0 + mm) * lda + r0 + rr];
-      as[mm][rr] = gcdf_split(v);
+      gcdf v = zero_df<TA>();
+      if (m0 + mm < m && r0 + rr < k) v = ld_df(a, (size_t)(m0 + mm) * lda + r0 + rr);
+      as[mm][rr] = v;
     }
     for (int e = threadIdx.x; e < DNN_M * DNN_C; e += 256) {
       const int cc = e & (DNN_C - 1), mm = e >> 5;
@@ -200,15 +235,21 @@ __global__ void __launch_bounds__(256, 1) k_gemm_nn_df(const double2* __restrict
       wsm[mm][cc] = gcdf_split(v);
     }
     __syncthreads();
+    for (int mm0 = 0; mm0 < DNN_M; mm0 += 4) {
 #pragma unroll 2
-    for (int mm = 0; mm < DNN_M; ++mm) {
-      const gcdf a0 = as[mm][rg], a1 = as[mm][rg + 64];
+      for (int mm = mm0; mm < mm0 + 4; ++mm) {
+        const gcdf a0 = as[mm][rg], a1 = as[mm][rg + 64];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const gcdf wv = wsm[mm][cg * 8 + j];
-        cdf_mac(acc[0][j], a0, wv);
-        cdf_mac(acc[1][j], a1, wv);
+        for (int j = 0; j < 8; ++j) {
+          const gcdf wv = wsm[mm][cg * 8 + j];
+          cdf_mac(acc[0][j], a0, wv);
+          cdf_mac(acc[1][j], a1, wv);
+        }
       }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cdf_renorm(acc[i][j]);   // every 8 updates of each part
     }
     __syncthreads();
   }
@@ -233,13 +274,62 @@ __global__ void __launch_bounds__(256, 1) k_gemm_nn_df(const double2* __restrict
   }
 }
 
-int gemm_nn_df(const double2* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
-               double2* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
+template <typename TA>
+static int gemm_nn_df_t(const TA* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
+                        int n, double2* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
   if (k <= 0 || n <= 0) return DKS_OK;
   dim3 grid((k + DNN_R - 1) / DNN_R, (n + DNN_C - 1) / DNN_C);
   Prof pr(cat, st, (double)m * k * 16.0 + (beta != 0.0 ? 2.0 : 1.0) * n * k * 16.0 + 16.0 * m * n,
           8.0 * (double)k * m * n);
-  k_gemm_nn_df<<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
+  k_gemm_nn_df<TA><<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
+}
+
+int gemm_nn_df(const double2* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
+               double2* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
+  return gemm_nn_df_t(a, lda, k, m, w, ldw, wscale, n, out, ldo, beta, st, alpha, cat);
+}
+int gemm_nn_df(const float4* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
+               double2* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
+  return gemm_nn_df_t(a, lda, k, m, w, ldw, wscale, n, out, ldo, beta, st, alpha, cat);
+}
+
+// ---------------------------------------------------------------- split complex128 -> double-float
+// Integer operations only: hi = the value with its mantissa truncated to 24 bits, lo = the
+// remaining 29 bits converted to FP32 (rounded), so hi + lo equals the value to 2^-47 relative.
+// Zero and magnitudes outside [2^-74, 2^127) take the FP64 conversions.  A block is split once
+// and then read by every contraction of the iteration.
+__device__ __forceinline__ void split_bits(double x, float& h, float& l) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi32 = (unsigned)(u >> 32), lo32 = (unsigned)u;
+  const int e = (int)((hi32 >> 20) & 0x7ffu);
+  if (e < 949 || e > 1149) {
+    h = (float)x;
+    l = (float)(x - (double)h);
+    return;
+  }
+  const unsigned sign = hi32 & 0x80000000u;
+  h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29));
+  const float lv = __uint2float_rn(lo32 & 0x1fffffffu) * __uint_as_float((unsigned)(e - 948) << 23);
+  l = sign ? -lv : lv;
+}
+
+__global__ void k_split_df(const double2* __restrict__ in, float4* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = in[i];
+    float4 o;
+    split_bits(v.x, o.x, o.y);
+    split_bits(v.y, o.z, o.w);
+    out[i] = o;
+  }
+}
+
+int split_df(const double2* in, float4* out, size_t n, cudaStream_t st) {
+  if (!n) return DKS_OK;
+  Prof pr(P_MISC, st, 32.0 * n, 0.0);
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)df_num_sms() * 16);
+  k_split_df<<<blocks, 256, 0, st>>>(in, out, n);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }

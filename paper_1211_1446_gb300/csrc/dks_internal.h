@@ -171,6 +171,13 @@ int gemm_hn_df(const double2* a, int lda, const double2* b, int ldb, int k, int 
 int gemm_nn_df(const double2* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
                int n, double2* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0,
                int cat = P_ROTATE);
+// the same with operands already split into (re hi, re lo, im hi, im lo) quadruples
+int gemm_hn_df(const float4* a, int lda, const float4* b, int ldb, int k, int m, int n, double2* c,
+               cudaStream_t st, int cat = P_GRAM, int ldc = 0, bool lower = false);
+int gemm_nn_df(const float4* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
+               int n, double2* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0,
+               int cat = P_ROTATE);
+int split_df(const double2* in, float4* out, size_t n, cudaStream_t st);
 template <typename Va, typename Vo = Va>
 int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
             int n, Vo* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0,

@@ -8,6 +8,8 @@
 //   HY = H' Y                                                     (one H' pass)
 //   A = Z^H HZ, S = Z^H Z, FP64 Rayleigh-Ritz, first n pairs      (lines 11-14)
 //   X, HX <- Z V, HZ V into the other buffer                       (line 15)
+//   (emulated FP64: Z and HZ are split into double-float copies once, before the Gram matrices,
+//    and the Gram and rotation kernels read the copies)
 //   column norms of HX - X Lambda (FP64), host reads them          (lines 16-19)
 //   P, HP <- [0, Y, P] V_active, HZ likewise                        (lines 20-22)
 // so H' is applied 3 times per active column per iteration (Sec. 3.2).
@@ -38,6 +40,10 @@ struct Blocks {
   V* z[2];
   V* hz[2];
   V* tmp;
+  // double-float copies of Z and HZ (emulated-FP64 phase): split once per iteration, read by
+  // the Gram matrices and all four rotations
+  float4* zdf = nullptr;
+  float4* hzdf = nullptr;
 };
 
 struct Small {
@@ -113,6 +119,15 @@ static int gram(const V* z, const V* hz, int rows, int nz, Small& sm, cudaStream
   DKS_TRY(mirror_lower(sm.a, nz, st));
   return mirror_lower(sm.s, nz, st);
 }
+// the same from double-float copies of Z and HZ
+static int gram_split(const float4* z, const float4* hz, int rows, int nz, Small& sm, cudaStream_t st) {
+  DKS_CUDA_TRY(cudaMemsetAsync(sm.a, 0, (size_t)nz * nz * sizeof(double2), st));
+  DKS_CUDA_TRY(cudaMemsetAsync(sm.s, 0, (size_t)nz * nz * sizeof(double2), st));
+  DKS_TRY(gemm_hn_df(z, rows, hz, rows, rows, nz, nz, sm.a, st, P_GRAM, 0, true));
+  DKS_TRY(gemm_hn_df(z, rows, z, rows, rows, nz, nz, sm.s, st, P_GRAM, 0, true));
+  DKS_TRY(mirror_lower(sm.a, nz, st));
+  return mirror_lower(sm.s, nz, st);
+}
 
 // reads lam and residual statistics of the n columns; returns the host residual norms
 static int fetch(Small& sm, Pinned& pin, int n, std::vector<double>& res, cudaStream_t st) {
@@ -146,11 +161,26 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
   // line 4-6: Rayleigh-Ritz on X0
   DKS_TRY(apply_h<V>(ctx, ex, ik, b.z[cur], b.hz[cur], n, 0.0, 1.0, st));
   happ += n;
-  DKS_TRY(gram<V>(b.z[cur], b.hz[cur], rows, n, sm, st, df));
+  // Gram matrices and rotations of nz columns of Z, HZ (from double-float copies when present)
+  const bool split = df && b.zdf && b.hzdf;
+  auto gram_z = [&](int nzc) -> int {
+    if (!split) return gram<V>(b.z[cur], b.hz[cur], rows, nzc, sm, st, df);
+    DKS_TRY(split_df((const double2*)b.z[cur], b.zdf, (size_t)nzc * colsz, st));
+    DKS_TRY(split_df((const double2*)b.hz[cur], b.hzdf, (size_t)nzc * colsz, st));
+    return gram_split(b.zdf, b.hzdf, rows, nzc, sm, st);
+  };
+  // out <- Z[c0:c0+m] W (h: from HZ instead of Z)
+  auto rotate = [&](bool h, size_t c0, int m, const double2* w, int ldw, int ncol, V* outp) -> int {
+    if (split)
+      return gemm_nn_df((h ? b.hzdf : b.zdf) + c0 * colsz, rows, rows, m, w, ldw, nullptr, ncol, (double2*)outp,
+                        rows, 0.0, st);
+    return nn<V>(df, (h ? b.hz[cur] : b.z[cur]) + c0 * colsz, rows, rows, m, w, ldw, ncol, outp, rows, st);
+  };
+  DKS_TRY(gram_z(n));
   DKS_TRY(rayleigh_ritz(sm.a, sm.s, n, n, sm.vm, sm.lam, sm.info, sm.rrs, st, chol_tol, drop_tol));
   int nx = cur ^ 1;
-  DKS_TRY(nn<V>(df, b.z[cur], rows, rows, n, sm.vm, n, n, b.z[nx], rows, st));
-  DKS_TRY(nn<V>(df, b.hz[cur], rows, rows, n, sm.vm, n, n, b.hz[nx], rows, st));
+  DKS_TRY(rotate(false, 0, n, sm.vm, n, n, b.z[nx]));
+  DKS_TRY(rotate(true, 0, n, sm.vm, n, n, b.hz[nx]));
   cur = nx;
   DKS_TRY(col_stats<V>(b.z[cur], b.hz[cur], sm.lam, kp.ek, kp.npw, n, sm.stats, st));
   std::vector<double> res;
@@ -179,11 +209,11 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
     DKS_TRY(apply_h<V>(ctx, ex, ik, y, hy, a, 0.0, 1.0, st));
     happ += a;
     const int nz = n + a + p;
-    DKS_TRY(gram<V>(b.z[cur], b.hz[cur], rows, nz, sm, st, df));
+    DKS_TRY(gram_z(nz));
     DKS_TRY(rayleigh_ritz(sm.a, sm.s, nz, n, sm.vm, sm.lam, sm.info, sm.rrs, st, chol_tol, drop_tol));
     nx = cur ^ 1;
-    DKS_TRY(nn<V>(df, b.z[cur], rows, rows, nz, sm.vm, nz, n, b.z[nx], rows, st));
-    DKS_TRY(nn<V>(df, b.hz[cur], rows, rows, nz, sm.vm, nz, n, b.hz[nx], rows, st));
+    DKS_TRY(rotate(false, 0, nz, sm.vm, nz, n, b.z[nx]));
+    DKS_TRY(rotate(true, 0, nz, sm.vm, nz, n, b.hz[nx]));
     DKS_TRY(col_stats<V>(b.z[nx], b.hz[nx], sm.lam, kp.ek, kp.npw, n, sm.stats, st));
     DKS_TRY(fetch(sm, pin, n, res, st));
     if (pin.info[1] < n) return fail(DKS_ERR_RANK, "Rayleigh-Ritz subspace rank below the block size");
@@ -217,8 +247,8 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
     DKS_TRY(gather_cols(sm.vm, nz, n, nz - n, sm.act, a2, sm.vp, st));
     V* pz = b.z[nx] + (size_t)(n + a2) * colsz;
     V* phz = b.hz[nx] + (size_t)(n + a2) * colsz;
-    DKS_TRY(nn<V>(df, b.z[cur] + (size_t)n * colsz, rows, rows, nz - n, sm.vp, nz - n, a2, pz, rows, st));
-    DKS_TRY(nn<V>(df, b.hz[cur] + (size_t)n * colsz, rows, rows, nz - n, sm.vp, nz - n, a2, phz, rows, st));
+    DKS_TRY(rotate(false, (size_t)n, nz - n, sm.vp, nz - n, a2, pz));
+    DKS_TRY(rotate(true, (size_t)n, nz - n, sm.vp, nz - n, a2, phz));
     // the Teter factor of the next iteration needs statistics of the new X (already in sm.stats)
     cur = nx;
     act.swap(act2);
@@ -295,7 +325,8 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
   const size_t nz = 3 * nmax;
   const size_t small = (2 * nz * nz + 2 * nz * nmax + rr_scratch_elems((int)nz)) * sizeof(double2) +
                        (nmax + 3 * nmax) * sizeof(double) + (nmax + 4) * sizeof(int) + 16 * 256;
-  const size_t total = 4 * big64 + tmp64 + 4 * big32 + tmp32 + small + 16 * 256;
+  const bool split_copies = mixed && opts.emulate_fp64 != 0;
+  const size_t total = 4 * big64 + tmp64 + 4 * big32 + tmp32 + small + (split_copies ? 2 * big64 : 0) + 16 * 256;
   // concurrent k-point workers, each with its own stream and workspace (bounded by free memory)
   int nworkers = opts.concurrency > 0 ? opts.concurrency : std::min(ctx->nk, 4);
   nworkers = std::max(1, std::min(nworkers, ctx->nk));
@@ -345,6 +376,10 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
     b64.hz[0] = (double2*)take(big64);
     b64.hz[1] = (double2*)take(big64);
     b64.tmp = (double2*)take(tmp64);
+    if (split_copies) {
+      b64.zdf = (float4*)take(big64);
+      b64.hzdf = (float4*)take(big64);
+    }
     if (mixed) {
       b32.z[0] = (float2*)take(big32);
       b32.z[1] = (float2*)take(big32);
