@@ -93,6 +93,40 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// double-float helpers for the distributed Householder steps
+__device__ __forceinline__ dfl dd_fma(dfl x, dfl y, dfl acc) {   // acc + x y
+  const float p = x.h * y.h;
+  float e = fmaf(x.h, y.h, -p);
+  e = fmaf(x.h, y.l, e);
+  e = fmaf(x.l, y.h, e);
+  const float t = acc.h + p;
+  const float bb = t - acc.h;
+  const float lo = ((acc.h - (t - bb)) + (p - bb)) + (acc.l + e);
+  const float h = t + lo;
+  return dfl{h, lo - (h - t)};
+}
+__device__ __forceinline__ cdf cdf0() { return cdf{{0.f, 0.f}, {0.f, 0.f}}; }
+__device__ __forceinline__ cdf ucdf(float4 v) { return cdf{{v.x, v.y}, {v.z, v.w}}; }
+__device__ __forceinline__ float4 c4(cdf c) { return float4{c.re.h, c.re.l, c.im.h, c.im.l}; }
+__device__ __forceinline__ float4 c4(double2 v) { return c4(cdf{df_from(v.x), df_from(v.y)}); }
+__device__ __forceinline__ cdf cdf_fmac(cdf a, cdf b, cdf acc) {   // acc + conj(a) b
+  acc.re = dd_fma(a.re, b.re, acc.re);
+  acc.re = dd_fma(a.im, b.im, acc.re);
+  acc.im = dd_fma(a.re, b.im, acc.im);
+  acc.im = dd_fma(df_neg(a.im), b.re, acc.im);
+  return acc;
+}
+__device__ __forceinline__ dfl warp_dsum(dfl v) {
+  for (int o = 16; o; o >>= 1)
+    v = df_add(v, dfl{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)});
+  return v;
+}
+__device__ __forceinline__ cdf warp_cdsum(cdf v) {
+  v.re = warp_dsum(v.re);
+  v.im = warp_dsum(v.im);
+  return v;
+}
+
 // number of eigenvalues of the real symmetric tridiagonal (d, e) below x (Sturm count): the
 // negative pivots of the LDL^T factorisation of T - x I, each pivot kept away from zero
 __device__ int sturm_count_f(const float* d, const float* e2, int m, float x, float pivmin) {
@@ -377,56 +411,66 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
   cl.sync();
   // 4. Householder reduction of cm to a complex tridiagonal.
   // Distributed form (when the staging area holds this CTA's share of the columns): column j
-  // lives in the shared memory of CTA j % csize.  Step k (reflector v of column k, rows > k):
+  // lives in the shared memory of CTA j % csize, as double-float (re hi, re lo, im hi, im lo).
+  // Step k (reflector v of column k, rows > k):
   //   A  every CTA copies v and tau from the owner of column k (DSMEM)
   //   B  p_i = tau C[:, i]^H v for the owned columns i > k (Hermitian C: p = tau C v) and the
   //      partial sum of conj(v_i) p_i
   //   -- cluster barrier --
   //   C  K = tau/2 sum of the partials, w = p - K v (p gathered from the owners)
   //   D  owned columns j > k: C[:, j] -= v conj(w_j) + w conj(v_j)
-  //   E  the owner of column k+1 forms the next reflector
+  //   E  the owner of column k+1 forms the next reflector (FP64 from the double-float column)
   //   -- cluster barrier --
-  // The reflectors stay in their columns (first element replaced by v0), as in the global form.
+  // B-D run in double-float arithmetic on the FP32 lanes (about 2^-47 per operation): in FP64
+  // they were bound by the FP64 pipe of each SM.  The reflectors stay in their columns (first
+  // element replaced by v0), as in the global form.
   const int ncol_own = (m + csize - 1) / csize;
   if (m >= 3 && scols >= ncol_own) {
-    double2* cb = stg;                                       // owned columns, column j at (j / csize) * m
-    double2* vl = reinterpret_cast<double2*>(rrc_smem);      // v of the current step, by row
-    double2* wf = vl + m;                                    // w, by row
-    double2* pb = wf + m;                                    // p at the owned indices (read by the cluster)
-    double2* bc = pb + m;                                    // 2 x (m + 1): reflector + tau, by parity
-    double2* kp = bc + 2 * (m + 1);                          // this CTA's partial of v^H p
-    double2* kw = kp + 1;                                    // per-warp partials
-    __shared__ double2 hk;                                   // K of the current step
+    float4* cb = reinterpret_cast<float4*>(stg);             // owned columns, column j at (j / csize) * m
+    float4* vl = reinterpret_cast<float4*>(rrc_smem);        // v of the current step, by row
+    float4* wf = vl + m;                                     // w, by row
+    float4* pb = wf + m;                                     // p at the owned indices (read by the cluster)
+    float4* bc = pb + m;                                     // 2 x (m + 1): reflector + tau, by parity
+    float4* kp = bc + 2 * (m + 1);                           // this CTA's partial of v^H p
+    float4* kw = kp + 1;                                     // per-warp partials
+    __shared__ float4 hk;                                    // K of the current step
     for (int e = tid; e < ncol_own * m; e += RRC_THREADS) {
       const int lj = e / m, r = e - lj * m, j = lj * csize + crank;
-      if (j < m) cb[e] = cm[(size_t)j * m + r];
+      if (j < m) cb[e] = c4(cm[(size_t)j * m + r]);
     }
     __syncthreads();
     // reflector of column k by warp 0 of its owner: broadcast buffer, v0 into the column, tau/ph
     auto make_reflector = [&](int k) {
-      double2* x = cb + (size_t)(k / csize) * m + k + 1;
+      float4* x = cb + (size_t)(k / csize) * m + k + 1;
       const int len = m - k - 1;
-      double a2 = 0;
-      for (int i = lane; i < len; i += 32) a2 += x[i].x * x[i].x + x[i].y * x[i].y;
-      a2 = warp_sum(a2);
-      const double2 x0 = x[0];
+      dfl a2{0.f, 0.f};
+      for (int i = lane; i < len; i += 32) {
+        const cdf xi = ucdf(x[i]);
+        a2 = dd_fma(xi.re, xi.re, a2);
+        a2 = dd_fma(xi.im, xi.im, a2);
+      }
+      a2 = warp_dsum(a2);
+      const double a2d = df_val(a2);
+      const cdf x0c = ucdf(x[0]);
+      const double2 x0 = double2{df_val(x0c.re), df_val(x0c.im)};
       const double ax0 = nr_hypot(x0.x, x0.y);
-      const double alpha = nr_sqrt(a2);
+      const double alpha = nr_sqrt(a2d);
       double t = 0.0;
       double2 beta = x0, v0 = x0;
-      if (alpha > 1e-300 && a2 - ax0 * ax0 > 1e-30 * a2) {
+      if (alpha > 1e-300 && a2d - ax0 * ax0 > 1e-30 * a2d) {
         const double ri = ax0 > 0 ? nr_rcp(ax0) : 0.0;
         const double2 phs = ax0 > 0 ? double2{x0.x * ri, x0.y * ri} : double2{1, 0};
         beta = double2{-phs.x * alpha, -phs.y * alpha};
         v0 = double2{x0.x - beta.x, x0.y - beta.y};
-        t = 2.0 * nr_rcp(a2 - ax0 * ax0 + v0.x * v0.x + v0.y * v0.y);
+        t = 2.0 * nr_rcp(a2d - ax0 * ax0 + v0.x * v0.x + v0.y * v0.y);
       }
-      double2* out = bc + (size_t)(k & 1) * (m + 1);
-      for (int i = lane; i < len; i += 32) out[k + 1 + i] = i == 0 ? v0 : x[i];
+      float4* out = bc + (size_t)(k & 1) * (m + 1);
+      const float4 v04 = c4(v0);
+      for (int i = lane; i < len; i += 32) out[k + 1 + i] = i == 0 ? v04 : x[i];
       __syncwarp();
       if (lane == 0) {
-        out[m] = double2{t, 0.0};
-        if (t != 0.0) x[0] = v0;
+        out[m] = c4(double2{t, 0.0});
+        if (t != 0.0) x[0] = v04;
         tau[k] = double2{t, 0.0};
         ph[k] = beta;
       }
@@ -436,44 +480,44 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
     for (int k = 0; k + 2 < m; ++k) {
       const int len = m - k - 1;
       // A
-      const double2* src = cl.map_shared_rank(bc + (size_t)(k & 1) * (m + 1), (unsigned)(k % csize));
+      const float4* src = cl.map_shared_rank(bc + (size_t)(k & 1) * (m + 1), (unsigned)(k % csize));
       for (int r = k + 1 + tid; r <= m; r += RRC_THREADS) vl[r == m ? 0 : r] = src[r];   // vl[0] <- tau
       __syncthreads();
-      const double t = vl[0].x;
+      const dfl t = ucdf(vl[0]).re;
       // B
       const int lj0 = (k + 1 - crank + csize - 1) / csize;   // first owned column > k
-      double2 kacc{0, 0};
+      cdf kacc = cdf0();
       for (int lj = lj0 + wl; lj < ncol_own; lj += RRC_WARPS) {
         const int i = lj * csize + crank;
         if (i >= m) break;
-        const double2* ci = cb + (size_t)lj * m;
-        double2 sacc{0, 0};
-        for (int r = k + 1 + lane; r < m; r += 32) sacc = cadd(sacc, cmulc(ci[r], vl[r]));
-        sacc = warp_csum(sacc);
-        const double2 p = double2{t * sacc.x, t * sacc.y};
-        if (lane == 0) pb[i] = p;
-        kacc = cadd(kacc, cmulc(vl[i], p));
+        const float4* ci = cb + (size_t)lj * m;
+        cdf sacc = cdf0();
+        for (int r = k + 1 + lane; r < m; r += 32) sacc = cdf_fmac(ucdf(ci[r]), ucdf(vl[r]), sacc);
+        sacc = warp_cdsum(sacc);
+        const cdf p = cdf{df_mul(t, sacc.re), df_mul(t, sacc.im)};
+        if (lane == 0) pb[i] = c4(p);
+        kacc = cdf_fmac(ucdf(vl[i]), p, kacc);
       }
-      if (lane == 0) kw[wl] = kacc;
+      if (lane == 0) kw[wl] = c4(kacc);
       __syncthreads();
-      if (tid == 0) {
-        double2 ks{0, 0};
-        for (int w = 0; w < RRC_WARPS; ++w) ks = cadd(ks, kw[w]);
-        kp[0] = ks;
+      if (wl == 0) {
+        cdf ks = lane < RRC_WARPS ? ucdf(kw[lane]) : cdf0();
+        ks = warp_cdsum(ks);
+        if (lane == 0) kp[0] = c4(ks);
       }
       cl.sync();
       // C
       if (wl == 0) {
-        double2 ks{0, 0};
-        if (lane < csize) ks = *cl.map_shared_rank(kp, (unsigned)lane);
-        ks = warp_csum(ks);
-        if (lane == 0) hk = double2{0.5 * t * ks.x, 0.5 * t * ks.y};
+        cdf ks = lane < csize ? ucdf(*cl.map_shared_rank(kp, (unsigned)lane)) : cdf0();
+        ks = warp_cdsum(ks);
+        const dfl ht = df_mul(t, dfl{0.5f, 0.f});
+        if (lane == 0) hk = c4(cdf{df_mul(ht, ks.re), df_mul(ht, ks.im)});
       }
       __syncthreads();
-      const double2 kv = hk;
+      const cdf kv = ucdf(hk);
       for (int r = k + 1 + tid; r < m; r += RRC_THREADS) {
-        const double2 p = *cl.map_shared_rank(pb + r, (unsigned)(r % csize));
-        wf[r] = csub(p, cmul(kv, vl[r]));
+        const cdf p = ucdf(*cl.map_shared_rank(pb + r, (unsigned)(r % csize)));
+        wf[r] = c4(csub(p, cmul(kv, ucdf(vl[r]))));
       }
       __syncthreads();
       // D
@@ -482,11 +526,19 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
         const int q = e / len, r = k + 1 + (e - q * len);
         const int lj = lj0 + q, j = lj * csize + crank;
         if (j >= m) continue;
-        const double2 vr = vl[r], wr = wf[r], vj = vl[j], wj = wf[j];
-        const double2 u1 = cmul(vr, double2{wj.x, -wj.y});
-        const double2 u2 = cmul(wr, double2{vj.x, -vj.y});
-        double2* cjr = cb + (size_t)lj * m + r;
-        *cjr = csub(*cjr, cadd(u1, u2));
+        const cdf vr = ucdf(vl[r]), wr = ucdf(wf[r]), vj = ucdf(vl[j]), wj = ucdf(wf[j]);
+        float4* cjr = cb + (size_t)lj * m + r;
+        cdf c = ucdf(*cjr);
+        // c -= vr conj(wj) + wr conj(vj)
+        c.re = dd_fma(df_neg(vr.re), wj.re, c.re);
+        c.re = dd_fma(df_neg(vr.im), wj.im, c.re);
+        c.re = dd_fma(df_neg(wr.re), vj.re, c.re);
+        c.re = dd_fma(df_neg(wr.im), vj.im, c.re);
+        c.im = dd_fma(df_neg(vr.im), wj.re, c.im);
+        c.im = dd_fma(vr.re, wj.im, c.im);
+        c.im = dd_fma(df_neg(wr.im), vj.re, c.im);
+        c.im = dd_fma(wr.re, vj.im, c.im);
+        *cjr = c4(c);
       }
       __syncthreads();
       // E
@@ -495,7 +547,10 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
     }
     for (int e = tid; e < ncol_own * m; e += RRC_THREADS) {
       const int lj = e / m, r = e - lj * m, j = lj * csize + crank;
-      if (j < m) cm[(size_t)j * m + r] = cb[e];
+      if (j < m) {
+        const cdf c = ucdf(cb[e]);
+        cm[(size_t)j * m + r] = double2{df_val(c.re), df_val(c.im)};
+      }
     }
     cl.sync();
   } else {
