@@ -44,6 +44,8 @@ struct Blocks {
   // the Gram matrices and all four rotations
   float4* zdf = nullptr;
   float4* hzdf = nullptr;
+  // FP32 phase: copy of the X with the lowest residual so far (the FP64 phase starts from it)
+  V* best = nullptr;
 };
 
 struct Small {
@@ -189,7 +191,7 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
   std::vector<int> act;
   for (int j = 0; j < n; ++j) act.push_back(j);   // line 9 uses every column of R first
   int p = 0;
-  double best = INFINITY;
+  double best = INFINITY, lowest = INFINITY;
   int since_best = 0;
   bool converged = false;
   int it = 0;
@@ -228,12 +230,20 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
     }
     if (stop_on_stall) {
       // FP32 phase: stop at its rounding floor -- no 30% gain in 3 iterations, or a jump above
-      // twice the best residual (FP32 noise reaching the negative band)
+      // twice the best residual (FP32 noise reaching the negative band).  The phase hands on
+      // the X with the lowest residual seen, not the last one.
+      if (b.best && maxres < lowest) {
+        lowest = maxres;
+        DKS_CUDA_TRY(cudaMemcpyAsync(b.best, b.z[nx], (size_t)n * colsz * sizeof(V), cudaMemcpyDeviceToDevice, st));
+      }
       if (maxres < 0.7 * best) {
         best = maxres;
         since_best = 0;
       } else if (++since_best >= 3 || maxres > 2.0 * best) {
         cur = nx;
+        if (b.best)
+          DKS_CUDA_TRY(cudaMemcpyAsync(b.z[cur], b.best, (size_t)n * colsz * sizeof(V), cudaMemcpyDeviceToDevice,
+                                       st));
         break;
       }
     }
@@ -326,7 +336,7 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
   const size_t small = (2 * nz * nz + 2 * nz * nmax + rr_scratch_elems((int)nz)) * sizeof(double2) +
                        (nmax + 3 * nmax) * sizeof(double) + (nmax + 4) * sizeof(int) + 16 * 256;
   const bool split_copies = mixed && opts.emulate_fp64 != 0;
-  const size_t total = 4 * big64 + tmp64 + 4 * big32 + tmp32 + small + (split_copies ? 2 * big64 : 0) + 16 * 256;
+  const size_t total = 4 * big64 + tmp64 + 4 * big32 + 2 * tmp32 + small + (split_copies ? 2 * big64 : 0) + 16 * 256;
   // concurrent k-point workers, each with its own stream and workspace (bounded by free memory)
   int nworkers = opts.concurrency > 0 ? opts.concurrency : std::min(ctx->nk, 4);
   nworkers = std::max(1, std::min(nworkers, ctx->nk));
@@ -386,6 +396,7 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
       b32.hz[0] = (float2*)take(big32);
       b32.hz[1] = (float2*)take(big32);
       b32.tmp = (float2*)take(tmp32);
+      b32.best = (float2*)take(tmp32);
     }
     Small sm;
     sm.a = (double2*)take(nz * nz * sizeof(double2));
