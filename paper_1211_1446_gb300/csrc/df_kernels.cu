@@ -198,18 +198,20 @@ int gemm_hn_df(const float4* a, int lda, const float4* b, int ldb, int k, int m,
 }
 
 // ---------------------------------------------------------------- OUT = alpha A diag(ws) W + beta OUT
-// 128 x 32 output tile per CTA, 2 rows x 8 columns per thread (rows t and t+64): the split of W
-// into double-float pairs is amortised over 128 rows.
-constexpr int DNN_R = 128, DNN_C = 32, DNN_M = 16;
+// 128 rows x (8 * ncg) columns per CTA (ncg <= 5 column groups, sized to the number of output
+// columns), 2 rows x 8 columns per thread (rows t and t+64): the split of W into double-float
+// pairs is amortised over 128 rows.
+constexpr int DNN_R = 128, DNN_GMAX = 5, DNN_CMAX = 8 * DNN_GMAX, DNN_M = 16;
 
 template <typename TA>
-__global__ void __launch_bounds__(256, 1) k_gemm_nn_df(const TA* __restrict__ a, int lda, int k, int m,
-                                                    const double2* __restrict__ w, int ldw,
-                                                    const double* __restrict__ ws, int n,
-                                                    double2* __restrict__ out, int ldo, double alpha, double beta) {
+__global__ void __launch_bounds__(64 * DNN_GMAX, 1) k_gemm_nn_df(const TA* __restrict__ a, int lda, int k, int m,
+                                                       const double2* __restrict__ w, int ldw,
+                                                       const double* __restrict__ ws, int n,
+                                                       double2* __restrict__ out, int ldo, double alpha, double beta) {
   __shared__ gcdf as[DNN_M][DNN_R];
-  __shared__ gcdf wsm[DNN_M][DNN_C];
-  const int r0 = blockIdx.x * DNN_R, c0 = blockIdx.y * DNN_C;
+  __shared__ gcdf wsm[DNN_M][DNN_CMAX];
+  const int ncols = (blockDim.x >> 6) * 8;
+  const int r0 = blockIdx.x * DNN_R, c0 = blockIdx.y * ncols;
   const int rg = threadIdx.x & 63, cg = threadIdx.x >> 6;
   gcdf acc[2][8];
 #pragma unroll
@@ -217,14 +219,14 @@ __global__ void __launch_bounds__(256, 1) k_gemm_nn_df(const TA* __restrict__ a,
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = gcdf{{0.f, 0.f}, {0.f, 0.f}};
   for (int m0 = 0; m0 < m; m0 += DNN_M) {
-    for (int e = threadIdx.x; e < DNN_M * DNN_R; e += 256) {
+    for (int e = threadIdx.x; e < DNN_M * DNN_R; e += blockDim.x) {
       const int rr = e & (DNN_R - 1), mm = e >> 7;
       gcdf v = zero_df<TA>();
       if (m0 + mm < m && r0 + rr < k) v = ld_df(a, (size_t)(m0 + mm) * lda + r0 + rr);
       as[mm][rr] = v;
     }
-    for (int e = threadIdx.x; e < DNN_M * DNN_C; e += 256) {
-      const int cc = e & (DNN_C - 1), mm = e >> 5;
+    for (int e = threadIdx.x; e < DNN_M * ncols; e += blockDim.x) {
+      const int mm = e / ncols, cc = e - mm * ncols;
       double2 v{0, 0};
       if (m0 + mm < m && c0 + cc < n) {
         v = w[(size_t)(c0 + cc) * ldw + m0 + mm];
@@ -278,10 +280,13 @@ template <typename TA>
 static int gemm_nn_df_t(const TA* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
                         int n, double2* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
   if (k <= 0 || n <= 0) return DKS_OK;
-  dim3 grid((k + DNN_R - 1) / DNN_R, (n + DNN_C - 1) / DNN_C);
+  // column groups of 8 per CTA: the fewest CTAs along n, then the smallest tile covering them
+  const int tiles = (n + 8 * DNN_GMAX - 1) / (8 * DNN_GMAX);
+  const int g = std::max(1, ((n + tiles - 1) / tiles + 7) / 8);
+  dim3 grid((k + DNN_R - 1) / DNN_R, tiles);
   Prof pr(cat, st, (double)m * k * 16.0 + (beta != 0.0 ? 2.0 : 1.0) * n * k * 16.0 + 16.0 * m * n,
           8.0 * (double)k * m * n);
-  k_gemm_nn_df<TA><<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
+  k_gemm_nn_df<TA><<<grid, 64 * g, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }

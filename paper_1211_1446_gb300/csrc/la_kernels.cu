@@ -228,18 +228,20 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const Va* __restrict__ a, int l
   }
 }
 
-// FP32 operands and output: 256 x 32 output tile per CTA, 4 rows x 8 columns per thread (rows
-// t, t+64, t+128, t+192), so the FP64 -> FP32 conversion of W is amortised over 256 rows and
-// every shared-memory load of W feeds four complex multiply-adds.
-constexpr int NF_R = 256, NF_C = 32, NF_M = 16;
+// FP32 operands and output: 256 rows x (8 * ncg) columns per CTA (ncg <= 5 column groups, sized
+// to the number of output columns so that no column of the tile is padding), one thread per
+// 4 rows (t, t+64, t+128, t+192) x 8 columns; the FP64 -> FP32 conversion of W is amortised
+// over 256 rows and every shared-memory load of W feeds four complex multiply-adds.
+constexpr int NF_R = 256, NF_GMAX = 5, NF_CMAX = 8 * NF_GMAX, NF_M = 16;
 
-__global__ void __launch_bounds__(256) k_gemm_nn_f32(const float2* __restrict__ a, int lda, int k, int m,
+__global__ void __launch_bounds__(64 * NF_GMAX) k_gemm_nn_f32(const float2* __restrict__ a, int lda, int k, int m,
                                                      const double2* __restrict__ w, int ldw,
                                                      const double* __restrict__ ws, int n,
                                                      float2* __restrict__ out, int ldo, double alpha, float beta) {
   __shared__ float2 as[NF_M][NF_R];
-  __shared__ float2 wsm[NF_M][NF_C];
-  const int r0 = blockIdx.x * NF_R, c0 = blockIdx.y * NF_C;
+  __shared__ float2 wsm[NF_M][NF_CMAX];
+  const int ncols = (blockDim.x >> 6) * 8;
+  const int r0 = blockIdx.x * NF_R, c0 = blockIdx.y * ncols;
   const int rg = threadIdx.x & 63, cg = threadIdx.x >> 6;
   float2 acc[4][8];
 #pragma unroll
@@ -247,14 +249,14 @@ __global__ void __launch_bounds__(256) k_gemm_nn_f32(const float2* __restrict__ 
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = float2{0.f, 0.f};
   for (int m0 = 0; m0 < m; m0 += NF_M) {
-    for (int e = threadIdx.x; e < NF_M * NF_R; e += 256) {
+    for (int e = threadIdx.x; e < NF_M * NF_R; e += blockDim.x) {
       const int rr = e & (NF_R - 1), mm = e >> 8;
       float2 v{0.f, 0.f};
       if (m0 + mm < m && r0 + rr < k) v = a[(size_t)(m0 + mm) * lda + r0 + rr];
       as[mm][rr] = v;
     }
-    for (int e = threadIdx.x; e < NF_M * NF_C; e += 256) {
-      const int cc = e & (NF_C - 1), mm = e >> 5;
+    for (int e = threadIdx.x; e < NF_M * ncols; e += blockDim.x) {
+      const int mm = e / ncols, cc = e - mm * ncols;
       float2 v{0.f, 0.f};
       if (m0 + mm < m && c0 + cc < n) {
         const double2 wv = w[(size_t)(c0 + cc) * ldw + m0 + mm];
@@ -299,6 +301,14 @@ __global__ void __launch_bounds__(256) k_gemm_nn_f32(const float2* __restrict__ 
   }
 }
 
+// column groups of 8 per CTA for n output columns: the fewest CTAs along n, then the
+// smallest tile that covers n / (number of column tiles)
+static int col_groups(int n, int maxg) {
+  const int tiles = (n + 8 * maxg - 1) / (8 * maxg);
+  const int per = (n + tiles - 1) / tiles;
+  return std::max(1, (per + 7) / 8);
+}
+
 template <typename Va, typename Vo>
 int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
             Vo* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
@@ -307,8 +317,9 @@ int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const
   Prof pr(f32 && cat < P_RR ? cat + kProf32 : cat, st, (double)m * k * sizeof(Va) + (beta != 0.0 ? 2.0 : 1.0) * n * k * sizeof(Vo) + 16.0 * m * n,
           8.0 * (double)k * m * n);
   if constexpr (std::is_same<Va, float2>::value && std::is_same<Vo, float2>::value) {
-    dim3 grid((k + NF_R - 1) / NF_R, (n + NF_C - 1) / NF_C);
-    k_gemm_nn_f32<<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, (float)beta);
+    const int g = col_groups(n, NF_GMAX);
+    dim3 grid((k + NF_R - 1) / NF_R, (n + NF_CMAX - 1) / NF_CMAX);
+    k_gemm_nn_f32<<<grid, 64 * g, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, (float)beta);
   } else {
     dim3 grid((k + NN_R - 1) / NN_R, (n + NN_C - 1) / NN_C);
     k_gemm_nn<Va, Vo><<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
