@@ -736,12 +736,14 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
   cl.sync();
   RR_MARK(4);
   // 6. inverse iteration; clusters of close eigenvalues go to one lane in order.  Warps that own
-  // a shared-memory slot (nslots per CTA) take the cluster starts round-robin.
+  // a shared-memory slot (nslots per CTA) take the cluster starts round-robin over the CTAs first
+  // (a lone FP64 lane still occupies its SM's FP64 pipe for a whole warp instruction, so chains
+  // sharing an SM slow each other down).
   const double ortol = 1e-7 * fmax(tnorm, 1e-300);
   const int nslots = min(RRC_WARPS, (int)(rr_tri_smem_offset(m) / (sizeof(double) * 6 * (size_t)m)));
   double* fws = reinterpret_cast<double*>(rrc_smem);   // per-slot 5m factors + m vector
   if (wl < nslots && lane == 0) {
-    const int gslot = crank * nslots + wl, nslot_all = csize * nslots;
+    const int gslot = wl * csize + crank, nslot_all = csize * nslots;
     for (int start = gslot; start < n; start += nslot_all) {
       const bool begins = start == 0 || lamw[start] - lamw[start - 1] > ortol;
       if (!begins) continue;
