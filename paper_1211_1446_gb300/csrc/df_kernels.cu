@@ -86,12 +86,14 @@ __device__ __forceinline__ void cdf_renorm(gcdf& acc) {
 // ---------------------------------------------------------------- C += A^H B
 constexpr int DHN_T = 32;
 
-template <typename TA, typename TB>
+// RM = 2: 32 x 32 tiles of C; RM = 3: 48 x 32 tiles (less padding when m is just above 32)
+template <typename TA, typename TB, int RM>
 __global__ void __launch_bounds__(256) k_gemm_hn_df(const TA* __restrict__ a, int lda,
                                                     const TB* __restrict__ b, int ldb, int k, int m, int n,
                                                     int mt, int kchunk, double2* __restrict__ c, int ldc,
                                                     int lower) {
-  __shared__ gcdf as[DHN_T][DHN_T + 1];
+  constexpr int TM = 16 * RM;
+  __shared__ gcdf as[DHN_T][TM + 1];
   __shared__ gcdf bs[DHN_T][DHN_T + 1];
   int tm, tn;
   if (lower) {
@@ -104,47 +106,51 @@ __global__ void __launch_bounds__(256) k_gemm_hn_df(const TA* __restrict__ a, in
     tm = blockIdx.x % mt;
     tn = blockIdx.x / mt;
   }
-  const int m0 = tm * DHN_T, n0 = tn * DHN_T;
+  const int m0 = tm * TM, n0 = tn * DHN_T;
   const int kb = blockIdx.y * kchunk;
   const int ke = min(k, kb + kchunk);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  gcdf acc[2][2];
+  gcdf acc[RM][2];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < RM; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) acc[i][j] = gcdf{{0.f, 0.f}, {0.f, 0.f}};
   for (int k0 = kb; k0 < ke; k0 += DHN_T) {
+    for (int e = threadIdx.x; e < DHN_T * TM; e += 256) {
+      const int kq = e & (DHN_T - 1), q = e >> 5;
+      const int gk = k0 + kq;
+      gcdf va = zero_df<TA>();
+      if (gk < ke && m0 + q < m) va = ld_df(a, (size_t)(m0 + q) * lda + gk);
+      as[kq][q] = va;
+    }
     for (int e = threadIdx.x; e < DHN_T * DHN_T; e += 256) {
       const int kq = e & (DHN_T - 1), q = e >> 5;
       const int gk = k0 + kq;
-      gcdf va = zero_df<TA>(), vb = zero_df<TB>();
-      if (gk < ke) {
-        if (m0 + q < m) va = ld_df(a, (size_t)(m0 + q) * lda + gk);
-        if (n0 + q < n) vb = ld_df(b, (size_t)(n0 + q) * ldb + gk);
-      }
-      as[kq][q] = va;
+      gcdf vb = zero_df<TB>();
+      if (gk < ke && n0 + q < n) vb = ld_df(b, (size_t)(n0 + q) * ldb + gk);
       bs[kq][q] = vb;
     }
     __syncthreads();
     for (int kq0 = 0; kq0 < DHN_T; kq0 += 4) {
 #pragma unroll
       for (int kq = kq0; kq < kq0 + 4; ++kq) {
-        const gcdf a0 = as[kq][ty], a1 = as[kq][ty + 16];
         const gcdf b0 = bs[kq][tx], b1 = bs[kq][tx + 16];
-        cdf_macc(acc[0][0], a0, b0);
-        cdf_macc(acc[0][1], a0, b1);
-        cdf_macc(acc[1][0], a1, b0);
-        cdf_macc(acc[1][1], a1, b1);
+#pragma unroll
+        for (int i = 0; i < RM; ++i) {
+          const gcdf ai = as[kq][ty + 16 * i];
+          cdf_macc(acc[i][0], ai, b0);
+          cdf_macc(acc[i][1], ai, b1);
+        }
       }
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
+      for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int j = 0; j < 2; ++j) cdf_renorm(acc[i][j]);   // every 8 updates of each part
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < RM; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int mm = m0 + ty + 16 * i, nn = n0 + tx + 16 * j;
@@ -172,7 +178,9 @@ static int gemm_hn_df_t(const TA* a, int lda, const TB* b, int ldb, int k, int m
   if (m <= 0 || n <= 0 || k <= 0) return DKS_OK;
   if (ldc <= 0) ldc = m;
   if (lower && m != n) return fail(DKS_ERR_INVALID_ARG, "gemm_hn_df: lower-triangle mode needs a square result");
-  const int mt = (m + DHN_T - 1) / DHN_T, nt = (n + DHN_T - 1) / DHN_T;
+  const bool rm3 = !lower && (m + 47) / 48 * 48 < (m + 31) / 32 * 32;
+  const int tmr = rm3 ? 48 : DHN_T;
+  const int mt = (m + tmr - 1) / tmr, nt = (n + DHN_T - 1) / DHN_T;
   const int tiles = lower ? mt * (mt + 1) / 2 : mt * nt;
   const int ktiles = (k + DHN_T - 1) / DHN_T;
   int splits = std::max(1, (4 * df_num_sms()) / tiles);
@@ -183,7 +191,10 @@ static int gemm_hn_df_t(const TA* a, int lda, const TB* b, int ldb, int k, int m
   const bool same = (const void*)a == (const void*)b;
   Prof pr(cat, st, (same ? (double)m : (double)(m + n)) * k * 16.0 + 16.0 * m * n,
           (lower ? 4.0 * m * (m + 1.0) : 8.0 * m * n) * (double)k);
-  k_gemm_hn_df<TA, TB><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
+  if (rm3)
+    k_gemm_hn_df<TA, TB, 3><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
+  else
+    k_gemm_hn_df<TA, TB, 2><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
@@ -193,6 +204,10 @@ int gemm_hn_df(const double2* a, int lda, const double2* b, int ldb, int k, int 
   return gemm_hn_df_t(a, lda, b, ldb, k, m, n, c, st, cat, ldc, lower);
 }
 int gemm_hn_df(const float4* a, int lda, const float4* b, int ldb, int k, int m, int n, double2* c,
+               cudaStream_t st, int cat, int ldc, bool lower) {
+  return gemm_hn_df_t(a, lda, b, ldb, k, m, n, c, st, cat, ldc, lower);
+}
+int gemm_hn_df(const float4* a, int lda, const double2* b, int ldb, int k, int m, int n, double2* c,
                cudaStream_t st, int cat, int ldc, bool lower) {
   return gemm_hn_df_t(a, lda, b, ldb, k, m, n, c, st, cat, ldc, lower);
 }

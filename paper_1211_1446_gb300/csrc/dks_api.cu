@@ -253,6 +253,12 @@ static int build_k(dks_ctx* ctx, const double kfrac[3], double ecut, const dks_p
     }
     DKS_TRY(upload(&kp.bt64, bt.data(), bt.size()));
     DKS_TRY(upload(&kp.bt32, bt32.data(), bt32.size()));
+    std::vector<float4> btd(bt.size());
+    for (size_t e = 0; e < bt.size(); ++e) {
+      const float rh = (float)bt[e].x, ih = (float)bt[e].y;
+      btd[e] = float4{rh, (float)(bt[e].x - (double)rh), ih, (float)(bt[e].y - (double)ih)};
+    }
+    DKS_TRY(upload(&kp.btdf, btd.data(), btd.size()));
   }
   // default filter constants (shifted units)
   const double c = ctx->c;
@@ -284,6 +290,7 @@ static void free_ctx(dks_ctx* ctx) {
     cudaFree(kp.ek);
     cudaFree(kp.bt64);
     cudaFree(kp.bt32);
+    cudaFree(kp.btdf);
   }
   for (Exec* e : ctx->exec) {
     release(e->ws_h);

@@ -63,6 +63,7 @@ struct KPoint {
   double* ek = nullptr;         // npw, |k+G|^2/2
   double2* bt64 = nullptr;      // nproj x (2 npw) projector rows (beta, spin-major)
   float2* bt32 = nullptr;
+  float4* btdf = nullptr;       // the same rows as double-float (re hi, re lo, im hi, im lo)
   double cshift = 0, omega = 1; // default filter constants
 };
 
@@ -173,6 +174,8 @@ int gemm_nn_df(const double2* a, int lda, int k, int m, const double2* w, int ld
                int cat = P_ROTATE);
 // the same with operands already split into (re hi, re lo, im hi, im lo) quadruples
 int gemm_hn_df(const float4* a, int lda, const float4* b, int ldb, int k, int m, int n, double2* c,
+               cudaStream_t st, int cat = P_GRAM, int ldc = 0, bool lower = false);
+int gemm_hn_df(const float4* a, int lda, const double2* b, int ldb, int k, int m, int n, double2* c,
                cudaStream_t st, int cat = P_GRAM, int ldc = 0, bool lower = false);
 int gemm_nn_df(const float4* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
                int n, double2* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0,

@@ -336,8 +336,8 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
     DKS_CUDA_TRY(cudaMemsetAsync(zp, 0, zp_elems * sizeof(double2), st));
     // Z = B^H x~ : (nproj x 2npw) (2npw x 2nb)
     if (fp64 && ex.df_gemm)
-      DKS_TRY(gemm_hn_df((const double2*)bt, 2 * npw, (const double2*)x, 2 * npw, 2 * npw, ctx->nproj, 2 * nb, zp,
-                         st, P_PROJ_HN));
+      DKS_TRY(gemm_hn_df(kp.btdf, 2 * npw, (const double2*)x, 2 * npw, 2 * npw, ctx->nproj, 2 * nb, zp, st,
+                         P_PROJ_HN));
     else
       DKS_TRY(gemm_hn<V>(bt, 2 * npw, x, 2 * npw, 2 * npw, ctx->nproj, 2 * nb, zp, st, P_PROJ_HN));
   }
@@ -359,7 +359,7 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
   if (ctx->nproj) {
     // out~ += B (scale D Z)
     if (fp64 && ex.df_gemm)
-      DKS_TRY(gemm_nn_df((const double2*)bt, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, 2 * nb,
+      DKS_TRY(gemm_nn_df(kp.btdf, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, 2 * nb,
                          (double2*)out, 2 * npw, 1.0, st, scale, P_PROJ_NN));
     else
       DKS_TRY(gemm_nn<V>(bt, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, 2 * nb, out, 2 * npw,

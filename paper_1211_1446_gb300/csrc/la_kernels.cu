@@ -37,11 +37,13 @@ template <> __device__ __forceinline__ float2 cvt<float2>(float2 v) { return v; 
 // ---------------------------------------------------------------- gemm_hn
 constexpr int HN_T = 32;
 
-template <typename Va, typename Vb, typename A>
+// RM = 2: 32 x 32 tiles of C; RM = 3: 48 x 32 tiles (less padding when m is just above 32)
+template <typename Va, typename Vb, typename A, int RM>
 __global__ void __launch_bounds__(256) k_gemm_hn(const Va* __restrict__ a, int lda, const Vb* __restrict__ b,
                                                  int ldb, int k, int m, int n, int mt, int kchunk,
                                                  double2* __restrict__ c, int ldc, int lower) {
-  __shared__ A as[HN_T][HN_T + 1];
+  constexpr int TM = 16 * RM;
+  __shared__ A as[HN_T][TM + 1];
   __shared__ A bs[HN_T][HN_T + 1];
   int tm, tn;
   if (lower) {   // only tiles with tn <= tm (the block lower triangle of a Hermitian result)
@@ -54,40 +56,46 @@ __global__ void __launch_bounds__(256) k_gemm_hn(const Va* __restrict__ a, int l
     tm = blockIdx.x % mt;
     tn = blockIdx.x / mt;
   }
-  const int m0 = tm * HN_T, n0 = tn * HN_T;
+  const int m0 = tm * TM, n0 = tn * HN_T;
   const int kb = blockIdx.y * kchunk;
   const int ke = min(k, kb + kchunk);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  A acc[2][2] = {{A{0, 0}, A{0, 0}}, {A{0, 0}, A{0, 0}}};
+  A acc[RM][2];
+#pragma unroll
+  for (int i = 0; i < RM; ++i) acc[i][0] = acc[i][1] = A{0, 0};
   // FP32 arithmetic: each k-tile is summed in FP32 and folded into a double-float total, so
   // FP32 rounding accumulates over 32 terms instead of the whole k-range of the CTA
   constexpr bool fold = std::is_same<A, float2>::value;
-  dfl tot[2][2][2] = {};
+  dfl tot[RM][2][2] = {};
   for (int k0 = kb; k0 < ke; k0 += HN_T) {
+    for (int e = threadIdx.x; e < HN_T * TM; e += 256) {
+      const int kq = e & (HN_T - 1), q = e >> 5;
+      const int gk = k0 + kq;
+      A va{0, 0};
+      if (gk < ke && m0 + q < m) va = cvt<A>(a[(size_t)(m0 + q) * lda + gk]);
+      as[kq][q] = va;
+    }
     for (int e = threadIdx.x; e < HN_T * HN_T; e += 256) {
       const int kq = e & (HN_T - 1), q = e >> 5;
       const int gk = k0 + kq;
-      A va{0, 0}, vb{0, 0};
-      if (gk < ke) {
-        if (m0 + q < m) va = cvt<A>(a[(size_t)(m0 + q) * lda + gk]);
-        if (n0 + q < n) vb = cvt<A>(b[(size_t)(n0 + q) * ldb + gk]);
-      }
-      as[kq][q] = va;
+      A vb{0, 0};
+      if (gk < ke && n0 + q < n) vb = cvt<A>(b[(size_t)(n0 + q) * ldb + gk]);
       bs[kq][q] = vb;
     }
     __syncthreads();
 #pragma unroll 8
     for (int kq = 0; kq < HN_T; ++kq) {
-      const A a0 = as[kq][ty], a1 = as[kq][ty + 16];
       const A b0 = bs[kq][tx], b1 = bs[kq][tx + 16];
-      acc[0][0] = cfmac(a0, b0, acc[0][0]);
-      acc[0][1] = cfmac(a0, b1, acc[0][1]);
-      acc[1][0] = cfmac(a1, b0, acc[1][0]);
-      acc[1][1] = cfmac(a1, b1, acc[1][1]);
+#pragma unroll
+      for (int i = 0; i < RM; ++i) {
+        const A ai = as[kq][ty + 16 * i];
+        acc[i][0] = cfmac(ai, b0, acc[i][0]);
+        acc[i][1] = cfmac(ai, b1, acc[i][1]);
+      }
     }
     if constexpr (fold) {
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
+      for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           tot[i][j][0] = df_add_f(tot[i][j][0], acc[i][j].x);
@@ -98,7 +106,7 @@ __global__ void __launch_bounds__(256) k_gemm_hn(const Va* __restrict__ a, int l
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < RM; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int mm = m0 + ty + 16 * i, nn = n0 + tx + 16 * j;
@@ -128,7 +136,10 @@ int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, dou
   if (m <= 0 || n <= 0 || k <= 0) return DKS_OK;
   if (ldc <= 0) ldc = m;
   if (lower && m != n) return fail(DKS_ERR_INVALID_ARG, "gemm_hn: lower-triangle mode needs a square result");
-  const int mt = (m + HN_T - 1) / HN_T, nt = (n + HN_T - 1) / HN_T;
+  // 48-row tiles when they pad m less than 32-row tiles (not for the square lower-triangle mode)
+  const bool rm3 = !lower && (m + 47) / 48 * 48 < (m + 31) / 32 * 32;
+  const int tmr = rm3 ? 48 : HN_T;
+  const int mt = (m + tmr - 1) / tmr, nt = (n + HN_T - 1) / HN_T;
   const int tiles = lower ? mt * (mt + 1) / 2 : mt * nt;
   const int ktiles = (k + HN_T - 1) / HN_T;
   int splits = std::max(1, (4 * num_sms()) / tiles);
@@ -142,7 +153,10 @@ int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, dou
                        16.0 * m * n,
           (lower ? 4.0 * m * (m + 1.0) : 8.0 * m * n) * (double)k);
   using A = typename std::conditional<Acc64, double2, typename AccOf<Va, Vb>::T>::type;
-  k_gemm_hn<Va, Vb, A><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
+  if (rm3)
+    k_gemm_hn<Va, Vb, A, 3><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
+  else
+    k_gemm_hn<Va, Vb, A, 2><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
@@ -234,7 +248,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const Va* __restrict__ a, int l
 // over 256 rows and every shared-memory load of W feeds four complex multiply-adds.
 constexpr int NF_R = 256, NF_GMAX = 5, NF_CMAX = 8 * NF_GMAX, NF_M = 16;
 
-__global__ void __launch_bounds__(64 * NF_GMAX) k_gemm_nn_f32(const float2* __restrict__ a, int lda, int k, int m,
+__global__ void __launch_bounds__(64 * NF_GMAX, 2) k_gemm_nn_f32(const float2* __restrict__ a, int lda, int k, int m,
                                                      const double2* __restrict__ w, int ldw,
                                                      const double* __restrict__ ws, int n,
                                                      float2* __restrict__ out, int ldo, double alpha, float beta) {
