@@ -330,7 +330,10 @@ def main():
 
     # accuracy against the oracle's stored eigenvalues (written by tests/golden/make_golden.py)
     acc = {"max_residual": max(r["max_residual"][0] for r in reps), "iterations": reps[-1]["iterations"][0],
-           "fp64_iterations": reps[-1]["fp64_iterations"][0], "h_applications": reps[-1]["h_applications"]}
+           "fp64_iterations": reps[-1]["fp64_iterations"][0], "h_applications": reps[-1]["h_applications"],
+           "iterations_per_step": [r["iterations"][0] for r in reps],
+           "fp64_iterations_per_step": [r["fp64_iterations"][0] for r in reps],
+           "residual_history_last_step": [float(f"{v:.3g}") for v in reps[-1]["history"]]}
     gold = os.path.join(HERE, "tests", "golden", "dimer_lobpcgf_eigs.txt")
     if os.path.exists(gold):
         acc["max_eig_err_vs_oracle"] = float(np.abs(lam - np.loadtxt(gold)).max())
