@@ -213,13 +213,12 @@ int gemm_hn_df(const float4* a, int lda, const double2* b, int ldb, int k, int m
 }
 
 // ---------------------------------------------------------------- OUT = alpha A diag(ws) W + beta OUT
-// 128 rows x (8 * ncg) columns per CTA (ncg <= 5 column groups, sized to the number of output
-// columns), 2 rows x 8 columns per thread (rows t and t+64): the split of W into double-float
-// pairs is amortised over 128 rows.
-constexpr int DNN_R = 128, DNN_GMAX = 5, DNN_CMAX = 8 * DNN_GMAX, DNN_M = 16;
+// 64 rows x (8 * ncg) columns per CTA (ncg <= 5 column groups, sized to the number of output
+// columns), one row x 8 columns per thread, two CTAs per SM.
+constexpr int DNN_RPT = 1, DNN_R = 64 * DNN_RPT, DNN_GMAX = 5, DNN_CMAX = 8 * DNN_GMAX, DNN_M = 16;
 
 template <typename TA>
-__global__ void __launch_bounds__(64 * DNN_GMAX, 1) k_gemm_nn_df(const TA* __restrict__ a, int lda, int k, int m,
+__global__ void __launch_bounds__(64 * DNN_GMAX, 2) k_gemm_nn_df(const TA* __restrict__ a, int lda, int k, int m,
                                                        const double2* __restrict__ w, int ldw,
                                                        const double* __restrict__ ws, int n,
                                                        double2* __restrict__ out, int ldo, double alpha, double beta) {
@@ -228,14 +227,14 @@ __global__ void __launch_bounds__(64 * DNN_GMAX, 1) k_gemm_nn_df(const TA* __res
   const int ncols = (blockDim.x >> 6) * 8;
   const int r0 = blockIdx.x * DNN_R, c0 = blockIdx.y * ncols;
   const int rg = threadIdx.x & 63, cg = threadIdx.x >> 6;
-  gcdf acc[2][8];
+  gcdf acc[DNN_RPT][8];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < DNN_RPT; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = gcdf{{0.f, 0.f}, {0.f, 0.f}};
   for (int m0 = 0; m0 < m; m0 += DNN_M) {
     for (int e = threadIdx.x; e < DNN_M * DNN_R; e += blockDim.x) {
-      const int rr = e & (DNN_R - 1), mm = e >> 7;
+      const int mm = e / DNN_R, rr = e - mm * DNN_R;
       gcdf v = zero_df<TA>();
       if (m0 + mm < m && r0 + rr < k) v = ld_df(a, (size_t)(m0 + mm) * lda + r0 + rr);
       as[mm][rr] = v;
@@ -255,23 +254,25 @@ __global__ void __launch_bounds__(64 * DNN_GMAX, 1) k_gemm_nn_df(const TA* __res
     for (int mm0 = 0; mm0 < DNN_M; mm0 += 4) {
 #pragma unroll 2
       for (int mm = mm0; mm < mm0 + 4; ++mm) {
-        const gcdf a0 = as[mm][rg], a1 = as[mm][rg + 64];
+        gcdf av[DNN_RPT];
+#pragma unroll
+        for (int i = 0; i < DNN_RPT; ++i) av[i] = as[mm][rg + 64 * i];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const gcdf wv = wsm[mm][cg * 8 + j];
-          cdf_mac(acc[0][j], a0, wv);
-          cdf_mac(acc[1][j], a1, wv);
+#pragma unroll
+          for (int i = 0; i < DNN_RPT; ++i) cdf_mac(acc[i][j], av[i], wv);
         }
       }
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
+      for (int i = 0; i < DNN_RPT; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) cdf_renorm(acc[i][j]);   // every 8 updates of each part
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < DNN_RPT; ++i) {
     const int row = r0 + rg + 64 * i;
     if (row >= k) continue;
 #pragma unroll
