@@ -699,15 +699,17 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
   // 5. eigenvalue idx by one warp (eigenvalues spread round-robin over the CTAs): 33-way
   // multisection of the Sturm count, lane l counting at lo + (l+1)(hi-lo)/33, the bracket then
   // narrowed to the first section whose count exceeds idx.  FP32 counts take the bracket to
-  // ~2e-7 relative; it is widened by the FP32 error level and refined with double-float counts
-  // (~2^-47 per operation) to ~3e-14 relative.
+  // ~2e-7 relative (or 1e-7 of the matrix norm); it is widened by the FP32 error level and
+  // refined with double-float counts (~2^-47 per operation) to ~3e-14 relative or 1e-14 of the
+  // matrix norm, whichever is larger.
   for (int r0 = 0; r0 < n; r0 += gnw) {
     const int idx = r0 + wl * csize + crank;
     if (idx >= n) continue;
     double lo = lo0 - 1e-14 * tnorm - 1e-300, hi = hi0 + 1e-14 * tnorm + 1e-300;
     float flo = (float)lo, fhi = (float)hi;
+    const float fabs_tol = (float)(1e-7 * tnorm);
     for (int it = 0; it < 10; ++it) {
-      if (!(fhi - flo > 2e-7f * fmaxf(fabsf(flo), fabsf(fhi)))) break;
+      if (!(fhi - flo > fmaxf(2e-7f * fmaxf(fabsf(flo), fabsf(fhi)), fabs_tol))) break;
       const float step = (fhi - flo) * (1.0f / 33.0f);
       const float x = flo + step * (float)(lane + 1);
       const unsigned bal = __ballot_sync(0xffffffffu, sturm_count_f(fd, fe2, m, x, fpiv) > idx);
@@ -721,7 +723,7 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
     lo = fmax(lo, (double)flo - pad);
     hi = fmin(hi, (double)fhi + pad);
     for (int it = 0; it < 12; ++it) {
-      if (!(hi - lo > 3e-14 * fmax(fabs(lo), fabs(hi)) + 1e-300)) break;
+      if (!(hi - lo > fmax(3e-14 * fmax(fabs(lo), fabs(hi)), 1e-14 * tnorm) + 1e-300)) break;
       const double step = (hi - lo) * (1.0 / 33.0);
       const double x = lo + step * (double)(lane + 1);
       const unsigned bal = __ballot_sync(0xffffffffu, sturm_count_df(gd, ge2, m, df_from(x), fpiv) > idx);
