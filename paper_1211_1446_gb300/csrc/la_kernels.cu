@@ -421,33 +421,41 @@ int col_stats(const V* x, const V* hx, const double* lam, const double* ek, int 
 }
 
 // ---------------------------------------------------------------- Teter preconditioner
+// grid (planewave blocks, active columns): the per-column Teter scale 1/T_band is formed once
+// per thread; each thread then takes planewaves p and all four components, so |k+G|^2/2 is read
+// once per planewave and the Teter factor computed once for the four components
 template <typename V, typename Vo>
 __global__ void k_precond(const V* __restrict__ x, const V* __restrict__ hx, const double* __restrict__ lam,
-                          const double* __restrict__ stats, const int* __restrict__ act, int nact,
+                          const double* __restrict__ stats, const int* __restrict__ act,
                           const double* __restrict__ ek, int npw, int precond, Vo* __restrict__ y) {
   using T = typename RealOf<V>::T;
+  const int i = blockIdx.y;
+  const int j = act[i];
   const size_t rows = (size_t)4 * npw;
-  const size_t total = rows * nact;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / rows);
-    const size_t rr = e - (size_t)i * rows;
-    const int j = act[i];
-    const size_t src = (size_t)j * rows + rr;
-    const T l = (T)lam[j];
-    const V xv = x[src], hv = hx[src];
-    V r{hv.x - l * xv.x, hv.y - l * xv.y};
+  const V* xj = x + (size_t)j * rows;
+  const V* hj = hx + (size_t)j * rows;
+  Vo* yi = y + (size_t)i * rows;
+  const T l = (T)lam[j];
+  const double tb = fmax(stats[3 * j + 2] / fmax(stats[3 * j + 1], 1e-300), 1e-12);
+  const T itb = (T)(1.0 / tb);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npw; p += gridDim.x * blockDim.x) {
+    T kf = (T)1;
     if (precond == DKS_PRECOND_TETER) {
-      double tb = stats[3 * j + 2] / fmax(stats[3 * j + 1], 1e-300);
-      tb = fmax(tb, 1e-12);
-      const T xx = (T)(ek[rr % npw] / tb);
-      const T p = (T)27 + xx * ((T)18 + xx * ((T)12 + xx * (T)8));
+      const T xx = (T)ek[p] * itb;
+      const T pp = (T)27 + xx * ((T)18 + xx * ((T)12 + xx * (T)8));
       const T x2 = xx * xx;
-      const T kf = p / (p + (T)16 * x2 * x2);
-      r.x *= kf;
-      r.y *= kf;
+      kf = pp / (pp + (T)16 * x2 * x2);
     }
-    y[(size_t)i * rows + rr] = from_d2<Vo>(to_d2(r));
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const V xv = xj[(size_t)a * npw + p], hv = hj[(size_t)a * npw + p];
+      const V r{kf * (hv.x - l * xv.x), kf * (hv.y - l * xv.y)};
+      if constexpr (std::is_same<V, Vo>::value) {
+        yi[(size_t)a * npw + p] = r;
+      } else {
+        yi[(size_t)a * npw + p] = from_d2<Vo>(to_d2(r));
+      }
+    }
   }
 }
 
@@ -455,10 +463,11 @@ template <typename V, typename Vo>
 int precond_apply(const V* x, const V* hx, const double* lam, const double* stats, const int* act, int nact,
                   const double* ek, int npw, int precond, Vo* y, cudaStream_t st) {
   if (nact <= 0) return DKS_OK;
+  if (nact > 65535) return fail(DKS_ERR_INVALID_ARG, "precond: too many columns");
   const size_t total = (size_t)4 * npw * nact;
-  const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)num_sms() * 16);
+  const int bx = std::max(1, std::min((npw + 255) / 256, (num_sms() * 8 + nact - 1) / nact));
   Prof pr(P_PRECOND, st, 3.0 * total * sizeof(V) + 8.0 * npw, 20.0 * total);
-  k_precond<V, Vo><<<blocks, 256, 0, st>>>(x, hx, lam, stats, act, nact, ek, npw, precond, y);
+  k_precond<V, Vo><<<dim3(bx, nact), 256, 0, st>>>(x, hx, lam, stats, act, ek, npw, precond, y);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
