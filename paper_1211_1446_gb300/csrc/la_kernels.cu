@@ -119,6 +119,88 @@ __global__ void __launch_bounds__(256) k_gemm_hn(const Va* __restrict__ a, int l
     }
 }
 
+// Both Gram matrices of Algorithm 1 from FP32 blocks in one pass: S = Z^H Z and A = Z^H HZ, block
+// lower triangles of 32 x 32 tiles.  The Z tile of the row block serves both products and each
+// thread reuses its two Z row values for four outputs of S and four of A; FP32 within a
+// 32-deep k-tile, folded into double-float totals.
+__global__ void __launch_bounds__(256) k_gram_f32(const float2* __restrict__ z, const float2* __restrict__ hz,
+                                                  int ld, int k, int m, int kchunk, double2* __restrict__ a,
+                                                  double2* __restrict__ s) {
+  __shared__ float2 zs[HN_T][HN_T + 1];
+  __shared__ float2 zb[HN_T][HN_T + 1];
+  __shared__ float2 hb[HN_T][HN_T + 1];
+  const int t = blockIdx.x;
+  int tm = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
+  while (tm * (tm + 1) / 2 > t) --tm;
+  const int tn = t - tm * (tm + 1) / 2;
+  const int m0 = tm * HN_T, n0 = tn * HN_T;
+  const int kb = blockIdx.y * kchunk;
+  const int ke = min(k, kb + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float2 as_[2][2], aa[2][2];
+  dfl ts[2][2][2] = {}, ta[2][2][2] = {};
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) as_[i][j] = aa[i][j] = float2{0.f, 0.f};
+  for (int k0 = kb; k0 < ke; k0 += HN_T) {
+    for (int e = threadIdx.x; e < HN_T * HN_T; e += 256) {
+      const int kq = e & (HN_T - 1), q = e >> 5;
+      const int gk = k0 + kq;
+      float2 vz{0.f, 0.f}, vb{0.f, 0.f}, vh{0.f, 0.f};
+      if (gk < ke) {
+        if (m0 + q < m) vz = z[(size_t)(m0 + q) * ld + gk];
+        if (n0 + q < m) {
+          vb = z[(size_t)(n0 + q) * ld + gk];
+          vh = hz[(size_t)(n0 + q) * ld + gk];
+        }
+      }
+      zs[kq][q] = vz;
+      zb[kq][q] = vb;
+      hb[kq][q] = vh;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kq = 0; kq < HN_T; ++kq) {
+      const float2 a0 = zs[kq][ty], a1 = zs[kq][ty + 16];
+      const float2 b0 = zb[kq][tx], b1 = zb[kq][tx + 16];
+      const float2 h0 = hb[kq][tx], h1 = hb[kq][tx + 16];
+      as_[0][0] = cfmac(a0, b0, as_[0][0]);
+      as_[0][1] = cfmac(a0, b1, as_[0][1]);
+      as_[1][0] = cfmac(a1, b0, as_[1][0]);
+      as_[1][1] = cfmac(a1, b1, as_[1][1]);
+      aa[0][0] = cfmac(a0, h0, aa[0][0]);
+      aa[0][1] = cfmac(a0, h1, aa[0][1]);
+      aa[1][0] = cfmac(a1, h0, aa[1][0]);
+      aa[1][1] = cfmac(a1, h1, aa[1][1]);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        ts[i][j][0] = df_add_f(ts[i][j][0], as_[i][j].x);
+        ts[i][j][1] = df_add_f(ts[i][j][1], as_[i][j].y);
+        ta[i][j][0] = df_add_f(ta[i][j][0], aa[i][j].x);
+        ta[i][j][1] = df_add_f(ta[i][j][1], aa[i][j].y);
+        as_[i][j] = aa[i][j] = float2{0.f, 0.f};
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int mm = m0 + ty + 16 * i, nn = n0 + tx + 16 * j;
+      if (mm < m && nn < m) {
+        atomicAdd(&s[(size_t)nn * m + mm].x, df_val(ts[i][j][0]));
+        atomicAdd(&s[(size_t)nn * m + mm].y, df_val(ts[i][j][1]));
+        atomicAdd(&a[(size_t)nn * m + mm].x, df_val(ta[i][j][0]));
+        atomicAdd(&a[(size_t)nn * m + mm].y, df_val(ta[i][j][1]));
+      }
+    }
+}
+
 static int g_num_sms = 0;
 static int num_sms() {
   if (!g_num_sms) {
@@ -157,6 +239,20 @@ int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, dou
     k_gemm_hn<Va, Vb, A, 3><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
   else
     k_gemm_hn<Va, Vb, A, 2><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
+}
+
+int gram_f32(const float2* z, const float2* hz, int ld, int k, int m, double2* a, double2* s, cudaStream_t st) {
+  if (m <= 0 || k <= 0) return DKS_OK;
+  const int mt = (m + HN_T - 1) / HN_T;
+  const int tiles = mt * (mt + 1) / 2;
+  const int ktiles = (k + HN_T - 1) / HN_T;
+  int splits = std::min(std::max(1, (4 * num_sms()) / tiles), ktiles);
+  const int kchunk = ((ktiles + splits - 1) / splits) * HN_T;
+  splits = (k + kchunk - 1) / kchunk;
+  Prof pr(P_GRAM + kProf32, st, 2.0 * m * 8.0 * k + 32.0 * m * m, 8.0 * m * (m + 1.0) * (double)k);
+  k_gram_f32<<<dim3(tiles, splits), 256, 0, st>>>(z, hz, ld, k, m, kchunk, a, s);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }

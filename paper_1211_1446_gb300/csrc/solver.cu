@@ -29,6 +29,7 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "dks_internal.h"
@@ -116,8 +117,12 @@ template <typename V>
 static int gram(const V* z, const V* hz, int rows, int nz, Small& sm, cudaStream_t st, bool df = false) {
   DKS_CUDA_TRY(cudaMemsetAsync(sm.a, 0, (size_t)nz * nz * sizeof(double2), st));
   DKS_CUDA_TRY(cudaMemsetAsync(sm.s, 0, (size_t)nz * nz * sizeof(double2), st));
-  DKS_TRY(hn<V>(df, z, rows, hz, rows, rows, nz, nz, sm.a, st, true));
-  DKS_TRY(hn<V>(df, z, rows, z, rows, rows, nz, nz, sm.s, st, true));
+  if constexpr (std::is_same<V, float2>::value) {
+    DKS_TRY(gram_f32(z, hz, rows, rows, nz, sm.a, sm.s, st));
+  } else {
+    DKS_TRY(hn<V>(df, z, rows, hz, rows, rows, nz, nz, sm.a, st, true));
+    DKS_TRY(hn<V>(df, z, rows, z, rows, rows, nz, nz, sm.s, st, true));
+  }
   DKS_TRY(mirror_lower(sm.a, nz, st));
   return mirror_lower(sm.s, nz, st);
 }
