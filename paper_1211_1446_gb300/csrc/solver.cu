@@ -234,17 +234,20 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
       break;
     }
     if (stop_on_stall) {
-      // FP32 phase: stop at its rounding floor -- no 30% gain in 3 iterations, or a jump above
-      // twice the best residual (FP32 noise reaching the negative band).  The phase hands on
-      // the X with the lowest residual seen, not the last one.
+      // FP32 phase: stop at its rounding floor -- the best residual not lowered by 20% within 3
+      // iterations (5 while it is still above 30 tol: FP32 rounding can stall it there for a
+      // few iterations before it improves again) -- or on a rise above 10x the best (FP32 noise
+      // reaching the negative band).
+      // Smaller rises are transient and recover; the phase hands on the X with the lowest
+      // residual seen, not the last one.
       if (b.best && maxres < lowest) {
         lowest = maxres;
         DKS_CUDA_TRY(cudaMemcpyAsync(b.best, b.z[nx], (size_t)n * colsz * sizeof(V), cudaMemcpyDeviceToDevice, st));
       }
-      if (maxres < 0.7 * best) {
+      if (maxres < 0.8 * best) {
         best = maxres;
         since_best = 0;
-      } else if (++since_best >= 3 || maxres > 2.0 * best) {
+      } else if (++since_best >= (best > 30.0 * tol ? 5 : 3) || maxres > 10.0 * best) {
         cur = nx;
         if (b.best)
           DKS_CUDA_TRY(cudaMemcpyAsync(b.z[cur], b.best, (size_t)n * colsz * sizeof(V), cudaMemcpyDeviceToDevice,
