@@ -161,6 +161,86 @@ __global__ void __launch_bounds__(256) k_gemm_hn_df(const TA* __restrict__ a, in
     }
 }
 
+// Both Gram matrices from double-float copies in one pass: S = Z^H Z and A = Z^H HZ, block lower
+// triangles of 32 x 32 tiles; the Z tile of the row block serves both products.
+constexpr int DG_K = 16;
+
+__global__ void __launch_bounds__(256) k_gram_df(const float4* __restrict__ z, const float4* __restrict__ hz,
+                                                 int ld, int k, int m, int kchunk, double2* __restrict__ a,
+                                                 double2* __restrict__ s) {
+  __shared__ gcdf zs[DG_K][DHN_T + 1];
+  __shared__ gcdf zb[DG_K][DHN_T + 1];
+  __shared__ gcdf hb[DG_K][DHN_T + 1];
+  const int t = blockIdx.x;
+  int tm = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
+  while (tm * (tm + 1) / 2 > t) --tm;
+  const int tn = t - tm * (tm + 1) / 2;
+  const int m0 = tm * DHN_T, n0 = tn * DHN_T;
+  const int kb = blockIdx.y * kchunk;
+  const int ke = min(k, kb + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  gcdf as_[2][2], aa[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) as_[i][j] = aa[i][j] = gcdf{{0.f, 0.f}, {0.f, 0.f}};
+  for (int k0 = kb; k0 < ke; k0 += DG_K) {
+    for (int e = threadIdx.x; e < DG_K * DHN_T; e += 256) {
+      const int kq = e & (DG_K - 1), q = e >> 4;
+      const int gk = k0 + kq;
+      gcdf vz = zero_df<float4>(), vb = zero_df<float4>(), vh = zero_df<float4>();
+      if (gk < ke) {
+        if (m0 + q < m) vz = ld_df(z, (size_t)(m0 + q) * ld + gk);
+        if (n0 + q < m) {
+          vb = ld_df(z, (size_t)(n0 + q) * ld + gk);
+          vh = ld_df(hz, (size_t)(n0 + q) * ld + gk);
+        }
+      }
+      zs[kq][q] = vz;
+      zb[kq][q] = vb;
+      hb[kq][q] = vh;
+    }
+    __syncthreads();
+    for (int kq0 = 0; kq0 < DG_K; kq0 += 4) {
+#pragma unroll
+      for (int kq = kq0; kq < kq0 + 4; ++kq) {
+        const gcdf a0 = zs[kq][ty], a1 = zs[kq][ty + 16];
+        const gcdf b0 = zb[kq][tx], b1 = zb[kq][tx + 16];
+        const gcdf h0 = hb[kq][tx], h1 = hb[kq][tx + 16];
+        cdf_macc(as_[0][0], a0, b0);
+        cdf_macc(as_[0][1], a0, b1);
+        cdf_macc(as_[1][0], a1, b0);
+        cdf_macc(as_[1][1], a1, b1);
+        cdf_macc(aa[0][0], a0, h0);
+        cdf_macc(aa[0][1], a0, h1);
+        cdf_macc(aa[1][0], a1, h0);
+        cdf_macc(aa[1][1], a1, h1);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          cdf_renorm(as_[i][j]);   // every 8 updates of each part
+          cdf_renorm(aa[i][j]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int mm = m0 + ty + 16 * i, nn = n0 + tx + 16 * j;
+      if (mm < m && nn < m) {
+        atomicAdd(&s[(size_t)nn * m + mm].x, df_to_d(as_[i][j].re));
+        atomicAdd(&s[(size_t)nn * m + mm].y, df_to_d(as_[i][j].im));
+        atomicAdd(&a[(size_t)nn * m + mm].x, df_to_d(aa[i][j].re));
+        atomicAdd(&a[(size_t)nn * m + mm].y, df_to_d(aa[i][j].im));
+      }
+    }
+}
+
 static int df_num_sms() {
   static int n = 0;
   if (!n) {
@@ -310,6 +390,20 @@ static int gemm_nn_df_t(const TA* a, int lda, int k, int m, const double2* w, in
 int gemm_nn_df(const double2* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
                double2* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
   return gemm_nn_df_t(a, lda, k, m, w, ldw, wscale, n, out, ldo, beta, st, alpha, cat);
+}
+
+int gram_df(const float4* z, const float4* hz, int ld, int k, int m, double2* a, double2* s, cudaStream_t st) {
+  if (m <= 0 || k <= 0) return DKS_OK;
+  const int mt = (m + DHN_T - 1) / DHN_T;
+  const int tiles = mt * (mt + 1) / 2;
+  const int ktiles = (k + DG_K - 1) / DG_K;
+  int splits = std::min(std::max(1, (4 * df_num_sms()) / tiles), ktiles);
+  const int kchunk = ((ktiles + splits - 1) / splits) * DG_K;
+  splits = (k + kchunk - 1) / kchunk;
+  Prof pr(P_GRAM, st, 2.0 * m * 16.0 * k + 32.0 * m * m, 8.0 * m * (m + 1.0) * (double)k);
+  k_gram_df<<<dim3(tiles, splits), 256, 0, st>>>(z, hz, ld, k, m, kchunk, a, s);
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
 }
 int gemm_nn_df(const float4* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
                double2* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {

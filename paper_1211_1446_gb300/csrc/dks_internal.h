@@ -183,6 +183,8 @@ int gemm_nn_df(const float4* a, int lda, int k, int m, const double2* w, int ldw
                int n, double2* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0,
                int cat = P_ROTATE);
 int split_df(const double2* in, float4* out, size_t n, cudaStream_t st);
+// block lower triangles of A += Z^H HZ and S += Z^H Z from double-float copies in one pass
+int gram_df(const float4* z, const float4* hz, int ld, int k, int m, double2* a, double2* s, cudaStream_t st);
 template <typename Va, typename Vo = Va>
 int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
             int n, Vo* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0,

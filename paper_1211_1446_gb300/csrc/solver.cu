@@ -130,8 +130,7 @@ static int gram(const V* z, const V* hz, int rows, int nz, Small& sm, cudaStream
 static int gram_split(const float4* z, const float4* hz, int rows, int nz, Small& sm, cudaStream_t st) {
   DKS_CUDA_TRY(cudaMemsetAsync(sm.a, 0, (size_t)nz * nz * sizeof(double2), st));
   DKS_CUDA_TRY(cudaMemsetAsync(sm.s, 0, (size_t)nz * nz * sizeof(double2), st));
-  DKS_TRY(gemm_hn_df(z, rows, hz, rows, rows, nz, nz, sm.a, st, P_GRAM, 0, true));
-  DKS_TRY(gemm_hn_df(z, rows, z, rows, rows, nz, nz, sm.s, st, P_GRAM, 0, true));
+  DKS_TRY(gram_df(z, hz, rows, rows, nz, sm.a, sm.s, st));
   DKS_TRY(mirror_lower(sm.a, nz, st));
   return mirror_lower(sm.s, nz, st);
 }
