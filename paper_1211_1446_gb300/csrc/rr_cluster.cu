@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
                                                             const double2* __restrict__ S, int m, int n,
                                                             double2* __restrict__ V, double* __restrict__ lam,
                                                             int* __restrict__ info, double2* __restrict__ scr,
-                                                            double chol_tol, int scols) {
+                                                            double chol_tol, int scols, int phase) {
   extern __shared__ __align__(16) unsigned char rrc_smem[];
   cg::cluster_group cl = cg::this_cluster();
   const int crank = (int)cl.block_rank(), csize = (int)cl.num_blocks();
@@ -299,6 +299,8 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
   double* stau = slinv + m;
   double* sdsc = stau + m;
 
+  double2* cc = lm;   // C = L^-1 A' L^-H from the second triangular solve (k_rr_trsm)
+  if (phase == 0) {
   // 1. scaling (every CTA keeps D in shared memory)
   for (int i = tid; i < m; i += RRC_THREADS) {
     const double di = nr_rsqrt(fmax(S[(size_t)i * m + i].x, 1e-300));
@@ -347,61 +349,17 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
     return;   // every CTA leaves here; the single-CTA SVQB kernel that follows takes over
   }
   if (gtid == 0) *flag = 0;
-  double* linv = lamw + m;     // 1 / L_ii (the spare m-array)
-  for (int i = gtid; i < m; i += gnt) linv[i] = nr_rcp(lt[(size_t)i * m + i].x);
-  cl.sync();
-  RR_MARK(1);
-  double2* wvec = reinterpret_cast<double2*>(rrc_smem) + (size_t)wl * m;   // per-warp vector
-  for (int i = tid; i < m; i += RRC_THREADS) slinv[i] = linv[i];
-  // 3. two forward substitutions with L, column-oriented: lanes own rows k of the right-hand
-  // side b; at step i every lane forms w_i = b_i / L_ii from shared memory and updates its
-  // b_k -= L_ki w_i (k > i), so a step needs no reduction.  Columns of L come through the
-  // staging area in blocks; right-hand sides are spread round-robin over the CTAs.
-  //   pass 0: W = L^-1 A'   (column c of A')          -> cm
-  //   pass 1: C = L^-1 W^H  (column c = conj(row c of W)) -> cc (= lm, free after the Cholesky)
-  double2* cc = lm;
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int r0 = 0; r0 < m; r0 += gnw) {                 // same trip count in every CTA
-      const int c = r0 + wl * csize + crank;
-      const bool act = c < m;
-      if (act) {
-        if (pass == 0)
-          for (int k = lane; k < m; k += 32) wvec[k] = am[(size_t)c * m + k];
-        else
-          for (int k = lane; k < m; k += 32) {
-            const double2 w = cm[(size_t)k * m + c];
-            wvec[k] = double2{w.x, -w.y};
-          }
-      }
-      __syncwarp();
-      for (int i0 = 0; i0 < m; i0 += scols) {
-        const int nb = min(scols, m - i0);
-        __syncthreads();
-        for (int e = tid; e < nb * m; e += RRC_THREADS) stg[e] = lf[(size_t)i0 * m + e];
-        __syncthreads();
-        if (act) {
-          for (int i = i0; i < i0 + nb; ++i) {
-            const double2 b = wvec[i];
-            const double li = slinv[i];
-            const double2 w = double2{b.x * li, b.y * li};
-            const double2* lc = stg + (size_t)(i - i0) * m;
-            for (int k = i + 1 + lane; k < m; k += 32) wvec[k] = csub(wvec[k], cmul(lc[k], w));
-            __syncwarp();
-          }
-        }
-      }
-      if (act) {
-        double2* out = pass == 0 ? cm : cc;
-        for (int k = lane; k < m; k += 32) {
-          const double2 b = wvec[k];
-          out[(size_t)c * m + k] = double2{b.x * slinv[k], b.y * slinv[k]};
-        }
-      }
-      __syncwarp();
-    }
-    cl.sync();
+  {
+    double* linv = lamw + m;     // 1 / L_ii (the spare m-array)
+    for (int i = gtid; i < m; i += gnt) linv[i] = nr_rcp(lt[(size_t)i * m + i].x);
   }
-  RR_MARK(2);
+#ifdef DKS_RR_TIMING
+  RR_MARK(1);
+  if (gtid == 0) printf("rr_cluster m=%d n=%d csize=%d: scaling+cholesky %.1f us\n", m, n, csize, (tmark[1] - tmark[0]) * 1e-3);
+#endif
+  return;   // 3. the two triangular solves run in k_rr_trsm, one right-hand side per CTA
+  }
+  if (*flag) return;   // Cholesky failed: the single-CTA SVQB kernel takes over
   // Hermitian average into cm (full storage)
   for (size_t e = gtid; e < mm; e += gnt) {
     const int i = (int)(e % m), j = (int)(e / m);
@@ -775,82 +733,155 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
   }
   cl.sync();
   RR_MARK(5);
-  // 7. u = H_0 ... H_{m-3} (Phi z); V = D L^-H u.  Warp per eigenvector, spread round-robin over
-  // the CTAs; reflectors and rows of L come through the staging area in blocks.
-  for (int k = tid; k < m; k += RRC_THREADS) {
-    stau[k] = tau[k].x;
-    sph[k] = ph[k];
-  }
-  for (int r0 = 0; r0 < n; r0 += gnw) {                    // same trip count in every CTA
-    const int j = r0 + wl * csize + crank;
-    const bool act = j < n;
-    __syncthreads();
-    if (act)
-      for (int i = lane; i < m; i += 32) {
-        const double z = zt[(size_t)j * m + i];
-        wvec[i] = double2{sph[i].x * z, sph[i].y * z};
-      }
-    __syncwarp();
-    for (int k1 = m - 3; k1 >= 0; k1 -= scols) {
-      const int k0 = max(0, k1 - scols + 1);
-      __syncthreads();
-      for (int e = tid; e < (k1 - k0 + 1) * m; e += RRC_THREADS) stg[e] = cm[(size_t)k0 * m + e];
-      __syncthreads();
-      if (act) {
-        for (int k = k1; k >= k0; --k) {
-          const double t = stau[k];
-          if (t == 0.0) continue;
-          const double2* v = stg + (size_t)(k - k0) * m + k + 1;
-          const int len = m - k - 1;
-          double2 s{0, 0};
-          for (int i = lane; i < len; i += 32) s = cadd(s, cmulc(v[i], wvec[k + 1 + i]));
-          s = warp_csum(s);
-          s = double2{t * s.x, t * s.y};
-          for (int i = lane; i < len; i += 32) wvec[k + 1 + i] = csub(wvec[k + 1 + i], cmul(s, v[i]));
-          __syncwarp();
-        }
-      }
-    }
-    // L^H y = u, column-oriented: at step i (descending) y_i = u_i / L_ii and every lane updates
-    // its u_k -= conj(L[i, k]) y_i for k < i (row i of L from the staging area)
-    for (int i1 = m - 1; i1 >= 0; i1 -= scols) {
-      const int i0 = max(0, i1 - scols + 1);
-      __syncthreads();
-      for (int e = tid; e < (i1 - i0 + 1) * m; e += RRC_THREADS) stg[e] = lt[(size_t)i0 * m + e];
-      __syncthreads();
-      if (act) {
-        for (int i = i1; i >= i0; --i) {
-          const double2 u = wvec[i];
-          const double li = slinv[i];
-          const double2 y = double2{u.x * li, u.y * li};
-          const double2* lr = stg + (size_t)(i - i0) * m;
-          for (int k = lane; k < i; k += 32) wvec[k] = csub(wvec[k], cmulc(lr[k], y));
-          __syncwarp();
-        }
-      }
-    }
-    if (act) {
-      for (int i = lane; i < m; i += 32) {
-        const double2 u = wvec[i];
-        const double f = sdsc[i] * slinv[i];
-        V[(size_t)j * m + i] = double2{f * u.x, f * u.y};
-      }
-      if (lane == 0) lam[j] = lamw[j];
-    }
-    __syncwarp();
-  }
-  if (gtid == 0) {
-    info[0] = 0;
-    info[1] = m;
-    info[2] = 0;
-  }
 #ifdef DKS_RR_TIMING
-  RR_MARK(6);
   if (gtid == 0)
-    printf("rr_cluster m=%d n=%d csize=%d: chol %.1f trsm %.1f householder %.1f multisect %.1f invit %.1f backtr %.1f us\n",
-           m, n, csize, (tmark[1] - tmark[0]) * 1e-3, (tmark[2] - tmark[1]) * 1e-3, (tmark[3] - tmark[2]) * 1e-3,
-           (tmark[4] - tmark[3]) * 1e-3, (tmark[5] - tmark[4]) * 1e-3, (tmark[6] - tmark[5]) * 1e-3);
+    printf("rr_cluster m=%d n=%d: householder %.1f multisect %.1f invit %.1f us\n", m, n,
+           (tmark[3] - tmark[0]) * 1e-3, (tmark[4] - tmark[3]) * 1e-3, (tmark[5] - tmark[4]) * 1e-3);
 #endif
+}
+
+// 3. Forward substitution with L, column-oriented, one right-hand side per CTA (so each column
+// has an SM's FP64 pipes to itself): the 128 threads own rows k of b (one warp on each of the
+// SM's four FP64 units); at step i every thread forms w_i = b_i / L_ii and updates its
+// b_k -= L_ki w_i (k > i); columns of L are staged in shared memory in blocks.
+//   pass 0: W = L^-1 A'   (column c of A')              -> cm
+//   pass 1: C = L^-1 W^H  (column c = conj(row c of W))  -> lm (free after the Cholesky)
+__global__ void __launch_bounds__(128, 1) k_rr_trsm(double2* __restrict__ scr, int m, int pass, int scols) {
+  extern __shared__ __align__(16) unsigned char trs_smem[];
+  const size_t mm = (size_t)m * m;
+  double2* am = scr;
+  double2* lm = am + mm;
+  double2* lf = lm + mm;
+  double2* lt = lf + mm;
+  double2* cm = lt + mm;
+  double* lamw = reinterpret_cast<double*>(cm + mm) + 4 * m;
+  const double* linv = lamw + m;
+  const int* flag = reinterpret_cast<const int*>(reinterpret_cast<const double2*>(lamw + 2 * m) + 3 * m);
+  if (*flag) return;
+  (void)lt;
+  double2* stg = reinterpret_cast<double2*>(trs_smem);           // scols x m
+  double2* b = stg + (size_t)scols * m;                          // right-hand side / solution
+  double* sl = reinterpret_cast<double*>(b + m);
+  const int tid = threadIdx.x;
+  const int c = blockIdx.x;
+  for (int k = tid; k < m; k += blockDim.x) {
+    sl[k] = linv[k];
+    if (pass == 0) {
+      b[k] = am[(size_t)c * m + k];
+    } else {
+      const double2 w = cm[(size_t)k * m + c];
+      b[k] = double2{w.x, -w.y};
+    }
+  }
+  for (int i0 = 0; i0 < m; i0 += scols) {
+    const int nb = min(scols, m - i0);
+    __syncthreads();
+    for (int e = tid; e < nb * m; e += blockDim.x) stg[e] = lf[(size_t)i0 * m + e];
+    __syncthreads();
+    for (int i = i0; i < i0 + nb; ++i) {
+      const double2 bi = b[i];
+      const double li = sl[i];
+      const double2 w = double2{bi.x * li, bi.y * li};
+      const double2* lc = stg + (size_t)(i - i0) * m;
+      for (int k = tid; k < m; k += blockDim.x)
+        if (k > i) b[k] = csub(b[k], cmul(lc[k], w));
+      __syncthreads();
+    }
+  }
+  double2* out = pass == 0 ? cm : lm;
+  for (int k = tid; k < m; k += blockDim.x) out[(size_t)c * m + k] = double2{b[k].x * sl[k], b[k].y * sl[k]};
+}
+
+// 7. u = H_0 ... H_{m-3} (Phi z_j); V_j = D L^-H u, one eigenvector per CTA; the 128 threads own
+// rows (one warp per FP64 unit of the SM); reflectors and rows of L are staged in shared
+// memory.  A reflector step sums four warp partials through shared memory (double-buffered by
+// step parity, so one barrier per step).
+__global__ void __launch_bounds__(128, 1) k_rr_backtr(double2* __restrict__ scr, int m, int n, double2* __restrict__ V,
+                                                   double* __restrict__ lam, int* __restrict__ info, int scols) {
+  extern __shared__ __align__(16) unsigned char btr_smem[];
+  const size_t mm = (size_t)m * m;
+  double2* am = scr;
+  double2* lm = am + mm;
+  double2* lf = lm + mm;
+  double2* lt = lf + mm;
+  double2* cm = lt + mm;
+  double* dsc = reinterpret_cast<double*>(cm + mm);
+  double* lamw = dsc + 4 * m;
+  const double* linv = lamw + m;
+  const double2* tau = reinterpret_cast<const double2*>(lamw + 2 * m);
+  const double2* ph = tau + m;
+  const int* flag = reinterpret_cast<const int*>(ph + 2 * m);
+  const double* zt = reinterpret_cast<const double*>(lm);
+  if (*flag) return;
+  (void)lf;
+  double2* stg = reinterpret_cast<double2*>(btr_smem);           // scols x m
+  double2* wv = stg + (size_t)scols * m;
+  double2* sph = wv + m;
+  double* sl = reinterpret_cast<double*>(sph + m);
+  double* stau = sl + m;
+  double* sdsc = stau + m;
+  __shared__ double2 red[8];   // warp partials of the reflector dot products, by step parity
+  const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
+  const int j = blockIdx.x;
+  for (int k = tid; k < m; k += blockDim.x) {
+    sph[k] = ph[k];
+    sl[k] = linv[k];
+    stau[k] = tau[k].x;
+    sdsc[k] = dsc[k];
+    const double z = zt[(size_t)j * m + k];
+    wv[k] = double2{ph[k].x * z, ph[k].y * z};
+  }
+  for (int k1 = m - 3; k1 >= 0; k1 -= scols) {
+    const int k0 = max(0, k1 - scols + 1);
+    __syncthreads();
+    for (int e = tid; e < (k1 - k0 + 1) * m; e += blockDim.x) stg[e] = cm[(size_t)k0 * m + e];
+    __syncthreads();
+    for (int k = k1; k >= k0; --k) {
+      const double t = stau[k];
+      if (t == 0.0) continue;   // uniform: every thread reads the same tau
+      const double2* v = stg + (size_t)(k - k0) * m;
+      // rows r > k, thread-owned (r = tid + 128 q): partial dot, warp sums, four partials
+      double2 sacc{0, 0};
+      for (int r = tid; r < m; r += blockDim.x)
+        if (r > k) sacc = cadd(sacc, cmulc(v[r], wv[r]));
+      sacc = warp_csum(sacc);
+      double2* part = red + 4 * (k & 1);
+      if (lane == 0) part[wl] = sacc;
+      __syncthreads();
+      const double2 tot = cadd(cadd(part[0], part[1]), cadd(part[2], part[3]));
+      const double2 f = double2{t * tot.x, t * tot.y};
+      for (int r = tid; r < m; r += blockDim.x)
+        if (r > k) wv[r] = csub(wv[r], cmul(f, v[r]));
+    }
+  }
+  // L^H y = u, column-oriented: y_i = u_i / L_ii, then u_k -= conj(L[i, k]) y_i for k < i
+  for (int i1 = m - 1; i1 >= 0; i1 -= scols) {
+    const int i0 = max(0, i1 - scols + 1);
+    __syncthreads();
+    for (int e = tid; e < (i1 - i0 + 1) * m; e += blockDim.x) stg[e] = lt[(size_t)i0 * m + e];
+    __syncthreads();
+    __syncthreads();
+    for (int i = i1; i >= i0; --i) {
+      const double2 u = wv[i];
+      const double li = sl[i];
+      const double2 y = double2{u.x * li, u.y * li};
+      const double2* lr = stg + (size_t)(i - i0) * m;
+      for (int k = tid; k < i; k += blockDim.x) wv[k] = csub(wv[k], cmulc(lr[k], y));
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < m; i += blockDim.x) {
+    const double f = sdsc[i] * sl[i];
+    V[(size_t)j * m + i] = double2{f * wv[i].x, f * wv[i].y};
+  }
+  if (tid == 0) {
+    lam[j] = lamw[j];
+    if (j == 0) {
+      info[0] = 0;
+      info[1] = m;
+      info[2] = 0;
+    }
+  }
 }
 
 // byte offset of the hand-off flag inside the scratch layout above
@@ -861,6 +892,27 @@ size_t rr_cluster_flag_offset(int m) {
 
 static int g_cluster = 0;   // 0 = unknown, else cluster size that launched successfully
 
+static cudaError_t launch_cluster(int csz, size_t smem, cudaStream_t st, const double2* a, const double2* s, int nz,
+                                  int n, double2* v, double* lam, int* info, double2* scratch, double chol_tol,
+                                  int scols, int phase) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csz, 1, 1);
+  cfg.blockDim = dim3(RRC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csz;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_rr_cluster, a, s, nz, n, v, lam, info, scratch, chol_tol, scols, phase);
+}
+
+// Five launches: scaling + Cholesky (cluster), W = L^-1 A' and C = L^-1 W^H (one right-hand side
+// per CTA), Householder + multisection + inverse iteration (cluster), back-transformation (one
+// eigenvector per CTA).  Each later launch returns at once when the Cholesky factorisation failed.
 int rayleigh_ritz_cluster(const double2* a, const double2* s, int nz, int n, double2* v, double* lam, int* info,
                           double2* scratch, cudaStream_t st, double chol_tol, bool* launched) {
   *launched = false;
@@ -869,37 +921,37 @@ int rayleigh_ritz_cluster(const double2* a, const double2* s, int nz, int n, dou
   if (base + 8 * (size_t)nz * sizeof(double2) > kRrSmemMax) return DKS_OK;
   const int scols = (int)std::min<size_t>({(size_t)64, (size_t)nz, (kRrSmemMax - base) / ((size_t)nz * sizeof(double2))});
   const size_t smem = rr_cluster_smem(nz, scols);
+  // per-column kernels: staging area + one complex vector + four m-length scalar arrays
+  const size_t col_extra = (size_t)nz * (2 * sizeof(double2) + 4 * sizeof(double));
+  const int scols1 = (int)std::max<size_t>(1, std::min<size_t>((size_t)nz, (kRrSmemMax - col_extra) / ((size_t)nz * sizeof(double2))));
+  const size_t smem1 = (size_t)scols1 * nz * sizeof(double2) + col_extra;
   static bool attr_done = false;
   if (!attr_done) {
     cudaFuncSetAttribute((const void*)k_rr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute((const void*)k_rr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRrSmemMax);
+    cudaFuncSetAttribute((const void*)k_rr_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRrSmemMax);
+    cudaFuncSetAttribute((const void*)k_rr_backtr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRrSmemMax);
     attr_done = true;
   }
+  Prof pr(P_RR, st, 2.0 * nz * nz * 16.0 + 16.0 * nz * n, rr_flops(nz, n));
   const int tries[2] = {16, 8};
   for (int t = 0; t < 2; ++t) {
     const int csz = g_cluster ? g_cluster : tries[t];
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(csz, 1, 1);
-    cfg.blockDim = dim3(RRC_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = csz;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    Prof pr(P_RR, st, 2.0 * nz * nz * 16.0 + 16.0 * nz * n, rr_flops(nz, n));
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_rr_cluster, a, s, nz, n, v, lam, info, scratch, chol_tol, scols);
+    const cudaError_t e = launch_cluster(csz, smem, st, a, s, nz, n, v, lam, info, scratch, chol_tol, scols, 0);
     if (e == cudaSuccess) {
       g_cluster = csz;
       *launched = true;
-      return DKS_OK;
+      break;
     }
     cudaGetLastError();   // clear the launch error and try the portable size
     if (g_cluster) break;
   }
+  if (!*launched) return DKS_OK;
+  k_rr_trsm<<<nz, 128, smem1, st>>>(scratch, nz, 0, scols1);
+  k_rr_trsm<<<nz, 128, smem1, st>>>(scratch, nz, 1, scols1);
+  DKS_CUDA_TRY(launch_cluster(g_cluster, smem, st, a, s, nz, n, v, lam, info, scratch, chol_tol, scols, 1));
+  k_rr_backtr<<<n, 128, smem1, st>>>(scratch, nz, n, v, lam, info, scols1);
+  DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
 
