@@ -411,32 +411,13 @@ int gemm_nn_df(const float4* a, int lda, int k, int m, const double2* w, int ldw
 }
 
 // ---------------------------------------------------------------- split complex128 -> double-float
-// Integer operations only: hi = the value with its mantissa truncated to 24 bits, lo = the
-// remaining 29 bits converted to FP32 (rounded), so hi + lo equals the value to 2^-47 relative.
-// Zero and magnitudes outside [2^-74, 2^127) take the FP64 conversions.  A block is split once
-// and then read by every contraction of the iteration.
-__device__ __forceinline__ void split_bits(double x, float& h, float& l) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi32 = (unsigned)(u >> 32), lo32 = (unsigned)u;
-  const int e = (int)((hi32 >> 20) & 0x7ffu);
-  if (e < 949 || e > 1149) {
-    h = (float)x;
-    l = (float)(x - (double)h);
-    return;
-  }
-  const unsigned sign = hi32 & 0x80000000u;
-  h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29));
-  const float lv = __uint2float_rn(lo32 & 0x1fffffffu) * __uint_as_float((unsigned)(e - 948) << 23);
-  l = sign ? -lv : lv;
-}
-
+// df_from_bits (integer operations); a block is split once and then read by every contraction
+// of the iteration.
 __global__ void k_split_df(const double2* __restrict__ in, float4* __restrict__ out, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double2 v = in[i];
-    float4 o;
-    split_bits(v.x, o.x, o.y);
-    split_bits(v.y, o.z, o.w);
-    out[i] = o;
+    const dfl re = df_from_bits(v.x), im = df_from_bits(v.y);
+    out[i] = float4{re.h, re.l, im.h, im.l};
   }
 }
 

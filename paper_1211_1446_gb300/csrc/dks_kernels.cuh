@@ -73,6 +73,20 @@ __device__ __forceinline__ dfl df_from(double x) {
   return dfl{h, (float)(x - (double)h)};
 }
 __device__ __forceinline__ double df_val(dfl a) { return (double)a.h + (double)a.l; }
+// double -> (h, l) with integer operations (no FP64 unit): h = x with the mantissa truncated to
+// 24 bits, l = the remaining 29 bits converted to FP32 (rounded), h + l = x to 2^-47 relative.
+// Zero and magnitudes outside [2^-74, 2^127) take the FP64 conversions.  For bulk splits
+// (k_split_df, shared-memory staging).
+__device__ __forceinline__ dfl df_from_bits(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi32 = (unsigned)(u >> 32), lo32 = (unsigned)u;
+  const int e = (int)((hi32 >> 20) & 0x7ffu);
+  if (e < 949 || e > 1149) return df_from(x);
+  const unsigned sign = hi32 & 0x80000000u;
+  const float h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29));
+  const float lv = __uint2float_rn(lo32 & 0x1fffffffu) * __uint_as_float((unsigned)(e - 948) << 23);
+  return dfl{h, sign ? -lv : lv};
+}
 __device__ __forceinline__ dfl df_add(dfl a, dfl b) {
   const float s = a.h + b.h;
   const float bb = s - a.h;

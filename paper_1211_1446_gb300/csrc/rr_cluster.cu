@@ -740,6 +740,55 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
 #endif
 }
 
+// Bulk global -> shared copies for the per-column kernels (TMA, completion on an mbarrier).
+// Sources and destinations are 16-byte aligned and sizes multiples of 16 bytes (double2 arrays).
+__device__ __forceinline__ uint32_t sh_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// thread 0: expect `bytes` on the mbarrier and issue the copy in pieces of at most 48 KB
+__device__ __forceinline__ void stage_issue(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sh_u32(mbar)), "r"(bytes) : "memory");
+  for (uint32_t off = 0; off < bytes; off += 48u * 1024u) {
+    const uint32_t len = min(bytes - off, 48u * 1024u);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            sh_u32(static_cast<char*>(dst) + off)),
+        "l"(static_cast<const char*>(src) + off), "r"(len), "r"(sh_u32(mbar))
+        : "memory");
+  }
+}
+
+// every thread: bounded wait for the phase of the mbarrier
+__device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < (1u << 24) && !done; ++it)
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(done)
+        : "r"(sh_u32(mbar)), "r"(parity)
+        : "memory");
+  return done != 0;
+}
+
+// stage `bytes` from src into dst (whole block); false (uniform over the block) on a timeout,
+// after a second bounded wait for the copy still in flight
+__device__ bool stage_block(void* dst, const void* src, uint32_t bytes, uint64_t* mbar, uint32_t& phase) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier generic reads of dst
+  __syncthreads();
+  if (threadIdx.x == 0) stage_issue(dst, src, bytes, mbar);
+  const bool ok = __syncthreads_and(stage_wait(mbar, phase & 1) ? 1 : 0) != 0;
+  if (!ok) stage_wait(mbar, phase & 1);
+  ++phase;
+  return ok;
+}
+
+__device__ __forceinline__ void stage_init(uint64_t* mbar) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
 // 3. Forward substitution with L, column-oriented, one right-hand side per CTA (so each column
 // has an SM's FP64 pipes to itself): the 128 threads own rows k of b (one warp on each of the
 // SM's four FP64 units); at step i every thread forms w_i = b_i / L_ii and updates its
@@ -756,9 +805,12 @@ __global__ void __launch_bounds__(128, 1) k_rr_trsm(double2* __restrict__ scr, i
   double2* cm = lt + mm;
   double* lamw = reinterpret_cast<double*>(cm + mm) + 4 * m;
   const double* linv = lamw + m;
-  const int* flag = reinterpret_cast<const int*>(reinterpret_cast<const double2*>(lamw + 2 * m) + 3 * m);
+  int* flag = reinterpret_cast<int*>(reinterpret_cast<double2*>(lamw + 2 * m) + 3 * m);
   if (*flag) return;
   (void)lt;
+  __shared__ __align__(8) uint64_t mbar;
+  uint32_t phase = 0;
+  stage_init(&mbar);
   double2* stg = reinterpret_cast<double2*>(trs_smem);           // scols x m
   double2* b = stg + (size_t)scols * m;                          // right-hand side / solution
   double* sl = reinterpret_cast<double*>(b + m);
@@ -775,9 +827,10 @@ __global__ void __launch_bounds__(128, 1) k_rr_trsm(double2* __restrict__ scr, i
   }
   for (int i0 = 0; i0 < m; i0 += scols) {
     const int nb = min(scols, m - i0);
-    __syncthreads();
-    for (int e = tid; e < nb * m; e += blockDim.x) stg[e] = lf[(size_t)i0 * m + e];
-    __syncthreads();
+    if (!stage_block(stg, lf + (size_t)i0 * m, (uint32_t)(nb * m * sizeof(double2)), &mbar, phase)) {
+      if (tid == 0) *flag = 2;   // the single-CTA kernel recomputes the whole step
+      return;
+    }
     for (int i = i0; i < i0 + nb; ++i) {
       const double2 bi = b[i];
       const double li = sl[i];
@@ -810,17 +863,20 @@ __global__ void __launch_bounds__(128, 1) k_rr_backtr(double2* __restrict__ scr,
   const double* linv = lamw + m;
   const double2* tau = reinterpret_cast<const double2*>(lamw + 2 * m);
   const double2* ph = tau + m;
-  const int* flag = reinterpret_cast<const int*>(ph + 2 * m);
+  int* flag = reinterpret_cast<int*>(const_cast<double2*>(ph) + 2 * m);
   const double* zt = reinterpret_cast<const double*>(lm);
   if (*flag) return;
   (void)lf;
+  __shared__ __align__(8) uint64_t mbar;
+  uint32_t phase = 0;
+  stage_init(&mbar);
   double2* stg = reinterpret_cast<double2*>(btr_smem);           // scols x m
   double2* wv = stg + (size_t)scols * m;
   double2* sph = wv + m;
   double* sl = reinterpret_cast<double*>(sph + m);
   double* stau = sl + m;
   double* sdsc = stau + m;
-  __shared__ double2 red[8];   // warp partials of the reflector dot products, by step parity
+  __shared__ float4 red[8];    // warp partials of the reflector dot products, by step parity
   const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
   const int j = blockIdx.x;
   for (int k = tid; k < m; k += blockDim.x) {
@@ -831,35 +887,63 @@ __global__ void __launch_bounds__(128, 1) k_rr_backtr(double2* __restrict__ scr,
     const double z = zt[(size_t)j * m + k];
     wv[k] = double2{ph[k].x * z, ph[k].y * z};
   }
+  // the reflectors are applied in double-float arithmetic (an orthogonal transformation, so
+  // 2^-47 rounding per operation stays at that level; FP64 chains cost a whole FP64-unit
+  // warp instruction per dependent step): reflector elements are split as they are read, the
+  // vector is kept as double-float in the rows each thread owns
+  constexpr int RPT = 4;                       // rows per thread: m <= 512
+  cdf wq[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int r = tid + 128 * q;
+    wq[q] = r < m ? ucdf(c4(wv[r])) : cdf0();
+  }
   for (int k1 = m - 3; k1 >= 0; k1 -= scols) {
     const int k0 = max(0, k1 - scols + 1);
-    __syncthreads();
-    for (int e = tid; e < (k1 - k0 + 1) * m; e += blockDim.x) stg[e] = cm[(size_t)k0 * m + e];
-    __syncthreads();
+    if (!stage_block(stg, cm + (size_t)k0 * m, (uint32_t)((k1 - k0 + 1) * m * sizeof(double2)), &mbar, phase)) {
+      if (tid == 0) *flag = 2;
+      return;
+    }
     for (int k = k1; k >= k0; --k) {
       const double t = stau[k];
       if (t == 0.0) continue;   // uniform: every thread reads the same tau
       const double2* v = stg + (size_t)(k - k0) * m;
       // rows r > k, thread-owned (r = tid + 128 q): partial dot, warp sums, four partials
-      double2 sacc{0, 0};
-      for (int r = tid; r < m; r += blockDim.x)
-        if (r > k) sacc = cadd(sacc, cmulc(v[r], wv[r]));
-      sacc = warp_csum(sacc);
-      double2* part = red + 4 * (k & 1);
-      if (lane == 0) part[wl] = sacc;
+      cdf sacc = cdf0();
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = tid + 128 * q;
+        if (r > k && r < m) sacc = cdf_fmac(cdf{df_from_bits(v[r].x), df_from_bits(v[r].y)}, wq[q], sacc);
+      }
+      sacc = warp_cdsum(sacc);
+      float4* part = red + 4 * (k & 1);
+      if (lane == 0) part[wl] = c4(sacc);
       __syncthreads();
-      const double2 tot = cadd(cadd(part[0], part[1]), cadd(part[2], part[3]));
-      const double2 f = double2{t * tot.x, t * tot.y};
-      for (int r = tid; r < m; r += blockDim.x)
-        if (r > k) wv[r] = csub(wv[r], cmul(f, v[r]));
+      cdf tot = ucdf(part[0]);
+      tot = cadd(tot, ucdf(part[1]));
+      tot = cadd(tot, ucdf(part[2]));
+      tot = cadd(tot, ucdf(part[3]));
+      const dfl td = df_from(t);
+      const cdf f = cdf{df_mul(td, tot.re), df_mul(td, tot.im)};
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = tid + 128 * q;
+        if (r > k && r < m) wq[q] = csub(wq[q], cmul(f, cdf{df_from_bits(v[r].x), df_from_bits(v[r].y)}));
+      }
     }
+  }
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int r = tid + 128 * q;
+    if (r < m) wv[r] = double2{df_val(wq[q].re), df_val(wq[q].im)};
   }
   // L^H y = u, column-oriented: y_i = u_i / L_ii, then u_k -= conj(L[i, k]) y_i for k < i
   for (int i1 = m - 1; i1 >= 0; i1 -= scols) {
     const int i0 = max(0, i1 - scols + 1);
-    __syncthreads();
-    for (int e = tid; e < (i1 - i0 + 1) * m; e += blockDim.x) stg[e] = lt[(size_t)i0 * m + e];
-    __syncthreads();
+    if (!stage_block(stg, lt + (size_t)i0 * m, (uint32_t)((i1 - i0 + 1) * m * sizeof(double2)), &mbar, phase)) {
+      if (tid == 0) *flag = 2;
+      return;
+    }
     __syncthreads();
     for (int i = i1; i >= i0; --i) {
       const double2 u = wv[i];
