@@ -57,7 +57,11 @@ struct gcdf {   // complex double-float
 __device__ __forceinline__ gcdf gcdf_split(double2 v) { return gcdf{df_split(v.x), df_split(v.y)}; }
 // operand element as double-float: split a complex128 value, or take a pre-split (re hi, re lo,
 // im hi, im lo) quadruple as it is
-__device__ __forceinline__ gcdf ld_df(const double2* p, size_t i) { return gcdf_split(p[i]); }
+__device__ __forceinline__ gcdf ld_df(const double2* p, size_t i) {
+  const double2 v = p[i];
+  const dfl re = df_from_bits(v.x), im = df_from_bits(v.y);
+  return gcdf{{re.h, re.l}, {im.h, im.l}};
+}
 __device__ __forceinline__ gcdf ld_df(const float4* p, size_t i) {
   const float4 v = p[i];
   return gcdf{{v.x, v.y}, {v.z, v.w}};

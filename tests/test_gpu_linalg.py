@@ -64,7 +64,8 @@ def _pencil(nz, seed, rank_def=False, degenerate=False):
 
 @pytest.mark.parametrize("nz,n,kind", [(96, 32, "plain"), (40, 12, "rankdef"), (24, 24, "plain"),
                                        (60, 20, "degenerate"), (1, 1, "plain"), (200, 64, "plain"),
-                                       (37, 9, "plain"), (2, 1, "plain"), (3, 2, "degenerate")])
+                                       (37, 9, "plain"), (2, 1, "plain"), (3, 2, "degenerate"),
+                                       (301, 100, "plain")])
 def test_rayleigh_ritz(nz, n, kind):
     torch = gpu()
     import paper_1211_1446_gb300 as P
