@@ -174,7 +174,8 @@ def run_reference(args):
 
 def kernel_case(case):
     """One hot step of the solve at the bench's dimer size, three launches (ncu --set full target).
-    hx64/hx32/hxdf: H' on 40 columns; gram64/gram32/gramdf: A = Z^H HZ, S = Z^H Z with 120 columns;
+    hx64/hx32/hxdf: H' on 40 columns; gram64/gram32/gramdf: the solver's fused lower-triangle
+    A = Z^H HZ, S = Z^H Z with 120 columns (gramdf includes the split into double-float copies);
     rotate64/rotate32/rotatedf: X = Z V with Z of 120 columns and V 120 x 40; rr: the 120 x 120 pencil.
     The *df cases run the complex128 arithmetic in double-float form."""
     import numpy as np
@@ -200,7 +201,7 @@ def kernel_case(case):
         a = torch.empty((m, m), dtype=torch.complex128, device="cuda")
         s = torch.empty_like(a)
         for _ in range(3):
-            P.gram(z, z, a, s, emulated=df)
+            P.gram_hermitian(z, z, a, s, emulated=df)
     elif case.startswith("rotate"):
         z = torch.randn((m, rows), dtype=cdt, device="cuda", generator=g)
         w = torch.randn((n, m), dtype=torch.complex128, device="cuda", generator=g)

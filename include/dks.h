@@ -196,9 +196,23 @@ int dks_precond(dks_ctx* ctx, int ik, const void* X, const void* HX, const doubl
 
 /* Alg. 1 lines 12-13 (the projected pencil): A = Z^H HZ and S = Z^H Z for
  * Z, HZ [nz][rows]; A, S device double2 (complex128) nz x nz, column-major,
- * both full (Hermitian).  FP64 accumulation for prec FP64; FP32 for FP32. */
+ * every entry computed (no symmetry assumed).  prec FP64: FP64 arithmetic;
+ * FP64_EMULATED: complex128 data, double-float arithmetic; FP32: complex64
+ * data, FP32 products per 32-deep k-tile summed into double-float totals. */
 int dks_gram(const void* Z, const void* HZ, int rows, int nz, void* A, void* S, int prec,
              void* stream);
+
+/* The solver's form of Alg. 1 lines 12-13: the block lower triangles of A =
+ * Z^H HZ and S = Z^H Z in one fused pass over Z and HZ, then each strict upper
+ * triangle set to the conjugate transpose of the lower one (A is Hermitian when
+ * HZ = H' Z).  Arguments and layout as dks_gram; on return A[j][i] (column j,
+ * row i) for i >= j is the exact-arithmetic entry up to rounding and A[i][j] =
+ * conj(A[j][i]).  prec FP32: complex64 blocks; FP64_EMULATED: complex128 blocks
+ * split once into double-float copies (2 x 32 nz rows bytes of device memory
+ * allocated and freed on the stream per call); FP64: complex128 blocks, FP64
+ * arithmetic, two lower-triangle passes.  Returns INVALID_ARG, OOM or CUDA. */
+int dks_gram_hermitian(const void* Z, const void* HZ, int rows, int nz, void* A, void* S, int prec,
+                       void* stream);
 
 /* Alg. 1 lines 12-14 on the device in FP64: the n lowest pairs of A v = lam S v
  * (after diagonal scaling; Cholesky of S, or SVQB with drop tolerance

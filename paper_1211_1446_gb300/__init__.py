@@ -67,7 +67,7 @@ EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dk
            "dks_apply_H", "dks_filter", "dks_solve_opts_default", "dks_lobpcgf_solve", "dks_precond",
            "dks_gram", "dks_rayleigh_ritz", "dks_rotate", "dks_residual_norms", "dks_strerror",
            "dks_last_error", "dks_profile_ncat", "dks_profile_name", "dks_profile_enable", "dks_profile_read",
-           "dks_rayleigh_ritz_static"]
+           "dks_rayleigh_ritz_static", "dks_gram_hermitian"]
 
 _lib = None
 
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH):
                                       C.POINTER(SolveReport)]
     lib.dks_precond.argtypes = [vp, i, vp, vp, vp, vp, i, vp, i, i, vp]
     lib.dks_gram.argtypes = [vp, vp, i, i, vp, vp, i, vp]
+    lib.dks_gram_hermitian.argtypes = [vp, vp, i, i, vp, vp, i, vp]
     lib.dks_rayleigh_ritz.argtypes = [vp, vp, i, i, vp, vp, vp, vp]
     lib.dks_rayleigh_ritz_static.argtypes = [vp, vp, i, i, vp, vp, vp, vp]
     lib.dks_rotate.argtypes = [vp, i, i, vp, i, i, vp, d, i, vp]
@@ -300,6 +301,15 @@ def gram(z, hz, a_out, s_out, stream=None, emulated=False):
     nz, rows = z.shape[0], z[0].numel()
     prec = PREC_FP64_EMULATED if (emulated and _prec_of(z) == PREC_FP64) else _prec_of(z)
     _check(_lib.dks_gram(_dptr(z), _dptr(hz), rows, nz, _dptr(a_out), _dptr(s_out), prec, _stream(stream)))
+
+
+def gram_hermitian(z, hz, a_out, s_out, stream=None, emulated=False):
+    """dks_gram_hermitian: the solver's fused lower-triangle Gram, upper triangles mirrored."""
+    load_library()
+    nz, rows = z.shape[0], z[0].numel()
+    prec = PREC_FP64_EMULATED if (emulated and _prec_of(z) == PREC_FP64) else _prec_of(z)
+    _check(_lib.dks_gram_hermitian(_dptr(z), _dptr(hz), rows, nz, _dptr(a_out), _dptr(s_out), prec,
+                                   _stream(stream)))
 
 
 def rayleigh_ritz(a, s, n, v_out, lam_out, info_out, stream=None):

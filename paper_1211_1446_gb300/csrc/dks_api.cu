@@ -572,6 +572,36 @@ int dks_gram(const void* Z, const void* HZ, int rows, int nz, void* A, void* S, 
   return DKS_OK;
 }
 
+int dks_gram_hermitian(const void* Z, const void* HZ, int rows, int nz, void* A, void* S, int prec, void* stream) {
+  if (rows <= 0 || nz <= 0 || !Z || !HZ || !A || !S)
+    return fail(DKS_ERR_INVALID_ARG, "dks_gram_hermitian: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  DKS_CUDA_TRY(cudaMemsetAsync(A, 0, (size_t)nz * nz * sizeof(double2), st));
+  DKS_CUDA_TRY(cudaMemsetAsync(S, 0, (size_t)nz * nz * sizeof(double2), st));
+  if (prec == DKS_PREC_FP64_EMULATED) {
+    const size_t n = (size_t)nz * rows;
+    float4* zs = nullptr;
+    if (cudaMallocAsync((void**)&zs, 2 * n * sizeof(float4), st) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DKS_ERR_OOM, "dks_gram_hermitian: no device memory for the double-float copies");
+    }
+    int rc = split_df((const double2*)Z, zs, n, st);
+    if (!rc) rc = split_df((const double2*)HZ, zs + n, n, st);
+    if (!rc) rc = gram_df(zs, zs + n, rows, rows, nz, (double2*)A, (double2*)S, st);
+    cudaFreeAsync(zs, st);
+    DKS_TRY(rc);
+  } else if (prec == DKS_PREC_FP64) {
+    DKS_TRY(gemm_hn<double2>((const double2*)Z, rows, (const double2*)HZ, rows, rows, nz, nz, (double2*)A, st,
+                             P_GRAM, 0, true));
+    DKS_TRY(gemm_hn<double2>((const double2*)Z, rows, (const double2*)Z, rows, rows, nz, nz, (double2*)S, st,
+                             P_GRAM, 0, true));
+  } else {
+    DKS_TRY(gram_f32((const float2*)Z, (const float2*)HZ, rows, rows, nz, (double2*)A, (double2*)S, st));
+  }
+  DKS_TRY(mirror_lower((double2*)A, nz, st));
+  return mirror_lower((double2*)S, nz, st);
+}
+
 int dks_rayleigh_ritz(const void* A, const void* S, int nz, int n, void* V, double* lam, int* info, void* stream) {
   if (!A || !S || !V || !lam || !info) return fail(DKS_ERR_INVALID_ARG, "dks_rayleigh_ritz: NULL pointer");
   if (nz <= 0 || n <= 0 || n > nz) return fail(DKS_ERR_INVALID_ARG, "dks_rayleigh_ritz: need 0 < n <= nz");

@@ -134,7 +134,10 @@ class Prof {
  public:
   Prof(int cat, cudaStream_t st, double bytes, double flops);
   ~Prof();
+  // books n further kernel launches (negative: fewer) inside the same timed scope
+  void count(int n);
  private:
+  int cat_;
   cudaStream_t st_;
   long long idx_;
 };

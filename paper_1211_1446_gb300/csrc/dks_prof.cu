@@ -39,7 +39,7 @@ cudaEvent_t take() {
 }
 }  // namespace
 
-Prof::Prof(int cat, cudaStream_t st, double bytes, double flops) : st_(st), idx_(-1) {
+Prof::Prof(int cat, cudaStream_t st, double bytes, double flops) : cat_(cat), st_(st), idx_(-1) {
   std::lock_guard<std::mutex> g(g_mu);
   ++g_launch[cat];
   if (!g_on) return;
@@ -47,6 +47,11 @@ Prof::Prof(int cat, cudaStream_t st, double bytes, double flops) : st_(st), idx_
   cudaEventRecord(r.a, st);
   g_recs.push_back(r);
   idx_ = (long long)g_recs.size() - 1;
+}
+
+void Prof::count(int n) {
+  std::lock_guard<std::mutex> g(g_mu);
+  g_launch[cat_] += n;
 }
 
 Prof::~Prof() {

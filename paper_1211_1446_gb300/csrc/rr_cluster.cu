@@ -1030,7 +1030,11 @@ int rayleigh_ritz_cluster(const double2* a, const double2* s, int nz, int n, dou
     cudaGetLastError();   // clear the launch error and try the portable size
     if (g_cluster) break;
   }
-  if (!*launched) return DKS_OK;
+  if (!*launched) {
+    pr.count(-1);   // nothing ran in this scope
+    return DKS_OK;
+  }
+  pr.count(4);      // five kernels in all
   k_rr_trsm<<<nz, 128, smem1, st>>>(scratch, nz, 0, scols1);
   k_rr_trsm<<<nz, 128, smem1, st>>>(scratch, nz, 1, scols1);
   DKS_CUDA_TRY(launch_cluster(g_cluster, smem, st, a, s, nz, n, v, lam, info, scratch, chol_tol, scols, 1));

@@ -125,6 +125,33 @@ def test_gram_double_float(rows, nz):
     assert rel_err(s.cpu().numpy().T, z.conj() @ z.T) < 1e-12
 
 
+@pytest.mark.parametrize("prec,rows,nz", [("fp32", 4 * 3001, 120), ("fp32", 1000, 33), ("fp32", 4 * 5, 1),
+                                           ("fp32", 4 * 57419, 120), ("df", 4 * 3001, 120), ("df", 1000, 33),
+                                           ("df", 4 * 5, 1), ("df", 4 * 57419, 97), ("fp64", 1000, 33),
+                                           ("fp64", 4 * 3001, 120)])
+def test_gram_hermitian(prec, rows, nz):
+    """The solver's fused Gram (Alg. 1 lines 12-13): block lower triangles of A = Z^H HZ and
+    S = Z^H Z in one pass, strict upper triangles the exact conjugate mirror of the lower ones."""
+    torch = gpu()
+    import paper_1211_1446_gb300 as P
+    z = _rand((nz, rows), 21)
+    hz = _rand((nz, rows), 22)
+    if prec == "fp32":
+        z, hz = (v.astype(np.complex64).astype(np.complex128) for v in (z, hz))
+        dt, tol = torch.complex64, 1e-5
+    else:
+        dt, tol = torch.complex128, 1e-12
+    a = torch.empty((nz, nz), dtype=torch.complex128, device="cuda")
+    s = torch.empty_like(a)
+    P.gram_hermitian(to_dev(z, dt), to_dev(hz, dt), a, s, emulated=(prec == "df"))
+    torch.cuda.synchronize()
+    low = np.tril(np.ones((nz, nz), dtype=bool))
+    for got_t, ref in ((a, z.conj() @ hz.T), (s, z.conj() @ z.T)):
+        got = got_t.cpu().numpy().T
+        assert rel_err(np.where(low, got, 0), np.where(low, ref, 0)) < tol
+        assert np.array_equal(got[~low], got.conj().T[~low])
+
+
 def test_rotate_double_float():
     torch = gpu()
     import paper_1211_1446_gb300 as P
