@@ -45,8 +45,16 @@ constexpr int RRC_WARPS = RRC_THREADS / 32;
 #ifdef DKS_RR_TIMING
 #define RR_MARK(i) \
   if (gtid == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tmark[i]))
+// RR_LAP(i): SM cycles since the previous lap mark added to lap slot i (CTA 0, thread 0)
+#define RR_LAP(i)                                          \
+  if (gtid == 0) {                                         \
+    const unsigned long long c_ = clock64();               \
+    tlap[i] += c_ - tlast;                                 \
+    tlast = c_;                                            \
+  }
 #else
 #define RR_MARK(i)
+#define RR_LAP(i)
 #endif
 
 // Reciprocal and square root for the serial chains: FP64 division and square root are long
@@ -155,6 +163,17 @@ __device__ __forceinline__ dfl df_div(dfl a, dfl b) {
   return dfl{h, q2 - (h - q1)};
 }
 
+// sqrt(a) in double-float, a >= 0: s0 = fl32(sqrt(a.h)), then one correction from the exact
+// remainder a - s0^2 (for a correctly rounded s0, a.h - s0^2 is representable in FP32)
+__device__ __forceinline__ dfl df_sqrt(dfl a) {
+  if (!(a.h > 0.f)) return dfl{0.f, 0.f};
+  const float s0 = sqrtf(a.h);
+  const float r = fmaf(-s0, s0, a.h) + a.l;
+  const float c = r * (0.5f * __frcp_rn(s0));
+  const float h = s0 + c;
+  return dfl{h, c - (h - s0)};
+}
+
 // Sturm count in double-float arithmetic (same recurrence as above)
 __device__ int sturm_count_df(const dfl* d, const dfl* e2, int m, dfl x, float pivmin) {
   const dfl nx = df_neg(x);
@@ -171,81 +190,109 @@ __device__ int sturm_count_df(const dfl* d, const dfl* e2, int m, dfl x, float p
 }
 
 // deterministic start vector in (-1, 1)
-__device__ __forceinline__ double start_val(int i, int v) {
+__device__ __forceinline__ float start_val(int i, int v) {
   unsigned h = (unsigned)(i * 2654435761u) ^ (unsigned)(v * 40503u + 12345u);
   h ^= h >> 13;
   h *= 0x5bd1e995u;
   h ^= h >> 15;
-  return ((double)(h & 0xffffff) / (double)0x800000) - 1.0;
+  return (float)(h & 0xffffff) * (1.0f / 8388608.0f) - 1.0f;   // exact in FP32
 }
 
-// Solve (T - lam I) x = b in place (x holds b on entry) with the factors of
-// tridiagonal Gaussian elimination with partial pivoting; f: 5m doubles of workspace.
-// Factor: rows are processed top-down; at step i the pivot is the larger of the current
-// diagonal and the subdiagonal below it.
-__device__ void tri_factor(const double* d, const double* e, int m, double lam, double tiny, double* f) {
-  double* u0 = f;            // diagonal of U
-  double* u1 = f + m;        // first superdiagonal
-  double* u2 = f + 2 * m;    // second superdiagonal (fill-in from pivoting)
-  double* l = f + 3 * m;     // multipliers
-  double* piv = f + 4 * m;   // 1 if rows i, i+1 were swapped
-  double a = d[0] - lam;     // current diagonal
-  double b = m > 1 ? e[0] : 0.0;  // current superdiagonal
+// Inverse iteration on the real tridiagonal: solve (T - lam I) x = b in place (x holds b on
+// entry) with the factors of tridiagonal Gaussian elimination with partial pivoting.  Rows are
+// processed top-down; at step i the pivot is the larger of the current diagonal and the
+// subdiagonal below it.
+// The elimination and solve run in double-float arithmetic on the FP32 lanes (one lane runs a
+// whole vector, so every step is a dependent chain: a double-float step is a few FP32
+// instructions deep, an FP64 step a whole FP64-unit warp instruction).  f: 5m double-float
+// slots (U diagonal reciprocals, two superdiagonals, multipliers, pivot flags).
+__device__ void tri_factor_df(const dfl* d, const dfl* e, int m, dfl lam, float tiny, dfl* f) {
+  dfl* u0 = f;
+  dfl* u1 = f + m;
+  dfl* u2 = f + 2 * m;
+  dfl* l = f + 3 * m;
+  dfl* piv = f + 4 * m;
+  const dfl zero{0.f, 0.f}, nl = df_neg(lam);
+  dfl a = df_add(d[0], nl);
+  dfl b = m > 1 ? e[0] : zero;
   for (int i = 0; i < m - 1; ++i) {
-    const double c = e[i];               // subdiagonal (row i+1, col i)
-    const double dn = d[i + 1] - lam;    // next diagonal
-    const double bn = i + 1 < m - 1 ? e[i + 1] : 0.0;
-    if (fabs(a) >= fabs(c)) {
-      piv[i] = 0;
-      if (a == 0.0) a = tiny;
-      const double mult = c * nr_rcp(a);
+    const dfl c = e[i];
+    const dfl dn = df_add(d[i + 1], nl);
+    const dfl bn = i + 1 < m - 1 ? e[i + 1] : zero;
+    if (fabsf(a.h) >= fabsf(c.h)) {
+      piv[i] = zero;
+      if (a.h == 0.f) a = dfl{tiny, 0.f};
+      const dfl mult = df_div(c, a);
       l[i] = mult;
       u0[i] = a;
       u1[i] = b;
-      u2[i] = 0.0;
-      a = dn - mult * b;
+      u2[i] = zero;
+      a = dd_fma(df_neg(mult), b, dn);
       b = bn;
     } else {
-      piv[i] = 1;
-      const double mult = a * nr_rcp(c);
+      piv[i] = dfl{1.f, 0.f};
+      const dfl mult = df_div(a, c);
       l[i] = mult;
       u0[i] = c;
       u1[i] = dn;
       u2[i] = bn;
-      a = b - mult * dn;
-      b = -mult * bn;
+      a = dd_fma(df_neg(mult), dn, b);
+      b = df_neg(df_mul(mult, bn));
     }
   }
-  if (a == 0.0) a = tiny;
+  if (a.h == 0.f) a = dfl{tiny, 0.f};
   u0[m - 1] = a;
-  u1[m - 1] = 0.0;
-  u2[m - 1] = 0.0;
-  for (int i = 0; i < m; ++i) u0[i] = nr_rcp(u0[i]);   // the solves multiply by reciprocals
+  u1[m - 1] = zero;
+  u2[m - 1] = zero;
+  for (int i = 0; i < m; ++i) u0[i] = df_div(dfl{1.f, 0.f}, u0[i]);
 }
 
-__device__ void tri_solve(int m, const double* f, double* x) {
-  const double* u0 = f;
-  const double* u1 = f + m;
-  const double* u2 = f + 2 * m;
-  const double* l = f + 3 * m;
-  const double* piv = f + 4 * m;
+__device__ void tri_solve_df(int m, const dfl* f, dfl* x) {
+  const dfl* u0 = f;
+  const dfl* u1 = f + m;
+  const dfl* u2 = f + 2 * m;
+  const dfl* l = f + 3 * m;
+  const dfl* piv = f + 4 * m;
   for (int i = 0; i < m - 1; ++i) {
-    if (piv[i] != 0.0) {
-      const double t = x[i];
+    if (piv[i].h != 0.f) {
+      const dfl t = x[i];
       x[i] = x[i + 1];
-      x[i + 1] = t - l[i] * x[i];
+      x[i + 1] = dd_fma(df_neg(l[i]), x[i], t);
     } else {
-      x[i + 1] -= l[i] * x[i];
+      x[i + 1] = dd_fma(df_neg(l[i]), x[i], x[i + 1]);
     }
   }
-  x[m - 1] *= u0[m - 1];
-  if (m > 1) x[m - 2] = (x[m - 2] - u1[m - 2] * x[m - 1]) * u0[m - 2];
-  for (int i = m - 3; i >= 0; --i) x[i] = (x[i] - u1[i] * x[i + 1] - u2[i] * x[i + 2]) * u0[i];
+  x[m - 1] = df_mul(x[m - 1], u0[m - 1]);
+  if (m > 1) x[m - 2] = df_mul(dd_fma(df_neg(u1[m - 2]), x[m - 1], x[m - 2]), u0[m - 2]);
+  for (int i = m - 3; i >= 0; --i)
+    x[i] = df_mul(dd_fma(df_neg(u2[i]), x[i + 2], dd_fma(df_neg(u1[i]), x[i + 1], x[i])), u0[i]);
 }
 
-// shared memory: per-warp complex vectors (or inverse-iteration slots), the tridiagonal
-// (FP64, FP32 and double-float copies), then a staging area for blocks of L / reflector columns
-// and per-index scalars (1/L_ii, tau, D, the diagonal phases)
+// x <- x / |x| in double-float: scaled by a power of two first (exact), so that the squares stay
+// inside the FP32 range whatever the growth of the inverse-iteration solve
+__device__ void df_normalize(int m, dfl* x) {
+  float amax = 0.f;
+  for (int i = 0; i < m; ++i) amax = fmaxf(amax, fabsf(x[i].h));
+  if (!(amax > 0.f) || !(amax < INFINITY)) return;
+  int ex;
+  frexpf(amax, &ex);
+  const float sc = ldexpf(1.f, -ex);
+  dfl a0{0.f, 0.f}, a1{0.f, 0.f};   // two independent chains
+  int i = 0;
+  for (; i + 1 < m; i += 2) {
+    const dfl y0{x[i].h * sc, x[i].l * sc}, y1{x[i + 1].h * sc, x[i + 1].l * sc};
+    a0 = dd_fma(y0, y0, a0);
+    a1 = dd_fma(y1, y1, a1);
+  }
+  if (i < m) {
+    const dfl y0{x[i].h * sc, x[i].l * sc};
+    a0 = dd_fma(y0, y0, a0);
+  }
+  const dfl nrm = df_add(a0, a1);
+  const dfl r = df_div(dfl{sc, 0.f}, df_sqrt(nrm));
+  for (int i = 0; i < m; ++i) x[i] = df_mul(x[i], r);
+}
+
 __host__ __device__ inline size_t rr_tri_smem_offset(int m) {
   const size_t vec = (size_t)RRC_WARPS * m * sizeof(double2);
   return vec > 48 * 1024 ? vec : 48 * 1024;
@@ -273,6 +320,7 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
   const size_t mm = (size_t)m * m;
 #ifdef DKS_RR_TIMING
   unsigned long long tmark[10] = {0};
+  unsigned long long tlap[8] = {0}, tlast = clock64();
 #endif
   RR_MARK(0);
   double2* am = scr;           // A' (full Hermitian)
@@ -319,30 +367,63 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
   cl.sync();
   // 2. Cholesky: column j of L from the (final) column j of lm; trailing update in lm.
   // Every thread reads the same pivot, so the failure decision is uniform over the cluster.
+  // The pivot's reciprocal square root is formed once per CTA (thread 0) and shared; every
+  // thread loads its first trailing element before that, so the two latencies overlap.
+  __shared__ double chol_s[3];   // 1/sqrt(pivot) (negative: not positive definite), L_jj, 1/pivot
   bool failed = false;
+  RR_LAP(7);
   for (int j = 0; j < m; ++j) {
-    const double piv = lm[(size_t)j * m + j].x;
-    if (!(piv > chol_tol)) {
+    const int len = m - j - 1;
+    const double2* colj = lm + (size_t)j * m;
+    int i0 = 0, k0 = 0;
+    bool has0 = false;
+    double2 lij0{0, 0}, lkj0{0, 0}, c00{0, 0};
+    if (gtid < len * len) {
+      i0 = j + 1 + gtid % len;
+      k0 = j + 1 + gtid / len;
+      if (k0 <= i0) {
+        has0 = true;
+        lij0 = colj[i0];
+        lkj0 = colj[k0];
+        c00 = lm[(size_t)k0 * m + i0];
+      }
+    }
+    if (tid == 0) {
+      const double piv = colj[j].x;
+      const bool ok = piv > chol_tol;
+      const double inv = ok ? nr_rsqrt(piv) : 0.0;
+      chol_s[0] = ok ? inv : -1.0;
+      chol_s[1] = piv * inv;
+      chol_s[2] = inv * inv;
+    }
+    __syncthreads();
+    const double inv = chol_s[0], ljj = chol_s[1], inv2 = chol_s[2];
+    if (!(inv > 0.0)) {   // the same global pivot decides in every CTA
       failed = true;
       break;
     }
-    const double inv = nr_rsqrt(piv), ljj = piv * inv;
     for (int i = j + gtid; i < m; i += gnt) {
-      const double2 v = i == j ? double2{ljj, 0} : double2{lm[(size_t)j * m + i].x * inv, lm[(size_t)j * m + i].y * inv};
+      const double2 v = i == j ? double2{ljj, 0} : double2{colj[i].x * inv, colj[i].y * inv};
       lf[(size_t)j * m + i] = v;
       lt[(size_t)i * m + j] = v;
     }
-    const int len = m - j - 1;
-    for (int e = gtid; e < len * len; e += gnt) {
+    RR_LAP(0);
+    // trailing update lm[:, k] -= conj(l_kj) l_ij / pivot for j < k <= i
+    if (has0) {
+      const double2 u = cmulc(lkj0, lij0);
+      lm[(size_t)k0 * m + i0] = double2{fma(-u.x, inv2, c00.x), fma(-u.y, inv2, c00.y)};
+    }
+    for (int e = gtid + gnt; e < len * len; e += gnt) {
       const int i = j + 1 + e % len, k = j + 1 + e / len;
       if (k <= i) {
-        const double2 lij = lm[(size_t)j * m + i], lkj = lm[(size_t)j * m + k];
-        const double2 u = cmulc(lkj, lij);      // conj(l_kj) l_ij, times inv^2
-        lm[(size_t)k * m + i].x -= u.x * inv * inv;
-        lm[(size_t)k * m + i].y -= u.y * inv * inv;
+        const double2 u = cmulc(colj[k], colj[i]);
+        double2* c = lm + (size_t)k * m + i;
+        *c = double2{fma(-u.x, inv2, c->x), fma(-u.y, inv2, c->y)};
       }
     }
+    RR_LAP(1);
     cl.sync();
+    RR_LAP(2);
   }
   if (failed) {
     if (gtid == 0) *flag = 1;
@@ -355,7 +436,7 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
   }
 #ifdef DKS_RR_TIMING
   RR_MARK(1);
-  if (gtid == 0) printf("rr_cluster m=%d n=%d csize=%d: scaling+cholesky %.1f us\n", m, n, csize, (tmark[1] - tmark[0]) * 1e-3);
+  if (gtid == 0) printf("rr_cluster m=%d n=%d csize=%d: scaling+cholesky %.1f us (cycles: pivot+scale %llu update %llu sync %llu)\n", m, n, csize, (tmark[1] - tmark[0]) * 1e-3, tlap[0], tlap[1], tlap[2]);
 #endif
   return;   // 3. the two triangular solves run in k_rr_trsm, one right-hand side per CTA
   }
@@ -397,50 +478,59 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
       if (j < m) cb[e] = c4(cm[(size_t)j * m + r]);
     }
     __syncthreads();
-    // reflector of column k by warp 0 of its owner: broadcast buffer, v0 into the column, tau/ph
+    // reflector of column k by warp 0 of its owner: broadcast buffer, v0 into the column, tau/ph.
+    // All scalars in double-float on the FP32 lanes (a chain of FP64 operations here was the
+    // critical path of every step); tau[k] and ph[k] are left as double-float quadruples in
+    // their double2 slots and converted after the loop.
     auto make_reflector = [&](int k) {
       float4* x = cb + (size_t)(k / csize) * m + k + 1;
       const int len = m - k - 1;
-      dfl a2{0.f, 0.f};
-      for (int i = lane; i < len; i += 32) {
+      dfl t2{0.f, 0.f};   // sum of |x_i|^2 over i >= 1
+      for (int i = 1 + lane; i < len; i += 32) {
         const cdf xi = ucdf(x[i]);
-        a2 = dd_fma(xi.re, xi.re, a2);
-        a2 = dd_fma(xi.im, xi.im, a2);
+        t2 = dd_fma(xi.re, xi.re, t2);
+        t2 = dd_fma(xi.im, xi.im, t2);
       }
-      a2 = warp_dsum(a2);
-      const double a2d = df_val(a2);
-      const cdf x0c = ucdf(x[0]);
-      const double2 x0 = double2{df_val(x0c.re), df_val(x0c.im)};
-      const double ax0 = nr_hypot(x0.x, x0.y);
-      const double alpha = nr_sqrt(a2d);
-      double t = 0.0;
-      double2 beta = x0, v0 = x0;
-      if (alpha > 1e-300 && a2d - ax0 * ax0 > 1e-30 * a2d) {
-        const double ri = ax0 > 0 ? nr_rcp(ax0) : 0.0;
-        const double2 phs = ax0 > 0 ? double2{x0.x * ri, x0.y * ri} : double2{1, 0};
-        beta = double2{-phs.x * alpha, -phs.y * alpha};
-        v0 = double2{x0.x - beta.x, x0.y - beta.y};
-        t = 2.0 * nr_rcp(a2d - ax0 * ax0 + v0.x * v0.x + v0.y * v0.y);
+      t2 = warp_dsum(t2);
+      const cdf x0 = ucdf(x[0]);
+      const dfl ax02 = dd_fma(x0.im, x0.im, df_mul(x0.re, x0.re));
+      const dfl a2 = df_add(t2, ax02);
+      cdf beta = x0, v0 = x0;
+      dfl t{0.f, 0.f};
+      if (a2.h > 0.f && t2.h > 1e-30f * a2.h) {
+        const dfl alpha = df_sqrt(a2);
+        if (ax02.h > 0.f) {
+          // beta = -alpha x0 / |x0|, v0 = x0 - beta = x0 (1 + alpha / |x0|)
+          const dfl s_ = df_div(alpha, df_sqrt(ax02));
+          beta = cdf{df_neg(df_mul(x0.re, s_)), df_neg(df_mul(x0.im, s_))};
+        } else {
+          beta = cdf{df_neg(alpha), dfl{0.f, 0.f}};
+        }
+        v0 = csub(x0, beta);
+        const dfl nv = df_add(t2, dd_fma(v0.im, v0.im, df_mul(v0.re, v0.re)));
+        t = df_div(dfl{2.f, 0.f}, nv);
       }
       float4* out = bc + (size_t)(k & 1) * (m + 1);
       const float4 v04 = c4(v0);
       for (int i = lane; i < len; i += 32) out[k + 1 + i] = i == 0 ? v04 : x[i];
       __syncwarp();
       if (lane == 0) {
-        out[m] = c4(double2{t, 0.0});
-        if (t != 0.0) x[0] = v04;
-        tau[k] = double2{t, 0.0};
-        ph[k] = beta;
+        out[m] = float4{t.h, t.l, 0.f, 0.f};
+        if (t.h != 0.f) x[0] = v04;
+        reinterpret_cast<float4*>(tau)[k] = float4{t.h, t.l, 0.f, 0.f};
+        reinterpret_cast<float4*>(ph)[k] = c4(beta);
       }
     };
     if (crank == 0 && wl == 0) make_reflector(0);
     cl.sync();
+    RR_LAP(7);
     for (int k = 0; k + 2 < m; ++k) {
       const int len = m - k - 1;
       // A
       const float4* src = cl.map_shared_rank(bc + (size_t)(k & 1) * (m + 1), (unsigned)(k % csize));
       for (int r = k + 1 + tid; r <= m; r += RRC_THREADS) vl[r == m ? 0 : r] = src[r];   // vl[0] <- tau
       __syncthreads();
+      RR_LAP(0);
       const dfl t = ucdf(vl[0]).re;
       // B
       const int lj0 = (k + 1 - crank + csize - 1) / csize;   // first owned column > k
@@ -463,7 +553,9 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
         ks = warp_cdsum(ks);
         if (lane == 0) kp[0] = c4(ks);
       }
+      RR_LAP(1);
       cl.sync();
+      RR_LAP(2);
       // C
       if (wl == 0) {
         cdf ks = lane < csize ? ucdf(*cl.map_shared_rank(kp, (unsigned)lane)) : cdf0();
@@ -478,6 +570,7 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
         wf[r] = c4(csub(p, cmul(kv, ucdf(vl[r]))));
       }
       __syncthreads();
+      RR_LAP(3);
       // D
       const int nown = ncol_own - lj0;
       for (int e = tid; e < nown * len; e += RRC_THREADS) {
@@ -499,9 +592,12 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
         *cjr = c4(c);
       }
       __syncthreads();
+      RR_LAP(4);
       // E
       if (k + 3 < m && crank == (k + 1) % csize && wl == 0) make_reflector(k + 1);
+      RR_LAP(5);
       cl.sync();
+      RR_LAP(6);
     }
     for (int e = tid; e < ncol_own * m; e += RRC_THREADS) {
       const int lj = e / m, r = e - lj * m, j = lj * csize + crank;
@@ -509,6 +605,13 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
         const cdf c = ucdf(cb[e]);
         cm[(size_t)j * m + r] = double2{df_val(c.re), df_val(c.im)};
       }
+    }
+    // tau and ph of the reflectors from double-float to FP64 (every owner wrote before a barrier)
+    for (int k = gtid; k + 2 < m; k += gnt) {
+      const cdf tk = ucdf(reinterpret_cast<const float4*>(tau)[k]);
+      const cdf pk = ucdf(reinterpret_cast<const float4*>(ph)[k]);
+      tau[k] = double2{df_val(tk.re), 0.0};
+      ph[k] = double2{df_val(pk.re), df_val(pk.im)};
     }
     cl.sync();
   } else {
@@ -587,41 +690,65 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
   cl.sync();
   }
   RR_MARK(3);
-  // 5. real tridiagonal (every CTA keeps its own copy in shared memory for the multisection)
-  if (gtid == 0) {
-    if (m >= 2) {
-      tau[m - 2] = double2{0, 0};
-      ph[m - 2] = cm[(size_t)(m - 2) * m + (m - 1)];
-    }
-    double2 phi{1, 0};
-    for (int k = 0; k < m; ++k) dd[k] = cm[(size_t)k * m + k].x;
-    for (int k = 0; k + 1 < m; ++k) {
-      const double2 e = ph[k];
-      const double ae = nr_hypot(e.x, e.y);
-      ee[k] = ae;
-      e2[k] = ae * ae;
-      ph[k] = phi;
-      if (ae > 0) {
-        const double ri = nr_rcp(ae);
-        phi = cmul(phi, double2{e.x * ri, e.y * ri});
+  // 5. real tridiagonal (every CTA keeps its own copy in shared memory for the multisection).
+  // CTA 0: d_k = Re C_kk, e_k = |beta_k| and the unit factors u_k = beta_k / e_k in parallel,
+  // then the phases ph_k = u_0 ... u_(k-1) (which make the subdiagonal real) as a prefix
+  // product by warp 0: a serial chunk per lane and a shuffle scan over the lanes.
+  if (crank == 0) {
+    double2* su = reinterpret_cast<double2*>(rrc_smem);   // m factors (the per-warp vectors are free here)
+    for (int k = tid; k < m; k += RRC_THREADS) {
+      dd[k] = cm[(size_t)k * m + k].x;
+      if (k + 1 < m) {
+        const double2 e = k == m - 2 ? cm[(size_t)(m - 2) * m + (m - 1)] : ph[k];
+        const double ae = nr_hypot(e.x, e.y);
+        ee[k] = ae;
+        e2[k] = ae * ae;
+        double2 u{1.0, 0.0};
+        if (ae > 0) {
+          const double ri = nr_rcp(ae);
+          u = double2{e.x * ri, e.y * ri};
+        }
+        su[k] = u;
+      } else {
+        ee[k] = 0;
+        e2[k] = 0;
       }
     }
-    ph[m - 1] = phi;
-    ee[m - 1] = 0;
-    e2[m - 1] = 0;
+    if (tid == 0 && m >= 2) tau[m - 2] = double2{0, 0};
+    __syncthreads();
+    if (wl == 0) {
+      const int nf = m - 1;                        // factors u_0 .. u_(m-2)
+      const int c = (nf + 31) / 32;
+      const int b0 = min(nf, lane * c), b1 = min(nf, b0 + c);
+      double2 pr{1.0, 0.0};
+      for (int j = b0; j < b1; ++j) pr = cmul(pr, su[j]);
+      double2 inc = pr;                            // inclusive scan of the chunk products
+      for (int o = 1; o < 32; o <<= 1) {
+        const double2 y{__shfl_up_sync(0xffffffffu, inc.x, o), __shfl_up_sync(0xffffffffu, inc.y, o)};
+        if (lane >= o) inc = cmul(y, inc);
+      }
+      double2 ex{__shfl_up_sync(0xffffffffu, inc.x, 1), __shfl_up_sync(0xffffffffu, inc.y, 1)};
+      if (lane == 0) ex = double2{1.0, 0.0};
+      for (int j = b0; j < b1; ++j) {
+        ph[j] = ex;
+        ex = cmul(ex, su[j]);
+      }
+      if (b0 < b1 && b1 == nf) ph[nf] = ex;        // the product of all factors
+      if (nf == 0 && lane == 0) ph[0] = double2{1.0, 0.0};
+    }
   }
   cl.sync();
   // copy the tridiagonal into this CTA's shared memory (behind the per-warp vectors)
   double* sd = reinterpret_cast<double*>(rrc_smem + rr_tri_smem_offset(m));
-  double* se = sd + m;
-  double* se2 = se + m;
+  dfl* ge = reinterpret_cast<dfl*>(sd + m);   // |e| as double-float (inverse iteration)
+  double* se2 = sd + 2 * m;
   float* fd = reinterpret_cast<float*>(se2 + m);
   float* fe2 = fd + m;
   dfl* gd = reinterpret_cast<dfl*>(fe2 + m);
   dfl* ge2 = gd + m;
   for (int k = tid; k < m; k += RRC_THREADS) {
     sd[k] = dd[k];
-    se[k] = ee[k];
+    ge[k] = df_from(ee[k]);
     se2[k] = e2[k];
     fd[k] = (float)dd[k];
     fe2[k] = (float)e2[k];
@@ -701,33 +828,35 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
   // sharing an SM slow each other down).
   const double ortol = 1e-7 * fmax(tnorm, 1e-300);
   const int nslots = min(RRC_WARPS, (int)(rr_tri_smem_offset(m) / (sizeof(double) * 6 * (size_t)m)));
-  double* fws = reinterpret_cast<double*>(rrc_smem);   // per-slot 5m factors + m vector
+  dfl* fws = reinterpret_cast<dfl*>(rrc_smem);   // per-slot 5m factors + m vector
+  // the eigenvectors of T are written as double-float pairs into the double slots of zt
+  float2* zt2 = reinterpret_cast<float2*>(zt);
   if (wl < nslots && lane == 0) {
     const int gslot = wl * csize + crank, nslot_all = csize * nslots;
+    const float tiny = fmaxf((float)(DBL_EPSILON * tnorm), 1e-30f);
     for (int start = gslot; start < n; start += nslot_all) {
       const bool begins = start == 0 || lamw[start] - lamw[start - 1] > ortol;
       if (!begins) continue;
       int end = start + 1;
       while (end < n && lamw[end] - lamw[end - 1] <= ortol) ++end;
-      double* f = fws + (size_t)wl * 6 * m;
-      double* xv = f + 5 * m;
+      dfl* f = fws + (size_t)wl * 6 * m;
+      dfl* xv = f + 5 * m;
       for (int v = start; v < end; ++v) {
         const double shift = lamw[v] + (double)(v - start) * 10.0 * DBL_EPSILON * tnorm;
-        tri_factor(sd, se, m, shift, DBL_EPSILON * tnorm + 1e-300, f);
-        for (int i = 0; i < m; ++i) xv[i] = start_val(i, v);
+        tri_factor_df(gd, ge, m, df_from(shift), tiny, f);
+        for (int i = 0; i < m; ++i) xv[i] = dfl{start_val(i, v), 0.f};
         for (int itr = 0; itr < 3; ++itr) {
-          tri_solve(m, f, xv);
+          tri_solve_df(m, f, xv);
           for (int u = start; u < v; ++u) {        // orthogonalise against the cluster's earlier vectors
-            double dot = 0;
-            for (int i = 0; i < m; ++i) dot += zt[(size_t)u * m + i] * xv[i];
-            for (int i = 0; i < m; ++i) xv[i] -= dot * zt[(size_t)u * m + i];
+            const float2* zu = zt2 + (size_t)u * m;
+            dfl dot{0.f, 0.f};
+            for (int i = 0; i < m; ++i) dot = dd_fma(dfl{zu[i].x, zu[i].y}, xv[i], dot);
+            const dfl nd = df_neg(dot);
+            for (int i = 0; i < m; ++i) xv[i] = dd_fma(nd, dfl{zu[i].x, zu[i].y}, xv[i]);
           }
-          double nrm = 0;
-          for (int i = 0; i < m; ++i) nrm += xv[i] * xv[i];
-          nrm = nr_rsqrt(fmax(nrm, 1e-300));
-          for (int i = 0; i < m; ++i) xv[i] *= nrm;
+          df_normalize(m, xv);
         }
-        for (int i = 0; i < m; ++i) zt[(size_t)v * m + i] = xv[i];
+        for (int i = 0; i < m; ++i) zt2[(size_t)v * m + i] = float2{xv[i].h, xv[i].l};
       }
     }
   }
@@ -735,8 +864,9 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
   RR_MARK(5);
 #ifdef DKS_RR_TIMING
   if (gtid == 0)
-    printf("rr_cluster m=%d n=%d: householder %.1f multisect %.1f invit %.1f us\n", m, n,
-           (tmark[3] - tmark[0]) * 1e-3, (tmark[4] - tmark[3]) * 1e-3, (tmark[5] - tmark[4]) * 1e-3);
+    printf("rr_cluster m=%d n=%d: householder %.1f multisect %.1f invit %.1f us (cycles: A %llu B %llu sync1 %llu C %llu D %llu E %llu sync2 %llu)\n", m, n,
+           (tmark[3] - tmark[0]) * 1e-3, (tmark[4] - tmark[3]) * 1e-3, (tmark[5] - tmark[4]) * 1e-3,
+           tlap[0], tlap[1], tlap[2], tlap[3], tlap[4], tlap[5], tlap[6]);
 #endif
 }
 
@@ -880,23 +1010,28 @@ __global__ void __launch_bounds__(128, 1) k_rr_backtr(double2* __restrict__ scr,
   const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
   const int j = blockIdx.x;
   for (int k = tid; k < m; k += blockDim.x) {
-    sph[k] = ph[k];
     sl[k] = linv[k];
     stau[k] = tau[k].x;
     sdsc[k] = dsc[k];
-    const double z = zt[(size_t)j * m + k];
-    wv[k] = double2{ph[k].x * z, ph[k].y * z};
   }
   // the reflectors are applied in double-float arithmetic (an orthogonal transformation, so
   // 2^-47 rounding per operation stays at that level; FP64 chains cost a whole FP64-unit
   // warp instruction per dependent step): reflector elements are split as they are read, the
   // vector is kept as double-float in the rows each thread owns
   constexpr int RPT = 4;                       // rows per thread: m <= 512
+  // start vector: ph_r z_r, z the double-float eigenvector of the real tridiagonal
+  const float2* zj = reinterpret_cast<const float2*>(zt) + (size_t)j * m;
   cdf wq[RPT];
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int r = tid + 128 * q;
-    wq[q] = r < m ? ucdf(c4(wv[r])) : cdf0();
+    if (r < m) {
+      const dfl z{zj[r].x, zj[r].y};
+      const double2 p = ph[r];
+      wq[q] = cdf{df_mul(df_from_bits(p.x), z), df_mul(df_from_bits(p.y), z)};
+    } else {
+      wq[q] = cdf0();
+    }
   }
   for (int k1 = m - 3; k1 >= 0; k1 -= scols) {
     const int k0 = max(0, k1 - scols + 1);
