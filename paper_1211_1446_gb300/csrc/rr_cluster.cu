@@ -39,6 +39,7 @@ namespace dks {
 
 constexpr int RRC_THREADS = 512;
 constexpr int RRC_WARPS = RRC_THREADS / 32;
+static_assert(RRC_THREADS >= kMaxRR - 1, "one Householder row per thread");
 
 // Phase timer for development builds (-DDKS_RR_TIMING): CTA 0, thread 0 prints the
 // nanoseconds spent between the marks of the algorithm steps.
@@ -82,6 +83,14 @@ __device__ __forceinline__ double nr_rsqrt(double a) {
   return y;
 }
 __device__ __forceinline__ double nr_sqrt(double a) { return a == 0.0 ? 0.0 : a * nr_rsqrt(a); }
+// 1/a for a > 0, with the range test done on the FP32 value (fewer FP64 instructions)
+__device__ __forceinline__ double rcp_pos(double a) {
+  const float af = __double2float_rn(a);
+  if (!(af > 1e-37f && af < 1e37f)) return 1.0 / a;
+  double x = (double)__frcp_rn(af);
+  x = fma(x, fma(-a, x, 1.0), x);
+  return fma(x, fma(-a, x, 1.0), x);
+}
 __device__ __forceinline__ double nr_hypot(double x, double y) {
   const double s = fmax(fabs(x), fabs(y));
   if (s == 0.0) return 0.0;
@@ -320,7 +329,7 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
   const size_t mm = (size_t)m * m;
 #ifdef DKS_RR_TIMING
   unsigned long long tmark[10] = {0};
-  unsigned long long tlap[8] = {0}, tlast = clock64();
+  unsigned long long tlap[8] = {0}, tlast = clock64(), town[3] = {0, 0, 0};
 #endif
   RR_MARK(0);
   double2* am = scr;           // A' (full Hermitian)
@@ -356,21 +365,112 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
     if (crank == 0) dsc[i] = di;
   }
   __syncthreads();
+  // Distributed form when the owned columns fit in shared memory: column j of S' lives in
+  // CTA j % csize.  Step j: every CTA copies the published column j (rows > j) and 1 / pivot
+  // from its owner; the owner of column j+1 updates that column first (whole CTA), publishes
+  // it with its reciprocal pivot, then every CTA updates its remaining owned columns; one
+  // cluster barrier per column.
+  const int ncol_own = (m + csize - 1) / csize;
+  const bool dist = scols >= ncol_own + 3;
   for (size_t e = gtid; e < mm; e += gnt) {
     const int i = (int)(e % m), j = (int)(e / m);
     const double s = sdsc[i] * sdsc[j];
     const double2 a = A[e], at = A[(size_t)i * m + j];
     am[e] = double2{0.5 * s * (a.x + at.x), 0.5 * s * (a.y - at.y)};
-    const double2 b = S[e], bt = S[(size_t)i * m + j];
-    lm[e] = double2{0.5 * s * (b.x + bt.x), 0.5 * s * (b.y - bt.y)};
+    if (!dist) {
+      const double2 b = S[e], bt = S[(size_t)i * m + j];
+      lm[e] = double2{0.5 * s * (b.x + bt.x), 0.5 * s * (b.y - bt.y)};
+    }
   }
+  __shared__ double chol_s;   // 1 / pivot of the current column (negative: not positive definite)
+  bool failed = false;
+  if (dist) {
+    double2* cb = stg;                               // owned columns, column j at (j / csize) * m
+    double2* colb = stg + (size_t)ncol_own * m;      // the column this CTA publishes; [m].x = 1 / pivot
+    double2* colj = colb + (m + 1);                  // local copy of the current column
+    for (int e = tid; e < ncol_own * m; e += RRC_THREADS) {
+      const int lj = e / m, r = e - lj * m, j = lj * csize + crank;
+      if (j < m) {
+        const double s = sdsc[r] * sdsc[j];
+        const double2 b = S[(size_t)j * m + r], bt = S[(size_t)r * m + j];
+        cb[e] = double2{0.5 * s * (b.x + bt.x), 0.5 * s * (b.y - bt.y)};
+      }
+    }
+    __syncthreads();
+    auto publish = [&](int j) {   // whole CTA; column j is owned here and final
+      const double2* cj = cb + (size_t)(j / csize) * m;
+      for (int i = j + 1 + tid; i < m; i += RRC_THREADS) colb[i] = cj[i];
+      if (tid == 0) {
+        const double piv = cj[j].x;
+        colb[m] = double2{piv > chol_tol ? rcp_pos(piv) : -1.0, 0.0};
+      }
+    };
+    auto updc = [&](int lk, int i, double inv2) {   // lm[i, k] -= conj(l_kj) l_ij / pivot, i >= k
+      const int k = lk * csize + crank;
+      if (k >= m || i < k) return;
+      double2* c = cb + (size_t)lk * m + i;
+      const double2 u = cmulc(colj[k], colj[i]);
+      *c = double2{fma(-u.x, inv2, c->x), fma(-u.y, inv2, c->y)};
+    };
+    if (crank == 0) publish(0);
+    cl.sync();
+    RR_LAP(7);
+    for (int j = 0; j < m; ++j) {
+      const int len = m - j - 1;
+      const double2* src = cl.map_shared_rank(colb, (unsigned)(j % csize));
+      const int r = j + 1 + tid;   // one row per thread (m <= RRC_THREADS + 1)
+      double2 x = double2{0.0, 0.0};
+      if (r < m) x = src[r];
+      if (tid == 0) chol_s = src[m].x;
+      if (r < m) colj[r] = x;
+      __syncthreads();
+      const double inv2 = chol_s;
+      if (!(inv2 > 0.0)) {   // the same published value decides in every CTA
+        failed = true;
+        break;
+      }
+      RR_LAP(0);
+      const int lj0 = (j + 1 - crank + csize - 1) / csize;   // first owned column > j
+      const bool next = j + 1 < m && crank == (j + 1) % csize;
+      if (next) {
+        if (r < m) updc(lj0, r, inv2);
+        __syncthreads();
+        publish(j + 1);
+      }
+      const int l1 = lj0 + (next ? 1 : 0);
+      for (int e = tid; e < (ncol_own - l1) * len; e += RRC_THREADS) {
+        const int q = e / len;
+        updc(l1 + q, j + 1 + (e - q * len), inv2);
+      }
+      RR_LAP(1);
+      cl.sync();
+      RR_LAP(2);
+    }
+    if (failed) {
+      cl.sync();   // no CTA leaves while another may still read its published column
+    } else {
+      // L_ij = lm_ij / sqrt(lm_jj) (i > j), L_jj = sqrt(lm_jj), and 1 / L_ii, from the owned columns
+      double* linv = lamw + m;
+      for (int e = tid; e < ncol_own * m; e += RRC_THREADS) {
+        const int lj = e / m, i = e - lj * m, j = lj * csize + crank;
+        if (j >= m || i < j) continue;
+        const double piv = cb[(size_t)lj * m + j].x;
+        const double inv = nr_rsqrt(piv);
+        const double2 c = cb[e];
+        const double2 v = i == j ? double2{piv * inv, 0.0} : double2{c.x * inv, c.y * inv};
+        lf[(size_t)j * m + i] = v;
+        lt[(size_t)i * m + j] = v;
+        if (i == j) linv[j] = inv;
+      }
+    }
+  } else {
   cl.sync();
   // 2. Cholesky: column j of L from the (final) column j of lm; trailing update in lm.
   // Every thread reads the same pivot, so the failure decision is uniform over the cluster.
-  // The pivot's reciprocal square root is formed once per CTA (thread 0) and shared; every
-  // thread loads its first trailing element before that, so the two latencies overlap.
-  __shared__ double chol_s[3];   // 1/sqrt(pivot) (negative: not positive definite), L_jj, 1/pivot
-  bool failed = false;
+  // Right-looking on the unscaled columns: lm[:, k] -= conj(lm_kj) lm[:, j] / lm_jj, so the
+  // critical path of a column is one reciprocal (formed once per CTA by thread 0 and shared)
+  // and the trailing update; every thread loads its first trailing element before the
+  // reciprocal is known.  L is formed from the final columns in one pass after the loop.
   RR_LAP(7);
   for (int j = 0; j < m; ++j) {
     const int len = m - j - 1;
@@ -390,22 +490,13 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
     }
     if (tid == 0) {
       const double piv = colj[j].x;
-      const bool ok = piv > chol_tol;
-      const double inv = ok ? nr_rsqrt(piv) : 0.0;
-      chol_s[0] = ok ? inv : -1.0;
-      chol_s[1] = piv * inv;
-      chol_s[2] = inv * inv;
+      chol_s = piv > chol_tol ? rcp_pos(piv) : -1.0;
     }
     __syncthreads();
-    const double inv = chol_s[0], ljj = chol_s[1], inv2 = chol_s[2];
-    if (!(inv > 0.0)) {   // the same global pivot decides in every CTA
+    const double inv2 = chol_s;
+    if (!(inv2 > 0.0)) {   // the same global pivot decides in every CTA
       failed = true;
       break;
-    }
-    for (int i = j + gtid; i < m; i += gnt) {
-      const double2 v = i == j ? double2{ljj, 0} : double2{colj[i].x * inv, colj[i].y * inv};
-      lf[(size_t)j * m + i] = v;
-      lt[(size_t)i * m + j] = v;
     }
     RR_LAP(0);
     // trailing update lm[:, k] -= conj(l_kj) l_ij / pivot for j < k <= i
@@ -425,18 +516,30 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
     cl.sync();
     RR_LAP(2);
   }
+  if (!failed) {
+    // L_ij = lm_ij / sqrt(lm_jj) (i > j), L_jj = sqrt(lm_jj), and 1 / L_ii (the spare m-array)
+    double* linv = lamw + m;
+    for (size_t e = gtid; e < mm; e += gnt) {
+      const int i = (int)(e % m), j = (int)(e / m);
+      if (i < j) continue;
+      const double piv = lm[(size_t)j * m + j].x;
+      const double inv = nr_rsqrt(piv);
+      const double2 c = lm[e];
+      const double2 v = i == j ? double2{piv * inv, 0.0} : double2{c.x * inv, c.y * inv};
+      lf[e] = v;
+      lt[(size_t)i * m + j] = v;
+      if (i == j) linv[i] = inv;
+    }
+  }
+  }
   if (failed) {
     if (gtid == 0) *flag = 1;
     return;   // every CTA leaves here; the single-CTA SVQB kernel that follows takes over
   }
   if (gtid == 0) *flag = 0;
-  {
-    double* linv = lamw + m;     // 1 / L_ii (the spare m-array)
-    for (int i = gtid; i < m; i += gnt) linv[i] = nr_rcp(lt[(size_t)i * m + i].x);
-  }
 #ifdef DKS_RR_TIMING
   RR_MARK(1);
-  if (gtid == 0) printf("rr_cluster m=%d n=%d csize=%d: scaling+cholesky %.1f us (cycles: pivot+scale %llu update %llu sync %llu)\n", m, n, csize, (tmark[1] - tmark[0]) * 1e-3, tlap[0], tlap[1], tlap[2]);
+  if (gtid == 0) printf("rr_cluster m=%d n=%d csize=%d: scaling+cholesky %.1f us (cycles: pivot %llu update %llu sync %llu)\n", m, n, csize, (tmark[1] - tmark[0]) * 1e-3, tlap[0], tlap[1], tlap[2]);
 #endif
   return;   // 3. the two triangular solves run in k_rr_trsm, one right-hand side per CTA
   }
@@ -473,6 +576,7 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
     float4* kp = bc + 2 * (m + 1);                           // this CTA's partial of v^H p
     float4* kw = kp + 1;                                     // per-warp partials
     __shared__ float4 hk;                                    // K of the current step
+    __shared__ float2 tpart[RRC_WARPS];                      // per-warp partial norms of the next column
     for (int e = tid; e < ncol_own * m; e += RRC_THREADS) {
       const int lj = e / m, r = e - lj * m, j = lj * csize + crank;
       if (j < m) cb[e] = c4(cm[(size_t)j * m + r]);
@@ -482,16 +586,21 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
     // All scalars in double-float on the FP32 lanes (a chain of FP64 operations here was the
     // critical path of every step); tau[k] and ph[k] are left as double-float quadruples in
     // their double2 slots and converted after the loop.
-    auto make_reflector = [&](int k) {
+    // tsum: the sum of |x_i|^2 over i >= 1 when the caller has it (nullptr: formed here)
+    auto make_reflector = [&](int k, const dfl* tsum) {
       float4* x = cb + (size_t)(k / csize) * m + k + 1;
       const int len = m - k - 1;
-      dfl t2{0.f, 0.f};   // sum of |x_i|^2 over i >= 1
-      for (int i = 1 + lane; i < len; i += 32) {
-        const cdf xi = ucdf(x[i]);
-        t2 = dd_fma(xi.re, xi.re, t2);
-        t2 = dd_fma(xi.im, xi.im, t2);
+      dfl t2{0.f, 0.f};
+      if (tsum) {
+        t2 = *tsum;
+      } else {
+        for (int i = 1 + lane; i < len; i += 32) {
+          const cdf xi = ucdf(x[i]);
+          t2 = dd_fma(xi.re, xi.re, t2);
+          t2 = dd_fma(xi.im, xi.im, t2);
+        }
+        t2 = warp_dsum(t2);
       }
-      t2 = warp_dsum(t2);
       const cdf x0 = ucdf(x[0]);
       const dfl ax02 = dd_fma(x0.im, x0.im, df_mul(x0.re, x0.re));
       const dfl a2 = df_add(t2, ax02);
@@ -521,7 +630,7 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
         reinterpret_cast<float4*>(ph)[k] = c4(beta);
       }
     };
-    if (crank == 0 && wl == 0) make_reflector(0);
+    if (crank == 0 && wl == 0) make_reflector(0, nullptr);
     cl.sync();
     RR_LAP(7);
     for (int k = 0; k + 2 < m; ++k) {
@@ -556,7 +665,11 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
       RR_LAP(1);
       cl.sync();
       RR_LAP(2);
-      // C
+      // C: p_r gathered from the owners (one row per thread, issued first so that its latency
+      // overlaps the K reduction), K = tau/2 * sum of the partials, w = p - K v
+      const int rr = k + 1 + tid;
+      float4 p4 = float4{0.f, 0.f, 0.f, 0.f};
+      if (rr < m) p4 = *cl.map_shared_rank(pb + rr, (unsigned)(rr % csize));
       if (wl == 0) {
         cdf ks = lane < csize ? ucdf(*cl.map_shared_rank(kp, (unsigned)lane)) : cdf0();
         ks = warp_cdsum(ks);
@@ -565,22 +678,20 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
       }
       __syncthreads();
       const cdf kv = ucdf(hk);
-      for (int r = k + 1 + tid; r < m; r += RRC_THREADS) {
-        const cdf p = ucdf(*cl.map_shared_rank(pb + r, (unsigned)(r % csize)));
-        wf[r] = c4(csub(p, cmul(kv, ucdf(vl[r]))));
-      }
+      if (rr < m) wf[rr] = c4(csub(ucdf(p4), cmul(kv, ucdf(vl[rr]))));
       __syncthreads();
       RR_LAP(3);
-      // D
+      // D: owned columns j > k: C[:, j] -= v conj(w_j) + w conj(v_j).  The owner of column k+1
+      // updates that column first, one row per thread, with the partial sums of |C_r,k+1|^2 over
+      // the rows below its subdiagonal; warp 0 then forms the next reflector (E) while the
+      // other warps update the remaining columns.
       const int nown = ncol_own - lj0;
-      for (int e = tid; e < nown * len; e += RRC_THREADS) {
-        const int q = e / len, r = k + 1 + (e - q * len);
-        const int lj = lj0 + q, j = lj * csize + crank;
-        if (j >= m) continue;
+      auto upd = [&](int lj, int r) {
+        const int j = lj * csize + crank;
+        if (j >= m) return cdf0();
         const cdf vr = ucdf(vl[r]), wr = ucdf(wf[r]), vj = ucdf(vl[j]), wj = ucdf(wf[j]);
         float4* cjr = cb + (size_t)lj * m + r;
         cdf c = ucdf(*cjr);
-        // c -= vr conj(wj) + wr conj(vj)
         c.re = dd_fma(df_neg(vr.re), wj.re, c.re);
         c.re = dd_fma(df_neg(vr.im), wj.im, c.re);
         c.re = dd_fma(df_neg(wr.re), vj.re, c.re);
@@ -590,12 +701,51 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
         c.im = dd_fma(df_neg(wr.im), vj.re, c.im);
         c.im = dd_fma(wr.re, vj.im, c.im);
         *cjr = c4(c);
+        return c;
+      };
+      if (k + 3 < m && crank == (k + 1) % csize) {
+#ifdef DKS_RR_TIMING
+        const unsigned long long o0 = clock64();
+#endif
+        dfl part{0.f, 0.f};
+        if (rr < m) {
+          const cdf c = upd(lj0, rr);
+          if (rr >= k + 3) part = dd_fma(c.im, c.im, df_mul(c.re, c.re));
+        }
+        if (32 * wl < len) {
+          part = warp_dsum(part);
+          if (lane == 0) tpart[wl] = float2{part.h, part.l};
+        }
+        __syncthreads();
+        if (wl == 0) {
+#ifdef DKS_RR_TIMING
+          const unsigned long long o1 = clock64();
+#endif
+          dfl t2{0.f, 0.f};
+          const int nw = (len + 31) / 32;
+          if (lane < nw) t2 = dfl{tpart[lane].x, tpart[lane].y};
+          t2 = warp_dsum(t2);
+          make_reflector(k + 1, &t2);   // E
+#ifdef DKS_RR_TIMING
+          if (gtid == 0) {
+            town[0] += o1 - o0;
+            town[1] += clock64() - o1;
+            ++town[2];
+          }
+#endif
+        } else {
+          for (int e = tid - 32; e < (nown - 1) * len; e += RRC_THREADS - 32) {
+            const int q = e / len;
+            upd(lj0 + 1 + q, k + 1 + (e - q * len));
+          }
+        }
+      } else {
+        for (int e = tid; e < nown * len; e += RRC_THREADS) {
+          const int q = e / len;
+          upd(lj0 + q, k + 1 + (e - q * len));
+        }
       }
-      __syncthreads();
       RR_LAP(4);
-      // E
-      if (k + 3 < m && crank == (k + 1) % csize && wl == 0) make_reflector(k + 1);
-      RR_LAP(5);
       cl.sync();
       RR_LAP(6);
     }
@@ -867,6 +1017,8 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
     printf("rr_cluster m=%d n=%d: householder %.1f multisect %.1f invit %.1f us (cycles: A %llu B %llu sync1 %llu C %llu D %llu E %llu sync2 %llu)\n", m, n,
            (tmark[3] - tmark[0]) * 1e-3, (tmark[4] - tmark[3]) * 1e-3, (tmark[5] - tmark[4]) * 1e-3,
            tlap[0], tlap[1], tlap[2], tlap[3], tlap[4], tlap[5], tlap[6]);
+  if (gtid == 0)
+    printf("  owner steps of CTA 0: %llu, column update %llu cycles, reflector %llu cycles\n", town[2], town[0], town[1]);
 #endif
 }
 
