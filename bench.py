@@ -225,6 +225,48 @@ def kernel_case(case):
     return 0
 
 
+def warm_start(P, W, wl, ctx, x_conv, x0, mode, stream):
+    """Start vectors for a consecutive solve (Sec. 3.1): the operator of the next step of an outer
+    (SCF-like) loop is stood in for by the dimer with its local potential scaled by 1.01.  Three
+    starts on that operator, one solve each (after one untimed solve for its workspace):
+      cold     the seeded random X0 with N_init = 3 (the default solve);
+      previous X0 = the converged X of the unperturbed dimer, N_init = 1;
+      balance  X0 = the large components of that X with the small ones rebuilt by the kinetic-balance
+               prescription Eq. (RKB) (dks_kinetic_balance), N_init = 1 -- the start a two-component
+               (KS/KSSO) calculation would give."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+    wl2 = dataclasses.replace(wl, v_r=wl.v_r * 1.01)
+    ctx2 = P.Context.from_workload(wl2)
+    xs = torch.empty_like(x0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def run(start, n_init, kb=False):
+        xs.copy_(start)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        if kb:
+            ctx2.kinetic_balance(0, xs)
+        lam, rep, rc = ctx2.solve([xs], NEV, tol=TOL, n_init=n_init, mode=mode, nbuf=NBUF, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rc != 0:
+            raise RuntimeError(f"warm-start solve failed: {P.ERRORS.get(rc, rc)}")
+        return lam[0], {"ms": e0.elapsed_time(e1), "iterations": rep["iterations"][0],
+                        "fp64_iterations": rep["fp64_iterations"][0], "n_init": n_init}
+
+    run(x0, 3)
+    lam_c, cold = run(x0, 3)
+    prev = x_conv.clone()
+    lam_p, warm_p = run(prev, 1)
+    lam_k, warm_k = run(prev, 1, kb=True)
+    warm_p["max_eig_diff_vs_cold"] = float(np.abs(lam_p - lam_c).max())
+    warm_k["max_eig_diff_vs_cold"] = float(np.abs(lam_k - lam_c).max())
+    return {"operator": "dimer with V scaled by 1.01", "cold": cold, "previous": warm_p, "balance": warm_k}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -234,6 +276,7 @@ def main():
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-warm-start", action="store_true")
     ap.add_argument("--ref-iterations", type=int, default=60)
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--kernel-case", default=None,
@@ -389,6 +432,8 @@ def main():
                         "algorithmic_bytes": alg, "columns": nb}
     roof["hx"] = hx_line
 
+    warm = None if args.no_warm_start else warm_start(P, W, wl, ctx, x, x0, mode, stream)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, cores, sample, full = cpu_oracle_sample(wl, NEV, acc["iterations"])
@@ -402,7 +447,7 @@ def main():
             "e2e": {"value": NEV * ws / (ms_e2e / 1e3), "unit": "eigenpairs/s",
                     "h2d_bytes_per_step": bytes_vec, "d2h_bytes_per_step": bytes_vec + 8 * NEV},
             "gpu_launches": launches, "clocks": clk, "roofline": roof,
-            "cpu_baseline": cpu, "fp64_form": fp64, "accuracy": acc}
+            "cpu_baseline": cpu, "fp64_form": fp64, "warm_start": warm, "accuracy": acc}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -119,6 +119,17 @@ int dks_filter_constants(const dks_ctx* ctx, int ik, double* C, double* Omega);
  * INVALID_ARG, CUDA. */
 int dks_apply_H(dks_ctx* ctx, int ik, const void* X, void* HX, int nb, int prec, void* stream);
 
+/* dks_kinetic_balance: Eq. (RKB) with p -> q = k+G and m = 1 (atomic units):
+ * for every column of X [nb][4][npw] (device, precision `prec`), the small
+ * two-spinor (components 2, 3) is overwritten by (sigma.q) phi / (2c), phi the
+ * large two-spinor (components 0, 1, left unchanged), sigma.q =
+ * [[q_z, q_x - i q_y], [q_x + i q_y, -q_z]].  This turns large components from
+ * a two-component (KS/KSSO) calculation, or from an earlier solve, into a start
+ * block X0 for dks_lobpcgf_solve (Sec. 3.1 on initial vectors, with N_init = 1).
+ * In place; FP64 arithmetic for complex128, FP32 for complex64.  Errors:
+ * INVALID_ARG, CUDA. */
+int dks_kinetic_balance(dks_ctx* ctx, int ik, void* X, int nb, int prec, void* stream);
+
 /* dks_filter: FY = f(H') Y = (H' - C)^2 Y / Omega^2 (Eq. filter), applied as
  * two passes of (H' - C)/Omega.  C and Omega in shifted units (see
  * dks_filter_constants).  Same layout and rules as dks_apply_H. */

@@ -278,6 +278,23 @@ class MatrixFreeH:
 
 
 # ---------------------------------------------------------------------------
+# kinetic balance (Eq. RKB): start vectors from large components (Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+
+def kinetic_balance(q, x, c):
+    """Eq. (RKB) with p -> q = k+G and m = 1: for every column of x ([band, 4, npw] or
+    [4, npw]) the small two-spinor becomes (sigma.q) phi / (2c), phi the large two-spinor
+    (components 0, 1, unchanged).  Returns a new array."""
+    y = np.array(x, dtype=np.complex128, copy=True)
+    qx, qy, qz = q[:, 0], q[:, 1], q[:, 2]
+    up, dn = y[..., 0, :], y[..., 1, :]
+    y[..., 2, :] = (qz * up + (qx - 1j * qy) * dn) / (2.0 * c)
+    y[..., 3, :] = ((qx + 1j * qy) * up - qz * dn) / (2.0 * c)
+    return y
+
+
+# ---------------------------------------------------------------------------
 # filter (Eq. filter) and preconditioner (Sec. 4: Teter et al.)
 # ---------------------------------------------------------------------------
 

@@ -67,7 +67,7 @@ EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dk
            "dks_apply_H", "dks_filter", "dks_solve_opts_default", "dks_lobpcgf_solve", "dks_precond",
            "dks_gram", "dks_rayleigh_ritz", "dks_rotate", "dks_residual_norms", "dks_strerror",
            "dks_last_error", "dks_profile_ncat", "dks_profile_name", "dks_profile_enable", "dks_profile_read",
-           "dks_rayleigh_ritz_static", "dks_gram_hermitian"]
+           "dks_rayleigh_ritz_static", "dks_gram_hermitian", "dks_kinetic_balance"]
 
 _lib = None
 
@@ -97,6 +97,7 @@ def load_library(path: str = LIB_PATH):
     lib.dks_precond.argtypes = [vp, i, vp, vp, vp, vp, i, vp, i, i, vp]
     lib.dks_gram.argtypes = [vp, vp, i, i, vp, vp, i, vp]
     lib.dks_gram_hermitian.argtypes = [vp, vp, i, i, vp, vp, i, vp]
+    lib.dks_kinetic_balance.argtypes = [vp, i, vp, i, i, vp]
     lib.dks_rayleigh_ritz.argtypes = [vp, vp, i, i, vp, vp, vp, vp]
     lib.dks_rayleigh_ritz_static.argtypes = [vp, vp, i, i, vp, vp, vp, vp]
     lib.dks_rotate.argtypes = [vp, i, i, vp, i, i, vp, d, i, vp]
@@ -219,6 +220,11 @@ class Context:
         prec = PREC_FP64_EMULATED if (emulated and _prec_of(x) == PREC_FP64) else _prec_of(x)
         _check(_lib.dks_apply_H(self._h, ik, _dptr(x), _dptr(hx), x.shape[0], prec, _stream(stream)))
         return hx
+
+    def kinetic_balance(self, ik, x, stream=None):
+        """dks_kinetic_balance: small components of x ([nb, 4, npw], in place) from its large ones."""
+        _check(_lib.dks_kinetic_balance(self._h, ik, _dptr(x), x.shape[0], _prec_of(x), _stream(stream)))
+        return x
 
     def filter(self, ik, y, fy, cshift, omega, stream=None):
         _check(_lib.dks_filter(self._h, ik, _dptr(y), _dptr(fy), y.shape[0], float(cshift), float(omega),

@@ -495,6 +495,12 @@ int dks_apply_H(dks_ctx* ctx, int ik, const void* X, void* HX, int nb, int prec,
   return apply_h<float2>(ctx, ex, ik, (const float2*)X, (float2*)HX, nb, 0.0, 1.0, st);
 }
 
+int dks_kinetic_balance(dks_ctx* ctx, int ik, void* X, int nb, int prec, void* stream) {
+  if (!ctx || ik < 0 || ik >= ctx->nk || nb < 0 || (nb && !X) || prec < 0 || prec > 2)
+    return fail(DKS_ERR_INVALID_ARG, "dks_kinetic_balance: bad argument");
+  return kinetic_balance(ctx, ik, X, nb, prec != DKS_PREC_FP32, (cudaStream_t)stream);
+}
+
 int dks_filter(dks_ctx* ctx, int ik, const void* Y, void* FY, int nb, double C, double Omega, int prec,
                void* stream) {
   if (!ctx || ik < 0 || ik >= ctx->nk || nb < 0 || (nb && (!Y || !FY)) || (prec != 0 && prec != 1) ||

@@ -161,6 +161,8 @@ template <typename V>
 int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double shift, double scale,
             cudaStream_t st);
 Exec& exec0(dks_ctx* ctx);
+// small two-spinors of nb columns from their large ones, Eq. (RKB); x complex128 (fp64) or complex64
+int kinetic_balance(dks_ctx* ctx, int ik, void* x, int nb, bool fp64, cudaStream_t st);
 
 // kernels shared by the solver and the single-step entry points
 template <typename Va, typename Vb = Va, bool Acc64 = false>

@@ -229,6 +229,47 @@ __global__ void k_dirac_only(const V* __restrict__ x, V* __restrict__ out, int n
   }
 }
 
+// Eq. (RKB) in the planewave basis (p -> q = k+G, m = 1): small = (sigma.q) large / (2c).
+// Complex128 data: FP64 arithmetic with q; complex64 data: FP32 arithmetic with the leading
+// parts of c q (scaled by 1 / (2 c^2)).
+__device__ __forceinline__ void kb_spinor(double qx, double qy, double qz, double2 u, double2 d, double2& s0,
+                                          double2& s1) {
+  s0 = double2{qz * u.x + qx * d.x + qy * d.y, qz * u.y + qx * d.y - qy * d.x};
+  s1 = double2{qx * u.x - qy * u.y - qz * d.x, qx * u.y + qy * u.x - qz * d.y};
+}
+__device__ __forceinline__ void kb_spinor(float qx, float qy, float qz, float2 u, float2 d, float2& s0,
+                                          float2& s1) {
+  s0 = float2{qz * u.x + qx * d.x + qy * d.y, qz * u.y + qx * d.y - qy * d.x};
+  s1 = float2{qx * u.x - qy * u.y - qz * d.x, qx * u.y + qy * u.x - qz * d.y};
+}
+__global__ void k_kinetic_balance64(double2* __restrict__ x, int npw, int nb, const double* __restrict__ q,
+                                    double c) {
+  const size_t total = (size_t)nb * npw;
+  const double h = 0.5 / c;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = e / npw;
+    const int p = (int)(e - b * npw);
+    double2* xb = x + b * 4 * npw + p;
+    double2 s0, s1;
+    kb_spinor(h * q[3 * p], h * q[3 * p + 1], h * q[3 * p + 2], xb[0], xb[npw], s0, s1);
+    xb[2 * (size_t)npw] = s0;
+    xb[3 * (size_t)npw] = s1;
+  }
+}
+__global__ void k_kinetic_balance32(float2* __restrict__ x, int npw, int nb, const float* __restrict__ cq,
+                                    float h) {
+  const size_t total = (size_t)nb * npw;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = e / npw;
+    const int p = (int)(e - b * npw);
+    float2* xb = x + b * 4 * npw + p;
+    float2 s0, s1;
+    kb_spinor(h * cq[6 * p], h * cq[6 * p + 2], h * cq[6 * p + 4], xb[0], xb[npw], s0, s1);
+    xb[2 * (size_t)npw] = s0;
+    xb[3 * (size_t)npw] = s1;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -365,6 +406,20 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
       DKS_TRY(gemm_nn<V>(bt, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, 2 * nb, out, 2 * npw,
                          1.0, st, scale, P_PROJ_NN));
   }
+  return DKS_OK;
+}
+
+int kinetic_balance(dks_ctx* ctx, int ik, void* x, int nb, bool fp64, cudaStream_t st) {
+  const KPoint& kp = ctx->k[ik];
+  const size_t total = (size_t)nb * kp.npw;
+  if (!total) return DKS_OK;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)ctx->num_sms * 8);
+  Prof pr(P_MISC, st, 2.0 * total * 2 * (fp64 ? 16.0 : 8.0) + 24.0 * kp.npw, 16.0 * total);
+  if (fp64)
+    k_kinetic_balance64<<<blocks, 256, 0, st>>>((double2*)x, kp.npw, nb, kp.q, ctx->c);
+  else
+    k_kinetic_balance32<<<blocks, 256, 0, st>>>((float2*)x, kp.npw, nb, kp.cq32, (float)(0.5 / (ctx->c * ctx->c)));
+  DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
 

@@ -135,3 +135,22 @@ def test_invalid_arguments_are_reported():
     with pytest.raises(P.DKSError) as e:
         P.Context.from_workload(W.make("cubic", grid=(11, 12, 12)))   # prime 11 is not a supported radix
     assert e.value.code == -9
+
+
+@pytest.mark.parametrize("name,kw", [CASES[0], CASES[2], CASES[3], ("dimer", {})])
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_kinetic_balance(name, kw, dt):
+    """Eq. (RKB): small two-spinors from the large ones, every element against the oracle; the
+    large two-spinors are left bit-identical."""
+    torch = gpu()
+    wl, ctx, hop, q = make_pair(name, **kw)
+    x = W.random_block(len(q), 3, 31)
+    if dt == "c64":
+        x = x.astype(np.complex64).astype(np.complex128)
+    ref = oop.kinetic_balance(q, x, wl.c)
+    xd = to_dev(x, torch.complex128 if dt == "c128" else torch.complex64)
+    ctx.kinetic_balance(0, xd)
+    torch.cuda.synchronize()
+    got = xd.cpu().numpy().astype(np.complex128)
+    assert np.array_equal(got[:, 0:2], x[:, 0:2])
+    assert rel_err(got[:, 2:4], ref[:, 2:4]) < (1e-14 if dt == "c128" else 1e-6)

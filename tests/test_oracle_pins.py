@@ -298,6 +298,47 @@ def test_filter_suppression_ratio():
     assert neg.max() / pos.min() < 1e-6
 
 
+def test_kinetic_balance_free_positive_eigenvector():
+    """Eq. (RKB) against the exact positive-energy eigenvector of the free Dirac block: its small
+    two-spinor is c (sigma.q) phi / (E + c^2), E = sqrt(c^2 q^2 + c^4), so the kinetic-balance
+    vector differs from it by the factor 2c^2 / (E + c^2) = 1 - q^2/(4c^2) + O(q^4/c^4)."""
+    rng = np.random.default_rng(11)
+    for c in (137.036, 20.0):
+        for _ in range(6):
+            qv = rng.normal(size=3) * rng.uniform(0.2, 3.0)
+            h = op.dirac_block(qv, c)
+            lam, vec = np.linalg.eigh(h)
+            for k in (2, 3):                                  # the two positive-energy states
+                v = vec[:, k]
+                x = np.zeros((4, 1), dtype=np.complex128)
+                x[0:2, 0] = v[0:2]
+                kb = op.kinetic_balance(qv[None, :], x, c)[2:4, 0]
+                e = lam[k] + c * c                                 # unshifted energy
+                assert math.isclose(e, math.sqrt(c * c * (qv @ qv) + c ** 4), rel_tol=1e-12)
+                ratio = 2.0 * c * c / (e + c * c)
+                assert np.allclose(v[2:4], ratio * kb, rtol=0, atol=1e-12 * np.abs(v).max())
+
+
+def test_kinetic_balance_rayleigh_quotient_closed_form():
+    """For psi = [phi, (sigma.q) phi/(2c)] the shifted free Dirac block gives the Rayleigh quotient
+    (q^2/2) / (1 + q^2/(4c^2)) exactly ((sigma.q)^2 = q^2): the nonrelativistic kinetic energy
+    in the limit.  Also |chi|^2 = q^2 |phi|^2 / (4c^2) per planewave."""
+    rng = np.random.default_rng(12)
+    c = 137.036
+    q = rng.normal(size=(7, 3)) * 2.0
+    x = rng.normal(size=(3, 4, 7)) + 1j * rng.normal(size=(3, 4, 7))
+    y = op.kinetic_balance(q, x, c)
+    assert np.array_equal(y[:, 0:2], x[:, 0:2])
+    q2 = np.einsum("ij,ij->i", q, q)
+    np.testing.assert_allclose((np.abs(y[:, 2:4]) ** 2).sum(axis=1),
+                               q2 * (np.abs(x[:, 0:2]) ** 2).sum(axis=1) / (4 * c * c), rtol=1e-13)
+    for b in range(3):
+        for p in range(7):
+            psi = y[b, :, p]
+            rq = (psi.conj() @ op.dirac_block(q[p], c) @ psi).real / (psi.conj() @ psi).real
+            assert math.isclose(rq, 0.5 * q2[p] / (1 + q2[p] / (4 * c * c)), rel_tol=1e-12)
+
+
 def test_teter_factor_limits():
     """Teter-Payne-Allan design: K = 1 - O(x^4) near 0 (flat to third order) and K ~ 1/(2x)."""
     x = np.array([1e-3, 2e-3])
