@@ -102,6 +102,21 @@ int dks_create(const dks_cell* cell, double ecut, const dks_potentials* pot,
                const dks_projectors* proj, dks_ctx** out);
 void dks_destroy(dks_ctx* ctx);
 
+/* Operator models.  DKS: the shifted four-component Dirac-Kohn-Sham H' of
+ * Eq. (vDKS), columns [4][npw] (large then small two-spinor).  KSSO: the
+ * two-component Kohn-Sham operator with spin-orbit coupling of the paper's KSSO
+ * module (Sec. 4), |k+G|^2/2 + V + sum D beta beta^H on a two-spinor, columns
+ * [2][npw], energies unshifted; its solve is Algorithm 1 without the filter
+ * (standard LOBPCG), and dks_kinetic_balance does not apply to it. */
+#define DKS_MODEL_DKS 0
+#define DKS_MODEL_KSSO 1
+/* dks_create for a given model (dks_create is model DKS).  Every entry point
+ * taking a ctx then works on columns of dks_ncomp(ctx) x npw elements. */
+int dks_create_model(const dks_cell* cell, double ecut, const dks_potentials* pot,
+                     const dks_projectors* proj, int model, dks_ctx** out);
+/* Components per column: 4 (DKS) or 2 (KSSO). */
+int dks_ncomp(const dks_ctx* ctx, int* ncomp);
+
 /* Basis size of k-point ik, and its Miller triples (host int[npw*3]). */
 int dks_npw(const dks_ctx* ctx, int ik, int* npw);
 int dks_basis(const dks_ctx* ctx, int ik, int* miller);
@@ -119,7 +134,7 @@ int dks_filter_constants(const dks_ctx* ctx, int ik, double* C, double* Omega);
  * INVALID_ARG, CUDA. */
 int dks_apply_H(dks_ctx* ctx, int ik, const void* X, void* HX, int nb, int prec, void* stream);
 
-/* dks_kinetic_balance: Eq. (RKB) with p -> q = k+G and m = 1 (atomic units):
+/* dks_kinetic_balance (DKS contexts only): Eq. (RKB) with p -> q = k+G and m = 1 (atomic units):
  * for every column of X [nb][4][npw] (device, precision `prec`), the small
  * two-spinor (components 2, 3) is overwritten by (sigma.q) phi / (2c), phi the
  * large two-spinor (components 0, 1, left unchanged), sigma.q =
@@ -256,8 +271,9 @@ int dks_rotate(const void* Z, int rows, int nz, const void* W, int ldw, int n, v
                double beta, int prec, void* stream);
 
 /* Alg. 1 line 16-17: norms[j] = ||HX[j] - lam[j] X[j]||_2.  The residual and the sum over the
- * four components of a planewave are formed in the storage precision (DKS_PREC_FP32: FP32,
- * otherwise FP64); the sum over planewaves is accumulated in FP64.  rows % 4 == 0. */
+ * components of a planewave are formed in the storage precision (DKS_PREC_FP32: FP32,
+ * otherwise FP64); the sum over planewaves is accumulated in FP64.  rows even (4 npw for
+ * DKS four-spinors, 2 npw for KSSO two-spinors). */
 int dks_residual_norms(const void* X, const void* HX, const double* lam, int rows, int n,
                        double* norms, int prec, void* stream);
 

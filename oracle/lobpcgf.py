@@ -91,14 +91,16 @@ def _cols(blk):
     return blk.reshape(blk.shape[0], -1).T
 
 
-def _blk(mat, npw):
-    return mat.T.reshape(mat.shape[1], 4, npw)
+def _blk(mat, npw, ncomp=4):
+    return mat.T.reshape(mat.shape[1], ncomp, npw)
 
 
 def lobpcgf(hop, q, x0, n, cshift, omega, n_init=3, n_iter=200, tol=1e-6, nconv=None,
             use_filter=True, precond="teter", callback=None):
-    """Algorithm 1.  hop: x[nb,4,npw] -> H'x.  Returns SolveResult (lam ascending, x[n,4,npw])."""
+    """Algorithm 1.  hop: x[nb,ncomp,npw] -> H'x (ncomp = 4 four-spinors; 2 for the KSSO operator,
+    run with use_filter=False).  Returns SolveResult (lam ascending, x[n,ncomp,npw])."""
     npw = q.shape[0]
+    nc = np.asarray(x0).shape[1]
     nconv = n if nconv is None else nconv
     start = hop.count if hasattr(hop, "count") else 0
 
@@ -125,7 +127,7 @@ def lobpcgf(hop, q, x0, n, cshift, omega, n_init=3, n_iter=200, tol=1e-6, nconv=
     converged = False
     it = 0
     for it in range(1, n_iter + 1):                                     # line 8
-        yb = tinv(_blk(xm[:, act], npw), _blk(rm, npw))                 # line 9
+        yb = tinv(_blk(xm[:, act], npw, nc), _blk(rm, npw, nc))         # line 9
         yb = fh(yb)                                                     # line 10
         ym = _cols(yb)
         hym = _cols(hop(yb))
@@ -147,7 +149,7 @@ def lobpcgf(hop, q, x0, n, cshift, omega, n_init=3, n_iter=200, tol=1e-6, nconv=
         va = v[n:, act]                                                 # line 21
         pm, hpm = zm[:, n:] @ va, hzm[:, n:] @ va                       # line 22: [0, Y, P] V
     used = (hop.count - start) if hasattr(hop, "count") else -1
-    return SolveResult(lam=lam, x=_blk(xm, npw), iterations=it, converged=converged,
+    return SolveResult(lam=lam, x=_blk(xm, npw, nc), iterations=it, converged=converged,
                        resnorms=norms, history=history, h_applications=used)
 
 

@@ -278,6 +278,66 @@ class MatrixFreeH:
 
 
 # ---------------------------------------------------------------------------
+# KSSO: two-component Kohn-Sham operator with spin-orbit coupling (Sec. 4, module KSSO)
+# ---------------------------------------------------------------------------
+
+
+def dense_hamiltonian_ksso(wl, miller, q, with_local=True, with_nonlocal=True):
+    """Dense 2npw x 2npw KSSO operator on two-spinors (index comp*npw + pw): the kinetic energy
+    |q|^2/2 on the diagonal, V as Vhat[(m_i - m_j) mod N] on each spin, and the spin-orbit
+    projector operator N of Eq. (HGH) on the two-spinor.  Energies are not shifted."""
+    npw = q.shape[0]
+    h = np.zeros((2 * npw, 2 * npw), dtype=np.complex128)
+    ek = 0.5 * np.einsum("ij,ij->i", q, q)
+    h[np.arange(2 * npw), np.arange(2 * npw)] = np.concatenate([ek, ek])
+    if with_local:
+        vh = vhat(wl.v_r)
+        dm = np.mod(miller[:, None, :] - miller[None, :, :], np.asarray(wl.grid))
+        vloc = vh[dm[..., 0], dm[..., 1], dm[..., 2]]
+        for a in range(2):
+            h[a * npw:(a + 1) * npw, a * npw:(a + 1) * npw] += vloc
+    if with_nonlocal and int(np.max(wl.lmax, initial=-1)) >= 0:
+        h += nonlocal_dense(wl, q)
+    return h
+
+
+class MatrixFreeKSSO(MatrixFreeH):
+    """x[band, comp, pw] (comp = spin up, down) -> H_KSSO x with numpy FFTs for V and B D B^H."""
+
+    def kinetic(self, x):
+        ek = 0.5 * np.einsum("ij,ij->i", self.q, self.q)
+        return ek[None, None, :] * x
+
+    def local(self, x):
+        nb = x.shape[0]
+        grid = self.wl.grid
+        y = np.zeros_like(x)
+        for b in range(nb):
+            for a in range(2):
+                g = np.zeros(int(np.prod(grid)), dtype=np.complex128)
+                g[self.gidx] = x[b, a]
+                psi = np.fft.ifftn(g.reshape(grid))
+                y[b, a] = np.fft.fftn(self.v * psi).reshape(-1)[self.gidx]
+        return y
+
+    def nonlocal_(self, x):
+        nb, npw = x.shape[0], self.npw
+        xt = x.reshape(nb, 2 * npw).T                    # one two-spinor column per band
+        yt = self.b @ (self.dvec[:, None] * (self.b.conj().T @ xt))
+        return yt.T.reshape(nb, 2, npw)
+
+    def __call__(self, x):
+        x = np.asarray(x, dtype=np.complex128)
+        self.count += x.shape[0]
+        y = self.kinetic(x)
+        if self.v is not None:
+            y += self.local(x)
+        if self.b is not None:
+            y += self.nonlocal_(x)
+        return y
+
+
+# ---------------------------------------------------------------------------
 # kinetic balance (Eq. RKB): start vectors from large components (Sec. 3.1)
 # ---------------------------------------------------------------------------
 

@@ -6,8 +6,9 @@ memory and streams.  If the shared library is missing or fails to load, every
 entry point raises -- there is no CPU fallback.
 
 Layouts follow include/dks.h: vector blocks are complex tensors of shape
-[nb, 4, npw] (complex128 for FP64, complex64 for FP32), planewaves in the
-canonical (lexicographic Miller) order returned by Context.basis(ik).
+[nb, ncomp, npw] (ncomp = 4 for the DKS model, 2 for KSSO; complex128 for FP64,
+complex64 for FP32), planewaves in the canonical (lexicographic Miller) order
+returned by Context.basis(ik).
 """
 from __future__ import annotations
 
@@ -67,7 +68,8 @@ EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dk
            "dks_apply_H", "dks_filter", "dks_solve_opts_default", "dks_lobpcgf_solve", "dks_precond",
            "dks_gram", "dks_rayleigh_ritz", "dks_rotate", "dks_residual_norms", "dks_strerror",
            "dks_last_error", "dks_profile_ncat", "dks_profile_name", "dks_profile_enable", "dks_profile_read",
-           "dks_rayleigh_ritz_static", "dks_gram_hermitian", "dks_kinetic_balance"]
+           "dks_rayleigh_ritz_static", "dks_gram_hermitian", "dks_kinetic_balance", "dks_create_model",
+           "dks_ncomp"]
 
 _lib = None
 
@@ -85,6 +87,8 @@ def load_library(path: str = LIB_PATH):
     lib.dks_destroy.argtypes = [vp]
     lib.dks_destroy.restype = None
     lib.dks_npw.argtypes = [vp, i, C.POINTER(i)]
+    lib.dks_create_model.argtypes = [C.POINTER(_Cell), d, C.POINTER(_Pot), C.POINTER(_Proj), i, C.POINTER(vp)]
+    lib.dks_ncomp.argtypes = [vp, C.POINTER(i)]
     lib.dks_basis.argtypes = [vp, i, C.POINTER(i)]
     lib.dks_nproj.argtypes = [vp, C.POINTER(i)]
     lib.dks_filter_constants.argtypes = [vp, i, C.POINTER(d), C.POINTER(d)]
@@ -131,6 +135,11 @@ def _stream(stream):
     return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
+def _complex128():
+    import torch
+    return torch.complex128
+
+
 def _prec_of(t):
     import torch
     if t.dtype == torch.complex128:
@@ -140,11 +149,16 @@ def _prec_of(t):
     raise TypeError("blocks must be complex128 or complex64")
 
 
+MODELS = {"dks": 0, "ksso": 1}
+
+
 class Context:
     """Owns a dks_ctx: planewave spheres, FFT plans, V(r) and projector tables on the GPU."""
 
     def __init__(self, lattice, grid, c, kfrac, ecut, v_r=None, pos=None, lmax=None, rl=None, d=None,
-                 ecut_k=None):
+                 ecut_k=None, model="dks"):
+        """model "dks": four-component H' (columns [4, npw]); "ksso": the two-component KSSO
+        operator (columns [2, npw]) solved by Algorithm 1 without the filter."""
         lib = load_library()
         self._keep = []
         cell = _Cell()
@@ -167,8 +181,14 @@ class Context:
             proj.rl = self._arr(np.ascontiguousarray(rl, dtype=np.float64).reshape(-1), C.c_double)
             proj.d = self._arr(np.ascontiguousarray(d, dtype=np.float64).reshape(-1), C.c_double)
         self._h = C.c_void_p()
-        _check(lib.dks_create(C.byref(cell), float(ecut if ecut is not None else 0.0), C.byref(pot),
-                              C.byref(proj), C.byref(self._h)))
+        if model not in MODELS:
+            raise ValueError(f"model must be one of {sorted(MODELS)}")
+        _check(lib.dks_create_model(C.byref(cell), float(ecut if ecut is not None else 0.0), C.byref(pot),
+                                    C.byref(proj), MODELS[model], C.byref(self._h)))
+        nc = C.c_int()
+        _check(lib.dks_ncomp(self._h, C.byref(nc)))
+        self.ncomp = nc.value
+        self.model = model
         self.nk = cell.nk
         self.c = float(c)
         self._keep = []
@@ -178,10 +198,10 @@ class Context:
         return a.ctypes.data_as(C.POINTER(ctype))
 
     @classmethod
-    def from_workload(cls, wl):
+    def from_workload(cls, wl, model="dks"):
         """Build from any object with the attributes of workloads.Workload (duck-typed)."""
         return cls(wl.lattice, wl.grid, wl.c, wl.kfrac, None, v_r=wl.v_r, pos=wl.pos, lmax=wl.lmax,
-                   rl=wl.rl, d=wl.d, ecut_k=wl.ecut_k)
+                   rl=wl.rl, d=wl.d, ecut_k=wl.ecut_k, model=model)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -216,22 +236,39 @@ class Context:
         return cs.value, om.value
 
     # ---- operator
+    def _block(self, ik, *ts, nb=None):
+        """Shape check of device blocks before their pointers cross the ABI (which cannot check):
+        [nb, ncomp, npw], contiguous, one dtype; returns nb."""
+        npw = self.npw(ik)
+        nb = ts[0].shape[0] if nb is None else nb
+        for t in ts:
+            if t.dim() != 3 or t.shape[1] != self.ncomp or t.shape[2] != npw or t.shape[0] < nb:
+                raise ValueError(f"block of shape {tuple(t.shape)}: need [{nb}, {self.ncomp}, {npw}]")
+            if not t.is_contiguous() or t.dtype != ts[0].dtype:
+                raise ValueError("blocks must be contiguous and of one dtype")
+        return nb
+
     def apply_H(self, ik, x, hx, stream=None, emulated=False):
+        nb = self._block(ik, x, hx)
         prec = PREC_FP64_EMULATED if (emulated and _prec_of(x) == PREC_FP64) else _prec_of(x)
-        _check(_lib.dks_apply_H(self._h, ik, _dptr(x), _dptr(hx), x.shape[0], prec, _stream(stream)))
+        _check(_lib.dks_apply_H(self._h, ik, _dptr(x), _dptr(hx), nb, prec, _stream(stream)))
         return hx
 
     def kinetic_balance(self, ik, x, stream=None):
         """dks_kinetic_balance: small components of x ([nb, 4, npw], in place) from its large ones."""
-        _check(_lib.dks_kinetic_balance(self._h, ik, _dptr(x), x.shape[0], _prec_of(x), _stream(stream)))
+        nb = self._block(ik, x)
+        _check(_lib.dks_kinetic_balance(self._h, ik, _dptr(x), nb, _prec_of(x), _stream(stream)))
         return x
 
     def filter(self, ik, y, fy, cshift, omega, stream=None):
-        _check(_lib.dks_filter(self._h, ik, _dptr(y), _dptr(fy), y.shape[0], float(cshift), float(omega),
+        nb = self._block(ik, y, fy)
+        _check(_lib.dks_filter(self._h, ik, _dptr(y), _dptr(fy), nb, float(cshift), float(omega),
                                _prec_of(y), _stream(stream)))
         return fy
 
     def precond(self, ik, x, hx, lam, act, y, precond=PRECOND_TETER, stream=None):
+        self._block(ik, x, hx)
+        self._block(ik, y, nb=act.shape[0])
         _check(_lib.dks_precond(self._h, ik, _dptr(x), _dptr(hx), _dptr(lam), _dptr(act), act.shape[0],
                                 _dptr(y), precond, _prec_of(x), _stream(stream)))
         return y
@@ -240,7 +277,7 @@ class Context:
     def solve(self, x_list, nev, tol=1e-6, n_init=3, n_iter=200, mode=MODE_FP64, refine_tol=1e-5,
               precond=PRECOND_TETER, use_filter=True, cshift=None, omega=None, nev_k=None, nbuf=0,
               stream=None, check=True, chol_tol=None, drop_tol=None, emulate_fp64=True, concurrency=0):
-        """Algorithm 1 on every k-point.  x_list[ik]: complex128 [nev_k+nbuf, 4, npw] (X0 in, X out).
+        """Algorithm 1 on every k-point.  x_list[ik]: complex128 [nev_k+nbuf, ncomp, npw] (X0 in, X out).
         Returns (eigenvalues per k as numpy arrays, report dict, status code)."""
         opts = SolveOpts()
         _lib.dks_solve_opts_default(C.byref(opts))
@@ -261,6 +298,12 @@ class Context:
             self._keep.append(arr)
             opts.nev_k = arr.ctypes.data_as(C.POINTER(C.c_int))
         opts.stream = _stream(stream)
+        if len(x_list) != self.nk:
+            raise ValueError(f"need one block per k-point ({self.nk})")
+        for ik, t in enumerate(x_list):
+            self._block(ik, t, nb=nevs[ik] + int(nbuf))
+            if t.dtype != _complex128():
+                raise ValueError("solve blocks are complex128")
         eig = np.zeros(sum(nevs), dtype=np.float64)
         ptrs = (C.c_void_p * self.nk)(*[t.data_ptr() for t in x_list])
         rep = SolveReport()

@@ -455,6 +455,23 @@ int dks_create(const dks_cell* cell, double ecut, const dks_potentials* pot, con
 
 void dks_destroy(dks_ctx* ctx) { free_ctx(ctx); }
 
+int dks_create_model(const dks_cell* cell, double ecut, const dks_potentials* pot, const dks_projectors* proj,
+                     int model, dks_ctx** out) {
+  if (model != DKS_MODEL_DKS && model != DKS_MODEL_KSSO) {
+    if (out) *out = nullptr;
+    return fail(DKS_ERR_INVALID_ARG, "dks_create_model: unknown model");
+  }
+  const int rc = dks_create(cell, ecut, pot, proj, out);
+  if (rc == DKS_OK && model == DKS_MODEL_KSSO) (*out)->ncomp = 2;
+  return rc;
+}
+
+int dks_ncomp(const dks_ctx* ctx, int* ncomp) {
+  if (!ctx || !ncomp) return fail(DKS_ERR_INVALID_ARG, "dks_ncomp: bad argument");
+  *ncomp = ctx->ncomp;
+  return DKS_OK;
+}
+
 int dks_npw(const dks_ctx* ctx, int ik, int* npw) {
   if (!ctx || !npw || ik < 0 || ik >= ctx->nk) return fail(DKS_ERR_INVALID_ARG, "dks_npw: bad argument");
   *npw = ctx->k[ik].npw;
@@ -496,8 +513,8 @@ int dks_apply_H(dks_ctx* ctx, int ik, const void* X, void* HX, int nb, int prec,
 }
 
 int dks_kinetic_balance(dks_ctx* ctx, int ik, void* X, int nb, int prec, void* stream) {
-  if (!ctx || ik < 0 || ik >= ctx->nk || nb < 0 || (nb && !X) || prec < 0 || prec > 2)
-    return fail(DKS_ERR_INVALID_ARG, "dks_kinetic_balance: bad argument");
+  if (!ctx || ik < 0 || ik >= ctx->nk || nb < 0 || (nb && !X) || prec < 0 || prec > 2 || ctx->ncomp != 4)
+    return fail(DKS_ERR_INVALID_ARG, "dks_kinetic_balance: bad argument (DKS contexts only)");
   return kinetic_balance(ctx, ik, X, nb, prec != DKS_PREC_FP32, (cudaStream_t)stream);
 }
 
@@ -508,7 +525,7 @@ int dks_filter(dks_ctx* ctx, int ik, const void* Y, void* FY, int nb, double C, 
     return fail(DKS_ERR_INVALID_ARG, "dks_filter: bad argument");
   if (!nb) return DKS_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t elems = (size_t)nb * 4 * ctx->k[ik].npw;
+  const size_t elems = (size_t)nb * ctx->ncomp * ctx->k[ik].npw;
   const size_t es = prec == DKS_PREC_FP64 ? sizeof(double2) : sizeof(float2);
   void* tmp = nullptr;
   DKS_CUDA_TRY(cudaMallocAsync(&tmp, elems * es, st));
@@ -548,13 +565,13 @@ int dks_precond(dks_ctx* ctx, int ik, const void* X, const void* HX, const doubl
   DKS_CUDA_TRY(cudaMallocAsync((void**)&stats, (size_t)3 * ncol * sizeof(double), st));
   int rc;
   if (prec != DKS_PREC_FP32) {
-    rc = col_stats<double2>((const double2*)X, nullptr, nullptr, kp.ek, kp.npw, ncol, stats, st);
+    rc = col_stats<double2>((const double2*)X, nullptr, nullptr, kp.ek, kp.npw, ncol, stats, st, ctx->ncomp);
     if (!rc) rc = precond_apply<double2>((const double2*)X, (const double2*)HX, lam, stats, act, nact, kp.ek, kp.npw,
-                                         precond, (double2*)Y, st);
+                                         precond, (double2*)Y, st, ctx->ncomp);
   } else {
-    rc = col_stats<float2>((const float2*)X, nullptr, nullptr, kp.ek, kp.npw, ncol, stats, st);
+    rc = col_stats<float2>((const float2*)X, nullptr, nullptr, kp.ek, kp.npw, ncol, stats, st, ctx->ncomp);
     if (!rc) rc = precond_apply<float2>((const float2*)X, (const float2*)HX, lam, stats, act, nact, kp.ek, kp.npw,
-                                        precond, (float2*)Y, st);
+                                        precond, (float2*)Y, st, ctx->ncomp);
   }
   cudaFreeAsync(stats, st);
   return rc;
@@ -637,17 +654,18 @@ int dks_rotate(const void* Z, int rows, int nz, const void* W, int ldw, int n, v
 
 int dks_residual_norms(const void* X, const void* HX, const double* lam, int rows, int n, double* norms, int prec,
                        void* stream) {
-  if (rows <= 0 || rows % 4 || n <= 0 || !X || !HX || !lam || !norms || prec < 0 || prec > 2)
+  if (rows <= 0 || rows % 2 || n <= 0 || !X || !HX || !lam || !norms || prec < 0 || prec > 2)
     return fail(DKS_ERR_INVALID_ARG, "dks_residual_norms: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
+  const int nc = rows % 4 ? 2 : 4;   // the column sums do not depend on the grouping of rows
   double* stats = nullptr;
   double* ek = nullptr;
   DKS_CUDA_TRY(cudaMallocAsync((void**)&stats, (size_t)3 * n * sizeof(double), st));
-  DKS_CUDA_TRY(cudaMallocAsync((void**)&ek, (size_t)(rows / 4) * sizeof(double), st));
-  DKS_CUDA_TRY(cudaMemsetAsync(ek, 0, (size_t)(rows / 4) * sizeof(double), st));
+  DKS_CUDA_TRY(cudaMallocAsync((void**)&ek, (size_t)(rows / nc) * sizeof(double), st));
+  DKS_CUDA_TRY(cudaMemsetAsync(ek, 0, (size_t)(rows / nc) * sizeof(double), st));
   int rc = prec != DKS_PREC_FP32
-               ? col_stats<double2>((const double2*)X, (const double2*)HX, lam, ek, rows / 4, n, stats, st)
-               : col_stats<float2>((const float2*)X, (const float2*)HX, lam, ek, rows / 4, n, stats, st);
+               ? col_stats<double2>((const double2*)X, (const double2*)HX, lam, ek, rows / nc, n, stats, st, nc)
+               : col_stats<float2>((const float2*)X, (const float2*)HX, lam, ek, rows / nc, n, stats, st, nc);
   if (!rc) {
     // norms[j] = sqrt(stats[3j])
     std::vector<double> h((size_t)3 * n);

@@ -113,6 +113,7 @@ struct dks_ctx {
   // entry points and serial solves, exec[1..] the concurrent k-point workers
   std::vector<dks::Exec*> exec;
   size_t chunk_budget = 64u << 20;   // bytes of FFT intermediates per chunk (L2-resident)
+  int ncomp = 4;                     // components per column: 4 (DKS, Eq. vDKS) or 2 (KSSO two-spinors)
   int device = 0;
   int num_sms = 0;
 };
@@ -196,12 +197,13 @@ int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const
             int cat = P_ROTATE);
 // out (k x n) = alpha * a (k x m) * (diag(wscale) w) + beta * out; wscale may be NULL;
 // FP64 arithmetic when a or out is complex128
+// columns of ncomp x npw elements (ncomp = 4: DKS four-spinors, 2: KSSO two-spinors)
 template <typename V>
 int col_stats(const V* x, const V* hx, const double* lam, const double* ek, int npw, int n,
-              double* stats, cudaStream_t st);  // stats[3j..]: |hx - lam x|^2, |x|^2, sum ek|x|^2
+              double* stats, cudaStream_t st, int ncomp = 4);  // stats[3j..]: |hx - lam x|^2, |x|^2, sum ek|x|^2
 template <typename V, typename Vo = V>
 int precond_apply(const V* x, const V* hx, const double* lam, const double* stats, const int* act,
-                  int nact, const double* ek, int npw, int precond, Vo* y, cudaStream_t st);
+                  int nact, const double* ek, int npw, int precond, Vo* y, cudaStream_t st, int ncomp = 4);
 int rayleigh_ritz(const double2* a, const double2* s, int nz, int n, double2* v, double* lam,
                   int* info, double2* scratch, cudaStream_t st, double chol_tol = 1e-12,
                   double drop_tol = 1e-12);

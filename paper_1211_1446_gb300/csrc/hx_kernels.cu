@@ -208,6 +208,65 @@ __global__ void __launch_bounds__(256) k_stick_forward(
   }
 }
 
+// KSSO two-spinors: forward z-transform of the V psi sticks of both components, gathered onto
+// the sphere, plus the kinetic term: out = scale ((|k+G|^2/2 - shift) x + V psi)
+template <typename Vg, typename V>
+__global__ void __launch_bounds__(256) k_stick_forward_ks(
+    const Vg* __restrict__ t, const Vg* __restrict__ x, Vg* __restrict__ out, int npw, int nsticks,
+    const int* __restrict__ stick_start, const int* __restrict__ pw_stick, const int* __restrict__ pw_iz,
+    AxisPlan p3, const V* __restrict__ tw3, const double* __restrict__ ek, double shift, double scale, int spb,
+    int ls) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* line = reinterpret_cast<V*>(smem_raw);   // 2*spb lines of stride ls (odd)
+  const int n3 = p3.n;
+  const int s0 = blockIdx.x * spb;
+  const int ns = min(spb, nsticks - s0);
+  const int b = blockIdx.y;
+  const float rns = __fdividef(1.0f, (float)ns);
+  for (int a = 0; a < 2; ++a) {
+    const Vg* ta = t + (size_t)(b * 2 + a) * n3 * nsticks + s0;
+    for (int e = threadIdx.x; e < ns * n3; e += blockDim.x) {
+      const int z = qdiv(e, ns, rns), s = e - z * ns;
+      line[(a * spb + s) * ls + z] = to_s<V>(ta[(size_t)z * nsticks + s]);
+    }
+  }
+  __syncthreads();
+  fft_lines<V, true, true>(line, 2 * spb, ls, 1, p3, tw3);
+  const size_t fo = (size_t)b * 2 * npw;
+  const int q0 = stick_start[s0], q1 = stick_start[s0 + ns];
+  for (int p = q0 + threadIdx.x; p < q1; p += blockDim.x) {
+    const int s = pw_stick[p] - s0, iz = pw_iz[p];
+    if constexpr (std::is_same<Vg, float2>::value && std::is_same<V, float2>::value) {
+      const float kin = (float)(ek[p] - shift), sc = (float)scale;
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const float2 xv = x[fo + (size_t)a * npw + p], loc = line[(a * spb + s) * ls + iz];
+        out[fo + (size_t)a * npw + p] = float2{sc * fmaf(kin, xv.x, loc.x), sc * fmaf(kin, xv.y, loc.y)};
+      }
+    } else {
+      const double kin = ek[p] - shift;
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const double2 xv = to_d2(x[fo + (size_t)a * npw + p]), loc = to_d2(line[(a * spb + s) * ls + iz]);
+        out[fo + (size_t)a * npw + p] = from_d2<Vg>({scale * fma(kin, xv.x, loc.x), scale * fma(kin, xv.y, loc.y)});
+      }
+    }
+  }
+}
+
+// KSSO kinetic term alone (no local potential on the grid): fields of npw planewaves
+template <typename V>
+__global__ void k_kinetic_only(const V* __restrict__ x, V* __restrict__ out, int npw, int nfields,
+                               const double* __restrict__ ek, double shift, double scale) {
+  const size_t total = (size_t)nfields * npw;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e % npw);
+    const double k = scale * (ek[p] - shift);
+    const double2 xv = to_d2(x[e]);
+    out[e] = from_d2<V>({k * xv.x, k * xv.y});
+  }
+}
+
 // Dirac term alone (no local potential on the grid)
 template <typename V>
 __global__ void k_dirac_only(const V* __restrict__ x, V* __restrict__ out, int npw, int nb,
@@ -305,11 +364,12 @@ static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int n
   const VR* vp = df ? (const VR*)ctx->vpermdf : fp64 ? (const VR*)ctx->vperm64 : (const VR*)ctx->vperm32;
   const int ls = n3 | 1;                      // odd line stride: conflict-free shared memory
   const int ld = ctx->plane_ld;
+  const int nc = ctx->ncomp;                   // fields per band: 4 (DKS) or 2 (KSSO)
   const int spb_a = pick_spb(ls, sizeof(Vs), 1, 32 * 1024);
-  const int spb_c = pick_spb(ls, sizeof(Vs), 4, 64 * 1024);
+  const int spb_c = pick_spb(ls, sizeof(Vs), nc, 64 * 1024);
   const size_t sm_a = (size_t)spb_a * ls * sizeof(Vs);
   const size_t sm_b = (size_t)ctx->grid[0] * ld * sizeof(Vs);
-  const size_t sm_c = (size_t)4 * spb_c * ls * sizeof(Vs);
+  const size_t sm_c = (size_t)nc * spb_c * ls * sizeof(Vs);
   // threads of the plane kernel: the largest pass has N1 N2 / (smallest radix) butterflies;
   int rmin = 8;
   for (int a = 0; a < 2; ++a)
@@ -319,17 +379,18 @@ static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int n
   const int tb_plane = std::min(512, std::max(128, (nbf / 2 + 31) / 32 * 32));
   DKS_TRY(set_smem<Vs>((const void*)k_stick_inverse<Vg, Vs>, sm_a));
   DKS_TRY(set_smem<Vs>((const void*)k_plane<Vg, Vs>, sm_b));
-  DKS_TRY(set_smem<Vs>((const void*)k_stick_forward<Vg, Vs>, sm_c));
+  DKS_TRY(set_smem<Vs>(nc == 4 ? (const void*)k_stick_forward<Vg, Vs> : (const void*)k_stick_forward_ks<Vg, Vs>,
+                       sm_c));
   const int cat32 = fp64 ? 0 : kProf32;
   for (int b0 = 0; b0 < nb; b0 += chunk) {
     const int nbc = std::min(chunk, nb - b0);
-    const Vg* xb = x + (size_t)b0 * 4 * npw;
-    const double nf = 4.0 * nbc, es = (double)sizeof(Vg);
+    const Vg* xb = x + (size_t)b0 * nc * npw;
+    const double nf = (double)nc * nbc, es = (double)sizeof(Vg);
     const double tb = nf * (double)field_elems * es;          // one pass over the stick buffer
     const double f3 = 5.0 * n3 * std::log2((double)n3) * kp.nsticks * nf;
     {
       Prof pr(P_STICK_INV + cat32, st, nf * npw * es + tb, f3);
-      dim3 ga((kp.nsticks + spb_a - 1) / spb_a, 4 * nbc);
+      dim3 ga((kp.nsticks + spb_a - 1) / spb_a, nc * nbc);
       k_stick_inverse<Vg, Vs><<<ga, 256, sm_a, st>>>(xb, tbuf, npw, kp.nsticks, kp.stick_start, kp.pw_stick,
                                                      kp.pw_iz, ctx->plan[2], tw3, spb_a, ls);
     }
@@ -337,16 +398,22 @@ static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int n
       const double nn = (double)ctx->grid[0] * ctx->grid[1];
       Prof pr(P_PLANE + cat32, st, 2.0 * tb + (double)ctx->ng * es / 2,
               nf * n3 * (10.0 * nn * std::log2(nn) + 2.0 * nn));
-      dim3 gb(n3, 4 * nbc);
+      dim3 gb(n3, nc * nbc);
       k_plane<Vg, Vs><<<gb, tb_plane, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0], ctx->plan[1],
                                                   ld, n3, tw1, tw2, vp);
     }
     {
-      Prof pr(P_STICK_FWD + cat32, st, tb + 2.0 * nf * npw * es + 24.0 * npw, f3 + 64.0 * nbc * npw);
+      Prof pr(P_STICK_FWD + cat32, st, tb + 2.0 * nf * npw * es + 24.0 * npw,
+              f3 + (nc == 4 ? 64.0 : 8.0) * nbc * npw);
       dim3 gc((kp.nsticks + spb_c - 1) / spb_c, nbc);
-      k_stick_forward<Vg, Vs><<<gc, 256, sm_c, st>>>(tbuf, xb, out + (size_t)b0 * 4 * npw, npw, kp.nsticks,
-                                                     kp.stick_start, kp.pw_stick, kp.pw_iz, ctx->plan[2], tw3,
-                                                     kp.q, kp.cq32, ctx->c, shift, scale, spb_c, ls);
+      if (nc == 4)
+        k_stick_forward<Vg, Vs><<<gc, 256, sm_c, st>>>(tbuf, xb, out + (size_t)b0 * 4 * npw, npw, kp.nsticks,
+                                                       kp.stick_start, kp.pw_stick, kp.pw_iz, ctx->plan[2], tw3,
+                                                       kp.q, kp.cq32, ctx->c, shift, scale, spb_c, ls);
+      else
+        k_stick_forward_ks<Vg, Vs><<<gc, 256, sm_c, st>>>(tbuf, xb, out + (size_t)b0 * 2 * npw, npw, kp.nsticks,
+                                                          kp.stick_start, kp.pw_stick, kp.pw_iz, ctx->plan[2], tw3,
+                                                          kp.ek, shift, scale, spb_c, ls);
     }
   }
   DKS_CUDA_TRY(cudaGetLastError());
@@ -361,12 +428,14 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
   const int npw = kp.npw;
   const bool fp64 = sizeof(V) == sizeof(double2);
   const int n3 = ctx->grid[2];
-  const size_t zp_elems = (size_t)ctx->nproj * 2 * nb;
+  const int nc = ctx->ncomp;
+  const int ncol = nb * nc / 2;   // projector columns x~: two-spinors of 2 npw rows
+  const size_t zp_elems = (size_t)ctx->nproj * ncol;
   const size_t field_elems = (size_t)kp.nsticks * n3;
   // chunk of bands whose intermediates stay within the L2-resident budget
-  int chunk = (int)std::max<size_t>(1, ctx->chunk_budget / (4 * field_elems * sizeof(V)));
+  int chunk = (int)std::max<size_t>(1, ctx->chunk_budget / (nc * field_elems * sizeof(V)));
   chunk = std::min(chunk, nb);
-  const size_t need = zp_elems * sizeof(double2) + 256 + (ctx->has_v ? 4 * chunk * field_elems * sizeof(V) : 0);
+  const size_t need = zp_elems * sizeof(double2) + 256 + (ctx->has_v ? nc * chunk * field_elems * sizeof(V) : 0);
   DKS_TRY(grow(ex.ws_h, need));
   double2* zp = reinterpret_cast<double2*>(ex.ws_h.ptr);
   V* tbuf = reinterpret_cast<V*>(reinterpret_cast<char*>(ex.ws_h.ptr) +
@@ -377,10 +446,10 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
     DKS_CUDA_TRY(cudaMemsetAsync(zp, 0, zp_elems * sizeof(double2), st));
     // Z = B^H x~ : (nproj x 2npw) (2npw x 2nb)
     if (fp64 && ex.df_gemm)
-      DKS_TRY(gemm_hn_df(kp.btdf, 2 * npw, (const double2*)x, 2 * npw, 2 * npw, ctx->nproj, 2 * nb, zp, st,
+      DKS_TRY(gemm_hn_df(kp.btdf, 2 * npw, (const double2*)x, 2 * npw, 2 * npw, ctx->nproj, ncol, zp, st,
                          P_PROJ_HN));
     else
-      DKS_TRY(gemm_hn<V>(bt, 2 * npw, x, 2 * npw, 2 * npw, ctx->nproj, 2 * nb, zp, st, P_PROJ_HN));
+      DKS_TRY(gemm_hn<V>(bt, 2 * npw, x, 2 * npw, 2 * npw, ctx->nproj, ncol, zp, st, P_PROJ_HN));
   }
   if (ctx->has_v) {
     bool done = false;
@@ -391,19 +460,23 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
       }
     }
     if (!done) DKS_TRY((fft_local<V, V>(ctx, kp, x, out, nb, chunk, tbuf, shift, scale, st)));
-  } else {
+  } else if (nc == 4) {
     const int blocks = std::max(1, std::min(ctx->num_sms * 8, (int)(((size_t)nb * npw + 255) / 256)));
     Prof pr(P_DIRAC + (fp64 ? 0 : kProf32), st, 8.0 * nb * npw * sizeof(V) + 24.0 * npw, 64.0 * nb * npw);
     k_dirac_only<V><<<blocks, 256, 0, st>>>(x, out, npw, nb, kp.q, ctx->c, shift, scale);
+  } else {
+    const int blocks = std::max(1, std::min(ctx->num_sms * 8, (int)(((size_t)2 * nb * npw + 255) / 256)));
+    Prof pr(P_DIRAC + (fp64 ? 0 : kProf32), st, 4.0 * nb * npw * sizeof(V) + 8.0 * npw, 8.0 * nb * npw);
+    k_kinetic_only<V><<<blocks, 256, 0, st>>>(x, out, npw, 2 * nb, kp.ek, shift, scale);
   }
   DKS_CUDA_TRY(cudaGetLastError());
   if (ctx->nproj) {
     // out~ += B (scale D Z)
     if (fp64 && ex.df_gemm)
-      DKS_TRY(gemm_nn_df(kp.btdf, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, 2 * nb,
+      DKS_TRY(gemm_nn_df(kp.btdf, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, ncol,
                          (double2*)out, 2 * npw, 1.0, st, scale, P_PROJ_NN));
     else
-      DKS_TRY(gemm_nn<V>(bt, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, 2 * nb, out, 2 * npw,
+      DKS_TRY(gemm_nn<V>(bt, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, ncol, out, 2 * npw,
                          1.0, st, scale, P_PROJ_NN));
   }
   return DKS_OK;

@@ -444,14 +444,14 @@ int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const
 // eight partial sums from distributed shared memory in rank order (deterministic result).
 constexpr int STATS_SPLIT = 8;
 
-template <typename V>
+template <typename V, int NC>
 __global__ void __cluster_dims__(STATS_SPLIT, 1, 1) __launch_bounds__(256)
     k_col_stats(const V* __restrict__ x, const V* __restrict__ hx, const double* __restrict__ lam,
                 const double* __restrict__ ek, int npw, double* __restrict__ stats) {
   cg::cluster_group cl = cg::this_cluster();
   const int part = (int)cl.block_rank();
   const int j = blockIdx.y;
-  const size_t rows = (size_t)4 * npw;
+  const size_t rows = (size_t)NC * npw;
   const V* xj = x + (size_t)j * rows;
   const V* hj = hx ? hx + (size_t)j * rows : nullptr;
   const double l = lam ? lam[j] : 0.0;
@@ -464,7 +464,7 @@ __global__ void __cluster_dims__(STATS_SPLIT, 1, 1) __launch_bounds__(256)
   for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     T ax = 0, rr = 0;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < NC; ++a) {
       const V xv = xj[(size_t)a * npw + p];
       ax = fma(xv.x, xv.x, fma(xv.y, xv.y, ax));
       if (hj) {
@@ -507,11 +507,14 @@ __global__ void __cluster_dims__(STATS_SPLIT, 1, 1) __launch_bounds__(256)
 
 template <typename V>
 int col_stats(const V* x, const V* hx, const double* lam, const double* ek, int npw, int n, double* stats,
-              cudaStream_t st) {
+              cudaStream_t st, int ncomp) {
   if (n <= 0) return DKS_OK;
   if (n > 65535) return fail(DKS_ERR_INVALID_ARG, "col_stats: too many columns");
-  Prof pr(P_STATS, st, (hx ? 2.0 : 1.0) * n * 4.0 * npw * sizeof(V) + 8.0 * npw, 12.0 * n * 4.0 * npw);
-  k_col_stats<V><<<dim3(STATS_SPLIT, n), 256, 0, st>>>(x, hx, lam, ek, npw, stats);
+  Prof pr(P_STATS, st, (hx ? 2.0 : 1.0) * n * ncomp * npw * sizeof(V) + 8.0 * npw, 12.0 * n * ncomp * npw);
+  if (ncomp == 2)
+    k_col_stats<V, 2><<<dim3(STATS_SPLIT, n), 256, 0, st>>>(x, hx, lam, ek, npw, stats);
+  else
+    k_col_stats<V, 4><<<dim3(STATS_SPLIT, n), 256, 0, st>>>(x, hx, lam, ek, npw, stats);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
@@ -520,14 +523,14 @@ int col_stats(const V* x, const V* hx, const double* lam, const double* ek, int 
 // grid (planewave blocks, active columns): the per-column Teter scale 1/T_band is formed once
 // per thread; each thread then takes planewaves p and all four components, so |k+G|^2/2 is read
 // once per planewave and the Teter factor computed once for the four components
-template <typename V, typename Vo>
+template <typename V, typename Vo, int NC>
 __global__ void k_precond(const V* __restrict__ x, const V* __restrict__ hx, const double* __restrict__ lam,
                           const double* __restrict__ stats, const int* __restrict__ act,
                           const double* __restrict__ ek, int npw, int precond, Vo* __restrict__ y) {
   using T = typename RealOf<V>::T;
   const int i = blockIdx.y;
   const int j = act[i];
-  const size_t rows = (size_t)4 * npw;
+  const size_t rows = (size_t)NC * npw;
   const V* xj = x + (size_t)j * rows;
   const V* hj = hx + (size_t)j * rows;
   Vo* yi = y + (size_t)i * rows;
@@ -543,7 +546,7 @@ __global__ void k_precond(const V* __restrict__ x, const V* __restrict__ hx, con
       kf = pp / (pp + (T)16 * x2 * x2);
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < NC; ++a) {
       const V xv = xj[(size_t)a * npw + p], hv = hj[(size_t)a * npw + p];
       const V r{kf * (hv.x - l * xv.x), kf * (hv.y - l * xv.y)};
       if constexpr (std::is_same<V, Vo>::value) {
@@ -557,13 +560,16 @@ __global__ void k_precond(const V* __restrict__ x, const V* __restrict__ hx, con
 
 template <typename V, typename Vo>
 int precond_apply(const V* x, const V* hx, const double* lam, const double* stats, const int* act, int nact,
-                  const double* ek, int npw, int precond, Vo* y, cudaStream_t st) {
+                  const double* ek, int npw, int precond, Vo* y, cudaStream_t st, int ncomp) {
   if (nact <= 0) return DKS_OK;
   if (nact > 65535) return fail(DKS_ERR_INVALID_ARG, "precond: too many columns");
-  const size_t total = (size_t)4 * npw * nact;
+  const size_t total = (size_t)ncomp * npw * nact;
   const int bx = std::max(1, std::min((npw + 255) / 256, (num_sms() * 8 + nact - 1) / nact));
   Prof pr(P_PRECOND, st, 3.0 * total * sizeof(V) + 8.0 * npw, 20.0 * total);
-  k_precond<V, Vo><<<dim3(bx, nact), 256, 0, st>>>(x, hx, lam, stats, act, ek, npw, precond, y);
+  if (ncomp == 2)
+    k_precond<V, Vo, 2><<<dim3(bx, nact), 256, 0, st>>>(x, hx, lam, stats, act, ek, npw, precond, y);
+  else
+    k_precond<V, Vo, 4><<<dim3(bx, nact), 256, 0, st>>>(x, hx, lam, stats, act, ek, npw, precond, y);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
@@ -620,15 +626,15 @@ template int gemm_nn<float2, float2>(const float2*, int, int, int, const double2
 template int gemm_nn<float2, double2>(const float2*, int, int, int, const double2*, int, const double*, int,
                                       double2*, int, double, cudaStream_t, double, int);
 template int col_stats<double2>(const double2*, const double2*, const double*, const double*, int, int, double*,
-                                cudaStream_t);
+                                cudaStream_t, int);
 template int col_stats<float2>(const float2*, const float2*, const double*, const double*, int, int, double*,
-                               cudaStream_t);
+                               cudaStream_t, int);
 template int precond_apply<double2, double2>(const double2*, const double2*, const double*, const double*,
-                                             const int*, int, const double*, int, int, double2*, cudaStream_t);
+                                             const int*, int, const double*, int, int, double2*, cudaStream_t, int);
 template int precond_apply<float2, float2>(const float2*, const float2*, const double*, const double*, const int*,
-                                           int, const double*, int, int, float2*, cudaStream_t);
+                                           int, const double*, int, int, float2*, cudaStream_t, int);
 template int precond_apply<double2, float2>(const double2*, const double2*, const double*, const double*,
-                                            const int*, int, const double*, int, int, float2*, cudaStream_t);
+                                            const int*, int, const double*, int, int, float2*, cudaStream_t, int);
 template int convert<double2, float2>(const double2*, float2*, size_t, cudaStream_t);
 template int convert<float2, double2>(const float2*, double2*, size_t, cudaStream_t);
 template int convert<double2, double2>(const double2*, double2*, size_t, cudaStream_t);

@@ -154,7 +154,8 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
   df = df && sizeof(V) == sizeof(double2);
   ex.df_gemm = df;   // projector contractions inside apply_h follow the phase's arithmetic
   const KPoint& kp = ctx->k[ik];
-  const int rows = 4 * kp.npw;
+  const int nc = ctx->ncomp;
+  const int rows = nc * kp.npw;
   const size_t colsz = (size_t)rows;
   int cur = out.cur;
   long long happ = 0;
@@ -188,7 +189,7 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
   DKS_TRY(rotate(false, 0, n, sm.vm, n, n, b.z[nx]));
   DKS_TRY(rotate(true, 0, n, sm.vm, n, n, b.hz[nx]));
   cur = nx;
-  DKS_TRY(col_stats<V>(b.z[cur], b.hz[cur], sm.lam, kp.ek, kp.npw, n, sm.stats, st));
+  DKS_TRY(col_stats<V>(b.z[cur], b.hz[cur], sm.lam, kp.ek, kp.npw, n, sm.stats, st, nc));
   std::vector<double> res;
   DKS_TRY(fetch(sm, pin, n, res, st));
   if (pin.info[1] < n) return fail(DKS_ERR_RANK, "initial block is rank deficient");
@@ -207,7 +208,7 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
     const int a = (int)act.size();
     V* y = b.z[cur] + (size_t)n * colsz;
     V* hy = b.hz[cur] + (size_t)n * colsz;
-    DKS_TRY(precond_apply<V>(b.z[cur], b.hz[cur], sm.lam, sm.stats, sm.act, a, kp.ek, kp.npw, precond, y, st));
+    DKS_TRY(precond_apply<V>(b.z[cur], b.hz[cur], sm.lam, sm.stats, sm.act, a, kp.ek, kp.npw, precond, y, st, nc));
     if (use_filter) {
       DKS_TRY(filter_inplace<V>(ctx, ex, ik, y, b.tmp, a, C, om, st));
       happ += 2LL * a;
@@ -220,7 +221,7 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
     nx = cur ^ 1;
     DKS_TRY(rotate(false, 0, nz, sm.vm, nz, n, b.z[nx]));
     DKS_TRY(rotate(true, 0, nz, sm.vm, nz, n, b.hz[nx]));
-    DKS_TRY(col_stats<V>(b.z[nx], b.hz[nx], sm.lam, kp.ek, kp.npw, n, sm.stats, st));
+    DKS_TRY(col_stats<V>(b.z[nx], b.hz[nx], sm.lam, kp.ek, kp.npw, n, sm.stats, st, nc));
     DKS_TRY(fetch(sm, pin, n, res, st));
     if (pin.info[1] < n) return fail(DKS_ERR_RANK, "Rayleigh-Ritz subspace rank below the block size");
     maxres = 0;
@@ -317,9 +318,12 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
       opts.concurrency < 0 || (opts.mode != DKS_MODE_FP64 && opts.mode != DKS_MODE_MIXED))
     return fail(DKS_ERR_INVALID_ARG, "dks_lobpcgf_solve: bad argument");
   cudaStream_t st = (cudaStream_t)opts.stream;
+  // a KSSO operator has no negative continuum: Algorithm 1 without the filter (standard LOBPCG,
+  // the solver of the paper's KSSO module)
+  if (ctx->ncomp == 2) opts.use_filter = 0;
   if (report) {
     std::memset(report, 0, sizeof(*report));
-    report->shift = ctx->c * ctx->c;
+    report->shift = ctx->ncomp == 4 ? ctx->c * ctx->c : 0.0;
   }
   int nmax = 0, rowsmax = 0;
   std::vector<size_t> eoff(ctx->nk + 1, 0);
@@ -328,9 +332,9 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
     if (nv <= 0 || !X[ik]) return fail(DKS_ERR_INVALID_ARG, "dks_lobpcgf_solve: nev_k and X[ik] required");
     const int n = nv + opts.nbuf;
     if (3 * n > kMaxRR) return fail(DKS_ERR_UNSUPPORTED, "block wider than the Rayleigh-Ritz limit (3n <= 512)");
-    if (n > ctx->k[ik].npw * 4) return fail(DKS_ERR_INVALID_ARG, "block wider than the basis");
+    if (n > ctx->k[ik].npw * ctx->ncomp) return fail(DKS_ERR_INVALID_ARG, "block wider than the basis");
     nmax = std::max(nmax, n);
-    rowsmax = std::max(rowsmax, 4 * ctx->k[ik].npw);
+    rowsmax = std::max(rowsmax, ctx->ncomp * ctx->k[ik].npw);
     eoff[ik + 1] = eoff[ik] + nv;
   }
   const bool mixed = opts.mode == DKS_MODE_MIXED;
@@ -430,7 +434,7 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
         const KPoint& kp = ctx->k[ik];
         const int nv = opts.nev_k ? opts.nev_k[ik] : nev;
         const int n = nv + opts.nbuf;
-        const size_t elems = (size_t)n * 4 * kp.npw;
+        const size_t elems = (size_t)n * ctx->ncomp * kp.npw;
         const double C = std::isnan(opts.C) ? kp.cshift : opts.C;
         const double om = std::isnan(opts.Omega) ? kp.omega : opts.Omega;
         std::vector<double>* h = ik == 0 ? &hist : nullptr;

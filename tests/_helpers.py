@@ -14,15 +14,16 @@ def gpu():
     return torch
 
 
-def make_pair(name, ik=0, **kw):
-    """(workload, library Context, oracle MatrixFreeH, q) for k-point ik."""
+def make_pair(name, ik=0, model="dks", **kw):
+    """(workload, library Context, oracle matrix-free operator, q) for k-point ik; model "dks"
+    (four-spinors, MatrixFreeH) or "ksso" (two-spinors, MatrixFreeKSSO)."""
     import paper_1211_1446_gb300 as P
     wl = W.make(name, **kw)
-    ctx = P.Context.from_workload(wl)
+    ctx = P.Context.from_workload(wl, model=model)
     m, q = obasis.sphere(wl.lattice, wl.grid, wl.kfrac[ik], wl.ecut_k[ik])
     lib_m = ctx.basis(ik)
     assert lib_m.shape == m.shape and np.array_equal(lib_m, m), "planewave basis differs from the oracle's"
-    hop = oop.MatrixFreeH(wl, m, q)
+    hop = oop.MatrixFreeH(wl, m, q) if model == "dks" else oop.MatrixFreeKSSO(wl, m, q)
     return wl, ctx, hop, q
 
 

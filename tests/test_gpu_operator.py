@@ -154,3 +154,32 @@ def test_kinetic_balance(name, kw, dt):
     got = xd.cpu().numpy().astype(np.complex128)
     assert np.array_equal(got[:, 0:2], x[:, 0:2])
     assert rel_err(got[:, 2:4], ref[:, 2:4]) < (1e-14 if dt == "c128" else 1e-6)
+
+
+@pytest.mark.parametrize("name,kw", CASES)
+@pytest.mark.parametrize("dt", ["c128", "c64", "df"])
+def test_apply_h_ksso(name, kw, dt):
+    """The KSSO two-component operator (kinetic + V + spin-orbit projectors) against the oracle's
+    matrix-free KSSO operator, every element; complex128 in FP64 and in double-float arithmetic,
+    complex64 in FP32."""
+    torch = gpu()
+    wl, ctx, hop, q = make_pair(name, model="ksso", **kw)
+    assert ctx.ncomp == 2
+    x = W.random_block(len(q), 3, 41, ncomp=2)
+    if dt == "c64":
+        x = x.astype(np.complex64).astype(np.complex128)
+    ref = hop(x)
+    xd = to_dev(x, torch.complex64 if dt == "c64" else torch.complex128)
+    hx = torch.empty_like(xd)
+    ctx.apply_H(0, xd, hx, emulated=(dt == "df"))
+    torch.cuda.synchronize()
+    assert rel_err(hx.cpu().numpy(), ref) < (2e-6 if dt == "c64" else 1e-12)
+
+
+def test_kinetic_balance_rejects_ksso():
+    torch = gpu()
+    import paper_1211_1446_gb300 as P
+    wl, ctx, hop, q = make_pair("cubic", model="ksso")
+    xd = to_dev(W.random_block(len(q), 2, 3, ncomp=2), torch.complex128)
+    with pytest.raises(P.DKSError):
+        ctx.kinetic_balance(0, xd)

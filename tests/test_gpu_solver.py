@@ -18,7 +18,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 def _solve(ctx, wl, q, nev, mode, **kw):
     import torch
-    x0 = torch.from_numpy(W.start_block(len(q), nev, wl.seed)).cuda()
+    x0 = torch.from_numpy(W.start_block(len(q), nev + kw.get("nbuf", 0), wl.seed, ncomp=ctx.ncomp)).cuda()
     lam, rep, rc = ctx.solve([x0], nev, mode=mode, check=False, **kw)
     return lam[0], x0.cpu().numpy(), rep, rc
 
@@ -53,6 +53,35 @@ def test_small_spin_orbit_vs_dense(mode, kf):
     assert rc == 0, rep
     assert np.abs(lam - ref).max() < 1e-8
     assert _residuals(hop, x, lam).max() < 1e-6
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("kf", [[0.0, 0.0, 0.0], [0.25, -0.125, 0.5]])
+def test_ksso_vs_dense(mode, kf):
+    """KSSO module: the two-component operator solved by Algorithm 1 without the filter (standard
+    LOBPCG) against the lowest dense eigenvalues of the oracle's KSSO matrix."""
+    gpu()
+    wl, ctx, hop, q = make_pair("small", model="ksso", kfrac=[kf])
+    import oracle.basis as ob
+    m, _ = ob.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
+    ref = np.linalg.eigvalsh(oop.dense_hamiltonian_ksso(wl, m, q))[:6]
+    lam, x, rep, rc = _solve(ctx, wl, q, 6, mode, nbuf=2)
+    assert rc == 0, rep
+    assert rep["shift"] == 0.0
+    assert np.abs(lam - ref).max() < 1e-8
+    assert _residuals(hop, x[:6], lam).max() < 1e-6
+
+
+def test_ksso_is_nonrelativistic_limit_of_dks():
+    """At c = 1e4 the DKS eigenvalues (shifted by -mc^2) approach the KSSO eigenvalues of the same
+    sphere, grid and projectors to O(1/c^2); both solved on the GPU."""
+    gpu()
+    wl, ctx_d, _, q = make_pair("small", c=1.0e4)
+    _, ctx_k, _, _ = make_pair("small", model="ksso", c=1.0e4)
+    lam_d, _, rep_d, rc_d = _solve(ctx_d, wl, q, 6, 0, nbuf=2)
+    lam_k, _, rep_k, rc_k = _solve(ctx_k, wl, q, 6, 0, nbuf=2)
+    assert rc_d == 0 and rc_k == 0
+    assert np.abs(lam_d - lam_k).max() < 1e-5
 
 
 def test_standard_lobpcg_collapses_on_gpu():

@@ -263,9 +263,53 @@ def test_nonrelativistic_limit():
         hs += hd[:2 * npw, :2 * npw]          # large-large block: Vhat + N (Dirac part is 0 there)
         ls = np.linalg.eigvalsh(hs)[:6]
         errs.append(np.abs(lam - ls).max())
+        # the KSSO oracle operator is this limit
+        lk = np.linalg.eigvalsh(op.dense_hamiltonian_ksso(wl, m, q))[:6]
+        assert np.abs(lk - ls).max() < 1e-10
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 8.0 < r1 < 13.0 and 7.0 < r2 < 11.0, errs   # (c ratio)^2 = 11.1, 9
     assert errs[2] < 1e-4
+
+
+# ---------------------------------------------------------------- KSSO operator (Sec. 4)
+
+def test_ksso_free_particle_closed_form():
+    """V = 0, no projectors: the KSSO spectrum is |q|^2/2, each twice (spin)."""
+    wl, m, q = _setup("cubic", potential=False)
+    w = np.linalg.eigvalsh(op.dense_hamiltonian_ksso(wl, m, q))
+    ek = 0.5 * np.einsum("ij,ij->i", q, q)
+    assert np.allclose(w, np.sort(np.concatenate([ek, ek])), rtol=1e-13, atol=1e-13)
+
+
+def test_ksso_matrix_free_equals_dense_and_hermitian():
+    """Matrix-free KSSO (numpy FFT, spinor-harmonic projectors) against the dense matrix (Vhat
+    wrap, Legendre closed form); the dense matrix is Hermitian and, at Gamma, Kramers-paired."""
+    for kf in ([0.0, 0.0, 0.0], [0.25, -0.125, 0.5]):
+        wl = W.make("small", kfrac=[kf])
+        m, q = basis.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
+        h = op.dense_hamiltonian_ksso(wl, m, q)
+        assert np.abs(h - h.conj().T).max() < 1e-14 * np.abs(h).max()
+        hop = op.MatrixFreeKSSO(wl, m, q)
+        x = W.random_block(len(q), 3, 6, ncomp=2)
+        y = hop(x)
+        yd = (h @ x.reshape(3, -1).T).T.reshape(y.shape)
+        assert np.abs(y - yd).max() < 1e-12 * np.abs(yd).max()
+    wl, m, q = _setup("small")
+    w = np.linalg.eigvalsh(op.dense_hamiltonian_ksso(wl, m, q))[:40]
+    assert np.abs(w[0::2] - w[1::2]).max() < 1e-10
+    assert np.abs(w[1:-1:2] - w[2::2]).max() > 1e-4
+
+
+def test_ksso_lobpcg_matches_dense():
+    """Algorithm 1 without the filter (standard LOBPCG, the KSSO module's solver) on the KSSO
+    operator reaches the lowest dense eigenvalues."""
+    wl, m, q = _setup("small")
+    hop = op.MatrixFreeKSSO(wl, m, q)
+    ref = np.linalg.eigvalsh(op.dense_hamiltonian_ksso(wl, m, q))[:8]
+    x0 = W.start_block(len(q), 12, wl.seed, ncomp=2)
+    res = lb.lobpcgf(hop, q, x0, 12, 0.0, 1.0, tol=1e-8, n_iter=300, nconv=8, use_filter=False)
+    assert res.converged
+    assert np.abs(res.lam[:8] - ref).max() < 1e-8
 
 
 # ---------------------------------------------------------------- filter (Eq. filter) and Teter

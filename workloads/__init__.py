@@ -229,12 +229,13 @@ def make(name: str, seed: int = DEFAULT_SEED, **kw) -> Workload:
     return wl
 
 
-def start_block(npw: int, nb: int, seed: int = DEFAULT_SEED, ik: int = 0) -> np.ndarray:
-    """Seed-fixed complex normal start block x0[band, comp, pw] (canonical pw order)."""
+def start_block(npw: int, nb: int, seed: int = DEFAULT_SEED, ik: int = 0, ncomp: int = 4) -> np.ndarray:
+    """Seed-fixed complex normal start block x0[band, comp, pw] (canonical pw order); ncomp = 4 for
+    four-spinors, 2 for two-spinors (the first two components of the same draw)."""
     rng = np.random.Generator(np.random.PCG64([seed, 1000 + ik, nb]))
     re = rng.standard_normal((nb, 4, npw))
     im = rng.standard_normal((nb, 4, npw))
-    return (re + 1j * im) / math.sqrt(2.0)
+    return ((re + 1j * im) / math.sqrt(2.0))[:, :ncomp].copy()
 
 
 def random_block(npw: int, nb: int, seed: int, ncomp: int = 4) -> np.ndarray:
