@@ -312,6 +312,32 @@ def ksso_section(P, W, wl, ctx, x0, lam_dks, ms_dks, mode, stream):
                                     "max_eig_diff_vs_cold": float(np.abs(lam_p[0] - lam_dks).max())}}
 
 
+def davidson_section(P, ctx, x0, lam_dks, ms_dks, mode, stream, m_max=160):
+    """Davidson-F: block Davidson with the filter of Algorithm 1 (the paper's remark that the
+    filter carries over to Davidson-type solvers), on the same dimer and start block, basis of at
+    most m_max columns; one warm-up and one timed solve, against the LOBPCG-F solve."""
+    import numpy as np
+    import torch
+    x = torch.empty_like(x0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = None
+    for _ in range(2):
+        x.copy_(x0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lam, rep, rc = ctx.solve([x], NEV, tol=TOL, mode=mode, nbuf=NBUF, check=False, solver="davidson",
+                                 m_max=m_max)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out = {"ms_per_solve": e0.elapsed_time(e1), "status": int(rc), "m_max": m_max,
+               "iterations": rep["iterations"][0], "fp64_iterations": rep["fp64_iterations"][0],
+               "h_applications": rep["h_applications"]}
+        if rc == 0:
+            out["max_eig_diff_vs_lobpcgf"] = float(np.abs(lam[0] - lam_dks).max())
+            out["time_vs_lobpcgf"] = out["ms_per_solve"] / ms_dks
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -323,6 +349,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-warm-start", action="store_true")
     ap.add_argument("--no-ksso", action="store_true")
+    ap.add_argument("--no-davidson", action="store_true")
     ap.add_argument("--ref-iterations", type=int, default=60)
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--kernel-case", default=None,
@@ -480,6 +507,7 @@ def main():
 
     warm = None if args.no_warm_start else warm_start(P, W, wl, ctx, x, x0, mode, stream)
     ksso = None if args.no_ksso else ksso_section(P, W, wl, ctx, x0, lam, ms, mode, stream)
+    dav = None if args.no_davidson else davidson_section(P, ctx, x0, lam, ms, mode, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -494,7 +522,8 @@ def main():
             "e2e": {"value": NEV * ws / (ms_e2e / 1e3), "unit": "eigenpairs/s",
                     "h2d_bytes_per_step": bytes_vec, "d2h_bytes_per_step": bytes_vec + 8 * NEV},
             "gpu_launches": launches, "clocks": clk, "roofline": roof,
-            "cpu_baseline": cpu, "fp64_form": fp64, "warm_start": warm, "ksso": ksso, "accuracy": acc}
+            "cpu_baseline": cpu, "fp64_form": fp64, "warm_start": warm, "ksso": ksso, "davidson_f": dav,
+            "accuracy": acc}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

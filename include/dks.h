@@ -177,7 +177,19 @@ typedef struct {
   int concurrency;     /* k-points solved at the same time, each on its own internal stream
                           and host thread (0 = min(nk, 4), bounded by free device memory);
                           with more than one, `stream` is synchronised first             */
+  int solver;          /* DKS_SOLVER_LOBPCG (Algorithm 1, default) or DKS_SOLVER_DAVIDSON */
+  int m_max;           /* DAVIDSON: largest basis, in columns (0 = 4 (nev + nbuf)); at
+                          least 2 (nev + nbuf) and at most 512                           */
 } dks_solve_opts;
+
+/* Solvers.  LOBPCG: Algorithm 1 (LOBPCG-F with use_filter = 1).  DAVIDSON: block Davidson with
+ * the same filter step (the paper notes that the filter carries over to Davidson-type
+ * solvers, Sec. 3): a growing orthonormal basis V replaces [X, Y, P]; every iteration does
+ * Rayleigh-Ritz on V, forms T = f(H) K(R) on the active columns (as lines 9-10 of Alg. 1),
+ * restarts V from the Ritz vectors when it would exceed m_max columns, projects T out of V
+ * (twice), orthonormalises it and appends it.  Same options, modes and report otherwise. */
+#define DKS_SOLVER_LOBPCG 0
+#define DKS_SOLVER_DAVIDSON 1
 
 typedef struct {
   int iterations[64];        /* per k (first 64 k-points)                         */

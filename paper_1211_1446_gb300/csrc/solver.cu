@@ -283,6 +283,156 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
 }
 
 
+// ---------------------------------------------------------------- Davidson-F
+// Block Davidson with the filter of Algorithm 1 (the paper notes that its filter step carries
+// over to Davidson-type solvers, Sec. 3): a growing orthonormal basis V replaces [X, Y, P].
+// Per iteration: Rayleigh-Ritz on V, X = V C, R = HX - X Theta, T = f(H) K(R) on the active
+// columns, restart V = X when V would exceed mmax columns, T projected out of V twice
+// (classical Gram-Schmidt with one reorthogonalisation), T orthonormalised through the
+// Rayleigh-Ritz kernel on the pencil (T^H T, T^H T) (Cholesky, or SVQB when T is rank
+// deficient), then V = [V, T], HV = [HV, H T].
+template <typename V>
+struct DBlocks {
+  V* v = nullptr;      // mmax columns
+  V* hv = nullptr;     // mmax columns
+  V* x = nullptr;      // n columns: X0 on entry, X on exit
+  V* hx = nullptr;
+  V* t = nullptr;      // n columns: the new directions
+  V* tmp = nullptr;    // n columns: filter intermediate
+  V* best = nullptr;   // FP32 phase: X with the lowest residual
+};
+
+template <typename V>
+static int davidson_phase(dks_ctx* ctx, Exec& ex, int ik, DBlocks<V>& b, Small& sm, Pinned& pin, int n,
+                          int nconv, double tol, int n_init, int n_iter, double C, double om, int precond,
+                          int use_filter, bool stop_on_stall, double chol_tol, double drop_tol,
+                          std::vector<double>* hist, PhaseOut& out, cudaStream_t st, bool df, int mmax) {
+  df = df && sizeof(V) == sizeof(double2);
+  ex.df_gemm = df;
+  const KPoint& kp = ctx->k[ik];
+  const int nc = ctx->ncomp;
+  const int rows = nc * kp.npw;
+  const size_t colsz = (size_t)rows;
+  long long happ = 0;
+  auto hn_full = [&](const V* a, int m, const V* bb, int nn, double2* c, bool lower) -> int {
+    DKS_CUDA_TRY(cudaMemsetAsync(c, 0, (size_t)m * nn * sizeof(double2), st));
+    return hn<V>(df, a, rows, bb, rows, rows, m, nn, c, st, lower);
+  };
+  auto nn_into = [&](const V* a, int m, const double2* w, int ldw, int ncol, V* o, double beta,
+                     double alpha) -> int {
+    if (df)
+      return gemm_nn_df((const double2*)a, rows, rows, m, w, ldw, nullptr, ncol, (double2*)o, rows, beta, st,
+                        alpha);
+    return gemm_nn<V>(a, rows, rows, m, w, ldw, nullptr, ncol, o, rows, beta, st, alpha);
+  };
+  // an orthonormal basis of the nt columns of t, written to dst; returns its width (rank).  With
+  // FP32 blocks the Gram matrix carries ~1e-7 relative rounding, so directions whose scaled
+  // Cholesky pivot or Gram eigenvalue is below 1e-6 are treated as dependent (SVQB drops them).
+  const double otol_c = sizeof(V) == sizeof(double2) ? chol_tol : std::max(chol_tol, 1e-6);
+  const double otol_d = sizeof(V) == sizeof(double2) ? drop_tol : std::max(drop_tol, 1e-6);
+  auto orthonormalise = [&](const V* t, int nt, V* dst, int& rank) -> int {
+    DKS_TRY(hn_full(t, nt, t, nt, sm.s, true));
+    DKS_TRY(mirror_lower(sm.s, nt, st));
+    DKS_TRY(rayleigh_ritz(sm.s, sm.s, nt, nt, sm.vm, sm.lam, sm.info, sm.rrs, st, otol_c, otol_d));
+    DKS_CUDA_TRY(cudaMemcpyAsync(pin.info, sm.info, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    DKS_CUDA_TRY(cudaStreamSynchronize(st));
+    rank = std::min(nt, pin.info[1]);
+    if (rank < nt && rank > 0)   // the first rank pairs of the reduced problem
+      DKS_TRY(rayleigh_ritz(sm.s, sm.s, nt, rank, sm.vm, sm.lam, sm.info, sm.rrs, st, otol_c, otol_d));
+    if (rank > 0) DKS_TRY(nn_into(t, nt, sm.vm, nt, rank, dst, 0.0, 1.0));
+    return DKS_OK;
+  };
+  // lines 1-3 of Algorithm 1
+  if (use_filter)
+    for (int i = 0; i < n_init; ++i) {
+      DKS_TRY(filter_inplace<V>(ctx, ex, ik, b.x, b.tmp, n, C, om, st));
+      happ += 2LL * n;
+    }
+  int k = 0;
+  DKS_TRY(orthonormalise(b.x, n, b.v, k));
+  if (k < n) return fail(DKS_ERR_RANK, "initial block is rank deficient");
+  DKS_TRY(apply_h<V>(ctx, ex, ik, b.v, b.hv, n, 0.0, 1.0, st));
+  happ += n;
+  std::vector<double> res;
+  std::vector<int> act;
+  double best = INFINITY, lowest = INFINITY, maxres = 0;
+  int since_best = 0, it = 0;
+  bool converged = false;
+  for (it = 1; it <= n_iter; ++it) {
+    DKS_TRY(gram<V>(b.v, b.hv, rows, k, sm, st, df));
+    DKS_TRY(rayleigh_ritz(sm.a, sm.s, k, n, sm.vm, sm.lam, sm.info, sm.rrs, st, chol_tol, drop_tol));
+    DKS_TRY(nn_into(b.v, k, sm.vm, k, n, b.x, 0.0, 1.0));
+    DKS_TRY(nn_into(b.hv, k, sm.vm, k, n, b.hx, 0.0, 1.0));
+    DKS_TRY(col_stats<V>(b.x, b.hx, sm.lam, kp.ek, kp.npw, n, sm.stats, st, nc));
+    DKS_TRY(fetch(sm, pin, n, res, st));
+    if (pin.info[1] < n) {
+      // FP32 phase: a basis that rounding has made numerically dependent ends the phase like a
+      // stall, from the best X so far; in FP64 it is an error
+      if (stop_on_stall && b.best && std::isfinite(lowest)) {
+        DKS_CUDA_TRY(cudaMemcpyAsync(b.x, b.best, (size_t)n * colsz * sizeof(V), cudaMemcpyDeviceToDevice, st));
+        break;
+      }
+      return fail(DKS_ERR_RANK, "Davidson basis rank below the block size");
+    }
+    maxres = 0;
+    for (int j = 0; j < nconv; ++j) maxres = std::max(maxres, res[j]);
+    if (hist) hist->push_back(maxres);
+    if (!std::isfinite(maxres)) return fail(DKS_ERR_NOT_CONVERGED, "non-finite residual norm");
+    if (maxres < tol) {
+      converged = true;
+      break;
+    }
+    if (stop_on_stall) {   // the FP32 phase's floor, as in Algorithm 1's mixed mode
+      if (b.best && maxres < lowest) {
+        lowest = maxres;
+        DKS_CUDA_TRY(cudaMemcpyAsync(b.best, b.x, (size_t)n * colsz * sizeof(V), cudaMemcpyDeviceToDevice, st));
+      }
+      if (maxres < 0.8 * best) {
+        best = maxres;
+        since_best = 0;
+      } else if (++since_best >= (best > 30.0 * tol ? 5 : 3) || maxres > 10.0 * best) {
+        if (b.best)
+          DKS_CUDA_TRY(cudaMemcpyAsync(b.x, b.best, (size_t)n * colsz * sizeof(V), cudaMemcpyDeviceToDevice, st));
+        break;
+      }
+    }
+    act.clear();
+    for (int j = 0; j < n; ++j)
+      if (res[j] > tol) act.push_back(j);
+    const int a = (int)act.size();
+    std::memcpy(pin.act, act.data(), a * sizeof(int));
+    DKS_CUDA_TRY(cudaMemcpyAsync(sm.act, pin.act, a * sizeof(int), cudaMemcpyHostToDevice, st));
+    DKS_TRY(precond_apply<V>(b.x, b.hx, sm.lam, sm.stats, sm.act, a, kp.ek, kp.npw, precond, b.t, st, nc));
+    if (use_filter) {
+      DKS_TRY(filter_inplace<V>(ctx, ex, ik, b.t, b.tmp, a, C, om, st));
+      happ += 2LL * a;
+    }
+    if (k + a > mmax) {   // restart from the Ritz vectors (orthonormal: V C with C^H V^H V C = I)
+      DKS_CUDA_TRY(cudaMemcpyAsync(b.v, b.x, (size_t)n * colsz * sizeof(V), cudaMemcpyDeviceToDevice, st));
+      DKS_CUDA_TRY(cudaMemcpyAsync(b.hv, b.hx, (size_t)n * colsz * sizeof(V), cudaMemcpyDeviceToDevice, st));
+      k = n;
+    }
+    for (int pass = 0; pass < 2; ++pass) {   // T <- T - V (V^H T)
+      DKS_TRY(hn_full(b.v, k, b.t, a, sm.vp, false));
+      DKS_TRY(nn_into(b.v, k, sm.vp, k, a, b.t, 1.0, -1.0));
+    }
+    int r = 0;
+    DKS_TRY(orthonormalise(b.t, a, b.v + (size_t)k * colsz, r));
+    if (r == 0) return fail(DKS_ERR_NOT_CONVERGED, "Davidson: no new direction outside the basis");
+    DKS_TRY(apply_h<V>(ctx, ex, ik, b.v + (size_t)k * colsz, b.hv + (size_t)k * colsz, r, 0.0, 1.0, st));
+    happ += r;
+    k += r;
+  }
+  out.iterations = std::min(it, n_iter);
+  out.converged = converged;
+  out.max_res = maxres;
+  out.happ = happ;
+  out.cur = 0;
+  out.neg = pin.lam[0] < -ctx->c * ctx->c;
+  ex.df_gemm = false;
+  return DKS_OK;
+}
+
 }  // namespace dks
 
 using namespace dks;
@@ -306,6 +456,8 @@ void dks_solve_opts_default(dks_solve_opts* o) {
   o->drop_tol = 1e-12;
   o->emulate_fp64 = 1;
   o->concurrency = 0;
+  o->solver = DKS_SOLVER_LOBPCG;
+  o->m_max = 0;
 }
 
 int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* opts_in, double* eig, void* const* X,
@@ -315,8 +467,10 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
   if (opts_in) opts = *opts_in;
   else dks_solve_opts_default(&opts);
   if (!ctx || !eig || !X || !(tol > 0) || opts.n_init < 0 || opts.n_iter < 0 || opts.nbuf < 0 ||
-      opts.concurrency < 0 || (opts.mode != DKS_MODE_FP64 && opts.mode != DKS_MODE_MIXED))
+      opts.concurrency < 0 || (opts.mode != DKS_MODE_FP64 && opts.mode != DKS_MODE_MIXED) ||
+      (opts.solver != DKS_SOLVER_LOBPCG && opts.solver != DKS_SOLVER_DAVIDSON) || opts.m_max < 0)
     return fail(DKS_ERR_INVALID_ARG, "dks_lobpcgf_solve: bad argument");
+  const bool davidson = opts.solver == DKS_SOLVER_DAVIDSON;
   cudaStream_t st = (cudaStream_t)opts.stream;
   // a KSSO operator has no negative continuum: Algorithm 1 without the filter (standard LOBPCG,
   // the solver of the paper's KSSO module)
@@ -332,22 +486,32 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
     if (nv <= 0 || !X[ik]) return fail(DKS_ERR_INVALID_ARG, "dks_lobpcgf_solve: nev_k and X[ik] required");
     const int n = nv + opts.nbuf;
     if (3 * n > kMaxRR) return fail(DKS_ERR_UNSUPPORTED, "block wider than the Rayleigh-Ritz limit (3n <= 512)");
+    if (davidson) {
+      const int mm = opts.m_max ? opts.m_max : std::min(4 * n, kMaxRR);
+      if (mm < 2 * n || mm > kMaxRR)
+        return fail(DKS_ERR_INVALID_ARG, "dks_lobpcgf_solve: need 2 (nev + nbuf) <= m_max <= 512");
+    }
     if (n > ctx->k[ik].npw * ctx->ncomp) return fail(DKS_ERR_INVALID_ARG, "block wider than the basis");
     nmax = std::max(nmax, n);
     rowsmax = std::max(rowsmax, ctx->ncomp * ctx->k[ik].npw);
     eoff[ik + 1] = eoff[ik] + nv;
   }
   const bool mixed = opts.mode == DKS_MODE_MIXED;
+  // Davidson: basis of mmax columns (V and HV) and four n-column blocks; LOBPCG: [X|Y|P] ping-pong
+  const int mmax = davidson ? (opts.m_max ? opts.m_max : std::min(4 * nmax, kMaxRR)) : 0;
   const size_t cols = (size_t)3 * nmax;
   const size_t big64 = cols * rowsmax * sizeof(double2);
   const size_t big32 = mixed ? cols * rowsmax * sizeof(float2) : 0;
   const size_t tmp64 = (size_t)nmax * rowsmax * sizeof(double2);
   const size_t tmp32 = mixed ? (size_t)nmax * rowsmax * sizeof(float2) : 0;
-  const size_t nz = 3 * nmax;
+  const size_t nz = davidson ? (size_t)std::max(mmax, 3 * nmax) : (size_t)3 * nmax;
   const size_t small = (2 * nz * nz + 2 * nz * nmax + rr_scratch_elems((int)nz)) * sizeof(double2) +
                        (nmax + 3 * nmax) * sizeof(double) + (nmax + 4) * sizeof(int) + 16 * 256;
-  const bool split_copies = mixed && opts.emulate_fp64 != 0;
-  const size_t total = 4 * big64 + tmp64 + 4 * big32 + 2 * tmp32 + small + (split_copies ? 2 * big64 : 0) + 16 * 256;
+  const bool split_copies = mixed && opts.emulate_fp64 != 0 && !davidson;
+  const size_t dcols64 = (size_t)2 * mmax + 4 * (size_t)nmax, dcols32 = mixed ? (size_t)2 * mmax + 5 * (size_t)nmax : 0;
+  const size_t total =
+      davidson ? (dcols64 * sizeof(double2) + dcols32 * sizeof(float2)) * rowsmax + small + 32 * 256
+               : 4 * big64 + tmp64 + 4 * big32 + 2 * tmp32 + small + (split_copies ? 2 * big64 : 0) + 16 * 256;
   // concurrent k-point workers, each with its own stream and workspace (bounded by free memory)
   int nworkers = opts.concurrency > 0 ? opts.concurrency : std::min(ctx->nk, 4);
   nworkers = std::max(1, std::min(nworkers, ctx->nk));
@@ -392,22 +556,43 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
     };
     Blocks<double2> b64{};
     Blocks<float2> b32{};
-    b64.z[0] = (double2*)take(big64);
-    b64.z[1] = (double2*)take(big64);
-    b64.hz[0] = (double2*)take(big64);
-    b64.hz[1] = (double2*)take(big64);
-    b64.tmp = (double2*)take(tmp64);
-    if (split_copies) {
-      b64.zdf = (float4*)take(big64);
-      b64.hzdf = (float4*)take(big64);
-    }
-    if (mixed) {
-      b32.z[0] = (float2*)take(big32);
-      b32.z[1] = (float2*)take(big32);
-      b32.hz[0] = (float2*)take(big32);
-      b32.hz[1] = (float2*)take(big32);
-      b32.tmp = (float2*)take(tmp32);
-      b32.best = (float2*)take(tmp32);
+    DBlocks<double2> d64{};
+    DBlocks<float2> d32{};
+    if (davidson) {
+      const size_t r = (size_t)rowsmax;
+      d64.v = (double2*)take(mmax * r * sizeof(double2));
+      d64.hv = (double2*)take(mmax * r * sizeof(double2));
+      d64.x = (double2*)take(nmax * r * sizeof(double2));
+      d64.hx = (double2*)take(nmax * r * sizeof(double2));
+      d64.t = (double2*)take(nmax * r * sizeof(double2));
+      d64.tmp = (double2*)take(nmax * r * sizeof(double2));
+      if (mixed) {
+        d32.v = (float2*)take(mmax * r * sizeof(float2));
+        d32.hv = (float2*)take(mmax * r * sizeof(float2));
+        d32.x = (float2*)take(nmax * r * sizeof(float2));
+        d32.hx = (float2*)take(nmax * r * sizeof(float2));
+        d32.t = (float2*)take(nmax * r * sizeof(float2));
+        d32.tmp = (float2*)take(nmax * r * sizeof(float2));
+        d32.best = (float2*)take(nmax * r * sizeof(float2));
+      }
+    } else {
+      b64.z[0] = (double2*)take(big64);
+      b64.z[1] = (double2*)take(big64);
+      b64.hz[0] = (double2*)take(big64);
+      b64.hz[1] = (double2*)take(big64);
+      b64.tmp = (double2*)take(tmp64);
+      if (split_copies) {
+        b64.zdf = (float4*)take(big64);
+        b64.hzdf = (float4*)take(big64);
+      }
+      if (mixed) {
+        b32.z[0] = (float2*)take(big32);
+        b32.z[1] = (float2*)take(big32);
+        b32.hz[0] = (float2*)take(big32);
+        b32.hz[1] = (float2*)take(big32);
+        b32.tmp = (float2*)take(tmp32);
+        b32.best = (float2*)take(tmp32);
+      }
     }
     Small sm;
     sm.a = (double2*)take(nz * nz * sizeof(double2));
@@ -440,6 +625,30 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
         std::vector<double>* h = ik == 0 ? &hist : nullptr;
         PhaseOut& o32 = o32s[ik];
         PhaseOut& o64 = o64s[ik];
+        if (davidson) {
+          const bool emu = opts.emulate_fp64 != 0;
+          if (mixed) {
+            DKS_TRY(convert<double2, float2>((const double2*)X[ik], d32.x, elems, ws));
+            DKS_TRY(davidson_phase<float2>(ctx, ex, ik, d32, sm, pin, n, nv, std::max(opts.refine_tol, tol),
+                                           opts.n_init, opts.n_iter, C, om, opts.precond, opts.use_filter, true,
+                                           opts.chol_tol, opts.drop_tol, h, o32, ws, false, mmax));
+            DKS_TRY(convert<float2, double2>(d32.x, d64.x, elems, ws));
+            const int left = std::max(0, opts.n_iter - o32.iterations);
+            DKS_TRY(davidson_phase<double2>(ctx, ex, ik, d64, sm, pin, n, nv, tol, opts.use_filter ? 1 : 0, left, C,
+                                            om, opts.precond, opts.use_filter, false, opts.chol_tol, opts.drop_tol,
+                                            h, o64, ws, emu, mmax));
+          } else {
+            DKS_CUDA_TRY(cudaMemcpyAsync(d64.x, X[ik], elems * sizeof(double2), cudaMemcpyDeviceToDevice, ws));
+            DKS_TRY(davidson_phase<double2>(ctx, ex, ik, d64, sm, pin, n, nv, tol, opts.n_init, opts.n_iter, C, om,
+                                            opts.precond, opts.use_filter, false, opts.chol_tol, opts.drop_tol, h,
+                                            o64, ws, false, mmax));
+          }
+          DKS_CUDA_TRY(cudaMemcpyAsync(X[ik], d64.x, elems * sizeof(double2), cudaMemcpyDeviceToDevice, ws));
+          DKS_CUDA_TRY(cudaStreamSynchronize(ws));
+          for (int j = 0; j < nv; ++j) eig[eoff[ik] + j] = pin.lam[j];
+          happ += o32.happ + o64.happ;
+          return DKS_OK;
+        }
         if (mixed) {
           DKS_TRY(convert<double2, float2>((const double2*)X[ik], b32.z[0], elems, ws));
           o32.cur = 0;

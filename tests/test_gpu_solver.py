@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from oracle import davidson as odv
 from oracle import lobpcgf as olb
 from oracle import operator as oop
 
@@ -82,6 +83,59 @@ def test_ksso_is_nonrelativistic_limit_of_dks():
     lam_k, _, rep_k, rc_k = _solve(ctx_k, wl, q, 6, 0, nbuf=2)
     assert rc_d == 0 and rc_k == 0
     assert np.abs(lam_d - lam_k).max() < 1e-5
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name,nev", [("cubic", 8), ("small", 6)])
+def test_davidson_f_vs_dense(mode, name, nev):
+    """Davidson-F (block Davidson with the filter of Algorithm 1) reaches the lowest nev dense
+    eigenvalues above the gap midpoint, FP64 and mixed."""
+    gpu()
+    wl, ctx, hop, q = make_pair(name)
+    import oracle.basis as ob
+    m, _ = ob.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
+    ref, _, _ = olb.dense_eigs(oop.dense_hamiltonian(wl, m, q), wl.c, nev)
+    lam, x, rep, rc = _solve(ctx, wl, q, nev, mode, nbuf=2, solver="davidson")
+    assert rc == 0, rep
+    assert np.abs(lam - ref).max() < 1e-8
+    assert _residuals(hop, x[:nev], lam).max() < 1e-6
+    assert np.all(lam > -wl.c ** 2)
+
+
+def test_davidson_f_small_basis_restarts_and_matches_oracle():
+    """A basis limit of 2n forces a restart every other iteration; the result still matches the
+    oracle's Davidson-F with the same limit."""
+    gpu()
+    wl, ctx, hop, q = make_pair("small")
+    cs, om = ctx.filter_constants(0)
+    x0 = W.start_block(len(q), 8, wl.seed)
+    ref = odv.davidson_f(hop, q, x0, 8, cs, om, tol=1e-7, nconv=6, m_max=16).lam[:6]
+    lam, x, rep, rc = _solve(ctx, wl, q, 6, 0, nbuf=2, solver="davidson", m_max=16, tol=1e-7)
+    assert rc == 0, rep
+    assert np.abs(lam - ref).max() < 1e-8
+
+
+def test_davidson_without_filter_collapses_on_gpu():
+    """Without the filter the Davidson basis takes in negative-band directions and the iteration
+    breaks down (a state below the gap, a rank-deficient basis, or no convergence); with it the
+    same start converges to positive-band states."""
+    gpu()
+    wl, ctx, hop, q = make_pair("cubic", c=39.0)
+    lam, x, rep, rc = _solve(ctx, wl, q, 8, 0, use_filter=False, precond=1, n_iter=60, solver="davidson")
+    assert rc in (-6, -5, -4)
+    lam, x, rep, rc = _solve(ctx, wl, q, 8, 0, precond=1, n_iter=120, solver="davidson")
+    assert rc == 0 and np.all(lam > -wl.c ** 2)
+
+
+def test_davidson_ksso_vs_dense():
+    gpu()
+    wl, ctx, hop, q = make_pair("small", model="ksso")
+    import oracle.basis as ob
+    m, _ = ob.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
+    ref = np.linalg.eigvalsh(oop.dense_hamiltonian_ksso(wl, m, q))[:6]
+    lam, x, rep, rc = _solve(ctx, wl, q, 6, 1, nbuf=2, solver="davidson")
+    assert rc == 0, rep
+    assert np.abs(lam - ref).max() < 1e-8
 
 
 def test_standard_lobpcg_collapses_on_gpu():

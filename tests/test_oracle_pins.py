@@ -12,7 +12,7 @@ import pytest
 import scipy.linalg as sla
 
 import workloads as W
-from oracle import basis, lobpcgf as lb, operator as op
+from oracle import basis, davidson as dv, lobpcgf as lb, operator as op
 
 
 def _setup(name, **kw):
@@ -474,6 +474,50 @@ def test_standard_lobpcg_collapses_lobpcgf_does_not(c):
     plain = lb.lobpcgf(hop, q, x0, 8, cs, om, tol=1e-6, n_iter=60, use_filter=False, precond="identity")
     assert plain.lam.min() < -c * c          # collapsed below the gap midpoint
     filt = lb.lobpcgf(hop, q, x0, 8, cs, om, tol=1e-6, n_iter=60, precond="identity")
+    assert filt.converged and np.abs(filt.lam - lam_ref).max() < 1e-8
+
+
+# ---------------------------------------------------------------- Davidson-F (Sec. 3: filter in other solvers)
+
+def test_davidson_f_orthonormal_basis():
+    """SVQB basis: orthonormal, same span, dependent columns dropped."""
+    rng = np.random.default_rng(5)
+    t = rng.normal(size=(50, 6)) + 1j * rng.normal(size=(50, 6))
+    t[:, 5] = 2.0 * t[:, 0] - 1j * t[:, 3]
+    b = dv.orthonormal_basis(t)
+    assert b.shape[1] == 5
+    assert np.abs(b.conj().T @ b - np.eye(5)).max() < 1e-13
+    proj = b @ (b.conj().T @ t)
+    assert np.abs(proj - t).max() < 1e-12 * np.abs(t).max()
+
+
+def test_davidson_f_matches_dense_definition():
+    """Davidson-F reaches the lowest nev dense eigenvalues above the gap midpoint, on the local-only
+    cubic case and on the spin-orbit case, with three H applications per active column per
+    iteration."""
+    for name, nev in (("cubic", 8), ("small", 6)):
+        wl, m, q = _setup(name)
+        lam_ref, _, _ = lb.dense_eigs(op.dense_hamiltonian(wl, m, q), wl.c, nev)
+        hop = op.MatrixFreeH(wl, m, q)
+        cs, om = op.filter_constants(wl, q)
+        r = dv.davidson_f(hop, q, W.start_block(len(q), nev + 2, wl.seed), nev + 2, cs, om, tol=1e-7,
+                          nconv=nev, n_iter=300)
+        assert r.converged and np.all(r.lam > -wl.c ** 2)
+        assert np.abs(r.lam[:nev] - lam_ref).max() < 1e-8
+
+
+@pytest.mark.parametrize("c", [39.0, 137.036])
+def test_davidson_without_filter_collapses(c):
+    """The filter protects Davidson as it protects LOBPCG (Sec. 3.1 mechanism): without it the
+    basis picks up negative-band directions and the iteration returns states below the gap."""
+    wl, m, q = _setup("cubic", c=c)
+    hop = op.MatrixFreeH(wl, m, q)
+    cs, om = op.filter_constants(wl, q)
+    x0 = W.start_block(len(q), 8, wl.seed)
+    lam_ref, _, _ = lb.dense_eigs(op.dense_hamiltonian(wl, m, q), c, 8)
+    plain = dv.davidson_f(hop, q, x0, 8, cs, om, tol=1e-6, n_iter=60, use_filter=False, precond="identity")
+    assert plain.lam.min() < -c * c
+    filt = dv.davidson_f(hop, q, x0, 8, cs, om, tol=1e-6, n_iter=120, precond="identity")
     assert filt.converged and np.abs(filt.lam - lam_ref).max() < 1e-8
 
 
