@@ -172,6 +172,19 @@ def run_reference(args):
     return 0
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per kernel launch from ncu captures of
+# the current kernels at the dimer's sizes (python bench.py --kernel-case <case> under ncu --set full)
+NCU_TRAFFIC = {
+    "rayleigh_ritz": {"bytes_per_launch": (526.6e3 + 2 * 469.2e3 + 425.7e3 + 539.9e3) / 5,
+                      "note": "kernel case rr (m = 120, n = 40): mean over the five kernels of a step, "
+                              "each captured cold (the pencil is 537 KB)"},
+    "gram": {"bytes_per_launch": 922.6e6 + 4.5e6,
+             "note": "kernel case gramdf (k_gram_df, 120 columns of 229,676 rows)"},
+    "gram_fp32": {"bytes_per_launch": 223.2e6 + 3.5e6,
+                  "note": "kernel case gram32 (k_gram_f32, 120 columns of 229,676 rows)"},
+}
+
+
 def kernel_case(case):
     """One hot step of the solve at the bench's dimer size, three launches (ncu --set full target).
     hx64/hx32/hxdf: H' on 40 columns; gram64/gram32/gramdf: the solver's fused lower-triangle
@@ -481,7 +494,10 @@ def main():
         ach = d["flops"] / max(d["launches"], 1) / per_launch_s / 1e9
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "GFLOP/s", "frac": ach / pk,
                 "peak_source": psrc}
-    roof.update({"traffic": None, "share_of_step": d["ms"] / (ms * args.steps),
+    tr = NCU_TRAFFIC.get(dom)
+    roof.update({"traffic": tr["bytes_per_launch"] if tr else None,
+                 "traffic_note": tr["note"] if tr else "no ncu DRAM capture of this category's kernels",
+                 "share_of_step": d["ms"] / (ms * args.steps),
                  "per_category_ms": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items() if v["launches"]}})
 
     # H' x effective bandwidth (sphere-only algorithmic bytes) on the bench block, outside the timed region
