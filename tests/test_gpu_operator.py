@@ -183,3 +183,20 @@ def test_kinetic_balance_rejects_ksso():
     xd = to_dev(W.random_block(len(q), 2, 3, ncomp=2), torch.complex128)
     with pytest.raises(P.DKSError):
         ctx.kinetic_balance(0, xd)
+
+
+@pytest.mark.parametrize("dt", ["c64", "df"])
+def test_apply_h_ksso_full_dimer(dt):
+    """KSSO operator at the bench size (npw 57419, 48x48x56 grid, 36 projector channels), every
+    output element against the oracle."""
+    torch = gpu()
+    wl, ctx, hop, q = make_pair("dimer", model="ksso")
+    x = W.random_block(len(q), 3, 43, ncomp=2)
+    if dt == "c64":
+        x = x.astype(np.complex64).astype(np.complex128)
+    ref = hop(x)
+    xd = to_dev(x, torch.complex64 if dt == "c64" else torch.complex128)
+    hx = torch.empty_like(xd)
+    ctx.apply_H(0, xd, hx, emulated=(dt == "df"))
+    torch.cuda.synchronize()
+    assert rel_err(hx.cpu().numpy(), ref) < (2e-6 if dt == "c64" else 1e-12)

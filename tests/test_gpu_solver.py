@@ -180,6 +180,37 @@ def test_dimer_full_size_vs_oracle(mode):
     assert res.max() < 1e-6, res
 
 
+def test_davidson_f_dimer_full_size_vs_oracle():
+    """Davidson-F on the bench configuration (mixed precision, basis of 160 columns): the same 32
+    eigenvalues as the oracle's Algorithm 1 within 1e-8 Ha, sampled residuals below 1e-6."""
+    gpu()
+    import torch
+    wl, ctx, hop, q = make_pair("dimer")
+    ref = np.loadtxt(os.path.join(GOLDEN, "dimer_lobpcgf_eigs.txt"))
+    x0 = torch.from_numpy(W.start_block(len(q), 40, wl.seed)).cuda()
+    lam, rep, rc = ctx.solve([x0], 32, nbuf=8, tol=1e-6, mode=1, check=False, solver="davidson", m_max=160)
+    assert rc == 0, rep
+    assert np.abs(lam[0] - ref).max() < 1e-8
+    pick = np.array([0, 13, 31])
+    assert _residuals(hop, x0.cpu().numpy()[pick], lam[0][pick]).max() < 1e-6
+
+
+def test_ksso_dimer_full_size_vs_oracle():
+    """KSSO module on the dimer (two-component operator, 32 + 8 columns, mixed precision) against
+    the oracle's standard LOBPCG (tests/golden/dimer_ksso_eigs.txt), sampled residuals by the
+    oracle's matrix-free KSSO operator."""
+    gpu()
+    import torch
+    wl, ctx, hop, q = make_pair("dimer", model="ksso")
+    ref = np.loadtxt(os.path.join(GOLDEN, "dimer_ksso_eigs.txt"))
+    x0 = torch.from_numpy(W.start_block(len(q), 40, wl.seed, ncomp=2)).cuda()
+    lam, rep, rc = ctx.solve([x0], 32, nbuf=8, tol=1e-6, mode=1, check=False)
+    assert rc == 0, rep
+    assert np.abs(lam[0] - ref).max() < 1e-8
+    pick = np.array([0, 13, 31])
+    assert _residuals(hop, x0.cpu().numpy()[pick], lam[0][pick]).max() < 1e-6
+
+
 def test_multi_k_concurrent_matches_serial_and_dense():
     """Several k-points (a k/-k pair and time-reversal-invariant points) solved by concurrent
     workers: identical to the serial solve, each k within 1e-8 Ha of dense zheevd, E(k) = E(-k)
