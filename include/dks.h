@@ -17,7 +17,8 @@
  *    in canonical order (Miller triples sorted lexicographically, signed).
  *    dks_basis() returns the Miller triples in that order.
  *  - Vector blocks: X[band][comp][pw], complex interleaved (re, im), contiguous,
- *    comp 0,1 the large two-spinor (spin up, down), comp 2,3 the small one.
+ *    comp 0,1 the large two-spinor (spin up, down), comp 2,3 the small one
+ *    (contexts of model DKS_MODEL_KSSO: comp 0,1 only, see dks_create_model).
  *    complex128 for DKS_PREC_FP64, complex64 for DKS_PREC_FP32.
  *  - Device pointers are CUDA device memory owned by the caller; host pointers
  *    are read during the call only.  `stream` is a cudaStream_t (NULL = legacy
@@ -129,7 +130,8 @@ int dks_nproj(const dks_ctx* ctx, int* nproj);
 int dks_filter_constants(const dks_ctx* ctx, int ik, double* C, double* Omega);
 
 /* dks_apply_H: HX = H' X for nb bands of k-point ik (Eq. vDKS, Sec. 3.1
- * "matrix-free" Hx).  X, HX: device, [nb][4][npw], precision `prec`; X and HX
+ * "matrix-free" Hx; the KSSO operator for a KSSO context).  X, HX: device,
+ * [nb][ncomp][npw] (ncomp from dks_ncomp), precision `prec`; X and HX
  * must not overlap.  Uses ctx workspace (not reentrant per ctx).  Errors:
  * INVALID_ARG, CUDA. */
 int dks_apply_H(dks_ctx* ctx, int ik, const void* X, void* HX, int nb, int prec, void* stream);
