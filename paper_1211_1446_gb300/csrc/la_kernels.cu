@@ -344,12 +344,25 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const Va* __restrict__ a, int l
 // over 256 rows and every shared-memory load of W feeds four complex multiply-adds.
 constexpr int NF_R = 256, NF_GMAX = 5, NF_CMAX = 8 * NF_GMAX, NF_M = 16;
 
+// Two shared-memory stages: the A chunk of the next 16 inner indices is copied with cp.async and
+// the W chunk fetched into registers while the current chunk is multiplied.
+constexpr size_t NF_SMEM = 2 * (size_t)NF_M * NF_R * sizeof(float2) + 2 * (size_t)NF_M * NF_CMAX * sizeof(float2);
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 __global__ void __launch_bounds__(64 * NF_GMAX, 2) k_gemm_nn_f32(const float2* __restrict__ a, int lda, int k, int m,
                                                      const double2* __restrict__ w, int ldw,
                                                      const double* __restrict__ ws, int n,
                                                      float2* __restrict__ out, int ldo, double alpha, float beta) {
-  __shared__ float2 as[NF_M][NF_R];
-  __shared__ float2 wsm[NF_M][NF_CMAX];
+  extern __shared__ __align__(16) unsigned char nf_smem[];
+  float2* as_base = reinterpret_cast<float2*>(nf_smem);                          // [2][NF_M][NF_R]
+  float2* ws_base = as_base + 2 * NF_M * NF_R;                                     // [2][NF_M][NF_CMAX]
   const int ncols = (blockDim.x >> 6) * 8;
   const int r0 = blockIdx.x * NF_R, c0 = blockIdx.y * ncols;
   const int rg = threadIdx.x & 63, cg = threadIdx.x >> 6;
@@ -358,14 +371,20 @@ __global__ void __launch_bounds__(64 * NF_GMAX, 2) k_gemm_nn_f32(const float2* _
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = float2{0.f, 0.f};
-  for (int m0 = 0; m0 < m; m0 += NF_M) {
+  auto load_a = [&](int buf, int m0) {
+    float2* dst = as_base + (size_t)buf * NF_M * NF_R;
     for (int e = threadIdx.x; e < NF_M * NF_R; e += blockDim.x) {
       const int rr = e & (NF_R - 1), mm = e >> 8;
-      float2 v{0.f, 0.f};
-      if (m0 + mm < m && r0 + rr < k) v = a[(size_t)(m0 + mm) * lda + r0 + rr];
-      as[mm][rr] = v;
+      if (m0 + mm < m && r0 + rr < k) cp_async8(dst + e, a + (size_t)(m0 + mm) * lda + r0 + rr);
+      else dst[e] = float2{0.f, 0.f};
     }
-    for (int e = threadIdx.x; e < NF_M * ncols; e += blockDim.x) {
+    cp_async_commit();
+  };
+  // W chunk: NF_M x ncols = 2 blockDim elements, two per thread, scaled and rounded to FP32
+  auto fetch_w = [&](int m0, float2 (&wr)[2]) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
       const int mm = e / ncols, cc = e - mm * ncols;
       float2 v{0.f, 0.f};
       if (m0 + mm < m && c0 + cc < n) {
@@ -373,21 +392,52 @@ __global__ void __launch_bounds__(64 * NF_GMAX, 2) k_gemm_nn_f32(const float2* _
         const float s = (float)((ws ? ws[m0 + mm] : 1.0) * alpha);
         v = float2{(float)wv.x * s, (float)wv.y * s};
       }
-      wsm[mm][cc] = v;
+      wr[q] = v;
+    }
+  };
+  auto store_w = [&](int buf, const float2 (&wr)[2]) {
+    float2* dst = ws_base + (size_t)buf * NF_M * NF_CMAX;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      const int mm = e / ncols, cc = e - mm * ncols;
+      dst[mm * NF_CMAX + cc] = wr[q];
+    }
+  };
+  const int nch = (m + NF_M - 1) / NF_M;
+  {
+    float2 wr[2];
+    load_a(0, 0);
+    fetch_w(0, wr);
+    store_w(0, wr);
+  }
+  for (int ch = 0; ch < nch; ++ch) {
+    const int cur = ch & 1;
+    const bool more = ch + 1 < nch;
+    float2 wr[2];
+    if (more) {
+      load_a(cur ^ 1, (ch + 1) * NF_M);
+      fetch_w((ch + 1) * NF_M, wr);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const float2* as = as_base + (size_t)cur * NF_M * NF_R;
+    const float2* wsm = ws_base + (size_t)cur * NF_M * NF_CMAX;
 #pragma unroll 2
     for (int mm = 0; mm < NF_M; ++mm) {
       float2 av[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = as[mm][rg + 64 * i];
+      for (int i = 0; i < 4; ++i) av[i] = as[mm * NF_R + rg + 64 * i];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const float2 wv = wsm[mm][cg * 8 + j];
+        const float2 wv = wsm[mm * NF_CMAX + cg * 8 + j];
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[i][j] = cfma(av[i], wv, acc[i][j]);
       }
     }
+    if (more) store_w(cur ^ 1, wr);
     __syncthreads();
   }
 #pragma unroll
@@ -429,7 +479,13 @@ int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const
   if constexpr (std::is_same<Va, float2>::value && std::is_same<Vo, float2>::value) {
     const int g = col_groups(n, NF_GMAX);
     dim3 grid((k + NF_R - 1) / NF_R, (n + NF_CMAX - 1) / NF_CMAX);
-    k_gemm_nn_f32<<<grid, 64 * g, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, (float)beta);
+    static bool attr = false;
+    if (!attr) {
+      DKS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_nn_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)NF_SMEM));
+      attr = true;
+    }
+    k_gemm_nn_f32<<<grid, 64 * g, NF_SMEM, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, (float)beta);
   } else {
     dim3 grid((k + NN_R - 1) / NN_R, (n + NN_C - 1) / NN_C);
     k_gemm_nn<Va, Vo><<<grid, 256, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
