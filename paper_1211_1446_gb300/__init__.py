@@ -326,7 +326,8 @@ class Context:
         report = dict(iterations=list(rep.iterations[:nk]), fp64_iterations=list(rep.fp64_iterations[:nk]),
                       max_residual=list(rep.max_residual[:nk]), h_applications=int(rep.h_applications),
                       shift=rep.shift, seconds=rep.seconds, status=rep.status,
-                      history=list(rep.res_history[:rep.hist_len]))
+                      history=list(rep.res_history[:rep.hist_len]),
+                      message=_lib.dks_last_error().decode() if rc else "")
         return out, report, rc
 
 

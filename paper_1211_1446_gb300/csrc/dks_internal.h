@@ -172,6 +172,7 @@ int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, dou
 // c (m x n, col-major, leading dimension ldc or m) += a^H b, FP64 atomics; FP64 arithmetic when
 // either operand is complex128 or Acc64; lower: only the block lower triangle (square results)
 int mirror_lower(double2* c, int m, cudaStream_t st);   // upper triangle = conj of the lower
+int set_diag_ramp(double2* a, int m, cudaStream_t st);  // a = diag(1, ..., m)
 // block lower triangles of A += Z^H HZ and S += Z^H Z (m x m, column-major) from FP32 blocks in one pass
 int gram_f32(const float2* z, const float2* hz, int ld, int k, int m, double2* a, double2* s, cudaStream_t st);
 // double-float (FP32-pair) versions of the two contractions for complex128 data

@@ -37,6 +37,15 @@ template <> __device__ __forceinline__ float2 cvt<float2>(float2 v) { return v; 
 // ---------------------------------------------------------------- gemm_hn
 constexpr int HN_T = 32;
 
+// asynchronous global -> shared copies (cp.async, 8 bytes) for the multi-stage tile loops
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 // RM = 2: 32 x 32 tiles of C; RM = 3: 48 x 32 tiles (less padding when m is just above 32)
 template <typename Va, typename Vb, typename A, int RM>
 __global__ void __launch_bounds__(256) k_gemm_hn(const Va* __restrict__ a, int lda, const Vb* __restrict__ b,
@@ -123,12 +132,16 @@ __global__ void __launch_bounds__(256) k_gemm_hn(const Va* __restrict__ a, int l
 // lower triangles of 32 x 32 tiles.  The Z tile of the row block serves both products and each
 // thread reuses its two Z row values for four outputs of S and four of A; FP32 within a
 // 32-deep k-tile, folded into double-float totals.
+// two shared-memory stages of (Z rows of the tile's row block, Z and HZ rows of its column block):
+// the next 32-deep k-tile is copied with cp.async while the current one is multiplied
+constexpr int GF_TILE = HN_T * (HN_T + 1);   // one padded 32 x 33 tile, float2
+constexpr size_t GF_SMEM = 2 * 3 * (size_t)GF_TILE * sizeof(float2);
+
 __global__ void __launch_bounds__(256) k_gram_f32(const float2* __restrict__ z, const float2* __restrict__ hz,
                                                   int ld, int k, int m, int kchunk, double2* __restrict__ a,
                                                   double2* __restrict__ s) {
-  __shared__ float2 zs[HN_T][HN_T + 1];
-  __shared__ float2 zb[HN_T][HN_T + 1];
-  __shared__ float2 hb[HN_T][HN_T + 1];
+  extern __shared__ __align__(16) unsigned char gf_smem[];
+  float2* stage = reinterpret_cast<float2*>(gf_smem);   // [2][zs | zb | hb], each [HN_T][HN_T + 1]
   const int t = blockIdx.x;
   int tm = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
   while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
@@ -144,28 +157,48 @@ __global__ void __launch_bounds__(256) k_gram_f32(const float2* __restrict__ z, 
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) as_[i][j] = aa[i][j] = float2{0.f, 0.f};
-  for (int k0 = kb; k0 < ke; k0 += HN_T) {
+  auto load = [&](int buf, int k0) {
+    float2* zs = stage + (size_t)buf * 3 * GF_TILE;
+    float2* zb = zs + GF_TILE;
+    float2* hb = zb + GF_TILE;
     for (int e = threadIdx.x; e < HN_T * HN_T; e += 256) {
       const int kq = e & (HN_T - 1), q = e >> 5;
       const int gk = k0 + kq;
-      float2 vz{0.f, 0.f}, vb{0.f, 0.f}, vh{0.f, 0.f};
-      if (gk < ke) {
-        if (m0 + q < m) vz = z[(size_t)(m0 + q) * ld + gk];
-        if (n0 + q < m) {
-          vb = z[(size_t)(n0 + q) * ld + gk];
-          vh = hz[(size_t)(n0 + q) * ld + gk];
-        }
+      const int o = kq * (HN_T + 1) + q;
+      const bool kin = gk < ke;
+      if (kin && m0 + q < m) cp_async8(zs + o, z + (size_t)(m0 + q) * ld + gk);
+      else zs[o] = float2{0.f, 0.f};
+      if (kin && n0 + q < m) {
+        cp_async8(zb + o, z + (size_t)(n0 + q) * ld + gk);
+        cp_async8(hb + o, hz + (size_t)(n0 + q) * ld + gk);
+      } else {
+        zb[o] = float2{0.f, 0.f};
+        hb[o] = float2{0.f, 0.f};
       }
-      zs[kq][q] = vz;
-      zb[kq][q] = vb;
-      hb[kq][q] = vh;
+    }
+    cp_async_commit();
+  };
+  if (kb < ke) load(0, kb);
+  for (int k0 = kb, it = 0; k0 < ke; k0 += HN_T, ++it) {
+    const int cur = it & 1;
+    if (k0 + HN_T < ke) {
+      load(cur ^ 1, k0 + HN_T);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const float2* zs = stage + (size_t)cur * 3 * GF_TILE;
+    const float2* zb = zs + GF_TILE;
+    const float2* hb = zb + GF_TILE;
 #pragma unroll 8
     for (int kq = 0; kq < HN_T; ++kq) {
-      const float2 a0 = zs[kq][ty], a1 = zs[kq][ty + 16];
-      const float2 b0 = zb[kq][tx], b1 = zb[kq][tx + 16];
-      const float2 h0 = hb[kq][tx], h1 = hb[kq][tx + 16];
+      const float2* zr = zs + kq * (HN_T + 1);
+      const float2* br = zb + kq * (HN_T + 1);
+      const float2* hr = hb + kq * (HN_T + 1);
+      const float2 a0 = zr[ty], a1 = zr[ty + 16];
+      const float2 b0 = br[tx], b1 = br[tx + 16];
+      const float2 h0 = hr[tx], h1 = hr[tx + 16];
       as_[0][0] = cfmac(a0, b0, as_[0][0]);
       as_[0][1] = cfmac(a0, b1, as_[0][1]);
       as_[1][0] = cfmac(a1, b0, as_[1][0]);
@@ -252,7 +285,30 @@ int gram_f32(const float2* z, const float2* hz, int ld, int k, int m, double2* a
   const int kchunk = ((ktiles + splits - 1) / splits) * HN_T;
   splits = (k + kchunk - 1) / kchunk;
   Prof pr(P_GRAM + kProf32, st, 2.0 * m * 8.0 * k + 32.0 * m * m, 8.0 * m * (m + 1.0) * (double)k);
-  k_gram_f32<<<dim3(tiles, splits), 256, 0, st>>>(z, hz, ld, k, m, kchunk, a, s);
+  static bool attr = false;
+  if (!attr) {
+    DKS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gram_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)GF_SMEM));
+    attr = true;
+  }
+  k_gram_f32<<<dim3(tiles, splits), 256, GF_SMEM, st>>>(z, hz, ld, k, m, kchunk, a, s);
+  DKS_CUDA_TRY(cudaGetLastError());
+  return DKS_OK;
+}
+
+// a = diag(1, 2, ..., m) (m x m, column-major)
+__global__ void k_set_diag_ramp(double2* __restrict__ a, int m) {
+  const int total = m * m;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int i = e % m, j = e / m;
+    a[e] = double2{i == j ? (double)(i + 1) : 0.0, 0.0};
+  }
+}
+
+int set_diag_ramp(double2* a, int m, cudaStream_t st) {
+  if (m <= 0) return DKS_OK;
+  Prof pr(P_MISC, st, 16.0 * m * m, 0.0);
+  k_set_diag_ramp<<<std::min(1024, (m * m + 255) / 256), 256, 0, st>>>(a, m);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
@@ -348,13 +404,6 @@ constexpr int NF_R = 256, NF_GMAX = 5, NF_CMAX = 8 * NF_GMAX, NF_M = 16;
 // the W chunk fetched into registers while the current chunk is multiplied.
 constexpr size_t NF_SMEM = 2 * (size_t)NF_M * NF_R * sizeof(float2) + 2 * (size_t)NF_M * NF_CMAX * sizeof(float2);
 
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 __global__ void __launch_bounds__(64 * NF_GMAX, 2) k_gemm_nn_f32(const float2* __restrict__ a, int lda, int k, int m,
                                                      const double2* __restrict__ w, int ldw,

@@ -618,6 +618,15 @@ __global__ void __launch_bounds__(RRC_THREADS, 1) k_rr_cluster(const double2* __
         v0 = csub(x0, beta);
         const dfl nv = df_add(t2, dd_fma(v0.im, v0.im, df_mul(v0.re, v0.re)));
         t = df_div(dfl{2.f, 0.f}, nv);
+        // a tail so small that its squares leave the FP32 exponent range (below ~1e-19 in norm)
+        // gives no representable reflector: the column is left as it is (already reduced to
+        // double-float precision unless the whole matrix is that small)
+        if (!(isfinite(t.h) && isfinite(t.l) && isfinite(v0.re.h) && isfinite(v0.im.h) && isfinite(beta.re.h) &&
+              isfinite(beta.im.h))) {
+          t = dfl{0.f, 0.f};
+          beta = x0;
+          v0 = x0;
+        }
       }
       float4* out = bc + (size_t)(k & 1) * (m + 1);
       const float4 v04 = c4(v0);

@@ -330,15 +330,20 @@ static int davidson_phase(dks_ctx* ctx, Exec& ex, int ik, DBlocks<V>& b, Small& 
   // Cholesky pivot or Gram eigenvalue is below 1e-6 are treated as dependent (SVQB drops them).
   const double otol_c = sizeof(V) == sizeof(double2) ? chol_tol : std::max(chol_tol, 1e-6);
   const double otol_d = sizeof(V) == sizeof(double2) ? drop_tol : std::max(drop_tol, 1e-6);
+  // The basis comes from the generalized eigenvectors of (diag(1, ..., nt), G), G = T^H T: they
+  // are G-orthonormal, so T times them is orthonormal; the distinct diagonal keeps the small
+  // eigenproblem free of one large degenerate cluster (the pencil (G, G) would have nt equal
+  // eigenvalues).
   auto orthonormalise = [&](const V* t, int nt, V* dst, int& rank) -> int {
     DKS_TRY(hn_full(t, nt, t, nt, sm.s, true));
     DKS_TRY(mirror_lower(sm.s, nt, st));
-    DKS_TRY(rayleigh_ritz(sm.s, sm.s, nt, nt, sm.vm, sm.lam, sm.info, sm.rrs, st, otol_c, otol_d));
+    DKS_TRY(set_diag_ramp(sm.a, nt, st));
+    DKS_TRY(rayleigh_ritz(sm.a, sm.s, nt, nt, sm.vm, sm.lam, sm.info, sm.rrs, st, otol_c, otol_d));
     DKS_CUDA_TRY(cudaMemcpyAsync(pin.info, sm.info, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     DKS_CUDA_TRY(cudaStreamSynchronize(st));
     rank = std::min(nt, pin.info[1]);
     if (rank < nt && rank > 0)   // the first rank pairs of the reduced problem
-      DKS_TRY(rayleigh_ritz(sm.s, sm.s, nt, rank, sm.vm, sm.lam, sm.info, sm.rrs, st, otol_c, otol_d));
+      DKS_TRY(rayleigh_ritz(sm.a, sm.s, nt, rank, sm.vm, sm.lam, sm.info, sm.rrs, st, otol_c, otol_d));
     if (rank > 0) DKS_TRY(nn_into(t, nt, sm.vm, nt, rank, dst, 0.0, 1.0));
     return DKS_OK;
   };
@@ -350,7 +355,10 @@ static int davidson_phase(dks_ctx* ctx, Exec& ex, int ik, DBlocks<V>& b, Small& 
     }
   int k = 0;
   DKS_TRY(orthonormalise(b.x, n, b.v, k));
-  if (k < n) return fail(DKS_ERR_RANK, "initial block is rank deficient");
+  if (k < n)
+    return fail(DKS_ERR_RANK, std::string("Davidson: initial block is rank deficient (") +
+                                  (sizeof(V) == sizeof(double2) ? "FP64" : "FP32") + " phase, rank " +
+                                  std::to_string(k) + " of " + std::to_string(n) + ")");
   DKS_TRY(apply_h<V>(ctx, ex, ik, b.v, b.hv, n, 0.0, 1.0, st));
   happ += n;
   std::vector<double> res;
@@ -361,6 +369,18 @@ static int davidson_phase(dks_ctx* ctx, Exec& ex, int ik, DBlocks<V>& b, Small& 
   for (it = 1; it <= n_iter; ++it) {
     DKS_TRY(gram<V>(b.v, b.hv, rows, k, sm, st, df));
     DKS_TRY(rayleigh_ritz(sm.a, sm.s, k, n, sm.vm, sm.lam, sm.info, sm.rrs, st, chol_tol, drop_tol));
+    // A basis whose Gram matrix needed SVQB (Cholesky pivot below chol_tol) or lost rank has
+    // drifted from orthonormal (rounding in the projections, most of all with FP32 blocks):
+    // restart it from the current Ritz vectors (X, HX of the previous iteration) instead.
+    DKS_CUDA_TRY(cudaMemcpyAsync(pin.info, sm.info, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    DKS_CUDA_TRY(cudaStreamSynchronize(st));
+    const bool conditioned = pin.info[0] == 0 && pin.info[1] >= n;
+    if (!conditioned && k > n && it > 1) {
+      DKS_CUDA_TRY(cudaMemcpyAsync(b.v, b.x, (size_t)n * colsz * sizeof(V), cudaMemcpyDeviceToDevice, st));
+      DKS_CUDA_TRY(cudaMemcpyAsync(b.hv, b.hx, (size_t)n * colsz * sizeof(V), cudaMemcpyDeviceToDevice, st));
+      k = n;
+      continue;
+    }
     DKS_TRY(nn_into(b.v, k, sm.vm, k, n, b.x, 0.0, 1.0));
     DKS_TRY(nn_into(b.hv, k, sm.vm, k, n, b.hx, 0.0, 1.0));
     DKS_TRY(col_stats<V>(b.x, b.hx, sm.lam, kp.ek, kp.npw, n, sm.stats, st, nc));
@@ -372,7 +392,10 @@ static int davidson_phase(dks_ctx* ctx, Exec& ex, int ik, DBlocks<V>& b, Small& 
         DKS_CUDA_TRY(cudaMemcpyAsync(b.x, b.best, (size_t)n * colsz * sizeof(V), cudaMemcpyDeviceToDevice, st));
         break;
       }
-      return fail(DKS_ERR_RANK, "Davidson basis rank below the block size");
+      return fail(DKS_ERR_RANK, std::string("Davidson basis rank below the block size (") +
+                                    (sizeof(V) == sizeof(double2) ? "FP64" : "FP32") + " phase, iteration " +
+                                    std::to_string(it) + ", basis " + std::to_string(k) + ", rank " +
+                                    std::to_string(pin.info[1]) + ", svqb " + std::to_string(pin.info[0]) + ")");
     }
     maxres = 0;
     for (int j = 0; j < nconv; ++j) maxres = std::max(maxres, res[j]);
@@ -383,7 +406,7 @@ static int davidson_phase(dks_ctx* ctx, Exec& ex, int ik, DBlocks<V>& b, Small& 
       break;
     }
     if (stop_on_stall) {   // the FP32 phase's floor, as in Algorithm 1's mixed mode
-      if (b.best && maxres < lowest) {
+      if (b.best && maxres < lowest && conditioned) {   // hand on only X from a well-conditioned basis
         lowest = maxres;
         DKS_CUDA_TRY(cudaMemcpyAsync(b.best, b.x, (size_t)n * colsz * sizeof(V), cudaMemcpyDeviceToDevice, st));
       }

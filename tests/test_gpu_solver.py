@@ -36,7 +36,7 @@ def test_cubic_vs_dense(mode):
     wl, ctx, hop, q = make_pair("cubic")
     ref = np.loadtxt(os.path.join(GOLDEN, "cubic_dense_eigs.txt"))
     lam, x, rep, rc = _solve(ctx, wl, q, 8, mode)
-    assert rc == 0, rep
+    assert rc == 0, (rc, rep["message"], rep["iterations"], rep["fp64_iterations"])
     assert np.abs(lam - ref).max() < 1e-8
     assert _residuals(hop, x, lam).max() < 1e-6
     assert np.all(lam > -wl.c ** 2)
@@ -51,7 +51,7 @@ def test_small_spin_orbit_vs_dense(mode, kf):
     m, _ = ob.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
     ref, _, _ = olb.dense_eigs(oop.dense_hamiltonian(wl, m, q), wl.c, 6)
     lam, x, rep, rc = _solve(ctx, wl, q, 6, mode)
-    assert rc == 0, rep
+    assert rc == 0, (rc, rep["message"], rep["iterations"], rep["fp64_iterations"])
     assert np.abs(lam - ref).max() < 1e-8
     assert _residuals(hop, x, lam).max() < 1e-6
 
@@ -67,7 +67,7 @@ def test_ksso_vs_dense(mode, kf):
     m, _ = ob.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
     ref = np.linalg.eigvalsh(oop.dense_hamiltonian_ksso(wl, m, q))[:6]
     lam, x, rep, rc = _solve(ctx, wl, q, 6, mode, nbuf=2)
-    assert rc == 0, rep
+    assert rc == 0, (rc, rep["message"], rep["iterations"], rep["fp64_iterations"])
     assert rep["shift"] == 0.0
     assert np.abs(lam - ref).max() < 1e-8
     assert _residuals(hop, x[:6], lam).max() < 1e-6
@@ -96,7 +96,7 @@ def test_davidson_f_vs_dense(mode, name, nev):
     m, _ = ob.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
     ref, _, _ = olb.dense_eigs(oop.dense_hamiltonian(wl, m, q), wl.c, nev)
     lam, x, rep, rc = _solve(ctx, wl, q, nev, mode, nbuf=2, solver="davidson")
-    assert rc == 0, rep
+    assert rc == 0, (rc, rep["message"], rep["iterations"], rep["fp64_iterations"])
     assert np.abs(lam - ref).max() < 1e-8
     assert _residuals(hop, x[:nev], lam).max() < 1e-6
     assert np.all(lam > -wl.c ** 2)
@@ -111,7 +111,7 @@ def test_davidson_f_small_basis_restarts_and_matches_oracle():
     x0 = W.start_block(len(q), 8, wl.seed)
     ref = odv.davidson_f(hop, q, x0, 8, cs, om, tol=1e-7, nconv=6, m_max=16).lam[:6]
     lam, x, rep, rc = _solve(ctx, wl, q, 6, 0, nbuf=2, solver="davidson", m_max=16, tol=1e-7)
-    assert rc == 0, rep
+    assert rc == 0, (rc, rep["message"], rep["iterations"], rep["fp64_iterations"])
     assert np.abs(lam - ref).max() < 1e-8
 
 
@@ -134,7 +134,7 @@ def test_davidson_ksso_vs_dense():
     m, _ = ob.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
     ref = np.linalg.eigvalsh(oop.dense_hamiltonian_ksso(wl, m, q))[:6]
     lam, x, rep, rc = _solve(ctx, wl, q, 6, 1, nbuf=2, solver="davidson")
-    assert rc == 0, rep
+    assert rc == 0, (rc, rep["message"], rep["iterations"], rep["fp64_iterations"])
     assert np.abs(lam - ref).max() < 1e-8
 
 
@@ -170,7 +170,7 @@ def test_dimer_full_size_vs_oracle(mode):
     ref = np.loadtxt(os.path.join(GOLDEN, "dimer_lobpcgf_eigs.txt"))
     x0 = torch.from_numpy(W.start_block(len(q), 40, wl.seed)).cuda()
     lam, rep, rc = ctx.solve([x0], 32, nbuf=8, tol=1e-6, mode=mode, check=False)
-    assert rc == 0, rep
+    assert rc == 0, (rc, rep["message"], rep["iterations"], rep["fp64_iterations"])
     lam = lam[0]
     assert np.abs(lam - ref).max() < 1e-8
     assert np.all(lam > -wl.c ** 2)
@@ -189,7 +189,7 @@ def test_davidson_f_dimer_full_size_vs_oracle():
     ref = np.loadtxt(os.path.join(GOLDEN, "dimer_lobpcgf_eigs.txt"))
     x0 = torch.from_numpy(W.start_block(len(q), 40, wl.seed)).cuda()
     lam, rep, rc = ctx.solve([x0], 32, nbuf=8, tol=1e-6, mode=1, check=False, solver="davidson", m_max=160)
-    assert rc == 0, rep
+    assert rc == 0, (rc, rep["message"], rep["iterations"], rep["fp64_iterations"], rep["history"][-8:])
     assert np.abs(lam[0] - ref).max() < 1e-8
     pick = np.array([0, 13, 31])
     assert _residuals(hop, x0.cpu().numpy()[pick], lam[0][pick]).max() < 1e-6
@@ -205,7 +205,7 @@ def test_ksso_dimer_full_size_vs_oracle():
     ref = np.loadtxt(os.path.join(GOLDEN, "dimer_ksso_eigs.txt"))
     x0 = torch.from_numpy(W.start_block(len(q), 40, wl.seed, ncomp=2)).cuda()
     lam, rep, rc = ctx.solve([x0], 32, nbuf=8, tol=1e-6, mode=1, check=False)
-    assert rc == 0, rep
+    assert rc == 0, (rc, rep["message"], rep["iterations"], rep["fp64_iterations"])
     assert np.abs(lam[0] - ref).max() < 1e-8
     pick = np.array([0, 13, 31])
     assert _residuals(hop, x0.cpu().numpy()[pick], lam[0][pick]).max() < 1e-6
@@ -227,7 +227,7 @@ def test_multi_k_concurrent_matches_serial_and_dense():
     for conc in (4, 1):
         xs = [torch.from_numpy(W.start_block(ctx.npw(ik), nev, wl.seed, ik)).cuda() for ik in range(4)]
         lam, rep, rc = ctx.solve(xs, nev, mode=1, concurrency=conc, check=False)
-        assert rc == 0, rep
+        assert rc == 0, (rc, rep["message"], rep["iterations"], rep["fp64_iterations"])
         runs.append(lam)
     for ik in range(4):
         assert np.abs(runs[0][ik] - runs[1][ik]).max() < 1e-9
