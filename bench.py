@@ -175,12 +175,12 @@ def run_reference(args):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per kernel launch from ncu captures of
 # the current kernels at the dimer's sizes (python bench.py --kernel-case <case> under ncu --set full)
 NCU_TRAFFIC = {
-    "rayleigh_ritz": {"bytes_per_launch": (526.6e3 + 2 * 469.2e3 + 425.7e3 + 539.9e3) / 5,
+    "rayleigh_ritz": {"bytes_per_launch": (526.3e3 + 2 * 469.2e3 + 425.5e3 + 539.9e3) / 5,
                       "note": "kernel case rr (m = 120, n = 40): mean over the five kernels of a step, "
                               "each captured cold (the pencil is 537 KB)"},
     "gram": {"bytes_per_launch": 922.6e6 + 4.5e6,
              "note": "kernel case gramdf (k_gram_df, 120 columns of 229,676 rows)"},
-    "gram_fp32": {"bytes_per_launch": 223.2e6 + 3.5e6,
+    "gram_fp32": {"bytes_per_launch": 223.3e6 + 3.3e6,
                   "note": "kernel case gram32 (k_gram_f32, 120 columns of 229,676 rows)"},
 }
 
