@@ -376,6 +376,98 @@ __global__ void __launch_bounds__(64 * DNN_GMAX, 2) k_gemm_nn_df(const TA* __res
   }
 }
 
+// The same product for pre-split (float4) A in two shared-memory stages: the A chunk of the
+// next 16 inner indices is copied with cp.async (16 bytes per element) while the current one is
+// multiplied; W is split into double-float pairs after the multiply.
+constexpr size_t DNN_SMEM = 2 * (size_t)DNN_M * DNN_R * sizeof(gcdf) + 2 * (size_t)DNN_M * DNN_CMAX * sizeof(gcdf);
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src));
+}
+
+__global__ void __launch_bounds__(64 * DNN_GMAX, 2) k_gemm_nn_df4(const float4* __restrict__ a, int lda, int k, int m,
+                                                        const double2* __restrict__ w, int ldw,
+                                                        const double* __restrict__ ws, int n,
+                                                        double2* __restrict__ out, int ldo, double alpha, double beta) {
+  extern __shared__ __align__(16) unsigned char dn_smem[];
+  gcdf* as_base = reinterpret_cast<gcdf*>(dn_smem);          // [2][DNN_M][DNN_R]
+  gcdf* ws_base = as_base + 2 * DNN_M * DNN_R;                // [2][DNN_M][DNN_CMAX]
+  const int ncols = (blockDim.x >> 6) * 8;
+  const int r0 = blockIdx.x * DNN_R, c0 = blockIdx.y * ncols;
+  const int rg = threadIdx.x & 63, cg = threadIdx.x >> 6;
+  gcdf acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = gcdf{{0.f, 0.f}, {0.f, 0.f}};
+  auto load_a = [&](int buf, int m0) {
+    gcdf* dst = as_base + (size_t)buf * DNN_M * DNN_R;
+    for (int e = threadIdx.x; e < DNN_M * DNN_R; e += blockDim.x) {
+      const int mm = e / DNN_R, rr = e - mm * DNN_R;
+      if (m0 + mm < m && r0 + rr < k) cp_async16(dst + e, a + (size_t)(m0 + mm) * lda + r0 + rr);
+      else dst[e] = gcdf{{0.f, 0.f}, {0.f, 0.f}};
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+  auto load_w = [&](int buf, int m0) {
+    gcdf* dst = ws_base + (size_t)buf * DNN_M * DNN_CMAX;
+    for (int e = threadIdx.x; e < DNN_M * ncols; e += blockDim.x) {
+      const int mm = e / ncols, cc = e - mm * ncols;
+      double2 v{0, 0};
+      if (m0 + mm < m && c0 + cc < n) {
+        v = w[(size_t)(c0 + cc) * ldw + m0 + mm];
+        const double sc = (ws ? ws[m0 + mm] : 1.0) * alpha;
+        v.x *= sc;
+        v.y *= sc;
+      }
+      dst[mm * DNN_CMAX + cc] = gcdf_split(v);
+    }
+  };
+  const int nch = (m + DNN_M - 1) / DNN_M;
+  load_a(0, 0);
+  load_w(0, 0);
+  for (int ch = 0; ch < nch; ++ch) {
+    const int cur = ch & 1;
+    const bool more = ch + 1 < nch;
+    if (more) {
+      load_a(cur ^ 1, (ch + 1) * DNN_M);
+      asm volatile("cp.async.wait_group 1;\n" ::);
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::);
+    }
+    __syncthreads();
+    const gcdf* as = as_base + (size_t)cur * DNN_M * DNN_R;
+    const gcdf* wsm = ws_base + (size_t)cur * DNN_M * DNN_CMAX;
+    for (int mm0 = 0; mm0 < DNN_M; mm0 += 4) {
+#pragma unroll 2
+      for (int mm = mm0; mm < mm0 + 4; ++mm) {
+        const gcdf av = as[mm * DNN_R + rg];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cdf_mac(acc[j], av, wsm[mm * DNN_CMAX + cg * 8 + j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) cdf_renorm(acc[j]);   // every 8 updates of each part
+    }
+    if (more) load_w(cur ^ 1, (ch + 1) * DNN_M);
+    __syncthreads();
+  }
+  const int row = r0 + rg;
+  if (row >= k) return;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int cc = c0 + cg * 8 + j;
+    if (cc < n) {
+      double2* o = out + (size_t)cc * ldo + row;
+      double2 r{df_to_d(acc[j].re), df_to_d(acc[j].im)};
+      if (beta != 0.0) {
+        const double2 old = *o;
+        r.x += beta * old.x;
+        r.y += beta * old.y;
+      }
+      *o = r;
+    }
+  }
+}
+
 template <typename TA>
 static int gemm_nn_df_t(const TA* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
                         int n, double2* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
@@ -386,7 +478,17 @@ static int gemm_nn_df_t(const TA* a, int lda, int k, int m, const double2* w, in
   dim3 grid((k + DNN_R - 1) / DNN_R, tiles);
   Prof pr(cat, st, (double)m * k * 16.0 + (beta != 0.0 ? 2.0 : 1.0) * n * k * 16.0 + 16.0 * m * n,
           8.0 * (double)k * m * n);
-  k_gemm_nn_df<TA><<<grid, 64 * g, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
+  if constexpr (std::is_same<TA, float4>::value) {
+    static bool attr = false;
+    if (!attr) {
+      DKS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_nn_df4, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)DNN_SMEM));
+      attr = true;
+    }
+    k_gemm_nn_df4<<<grid, 64 * g, DNN_SMEM, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
+  } else {
+    k_gemm_nn_df<TA><<<grid, 64 * g, 0, st>>>(a, lda, k, m, w, ldw, wscale, n, out, ldo, alpha, beta);
+  }
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
