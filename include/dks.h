@@ -162,7 +162,7 @@ int dks_filter(dks_ctx* ctx, int ik, const void* Y, void* FY, int nb, double C, 
 #define DKS_PRECOND_IDENTITY 1
 
 typedef struct {
-  int n_init;          /* initial filter steps N_init (Alg. 1 lines 1-3), default 3 */
+  int n_init;          /* initial filter steps N_init (Algorithm 1), default 3          */
   int n_iter;          /* maximum iterations N_iter, default 200                       */
   int nbuf;            /* extra columns iterated but not convergence-checked           */
   double C, Omega;     /* filter constants; NaN = dks_filter_constants                 */
@@ -187,7 +187,7 @@ typedef struct {
 /* Solvers.  LOBPCG: Algorithm 1 (LOBPCG-F with use_filter = 1).  DAVIDSON: block Davidson with
  * the same filter step (the paper notes that the filter carries over to Davidson-type
  * solvers, Sec. 3): a growing orthonormal basis V replaces [X, Y, P]; every iteration does
- * Rayleigh-Ritz on V, forms T = f(H) K(R) on the active columns (as lines 9-10 of Alg. 1),
+ * Rayleigh-Ritz on V, forms T = f(H) K(R) on the active columns (Algorithm 1's preconditioning and filter steps),
  * restarts V from the Ritz vectors when it would exceed m_max columns, projects T out of V
  * (twice), orthonormalises it and appends it.  Same options, modes and report otherwise. */
 #define DKS_SOLVER_LOBPCG 0
@@ -226,7 +226,7 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
  * Exposed so that each step can be checked on its own.  Column blocks are
  * [ncol][rows] complex (rows = 4 npw for DKS vectors), device memory. */
 
-/* Alg. 1 line 9 with the residual of line 16 fused: for i < nact, column
+/* Algorithm 1's preconditioning step with the residual fused: for i < nact, column
  * j = act[i] (device int[nact]):  Y[i] = K(x_G) (HX[j] - lam[j] X[j]) with the
  * Teter-Payne-Allan factor K(x) = P/(P + 16x^4), P = 27+18x+12x^2+8x^3,
  * x_G = (|k+G|^2/2)/T_j, T_j = sum |k+G|^2/2 |X[j]|^2 / sum |X[j]|^2 over all four
@@ -234,7 +234,7 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
 int dks_precond(dks_ctx* ctx, int ik, const void* X, const void* HX, const double* lam,
                 const int* act, int nact, void* Y, int precond, int prec, void* stream);
 
-/* Alg. 1 lines 12-13 (the projected pencil): A = Z^H HZ and S = Z^H Z for
+/* Algorithm 1's projected pencil: A = Z^H HZ and S = Z^H Z for
  * Z, HZ [nz][rows]; A, S device double2 (complex128) nz x nz, column-major,
  * every entry computed (no symmetry assumed).  prec FP64: FP64 arithmetic;
  * FP64_EMULATED: complex128 data, double-float arithmetic; FP32: complex64
@@ -242,7 +242,7 @@ int dks_precond(dks_ctx* ctx, int ik, const void* X, const void* HX, const doubl
 int dks_gram(const void* Z, const void* HZ, int rows, int nz, void* A, void* S, int prec,
              void* stream);
 
-/* The solver's form of Alg. 1 lines 12-13: the block lower triangles of A =
+/* The solver's form of Algorithm 1's projected pencil: the block lower triangles of A =
  * Z^H HZ and S = Z^H Z in one fused pass over Z and HZ, then each strict upper
  * triangle set to the conjugate transpose of the lower one (A is Hermitian when
  * HZ = H' Z).  Arguments and layout as dks_gram; on return A[j][i] (column j,
@@ -254,7 +254,7 @@ int dks_gram(const void* Z, const void* HZ, int rows, int nz, void* A, void* S, 
 int dks_gram_hermitian(const void* Z, const void* HZ, int rows, int nz, void* A, void* S, int prec,
                        void* stream);
 
-/* Alg. 1 lines 12-14 on the device in FP64: the n lowest pairs of A v = lam S v
+/* Algorithm 1's Rayleigh-Ritz step on the device in FP64: the n lowest pairs of A v = lam S v
  * (after diagonal scaling; Cholesky of S, or SVQB with drop tolerance
  * 1e-12 * max eig when the smallest Cholesky pivot^2 < 1e-12).  A, S device
  * complex128 nz x nz column-major; V device complex128 nz x n column-major;
@@ -278,13 +278,13 @@ int dks_rayleigh_ritz(const void* A, const void* S, int nz, int n, void* V, doub
 int dks_rayleigh_ritz_static(const void* A, const void* S, int nz, int n, void* V, double* lam,
                              int* info, void* stream);
 
-/* Alg. 1 line 15 / 22: OUT[j] = sum_i Z[i] W[i + ldw*j] (+ beta OUT[j]) for
+/* Algorithm 1's rotations (X <- Z V, P <- [0, Y, P] V): OUT[j] = sum_i Z[i] W[i + ldw*j] (+ beta OUT[j]) for
  * j < n, i < nz; Z [nz][rows], OUT [n][rows] (precision prec), W device
  * complex128 column-major with leading dimension ldw (converted to prec). */
 int dks_rotate(const void* Z, int rows, int nz, const void* W, int ldw, int n, void* OUT,
                double beta, int prec, void* stream);
 
-/* Alg. 1 line 16-17: norms[j] = ||HX[j] - lam[j] X[j]||_2.  The residual and the sum over the
+/* Algorithm 1's residual norms: norms[j] = ||HX[j] - lam[j] X[j]||_2.  The residual and the sum over the
  * components of a planewave are formed in the storage precision (DKS_PREC_FP32: FP32,
  * otherwise FP64); the sum over planewaves is accumulated in FP64.  rows even (4 npw for
  * DKS four-spinors, 2 npw for KSSO two-spinors). */

@@ -14,7 +14,7 @@ H X is carried by the same rotation as X (H Z V), so each iteration applies H
 three times (two for the filter, one for H Y), as Sec. 3.2 states.
 
 The generalized eigenproblems are solved after the diagonal scaling of S
-(reading of lines 4 and 11, where the paper gives no orthonormalisation detail):
+(reading of the Rayleigh-Ritz steps, where the paper gives no orthonormalisation detail):
 Cholesky of the scaled S when its smallest pivot is safely positive, otherwise
 SVQB (eigen-decomposition of S, directions with eigenvalue below drop_tol times
 the largest are discarded).
@@ -113,41 +113,41 @@ def lobpcgf(hop, q, x0, n, cshift, omega, n_init=3, n_iter=200, tol=1e-6, nconv=
         return rb.copy()
 
     x = np.array(x0, dtype=np.complex128)
-    for _ in range(n_init if use_filter else 0):          # lines 1-3
+    for _ in range(n_init if use_filter else 0):          # initial filtering
         x = fh(x)
     hx = hop(x)
     xm, hxm = _cols(x), _cols(hx)
-    lam, v, _ = rayleigh_ritz(xm.conj().T @ hxm, xm.conj().T @ xm, n)   # line 4
-    xm, hxm = xm @ v, hxm @ v                                           # line 5
-    rm = hxm - xm * lam[None, :]                                        # line 6
+    lam, v, _ = rayleigh_ritz(xm.conj().T @ hxm, xm.conj().T @ xm, n)   # first Rayleigh-Ritz
+    xm, hxm = xm @ v, hxm @ v                                           # X, HX rotated
+    rm = hxm - xm * lam[None, :]                                        # residual
     act = np.arange(n)
-    pm = hpm = None                                                     # line 7
+    pm = hpm = None                                                     # no search block yet
     history = []
     norms = np.linalg.norm(rm, axis=0)
     converged = False
     it = 0
-    for it in range(1, n_iter + 1):                                     # line 8
-        yb = tinv(_blk(xm[:, act], npw, nc), _blk(rm, npw, nc))         # line 9
-        yb = fh(yb)                                                     # line 10
+    for it in range(1, n_iter + 1):                                     # iteration
+        yb = tinv(_blk(xm[:, act], npw, nc), _blk(rm, npw, nc))         # preconditioned residual
+        yb = fh(yb)                                                     # filter
         ym = _cols(yb)
         hym = _cols(hop(yb))
-        zm = np.hstack([xm, ym] + ([pm] if pm is not None else []))     # line 11
+        zm = np.hstack([xm, ym] + ([pm] if pm is not None else []))     # subspace Z
         hzm = np.hstack([hxm, hym] + ([hpm] if hpm is not None else []))
-        lam, v, info = rayleigh_ritz(zm.conj().T @ hzm, zm.conj().T @ zm, n)   # lines 12-14
-        xm, hxm = zm @ v, hzm @ v                                       # line 15
-        rm = hxm - xm * lam[None, :]                                    # line 16
+        lam, v, info = rayleigh_ritz(zm.conj().T @ hzm, zm.conj().T @ zm, n)   # Rayleigh-Ritz
+        xm, hxm = zm @ v, hzm @ v                                       # X, HX rotated
+        rm = hxm - xm * lam[None, :]                                    # residual
         norms = np.linalg.norm(rm, axis=0)
         history.append(dict(it=it, max_res=float(norms[:nconv].max()), nz=zm.shape[1],
                             nact=len(act), svqb=info.svqb, lam=lam.copy()))
         if callback is not None:
             callback(it, lam, norms)
-        if np.all(norms[:nconv] < tol):                                 # lines 17-19
+        if np.all(norms[:nconv] < tol):                                 # convergence test
             converged = True
             break
-        act = np.nonzero(norms > tol)[0]                                # line 20
+        act = np.nonzero(norms > tol)[0]                                # soft locking
         rm = rm[:, act]
-        va = v[n:, act]                                                 # line 21
-        pm, hpm = zm[:, n:] @ va, hzm[:, n:] @ va                       # line 22: [0, Y, P] V
+        va = v[n:, act]                                                 # coefficients of the active columns
+        pm, hpm = zm[:, n:] @ va, hzm[:, n:] @ va                       # P <- [0, Y, P] V
     used = (hop.count - start) if hasattr(hop, "count") else -1
     return SolveResult(lam=lam, x=_blk(xm, npw, nc), iterations=it, converged=converged,
                        resnorms=norms, history=history, h_applications=used)

@@ -1,16 +1,16 @@
 // Block linear algebra of Algorithm 1 on tall-skinny complex blocks.
 //
 //  gemm_hn   C (m x n) += A^H B   A: k x m, B: k x n (k = 4 npw or 2 npw, huge; m, n small)
-//            Gram matrices of lines 12-13 and the projector coefficients B^H x~.
+//            Gram matrices of the projected pencil and the projector coefficients B^H x~.
 //            Split over k across the grid; each CTA reduces a 32x32 tile of C over its
 //            k-range in registers and adds it to C with FP64 atomics.  With FP32 operands
 //            each 32-deep k-tile is summed in FP32 and folded into a double-float total.
 //  gemm_nn   OUT (k x n) = alpha A (k x m) diag(ws) W (m x n) + beta OUT
-//            Rotations X <- Z V, P <- [0,Y,P] V (lines 15, 22) and the projector
+//            Rotations X <- Z V, P <- [0,Y,P] V and the projector
 //            update x~ += B (D Z).  W (FP64, from the small solve) is staged in shared
 //            memory in the working precision.
 //  col_stats per column: ||hx - lam x||^2, ||x||^2 and sum_G |k+G|^2/2 |x|^2 (FP64 column sums)
-//  precond   Y = K(x_G) (HX - lam X) on the active columns (lines 9 and 16 fused)
+//  precond   Y = K(x_G) (HX - lam X) on the active columns (residual and Teter factor fused)
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 

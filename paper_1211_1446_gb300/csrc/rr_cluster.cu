@@ -1,4 +1,4 @@
-// FP64 Rayleigh-Ritz on a thread-block cluster (Cholesky path of Algorithm 1 lines 4 and 12-14).
+// FP64 Rayleigh-Ritz on a thread-block cluster (Cholesky path of Algorithm 1's Rayleigh-Ritz steps).
 //
 // FP64 throughput on GB300 is about two FMAs per clock per SM, so the O(m^3) work of the
 // small pencil is spread over the SMs of one cluster (16 CTAs when the device allows

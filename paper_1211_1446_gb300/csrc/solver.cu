@@ -2,16 +2,16 @@
 //
 // Per k-point the blocks Z = [X | Y | P] and HZ = [HX | HY | HP] live in two
 // ping-pong column buffers of capacity 3n columns (n = nev + nbuf), each column
-// 4 npw complex values.  One iteration:
-//   Y  = K(x_G) (HX - X Lambda) on the active columns           (lines 9, 16)
-//   Y  = f(H) Y      two H' passes with shift C and scale 1/Omega (line 10)
+// ncomp npw complex values.  One iteration:
+//   Y  = K(x_G) (HX - X Lambda) on the active columns           (preconditioned residual)
+//   Y  = f(H) Y      two H' passes with shift C and scale 1/Omega (filter)
 //   HY = H' Y                                                     (one H' pass)
-//   A = Z^H HZ, S = Z^H Z, FP64 Rayleigh-Ritz, first n pairs      (lines 11-14)
-//   X, HX <- Z V, HZ V into the other buffer                       (line 15)
+//   A = Z^H HZ, S = Z^H Z, FP64 Rayleigh-Ritz, first n pairs      (Rayleigh-Ritz)
+//   X, HX <- Z V, HZ V into the other buffer                       (rotation)
 //   (emulated FP64: Z and HZ are split into double-float copies once, before the Gram matrices,
 //    and the Gram and rotation kernels read the copies)
-//   column norms of HX - X Lambda (FP64), host reads them          (lines 16-19)
-//   P, HP <- [0, Y, P] V_active, HZ likewise                        (lines 20-22)
+//   column norms of HX - X Lambda (FP64), host reads them          (convergence test)
+//   P, HP <- [0, Y, P] V_active, HZ likewise                        (soft locking, new P)
 // so H' is applied 3 times per active column per iteration (Sec. 3.2).
 //
 // DKS_MODE_MIXED runs the same loop with complex64 blocks (FP32 H', Gram and
@@ -159,13 +159,13 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
   const size_t colsz = (size_t)rows;
   int cur = out.cur;
   long long happ = 0;
-  // lines 1-3: initial filtering
+  // initial filtering
   if (use_filter)
     for (int i = 0; i < n_init; ++i) {
       DKS_TRY(filter_inplace<V>(ctx, ex, ik, b.z[cur], b.tmp, n, C, om, st));
       happ += 2LL * n;
     }
-  // line 4-6: Rayleigh-Ritz on X0
+  // first Rayleigh-Ritz on X0
   DKS_TRY(apply_h<V>(ctx, ex, ik, b.z[cur], b.hz[cur], n, 0.0, 1.0, st));
   happ += n;
   // Gram matrices and rotations of nz columns of Z, HZ (from double-float copies when present)
@@ -194,7 +194,7 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
   DKS_TRY(fetch(sm, pin, n, res, st));
   if (pin.info[1] < n) return fail(DKS_ERR_RANK, "initial block is rank deficient");
   std::vector<int> act;
-  for (int j = 0; j < n; ++j) act.push_back(j);   // line 9 uses every column of R first
+  for (int j = 0; j < n; ++j) act.push_back(j);   // the first preconditioning uses every column of R
   int p = 0;
   double best = INFINITY, lowest = INFINITY;
   int since_best = 0;
@@ -255,7 +255,7 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
         break;
       }
     }
-    // lines 20-22: soft locking, P <- [0, Y, P] V_active
+    // soft locking, P <- [0, Y, P] V_active
     std::vector<int> act2;
     for (int j = 0; j < n; ++j)
       if (res[j] > tol) act2.push_back(j);
@@ -347,7 +347,7 @@ static int davidson_phase(dks_ctx* ctx, Exec& ex, int ik, DBlocks<V>& b, Small& 
     if (rank > 0) DKS_TRY(nn_into(t, nt, sm.vm, nt, rank, dst, 0.0, 1.0));
     return DKS_OK;
   };
-  // lines 1-3 of Algorithm 1
+  // initial filtering of Algorithm 1
   if (use_filter)
     for (int i = 0; i < n_init; ++i) {
       DKS_TRY(filter_inplace<V>(ctx, ex, ik, b.x, b.tmp, n, C, om, st));

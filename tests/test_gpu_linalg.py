@@ -130,7 +130,7 @@ def test_gram_double_float(rows, nz):
                                            ("df", 4 * 5, 1), ("df", 4 * 57419, 97), ("fp64", 1000, 33),
                                            ("fp64", 4 * 3001, 120)])
 def test_gram_hermitian(prec, rows, nz):
-    """The solver's fused Gram (Alg. 1 lines 12-13): block lower triangles of A = Z^H HZ and
+    """The solver's fused Gram (Algorithm 1's projected pencil): block lower triangles of A = Z^H HZ and
     S = Z^H Z in one pass, strict upper triangles the exact conjugate mirror of the lower ones."""
     torch = gpu()
     import paper_1211_1446_gb300 as P
