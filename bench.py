@@ -423,9 +423,8 @@ def main():
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        from paper_1211_1446_gb300 import shard
+        ms = shard.max_over_ranks(ms)
         dist.barrier()
     value = NEV * ws / (ms / 1e3)
 
