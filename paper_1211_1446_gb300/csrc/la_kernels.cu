@@ -128,6 +128,105 @@ __global__ void __launch_bounds__(256) k_gemm_hn(const Va* __restrict__ a, int l
     }
 }
 
+// The FP32 case of k_gemm_hn (complex64 operands, FP32 k-tiles folded into double-float totals)
+// with two shared-memory stages: the next 32-deep k-tile of A and B is copied with cp.async
+// while the current one is multiplied.
+template <int RM>
+constexpr size_t hn32_smem() {
+  return 2 * ((size_t)HN_T * (16 * RM + 1) + (size_t)HN_T * (HN_T + 1)) * sizeof(float2);
+}
+
+template <int RM>
+__global__ void __launch_bounds__(256) k_gemm_hn_f32p(const float2* __restrict__ a, int lda,
+                                                      const float2* __restrict__ b, int ldb, int k, int m, int n,
+                                                      int mt, int kchunk, double2* __restrict__ c, int ldc,
+                                                      int lower) {
+  constexpr int TM = 16 * RM;
+  constexpr int AS = HN_T * (TM + 1), BS = HN_T * (HN_T + 1);
+  extern __shared__ __align__(16) unsigned char h32_smem[];
+  float2* stage = reinterpret_cast<float2*>(h32_smem);   // [2][as | bs]
+  int tm, tn;
+  if (lower) {
+    const int t = blockIdx.x;
+    tm = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
+    while (tm * (tm + 1) / 2 > t) --tm;
+    tn = t - tm * (tm + 1) / 2;
+  } else {
+    tm = blockIdx.x % mt;
+    tn = blockIdx.x / mt;
+  }
+  const int m0 = tm * TM, n0 = tn * HN_T;
+  const int kb = blockIdx.y * kchunk;
+  const int ke = min(k, kb + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float2 acc[RM][2];
+#pragma unroll
+  for (int i = 0; i < RM; ++i) acc[i][0] = acc[i][1] = float2{0.f, 0.f};
+  dfl tot[RM][2][2] = {};
+  auto load = [&](int buf, int k0) {
+    float2* as = stage + (size_t)buf * (AS + BS);
+    float2* bs = as + AS;
+    for (int e = threadIdx.x; e < HN_T * TM; e += 256) {
+      const int kq = e & (HN_T - 1), q = e >> 5;
+      const int gk = k0 + kq;
+      float2* d = as + kq * (TM + 1) + q;
+      if (gk < ke && m0 + q < m) cp_async8(d, a + (size_t)(m0 + q) * lda + gk);
+      else *d = float2{0.f, 0.f};
+    }
+    for (int e = threadIdx.x; e < HN_T * HN_T; e += 256) {
+      const int kq = e & (HN_T - 1), q = e >> 5;
+      const int gk = k0 + kq;
+      float2* d = bs + kq * (HN_T + 1) + q;
+      if (gk < ke && n0 + q < n) cp_async8(d, b + (size_t)(n0 + q) * ldb + gk);
+      else *d = float2{0.f, 0.f};
+    }
+    cp_async_commit();
+  };
+  if (kb < ke) load(0, kb);
+  for (int k0 = kb, it = 0; k0 < ke; k0 += HN_T, ++it) {
+    const int cur = it & 1;
+    if (k0 + HN_T < ke) {
+      load(cur ^ 1, k0 + HN_T);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float2* as = stage + (size_t)cur * (AS + BS);
+    const float2* bs = as + AS;
+#pragma unroll 8
+    for (int kq = 0; kq < HN_T; ++kq) {
+      const float2 b0 = bs[kq * (HN_T + 1) + tx], b1 = bs[kq * (HN_T + 1) + tx + 16];
+#pragma unroll
+      for (int i = 0; i < RM; ++i) {
+        const float2 ai = as[kq * (TM + 1) + ty + 16 * i];
+        acc[i][0] = cfmac(ai, b0, acc[i][0]);
+        acc[i][1] = cfmac(ai, b1, acc[i][1]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        tot[i][j][0] = df_add_f(tot[i][j][0], acc[i][j].x);
+        tot[i][j][1] = df_add_f(tot[i][j][1], acc[i][j].y);
+        acc[i][j] = float2{0.f, 0.f};
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < RM; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int mm = m0 + ty + 16 * i, nn = n0 + tx + 16 * j;
+      if (mm < m && nn < n) {
+        atomicAdd(&c[(size_t)nn * ldc + mm].x, df_val(tot[i][j][0]));
+        atomicAdd(&c[(size_t)nn * ldc + mm].y, df_val(tot[i][j][1]));
+      }
+    }
+}
+
 // Both Gram matrices of Algorithm 1 from FP32 blocks in one pass: S = Z^H Z and A = Z^H HZ, block
 // lower triangles of 32 x 32 tiles.  The Z tile of the row block serves both products and each
 // thread reuses its two Z row values for four outputs of S and four of A; FP32 within a
@@ -268,10 +367,25 @@ int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, dou
                        16.0 * m * n,
           (lower ? 4.0 * m * (m + 1.0) : 8.0 * m * n) * (double)k);
   using A = typename std::conditional<Acc64, double2, typename AccOf<Va, Vb>::T>::type;
-  if (rm3)
+  if constexpr (std::is_same<A, float2>::value && std::is_same<Va, float2>::value &&
+                std::is_same<Vb, float2>::value) {
+    static bool attr = false;
+    if (!attr) {
+      DKS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_hn_f32p<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)hn32_smem<3>()));
+      DKS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_hn_f32p<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)hn32_smem<2>()));
+      attr = true;
+    }
+    if (rm3)
+      k_gemm_hn_f32p<3><<<grid, 256, hn32_smem<3>(), st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
+    else
+      k_gemm_hn_f32p<2><<<grid, 256, hn32_smem<2>(), st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
+  } else if (rm3) {
     k_gemm_hn<Va, Vb, A, 3><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
-  else
+  } else {
     k_gemm_hn<Va, Vb, A, 2><<<grid, 256, 0, st>>>(a, lda, b, ldb, k, m, n, mt, kchunk, c, ldc, lower ? 1 : 0);
+  }
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
