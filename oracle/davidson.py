@@ -66,11 +66,12 @@ def davidson_f(hop, q, x0, n, cshift, omega, n_init=3, n_iter=200, tol=1e-6, nco
         xm, hxm = v @ cm, hv @ cm
         rm = hxm - xm * lam[None, :]
         norms = np.linalg.norm(rm, axis=0)
-        history.append(dict(it=it, max_res=float(norms[:nconv].max()), m=v.shape[1], lam=lam.copy()))
+        act = np.nonzero(norms > tol)[0]
+        history.append(dict(it=it, max_res=float(norms[:nconv].max()), m=v.shape[1], lam=lam.copy(),
+                            nact=len(act)))
         if np.all(norms[:nconv] < tol):
             converged = True
             break
-        act = np.nonzero(norms > tol)[0]
         xb, rb = _blk(xm[:, act], npw, nc), _blk(rm[:, act], npw, nc)
         t = _cols(fh(teter_precondition(q, xb, rb) if precond == "teter" else rb.copy()))
         if v.shape[1] + t.shape[1] > m_max:
@@ -78,6 +79,7 @@ def davidson_f(hop, q, x0, n, cshift, omega, n_init=3, n_iter=200, tol=1e-6, nco
         for _ in range(2):
             t = t - v @ (v.conj().T @ t)
         t = orthonormal_basis(t)
+        history[-1]["added"] = t.shape[1]
         v = np.hstack([v, t])
         hv = np.hstack([hv, _cols(hop(_blk(t, npw, nc)))])
     used = (hop.count - start) if hasattr(hop, "count") else -1

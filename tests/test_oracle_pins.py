@@ -506,6 +506,20 @@ def test_davidson_f_matches_dense_definition():
         assert np.abs(r.lam[:nev] - lam_ref).max() < 1e-8
 
 
+def test_davidson_f_h_count():
+    """Like LOBPCG-F (Sec. 3.2), Davidson-F applies H' three times per new direction: twice in the
+    filter and once to extend HV; plus 2 n N_init for the initial filtering and n for HV0."""
+    wl, m, q = _setup("cubic")
+    hop = op.MatrixFreeH(wl, m, q)
+    cs, om = op.filter_constants(wl, q)
+    r = dv.davidson_f(hop, q, W.start_block(len(q), 8, wl.seed), 8, cs, om, tol=1e-6)
+    assert r.converged
+    filt = sum(2 * h["nact"] for h in r.history if "added" in h)
+    ext = sum(h["added"] for h in r.history if "added" in h)
+    assert r.h_applications == 2 * 8 * 3 + 8 + filt + ext
+    assert ext == sum(h["nact"] for h in r.history if "added" in h)   # no direction dropped here
+
+
 @pytest.mark.parametrize("c", [39.0, 137.036])
 def test_davidson_without_filter_collapses(c):
     """The filter protects Davidson as it protects LOBPCG (Sec. 3.1 mechanism): without it the
