@@ -291,6 +291,100 @@ int dks_rotate(const void* Z, int rows, int nz, const void* W, int ldw, int n, v
 int dks_residual_norms(const void* X, const void* HX, const double* lam, int rows, int n,
                        double* norms, int prec, void* stream);
 
+/* ------------------------------------------------ self-consistent field (Sec. 2.1, Sec. 4.1)
+ * The SCF loop around the eigensolver: density of the occupied states, Hartree and LDA
+ * exchange-correlation potential, Anderson mixing with the Kerker preconditioner.
+ * Grids are FP64 device arrays of Ng = N1 N2 N3 values f[(i1*N2 + i2)*N3 + i3] at
+ * r = sum_i (i_i/N_i) a_i, the layout of dks_potentials::v_r; the caller owns them.  Along an
+ * axis of length N, grid frequency index m stands for the signed integer m - N when 2m >= N
+ * (the Nyquist index counts as -N/2), and G = m1 b1 + m2 b2 + m3 b3. */
+
+/* dks_density: rho += sum_{j < nb} occ[j] psi_j(r)^dag psi_j(r) on the grid (Eq. density with
+ * the magnetisation term dropped), psi_j(r) = vol^-1/2 sum_G X[j][comp][G] exp(i (k+G).r),
+ * summed over the dks_ncomp(ctx) components.  X: device complex128 [nb][ncomp][npw] of k-point
+ * ik; occ: host double[nb]; rho: device double[Ng], accumulated (zero it first; call once per
+ * k-point with occ holding the k-point weights for a k-point sum).  FP64 transforms.  Uses
+ * ctx workspace (not reentrant per ctx).  Errors: INVALID_ARG, UNSUPPORTED (plane too large
+ * for shared memory), OOM, CUDA. */
+int dks_density(dks_ctx* ctx, int ik, const void* X, int nb, const double* occ, double* rho, void* stream);
+
+/* dks_hxc: vhxc = V_H + v_xc of the density rho (the Hartree-exchange-correlation potential of
+ * Sec. 2.1).  V_H(G) = 4 pi rho(G) / |G|^2 for G != 0 and V_H(0) = 0 (a neutralising uniform
+ * background), rho(G) the Fourier coefficients of rho on the grid; v_xc the spin-unpolarised
+ * LDA: Dirac exchange plus the Perdew-Zunger (1981) fit of the Ceperley-Alder correlation;
+ * grid points with rho <= 1e-30 get v_xc = 0.  rho, vhxc: device double[Ng], distinct.
+ * energies: host double[2] = {E_H = 1/2 int rho V_H, E_xc = int rho eps_xc}, or NULL; when
+ * given, the call synchronises `stream`.  Errors: INVALID_ARG, OOM, CUDA. */
+int dks_hxc(dks_ctx* ctx, const double* rho, double* vhxc, double* energies, void* stream);
+
+/* dks_set_potential: the context's local potential V(r) becomes v (device double[Ng], Ha) for
+ * every later dks_apply_H, dks_filter and solve; the default filter constants follow the new
+ * max|V| (dks_filter_constants).  The potential given at creation stays the context's
+ * external part for dks_scf.  Synchronous.  Errors: INVALID_ARG, OOM, CUDA. */
+int dks_set_potential(dks_ctx* ctx, const double* v, void* stream);
+
+/* Anderson mixer of densities with the Kerker preconditioner (Sec. 4.1).  One step, given the
+ * input density rho_in of the last potential and the output density rho_out of its solve:
+ *   F = rho_out - rho_in; with the stored differences dR_j, dF_j of the last `history` steps,
+ *   gamma = argmin_g |F - sum_j g_j dF_j|_2 (plain sum over grid points; directions whose
+ *   singular value is below 1e-6 of the largest are left out),
+ *   rho_next = rho_in - sum_j gamma_j dR_j + P (F - sum_j gamma_j dF_j),
+ *   P: each Fourier component times alpha |G|^2 / (|G|^2 + q0^2) (0 at G = 0),
+ * then (rho_in - previous rho_in, F - previous F) joins the history.  history = 0 gives
+ * Kerker-preconditioned linear mixing.  0 <= history <= 16, alpha > 0, q0 >= 0. */
+typedef struct dks_mixer dks_mixer;
+int dks_mixer_create(dks_ctx* ctx, int history, double alpha, double q0, dks_mixer** out);
+/* rho_in, rho_out, rho_next: device double[Ng]; rho_next may be rho_in, not rho_out.
+ * Synchronous (the small least-squares problem is solved on the host).  The mixer keeps its
+ * own device copies of the history.  Errors: INVALID_ARG, OOM, CUDA. */
+int dks_mix(dks_mixer* mixer, const double* rho_in, const double* rho_out, double* rho_next, void* stream);
+void dks_mixer_destroy(dks_mixer* mixer);
+
+typedef struct {
+  int nocc;            /* occupied states per k-point, one electron each (k-points weighted
+                          1/nk); nocc <= nev_k                                          */
+  int max_iter;        /* SCF iterations after the first solve (default 60)             */
+  double tol;          /* stop when int |rho_out - rho_in| dr < tol electrons (1e-8)    */
+  double alpha;        /* Kerker-Anderson mixing: alpha (0.5), q0 in 1/bohr (1.0),       */
+  double kerker_q0;    /*   history (8)                                                  */
+  int history;
+  int n_init_warm;     /* N_init of the solves after the first (warm start from the
+                          previous eigenvectors, default 1)                              */
+  double solve_tol;    /* residual tolerance of every eigensolve (1e-8)                  */
+  dks_solve_opts solve;/* options of the eigensolves (dks_solve_opts_default); its
+                          n_init is the first solve's                                    */
+} dks_scf_opts;
+
+typedef struct {
+  int iterations;            /* SCF iterations after the first solve                     */
+  int converged;
+  double residual;           /* int |rho_out - rho_in| dr of the last iteration           */
+  double e_h, e_xc;          /* Hartree and xc energies of the last input density (Ha)    */
+  long long solve_iterations;/* eigensolver iterations, all solves and k-points           */
+  long long h_applications;  /* single-band H' applications, all solves                   */
+  double seconds;            /* wall time of the call                                     */
+  int status;                /* DKS_OK or the first error                                 */
+  int hist_len;
+  double res_history[128];   /* residual after each SCF iteration                         */
+} dks_scf_report;
+
+void dks_scf_opts_default(dks_scf_opts* opts);
+
+/* dks_scf: the SCF loop.  The first solve uses the potential given at creation (V_loc);
+ * then, until the residual is below tol or max_iter is reached:
+ *   V = V_loc + V_hxc(rho_in) (dks_hxc), solve for nev_k pairs per k (warm start),
+ *   rho_out = density of the nocc lowest (dks_density), residual, rho_in = mix(rho_in, rho_out);
+ * the first rho_in is the density of the first solve.
+ *  eig   host double[sum_k nev_k]: the last solve's eigenvalues (shifted as dks_lobpcgf_solve)
+ *  X     as dks_lobpcgf_solve (start block in, last eigenvectors out)
+ *  rho   device double[Ng] for the last rho_out, or NULL
+ * On return the context's potential is the last V (dks_set_potential).  Synchronous.
+ * Returns NOT_CONVERGED when max_iter ends the loop (results of the last iteration are
+ * written), or the first error of a step; an eigensolve that ends NOT_CONVERGED does not stop
+ * the loop. */
+int dks_scf(dks_ctx* ctx, int nev, const dks_scf_opts* opts, double* eig, void* const* X, double* rho,
+            dks_scf_report* report);
+
 /* ------------------------------------------------ instrumentation (no counterpart in the paper;
  * the solve report's phase timers of a production code).  Every kernel launch of the library is
  * counted per category; while profiling is enabled each launch is also bracketed by a CUDA event

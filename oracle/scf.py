@@ -21,7 +21,9 @@ Readings (the paper names the ingredients only):
     maps to -N/2), and every potential is the real part of its inverse transform;
   * density below zero (possible after Anderson extrapolation) counts as zero in the LDA;
   * Anderson step with history dR_j = rho_in^(j+1) - rho_in^(j), dF_j = F^(j+1) - F^(j)
-    (F = rho_out - rho_in): gamma = argmin |F - dF gamma|_2 (plain sum over grid points),
+    (F = rho_out - rho_in): gamma = argmin |F - dF gamma|_2 (plain sum over grid points;
+    singular directions of dF below 1e-6 of the largest are left out, so that a history that
+    has become nearly dependent does not amplify rounding),
     rho_bar = rho_in - dR gamma, F_bar = F - dF gamma, rho_next = rho_bar + P F_bar,
     with P the Kerker factor alpha |G|^2 / (|G|^2 + q0^2) applied in reciprocal space;
   * the first density comes from the operator with V_loc alone (no Hartree, no xc).
@@ -157,7 +159,7 @@ class AndersonMixer:
         rbar, fbar = rho_in, f
         if self.df:
             dfm, drm = np.stack(self.df, axis=1), np.stack(self.dr, axis=1)
-            gam = np.linalg.lstsq(dfm, f.reshape(-1), rcond=None)[0]
+            gam = np.linalg.lstsq(dfm, f.reshape(-1), rcond=1e-6)[0]
             rbar = rho_in - (drm @ gam).reshape(rho_in.shape)
             fbar = f - (dfm @ gam).reshape(rho_in.shape)
         return rbar + self.pre(fbar)

@@ -64,12 +64,26 @@ class SolveReport(C.Structure):
                 ("res_history", C.c_double * 512)]
 
 
+class ScfOpts(C.Structure):
+    _fields_ = [("nocc", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double), ("alpha", C.c_double),
+                ("kerker_q0", C.c_double), ("history", C.c_int), ("n_init_warm", C.c_int),
+                ("solve_tol", C.c_double), ("solve", SolveOpts)]
+
+
+class ScfReport(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("residual", C.c_double), ("e_h", C.c_double),
+                ("e_xc", C.c_double), ("solve_iterations", C.c_longlong), ("h_applications", C.c_longlong),
+                ("seconds", C.c_double), ("status", C.c_int), ("hist_len", C.c_int),
+                ("res_history", C.c_double * 128)]
+
+
 EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dks_filter_constants",
            "dks_apply_H", "dks_filter", "dks_solve_opts_default", "dks_lobpcgf_solve", "dks_precond",
            "dks_gram", "dks_rayleigh_ritz", "dks_rotate", "dks_residual_norms", "dks_strerror",
            "dks_last_error", "dks_profile_ncat", "dks_profile_name", "dks_profile_enable", "dks_profile_read",
            "dks_rayleigh_ritz_static", "dks_gram_hermitian", "dks_kinetic_balance", "dks_create_model",
-           "dks_ncomp"]
+           "dks_ncomp", "dks_density", "dks_hxc", "dks_set_potential", "dks_mixer_create", "dks_mix",
+           "dks_mixer_destroy", "dks_scf_opts_default", "dks_scf"]
 
 _lib = None
 
@@ -106,6 +120,16 @@ def load_library(path: str = LIB_PATH):
     lib.dks_rayleigh_ritz_static.argtypes = [vp, vp, i, i, vp, vp, vp, vp]
     lib.dks_rotate.argtypes = [vp, i, i, vp, i, i, vp, d, i, vp]
     lib.dks_residual_norms.argtypes = [vp, vp, vp, i, i, vp, i, vp]
+    lib.dks_density.argtypes = [vp, i, vp, i, C.POINTER(d), vp, vp]
+    lib.dks_hxc.argtypes = [vp, vp, vp, C.POINTER(d), vp]
+    lib.dks_set_potential.argtypes = [vp, vp, vp]
+    lib.dks_mixer_create.argtypes = [vp, i, d, d, C.POINTER(vp)]
+    lib.dks_mix.argtypes = [vp, vp, vp, vp, vp]
+    lib.dks_mixer_destroy.argtypes = [vp]
+    lib.dks_mixer_destroy.restype = None
+    lib.dks_scf_opts_default.argtypes = [C.POINTER(ScfOpts)]
+    lib.dks_scf_opts_default.restype = None
+    lib.dks_scf.argtypes = [vp, i, C.POINTER(ScfOpts), C.POINTER(d), C.POINTER(vp), vp, C.POINTER(ScfReport)]
     lib.dks_strerror.argtypes = [i]
     lib.dks_strerror.restype = C.c_char_p
     lib.dks_last_error.argtypes = []
@@ -190,6 +214,7 @@ class Context:
         _check(lib.dks_ncomp(self._h, C.byref(nc)))
         self.ncomp = nc.value
         self.model = model
+        self.grid = tuple(int(x) for x in grid)
         self.nk = cell.nk
         self.c = float(c)
         self._keep = []
@@ -274,6 +299,74 @@ class Context:
                                 _dptr(y), precond, _prec_of(x), _stream(stream)))
         return y
 
+    # ---- SCF pieces (grids: float64 device tensors of shape grid, natural order)
+    def _grid(self, *ts):
+        import torch
+        for t in ts:
+            if t is None:
+                continue
+            if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != int(np.prod(self.grid)):
+                raise ValueError(f"grid arrays are contiguous float64 with {int(np.prod(self.grid))} values")
+
+    def density(self, ik, x, occ, rho, stream=None):
+        """dks_density: rho += sum_j occ[j] |psi_j(r)|^2 for the columns of x (complex128)."""
+        nb = self._block(ik, x, nb=len(occ))
+        if x.dtype != _complex128():
+            raise ValueError("density blocks are complex128")
+        self._grid(rho)
+        o = np.ascontiguousarray(occ, dtype=np.float64)
+        _check(_lib.dks_density(self._h, ik, _dptr(x), nb, o.ctypes.data_as(C.POINTER(C.c_double)), _dptr(rho),
+                                _stream(stream)))
+        return rho
+
+    def hxc(self, rho, vhxc, stream=None):
+        """dks_hxc: vhxc = V_H + v_xc of rho; returns (E_H, E_xc) (synchronises the stream)."""
+        self._grid(rho, vhxc)
+        e = (C.c_double * 2)()
+        _check(_lib.dks_hxc(self._h, _dptr(rho), _dptr(vhxc), e, _stream(stream)))
+        return e[0], e[1]
+
+    def set_potential(self, v, stream=None):
+        """dks_set_potential: V(r) of the operator becomes v (synchronous)."""
+        self._grid(v)
+        _check(_lib.dks_set_potential(self._h, _dptr(v), _stream(stream)))
+
+    def mixer(self, history=8, alpha=0.5, q0=1.0):
+        return Mixer(self, history, alpha, q0)
+
+    def scf(self, x_list, nev, nocc, tol=1e-8, max_iter=60, alpha=0.5, q0=1.0, history=8, n_init_warm=1,
+            solve_tol=1e-8, rho=None, n_init=3, mode=MODE_FP64, nbuf=0, n_iter=200, precond=PRECOND_TETER,
+            stream=None, check=True):
+        """dks_scf: the SCF loop (solve, density, V_hxc, Kerker-Anderson mixing) from the potential
+        given at creation.  Returns (eigenvalues per k, report dict, status code)."""
+        o = ScfOpts()
+        _lib.dks_scf_opts_default(C.byref(o))
+        o.nocc, o.max_iter, o.tol, o.alpha, o.kerker_q0 = int(nocc), int(max_iter), float(tol), float(alpha), float(q0)
+        o.history, o.n_init_warm, o.solve_tol = int(history), int(n_init_warm), float(solve_tol)
+        o.solve.n_init, o.solve.n_iter, o.solve.nbuf = int(n_init), int(n_iter), int(nbuf)
+        o.solve.mode, o.solve.precond = int(mode), int(precond)
+        o.solve.stream = _stream(stream)
+        if len(x_list) != self.nk:
+            raise ValueError(f"need one block per k-point ({self.nk})")
+        for ik, t in enumerate(x_list):
+            self._block(ik, t, nb=int(nev) + int(nbuf))
+            if t.dtype != _complex128():
+                raise ValueError("SCF blocks are complex128")
+        self._grid(rho)
+        eig = np.zeros(int(nev) * self.nk, dtype=np.float64)
+        ptrs = (C.c_void_p * self.nk)(*[t.data_ptr() for t in x_list])
+        rep = ScfReport()
+        rc = _lib.dks_scf(self._h, int(nev), C.byref(o), eig.ctypes.data_as(C.POINTER(C.c_double)), ptrs,
+                          _dptr(rho), C.byref(rep))
+        if check and rc != 0:
+            _check(rc)
+        report = dict(iterations=rep.iterations, converged=bool(rep.converged), residual=rep.residual,
+                      e_h=rep.e_h, e_xc=rep.e_xc, solve_iterations=int(rep.solve_iterations),
+                      h_applications=int(rep.h_applications), seconds=rep.seconds, status=rep.status,
+                      history=list(rep.res_history[:rep.hist_len]),
+                      message=_lib.dks_last_error().decode() if rc else "")
+        return [eig[i * nev:(i + 1) * nev].copy() for i in range(self.nk)], report, rc
+
     # ---- solver
     def solve(self, x_list, nev, tol=1e-6, n_init=3, n_iter=200, mode=MODE_FP64, refine_tol=1e-5,
               precond=PRECOND_TETER, use_filter=True, cshift=None, omega=None, nev_k=None, nbuf=0,
@@ -329,6 +422,31 @@ class Context:
                       history=list(rep.res_history[:rep.hist_len]),
                       message=_lib.dks_last_error().decode() if rc else "")
         return out, report, rc
+
+
+class Mixer:
+    """dks_mixer: Anderson mixing of densities with the Kerker preconditioner (device history)."""
+
+    def __init__(self, ctx, history=8, alpha=0.5, q0=1.0):
+        self._ctx = ctx
+        self._h = C.c_void_p()
+        _check(_lib.dks_mixer_create(ctx._h, int(history), float(alpha), float(q0), C.byref(self._h)))
+
+    def step(self, rho_in, rho_out, rho_next, stream=None):
+        self._ctx._grid(rho_in, rho_out, rho_next)
+        _check(_lib.dks_mix(self._h, _dptr(rho_in), _dptr(rho_out), _dptr(rho_next), _stream(stream)))
+        return rho_next
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dks_mixer_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def profile_enable(on=True):

@@ -279,6 +279,8 @@ static void free_ctx(dks_ctx* ctx) {
   cudaFree(ctx->vperm64);
   cudaFree(ctx->vperm32);
   cudaFree(ctx->vpermdf);
+  cudaFree(ctx->vloc_dev);
+  for (int a = 0; a < 3; ++a) cudaFree(ctx->posd[a]);
   cudaFree(ctx->dvec_dev);
   for (KPoint& kp : ctx->k) {
     cudaFree(kp.stick_start);
@@ -393,9 +395,15 @@ int dks_create(const dks_cell* cell, double ecut, const dks_potentials* pot, con
     if ((rc = upload(&ctx->tw32[a], tw32.data(), n))) return bail(rc);
     if ((rc = upload(&ctx->twdf[a], twd.data(), n))) return bail(rc);
   }
+  // DIF positions of the natural grid indices (density and potential updates on the device)
+  for (int a = 0; a < 3; ++a) {
+    const std::vector<int> pa = dif_positions(ctx->plan[a]);
+    if ((rc = upload(&ctx->posd[a], pa.data(), pa.size()))) return bail(rc);
+  }
   // potential in DIF order, scaled by 1/Ng
   ctx->has_v = pot && pot->v_r;
   if (ctx->has_v) {
+    if ((rc = upload(&ctx->vloc_dev, pot->v_r, (size_t)ctx->ng))) return bail(rc);
     const int n1 = ctx->grid[0], n2 = ctx->grid[1], n3 = ctx->grid[2];
     const std::vector<int> p1 = dif_positions(ctx->plan[0]), p2 = dif_positions(ctx->plan[1]),
                            p3 = dif_positions(ctx->plan[2]);

@@ -103,6 +103,8 @@ struct dks_ctx {
   float2* vpermdf = nullptr;    // double-float (hi, lo) copy
   double vmax = 0;
   bool has_v = false;
+  int* posd[3] = {nullptr, nullptr, nullptr};   // device: DIF position of natural index i per axis
+  double* vloc_dev = nullptr;   // device: the potential given at creation, natural grid order (or NULL)
   // projectors
   int nproj = 0;
   double dsum = 0;
@@ -123,7 +125,7 @@ namespace dks {
 // ---------------------------------------------------------------- profiling
 enum ProfCat {
   P_STICK_INV, P_PLANE, P_STICK_FWD, P_DIRAC, P_PROJ_HN, P_PROJ_NN, P_GRAM, P_ROTATE, P_RR, P_STATS,
-  P_PRECOND, P_MISC,
+  P_PRECOND, P_MISC, P_SCF,
   // the same kernels launched on complex64 data (FP32 arithmetic)
   P_STICK_INV32, P_PLANE32, P_STICK_FWD32, P_DIRAC32, P_PROJ_HN32, P_PROJ_NN32, P_GRAM32, P_ROTATE32,
   P_NCAT
@@ -164,6 +166,9 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
 Exec& exec0(dks_ctx* ctx);
 // small two-spinors of nb columns from their large ones, Eq. (RKB); x complex128 (fp64) or complex64
 int kinetic_balance(dks_ctx* ctx, int ik, void* x, int nb, bool fp64, cudaStream_t st);
+// rho (natural grid order) += sum_j occ[j] |psi_j(r)|^2 / vol over the columns of x (complex128)
+int density_accumulate(dks_ctx* ctx, int ik, const double2* x, int nb, const double* occ, double* rho,
+                       cudaStream_t st);
 
 // kernels shared by the solver and the single-step entry points
 template <typename Va, typename Vb = Va, bool Acc64 = false>

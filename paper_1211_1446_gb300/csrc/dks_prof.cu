@@ -24,6 +24,7 @@ const char* g_names[P_NCAT] = {"stick_inverse_fft",      "plane_fft_v",        "
                                "dirac_only",             "proj_bh_x",          "proj_b_dz",
                                "gram",                   "rotate",             "rayleigh_ritz",
                                "col_stats",              "precond_teter",      "convert_gather",
+                               "scf_grid",
                                "stick_inverse_fft_fp32", "plane_fft_v_fp32",   "stick_forward_fft_dirac_fp32",
                                "dirac_only_fp32",        "proj_bh_x_fp32",     "proj_b_dz_fp32",
                                "gram_fp32",              "rotate_fp32"};

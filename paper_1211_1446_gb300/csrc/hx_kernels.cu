@@ -98,6 +98,58 @@ __global__ void __launch_bounds__(512) k_plane(Vg* __restrict__ t, int nsticks,
 }
 
 // ---------------------------------------------------------------------------
+// electron density (Eq. density): pass A as above, then per plane the inverse 2D FFT of
+// every field and the weighted sum of |psi|^2 over the fields, FP64 throughout.  The sum
+// stays in shared memory across the fields a CTA owns; the planes are in the DIF-permuted
+// order of the potential ([p3][p1*LD + p2]).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_plane_density(const double2* __restrict__ t, int nsticks,
+                                                       const int* __restrict__ stick_plane, AxisPlan p1,
+                                                       AxisPlan p2, int ld, int n3, const double2* __restrict__ tw1,
+                                                       const double2* __restrict__ tw2,
+                                                       const double* __restrict__ wfield, int nf, int fper,
+                                                       double* __restrict__ rho_perm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n1 = p1.n, n2 = p2.n, np = n1 * ld;
+  double2* plane = reinterpret_cast<double2*>(smem_raw);
+  double* acc = reinterpret_cast<double*>(plane + np);
+  const int z = blockIdx.x;
+  const int f0 = blockIdx.y * fper, f1 = min(nf, f0 + fper);
+  for (int e = threadIdx.x; e < np; e += blockDim.x) acc[e] = 0.0;
+  for (int f = f0; f < f1; ++f) {
+    for (int e = threadIdx.x; e < np; e += blockDim.x) plane[e] = double2{0.0, 0.0};
+    __syncthreads();
+    const double2* row = t + ((size_t)f * n3 + z) * nsticks;
+    for (int s = threadIdx.x; s < nsticks; s += blockDim.x) plane[stick_plane[s]] = row[s];
+    __syncthreads();
+    fft_lines<double2, false, false>(plane, n1, ld, 1, p2, tw2);
+    fft_lines<double2, false, false>(plane, n2, 1, ld, p1, tw1);
+    const double w = wfield[f];
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+      const double2 v = plane[e];
+      acc[e] = fma(w, fma(v.x, v.x, v.y * v.y), acc[e]);
+    }
+    __syncthreads();
+  }
+  double* out = rho_perm + (size_t)z * np;
+  for (int e = threadIdx.x; e < np; e += blockDim.x)
+    if (acc[e] != 0.0) atomicAdd(out + e, acc[e]);
+}
+
+// rho[(i1 N2 + i2) N3 + i3] += scale * rho_perm[(p3[i3] N1 + p1[i1]) LD + p2[i2]]
+__global__ void k_unpermute_add(const double* __restrict__ rho_perm, double* __restrict__ rho, int n1, int n2,
+                                int n3, int ld, const int* __restrict__ p1, const int* __restrict__ p2,
+                                const int* __restrict__ p3, double scale) {
+  const size_t ng = (size_t)n1 * n2 * n3;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < ng; n += (size_t)gridDim.x * blockDim.x) {
+    const int i3 = (int)(n % n3);
+    const size_t r = n / n3;
+    const int i2 = (int)(r % n2), i1 = (int)(r / n2);
+    rho[n] += scale * rho_perm[((size_t)p3[i3] * n1 + p1[i1]) * ld + p2[i2]];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // pass C: forward FFT along axis 3, gather, Dirac term (FP64), shift, scale
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void dirac4(const double2 xv[4], double qx, double qy, double qz, double c,
@@ -479,6 +531,74 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
       DKS_TRY(gemm_nn<V>(bt, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, ncol, out, 2 * npw,
                          1.0, st, scale, P_PROJ_NN));
   }
+  return DKS_OK;
+}
+
+int density_accumulate(dks_ctx* ctx, int ik, const double2* x, int nb, const double* occ, double* rho,
+                       cudaStream_t st) {
+  if (nb <= 0) return DKS_OK;
+  KPoint& kp = ctx->k[ik];
+  Exec& ex = exec0(ctx);
+  const int npw = kp.npw, nc = ctx->ncomp;
+  const int n1 = ctx->grid[0], n2 = ctx->grid[1], n3 = ctx->grid[2], ld = ctx->plane_ld;
+  const size_t field_elems = (size_t)kp.nsticks * n3;
+  const size_t np = (size_t)n1 * ld;
+  const size_t sm_b = np * (sizeof(double2) + sizeof(double));
+  if (sm_b > 227 * 1024) return fail(DKS_ERR_UNSUPPORTED, "density: N1*N2 plane exceeds the shared-memory limit");
+  int chunk = (int)std::max<size_t>(1, ctx->chunk_budget / (nc * field_elems * sizeof(double2)));
+  chunk = std::min(chunk, nb);
+  const size_t perm_bytes = ((n3 * np * sizeof(double) + 255) / 256) * 256;
+  const size_t w_bytes = ((nc * (size_t)nb * sizeof(double) + 255) / 256) * 256;
+  DKS_TRY(grow(ex.ws_h, perm_bytes + w_bytes + nc * (size_t)chunk * field_elems * sizeof(double2)));
+  double* rho_perm = reinterpret_cast<double*>(ex.ws_h.ptr);
+  double* wf = reinterpret_cast<double*>(reinterpret_cast<char*>(ex.ws_h.ptr) + perm_bytes);
+  double2* tbuf = reinterpret_cast<double2*>(reinterpret_cast<char*>(ex.ws_h.ptr) + perm_bytes + w_bytes);
+  std::vector<double> wh((size_t)nc * nb);
+  for (int b = 0; b < nb; ++b)
+    for (int c = 0; c < nc; ++c) wh[(size_t)b * nc + c] = occ[b];
+  DKS_CUDA_TRY(cudaMemcpyAsync(wf, wh.data(), wh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  DKS_CUDA_TRY(cudaMemsetAsync(rho_perm, 0, n3 * np * sizeof(double), st));
+  const int ls = n3 | 1;
+  const int spb_a = pick_spb(ls, sizeof(double2), 1, 32 * 1024);
+  const size_t sm_a = (size_t)spb_a * ls * sizeof(double2);
+  DKS_TRY(set_smem<double2>((const void*)k_stick_inverse<double2, double2>, sm_a));
+  DKS_TRY(set_smem<double2>((const void*)k_plane_density, sm_b));
+  int rmin = 8;
+  for (int a = 0; a < 2; ++a)
+    for (int i = 0; i < ctx->plan[a].nst; ++i) rmin = std::min(rmin, ctx->plan[a].radix[i]);
+  const int nbf = n1 * n2 / rmin;
+  const int tb_plane = std::min(512, std::max(128, (nbf / 2 + 31) / 32 * 32));
+  for (int b0 = 0; b0 < nb; b0 += chunk) {
+    const int nbc = std::min(chunk, nb - b0);
+    const int nf = nc * nbc;
+    const double es = sizeof(double2), tb = (double)nf * field_elems * es;
+    {
+      Prof pr(P_STICK_INV, st, (double)nf * npw * es + tb, 5.0 * n3 * std::log2((double)n3) * kp.nsticks * nf);
+      dim3 ga((kp.nsticks + spb_a - 1) / spb_a, nf);
+      k_stick_inverse<double2, double2><<<ga, 256, sm_a, st>>>(x + (size_t)b0 * nc * npw, tbuf, npw, kp.nsticks,
+                                                               kp.stick_start, kp.pw_stick, kp.pw_iz, ctx->plan[2],
+                                                               ctx->tw64[2], spb_a, ls);
+    }
+    {
+      // split the fields of a plane over enough CTAs to fill the GPU twice; atomics combine them
+      const int nsplit = std::max(1, std::min(nf, (2 * ctx->num_sms + n3 - 1) / n3));
+      const int fper = (nf + nsplit - 1) / nsplit;
+      const double nn = (double)n1 * n2;
+      Prof pr(P_SCF, st, tb + 2.0 * n3 * np * sizeof(double), nf * n3 * (5.0 * nn * std::log2(nn) + 3.0 * nn));
+      dim3 gb(n3, (nf + fper - 1) / fper);
+      k_plane_density<<<gb, tb_plane, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0], ctx->plan[1], ld,
+                                                  n3, ctx->tw64[0], ctx->tw64[1], wf + (size_t)b0 * nc, nf, fper,
+                                                  rho_perm);
+    }
+  }
+  {
+    const size_t ng = (size_t)ctx->ng;
+    Prof pr(P_SCF, st, 3.0 * ng * sizeof(double), 2.0 * ng);
+    const int blocks = (int)std::min<size_t>((ng + 255) / 256, (size_t)ctx->num_sms * 8);
+    k_unpermute_add<<<blocks, 256, 0, st>>>(rho_perm, rho, n1, n2, n3, ld, ctx->posd[0], ctx->posd[1], ctx->posd[2],
+                                            1.0 / ctx->volume);
+  }
+  DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
 
