@@ -351,6 +351,60 @@ def davidson_section(P, ctx, x0, lam_dks, ms_dks, mode, stream, m_max=160):
     return out
 
 
+def scf_section(P, W, wl, ctx, mode, stream, nocc=20, tol=1e-4, solve_tol=1e-7, max_iter=40):
+    """The SCF loop around the solver (Sec. 2.1 density and V_hxc, Sec. 4.1 Kerker-Anderson
+    mixing) on the dimer: nocc = 20 occupied states (the first 20 eigenpairs are separated from
+    the rest by 1.3 Ha), the workload's 32 + 8 columns per solve, warm starts with N_init = 1.
+    One timed run from the seeded start block; then the grid steps of one SCF iteration
+    (density of nocc states, V_hxc, mixing, potential update) timed on their own."""
+    import numpy as np
+    import torch
+    x = torch.from_numpy(W.start_block(ctx.npw(0), NEV + NBUF, wl.seed)).cuda()
+    rho = torch.zeros(wl.grid, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lam, rep, rc = ctx.scf([x], NEV, nocc, tol=tol, solve_tol=solve_tol, max_iter=max_iter, nbuf=NBUF, mode=mode,
+                           rho=rho, check=False, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    total = e0.elapsed_time(e1)
+    its = rep["iterations"]
+    out = {"status": int(rc), "converged": rep["converged"], "nocc": nocc, "scf_iterations": its,
+           "tol_electrons": tol, "solve_tol": solve_tol, "residual": rep["residual"], "ms_total": total,
+           "ms_per_solve_and_update": total / (its + 1), "solve_iterations": rep["solve_iterations"],
+           "h_applications": rep["h_applications"], "e_h": rep["e_h"], "e_xc": rep["e_xc"],
+           "electrons": float(rho.sum().item() * wl.volume / wl.ng),
+           "residual_history": [float("%.3e" % r) for r in rep["history"]]}
+    if rc == 0:
+        out["eig_lowest"] = [float(v) for v in lam[0][:4]]
+    # grid steps of one SCF iteration, each timed alone (3 repetitions after one warm-up)
+    occ = [1.0] * nocc
+    rout = torch.zeros_like(rho)
+    vh = torch.empty_like(rho)
+    mx = ctx.mixer()
+    steps = {"density": lambda: ctx.density(0, x, occ, rout, stream=stream),
+             "hxc": lambda: ctx.hxc(rho, vh, stream=stream),
+             "mix": lambda: mx.step(rho, rout, vh, stream=stream),
+             "set_potential": lambda: ctx.set_potential(vh, stream=stream)}
+    grid = {}
+    for name, fn in steps.items():
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        grid[name] = e0.elapsed_time(e1) / 3
+    mx.close()
+    out["grid_steps_ms"] = grid
+    out["grid_share"] = sum(grid.values()) / out["ms_per_solve_and_update"]
+    # restore the creation potential for whatever runs after
+    ctx.set_potential(torch.from_numpy(np.ascontiguousarray(wl.v_r)).cuda())
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,6 +417,7 @@ def main():
     ap.add_argument("--no-warm-start", action="store_true")
     ap.add_argument("--no-ksso", action="store_true")
     ap.add_argument("--no-davidson", action="store_true")
+    ap.add_argument("--no-scf", action="store_true")
     ap.add_argument("--ref-iterations", type=int, default=60)
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--kernel-case", default=None,
@@ -523,6 +578,7 @@ def main():
     warm = None if args.no_warm_start else warm_start(P, W, wl, ctx, x, x0, mode, stream)
     ksso = None if args.no_ksso else ksso_section(P, W, wl, ctx, x0, lam, ms, mode, stream)
     dav = None if args.no_davidson else davidson_section(P, ctx, x0, lam, ms, mode, stream)
+    scf = None if args.no_scf else scf_section(P, W, wl, ctx, mode, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -538,7 +594,7 @@ def main():
                     "h2d_bytes_per_step": bytes_vec, "d2h_bytes_per_step": bytes_vec + 8 * NEV},
             "gpu_launches": launches, "clocks": clk, "roofline": roof,
             "cpu_baseline": cpu, "fp64_form": fp64, "warm_start": warm, "ksso": ksso, "davidson_f": dav,
-            "accuracy": acc}
+            "scf": scf, "accuracy": acc}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

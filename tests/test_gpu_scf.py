@@ -139,3 +139,26 @@ def test_scf_matches_oracle(name, kw, nocc, nev, model):
     eh0, exc0 = ref.history[-1]["eh"], ref.history[-1]["exc"]
     assert abs(rep["e_h"] - eh0) < 1e-6 and abs(rep["e_xc"] - exc0) < 1e-6
     assert rep["iterations"] >= 2
+
+
+def test_scf_dimer_first_iterations():
+    """The bench workload at full size: three SCF iterations in mixed precision; the density
+    holds nocc electrons, the residual falls, the eigenvalues of the final potential are those
+    of a plain solve with the same potential."""
+    torch = gpu()
+    import paper_1211_1446_gb300 as P
+    wl = W.make("dimer")
+    ctx = P.Context.from_workload(wl)
+    nev, nbuf, nocc = 32, 8, 20
+    x = torch.from_numpy(W.start_block(ctx.npw(0), nev + nbuf, wl.seed)).cuda()
+    rho = torch.zeros(wl.grid, dtype=torch.float64, device="cuda")
+    lam, rep, rc = ctx.scf([x], nev, nocc, tol=1e-12, solve_tol=1e-7, max_iter=3, nbuf=nbuf, rho=rho,
+                           mode=P.MODE_MIXED, check=False)
+    assert rc == -4 and rep["iterations"] == 3 and not rep["converged"], rep   # NOT_CONVERGED by design
+    h = rep["history"]
+    assert len(h) == 3 and h[2] < h[0], h
+    assert abs(rho.sum().item() * wl.volume / wl.ng - nocc) < 1e-6
+    # the context now holds the last potential: a fresh solve of it reproduces the eigenvalues
+    x2 = torch.from_numpy(W.start_block(ctx.npw(0), nev + nbuf, wl.seed + 1)).cuda()
+    lam2, rep2, rc2 = ctx.solve([x2], nev, tol=1e-7, nbuf=nbuf, mode=P.MODE_MIXED)
+    assert rc2 == 0 and np.abs(lam2[0] - lam[0]).max() < 1e-8, rep2["message"]
