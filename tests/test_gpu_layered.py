@@ -68,8 +68,9 @@ def test_layered_solve_all_kpoints(layered):
         assert np.abs(lam[ik][0::2] - lam[ik][1::2]).max() < 1e-7, ik
     # orthonormal columns (all nev + nbuf of them) at two k-points.  X = Z V with V orthonormal
     # in the metric S = Z^H Z of the last Rayleigh-Ritz step, so X^H X - I is the rounding of that
-    # FP64 step times the conditioning of S, which grows as the directions of P converge; the
-    # unchecked buffer columns showed up to 6.5e-10 on a GB300, the bound leaves a factor 15
+    # FP64 step times the conditioning of S, which grows as the directions of P converge; on a
+    # GB300 the largest entry was 6.5e-10 (k = 13, among the buffer columns), the bound leaves a
+    # factor 15
     for ik in (0, 13):
         x = xs[ik].reshape(xs[ik].shape[0], -1)
         g = (x.conj() @ x.T).cpu().numpy()
