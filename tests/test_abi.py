@@ -33,3 +33,28 @@ def test_strerror_without_gpu():
     lib = P.load_library()
     assert lib.dks_strerror(-8).decode().startswith("planewave sphere")
     assert lib.dks_strerror(0).decode() == "ok"
+
+
+def test_scf_entry_points_validate_arguments_without_gpu():
+    """The SCF entry points reject bad arguments before touching the device: every call below
+    returns DKS_ERR_INVALID_ARG and leaves a message; the option defaults are host-only."""
+    import ctypes as C
+    import paper_1211_1446_gb300 as P
+    lib = P.load_library()
+    bad = -1
+    out = C.c_void_p()
+    assert lib.dks_mixer_create(None, 8, 0.5, 1.0, C.byref(out)) == bad and not out.value
+    assert lib.dks_mixer_create(None, 8, 0.5, 1.0, None) == bad
+    assert lib.dks_density(None, 0, None, 1, None, None, None) == bad
+    assert lib.dks_hxc(None, None, None, None, None) == bad
+    assert lib.dks_set_potential(None, None, None) == bad
+    assert lib.dks_mix(None, None, None, None, None) == bad
+    assert "dks_mix" in lib.dks_last_error().decode()
+    o = P.ScfOpts()
+    lib.dks_scf_opts_default(C.byref(o))
+    assert (o.nocc, o.max_iter, o.history, o.n_init_warm) == (0, 60, 8, 1)
+    assert (o.tol, o.alpha, o.kerker_q0, o.solve_tol) == (1e-8, 0.5, 1.0, 1e-8)
+    assert o.solve.n_init == 3 and o.solve.n_iter == 200          # the solver's own defaults
+    eig = (C.c_double * 4)()
+    assert lib.dks_scf(None, 4, C.byref(o), eig, None, None, None) == bad
+    lib.dks_mixer_destroy(None)                                    # no-op on NULL
