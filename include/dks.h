@@ -323,6 +323,17 @@ int dks_hxc(dks_ctx* ctx, const double* rho, double* vhxc, double* energies, voi
  * external part for dks_scf.  Synchronous.  Errors: INVALID_ARG, OOM, CUDA. */
 int dks_set_potential(dks_ctx* ctx, const double* v, void* stream);
 
+/* dks_update_potential: the SCF step V = V_loc + V_hxc(rho) in one call: dks_hxc of rho (device
+ * double[Ng]) plus the potential given at creation (V_loc; zero if none), made the context's
+ * potential as by dks_set_potential.  rho = NULL sets V = V_loc (the SCF's first potential).
+ * energies: host double[2] = {E_H, E_xc} of rho (zeros for rho = NULL), or NULL.  Synchronous.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int dks_update_potential(dks_ctx* ctx, const double* rho, double* energies, void* stream);
+
+/* dks_density_residual: *out = int |a - b| dr = (vol / Ng) sum_n |a_n - b_n| for two device
+ * grids (the SCF convergence measure, in electrons).  Synchronous.  Errors: INVALID_ARG, CUDA. */
+int dks_density_residual(dks_ctx* ctx, const double* a, const double* b, double* out, void* stream);
+
 /* Anderson mixer of densities with the Kerker preconditioner (Sec. 4.1).  One step, given the
  * input density rho_in of the last potential and the output density rho_out of its solve:
  *   F = rho_out - rho_in; with the stored differences dR_j, dF_j of the last `history` steps,

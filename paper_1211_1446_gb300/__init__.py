@@ -83,7 +83,8 @@ EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dk
            "dks_last_error", "dks_profile_ncat", "dks_profile_name", "dks_profile_enable", "dks_profile_read",
            "dks_rayleigh_ritz_static", "dks_gram_hermitian", "dks_kinetic_balance", "dks_create_model",
            "dks_ncomp", "dks_density", "dks_hxc", "dks_set_potential", "dks_mixer_create", "dks_mix",
-           "dks_mixer_destroy", "dks_scf_opts_default", "dks_scf"]
+           "dks_mixer_destroy", "dks_scf_opts_default", "dks_scf", "dks_update_potential",
+           "dks_density_residual"]
 
 _lib = None
 
@@ -123,6 +124,8 @@ def load_library(path: str = LIB_PATH):
     lib.dks_density.argtypes = [vp, i, vp, i, C.POINTER(d), vp, vp]
     lib.dks_hxc.argtypes = [vp, vp, vp, C.POINTER(d), vp]
     lib.dks_set_potential.argtypes = [vp, vp, vp]
+    lib.dks_update_potential.argtypes = [vp, vp, C.POINTER(d), vp]
+    lib.dks_density_residual.argtypes = [vp, vp, vp, C.POINTER(d), vp]
     lib.dks_mixer_create.argtypes = [vp, i, d, d, C.POINTER(vp)]
     lib.dks_mix.argtypes = [vp, vp, vp, vp, vp]
     lib.dks_mixer_destroy.argtypes = [vp]
@@ -330,6 +333,21 @@ class Context:
         """dks_set_potential: V(r) of the operator becomes v (synchronous)."""
         self._grid(v)
         _check(_lib.dks_set_potential(self._h, _dptr(v), _stream(stream)))
+
+    def update_potential(self, rho=None, stream=None):
+        """dks_update_potential: V = V_loc + V_hxc(rho) (V_loc alone for rho None); returns
+        (E_H, E_xc) of rho (synchronous)."""
+        self._grid(rho)
+        e = (C.c_double * 2)()
+        _check(_lib.dks_update_potential(self._h, _dptr(rho), e, _stream(stream)))
+        return e[0], e[1]
+
+    def density_residual(self, a, b, stream=None):
+        """dks_density_residual: int |a - b| dr over the grid (synchronous)."""
+        self._grid(a, b)
+        out = C.c_double()
+        _check(_lib.dks_density_residual(self._h, _dptr(a), _dptr(b), C.byref(out), _stream(stream)))
+        return out.value
 
     def mixer(self, history=8, alpha=0.5, q0=1.0):
         return Mixer(self, history, alpha, q0)

@@ -568,6 +568,68 @@ int dks_set_potential(dks_ctx* ctx, const double* v, void* stream) {
   return set_potential(ctx, v, (cudaStream_t)stream);
 }
 
+int dks_update_potential(dks_ctx* ctx, const double* rho, double* energies, void* stream) {
+  if (!ctx) return fail(DKS_ERR_INVALID_ARG, "dks_update_potential: ctx is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ng = (size_t)ctx->ng;
+  void* tmp = nullptr;
+  DKS_CUDA_TRY(cudaMallocAsync(&tmp, ng * (sizeof(double2) + sizeof(double)) + 2 * sizeof(double), st));
+  double2* cg = (double2*)tmp;
+  double* v = (double*)(cg + ng);
+  double* esum = v + ng;
+  auto body = [&]() -> int {
+    if (rho) {
+      DKS_TRY(hxc_potential(ctx, rho, v, cg, esum, st));
+      if (ctx->vloc_dev) {
+        Prof pr(P_SCF, st, 24.0 * ng, (double)ng);
+        k_axpy_grid<<<grid_blocks(ctx, ng), 256, 0, st>>>(ctx->vloc_dev, v, v, ng);
+        DKS_CUDA_TRY(cudaGetLastError());
+      }
+    } else if (ctx->vloc_dev) {
+      DKS_CUDA_TRY(cudaMemcpyAsync(v, ctx->vloc_dev, ng * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      DKS_CUDA_TRY(cudaMemsetAsync(v, 0, ng * sizeof(double), st));
+    }
+    DKS_TRY(set_potential(ctx, v, st));   // synchronises st
+    if (energies) {
+      energies[0] = energies[1] = 0.0;
+      if (rho) {
+        double e[2];
+        DKS_CUDA_TRY(cudaMemcpyAsync(e, esum, sizeof(e), cudaMemcpyDeviceToHost, st));
+        DKS_CUDA_TRY(cudaStreamSynchronize(st));
+        const double dv = ctx->volume / (double)ng;
+        energies[0] = 0.5 * dv * e[0];
+        energies[1] = dv * e[1];
+      }
+    }
+    return DKS_OK;
+  };
+  const int rc = body();
+  cudaFreeAsync(tmp, st);
+  return rc;
+}
+
+int dks_density_residual(dks_ctx* ctx, const double* a, const double* b, double* out, void* stream) {
+  if (!ctx || !a || !b || !out) return fail(DKS_ERR_INVALID_ARG, "dks_density_residual: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ng = (size_t)ctx->ng;
+  double* sum = nullptr;
+  DKS_CUDA_TRY(cudaMallocAsync((void**)&sum, sizeof(double), st));
+  double h = 0.0;
+  cudaError_t e = cudaMemsetAsync(sum, 0, sizeof(double), st);
+  if (e == cudaSuccess) {
+    Prof pr(P_SCF, st, 16.0 * ng, 2.0 * ng);
+    k_absdiff_sum<<<grid_blocks(ctx, ng), 256, 0, st>>>(a, b, sum, ng);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sum, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(sum, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(DKS_ERR_CUDA, std::string("dks_density_residual: ") + cudaGetErrorString(e));
+  *out = h * ctx->volume / (double)ng;
+  return DKS_OK;
+}
+
 void dks_scf_opts_default(dks_scf_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));

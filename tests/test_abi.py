@@ -58,3 +58,6 @@ def test_scf_entry_points_validate_arguments_without_gpu():
     eig = (C.c_double * 4)()
     assert lib.dks_scf(None, 4, C.byref(o), eig, None, None, None) == bad
     lib.dks_mixer_destroy(None)                                    # no-op on NULL
+    assert lib.dks_update_potential(None, None, None, None) == bad
+    res = C.c_double(-1.0)
+    assert lib.dks_density_residual(None, None, None, C.byref(res), None) == bad and res.value == -1.0

@@ -162,3 +162,31 @@ def test_scf_dimer_first_iterations():
     x2 = torch.from_numpy(W.start_block(ctx.npw(0), nev + nbuf, wl.seed + 1)).cuda()
     lam2, rep2, rc2 = ctx.solve([x2], nev, tol=1e-7, nbuf=nbuf, mode=P.MODE_MIXED)
     assert rc2 == 0 and np.abs(lam2[0] - lam[0]).max() < 1e-8, rep2["message"]
+
+
+def test_scf_step_entry_points_reproduce_the_library_loop():
+    """shard.scf_sharded driven by shard.ContextSCF on one rank (dks_update_potential, the solve,
+    dks_density, dks_density_residual, dks_mix) runs the same loop as dks_scf."""
+    torch = gpu()
+    import paper_1211_1446_gb300 as P
+    from paper_1211_1446_gb300 import shard
+    wl = W.make("small", ecut=4.0)
+    nev, nocc, nbuf = 6, 4, 2
+    out = []
+    for way in ("library", "steps"):
+        ctx = P.Context.from_workload(wl)
+        x = torch.from_numpy(W.start_block(ctx.npw(0), nev + nbuf, wl.seed)).cuda()
+        if way == "library":
+            lam, rep, rc = ctx.scf([x], nev, nocc, tol=1e-9, solve_tol=1e-9, nbuf=nbuf)
+            assert rc == 0
+            out.append((lam[0], rep["iterations"], rep["e_h"]))
+        else:
+            steps = shard.ContextSCF(ctx, [x], nev, nocc, 1, tol=1e-9, nbuf=nbuf)
+            r = shard.scf_sharded(steps, tol=1e-9)
+            assert r["converged"]
+            out.append((steps.lam[0], r["iterations"], r["e_h"]))
+            # dks_density_residual against the same integral on the host
+            a, b = r["rho"], torch.zeros_like(r["rho"])
+            assert abs(ctx.density_residual(a, b) - a.abs().sum().item() * wl.volume / wl.ng) < 1e-12 * nocc
+    (l0, i0, e0), (l1, i1, e1) = out
+    assert np.abs(l0 - l1).max() < 1e-8 and abs(i0 - i1) <= 1 and abs(e0 - e1) < 1e-7
