@@ -20,8 +20,15 @@ Dirac-Kohn-Sham density functional theory"):
 * ``lobpcgf``   -- Algorithm 1 (LOBPCG-F; without the filter lines it is
                    standard LOBPCG) and the plain definition of the result: the
                    lowest nev eigenpairs of the dense matrix above the gap.
+* ``davidson``  -- block Davidson with the filter step of Algorithm 1 (the
+                   paper's remark that the filter carries over to Davidson-type
+                   solvers, Sec. 3).
+* ``scf``       -- the self-consistent field loop around the eigenproblem: the
+                   density of Eq. (density), the Hartree and LDA potential of
+                   Sec. 2.1, Anderson mixing with the Kerker preconditioner
+                   (Sec. 4.1), on the dense operator.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants, library routines or brute force (see each test's docstring).
 """
-from . import basis, operator, lobpcgf  # noqa: F401
+from . import basis, operator, lobpcgf, davidson, scf  # noqa: F401
