@@ -159,3 +159,92 @@ def dense_eigs(h, c, nev):
     pos = np.nonzero(w > -c * c)[0]
     sel = pos[:nev]
     return w[sel], u[:, sel], w
+
+
+def _project_out(qm, ym):
+    """Y <- Y - Q (Q^H Y), twice (classical Gram-Schmidt with one reorthogonalisation)."""
+    if qm is None or qm.shape[1] == 0:
+        return ym
+    for _ in range(2):
+        ym = ym - qm @ (qm.conj().T @ ym)
+    return ym
+
+
+def lobpcgf_blocked(hop, q, x0, n, block, cshift, omega, nbuf=0, n_init=3, n_iter=200, tol=1e-6,
+                    use_filter=True, precond="teter"):
+    """Algorithm 1 on band blocks, for more wanted pairs than one block can hold (reading of a
+    large-cell configuration: bands of at most `block` wanted columns, each block deflated
+    against the converged earlier ones).
+
+    Block b wants the pairs b*block .. min(n, (b+1)*block) - 1 and iterates them with nbuf
+    buffer columns above them (not convergence-checked).  Its start block is the previous
+    block's buffer columns followed by unused columns of x0; every block that enters the
+    subspace -- the filtered start block and every filtered correction Y -- has the span of
+    the locked vectors Q (all earlier blocks' converged columns) projected out, so the block
+    converges to the next pairs above them.  Each block is otherwise Algorithm 1 as in
+    lobpcgf().  Returns SolveResult with the n eigenvalues in ascending block order."""
+    npw = q.shape[0]
+    x0 = np.array(x0, dtype=np.complex128)
+    nc = x0.shape[1]
+    start = hop.count if hasattr(hop, "count") else 0
+
+    def fh(y):
+        return apply_filter(hop, y, cshift, omega) if use_filter else y
+
+    def tinv(xb, rb):
+        if precond == "teter":
+            return teter_precondition(q, xb, rb)
+        return rb.copy()
+
+    qm = None                                   # locked vectors, columns
+    lams, history = [], []
+    pool = [x0[j] for j in range(x0.shape[0])]  # unused start columns
+    carry = []                                  # buffer columns of the previous block
+    iterations, converged = 0, True
+    nblk = (n + block - 1) // block
+    for b in range(nblk):
+        nw = min(block, n - b * block)
+        m = nw + nbuf
+        cols = carry[:m]
+        while len(cols) < m:
+            if not pool:
+                raise ValueError("x0 has too few columns for the blocks")
+            cols.append(pool.pop(0))
+        x = np.stack(cols)
+        for _ in range(n_init if use_filter else 0):
+            x = fh(x)
+        xm = _project_out(qm, _cols(x))
+        hxm = _cols(hop(_blk(xm, npw, nc)))
+        lam, v, _ = rayleigh_ritz(xm.conj().T @ hxm, xm.conj().T @ xm, m)
+        xm, hxm = xm @ v, hxm @ v
+        rm = hxm - xm * lam[None, :]
+        act = np.arange(m)
+        pm = hpm = None
+        norms = np.linalg.norm(rm, axis=0)
+        ok = False
+        for it in range(1, n_iter + 1):
+            yb = fh(tinv(_blk(xm[:, act], npw, nc), _blk(rm, npw, nc)))
+            ym = _project_out(qm, _cols(yb))
+            hym = _cols(hop(_blk(ym, npw, nc)))
+            zm = np.hstack([xm, ym] + ([pm] if pm is not None else []))
+            hzm = np.hstack([hxm, hym] + ([hpm] if hpm is not None else []))
+            lam, v, info = rayleigh_ritz(zm.conj().T @ hzm, zm.conj().T @ zm, m)
+            xm, hxm = zm @ v, hzm @ v
+            rm = hxm - xm * lam[None, :]
+            norms = np.linalg.norm(rm, axis=0)
+            history.append(dict(block=b, it=it, max_res=float(norms[:nw].max()), nz=zm.shape[1]))
+            if np.all(norms[:nw] < tol):
+                ok = True
+                break
+            act = np.nonzero(norms > tol)[0]
+            rm = rm[:, act]
+            va = v[m:, act]
+            pm, hpm = zm[:, m:] @ va, hzm[:, m:] @ va
+        iterations += it
+        converged = converged and ok
+        lams.append(lam[:nw])
+        qm = xm[:, :nw] if qm is None else np.hstack([qm, xm[:, :nw]])
+        carry = [c for c in _blk(xm[:, nw:], npw, nc)]
+    used = (hop.count - start) if hasattr(hop, "count") else -1
+    return SolveResult(lam=np.concatenate(lams), x=_blk(qm, npw, nc), iterations=iterations,
+                       converged=converged, resnorms=None, history=history, h_applications=used)

@@ -543,3 +543,33 @@ def test_golden_cubic_dense_eigs():
     wl, m, q = _setup("cubic")
     lam, _, _ = lb.dense_eigs(op.dense_hamiltonian(wl, m, q), wl.c, 8)
     assert np.abs(lam - ref).max() < 1e-10
+
+
+# ---------------------------------------------------------------- band blocks with deflation
+
+@pytest.mark.parametrize("n,block,nbuf", [(20, 8, 4), (14, 7, 2)])
+def test_blocked_lobpcgf_matches_dense(n, block, nbuf):
+    """Algorithm 1 on band blocks deflated against the earlier blocks gives the n lowest dense
+    eigenvalues above the gap (block 7 puts a block edge inside a Kramers pair), with orthonormal
+    vectors that satisfy the eigen-equation of the dense matrix."""
+    wl, m, q = _setup("small", ecut=4.0)
+    hop = op.MatrixFreeH(wl, m, q)
+    cs, om = op.filter_constants(wl, q)
+    x0 = W.start_block(len(m), n + 3 * nbuf + block, wl.seed)
+    res = lb.lobpcgf_blocked(hop, q, x0, n, block, cs, om, nbuf=nbuf, tol=1e-8)
+    h = op.dense_hamiltonian(wl, m, q)
+    ref, _, _ = lb.dense_eigs(h, wl.c, n)
+    assert res.converged and np.abs(res.lam - ref).max() < 1e-9
+    x = res.x.reshape(n, -1).T
+    assert np.abs(x.conj().T @ x - np.eye(n)).max() < 1e-12
+    assert np.abs(h @ x - x * res.lam[None, :]).max() < 1e-7
+
+
+def test_blocked_lobpcgf_one_block_is_algorithm_1():
+    """With one block holding every wanted pair, the blocked form is lobpcgf() itself."""
+    wl, m, q = _setup("small", ecut=4.0)
+    cs, om = op.filter_constants(wl, q)
+    x0 = W.start_block(len(m), 8, wl.seed)
+    a = lb.lobpcgf(op.MatrixFreeH(wl, m, q), q, x0, 8, cs, om, tol=1e-8)
+    b = lb.lobpcgf_blocked(op.MatrixFreeH(wl, m, q), q, x0, 8, 8, cs, om, tol=1e-8)
+    assert a.iterations == b.iterations and np.abs(a.lam - b.lam).max() < 1e-13
