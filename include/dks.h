@@ -182,6 +182,14 @@ typedef struct {
   int solver;          /* DKS_SOLVER_LOBPCG (Algorithm 1, default) or DKS_SOLVER_DAVIDSON */
   int m_max;           /* DAVIDSON: largest basis, in columns (0 = 4 (nev + nbuf)); at
                           least 2 (nev + nbuf) and at most 512                           */
+  int block;           /* LOBPCG: wanted pairs per band block (0 = all in one block).  With
+                          nev_k > block the pairs are found block by block: each block
+                          iterates its `block` wanted columns plus the nbuf buffer columns
+                          and has the converged vectors of the earlier blocks projected out
+                          of its filtered start block and of every filtered correction
+                          (deflation); it starts from the previous block's buffer columns
+                          followed by the next unused columns of X.  The Rayleigh-Ritz limit
+                          then applies to block + nbuf, not to nev_k + nbuf               */
 } dks_solve_opts;
 
 /* Solvers.  LOBPCG: Algorithm 1 (LOBPCG-F with use_filter = 1).  DAVIDSON: block Davidson with

@@ -54,7 +54,7 @@ class SolveOpts(C.Structure):
                 ("Omega", C.c_double), ("mode", C.c_int), ("refine_tol", C.c_double), ("precond", C.c_int),
                 ("use_filter", C.c_int), ("nev_k", C.POINTER(C.c_int)), ("stream", C.c_void_p),
                 ("chol_tol", C.c_double), ("drop_tol", C.c_double), ("emulate_fp64", C.c_int),
-                ("concurrency", C.c_int), ("solver", C.c_int), ("m_max", C.c_int)]
+                ("concurrency", C.c_int), ("solver", C.c_int), ("m_max", C.c_int), ("block", C.c_int)]
 
 
 class SolveReport(C.Structure):
@@ -389,9 +389,11 @@ class Context:
     def solve(self, x_list, nev, tol=1e-6, n_init=3, n_iter=200, mode=MODE_FP64, refine_tol=1e-5,
               precond=PRECOND_TETER, use_filter=True, cshift=None, omega=None, nev_k=None, nbuf=0,
               stream=None, check=True, chol_tol=None, drop_tol=None, emulate_fp64=True, concurrency=0,
-              solver="lobpcg", m_max=0):
+              solver="lobpcg", m_max=0, block=0):
         """Algorithm 1 on every k-point (solver="davidson": block Davidson with the same filter, basis
         of at most m_max columns).  x_list[ik]: complex128 [nev_k+nbuf, ncomp, npw] (X0 in, X out).
+        block > 0: the pairs are found in band blocks of `block` wanted columns (plus nbuf buffer
+        columns each), every block deflated against the converged earlier ones.
         Returns (eigenvalues per k as numpy arrays, report dict, status code)."""
         opts = SolveOpts()
         _lib.dks_solve_opts_default(C.byref(opts))
@@ -408,7 +410,7 @@ class Context:
         opts.concurrency = int(concurrency)
         if solver not in SOLVERS:
             raise ValueError(f"solver must be one of {sorted(SOLVERS)}")
-        opts.solver, opts.m_max = SOLVERS[solver], int(m_max)
+        opts.solver, opts.m_max, opts.block = SOLVERS[solver], int(m_max), int(block)
         nevs = [int(nev)] * self.nk if nev_k is None else [int(v) for v in nev_k]
         if nev_k is not None:
             arr = np.ascontiguousarray(nevs, dtype=np.int32)

@@ -113,6 +113,23 @@ static int nn(bool df, const V* a, int lda, int k, int m, const double2* w, int 
   return gemm_nn<V>(a, lda, k, m, w, ldw, nullptr, n, out, ldo, 0.0, st);
 }
 
+// Y <- Y - Q (Q^H Y), twice (classical Gram-Schmidt with one reorthogonalisation): the locked
+// vectors Q (nq columns) of earlier band blocks leave the span of the ncol columns of Y.  coef
+// holds nq x ncol complex128 coefficients.
+template <typename V>
+static int project_out(const V* q, int nq, V* y, int ncol, int rows, double2* coef, bool df, cudaStream_t st) {
+  if (!q || nq <= 0 || ncol <= 0) return DKS_OK;
+  for (int pass = 0; pass < 2; ++pass) {
+    DKS_CUDA_TRY(cudaMemsetAsync(coef, 0, (size_t)nq * ncol * sizeof(double2), st));
+    DKS_TRY(hn<V>(df, q, rows, y, rows, rows, nq, ncol, coef, st, false));
+    if (df)
+      DKS_TRY(gemm_nn_df((const double2*)q, rows, rows, nq, coef, nq, nullptr, ncol, (double2*)y, rows, 1.0, st, -1.0));
+    else
+      DKS_TRY(gemm_nn<V>(q, rows, rows, nq, coef, nq, nullptr, ncol, y, rows, 1.0, st, -1.0));
+  }
+  return DKS_OK;
+}
+
 template <typename V>
 static int gram(const V* z, const V* hz, int rows, int nz, Small& sm, cudaStream_t st, bool df = false) {
   DKS_CUDA_TRY(cudaMemsetAsync(sm.a, 0, (size_t)nz * nz * sizeof(double2), st));
@@ -150,7 +167,9 @@ template <typename V>
 static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned& pin, int n, int nconv, double tol,
                  int n_init, int n_iter, double C, double om, int precond, int use_filter, bool stop_on_stall,
                  double chol_tol, double drop_tol, std::vector<double>* hist, PhaseOut& out, cudaStream_t st,
-                 bool df = false) {
+                 bool df = false, const V* q = nullptr, int nq = 0, double2* coef = nullptr) {
+  // q: nq locked vectors of earlier band blocks (deflation), projected out of the filtered start
+  // block and of every filtered correction Y
   df = df && sizeof(V) == sizeof(double2);
   ex.df_gemm = df;   // projector contractions inside apply_h follow the phase's arithmetic
   const KPoint& kp = ctx->k[ik];
@@ -165,6 +184,7 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
       DKS_TRY(filter_inplace<V>(ctx, ex, ik, b.z[cur], b.tmp, n, C, om, st));
       happ += 2LL * n;
     }
+  DKS_TRY(project_out<V>(q, nq, b.z[cur], n, rows, coef, df, st));
   // first Rayleigh-Ritz on X0
   DKS_TRY(apply_h<V>(ctx, ex, ik, b.z[cur], b.hz[cur], n, 0.0, 1.0, st));
   happ += n;
@@ -213,6 +233,7 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
       DKS_TRY(filter_inplace<V>(ctx, ex, ik, y, b.tmp, a, C, om, st));
       happ += 2LL * a;
     }
+    DKS_TRY(project_out<V>(q, nq, y, a, rows, coef, df, st));
     DKS_TRY(apply_h<V>(ctx, ex, ik, y, hy, a, 0.0, 1.0, st));
     happ += a;
     const int nz = n + a + p;
@@ -481,6 +502,7 @@ void dks_solve_opts_default(dks_solve_opts* o) {
   o->concurrency = 0;
   o->solver = DKS_SOLVER_LOBPCG;
   o->m_max = 0;
+  o->block = 0;
 }
 
 int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* opts_in, double* eig, void* const* X,
@@ -491,7 +513,8 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
   else dks_solve_opts_default(&opts);
   if (!ctx || !eig || !X || !(tol > 0) || opts.n_init < 0 || opts.n_iter < 0 || opts.nbuf < 0 ||
       opts.concurrency < 0 || (opts.mode != DKS_MODE_FP64 && opts.mode != DKS_MODE_MIXED) ||
-      (opts.solver != DKS_SOLVER_LOBPCG && opts.solver != DKS_SOLVER_DAVIDSON) || opts.m_max < 0)
+      (opts.solver != DKS_SOLVER_LOBPCG && opts.solver != DKS_SOLVER_DAVIDSON) || opts.m_max < 0 ||
+      opts.block < 0 || (opts.block > 0 && opts.solver != DKS_SOLVER_LOBPCG))
     return fail(DKS_ERR_INVALID_ARG, "dks_lobpcgf_solve: bad argument");
   const bool davidson = opts.solver == DKS_SOLVER_DAVIDSON;
   cudaStream_t st = (cudaStream_t)opts.stream;
@@ -502,12 +525,18 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
     std::memset(report, 0, sizeof(*report));
     report->shift = ctx->ncomp == 4 ? ctx->c * ctx->c : 0.0;
   }
-  int nmax = 0, rowsmax = 0;
+  int nmax = 0, rowsmax = 0, nlockmax = 0;
   std::vector<size_t> eoff(ctx->nk + 1, 0);
   for (int ik = 0; ik < ctx->nk; ++ik) {
     const int nv = opts.nev_k ? opts.nev_k[ik] : nev;
     if (nv <= 0 || !X[ik]) return fail(DKS_ERR_INVALID_ARG, "dks_lobpcgf_solve: nev_k and X[ik] required");
-    const int n = nv + opts.nbuf;
+    // band blocks: the iterated width is block + nbuf; the locked vectors are the earlier blocks'
+    const bool blocked = opts.block > 0 && nv > opts.block;
+    const int n = (blocked ? opts.block : nv) + opts.nbuf;
+    if (blocked) {
+      nlockmax = std::max(nlockmax, nv);
+      if (nv + opts.nbuf > ctx->k[ik].npw * ctx->ncomp) return fail(DKS_ERR_INVALID_ARG, "more pairs than the basis");
+    }
     if (3 * n > kMaxRR) return fail(DKS_ERR_UNSUPPORTED, "block wider than the Rayleigh-Ritz limit (3n <= 512)");
     if (davidson) {
       const int mm = opts.m_max ? opts.m_max : std::min(4 * n, kMaxRR);
@@ -531,10 +560,14 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
   const size_t small = (2 * nz * nz + 2 * nz * nmax + rr_scratch_elems((int)nz)) * sizeof(double2) +
                        (nmax + 3 * nmax) * sizeof(double) + (nmax + 4) * sizeof(int) + 16 * 256;
   const bool split_copies = mixed && opts.emulate_fp64 != 0 && !davidson;
+  // band blocks: FP32 copy of the locked vectors (mixed mode) and the projection coefficients
+  const size_t lock32 = mixed ? (size_t)nlockmax * rowsmax * sizeof(float2) : 0;
+  const size_t lockcoef = (size_t)nlockmax * nmax * sizeof(double2);
   const size_t dcols64 = (size_t)2 * mmax + 4 * (size_t)nmax, dcols32 = mixed ? (size_t)2 * mmax + 5 * (size_t)nmax : 0;
   const size_t total =
       davidson ? (dcols64 * sizeof(double2) + dcols32 * sizeof(float2)) * rowsmax + small + 32 * 256
-               : 4 * big64 + tmp64 + 4 * big32 + 2 * tmp32 + small + (split_copies ? 2 * big64 : 0) + 16 * 256;
+               : 4 * big64 + tmp64 + 4 * big32 + 2 * tmp32 + small + (split_copies ? 2 * big64 : 0) + lock32 +
+                     lockcoef + 18 * 256;
   // concurrent k-point workers, each with its own stream and workspace (bounded by free memory)
   int nworkers = opts.concurrency > 0 ? opts.concurrency : std::min(ctx->nk, 4);
   nworkers = std::max(1, std::min(nworkers, ctx->nk));
@@ -617,6 +650,8 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
         b32.best = (float2*)take(tmp32);
       }
     }
+    float2* q32 = lock32 ? (float2*)take(lock32) : nullptr;
+    double2* qcoef = lockcoef ? (double2*)take(lockcoef) : nullptr;
     Small sm;
     sm.a = (double2*)take(nz * nz * sizeof(double2));
     sm.s = (double2*)take(nz * nz * sizeof(double2));
@@ -670,6 +705,82 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
           DKS_CUDA_TRY(cudaStreamSynchronize(ws));
           for (int j = 0; j < nv; ++j) eig[eoff[ik] + j] = pin.lam[j];
           happ += o32.happ + o64.happ;
+          return DKS_OK;
+        }
+        if (opts.block > 0 && nv > opts.block) {
+          // band blocks with deflation.  Block bi wants the pairs bi*blk .. bi*blk + nw - 1 and
+          // iterates m = nw + nbuf columns.  Its start block: block 0 takes columns 0 .. m-1 of
+          // X; block bi > 0 takes the previous block's nbuf buffer columns and then columns
+          // nbuf + bi*blk .. nbuf + bi*blk + nw - 1 of X (not yet read by an earlier block).  The
+          // converged wanted columns are written to X[bi*blk ..] (columns every earlier block has
+          // already consumed) and serve as the locked vectors Q of the later blocks.
+          const int blk = opts.block, nb = opts.nbuf;
+          const size_t rows = (size_t)ctx->ncomp * kp.npw;
+          double2* xk = (double2*)X[ik];
+          const int nblk = (nv + blk - 1) / blk;
+          int prev_nw = 0, prev_cur = 0;
+          PhaseOut acc32, acc64;
+          acc64.converged = true;
+          for (int bi = 0; bi < nblk; ++bi) {
+            const int nw = std::min(blk, nv - bi * blk);
+            const int m = nw + nb;
+            const int nq = bi * blk;
+            const size_t me = (size_t)m * rows;
+            const int sidx = bi == 0 ? 0 : (prev_cur ^ 1);
+            double2* zs = b64.z[sidx];
+            if (bi == 0) {
+              DKS_CUDA_TRY(cudaMemcpyAsync(zs, xk, me * sizeof(double2), cudaMemcpyDeviceToDevice, ws));
+            } else {
+              if (nb)
+                DKS_CUDA_TRY(cudaMemcpyAsync(zs, b64.z[prev_cur] + (size_t)prev_nw * rows, (size_t)nb * rows * sizeof(double2),
+                                             cudaMemcpyDeviceToDevice, ws));
+              DKS_CUDA_TRY(cudaMemcpyAsync(zs + (size_t)nb * rows, xk + (size_t)(nb + bi * blk) * rows,
+                                           (size_t)nw * rows * sizeof(double2), cudaMemcpyDeviceToDevice, ws));
+            }
+            PhaseOut p32, p64;
+            if (mixed) {
+              DKS_TRY(convert<double2, float2>(zs, b32.z[0], me, ws));
+              p32.cur = 0;
+              DKS_TRY(phase<float2>(ctx, ex, ik, b32, sm, pin, m, nw, std::max(opts.refine_tol, tol), opts.n_init,
+                                    opts.n_iter, C, om, opts.precond, opts.use_filter, true, opts.chol_tol,
+                                    opts.drop_tol, h, p32, ws, false, q32, nq, qcoef));
+              DKS_TRY(convert<float2, double2>(b32.z[p32.cur], b64.z[0], me, ws));
+              p64.cur = 0;
+              const int left = std::max(0, opts.n_iter - p32.iterations);
+              DKS_TRY(phase<double2>(ctx, ex, ik, b64, sm, pin, m, nw, tol, opts.use_filter ? 1 : 0, left, C, om,
+                                     opts.precond, opts.use_filter, false, opts.chol_tol, opts.drop_tol, h, p64, ws,
+                                     opts.emulate_fp64 != 0, xk, nq, qcoef));
+            } else {
+              p64.cur = sidx;
+              DKS_TRY(phase<double2>(ctx, ex, ik, b64, sm, pin, m, nw, tol, opts.n_init, opts.n_iter, C, om,
+                                     opts.precond, opts.use_filter, false, opts.chol_tol, opts.drop_tol, h, p64, ws,
+                                     false, xk, nq, qcoef));
+            }
+            // lock the wanted columns: X[nq .. nq + nw - 1], and their FP32 copy for later blocks
+            DKS_CUDA_TRY(cudaMemcpyAsync(xk + (size_t)nq * rows, b64.z[p64.cur], (size_t)nw * rows * sizeof(double2),
+                                         cudaMemcpyDeviceToDevice, ws));
+            if (mixed)
+              DKS_TRY(convert<double2, float2>(xk + (size_t)nq * rows, q32 + (size_t)nq * rows, (size_t)nw * rows, ws));
+            DKS_CUDA_TRY(cudaStreamSynchronize(ws));
+            for (int j = 0; j < nw; ++j) eig[eoff[ik] + nq + j] = pin.lam[j];
+            acc32.iterations += p32.iterations;
+            acc32.happ += p32.happ;
+            acc64.iterations += p64.iterations;
+            acc64.happ += p64.happ;
+            acc64.converged = acc64.converged && p64.converged;
+            acc64.max_res = std::max(acc64.max_res, p64.max_res);
+            acc64.neg = acc64.neg || p64.neg;
+            prev_nw = nw;
+            prev_cur = p64.cur;
+          }
+          // the last block's buffer columns follow the nev_k locked ones
+          if (nb)
+            DKS_CUDA_TRY(cudaMemcpyAsync(xk + (size_t)nv * rows, b64.z[prev_cur] + (size_t)prev_nw * rows,
+                                         (size_t)nb * rows * sizeof(double2), cudaMemcpyDeviceToDevice, ws));
+          DKS_CUDA_TRY(cudaStreamSynchronize(ws));
+          o32 = acc32;
+          o64 = acc64;
+          happ += acc32.happ + acc64.happ;
           return DKS_OK;
         }
         if (mixed) {

@@ -61,3 +61,23 @@ def test_scf_entry_points_validate_arguments_without_gpu():
     assert lib.dks_update_potential(None, None, None, None) == bad
     res = C.c_double(-1.0)
     assert lib.dks_density_residual(None, None, None, C.byref(res), None) == bad and res.value == -1.0
+
+
+def test_solve_opts_layout_matches_the_library():
+    """dks_solve_opts_default writes every field at the offset the binding reads it from: fill the
+    ctypes structure with sentinels, let the library write its defaults, read them back."""
+    import ctypes as C
+    import math
+    import paper_1211_1446_gb300 as P
+    lib = P.load_library()
+    o = P.SolveOpts()
+    C.memset(C.byref(o), 0x7f, C.sizeof(o))
+    lib.dks_solve_opts_default(C.byref(o))
+    assert (o.n_init, o.n_iter, o.nbuf, o.mode, o.precond, o.use_filter) == (3, 200, 0, 0, 0, 1)
+    assert math.isnan(o.C) and math.isnan(o.Omega) and o.refine_tol == 1e-5
+    assert (o.chol_tol, o.drop_tol, o.emulate_fp64, o.concurrency) == (1e-12, 1e-12, 1, 0)
+    assert (o.solver, o.m_max, o.block) == (0, 0, 0) and not o.nev_k and not o.stream
+    s = P.ScfOpts()
+    C.memset(C.byref(s), 0x7f, C.sizeof(s))
+    lib.dks_scf_opts_default(C.byref(s))
+    assert (s.nocc, s.history, s.n_init_warm, s.solve.block, s.solve.n_iter) == (0, 8, 1, 0, 200)
