@@ -77,6 +77,11 @@ class ScfReport(C.Structure):
                 ("res_history", C.c_double * 128)]
 
 
+class TuneReport(C.Structure):
+    _fields_ = [("ncand", C.c_int), ("best", C.c_int), ("chunk_bytes", C.c_longlong * 16),
+                ("plane_threads", C.c_int * 16), ("ms", C.c_double * 16)]
+
+
 EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dks_filter_constants",
            "dks_apply_H", "dks_filter", "dks_solve_opts_default", "dks_lobpcgf_solve", "dks_precond",
            "dks_gram", "dks_rayleigh_ritz", "dks_rotate", "dks_residual_norms", "dks_strerror",
@@ -84,7 +89,7 @@ EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dk
            "dks_rayleigh_ritz_static", "dks_gram_hermitian", "dks_kinetic_balance", "dks_create_model",
            "dks_ncomp", "dks_density", "dks_hxc", "dks_set_potential", "dks_mixer_create", "dks_mix",
            "dks_mixer_destroy", "dks_scf_opts_default", "dks_scf", "dks_update_potential",
-           "dks_density_residual"]
+           "dks_density_residual", "dks_autotune", "dks_tune_get", "dks_tune_set"]
 
 _lib = None
 
@@ -133,6 +138,9 @@ def load_library(path: str = LIB_PATH):
     lib.dks_scf_opts_default.argtypes = [C.POINTER(ScfOpts)]
     lib.dks_scf_opts_default.restype = None
     lib.dks_scf.argtypes = [vp, i, C.POINTER(ScfOpts), C.POINTER(d), C.POINTER(vp), vp, C.POINTER(ScfReport)]
+    lib.dks_autotune.argtypes = [vp, i, i, i, vp, C.POINTER(TuneReport)]
+    lib.dks_tune_get.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(i)]
+    lib.dks_tune_set.argtypes = [vp, C.c_longlong, i]
     lib.dks_strerror.argtypes = [i]
     lib.dks_strerror.restype = C.c_char_p
     lib.dks_last_error.argtypes = []
@@ -302,6 +310,36 @@ class Context:
                                 _dptr(y), precond, _prec_of(x), _stream(stream)))
         return y
 
+    # ---- launch-parameter tuning (results never depend on it, only the time)
+    def tuning(self):
+        chunk, threads = C.c_longlong(), C.c_int()
+        _check(_lib.dks_tune_get(self._h, C.byref(chunk), C.byref(threads)))
+        return dict(chunk_bytes=chunk.value, plane_threads=threads.value)
+
+    def set_tuning(self, chunk_bytes, plane_threads):
+        _check(_lib.dks_tune_set(self._h, int(chunk_bytes), int(plane_threads)))
+
+    def autotune(self, ik=0, nb=40, prec=PREC_FP32, cache=None, stream=None):
+        """dks_autotune on an nb-column block of k-point ik; with `cache` (a JSON file path) a stored
+        choice for the same grid, basis size, model, block width, precision and device is applied
+        instead, and a new choice is stored.  Returns the chosen parameters (and, when timed, the
+        candidates' times)."""
+        import torch
+        key = tuning_key(self.grid, self.npw(ik), self.ncomp, nb, prec, torch.cuda.get_device_name())
+        if cache:
+            hit = tuning_cache_lookup(cache, key)
+            if hit is not None:
+                self.set_tuning(hit["chunk_bytes"], hit["plane_threads"])
+                return dict(hit, cached=True)
+        rep = TuneReport()
+        _check(_lib.dks_autotune(self._h, int(ik), int(nb), int(prec), _stream(stream), C.byref(rep)))
+        choice = dict(chunk_bytes=int(rep.chunk_bytes[rep.best]), plane_threads=int(rep.plane_threads[rep.best]))
+        if cache:
+            tuning_cache_store(cache, key, choice)
+        cands = [dict(chunk_bytes=int(rep.chunk_bytes[i]), plane_threads=int(rep.plane_threads[i]),
+                      ms=float(rep.ms[i])) for i in range(rep.ncand)]
+        return dict(choice, cached=False, candidates=cands)
+
     # ---- SCF pieces (grids: float64 device tensors of shape grid, natural order)
     def _grid(self, *ts):
         import torch
@@ -442,6 +480,44 @@ class Context:
                       history=list(rep.res_history[:rep.hist_len]),
                       message=_lib.dks_last_error().decode() if rc else "")
         return out, report, rc
+
+
+def tuning_key(grid, npw, ncomp, nb, prec, device):
+    """Cache key of one tuning problem."""
+    return "grid=%dx%dx%d npw=%d ncomp=%d nb=%d prec=%d device=%s" % (tuple(int(g) for g in grid) +
+                                                                      (int(npw), int(ncomp), int(nb), int(prec),
+                                                                       str(device)))
+
+
+def tuning_cache_lookup(path, key):
+    """The stored choice for key in the JSON cache at path, or None (missing or unreadable file)."""
+    import json
+    try:
+        with open(path) as f:
+            entry = json.load(f).get(key)
+    except (OSError, ValueError, AttributeError):
+        return None
+    if not isinstance(entry, dict) or "chunk_bytes" not in entry or "plane_threads" not in entry:
+        return None
+    return dict(chunk_bytes=int(entry["chunk_bytes"]), plane_threads=int(entry["plane_threads"]))
+
+
+def tuning_cache_store(path, key, choice):
+    """Adds (or replaces) key in the JSON cache at path, written atomically."""
+    import json
+    data = {}
+    try:
+        with open(path) as f:
+            data = json.load(f)
+        if not isinstance(data, dict):
+            data = {}
+    except (OSError, ValueError):
+        data = {}
+    data[key] = dict(chunk_bytes=int(choice["chunk_bytes"]), plane_threads=int(choice["plane_threads"]))
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 class Mixer:

@@ -115,6 +115,7 @@ struct dks_ctx {
   // entry points and serial solves, exec[1..] the concurrent k-point workers
   std::vector<dks::Exec*> exec;
   size_t chunk_budget = 64u << 20;   // bytes of FFT intermediates per chunk (L2-resident)
+  int plane_threads = 0;             // CTA size of the plane FFT kernel (0: from the FFT plan)
   int ncomp = 4;                     // components per column: 4 (DKS, Eq. vDKS) or 2 (KSSO two-spinors)
   int device = 0;
   int num_sms = 0;

@@ -428,7 +428,8 @@ static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int n
     for (int i = 0; i < ctx->plan[a].nst; ++i) rmin = std::min(rmin, ctx->plan[a].radix[i]);
   // two butterflies per thread and pass (independent work for latency hiding, more CTAs per SM)
   const int nbf = ctx->grid[0] * ctx->grid[1] / rmin;
-  const int tb_plane = std::min(512, std::max(128, (nbf / 2 + 31) / 32 * 32));
+  const int tb_plane =
+      ctx->plane_threads > 0 ? ctx->plane_threads : std::min(512, std::max(128, (nbf / 2 + 31) / 32 * 32));
   DKS_TRY(set_smem<Vs>((const void*)k_stick_inverse<Vg, Vs>, sm_a));
   DKS_TRY(set_smem<Vs>((const void*)k_plane<Vg, Vs>, sm_b));
   DKS_TRY(set_smem<Vs>(nc == 4 ? (const void*)k_stick_forward<Vg, Vs> : (const void*)k_stick_forward_ks<Vg, Vs>,

@@ -81,3 +81,29 @@ def test_solve_opts_layout_matches_the_library():
     C.memset(C.byref(s), 0x7f, C.sizeof(s))
     lib.dks_scf_opts_default(C.byref(s))
     assert (s.nocc, s.history, s.n_init_warm, s.solve.block, s.solve.n_iter) == (0, 8, 1, 0, 200)
+
+
+def test_tuning_entry_points_and_cache_without_gpu(tmp_path):
+    """The tuning entry points reject bad arguments before touching the device; the JSON cache
+    of tuning choices round-trips, keeps other keys and ignores unreadable files."""
+    import ctypes as C
+    import paper_1211_1446_gb300 as P
+    lib = P.load_library()
+    assert lib.dks_autotune(None, 0, 8, 1, None, None) == -1
+    assert lib.dks_tune_set(None, 64 << 20, 0) == -1
+    chunk, thr = C.c_longlong(), C.c_int()
+    assert lib.dks_tune_get(None, C.byref(chunk), C.byref(thr)) == -1
+    rep = P.TuneReport()
+    assert C.sizeof(rep) == 8 + 16 * 8 + 16 * 4 + 16 * 8
+    path = str(tmp_path / "tune.json")
+    k1 = P.tuning_key((48, 48, 56), 57419, 4, 40, 1, "GB300")
+    k2 = P.tuning_key((48, 48, 56), 57419, 4, 40, 0, "GB300")
+    assert k1 != k2 and P.tuning_cache_lookup(path, k1) is None
+    P.tuning_cache_store(path, k1, dict(chunk_bytes=32 << 20, plane_threads=256))
+    P.tuning_cache_store(path, k2, dict(chunk_bytes=64 << 20, plane_threads=0))
+    assert P.tuning_cache_lookup(path, k1) == dict(chunk_bytes=32 << 20, plane_threads=256)
+    assert P.tuning_cache_lookup(path, k2) == dict(chunk_bytes=64 << 20, plane_threads=0)
+    open(path, "w").write("{not json")
+    assert P.tuning_cache_lookup(path, k1) is None
+    P.tuning_cache_store(path, k1, dict(chunk_bytes=16 << 20, plane_threads=128))
+    assert P.tuning_cache_lookup(path, k1) == dict(chunk_bytes=16 << 20, plane_threads=128)

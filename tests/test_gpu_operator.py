@@ -200,3 +200,33 @@ def test_apply_h_ksso_full_dimer(dt):
     ctx.apply_H(0, xd, hx, emulated=(dt == "df"))
     torch.cuda.synchronize()
     assert rel_err(hx.cpu().numpy(), ref) < (2e-6 if dt == "c64" else 1e-12)
+
+
+def test_autotune_changes_time_not_results(tmp_path):
+    """dks_autotune times the 16 candidate (chunk budget, plane CTA size) pairs, keeps one of
+    them, and H' x is the same under every pair (each FFT output is one thread's butterfly, so
+    neither parameter changes the arithmetic); the JSON cache returns the stored choice."""
+    torch = gpu()
+    import paper_1211_1446_gb300 as P
+    wl, ctx, hop, q = make_pair("dimer", ecut=4.0)
+    npw = ctx.npw(0)
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((6, 4, npw)) + 1j * rng.standard_normal((6, 4, npw))
+    want = hop(x)
+    cache = str(tmp_path / "tune.json")
+    r = ctx.autotune(0, nb=8, prec=P.PREC_FP32, cache=cache)
+    assert not r["cached"] and len(r["candidates"]) == 16
+    assert all(c["ms"] > 0 for c in r["candidates"])
+    assert ctx.tuning() == dict(chunk_bytes=r["chunk_bytes"], plane_threads=r["plane_threads"])
+    xd = to_dev(x, torch.complex128)
+    outs = []
+    for chunk, thr in [(r["chunk_bytes"], r["plane_threads"]), (16 << 20, 128), (128 << 20, 512), (64 << 20, 0)]:
+        ctx.set_tuning(chunk, thr)
+        hx = torch.empty_like(xd)
+        ctx.apply_H(0, xd, hx)
+        outs.append(hx.cpu().numpy())
+    assert rel_err(outs[0], want) < 1e-11
+    for o in outs[1:]:
+        assert rel_err(o, outs[0]) < 1e-14
+    r2 = ctx.autotune(0, nb=8, prec=P.PREC_FP32, cache=cache)
+    assert r2["cached"] and (r2["chunk_bytes"], r2["plane_threads"]) == (r["chunk_bytes"], r["plane_threads"])
