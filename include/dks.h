@@ -405,28 +405,33 @@ int dks_scf(dks_ctx* ctx, int nev, const dks_scf_opts* opts, double* eig, void* 
             dks_scf_report* report);
 
 /* ------------------------------------------------ launch-parameter tuning (no counterpart in the
- * paper, whose code ran on CPUs).  Two parameters of this implementation's H' application:
+ * paper, whose code ran on CPUs).  Three parameters of this implementation's H' application:
  * the byte budget of one chunk of FFT intermediates (default 64 MB: how many bands' stick
- * buffers stay resident in L2 between the three FFT passes) and the CTA size of the plane FFT
- * kernel (0 = from the FFT plan: two butterflies per thread and pass).  Results never depend
- * on them; only the time does.  Not reentrant per ctx (do not tune during a solve). */
+ * buffers stay resident in L2 between the three FFT passes), the CTA size of the one-kernel
+ * plane FFT (0 = from the FFT plan: two butterflies per thread and pass), and plane_split: 1 runs
+ * the plane FFT as row and column kernels through an L2-resident plane buffer (always the case
+ * for planes above one CTA's shared memory, N1 (N2 | 1) x 16 bytes > 227 KB for complex128).
+ * Results never depend on them (every line transform is the same arithmetic); only the time
+ * does.  Not reentrant per ctx (do not tune during a solve). */
 typedef struct {
   int ncand;                  /* candidates timed                                     */
   int best;                   /* index of the fastest                                 */
-  long long chunk_bytes[16];
-  int plane_threads[16];
-  double ms[16];              /* mean time of one H' application on the nb columns     */
+  long long chunk_bytes[32];
+  int plane_threads[32];
+  int plane_split[32];
+  double ms[32];              /* mean time of one H' application on the nb columns     */
 } dks_tune_report;
 /* dks_autotune: times dks_apply_H on an nb-column scratch block of k-point ik in precision
  * prec (device memory allocated and freed on `stream`) for chunk budgets {16, 32, 64, 128} MB
- * x plane CTA sizes {plan, 128, 256, 512}, one warm-up and three timed applications each
- * (CUDA events on `stream`), and keeps the fastest pair.  Synchronous.  On error the previous
- * parameters stay.  report may be NULL.  Errors: INVALID_ARG, OOM, CUDA. */
+ * x {one-kernel plane FFT with CTA sizes {plan, 128, 256, 512} (where the plane fits), split
+ * plane FFT}, one warm-up and three timed applications each (CUDA events on `stream`), and keeps
+ * the fastest.  Synchronous.  On error the previous parameters stay.  report may be NULL.
+ * Errors: INVALID_ARG, OOM, CUDA. */
 int dks_autotune(dks_ctx* ctx, int ik, int nb, int prec, void* stream, dks_tune_report* report);
 /* Current parameters, and setting stored ones: 1 MB <= fft_chunk_bytes <= 64 GB; plane_threads 0
- * or a multiple of 32 in 64..512.  Errors: INVALID_ARG. */
-int dks_tune_get(const dks_ctx* ctx, long long* fft_chunk_bytes, int* plane_threads);
-int dks_tune_set(dks_ctx* ctx, long long fft_chunk_bytes, int plane_threads);
+ * or a multiple of 32 in 64..512; plane_split 0 or 1.  Errors: INVALID_ARG. */
+int dks_tune_get(const dks_ctx* ctx, long long* fft_chunk_bytes, int* plane_threads, int* plane_split);
+int dks_tune_set(dks_ctx* ctx, long long fft_chunk_bytes, int plane_threads, int plane_split);
 
 /* ------------------------------------------------ instrumentation (no counterpart in the paper;
  * the solve report's phase timers of a production code).  Every kernel launch of the library is

@@ -78,8 +78,8 @@ class ScfReport(C.Structure):
 
 
 class TuneReport(C.Structure):
-    _fields_ = [("ncand", C.c_int), ("best", C.c_int), ("chunk_bytes", C.c_longlong * 16),
-                ("plane_threads", C.c_int * 16), ("ms", C.c_double * 16)]
+    _fields_ = [("ncand", C.c_int), ("best", C.c_int), ("chunk_bytes", C.c_longlong * 32),
+                ("plane_threads", C.c_int * 32), ("plane_split", C.c_int * 32), ("ms", C.c_double * 32)]
 
 
 EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dks_filter_constants",
@@ -139,8 +139,8 @@ def load_library(path: str = LIB_PATH):
     lib.dks_scf_opts_default.restype = None
     lib.dks_scf.argtypes = [vp, i, C.POINTER(ScfOpts), C.POINTER(d), C.POINTER(vp), vp, C.POINTER(ScfReport)]
     lib.dks_autotune.argtypes = [vp, i, i, i, vp, C.POINTER(TuneReport)]
-    lib.dks_tune_get.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(i)]
-    lib.dks_tune_set.argtypes = [vp, C.c_longlong, i]
+    lib.dks_tune_get.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(i), C.POINTER(i)]
+    lib.dks_tune_set.argtypes = [vp, C.c_longlong, i, i]
     lib.dks_strerror.argtypes = [i]
     lib.dks_strerror.restype = C.c_char_p
     lib.dks_last_error.argtypes = []
@@ -312,12 +312,12 @@ class Context:
 
     # ---- launch-parameter tuning (results never depend on it, only the time)
     def tuning(self):
-        chunk, threads = C.c_longlong(), C.c_int()
-        _check(_lib.dks_tune_get(self._h, C.byref(chunk), C.byref(threads)))
-        return dict(chunk_bytes=chunk.value, plane_threads=threads.value)
+        chunk, threads, split = C.c_longlong(), C.c_int(), C.c_int()
+        _check(_lib.dks_tune_get(self._h, C.byref(chunk), C.byref(threads), C.byref(split)))
+        return dict(chunk_bytes=chunk.value, plane_threads=threads.value, plane_split=split.value)
 
-    def set_tuning(self, chunk_bytes, plane_threads):
-        _check(_lib.dks_tune_set(self._h, int(chunk_bytes), int(plane_threads)))
+    def set_tuning(self, chunk_bytes, plane_threads=0, plane_split=0):
+        _check(_lib.dks_tune_set(self._h, int(chunk_bytes), int(plane_threads), int(plane_split)))
 
     def autotune(self, ik=0, nb=40, prec=PREC_FP32, cache=None, stream=None):
         """dks_autotune on an nb-column block of k-point ik; with `cache` (a JSON file path) a stored
@@ -329,15 +329,16 @@ class Context:
         if cache:
             hit = tuning_cache_lookup(cache, key)
             if hit is not None:
-                self.set_tuning(hit["chunk_bytes"], hit["plane_threads"])
+                self.set_tuning(hit["chunk_bytes"], hit["plane_threads"], hit["plane_split"])
                 return dict(hit, cached=True)
         rep = TuneReport()
         _check(_lib.dks_autotune(self._h, int(ik), int(nb), int(prec), _stream(stream), C.byref(rep)))
-        choice = dict(chunk_bytes=int(rep.chunk_bytes[rep.best]), plane_threads=int(rep.plane_threads[rep.best]))
+        choice = dict(chunk_bytes=int(rep.chunk_bytes[rep.best]), plane_threads=int(rep.plane_threads[rep.best]),
+                      plane_split=int(rep.plane_split[rep.best]))
         if cache:
             tuning_cache_store(cache, key, choice)
         cands = [dict(chunk_bytes=int(rep.chunk_bytes[i]), plane_threads=int(rep.plane_threads[i]),
-                      ms=float(rep.ms[i])) for i in range(rep.ncand)]
+                      plane_split=int(rep.plane_split[i]), ms=float(rep.ms[i])) for i in range(rep.ncand)]
         return dict(choice, cached=False, candidates=cands)
 
     # ---- SCF pieces (grids: float64 device tensors of shape grid, natural order)
@@ -497,9 +498,10 @@ def tuning_cache_lookup(path, key):
             entry = json.load(f).get(key)
     except (OSError, ValueError, AttributeError):
         return None
-    if not isinstance(entry, dict) or "chunk_bytes" not in entry or "plane_threads" not in entry:
+    if not isinstance(entry, dict) or any(k not in entry for k in ("chunk_bytes", "plane_threads", "plane_split")):
         return None
-    return dict(chunk_bytes=int(entry["chunk_bytes"]), plane_threads=int(entry["plane_threads"]))
+    return dict(chunk_bytes=int(entry["chunk_bytes"]), plane_threads=int(entry["plane_threads"]),
+                plane_split=int(entry["plane_split"]))
 
 
 def tuning_cache_store(path, key, choice):
@@ -513,7 +515,8 @@ def tuning_cache_store(path, key, choice):
             data = {}
     except (OSError, ValueError):
         data = {}
-    data[key] = dict(chunk_bytes=int(choice["chunk_bytes"]), plane_threads=int(choice["plane_threads"]))
+    data[key] = dict(chunk_bytes=int(choice["chunk_bytes"]), plane_threads=int(choice["plane_threads"]),
+                     plane_split=int(choice["plane_split"]))
     tmp = f"{path}.tmp{os.getpid()}"
     with open(tmp, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)

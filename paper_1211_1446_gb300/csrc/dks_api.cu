@@ -353,8 +353,7 @@ int dks_create(const dks_cell* cell, double ecut, const dks_potentials* pot, con
   }
   ctx->ng = ctx->grid[0] * ctx->grid[1] * ctx->grid[2];
   ctx->plane_ld = ctx->grid[1] | 1;
-  if ((size_t)ctx->grid[0] * ctx->plane_ld * sizeof(double2) > 227 * 1024)
-    return bail(fail(DKS_ERR_UNSUPPORTED, "N1*N2 plane exceeds the shared-memory limit"));
+  // planes above one CTA's shared memory run pass B as row and column kernels (hx_kernels.cu)
   // reciprocal rows: b_i = 2 pi (A^-1)^T rows
   const double* A = ctx->lattice;
   const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +

@@ -116,6 +116,7 @@ struct dks_ctx {
   std::vector<dks::Exec*> exec;
   size_t chunk_budget = 64u << 20;   // bytes of FFT intermediates per chunk (L2-resident)
   int plane_threads = 0;             // CTA size of the plane FFT kernel (0: from the FFT plan)
+  int plane_split = 0;               // 1: pass B as row / column kernels even when a plane fits one CTA
   int ncomp = 4;                     // components per column: 4 (DKS, Eq. vDKS) or 2 (KSSO two-spinors)
   int device = 0;
   int num_sms = 0;

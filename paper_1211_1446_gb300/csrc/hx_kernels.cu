@@ -98,6 +98,127 @@ __global__ void __launch_bounds__(512) k_plane(Vg* __restrict__ t, int nsticks,
 }
 
 // ---------------------------------------------------------------------------
+// pass B split in three kernels, for planes too large for one CTA's shared memory (N1 LD
+// sizeof(Vs) above the 227 KB limit, e.g. 120 x 121 complex128) or when chosen by the tuner.
+// The plane of one (field, p3) goes through an L2-resident buffer P[field][p3][i1][LD] (rows in
+// natural i1 order before the column transform, in DIF position order after it); every line
+// transform is the same fft_lines call as in k_plane, so the results are the same bit for bit.
+//   B1  rows r0 .. r0+nr-1: scatter their sticks, inverse FFT along axis 2     -> P
+//   B2  columns c0 .. c0+nc-1 (DIF positions along axis 2): inverse FFT along axis 1,
+//       x V/Ng, forward FFT along axis 1                                       -> P
+//   B3  rows: forward FFT along axis 2, gather the sticks                      -> T
+// ---------------------------------------------------------------------------
+template <typename Vg, typename Vs>
+__global__ void __launch_bounds__(256) k_plane_rows_inv(const Vg* __restrict__ t, Vs* __restrict__ pbuf, int nsticks,
+                                                        const int* __restrict__ stick_plane, AxisPlan p2, int ld,
+                                                        int n1, int n3, const Vs* __restrict__ tw2, int rpb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Vs* rows = reinterpret_cast<Vs*>(smem_raw);   // rpb rows of stride ld
+  const int z = blockIdx.x, f = blockIdx.y, r0 = blockIdx.z * rpb;
+  const int nr = min(rpb, n1 - r0);
+  for (int e = threadIdx.x; e < nr * ld; e += blockDim.x) rows[e] = vzero<Vs>();
+  __syncthreads();
+  const Vg* src = t + ((size_t)f * n3 + z) * nsticks;
+  const int lo = r0 * ld, hi = (r0 + nr) * ld;   // stick_plane = i1 LD + i2
+  for (int s = threadIdx.x; s < nsticks; s += blockDim.x) {
+    const int pos = stick_plane[s];
+    if (pos >= lo && pos < hi) rows[pos - lo] = to_s<Vs>(src[s]);
+  }
+  __syncthreads();
+  fft_lines<Vs, false, false>(rows, nr, ld, 1, p2, tw2);
+  Vs* out = pbuf + (((size_t)f * n3 + z) * n1 + r0) * ld;
+  for (int e = threadIdx.x; e < nr * ld; e += blockDim.x) out[e] = rows[e];
+}
+
+template <typename Vs>
+__global__ void __launch_bounds__(256) k_plane_cols_v(Vs* __restrict__ pbuf, AxisPlan p1, int ld, int n2, int n3,
+                                                      const Vs* __restrict__ tw1,
+                                                      const typename RealOf<Vs>::T* __restrict__ vperm, int cpb,
+                                                      int ls1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Vs* cols = reinterpret_cast<Vs*>(smem_raw);   // cpb lines of stride ls1 (odd), element i1
+  const int n1 = p1.n;
+  const int z = blockIdx.x, f = blockIdx.y, c0 = blockIdx.z * cpb;
+  const int ncl = min(cpb, n2 - c0);
+  Vs* pl = pbuf + ((size_t)f * n3 + z) * (size_t)n1 * ld;
+  const float rc = __fdividef(1.0f, (float)ncl);
+  for (int e = threadIdx.x; e < n1 * ncl; e += blockDim.x) {
+    const int i = qdiv(e, ncl, rc), c = e - i * ncl;
+    cols[c * ls1 + i] = pl[(size_t)i * ld + c0 + c];
+  }
+  __syncthreads();
+  fft_lines<Vs, false, false>(cols, ncl, ls1, 1, p1, tw1);
+  const typename RealOf<Vs>::T* vz = vperm + (size_t)z * n1 * ld;
+  for (int e = threadIdx.x; e < n1 * ncl; e += blockDim.x) {
+    const int i = qdiv(e, ncl, rc), c = e - i * ncl;
+    cols[c * ls1 + i] = cscale(cols[c * ls1 + i], vz[(size_t)i * ld + c0 + c]);
+  }
+  __syncthreads();
+  fft_lines<Vs, true, true>(cols, ncl, ls1, 1, p1, tw1);
+  for (int e = threadIdx.x; e < n1 * ncl; e += blockDim.x) {
+    const int i = qdiv(e, ncl, rc), c = e - i * ncl;
+    pl[(size_t)i * ld + c0 + c] = cols[c * ls1 + i];
+  }
+}
+
+template <typename Vg, typename Vs>
+__global__ void __launch_bounds__(256) k_plane_rows_fwd(Vg* __restrict__ t, const Vs* __restrict__ pbuf, int nsticks,
+                                                        const int* __restrict__ stick_plane, AxisPlan p2, int ld,
+                                                        int n1, int n3, const Vs* __restrict__ tw2, int rpb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Vs* rows = reinterpret_cast<Vs*>(smem_raw);
+  const int z = blockIdx.x, f = blockIdx.y, r0 = blockIdx.z * rpb;
+  const int nr = min(rpb, n1 - r0);
+  const Vs* in = pbuf + (((size_t)f * n3 + z) * n1 + r0) * ld;
+  for (int e = threadIdx.x; e < nr * ld; e += blockDim.x) rows[e] = in[e];
+  __syncthreads();
+  fft_lines<Vs, true, true>(rows, nr, ld, 1, p2, tw2);
+  Vg* dst = t + ((size_t)f * n3 + z) * nsticks;
+  const int lo = r0 * ld, hi = (r0 + nr) * ld;
+  for (int s = threadIdx.x; s < nsticks; s += blockDim.x) {
+    const int pos = stick_plane[s];
+    if (pos >= lo && pos < hi) dst[s] = to_g(rows[pos - lo]);
+  }
+}
+
+// density from the split plane: after B1, per (p3, column block) the inverse FFT along axis 1 of
+// every field it owns and the weighted sum of |psi|^2, added into the DIF-ordered planes
+__global__ void __launch_bounds__(256) k_plane_cols_density(const double2* __restrict__ pbuf, AxisPlan p1, int ld,
+                                                            int n2, int n3, const double2* __restrict__ tw1,
+                                                            const double* __restrict__ wfield, int nf, int fper,
+                                                            int cpb, int ls1, double* __restrict__ rho_perm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n1 = p1.n;
+  const int z = blockIdx.x, c0 = blockIdx.y * cpb, f0 = blockIdx.z * fper, f1 = min(nf, f0 + fper);
+  const int ncl = min(cpb, n2 - c0);
+  double2* cols = reinterpret_cast<double2*>(smem_raw);
+  double* acc = reinterpret_cast<double*>(cols + (size_t)cpb * ls1);
+  const float rc = __fdividef(1.0f, (float)ncl);
+  for (int e = threadIdx.x; e < n1 * ncl; e += blockDim.x) acc[e] = 0.0;
+  for (int f = f0; f < f1; ++f) {
+    const double2* pl = pbuf + ((size_t)f * n3 + z) * (size_t)n1 * ld;
+    for (int e = threadIdx.x; e < n1 * ncl; e += blockDim.x) {
+      const int i = qdiv(e, ncl, rc), c = e - i * ncl;
+      cols[c * ls1 + i] = pl[(size_t)i * ld + c0 + c];
+    }
+    __syncthreads();
+    fft_lines<double2, false, false>(cols, ncl, ls1, 1, p1, tw1);
+    const double w = wfield[f];
+    for (int e = threadIdx.x; e < n1 * ncl; e += blockDim.x) {
+      const int i = qdiv(e, ncl, rc), c = e - i * ncl;
+      const double2 v = cols[c * ls1 + i];
+      acc[e] = fma(w, fma(v.x, v.x, v.y * v.y), acc[e]);
+    }
+    __syncthreads();
+  }
+  double* out = rho_perm + (size_t)z * n1 * ld;
+  for (int e = threadIdx.x; e < n1 * ncl; e += blockDim.x) {
+    const int i = qdiv(e, ncl, rc), c = e - i * ncl;
+    if (acc[e] != 0.0) atomicAdd(out + (size_t)i * ld + c0 + c, acc[e]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // electron density (Eq. density): pass A as above, then per plane the inverse 2D FFT of
 // every field and the weighted sum of |psi|^2 over the fields, FP64 throughout.  The sum
 // stays in shared memory across the fields a CTA owns; the planes are in the DIF-permuted
@@ -399,11 +520,21 @@ static int pick_spb(int n3, size_t elem, int lines_per_stick, size_t target) {
   return spb;
 }
 
+// Pass B in one kernel needs the whole N1 x LD plane in shared memory; larger planes (or a
+// tuner's choice, ctx->plane_split) take the three-kernel form through the buffer P.
+static bool split_plane(const dks_ctx* ctx, size_t elem) {
+  return ctx->plane_split || (size_t)ctx->grid[0] * ctx->plane_ld * elem > 227 * 1024;
+}
+// rows (or columns) of a plane per CTA in the split form: about 64 KB of shared memory
+static int lines_per_cta(int nlines, int line_stride, size_t elem, size_t extra_per_line = 0) {
+  return std::max(1, std::min(nlines, (int)((64 * 1024) / (line_stride * elem + extra_per_line))));
+}
+
 // The three FFT passes over chunks of bands.  Vg is the storage type (global memory), Vs the
 // arithmetic type of the transforms in shared memory: the same type, or double-float (cdf) for
 // complex128 data in the emulated-FP64 mode.
 template <typename Vg, typename Vs>
-static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int nb, int chunk, Vg* tbuf,
+static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int nb, int chunk, Vg* tbuf, void* pbufv,
                      double shift, double scale, cudaStream_t st) {
   const bool fp64 = sizeof(Vg) == sizeof(double2);
   const bool df = !std::is_same<Vg, Vs>::value;
@@ -431,7 +562,19 @@ static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int n
   const int tb_plane =
       ctx->plane_threads > 0 ? ctx->plane_threads : std::min(512, std::max(128, (nbf / 2 + 31) / 32 * 32));
   DKS_TRY(set_smem<Vs>((const void*)k_stick_inverse<Vg, Vs>, sm_a));
-  DKS_TRY(set_smem<Vs>((const void*)k_plane<Vg, Vs>, sm_b));
+  const bool split = split_plane(ctx, sizeof(Vs));
+  Vs* pbuf = reinterpret_cast<Vs*>(pbufv);
+  const int n1 = ctx->grid[0], n2 = ctx->grid[1], ls1 = n1 | 1;
+  const int rpb = lines_per_cta(n1, ld, sizeof(Vs)), cpb = lines_per_cta(n2, ls1, sizeof(Vs));
+  const size_t sm_r = (size_t)rpb * ld * sizeof(Vs), sm_cv = (size_t)cpb * ls1 * sizeof(Vs);
+  if (split) {
+    if (!pbuf) return fail(DKS_ERR_INVALID_ARG, "split plane FFT without its buffer");
+    DKS_TRY(set_smem<Vs>((const void*)k_plane_rows_inv<Vg, Vs>, sm_r));
+    DKS_TRY(set_smem<Vs>((const void*)k_plane_cols_v<Vs>, sm_cv));
+    DKS_TRY(set_smem<Vs>((const void*)k_plane_rows_fwd<Vg, Vs>, sm_r));
+  } else {
+    DKS_TRY(set_smem<Vs>((const void*)k_plane<Vg, Vs>, sm_b));
+  }
   DKS_TRY(set_smem<Vs>(nc == 4 ? (const void*)k_stick_forward<Vg, Vs> : (const void*)k_stick_forward_ks<Vg, Vs>,
                        sm_c));
   const int cat32 = fp64 ? 0 : kProf32;
@@ -451,9 +594,20 @@ static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int n
       const double nn = (double)ctx->grid[0] * ctx->grid[1];
       Prof pr(P_PLANE + cat32, st, 2.0 * tb + (double)ctx->ng * es / 2,
               nf * n3 * (10.0 * nn * std::log2(nn) + 2.0 * nn));
-      dim3 gb(n3, nc * nbc);
-      k_plane<Vg, Vs><<<gb, tb_plane, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0], ctx->plan[1],
-                                                  ld, n3, tw1, tw2, vp);
+      if (split) {
+        pr.count(2);
+        const int nfi = nc * nbc;
+        const dim3 g1(n3, nfi, (n1 + rpb - 1) / rpb), g2(n3, nfi, (n2 + cpb - 1) / cpb);
+        k_plane_rows_inv<Vg, Vs><<<g1, 256, sm_r, st>>>(tbuf, pbuf, kp.nsticks, kp.stick_plane, ctx->plan[1], ld, n1,
+                                                        n3, tw2, rpb);
+        k_plane_cols_v<Vs><<<g2, 256, sm_cv, st>>>(pbuf, ctx->plan[0], ld, n2, n3, tw1, vp, cpb, ls1);
+        k_plane_rows_fwd<Vg, Vs><<<g1, 256, sm_r, st>>>(tbuf, pbuf, kp.nsticks, kp.stick_plane, ctx->plan[1], ld, n1,
+                                                        n3, tw2, rpb);
+      } else {
+        dim3 gb(n3, nc * nbc);
+        k_plane<Vg, Vs><<<gb, tb_plane, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0], ctx->plan[1],
+                                                    ld, n3, tw1, tw2, vp);
+      }
     }
     {
       Prof pr(P_STICK_FWD + cat32, st, tb + 2.0 * nf * npw * es + 24.0 * npw,
@@ -485,14 +639,19 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
   const int ncol = nb * nc / 2;   // projector columns x~: two-spinors of 2 npw rows
   const size_t zp_elems = (size_t)ctx->nproj * ncol;
   const size_t field_elems = (size_t)kp.nsticks * n3;
+  // split pass B: one N1 x LD plane per (field, p3) in the buffer P (the arithmetic type of the
+  // transforms has the size of V: complex128 and double-float pairs are both 16 bytes)
+  const size_t plane_elems = split_plane(ctx, sizeof(V)) ? (size_t)n3 * ctx->grid[0] * ctx->plane_ld : 0;
   // chunk of bands whose intermediates stay within the L2-resident budget
-  int chunk = (int)std::max<size_t>(1, ctx->chunk_budget / (nc * field_elems * sizeof(V)));
+  int chunk = (int)std::max<size_t>(1, ctx->chunk_budget / (nc * (field_elems + plane_elems) * sizeof(V)));
   chunk = std::min(chunk, nb);
-  const size_t need = zp_elems * sizeof(double2) + 256 + (ctx->has_v ? nc * chunk * field_elems * sizeof(V) : 0);
-  DKS_TRY(grow(ex.ws_h, need));
+  const size_t zp_bytes = ((zp_elems * sizeof(double2) + 255) / 256) * 256;
+  const size_t t_bytes = ctx->has_v ? ((nc * chunk * field_elems * sizeof(V) + 255) / 256) * 256 : 0;
+  const size_t p_bytes = ctx->has_v ? nc * chunk * plane_elems * sizeof(V) : 0;
+  DKS_TRY(grow(ex.ws_h, zp_bytes + t_bytes + p_bytes + 256));
   double2* zp = reinterpret_cast<double2*>(ex.ws_h.ptr);
-  V* tbuf = reinterpret_cast<V*>(reinterpret_cast<char*>(ex.ws_h.ptr) +
-                                 ((zp_elems * sizeof(double2) + 255) / 256) * 256);
+  V* tbuf = reinterpret_cast<V*>(reinterpret_cast<char*>(ex.ws_h.ptr) + zp_bytes);
+  void* pbuf = p_bytes ? reinterpret_cast<char*>(ex.ws_h.ptr) + zp_bytes + t_bytes : nullptr;
   const V* bt = nullptr;
   if (ctx->nproj) {
     bt = fp64 ? reinterpret_cast<const V*>(kp.bt64) : reinterpret_cast<const V*>(kp.bt32);
@@ -508,11 +667,11 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
     bool done = false;
     if constexpr (std::is_same<V, double2>::value) {
       if (ex.df_gemm) {
-        DKS_TRY((fft_local<double2, cdf>(ctx, kp, x, out, nb, chunk, tbuf, shift, scale, st)));
+        DKS_TRY((fft_local<double2, cdf>(ctx, kp, x, out, nb, chunk, tbuf, pbuf, shift, scale, st)));
         done = true;
       }
     }
-    if (!done) DKS_TRY((fft_local<V, V>(ctx, kp, x, out, nb, chunk, tbuf, shift, scale, st)));
+    if (!done) DKS_TRY((fft_local<V, V>(ctx, kp, x, out, nb, chunk, tbuf, pbuf, shift, scale, st)));
   } else if (nc == 4) {
     const int blocks = std::max(1, std::min(ctx->num_sms * 8, (int)(((size_t)nb * npw + 255) / 256)));
     Prof pr(P_DIRAC + (fp64 ? 0 : kProf32), st, 8.0 * nb * npw * sizeof(V) + 24.0 * npw, 64.0 * nb * npw);
@@ -545,15 +704,25 @@ int density_accumulate(dks_ctx* ctx, int ik, const double2* x, int nb, const dou
   const size_t field_elems = (size_t)kp.nsticks * n3;
   const size_t np = (size_t)n1 * ld;
   const size_t sm_b = np * (sizeof(double2) + sizeof(double));
-  if (sm_b > 227 * 1024) return fail(DKS_ERR_UNSUPPORTED, "density: N1*N2 plane exceeds the shared-memory limit");
-  int chunk = (int)std::max<size_t>(1, ctx->chunk_budget / (nc * field_elems * sizeof(double2)));
+  // one plane per CTA (the plane and its |psi|^2 sum in shared memory), or the split form: rows
+  // by k_plane_rows_inv into the buffer P, then columns by k_plane_cols_density
+  const bool split = ctx->plane_split || sm_b > 227 * 1024;
+  const size_t plane_elems = split ? (size_t)n3 * np : 0;
+  int chunk = (int)std::max<size_t>(1, ctx->chunk_budget / (nc * (field_elems + plane_elems) * sizeof(double2)));
   chunk = std::min(chunk, nb);
   const size_t perm_bytes = ((n3 * np * sizeof(double) + 255) / 256) * 256;
   const size_t w_bytes = ((nc * (size_t)nb * sizeof(double) + 255) / 256) * 256;
-  DKS_TRY(grow(ex.ws_h, perm_bytes + w_bytes + nc * (size_t)chunk * field_elems * sizeof(double2)));
+  const size_t t_bytes = ((nc * (size_t)chunk * field_elems * sizeof(double2) + 255) / 256) * 256;
+  DKS_TRY(grow(ex.ws_h, perm_bytes + w_bytes + t_bytes + nc * (size_t)chunk * plane_elems * sizeof(double2)));
   double* rho_perm = reinterpret_cast<double*>(ex.ws_h.ptr);
   double* wf = reinterpret_cast<double*>(reinterpret_cast<char*>(ex.ws_h.ptr) + perm_bytes);
   double2* tbuf = reinterpret_cast<double2*>(reinterpret_cast<char*>(ex.ws_h.ptr) + perm_bytes + w_bytes);
+  double2* pbuf = reinterpret_cast<double2*>(reinterpret_cast<char*>(ex.ws_h.ptr) + perm_bytes + w_bytes + t_bytes);
+  const int ls1 = n1 | 1;
+  const int rpb = lines_per_cta(n1, ld, sizeof(double2));
+  const int cpb = lines_per_cta(n2, ls1, sizeof(double2), (size_t)n1 * sizeof(double));
+  const size_t sm_r = (size_t)rpb * ld * sizeof(double2);
+  const size_t sm_cd = (size_t)cpb * (ls1 * sizeof(double2) + n1 * sizeof(double));
   std::vector<double> wh((size_t)nc * nb);
   for (int b = 0; b < nb; ++b)
     for (int c = 0; c < nc; ++c) wh[(size_t)b * nc + c] = occ[b];
@@ -563,7 +732,12 @@ int density_accumulate(dks_ctx* ctx, int ik, const double2* x, int nb, const dou
   const int spb_a = pick_spb(ls, sizeof(double2), 1, 32 * 1024);
   const size_t sm_a = (size_t)spb_a * ls * sizeof(double2);
   DKS_TRY(set_smem<double2>((const void*)k_stick_inverse<double2, double2>, sm_a));
-  DKS_TRY(set_smem<double2>((const void*)k_plane_density, sm_b));
+  if (split) {
+    DKS_TRY(set_smem<double2>((const void*)k_plane_rows_inv<double2, double2>, sm_r));
+    DKS_TRY(set_smem<double2>((const void*)k_plane_cols_density, sm_cd));
+  } else {
+    DKS_TRY(set_smem<double2>((const void*)k_plane_density, sm_b));
+  }
   int rmin = 8;
   for (int a = 0; a < 2; ++a)
     for (int i = 0; i < ctx->plan[a].nst; ++i) rmin = std::min(rmin, ctx->plan[a].radix[i]);
@@ -586,10 +760,20 @@ int density_accumulate(dks_ctx* ctx, int ik, const double2* x, int nb, const dou
       const int fper = (nf + nsplit - 1) / nsplit;
       const double nn = (double)n1 * n2;
       Prof pr(P_SCF, st, tb + 2.0 * n3 * np * sizeof(double), nf * n3 * (5.0 * nn * std::log2(nn) + 3.0 * nn));
-      dim3 gb(n3, (nf + fper - 1) / fper);
-      k_plane_density<<<gb, tb_plane, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0], ctx->plan[1], ld,
-                                                  n3, ctx->tw64[0], ctx->tw64[1], wf + (size_t)b0 * nc, nf, fper,
-                                                  rho_perm);
+      if (split) {
+        pr.count(1);
+        const dim3 g1(n3, nf, (n1 + rpb - 1) / rpb);
+        k_plane_rows_inv<double2, double2><<<g1, 256, sm_r, st>>>(tbuf, pbuf, kp.nsticks, kp.stick_plane,
+                                                                  ctx->plan[1], ld, n1, n3, ctx->tw64[1], rpb);
+        const dim3 g2(n3, (n2 + cpb - 1) / cpb, (nf + fper - 1) / fper);
+        k_plane_cols_density<<<g2, 256, sm_cd, st>>>(pbuf, ctx->plan[0], ld, n2, n3, ctx->tw64[0],
+                                                     wf + (size_t)b0 * nc, nf, fper, cpb, ls1, rho_perm);
+      } else {
+        dim3 gb(n3, (nf + fper - 1) / fper);
+        k_plane_density<<<gb, tb_plane, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0], ctx->plan[1], ld,
+                                                    n3, ctx->tw64[0], ctx->tw64[1], wf + (size_t)b0 * nc, nf, fper,
+                                                    rho_perm);
+      }
     }
   }
   {

@@ -90,20 +90,20 @@ def test_tuning_entry_points_and_cache_without_gpu(tmp_path):
     import paper_1211_1446_gb300 as P
     lib = P.load_library()
     assert lib.dks_autotune(None, 0, 8, 1, None, None) == -1
-    assert lib.dks_tune_set(None, 64 << 20, 0) == -1
-    chunk, thr = C.c_longlong(), C.c_int()
-    assert lib.dks_tune_get(None, C.byref(chunk), C.byref(thr)) == -1
+    assert lib.dks_tune_set(None, 64 << 20, 0, 0) == -1
+    chunk, thr, spl = C.c_longlong(), C.c_int(), C.c_int()
+    assert lib.dks_tune_get(None, C.byref(chunk), C.byref(thr), C.byref(spl)) == -1
     rep = P.TuneReport()
-    assert C.sizeof(rep) == 8 + 16 * 8 + 16 * 4 + 16 * 8
+    assert C.sizeof(rep) == 8 + 32 * 8 + 32 * 4 + 32 * 4 + 32 * 8
     path = str(tmp_path / "tune.json")
     k1 = P.tuning_key((48, 48, 56), 57419, 4, 40, 1, "GB300")
     k2 = P.tuning_key((48, 48, 56), 57419, 4, 40, 0, "GB300")
     assert k1 != k2 and P.tuning_cache_lookup(path, k1) is None
-    P.tuning_cache_store(path, k1, dict(chunk_bytes=32 << 20, plane_threads=256))
-    P.tuning_cache_store(path, k2, dict(chunk_bytes=64 << 20, plane_threads=0))
-    assert P.tuning_cache_lookup(path, k1) == dict(chunk_bytes=32 << 20, plane_threads=256)
-    assert P.tuning_cache_lookup(path, k2) == dict(chunk_bytes=64 << 20, plane_threads=0)
+    P.tuning_cache_store(path, k1, dict(chunk_bytes=32 << 20, plane_threads=256, plane_split=0))
+    P.tuning_cache_store(path, k2, dict(chunk_bytes=64 << 20, plane_threads=0, plane_split=1))
+    assert P.tuning_cache_lookup(path, k1) == dict(chunk_bytes=32 << 20, plane_threads=256, plane_split=0)
+    assert P.tuning_cache_lookup(path, k2) == dict(chunk_bytes=64 << 20, plane_threads=0, plane_split=1)
     open(path, "w").write("{not json")
     assert P.tuning_cache_lookup(path, k1) is None
-    P.tuning_cache_store(path, k1, dict(chunk_bytes=16 << 20, plane_threads=128))
-    assert P.tuning_cache_lookup(path, k1) == dict(chunk_bytes=16 << 20, plane_threads=128)
+    P.tuning_cache_store(path, k1, dict(chunk_bytes=16 << 20, plane_threads=128, plane_split=0))
+    assert P.tuning_cache_lookup(path, k1) == dict(chunk_bytes=16 << 20, plane_threads=128, plane_split=0)
