@@ -200,60 +200,3 @@ def test_apply_h_ksso_full_dimer(dt):
     ctx.apply_H(0, xd, hx, emulated=(dt == "df"))
     torch.cuda.synchronize()
     assert rel_err(hx.cpu().numpy(), ref) < (2e-6 if dt == "c64" else 1e-12)
-
-
-def test_autotune_changes_time_not_results(tmp_path):
-    """dks_autotune times its candidates (4 chunk budgets x {one-kernel plane FFT with 4 CTA sizes,
-    split plane FFT}), keeps one of them, and H' x is the same under every choice (every line
-    transform is the same butterfly arithmetic, whichever kernel and thread runs it); the JSON
-    cache returns the stored choice."""
-    torch = gpu()
-    import paper_1211_1446_gb300 as P
-    wl, ctx, hop, q = make_pair("dimer", ecut=4.0)
-    npw = ctx.npw(0)
-    rng = np.random.default_rng(8)
-    x = rng.standard_normal((6, 4, npw)) + 1j * rng.standard_normal((6, 4, npw))
-    want = hop(x)
-    cache = str(tmp_path / "tune.json")
-    r = ctx.autotune(0, nb=8, prec=P.PREC_FP32, cache=cache)
-    assert not r["cached"] and len(r["candidates"]) == 20
-    assert all(c["ms"] > 0 for c in r["candidates"])
-    assert ctx.tuning() == dict(chunk_bytes=r["chunk_bytes"], plane_threads=r["plane_threads"],
-                                plane_split=r["plane_split"])
-    xd = to_dev(x, torch.complex128)
-    for emulated in (False, True):
-        outs = []
-        for chunk, thr, split in [(r["chunk_bytes"], r["plane_threads"], r["plane_split"]), (16 << 20, 128, 0),
-                                  (128 << 20, 512, 0), (64 << 20, 0, 1), (16 << 20, 0, 1)]:
-            ctx.set_tuning(chunk, thr, split)
-            hx = torch.empty_like(xd)
-            ctx.apply_H(0, xd, hx, emulated=emulated)
-            outs.append(hx.cpu().numpy())
-        assert rel_err(outs[0], want) < 1e-11
-        for o in outs[1:]:
-            assert rel_err(o, outs[0]) < 1e-14                 # the same line transforms
-    r2 = ctx.autotune(0, nb=8, prec=P.PREC_FP32, cache=cache)
-    assert r2["cached"] and all(r2[k] == r[k] for k in ("chunk_bytes", "plane_threads", "plane_split"))
-
-
-def test_plane_too_large_for_one_cta():
-    """A 120 x 120 plane of complex128 (232 KB) exceeds one CTA's shared memory: H' runs the split
-    plane FFT in FP64 and double-float and the one-kernel form in FP32 (116 KB), the density the
-    split form; all against the oracle."""
-    torch = gpu()
-    from oracle import scf as oscf
-    wl, ctx, hop, q = make_pair("cubic", ecut=4.0, grid=(120, 120, 10))
-    npw = ctx.npw(0)
-    rng = np.random.default_rng(12)
-    x = rng.standard_normal((3, 4, npw)) + 1j * rng.standard_normal((3, 4, npw))
-    want = hop(x)
-    for dt, emu, tol in ((torch.complex128, False, 1e-11), (torch.complex128, True, 1e-11), (torch.complex64, False, 2e-6)):
-        xd = to_dev(x, dt)
-        hx = torch.empty_like(xd)
-        ctx.apply_H(0, xd, hx, emulated=emu)
-        assert rel_err(hx.cpu().numpy(), want) < tol, (dt, emu)
-    xn = x / np.linalg.norm(x.reshape(3, -1), axis=1)[:, None, None]
-    rho = torch.zeros(wl.grid, dtype=torch.float64, device="cuda")
-    ctx.density(0, to_dev(xn, torch.complex128), [1.0, 0.5, 0.25], rho)
-    dens = oscf.density(xn, ctx.basis(0), wl.grid, wl.volume, [1.0, 0.5, 0.25])
-    assert rel_err(rho.cpu().numpy(), dens) < 1e-11

@@ -32,12 +32,9 @@ def _unit_block(nb, nc, npw, seed):
     ("cubic", dict(), "dks", 2),
     ("dimer", dict(), "dks", 32),            # the bench workload: 32 bands, several chunks of planes
 ])
-@pytest.mark.parametrize("split", [0, 1])
-def test_density_matches_oracle(name, kw, model, nb, split):
-    """One-kernel and split (row / column kernels) plane transforms."""
+def test_density_matches_oracle(name, kw, model, nb):
     torch = gpu()
     wl, ctx, hop, q = make_pair(name, model=model, **kw)
-    ctx.set_tuning(64 << 20, 0, split)
     m = ctx.basis(0)
     nc = ctx.ncomp
     x = _unit_block(nb, nc, len(m), 11)

@@ -238,25 +238,3 @@ def test_multi_k_concurrent_matches_serial_and_dense():
     for ik in (0, 3):                                            # Kramers pairs at TRIM
         lam = runs[0][ik]
         assert np.abs(lam[0::2] - lam[1::2]).max() < 1e-7
-
-
-@pytest.mark.parametrize("mode", [0, 1])
-def test_band_blocks_with_deflation(mode):
-    """20 pairs in band blocks of 8 wanted + 4 buffer columns (FP64 and mixed precision): the
-    eigenvalues are the dense ones, the locked vectors orthonormal and eigenvectors of H'."""
-    torch = gpu()
-    import paper_1211_1446_gb300 as P
-    import oracle.basis as ob
-    wl = W.make("small", ecut=4.0)
-    ctx = P.Context.from_workload(wl)
-    n, blk, nbuf = 20, 8, 4
-    m, q = ob.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
-    x = torch.from_numpy(W.start_block(ctx.npw(0), n + nbuf, wl.seed)).cuda()
-    lam, rep, rc = ctx.solve([x], n, nbuf=nbuf, tol=1e-7, mode=mode, block=blk, check=False)
-    assert rc == 0, rep["message"]
-    h = oop.dense_hamiltonian(wl, m, q)
-    ref, _, _ = olb.dense_eigs(h, wl.c, n)
-    assert np.abs(lam[0] - ref).max() < 1e-8
-    xv = x[:n].reshape(n, -1).cpu().numpy().T
-    assert np.abs(xv.conj().T @ xv - np.eye(n)).max() < 1e-8
-    assert np.abs(h @ xv - xv * lam[0][None, :]).max() < 1e-6
