@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -155,6 +156,15 @@ inline double rr_flops(int m, int n) {
   const double md = m, nd = n;
   return 8.0 * (md * md * md * (1.0 / 6.0 + 1.0 + 2.0 / 3.0) + 1.5 * md * md * nd);
 }
+
+// NVTX range around a host scope (solves, phases, SCF iterations), for timeline tools; without
+// a tool attached the calls return at once
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 int grow(Workspace& w, size_t bytes);
 void release(Workspace& w);

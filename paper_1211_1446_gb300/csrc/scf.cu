@@ -701,6 +701,7 @@ int dks_scf(dks_ctx* ctx, int nev, const dks_scf_opts* o, double* eig, void* con
     DKS_TRY(density_of(rin));
     final_rc = DKS_ERR_NOT_CONVERGED;
     for (int it = 1; it <= o->max_iter; ++it) {
+      NvtxRange nvtx("SCF iteration");
       DKS_TRY(hxc_potential(ctx, rin, vtot, cg, small, st));
       {
         Prof pr(P_SCF, st, 24.0 * ng, ng);

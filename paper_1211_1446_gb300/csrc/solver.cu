@@ -171,6 +171,8 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
   // q: nq locked vectors of earlier band blocks (deflation), projected out of the filtered start
   // block and of every filtered correction Y
   df = df && sizeof(V) == sizeof(double2);
+  NvtxRange nvtx(sizeof(V) == sizeof(float2) ? "LOBPCG-F FP32 phase" : df ? "LOBPCG-F FP64 phase (double-float)"
+                                                                         : "LOBPCG-F FP64 phase");
   ex.df_gemm = df;   // projector contractions inside apply_h follow the phase's arithmetic
   const KPoint& kp = ctx->k[ik];
   const int nc = ctx->ncomp;
@@ -673,6 +675,7 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
     }
     for (int t = next.fetch_add(1); t < ctx->nk; t = next.fetch_add(1)) {
       const int ik = order[t];
+      NvtxRange nvtx_k("k-point solve");
       auto run = [&]() -> int {
         const KPoint& kp = ctx->k[ik];
         const int nv = opts.nev_k ? opts.nev_k[ik] : nev;
