@@ -573,3 +573,14 @@ def test_blocked_lobpcgf_one_block_is_algorithm_1():
     a = lb.lobpcgf(op.MatrixFreeH(wl, m, q), q, x0, 8, cs, om, tol=1e-8)
     b = lb.lobpcgf_blocked(op.MatrixFreeH(wl, m, q), q, x0, 8, 8, cs, om, tol=1e-8)
     assert a.iterations == b.iterations and np.abs(a.lam - b.lam).max() < 1e-13
+
+
+def test_blocked_lobpcg_ksso_matches_dense():
+    """Band blocks on the two-component KSSO operator (standard LOBPCG, no filter): the lowest
+    dense eigenvalues of the KSSO matrix."""
+    wl, m, q = _setup("small", ecut=4.0)
+    hop = op.MatrixFreeKSSO(wl, m, q)
+    x0 = W.start_block(len(m), 30, wl.seed, ncomp=2)
+    res = lb.lobpcgf_blocked(hop, q, x0, 16, 6, 0.0, 1.0, nbuf=2, tol=1e-8, use_filter=False)
+    ref = np.linalg.eigvalsh(op.dense_hamiltonian_ksso(wl, m, q))[:16]
+    assert res.converged and np.abs(res.lam - ref).max() < 1e-9
