@@ -242,3 +242,30 @@ def random_block(npw: int, nb: int, seed: int, ncomp: int = 4) -> np.ndarray:
     """Generic seeded complex normal block [band, comp, pw] for operator tests."""
     rng = np.random.Generator(np.random.PCG64([seed, 77, nb, npw]))
     return (rng.standard_normal((nb, ncomp, npw)) + 1j * rng.standard_normal((nb, ncomp, npw))) / math.sqrt(2.0)
+
+
+def save(wl: Workload, path: str) -> None:
+    """Freeze a workload -- every generated number, the potential grid included -- into one .npz
+    file that both sides can read back with load()."""
+    fields = {f.name: getattr(wl, f.name) for f in dataclasses.fields(Workload)}
+    arrays = {k: np.asarray(v) for k, v in fields.items()}
+    np.savez_compressed(path, **arrays)
+
+
+def load(path: str) -> Workload:
+    """The workload frozen by save()."""
+    with np.load(path, allow_pickle=False) as f:
+        kw = {}
+        for fld in dataclasses.fields(Workload):
+            v = f[fld.name]
+            if fld.name == "name":
+                kw[fld.name] = str(v)
+            elif fld.name == "grid":
+                kw[fld.name] = tuple(int(x) for x in v)
+            elif fld.name in ("c",):
+                kw[fld.name] = float(v)
+            elif fld.name in ("nbuf", "seed"):
+                kw[fld.name] = int(v)
+            else:
+                kw[fld.name] = np.array(v)
+    return Workload(**kw)
