@@ -148,6 +148,57 @@ def cpu_oracle_sample(wl, nev, n_iter_ref, budget_s=20.0):
     return nev / full, cores, sample, full
 
 
+def cpu_configs_section(n_iter_ref, gpu_layered_happ=None):
+    """The CPU baselines of the other configurations, oracle as it stands, on the host cores:
+    dense zheevd of the cubic cell (515 planewaves) and of the dimer at Ecut 2 Ha (1295
+    planewaves); the oracle's Algorithm 1 on the cubic cell; and, for one k-point of the layered
+    crystal (about 40,000 planewaves), the time of one H' application per column, extrapolated to
+    a solve by 3 applications per column and iteration over n_iter_ref iterations (marked as
+    extrapolated).  About 30 s."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import basis, lobpcgf, operator
+    out = {"cores": len(os.sched_getaffinity(0))}
+    wl = W.make("cubic")
+    m, q = basis.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
+    h = operator.dense_hamiltonian(wl, m, q)
+    t0 = time.perf_counter()
+    lobpcgf.dense_eigs(h, wl.c, 8)
+    out["cubic_dense_zheevd_s"] = time.perf_counter() - t0
+    out["cubic_dense_dim"] = int(h.shape[0])
+    cs, om = operator.filter_constants(wl, q)
+    t0 = time.perf_counter()
+    r = lobpcgf.lobpcgf(operator.MatrixFreeH(wl, m, q), q, W.start_block(len(q), 8, wl.seed), 8, cs, om, tol=TOL)
+    dt = time.perf_counter() - t0
+    out["cubic_lobpcgf_s"] = dt
+    out["cubic_lobpcgf_iterations"] = r.iterations
+    out["cubic_lobpcgf_eigenpairs_per_s"] = 8 / dt
+    wl = W.make("dimer", ecut=2.0)
+    m, q = basis.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
+    h = operator.dense_hamiltonian(wl, m, q)
+    t0 = time.perf_counter()
+    lobpcgf.dense_eigs(h, wl.c, 32)
+    out["dimer_ecut2_dense_zheevd_s"] = time.perf_counter() - t0
+    out["dimer_ecut2_dense_dim"] = int(h.shape[0])
+    del h
+    wl = W.make("layered")
+    m, q = basis.sphere(wl.lattice, wl.grid, wl.kfrac[0], wl.ecut_k[0])
+    hop = operator.MatrixFreeH(wl, m, q)
+    x = W.random_block(len(q), 4, wl.seed)
+    hop(x[:1])                                                      # first-call setup
+    t0 = time.perf_counter()
+    hop(x)
+    per_col = (time.perf_counter() - t0) / 4
+    nev0 = int(wl.nev_k[0])
+    out["layered_k0_npw"] = len(q)
+    out["layered_k0_hx_s_per_column"] = per_col
+    out["layered_k0_solve_s_extrapolated"] = per_col * 3 * nev0 * n_iter_ref
+    out["layered_k0_note"] = (f"extrapolated: {per_col:.3f} s per column x 3 applications x {nev0} columns x "
+                              f"{n_iter_ref} iterations (every column active)")
+    return out
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -614,6 +665,10 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, cores, sample, full = cpu_oracle_sample(wl, NEV, acc["iterations"])
         cpu = {"value": v, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle", "sample": sample}
+        try:
+            cpu["other_configs"] = cpu_configs_section(acc["iterations"])
+        except Exception as exc:                                  # a baseline must not cost the bench line
+            cpu["other_configs"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     line = {"metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
