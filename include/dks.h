@@ -115,6 +115,15 @@ void dks_destroy(dks_ctx* ctx);
  * taking a ctx then works on columns of dks_ncomp(ctx) x npw elements. */
 int dks_create_model(const dks_cell* cell, double ecut, const dks_potentials* pot,
                      const dks_projectors* proj, int model, dks_ctx** out);
+/* The FFT plan of one grid axis of length n (host only, no device needed; exposed so that the
+ * plan can be checked): nst passes of the radices radix[0..nst-1] (each of 2, 3, 4, 5, 6, 7, 8,
+ * product n, fewest passes), run as decimation-in-frequency passes in this order for the inverse
+ * transform.  pos (int[n], or NULL): the position at which the DIF passes leave frequency k
+ * (mixed-radix digit reversal; the real-space planes and V live in this order on the device).
+ * radix needs room for 8 entries.  Errors: INVALID_ARG, UNSUPPORTED (n > 256 or a prime factor
+ * above 7). */
+int dks_fft_plan(int n, int* nst, int* radix, int* pos);
+
 /* Components per column: 4 (DKS) or 2 (KSSO). */
 int dks_ncomp(const dks_ctx* ctx, int* ncomp);
 

@@ -89,7 +89,7 @@ EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dk
            "dks_rayleigh_ritz_static", "dks_gram_hermitian", "dks_kinetic_balance", "dks_create_model",
            "dks_ncomp", "dks_density", "dks_hxc", "dks_set_potential", "dks_mixer_create", "dks_mix",
            "dks_mixer_destroy", "dks_scf_opts_default", "dks_scf", "dks_update_potential",
-           "dks_density_residual", "dks_autotune", "dks_tune_get", "dks_tune_set"]
+           "dks_density_residual", "dks_autotune", "dks_tune_get", "dks_tune_set", "dks_fft_plan"]
 
 _lib = None
 
@@ -141,6 +141,7 @@ def load_library(path: str = LIB_PATH):
     lib.dks_autotune.argtypes = [vp, i, i, i, vp, C.POINTER(TuneReport)]
     lib.dks_tune_get.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(i), C.POINTER(i)]
     lib.dks_tune_set.argtypes = [vp, C.c_longlong, i, i]
+    lib.dks_fft_plan.argtypes = [i, C.POINTER(i), C.POINTER(i), C.POINTER(i)]
     lib.dks_strerror.argtypes = [i]
     lib.dks_strerror.restype = C.c_char_p
     lib.dks_last_error.argtypes = []
@@ -481,6 +482,16 @@ class Context:
                       history=list(rep.res_history[:rep.hist_len]),
                       message=_lib.dks_last_error().decode() if rc else "")
         return out, report, rc
+
+
+def fft_plan(n):
+    """dks_fft_plan: (radices of the passes, DIF position of every frequency) of an axis of length n."""
+    lib = load_library()
+    nst = C.c_int()
+    radix = (C.c_int * 8)()
+    pos = (C.c_int * max(1, int(n)))()
+    _check(lib.dks_fft_plan(int(n), C.byref(nst), radix, pos))
+    return [int(radix[i]) for i in range(nst.value)], [int(pos[k]) for k in range(int(n))]
 
 
 def tuning_key(grid, npw, ncomp, nb, prec, device):

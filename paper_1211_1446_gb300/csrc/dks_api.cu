@@ -462,6 +462,19 @@ int dks_create(const dks_cell* cell, double ecut, const dks_potentials* pot, con
 
 void dks_destroy(dks_ctx* ctx) { free_ctx(ctx); }
 
+int dks_fft_plan(int n, int* nst, int* radix, int* pos) {
+  if (!nst || !radix) return fail(DKS_ERR_INVALID_ARG, "dks_fft_plan: NULL output");
+  AxisPlan p;
+  if (!make_axis_plan(n, &p)) return fail(DKS_ERR_UNSUPPORTED, "axis length must be <= 256 with factors 2, 3, 5, 7");
+  *nst = p.nst;
+  for (int i = 0; i < p.nst; ++i) radix[i] = p.radix[i];
+  if (pos) {
+    const std::vector<int> v = dif_positions(p);
+    for (int k = 0; k < n; ++k) pos[k] = v[k];
+  }
+  return DKS_OK;
+}
+
 int dks_create_model(const dks_cell* cell, double ecut, const dks_potentials* pot, const dks_projectors* proj,
                      int model, dks_ctx** out) {
   if (model != DKS_MODEL_DKS && model != DKS_MODEL_KSSO) {

@@ -4,6 +4,9 @@ import ctypes
 import os
 import re
 
+import numpy as np
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -107,3 +110,55 @@ def test_tuning_entry_points_and_cache_without_gpu(tmp_path):
     assert P.tuning_cache_lookup(path, k1) is None
     P.tuning_cache_store(path, k1, dict(chunk_bytes=16 << 20, plane_threads=128, plane_split=0))
     assert P.tuning_cache_lookup(path, k1) == dict(chunk_bytes=16 << 20, plane_threads=128, plane_split=0)
+
+
+def _min_passes(n, memo={1: 0}):
+    if n not in memo:
+        memo[n] = min([1 + _min_passes(n // r) for r in (2, 3, 4, 5, 6, 7, 8) if n % r == 0] or [10 ** 6])
+    return memo[n]
+
+
+def _dif_inverse(x, radices):
+    """Mixed-radix decimation-in-frequency passes in the given order (inverse sign): pass s
+    combines elements j + r S (r < R) of every block of length L_s, S = L_s / R, with a size-R
+    DFT and then multiplies output m by exp(+2 pi i j m / L_s)."""
+    x = np.array(x, dtype=np.complex128)
+    n, blk = len(x), len(x)
+    for r in radices:
+        sub = blk // r
+        out = x.copy()
+        w = np.exp(2j * np.pi * np.outer(np.arange(r), np.arange(r)) / r)
+        for b in range(0, n, blk):
+            for j in range(sub):
+                v = w @ x[b + j + sub * np.arange(r)]
+                out[b + j + sub * np.arange(r)] = v * np.exp(2j * np.pi * j * np.arange(r) / blk)
+        x, blk = out, sub
+    return x
+
+
+def test_fft_plans_without_gpu():
+    """Every axis length 1..256 with prime factors 2, 3, 5, 7 gets a plan whose radices multiply to
+    n in the fewest passes (brute force over factorisations), and running its DIF passes leaves
+    frequency k of the inverse DFT at the reported position pos[k]; other lengths are refused."""
+    import paper_1211_1446_gb300 as P
+    rng = np.random.default_rng(3)
+    for n in range(1, 257):
+        m = n
+        for p in (2, 3, 5, 7):
+            while m % p == 0:
+                m //= p
+        if m != 1:
+            with pytest.raises(P.DKSError) as e:
+                P.fft_plan(n)
+            assert e.value.code == -9
+            continue
+        radices, pos = P.fft_plan(n)
+        assert all(r in (2, 3, 4, 5, 6, 7, 8) for r in radices)
+        assert int(np.prod(radices)) == n and len(radices) == _min_passes(n)
+        assert sorted(pos) == list(range(n))
+        x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        want = np.fft.ifft(x) * n                                   # sum_t x_t exp(+2 pi i k t / n)
+        got = _dif_inverse(x, radices)
+        assert np.abs(got[pos] - want).max() < 1e-9 * max(1.0, np.abs(want).max())
+    with pytest.raises(P.DKSError):
+        P.fft_plan(257)
