@@ -36,3 +36,23 @@ def rel_err(a, b):
     a = np.asarray(a)
     b = np.asarray(b)
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def cluster_sines(lam_ref, u_ref, x, gap=1e-6):
+    """Largest principal-angle sine between span(u_ref[:, cluster]) and span(x[:, cluster]) over the
+    clusters of lam_ref (eigenvalues closer than `gap` form one cluster, Kramers pairs included);
+    a cluster that reaches the last column may continue beyond it and is left out.  u_ref and x
+    are column matrices with orthonormal columns."""
+    lam_ref = np.asarray(lam_ref)
+    n = len(lam_ref)
+    worst = 0.0
+    i = 0
+    while i < n:
+        j = i + 1
+        while j < n and lam_ref[j] - lam_ref[j - 1] < gap:
+            j += 1
+        if j < n:
+            s = np.linalg.svd(u_ref[:, i:j].conj().T @ x[:, i:j], compute_uv=False)
+            worst = max(worst, float(np.sqrt(max(0.0, 1.0 - min(s) ** 2))))
+        i = j
+    return worst

@@ -584,3 +584,21 @@ def test_blocked_lobpcg_ksso_matches_dense():
     res = lb.lobpcgf_blocked(hop, q, x0, 16, 6, 0.0, 1.0, nbuf=2, tol=1e-8, use_filter=False)
     ref = np.linalg.eigvalsh(op.dense_hamiltonian_ksso(wl, m, q))[:16]
     assert res.converged and np.abs(res.lam - ref).max() < 1e-9
+
+
+def test_lobpcgf_eigenvectors_match_dense_subspaces():
+    """Eigenvectors of Algorithm 1 against the dense ones, compared per cluster as subspaces
+    (largest principal-angle sine): at residual tol the sines are of order tol / gap."""
+    from tests._helpers import cluster_sines
+    wl, m, q = _setup("cubic", ecut=4.0)
+    h = op.dense_hamiltonian(wl, m, q)
+    lam, u, _ = lb.dense_eigs(h, wl.c, 8)
+    cs, om = op.filter_constants(wl, q)
+    res = lb.lobpcgf(op.MatrixFreeH(wl, m, q), q, W.start_block(len(m), 10, wl.seed), 10, cs, om, tol=1e-8, nconv=8)
+    x = res.x.reshape(10, -1).T[:, :8]
+    assert np.abs(res.lam[:8] - lam).max() < 1e-9
+    assert cluster_sines(lam, u, x) < 1e-4          # tol / gap with the 2.3e-4 Ha p-level splitting
+    # a wrong vector in a cluster is seen: swap in a vector of another cluster
+    xb = x.copy()
+    xb[:, 0] = u[:, 5]
+    assert cluster_sines(lam, u, xb) > 0.5
