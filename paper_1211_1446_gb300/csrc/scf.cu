@@ -325,7 +325,7 @@ void jacobi_eig(std::vector<double>& a, int n, std::vector<double>& w, std::vect
 }  // namespace
 
 // vhxc = V_H + v_xc of rho; esum_dev (2 doubles, device) receives {sum rho V_H, sum rho eps_xc}
-int hxc_potential(dks_ctx* ctx, const double* rho, double* vhxc, double2* cg, double* esum_dev, cudaStream_t st) {
+static int hxc_potential(dks_ctx* ctx, const double* rho, double* vhxc, double2* cg, double* esum_dev, cudaStream_t st) {
   const size_t ng = (size_t)ctx->ng;
   const int blocks = grid_blocks(ctx, ng);
   {
@@ -348,7 +348,7 @@ int hxc_potential(dks_ctx* ctx, const double* rho, double* vhxc, double2* cg, do
   return DKS_OK;
 }
 
-int set_potential(dks_ctx* ctx, const double* v, cudaStream_t st) {
+static int set_potential(dks_ctx* ctx, const double* v, cudaStream_t st) {
   const int n1 = ctx->grid[0], n2 = ctx->grid[1], n3 = ctx->grid[2], ld = ctx->plane_ld;
   const size_t nvp = (size_t)n3 * n1 * ld;
   if (!ctx->vperm64) {
