@@ -455,6 +455,16 @@ int dks_profile_enable(int on);
  * launches[c], bytes[c], flops[c]; clears.  ncat must be >= dks_profile_ncat(). */
 int dks_profile_read(int ncat, double* ms, long long* launches, double* bytes, double* flops);
 
+/* dks_debug_check: *compiled = 1 in the debug build (libdks_debug.so, built with
+ * `python -m paper_1211_1446_gb300.build --debug`), whose FFT kernels check every sphere <-> grid
+ * and plane index before using it; *code = the first failed check since the last call (kernel
+ * in the top byte: 1 stick inverse, 2 stick forward, 3 stick forward KSSO, 4 plane, 5 plane of
+ * the density, 6 density gather; the item index in the low 24 bits), 0 when none, then cleared
+ * (synchronises the device).  A failed check skips its access, so the results are wrong but no
+ * memory outside the buffers is touched.  In the product build *compiled = 0, *code = 0 and no
+ * device call is made. */
+int dks_debug_check(int* compiled, unsigned* code);
+
 const char* dks_strerror(int code);
 const char* dks_last_error(void);
 

@@ -20,6 +20,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdks.so")
+DEBUG_LIB_PATH = os.path.join(HERE, "libdks_debug.so")   # index-checked build (build --debug)
 
 PREC_FP64, PREC_FP32, PREC_FP64_EMULATED = 0, 1, 2
 MODE_FP64, MODE_MIXED = 0, 1
@@ -89,7 +90,8 @@ EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dk
            "dks_rayleigh_ritz_static", "dks_gram_hermitian", "dks_kinetic_balance", "dks_create_model",
            "dks_ncomp", "dks_density", "dks_hxc", "dks_set_potential", "dks_mixer_create", "dks_mix",
            "dks_mixer_destroy", "dks_scf_opts_default", "dks_scf", "dks_update_potential",
-           "dks_density_residual", "dks_autotune", "dks_tune_get", "dks_tune_set", "dks_fft_plan"]
+           "dks_density_residual", "dks_autotune", "dks_tune_get", "dks_tune_set", "dks_fft_plan",
+           "dks_debug_check"]
 
 _lib = None
 
@@ -142,6 +144,7 @@ def load_library(path: str = LIB_PATH):
     lib.dks_tune_get.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(i), C.POINTER(i)]
     lib.dks_tune_set.argtypes = [vp, C.c_longlong, i, i]
     lib.dks_fft_plan.argtypes = [i, C.POINTER(i), C.POINTER(i), C.POINTER(i)]
+    lib.dks_debug_check.argtypes = [C.POINTER(i), C.POINTER(C.c_uint)]
     lib.dks_strerror.argtypes = [i]
     lib.dks_strerror.restype = C.c_char_p
     lib.dks_last_error.argtypes = []
@@ -482,6 +485,14 @@ class Context:
                       history=list(rep.res_history[:rep.hist_len]),
                       message=_lib.dks_last_error().decode() if rc else "")
         return out, report, rc
+
+
+def debug_check():
+    """dks_debug_check: (checks compiled in, first failed check code or 0)."""
+    lib = load_library()
+    compiled, code = C.c_int(), C.c_uint()
+    _check(lib.dks_debug_check(C.byref(compiled), C.byref(code)))
+    return bool(compiled.value), int(code.value)
 
 
 def fft_plan(n):

@@ -462,6 +462,18 @@ int dks_create(const dks_cell* cell, double ecut, const dks_potentials* pot, con
 
 void dks_destroy(dks_ctx* ctx) { free_ctx(ctx); }
 
+int dks_debug_check(int* compiled, unsigned* code) {
+  if (!compiled || !code) return fail(DKS_ERR_INVALID_ARG, "dks_debug_check: NULL output");
+#ifdef DKS_DEBUG
+  *compiled = 1;
+  *code = debug_check_take();
+#else
+  *compiled = 0;
+  *code = 0u;
+#endif
+  return DKS_OK;
+}
+
 int dks_fft_plan(int n, int* nst, int* radix, int* pos) {
   if (!nst || !radix) return fail(DKS_ERR_INVALID_ARG, "dks_fft_plan: NULL output");
   AxisPlan p;

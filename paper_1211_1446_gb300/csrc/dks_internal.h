@@ -178,6 +178,8 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
 Exec& exec0(dks_ctx* ctx);
 // small two-spinors of nb columns from their large ones, Eq. (RKB); x complex128 (fp64) or complex64
 int kinetic_balance(dks_ctx* ctx, int ik, void* x, int nb, bool fp64, cudaStream_t st);
+// debug build: first failed device index check of the FFT kernels (then cleared); 0 otherwise
+unsigned debug_check_take();
 // rho (natural grid order) += sum_j occ[j] |psi_j(r)|^2 / vol over the columns of x (complex128)
 int density_accumulate(dks_ctx* ctx, int ik, const double2* x, int nb, const double* occ, double* rho,
                        cudaStream_t st);

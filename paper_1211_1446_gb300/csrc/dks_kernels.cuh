@@ -143,4 +143,20 @@ __device__ __forceinline__ double2 to_g(double2 v) { return v; }
 __device__ __forceinline__ float2 to_g(float2 v) { return v; }
 __device__ __forceinline__ double2 to_g(cdf v) { return to_d2(v); }
 
+// Index checks of the debug build (-DDKS_DEBUG, libdks_debug.so): a failed check records its code
+// in its translation unit's status word (the first failure is kept) and the caller skips the
+// access.  In the product build the check is `true` and the comparisons compile away.
+#ifdef DKS_DEBUG
+static __device__ unsigned int g_dks_check = 0u;
+__device__ __forceinline__ bool dks_ok(bool ok, unsigned code) {
+  if (!ok) atomicCAS(&g_dks_check, 0u, code);
+  return ok;
+}
+#else
+__device__ __forceinline__ bool dks_ok(bool, unsigned) { return true; }
+#endif
+// check codes: kernel in the top byte, the failing item's low 24 bits below it
+constexpr unsigned kChkStickInverse = 1u << 24, kChkStickForward = 2u << 24, kChkStickForwardKs = 3u << 24,
+                   kChkPlane = 4u << 24, kChkPlaneDensity = 5u << 24, kChkUnpermute = 6u << 24;
+
 }  // namespace dks

@@ -57,8 +57,11 @@ __global__ void __launch_bounds__(256) k_stick_inverse(
   __syncthreads();
   const Vg* xf = x + (size_t)f * npw;
   const int q0 = stick_start[s0], q1 = stick_start[s0 + ns];
-  for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x)
-    line[(pw_stick[q] - s0) * ls + pw_iz[q]] = to_s<V>(xf[q]);
+  for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    const int sl = pw_stick[q] - s0, iz = pw_iz[q];
+    if (dks_ok(sl >= 0 && sl < ns && iz >= 0 && iz < n3, kChkStickInverse | (q & 0xffffff)))
+      line[sl * ls + iz] = to_s<V>(xf[q]);
+  }
   __syncthreads();
   fft_lines<V, false, false>(line, ns, ls, 1, p3, tw3);
   Vg* tf = t + (size_t)f * n3 * nsticks;
@@ -85,7 +88,9 @@ __global__ void __launch_bounds__(512) k_plane(Vg* __restrict__ t, int nsticks,
   for (int e = threadIdx.x; e < np; e += blockDim.x) plane[e] = vzero<V>();
   __syncthreads();
   Vg* row = t + ((size_t)f * n3 + z) * nsticks;
-  for (int s = threadIdx.x; s < nsticks; s += blockDim.x) plane[stick_plane[s]] = to_s<V>(row[s]);
+  for (int s = threadIdx.x; s < nsticks; s += blockDim.x)
+    if (dks_ok(stick_plane[s] >= 0 && stick_plane[s] < np, kChkPlane | (s & 0xffffff)))
+      plane[stick_plane[s]] = to_s<V>(row[s]);
   __syncthreads();
   fft_lines<V, false, false>(plane, n1, ld, 1, p2, tw2);   // along axis 2 (contiguous)
   fft_lines<V, false, false>(plane, n2, 1, ld, p1, tw1);   // along axis 1
@@ -94,7 +99,9 @@ __global__ void __launch_bounds__(512) k_plane(Vg* __restrict__ t, int nsticks,
   __syncthreads();
   fft_lines<V, true, true>(plane, n2, 1, ld, p1, tw1);
   fft_lines<V, true, true>(plane, n1, ld, 1, p2, tw2);
-  for (int s = threadIdx.x; s < nsticks; s += blockDim.x) row[s] = to_g(plane[stick_plane[s]]);
+  for (int s = threadIdx.x; s < nsticks; s += blockDim.x)
+    if (dks_ok(stick_plane[s] >= 0 && stick_plane[s] < np, kChkPlane | (s & 0xffffff)))
+      row[s] = to_g(plane[stick_plane[s]]);
 }
 
 // ---------------------------------------------------------------------------
@@ -241,7 +248,9 @@ __global__ void __launch_bounds__(512) k_plane_density(const double2* __restrict
     for (int e = threadIdx.x; e < np; e += blockDim.x) plane[e] = double2{0.0, 0.0};
     __syncthreads();
     const double2* row = t + ((size_t)f * n3 + z) * nsticks;
-    for (int s = threadIdx.x; s < nsticks; s += blockDim.x) plane[stick_plane[s]] = row[s];
+    for (int s = threadIdx.x; s < nsticks; s += blockDim.x)
+      if (dks_ok(stick_plane[s] >= 0 && stick_plane[s] < np, kChkPlaneDensity | (s & 0xffffff)))
+        plane[stick_plane[s]] = row[s];
     __syncthreads();
     fft_lines<double2, false, false>(plane, n1, ld, 1, p2, tw2);
     fft_lines<double2, false, false>(plane, n2, 1, ld, p1, tw1);
@@ -266,7 +275,8 @@ __global__ void k_unpermute_add(const double* __restrict__ rho_perm, double* __r
     const int i3 = (int)(n % n3);
     const size_t r = n / n3;
     const int i2 = (int)(r % n2), i1 = (int)(r / n2);
-    rho[n] += scale * rho_perm[((size_t)p3[i3] * n1 + p1[i1]) * ld + p2[i2]];
+    const size_t at = ((size_t)p3[i3] * n1 + p1[i1]) * ld + p2[i2];
+    if (dks_ok(at < (size_t)n3 * n1 * ld, kChkUnpermute | (unsigned)(n & 0xffffff))) rho[n] += scale * rho_perm[at];
   }
 }
 
@@ -342,6 +352,7 @@ __global__ void __launch_bounds__(256) k_stick_forward(
     const float kh = (float)kd, kl = (float)(kd - (double)kh), sh = (float)shift, sc = (float)scale;
     for (int p = q0 + threadIdx.x; p < q1; p += blockDim.x) {
       const int s = pw_stick[p] - s0, iz = pw_iz[p];
+      if (!dks_ok(s >= 0 && s < ns && iz >= 0 && iz < p3.n, kChkStickForward | (p & 0xffffff))) continue;
       const float2 x0 = x[fo + p], x1 = x[fo + (size_t)npw + p], x2 = x[fo + 2 * (size_t)npw + p],
                    x3 = x[fo + 3 * (size_t)npw + p];
       const float* cq = cq32 + 6 * (size_t)p;
@@ -369,6 +380,7 @@ __global__ void __launch_bounds__(256) k_stick_forward(
   const double diag_small = -2.0 * c * c;
   for (int p = q0 + threadIdx.x; p < q1; p += blockDim.x) {
     const int s = pw_stick[p] - s0, iz = pw_iz[p];
+    if (!dks_ok(s >= 0 && s < ns && iz >= 0 && iz < p3.n, kChkStickForward | (p & 0xffffff))) continue;
     double2 xv[4], h[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) xv[a] = to_d2(x[fo + (size_t)a * npw + p]);
@@ -409,6 +421,7 @@ __global__ void __launch_bounds__(256) k_stick_forward_ks(
   const int q0 = stick_start[s0], q1 = stick_start[s0 + ns];
   for (int p = q0 + threadIdx.x; p < q1; p += blockDim.x) {
     const int s = pw_stick[p] - s0, iz = pw_iz[p];
+    if (!dks_ok(s >= 0 && s < ns && iz >= 0 && iz < p3.n, kChkStickForwardKs | (p & 0xffffff))) continue;
     if constexpr (std::is_same<Vg, float2>::value && std::is_same<V, float2>::value) {
       const float kin = (float)(ek[p] - shift), sc = (float)scale;
 #pragma unroll
@@ -785,6 +798,19 @@ int density_accumulate(dks_ctx* ctx, int ik, const double2* x, int nb, const dou
   }
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
+}
+
+// the first failed index check of this file's kernels since the last call, then cleared
+// (debug build; 0 in the product build)
+unsigned debug_check_take() {
+#ifdef DKS_DEBUG
+  unsigned v = 0u, z = 0u;
+  if (cudaMemcpyFromSymbol(&v, g_dks_check, sizeof(v)) != cudaSuccess) return 0xffffffffu;
+  cudaMemcpyToSymbol(g_dks_check, &z, sizeof(z));
+  return v;
+#else
+  return 0u;
+#endif
 }
 
 int kinetic_balance(dks_ctx* ctx, int ik, void* x, int nb, bool fp64, cudaStream_t st) {

@@ -162,3 +162,16 @@ def test_fft_plans_without_gpu():
         assert np.abs(got[pos] - want).max() < 1e-9 * max(1.0, np.abs(want).max())
     with pytest.raises(P.DKSError):
         P.fft_plan(257)
+
+
+def test_debug_build_and_check_entry_without_gpu():
+    """The index-checked debug library builds and exports dks_debug_check; the product library
+    reports that its checks are compiled out (without any device call)."""
+    import paper_1211_1446_gb300 as P
+    from paper_1211_1446_gb300 import build
+    assert P.debug_check() == (False, 0)
+    path = build.build(debug=True)
+    assert path.endswith("libdks_debug.so")
+    lib = ctypes.CDLL(path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
