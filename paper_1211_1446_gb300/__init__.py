@@ -397,15 +397,16 @@ class Context:
 
     def scf(self, x_list, nev, nocc, tol=1e-8, max_iter=60, alpha=0.5, q0=1.0, history=8, n_init_warm=1,
             solve_tol=1e-8, rho=None, n_init=3, mode=MODE_FP64, nbuf=0, n_iter=200, precond=PRECOND_TETER,
-            stream=None, check=True):
+            stream=None, check=True, block=0):
         """dks_scf: the SCF loop (solve, density, V_hxc, Kerker-Anderson mixing) from the potential
-        given at creation.  Returns (eigenvalues per k, report dict, status code)."""
+        given at creation; block > 0 solves in band blocks (see solve).  Returns (eigenvalues per
+        k, report dict, status code)."""
         o = ScfOpts()
         _lib.dks_scf_opts_default(C.byref(o))
         o.nocc, o.max_iter, o.tol, o.alpha, o.kerker_q0 = int(nocc), int(max_iter), float(tol), float(alpha), float(q0)
         o.history, o.n_init_warm, o.solve_tol = int(history), int(n_init_warm), float(solve_tol)
         o.solve.n_init, o.solve.n_iter, o.solve.nbuf = int(n_init), int(n_iter), int(nbuf)
-        o.solve.mode, o.solve.precond = int(mode), int(precond)
+        o.solve.mode, o.solve.precond, o.solve.block = int(mode), int(precond), int(block)
         o.solve.stream = _stream(stream)
         if len(x_list) != self.nk:
             raise ValueError(f"need one block per k-point ({self.nk})")
