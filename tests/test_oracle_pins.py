@@ -602,3 +602,14 @@ def test_lobpcgf_eigenvectors_match_dense_subspaces():
     xb = x.copy()
     xb[:, 0] = u[:, 5]
     assert cluster_sines(lam, u, xb) > 0.5
+
+
+def test_davidson_ksso_matches_dense():
+    """The oracle's block Davidson on the two-component KSSO operator (no filter, as the KSSO
+    module has no negative continuum) gives its lowest dense eigenvalues."""
+    wl, m, q = _setup("small", ecut=4.0)
+    hop = op.MatrixFreeKSSO(wl, m, q)
+    x0 = W.start_block(len(m), 8, wl.seed, ncomp=2)
+    res = dv.davidson_f(hop, q, x0, 8, 0.0, 1.0, tol=1e-8, use_filter=False, nconv=6)
+    ref = np.linalg.eigvalsh(op.dense_hamiltonian_ksso(wl, m, q))[:6]
+    assert res.converged and np.abs(res.lam[:6] - ref).max() < 1e-9
