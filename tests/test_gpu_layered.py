@@ -9,8 +9,12 @@ oracle computes one by one and on properties that hold at any size:
   * a mixed-precision solve of all 16 k-points by concurrent workers (8 buffer columns per k):
     every checked residual below 1e-6, and for sampled columns recomputed here with the
     oracle's operator; orthonormal vectors; no eigenvalue below the gap midpoint; Kramers pairs
-    at the four time-reversal-invariant k-points of the mesh.
+    at the four time-reversal-invariant k-points of the mesh; the 48 lowest eigenvalues at
+    k = 0 within 1e-8 Ha of the oracle's Algorithm 1 run on that k-point alone (stored by
+    tests/golden/make_golden.py).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -66,6 +70,10 @@ def test_layered_solve_all_kpoints(layered):
         assert lam[ik][0] > -wl.c ** 2                           # above the gap midpoint
     for ik in TRIM:                                              # Kramers pairs
         assert np.abs(lam[ik][0::2] - lam[ik][1::2]).max() < 1e-7, ik
+    # eigenvalues at k = 0 against the oracle's Algorithm 1 on that k-point alone (48 lowest,
+    # tests/golden/layered_k0_eigs.txt): a state skipped inside the wanted window fails here
+    gold = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "layered_k0_eigs.txt"))
+    assert np.abs(lam[0][:len(gold)] - gold).max() < 1e-8, np.abs(lam[0][:len(gold)] - gold).max()
     # orthonormal columns (all nev + nbuf of them) at two k-points.  X = Z V with V orthonormal
     # in the metric S = Z^H Z of the last Rayleigh-Ritz step, so X^H X - I is the rounding of that
     # FP64 step times the conditioning of S, which grows as the directions of P converge; on a

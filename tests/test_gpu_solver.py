@@ -180,6 +180,24 @@ def test_dimer_full_size_vs_oracle(mode):
     assert res.max() < 1e-6, res
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_dimer_ecut2_vs_dense(mode):
+    """The dimer's cell, grid and 36 spin-orbit projector channels at Ecut 2 Ha (1295 planewaves,
+    dimension 5180) against the plain definition: the 32 lowest eigenvalues above the gap of the
+    dense H' (zheevd, tests/golden/dimer_ecut2_dense_eigs.txt) within 1e-8 Ha, in FP64 and in the
+    mixed mode, with every residual recomputed by the oracle's FP64 H' below 1e-6."""
+    gpu()
+    import torch
+    wl, ctx, hop, q = make_pair("dimer", ecut=2.0)
+    ref = np.loadtxt(os.path.join(GOLDEN, "dimer_ecut2_dense_eigs.txt"))[:32]
+    x0 = torch.from_numpy(W.start_block(len(q), 40, wl.seed)).cuda()
+    lam, rep, rc = ctx.solve([x0], 32, nbuf=8, tol=1e-6, mode=mode, check=False)
+    assert rc == 0, (rc, rep["message"], rep["iterations"], rep["fp64_iterations"])
+    lam = lam[0]
+    assert np.abs(lam - ref).max() < 1e-8, np.abs(lam - ref).max()
+    assert _residuals(hop, x0.cpu().numpy()[:32], lam).max() < 1e-6
+
+
 def test_davidson_f_dimer_full_size_vs_oracle():
     """Davidson-F on the bench configuration (mixed precision, basis of 160 columns): the same 32
     eigenvalues as the oracle's Algorithm 1 within 1e-8 Ha, sampled residuals below 1e-6."""

@@ -6,6 +6,7 @@ E(k) = E(-k)), a library routine (sympy Clebsch-Gordan, scipy generalized
 eigh, LAPACK zheevd), a brute-force sum, or a limit (nonrelativistic c -> oo).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -392,6 +393,17 @@ def test_teter_factor_limits():
     assert np.allclose(op.teter_factor(big) * 2 * big, 1.0, rtol=2e-3)
     xs = np.linspace(0, 50, 1001)
     assert np.all(np.diff(op.teter_factor(xs)) < 0)
+
+
+def test_teter_factor_published_values():
+    """K(x) at exact rational points worked out by hand from the Teter-Payne-Allan polynomial
+    (tests/golden/teter_factor_values.txt): pins every coefficient, 18 and 12 included -- a
+    changed coefficient moves K(1) = 65/81 or K(3/2) = 4/7."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "teter_factor_values.txt")
+    vals = np.loadtxt(path, comments="#")
+    assert vals.shape[0] >= 5
+    for xn, xd, kn, kd in vals:
+        assert abs(op.teter_factor(xn / xd) - kn / kd) < 1e-15
 
 
 def test_teter_precondition_brute_force():
