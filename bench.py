@@ -231,7 +231,8 @@ def run_reference(args):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per kernel launch from ncu captures of
-# the current kernels at the dimer's sizes (python bench.py --kernel-case <case> under ncu --set full)
+# the current kernels at the dimer's sizes, one kernel and one launch per capture, e.g.
+#   ncu --set full --clock-control none -k regex:k_gram_df -c 1 -o prof python bench.py --kernel-case gramdf
 NCU_TRAFFIC = {
     "rayleigh_ritz": {"bytes_per_launch": (526.3e3 + 2 * 469.2e3 + 425.5e3 + 539.9e3) / 5,
                       "note": "kernel case rr (m = 120, n = 40): mean over the five kernels of a step, "

@@ -275,8 +275,11 @@ int dks_gram_hermitian(const void* Z, const void* HZ, int rows, int nz, void* A,
  * (after diagonal scaling; Cholesky of S, or SVQB with drop tolerance
  * 1e-12 * max eig when the smallest Cholesky pivot^2 < 1e-12).  A, S device
  * complex128 nz x nz column-major; V device complex128 nz x n column-major;
- * lam device double[n] ascending; info device int[2] = {used SVQB, rank}.
- * nz <= 512.  Returns INVALID_ARG, UNSUPPORTED, CUDA. */
+ * lam device double[n] ascending; info device int[3] = {used SVQB, rank, eigensolver
+ * status}: info[2] is 0, or nonzero when the single-CTA fallback's tridiagonal QL did not
+ * converge within its sweep limit (the results it had are still written).  All three ints
+ * are written, so info must hold at least 3.  nz <= 512.  Returns INVALID_ARG, UNSUPPORTED,
+ * CUDA. */
 int dks_rayleigh_ritz(const void* A, const void* S, int nz, int n, void* V, double* lam,
                       int* info, void* stream);
 
@@ -289,8 +292,10 @@ int dks_rayleigh_ritz(const void* A, const void* S, int nz, int n, void* V, doub
  * nz <= DKS_RR_STATIC_MAX_NZ, larger pencils return DKS_ERR_UNSUPPORTED.  The first call on
  * each device caches the array's device address, so make it before any stream capture.  Every
  * call on a device shares the array (each call overwrites it completely before use); calls
- * whose executions overlap on the GPU race on it and must be ordered by the caller.  Calls no
- * cudaMalloc, cudaFree or other allocating routine. */
+ * whose executions overlap on the GPU race on it and must be ordered by the caller.  The array
+ * used is the one of the current device, so `stream` must belong to the current device
+ * (checked: a stream of another device returns DKS_ERR_INVALID_ARG).  info is int[3] as for
+ * dks_rayleigh_ritz.  Calls no cudaMalloc, cudaFree or other allocating routine. */
 #define DKS_RR_STATIC_MAX_NZ 128
 int dks_rayleigh_ritz_static(const void* A, const void* S, int nz, int n, void* V, double* lam,
                              int* info, void* stream);

@@ -608,8 +608,36 @@ def gram_hermitian(z, hz, a_out, s_out, stream=None, emulated=False):
                                    _stream(stream)))
 
 
+def _rr_args(a, s, n, v_out, lam_out, info_out):
+    """Shapes, dtypes, device and contiguity of a Rayleigh-Ritz call, checked before any pointer
+    reaches the library: A, S complex128 nz x nz, V complex128 with room for n x nz, lam float64
+    with room for n, info int32 with room for 3 (every call writes info[0..2])."""
+    import torch
+    nz = a.shape[0]
+    if a.dim() != 2 or tuple(a.shape) != (nz, nz) or tuple(s.shape) != (nz, nz):
+        raise ValueError("A and S must be nz x nz")
+    if not 0 < int(n) <= nz:
+        raise ValueError("need 0 < n <= nz")
+    args = (("A", a, torch.complex128, nz * nz), ("S", s, torch.complex128, nz * nz),
+            ("V", v_out, torch.complex128, int(n) * nz), ("lam", lam_out, torch.float64, int(n)),
+            ("info", info_out, torch.int32, 3))
+    for name, t, dt, need in args:
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}")
+        if t.numel() < need:
+            raise ValueError(f"{name} needs at least {need} elements")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    for name, t, _, _ in args:
+        if not t.is_cuda or t.device != a.device:
+            raise ValueError(f"{name} must be on the device of A")
+    return nz
+
+
 def rayleigh_ritz(a, s, n, v_out, lam_out, info_out, stream=None):
+    """dks_rayleigh_ritz: the n lowest pairs of A v = lam S v on the device (info: int32[>= 3])."""
     load_library()
+    _rr_args(a, s, n, v_out, lam_out, info_out)
     _check(_lib.dks_rayleigh_ritz(_dptr(a), _dptr(s), a.shape[0], int(n), _dptr(v_out), _dptr(lam_out),
                                   _dptr(info_out), _stream(stream)))
 
@@ -618,6 +646,7 @@ def rayleigh_ritz_static(a, s, n, v_out, lam_out, info_out, stream=None):
     """dks_rayleigh_ritz_static: same solve with the library's fixed device scratch array (no
     allocation; nz <= 128; calls that overlap on the GPU race on the shared array)."""
     load_library()
+    _rr_args(a, s, n, v_out, lam_out, info_out)
     _check(_lib.dks_rayleigh_ritz_static(_dptr(a), _dptr(s), a.shape[0], int(n), _dptr(v_out), _dptr(lam_out),
                                          _dptr(info_out), _stream(stream)))
 

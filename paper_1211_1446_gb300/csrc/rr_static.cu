@@ -17,6 +17,8 @@
 //    it.  The kernel writes every scratch element before reading it, so nothing has to be
 //    cleared between calls; calls whose executions overlap on the GPU (different streams
 //    without ordering) race on the array and must be serialised by the caller.
+//  * The array used is the current device's, so the stream must belong to the current device
+//    (a stream of another device is rejected with DKS_ERR_INVALID_ARG).
 //  * No cudaMalloc, cudaFree or other allocating routine is called.
 #include <cuda_runtime.h>
 
@@ -71,6 +73,14 @@ extern "C" int dks_rayleigh_ritz_static(const void* A, const void* S, int nz, in
                                          " exceeds the static scratch limit " + std::to_string(kStaticMaxNz));
   if (rr_scratch_elems(nz) > kStaticElems)
     return fail(DKS_ERR_UNSUPPORTED, "dks_rayleigh_ritz_static: scratch requirement exceeds the static array");
+  if (stream) {
+    // the scratch array is the current device's: a stream of another device would run the
+    // kernels there with this device's address
+    int dev = 0, sdev = 0;
+    DKS_CUDA_TRY(cudaGetDevice(&dev));
+    DKS_CUDA_TRY(cudaStreamGetDevice((cudaStream_t)stream, &sdev));
+    if (sdev != dev) return fail(DKS_ERR_INVALID_ARG, "dks_rayleigh_ritz_static: stream belongs to another device");
+  }
   double2* scr = nullptr;
   DKS_TRY(static_scratch(&scr));
   return rayleigh_ritz((const double2*)A, (const double2*)S, nz, n, (double2*)V, lam, info, scr,

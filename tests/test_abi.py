@@ -175,3 +175,25 @@ def test_debug_build_and_check_entry_without_gpu():
     lib = ctypes.CDLL(path)
     missing = [n for n in _declared() if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_rayleigh_ritz_binding_rejects_short_info_and_bad_shapes():
+    """The Rayleigh-Ritz entry points write info[0..2]: the binding refuses an info of two ints, a
+    non-square S and a V with room for fewer than n x nz values before any pointer reaches the
+    library (checked on CPU tensors, so no GPU call is made)."""
+    import torch
+
+    import paper_1211_1446_gb300 as P
+    nz, n = 6, 3
+    a = torch.zeros((nz, nz), dtype=torch.complex128)
+    v = torch.zeros((n, nz), dtype=torch.complex128)
+    lam = torch.zeros(n, dtype=torch.float64)
+    for fn in (P.rayleigh_ritz, P.rayleigh_ritz_static):
+        with pytest.raises(ValueError, match="info needs at least 3"):
+            fn(a, a, n, v, lam, torch.zeros(2, dtype=torch.int32))
+        with pytest.raises(ValueError, match="nz x nz"):
+            fn(a, a[:, :4], n, v, lam, torch.zeros(3, dtype=torch.int32))
+        with pytest.raises(ValueError, match="V needs"):
+            fn(a, a, n, v[:2], lam, torch.zeros(3, dtype=torch.int32))
+        with pytest.raises(ValueError, match="device of A"):
+            fn(a, a, n, v, lam, torch.zeros(3, dtype=torch.int32))

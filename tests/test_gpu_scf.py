@@ -141,6 +141,29 @@ def test_scf_matches_oracle(name, kw, nocc, nev, model):
     assert rep["iterations"] >= 2
 
 
+def test_scf_band_blocks_match_single_block():
+    """The SCF loop with its eigensolves in band blocks (block = 4 wanted columns plus the buffer
+    columns per block, deflated against the earlier blocks) reaches the same self-consistent
+    eigenvalues and density as with one block, and both match the oracle's SCF."""
+    torch = gpu()
+    import paper_1211_1446_gb300 as P
+    wl = W.make("cubic", ecut=4.0)
+    nocc, nev, nbuf = 2, 8, 2
+    ref = oscf.scf(wl, nocc, nev=nev, tol=1e-10)
+    out = {}
+    for block in (0, 4):
+        ctx = P.Context.from_workload(wl)
+        x = torch.from_numpy(W.start_block(ctx.npw(0), nev + nbuf, wl.seed)).cuda()
+        rho = torch.zeros(wl.grid, dtype=torch.float64, device="cuda")
+        lam, rep, rc = ctx.scf([x], nev, nocc, tol=1e-9, solve_tol=1e-9, nbuf=nbuf, rho=rho, max_iter=60,
+                               block=block)
+        assert rc == 0 and rep["converged"], (block, rep)
+        out[block] = (lam[0], rho.cpu().numpy())
+    assert np.abs(out[4][0] - out[0][0]).max() < 1e-7
+    assert np.abs(out[4][1] - out[0][1]).max() < 1e-7 * np.abs(out[0][1]).max()
+    assert np.abs(out[4][0] - ref.lam[0]).max() < 1e-7
+
+
 def test_scf_dimer_first_iterations():
     """The bench workload at full size: three SCF iterations in mixed precision; the density
     holds nocc electrons, the residual falls, the eigenvalues of the final potential are those
