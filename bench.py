@@ -464,6 +464,115 @@ def scf_section(P, W, wl, ctx, mode, stream, nocc=20, tol=1e-4, solve_tol=1e-7, 
     return out
 
 
+def hx_rate(P, ctx, ik, nb, npw, nproj, ng, dtype, emulated, stream, hbm, reps=5):
+    """H' on nb columns of k-point ik: mean CUDA-event time and the effective bandwidth of the
+    sphere-only algorithmic bytes (read X, write HX, V once, B twice), with its fraction of the
+    measured HBM copy bandwidth."""
+    import torch
+    es = 8 if dtype == torch.complex64 else 16
+    g = torch.Generator(device="cuda").manual_seed(11)
+    x = torch.randn((nb, 4, npw), dtype=dtype, device="cuda", generator=g)
+    hx = torch.empty_like(x)
+    for _ in range(2):
+        ctx.apply_H(ik, x, hx, emulated=emulated)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.apply_H(ik, x, hx, emulated=emulated)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / reps / 1e3
+    alg = 2 * 4 * npw * es * nb + ng * es / 2 + 2 * (2 * npw * nproj * es)
+    return {"ms": t * 1e3, "columns": nb, "algorithmic_bytes": alg, "achieved_gbs": alg / t / 1e9,
+            "frac_of_hbm": alg / t / 1e9 / hbm}
+
+
+def layered_section(P, W, mode, stream, hbm, nbuf=8, sample=(4, 9)):
+    """The layered crystal (hexagonal a = 7.8, c = 28 bohr, 15 sites, 270 spin-orbit projector
+    channels, 60 x 60 x 216 grid, 16 k-points with their own spheres of about 39,000-41,000
+    planewaves and nev_k of 48-96): all 16 k-points in one call (concurrent solve workers), mixed
+    precision, one timed solve after a one-iteration call that sizes the workspaces.  Beside it,
+    for a sample of k-points each solved alone, the mixed and the plain FP64 GPU forms (the
+    speedup denominator), H' bandwidth at k = 0, and the eigenvalue error at k = 0 against the
+    oracle's Algorithm 1 (tests/golden/layered_k0_eigs.txt)."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+    wl = W.make("layered")
+    ctx = P.Context.from_workload(wl)
+    nev_k = [int(v) for v in wl.nev_k]
+    x0 = [torch.from_numpy(W.start_block(ctx.npw(ik), nev_k[ik] + nbuf, wl.seed, ik)).cuda() for ik in range(wl.nk)]
+    xs = [t.clone() for t in x0]
+    ctx.solve(xs, 0, nev_k=nev_k, nbuf=nbuf, tol=TOL, mode=mode, n_iter=1, check=False)   # workspaces
+    for a, b in zip(xs, x0):
+        a.copy_(b)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lam, rep, rc = ctx.solve(xs, 0, nev_k=nev_k, nbuf=nbuf, tol=TOL, mode=mode, check=False, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"workload": "layered crystal: hexagonal a 7.8 c 28 bohr, 15 sites, 270 SO projector channels, "
+                       "60x60x216 grid, 16 k-points (4x4x1), npw 39000-41000 per k, nev_k 48-96 + 8 buffer",
+           "status": int(rc), "ms": ms, "eigenpairs": sum(nev_k), "eigenpairs_per_s": sum(nev_k) / (ms / 1e3),
+           "iterations": rep["iterations"][:wl.nk], "fp64_iterations": rep["fp64_iterations"][:wl.nk],
+           "max_residual": max(rep["max_residual"][:wl.nk])}
+    gold = os.path.join(HERE, "tests", "golden", "layered_k0_eigs.txt")
+    if rc == 0 and os.path.exists(gold):
+        g = np.loadtxt(gold)
+        out["max_eig_err_vs_oracle_k0"] = float(np.abs(lam[0][:len(g)] - g).max())
+    # mixed vs plain FP64 on sampled k-points, each alone (one k-point per context)
+    per = []
+    for ik in sample:
+        wk = dataclasses.replace(wl, kfrac=wl.kfrac[ik:ik + 1], ecut_k=wl.ecut_k[ik:ik + 1], nev_k=wl.nev_k[ik:ik + 1])
+        ck = P.Context.from_workload(wk)
+        row = {"k": ik, "nev": nev_k[ik], "npw": ck.npw(0)}
+        for tag, md in (("mixed", mode), ("fp64", P.MODE_FP64)):
+            xk = torch.from_numpy(W.start_block(ck.npw(0), nev_k[ik] + nbuf, wl.seed, ik)).cuda()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            lk, rk, rck = ck.solve([xk], nev_k[ik], nbuf=nbuf, tol=TOL, mode=md, check=False, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[tag + "_ms"] = e0.elapsed_time(e1)
+            row[tag + "_status"] = int(rck)
+            row[tag + "_iterations"] = rk["iterations"][0]
+            row[tag + "_eig"] = lk[0]
+        row["speedup_mixed_vs_fp64"] = row["fp64_ms"] / row["mixed_ms"]
+        row["max_eig_diff"] = float(np.abs(row.pop("mixed_eig") - row.pop("fp64_eig")).max())
+        per.append(row)
+        ck.close()
+    out["per_k_sample"] = per
+    out["speedup_mixed_vs_fp64_sample"] = sum(r["fp64_ms"] for r in per) / sum(r["mixed_ms"] for r in per)
+    nproj = ctx.nproj()
+    out["hx_k0"] = {"fp32": hx_rate(P, ctx, 0, 104, ctx.npw(0), nproj, wl.ng, torch.complex64, False, stream, hbm),
+                    "fp64_double_float": hx_rate(P, ctx, 0, 104, ctx.npw(0), nproj, wl.ng, torch.complex128, True,
+                                                 stream, hbm)}
+    ctx.close()
+    return out
+
+
+def supercell_hx_section(P, W, stream, hbm, nb=160):
+    """H' bandwidth at the large-cell size (2 x 2 x 1 supercell of the layered crystal: 120 x 120 x
+    216 grid, about 158,000 planewaves at Gamma, 1080 spin-orbit projector channels) on a block of
+    nb columns, FP32 and double-float; one k-point is enough for the operator's rate."""
+    import dataclasses
+    import torch
+    wl = W.make("supercell")
+    wk = dataclasses.replace(wl, kfrac=wl.kfrac[:1], ecut_k=wl.ecut_k[:1], nev_k=wl.nev_k[:1])
+    ctx = P.Context.from_workload(wk)
+    npw, nproj = ctx.npw(0), ctx.nproj()
+    out = {"workload": "supercell 2x2x1 of the layered crystal: 120x120x216 grid, Gamma, 1080 SO projector channels",
+           "npw": npw, "fp32": hx_rate(P, ctx, 0, nb, npw, nproj, wl.ng, torch.complex64, False, stream, hbm, reps=3),
+           "fp64_double_float": hx_rate(P, ctx, 0, nb // 4, npw, nproj, wl.ng, torch.complex128, True, stream, hbm,
+                                        reps=2)}
+    ctx.close()
+    return out
+
+
 def supercell_section(P, W, mode, stream, block=128, nbuf=32, tol=1e-6):
     """The large-cell configuration (2 x 2 x 1 supercell of the layered crystal: 120 x 120 x 216
     grid, about 158,000 planewaves per k, 1080 projector channels, 4 k-points, 480 pairs each),
@@ -491,6 +600,48 @@ def supercell_section(P, W, mode, stream, block=128, nbuf=32, tol=1e-6):
     return out
 
 
+def tc_study(masks, reps):
+    """The tensor-core study of the complex64 contractions: the dimer solve (mixed precision, the
+    bench configuration) reps times for each DKS_TC_* mask, recording the FP32 phase's residual
+    floor (lowest residual before the hand-off), the FP64-phase iterations and the solve time.
+    The FP32 floor sets how many FP64 iterations remain, so a contraction belongs on the tensor
+    cores only if it leaves the floor where the CUDA-core kernels put it."""
+    import numpy as np
+    import torch
+
+    import paper_1211_1446_gb300 as P
+    import workloads as W
+    wl = W.make("dimer")
+    ctx = P.Context.from_workload(wl)
+    x0 = torch.from_numpy(W.start_block(ctx.npw(0), NEV + NBUF, wl.seed)).cuda()
+    x = torch.empty_like(x0)
+    gold = np.loadtxt(os.path.join(HERE, "tests", "golden", "dimer_lobpcgf_eigs.txt"))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    old = P.tensor_cores()
+    out = {}
+    for mask in masks:
+        P.tensor_cores(mask)
+        rows = []
+        for _ in range(reps):
+            x.copy_(x0)
+            torch.cuda.synchronize()
+            e0.record()
+            lam, rep, rc = ctx.solve([x], NEV, tol=TOL, mode=P.MODE_MIXED, nbuf=NBUF, check=False)
+            e1.record()
+            torch.cuda.synchronize()
+            it32 = rep["iterations"][0] - rep["fp64_iterations"][0]
+            rows.append({"status": int(rc), "ms": e0.elapsed_time(e1), "iterations": rep["iterations"][0],
+                         "fp64_iterations": rep["fp64_iterations"][0],
+                         "fp32_floor": min(rep["history"][:it32]) if it32 > 0 else None,
+                         "max_eig_err_vs_oracle": float(np.abs(lam[0] - gold).max()) if rc == 0 else None})
+        out[str(mask)] = {"runs": rows, "median_ms": float(np.median([r["ms"] for r in rows])),
+                          "median_fp32_floor": float(np.median([r["fp32_floor"] for r in rows])),
+                          "median_fp64_iterations": float(np.median([r["fp64_iterations"] for r in rows]))}
+    P.tensor_cores(*old)
+    print(json.dumps({"tc_study": out, "workload": WORKLOAD}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -504,10 +655,17 @@ def main():
     ap.add_argument("--no-ksso", action="store_true")
     ap.add_argument("--no-davidson", action="store_true")
     ap.add_argument("--no-scf", action="store_true")
+    ap.add_argument("--no-layered", action="store_true", help="skip the layered-crystal (16 k-point) section")
+    ap.add_argument("--no-supercell-hx", action="store_true", help="skip H' bandwidth at the supercell size")
     ap.add_argument("--supercell", action="store_true",
                     help="also solve the large-cell configuration in band blocks (minutes, most of the GPU memory)")
     ap.add_argument("--ref-iterations", type=int, default=60)
     ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--tc-study", default=None,
+                    help="comma-separated DKS_TC_* masks: FP32-phase floor, FP64 iterations and time per mask "
+                         "(--steps solves each)")
+    ap.add_argument("--tc", type=int, default=None,
+                    help="DKS_TC_* mask: complex64 contractions on the tcgen05 tensor cores (default: library default)")
     ap.add_argument("--kernel-case", default=None,
                     choices=["hx64", "hx32", "hxdf", "gram64", "gram32", "gramdf", "rotate64", "rotate32", "rotatedf",
                              "rr"],
@@ -515,8 +673,13 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.tc is not None:
+        import paper_1211_1446_gb300 as P
+        P.tensor_cores(args.tc)
     if args.kernel_case:
         return kernel_case(args.kernel_case)
+    if args.tc_study:
+        return tc_study([int(v) for v in args.tc_study.split(",")], args.steps)
 
     import numpy as np
     import torch
@@ -642,32 +805,31 @@ def main():
                  "share_of_step": d["ms"] / (ms * args.steps),
                  "per_category_ms": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items() if v["launches"]}})
 
-    # H' x effective bandwidth (sphere-only algorithmic bytes) on the bench block, outside the timed region
-    hx_line = {}
+    # H' x effective bandwidth (sphere-only algorithmic bytes) on the bench block width, outside the
+    # timed region: FP32 (the first phase), double-float (the refinement) and native FP64
     nproj = ctx.nproj()
-    for dt, es, tag in ((torch.complex64, 8, "fp32"), (torch.complex128, 16, "fp64")):
-        xx = x0.to(dt)
-        hh = torch.empty_like(xx)
-        for _ in range(2):
-            ctx.apply_H(0, xx, hh)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(5):
-            ctx.apply_H(0, xx, hh)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 5 / 1e3
-        nb = xx.shape[0]
-        alg = 2 * 4 * npw * es * nb + wl.ng * es / 2 + 2 * (2 * npw * nproj * es)
-        hx_line[tag] = {"ms": t * 1e3, "achieved_gbs": alg / t / 1e9, "frac_of_hbm": alg / t / 1e9 / hbm,
-                        "algorithmic_bytes": alg, "columns": nb}
-    roof["hx"] = hx_line
+    hx_line = {tag: hx_rate(P, ctx, 0, NEV + NBUF, npw, nproj, wl.ng, dt, emu, stream, hbm)
+               for tag, dt, emu in (("fp32", torch.complex64, False), ("fp64_double_float", torch.complex128, True),
+                                    ("fp64", torch.complex128, False))}
+    # FP32 H' flops per column (FFT 8 transforms of 5 Ng log2 Ng, projectors 2 x 8 (2 npw) nproj x 2
+    # spinor columns, 4 x 4 term) against the FP32 CUDA-core peak
+    import math
+    fl = (8 * 5 * wl.ng * math.log2(wl.ng) + 2 * 8 * (2 * npw) * nproj * 2 + 4 * 32 * npw) * (NEV + NBUF)
+    hx_line["fp32"]["gflops"] = fl / (hx_line["fp32"]["ms"] / 1e3) / 1e9
+    hx_line["fp32"]["frac_of_fp32_alu"] = hx_line["fp32"]["gflops"] / fp32_peak
+    # flat copies, so that records which keep only scalars of the roofline object keep these too
+    roof.update({"hx_fp32_gbs": hx_line["fp32"]["achieved_gbs"], "hx_fp32_frac_hbm": hx_line["fp32"]["frac_of_hbm"],
+                 "hx_fp32_frac_fp32_alu": hx_line["fp32"]["frac_of_fp32_alu"],
+                 "hx_df_gbs": hx_line["fp64_double_float"]["achieved_gbs"],
+                 "hx_df_frac_hbm": hx_line["fp64_double_float"]["frac_of_hbm"]})
 
     warm = None if args.no_warm_start else warm_start(P, W, wl, ctx, x, x0, mode, stream)
     ksso = None if args.no_ksso else ksso_section(P, W, wl, ctx, x0, lam, ms, mode, stream)
     dav = None if args.no_davidson else davidson_section(P, ctx, x0, lam, ms, mode, stream)
     scf = None if args.no_scf else scf_section(P, W, wl, ctx, mode, stream)
     sup = supercell_section(P, W, mode, stream) if args.supercell else None
+    lay = None if args.no_layered else layered_section(P, W, mode, stream, hbm)
+    sup_hx = None if args.no_supercell_hx else supercell_hx_section(P, W, stream, hbm)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -686,8 +848,8 @@ def main():
             "e2e": {"value": NEV * ws / (ms_e2e / 1e3), "unit": "eigenpairs/s",
                     "h2d_bytes_per_step": bytes_vec, "d2h_bytes_per_step": bytes_vec + 8 * NEV},
             "gpu_launches": launches, "clocks": clk, "roofline": roof,
-            "cpu_baseline": cpu, "fp64_form": fp64, "warm_start": warm, "ksso": ksso, "davidson_f": dav,
-            "scf": scf, "supercell": sup, "accuracy": acc}
+            "cpu_baseline": cpu, "hx": hx_line, "layered": lay, "supercell_hx": sup_hx, "fp64_form": fp64,
+            "warm_start": warm, "ksso": ksso, "davidson_f": dav, "scf": scf, "supercell": sup, "accuracy": acc}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

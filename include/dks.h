@@ -300,6 +300,45 @@ int dks_rayleigh_ritz(const void* A, const void* S, int nz, int n, void* V, doub
 int dks_rayleigh_ritz_static(const void* A, const void* S, int nz, int n, void* V, double* lam,
                              int* info, void* stream);
 
+/* Failure-detection test hook for the bounded waits of the Rayleigh-Ritz step (no counterpart in
+ * the paper).  The per-column kernels of the device Rayleigh-Ritz step stage the Cholesky factor
+ * and the reflectors into shared memory with TMA bulk copies and wait for them on an mbarrier
+ * for at most first_wait_polls polls (default 1 << 24); a wait that gives up lets the copy land
+ * (a second wait with the full limit), sets a flag in device memory, and the single-CTA kernel
+ * redoes the whole step.  first_wait_polls = 0 makes every such wait give up at once, so that
+ * this path runs on every step; restore 1 << 24 afterwards.  redone (may be NULL) receives the
+ * number of steps redone that way since the previous call, and the count is cleared.
+ * Process-wide, current device.  Synchronous.  Returns DKS_OK or DKS_ERR_CUDA. */
+int dks_debug_rr_wait(unsigned first_wait_polls, unsigned* redone);
+
+/* Tensor cores for the complex64 contractions (the FP32 phase of the mixed mode and DKS_PREC_FP32
+ * blocks).  The tall-skinny contractions that Algorithm 1 and Eq. (HGH) reduce to -- the
+ * rotations X <- Z V and P <- [0, Y, P] V, the Gram matrices of the Rayleigh-Ritz pencil, and
+ * the projector coefficients B^H x~ and update x~ += B D (B^H x~) -- can run on the GB300's
+ * fifth-generation tensor cores (tcgen05 MMA, TMA-staged operands) instead of the FP32 CUDA
+ * cores.  Each FP32 value is split exactly into three bfloat16 slices and every product is
+ * formed from the six leading slice products (left-out terms below 2^-24 of the product), with
+ * FP32 accumulation in tensor memory; the Gram and B^H x~ forms split the long index into
+ * chunks of at most kchunk rows per FP32 accumulation and add the chunk partials in FP64 in a
+ * fixed order.  mask: DKS_TC_* bits (DKS_TC_DEFAULT at load); kchunk <= 0 keeps the current chunk
+ * length (default 512).
+ * Process-wide; a device other than a GB300 (sm_103) keeps the CUDA-core kernels.  Operands
+ * that are not 16-byte aligned or have an odd leading dimension also take the CUDA-core path.
+ * Returns DKS_OK. */
+#define DKS_TC_ROTATE 1   /* X <- Z V, P <- [0, Y, P] V, projections of earlier band blocks */
+#define DKS_TC_GRAM 2     /* S = Z^H Z, A = Z^H HZ (and the other FP32 A^H B Gram forms)    */
+#define DKS_TC_PROJ_HN 4  /* projector coefficients B^H x~                                  */
+#define DKS_TC_PROJ_NN 8  /* projector update x~ += B (D B^H x~)                            */
+#define DKS_TC_ALL 15
+/* default: the projector contractions.  Rotations and Gram matrices stay on the CUDA cores: on
+ * the tensor cores they raise the residual floor of the FP32 phase (the residual H X - X Lambda
+ * is formed from separately rotated X and HX blocks and the negative continuum amplifies what
+ * their rounding leaves), which costs more FP64 iterations than the contraction saves. */
+#define DKS_TC_DEFAULT (DKS_TC_PROJ_HN | DKS_TC_PROJ_NN)
+int dks_tensor_cores(int mask, int kchunk);
+/* the current mask and chunk length */
+int dks_tensor_cores_get(int* mask, int* kchunk);
+
 /* Algorithm 1's rotations (X <- Z V, P <- [0, Y, P] V): OUT[j] = sum_i Z[i] W[i + ldw*j] (+ beta OUT[j]) for
  * j < n, i < nz; Z [nz][rows], OUT [n][rows] (precision prec), W device
  * complex128 column-major with leading dimension ldw (converted to prec). */

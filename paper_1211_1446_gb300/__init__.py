@@ -26,6 +26,7 @@ PREC_FP64, PREC_FP32, PREC_FP64_EMULATED = 0, 1, 2
 MODE_FP64, MODE_MIXED = 0, 1
 PRECOND_TETER, PRECOND_IDENTITY = 0, 1
 
+ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_NEG_STATE, ERR_RANK, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6, -7
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "NOT_CONVERGED", -5: "NEG_STATE",
           -6: "RANK", -7: "TIMEOUT", -8: "GRID", -9: "UNSUPPORTED"}
 
@@ -91,7 +92,7 @@ EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dk
            "dks_ncomp", "dks_density", "dks_hxc", "dks_set_potential", "dks_mixer_create", "dks_mix",
            "dks_mixer_destroy", "dks_scf_opts_default", "dks_scf", "dks_update_potential",
            "dks_density_residual", "dks_autotune", "dks_tune_get", "dks_tune_set", "dks_fft_plan",
-           "dks_debug_check"]
+           "dks_debug_check", "dks_tensor_cores", "dks_tensor_cores_get", "dks_debug_rr_wait"]
 
 _lib = None
 
@@ -154,6 +155,9 @@ def load_library(path: str = LIB_PATH):
     lib.dks_profile_name.restype = C.c_char_p
     lib.dks_profile_enable.argtypes = [i]
     lib.dks_profile_read.argtypes = [i, vp, vp, vp, vp]
+    lib.dks_tensor_cores.argtypes = [i, i]
+    lib.dks_debug_rr_wait.argtypes = [C.c_uint, C.POINTER(C.c_uint)]
+    lib.dks_tensor_cores_get.argtypes = [C.POINTER(i), C.POINTER(i)]
     _lib = lib
     return lib
 
@@ -569,6 +573,30 @@ class Mixer:
             self.close()
         except Exception:
             pass
+
+
+TC_ROTATE, TC_GRAM, TC_PROJ_HN, TC_PROJ_NN, TC_ALL = 1, 2, 4, 8, 15
+
+
+def tensor_cores(mask=None, kchunk=0):
+    """dks_tensor_cores: select which complex64 contractions run on the tcgen05 tensor cores
+    (TC_* bits; None leaves the mask) and the longest FP32 accumulation of the Gram forms
+    (kchunk rows, 0 = unchanged).  Returns the previous (mask, kchunk)."""
+    lib = load_library()
+    m, k = C.c_int(), C.c_int()
+    _check(lib.dks_tensor_cores_get(C.byref(m), C.byref(k)))
+    _check(lib.dks_tensor_cores(int(m.value if mask is None else mask), int(kchunk)))
+    return m.value, k.value
+
+
+def debug_rr_wait(first_wait_polls=1 << 24):
+    """dks_debug_rr_wait: set the polls of the first staging wait of the Rayleigh-Ritz per-column
+    kernels (0: every such wait gives up at once and the single-CTA kernel redoes the step) and
+    return the number of steps redone that way since the previous call."""
+    lib = load_library()
+    n = C.c_uint()
+    _check(lib.dks_debug_rr_wait(int(first_wait_polls), C.byref(n)))
+    return n.value
 
 
 def profile_enable(on=True):

@@ -684,6 +684,18 @@ int dks_rotate(const void* Z, int rows, int nz, const void* W, int ldw, int n, v
                          beta, st);
 }
 
+int dks_debug_rr_wait(unsigned first_wait_polls, unsigned* redone) {
+  if (redone) DKS_TRY(rr_timeout_redos_take(redone));
+  return rr_set_first_wait(first_wait_polls);
+}
+
+int dks_tensor_cores(int mask, int kchunk) {
+  if (mask < 0 || mask > DKS_TC_ALL) return fail(DKS_ERR_INVALID_ARG, "dks_tensor_cores: mask outside DKS_TC_ALL");
+  return tc_set(mask, kchunk);
+}
+
+int dks_tensor_cores_get(int* mask, int* kchunk) { return tc_get(mask, kchunk); }
+
 int dks_residual_norms(const void* X, const void* HX, const double* lam, int rows, int n, double* norms, int prec,
                        void* stream) {
   if (rows <= 0 || rows % 2 || n <= 0 || !X || !HX || !lam || !norms || prec < 0 || prec > 2)

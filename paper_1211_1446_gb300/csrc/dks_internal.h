@@ -228,9 +228,35 @@ int rayleigh_ritz(const double2* a, const double2* s, int nz, int n, double2* v,
                   int* info, double2* scratch, cudaStream_t st, double chol_tol = 1e-12,
                   double drop_tol = 1e-12);
 size_t rr_scratch_elems(int nz);
+// failure-detection test hook: polls of the first staging wait of the per-column Rayleigh-Ritz
+// kernels, and the count (then cleared) of steps the single-CTA kernel redid after such a wait
+// gave up
+int rr_set_first_wait(unsigned polls);
+int rr_timeout_redos_take(unsigned* out);
 template <typename Vi, typename Vo>
 int convert(const Vi* in, Vo* out, size_t n, cudaStream_t st);
 int gather_cols(const double2* v, int ldv, int row0, int rows, const int* act, int nact,
                 double2* out, cudaStream_t st);
+
+// ---------------------------------------------------------------- tensor-core contractions
+// complex64 contractions on tcgen05 with three BF16 slices per FP32 value (tc_gemm.cu); the
+// bits select which of the FP32 contractions take that path (dks_tensor_cores)
+constexpr int TC_ROTATE = DKS_TC_ROTATE, TC_GRAM = DKS_TC_GRAM, TC_PROJ_HN = DKS_TC_PROJ_HN,
+              TC_PROJ_NN = DKS_TC_PROJ_NN, TC_ALL = DKS_TC_ALL, TC_DEFAULT = DKS_TC_DEFAULT;
+bool tc_enabled(int bit);            // bit selected and the device is a GB300 (sm_103)
+int tc_mask();
+int tc_set(int mask, int kchunk);
+int tc_get(int* mask, int* kchunk);
+int tc_status_take();                // DKS_ERR_TIMEOUT when a tensor-core kernel gave up a wait (then cleared)
+bool tc_nn_supported(const float2* a, int lda, int k, int m, int n);
+bool tc_hn_supported(const float2* a, int lda, const float2* b, int ldb, int k);
+// out (k x n) = alpha a (k x m) diag(wscale) w + beta out
+int tc_gemm_nn(const float2* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
+               float2* out, int ldo, double beta, cudaStream_t st, double alpha, int nsm);
+// lower triangles of A = Z^H HZ and S = Z^H Z (m x m), written (not accumulated)
+int tc_gram(const float2* z, const float2* hz, int ld, int k, int m, double2* a, double2* s, cudaStream_t st, int nsm);
+// c = a^H b (m x n, ldc), or with conj_transpose_out c = b^H a (n x m, ldc), written
+int tc_gemm_hn(const float2* a, int lda, const float2* b, int ldb, int k, int m, int n, double2* c, int ldc,
+               bool conj_transpose_out, cudaStream_t st, int nsm);
 
 }  // namespace dks

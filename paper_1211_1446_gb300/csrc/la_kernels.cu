@@ -350,6 +350,19 @@ int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, dou
   if (m <= 0 || n <= 0 || k <= 0) return DKS_OK;
   if (ldc <= 0) ldc = m;
   if (lower && m != n) return fail(DKS_ERR_INVALID_ARG, "gemm_hn: lower-triangle mode needs a square result");
+  if constexpr (std::is_same<Va, float2>::value && std::is_same<Vb, float2>::value && !Acc64) {
+    // tensor cores: the result is written, which equals the accumulation into the zeroed c the
+    // callers provide.  Projector coefficients are formed as (x~^H B)^H so that the wider block
+    // x~ runs along the 128-row MMA dimension.
+    const int bit = cat == P_PROJ_HN ? TC_PROJ_HN : TC_GRAM;
+    if (!lower && tc_enabled(bit) && tc_hn_supported(a, lda, b, ldb, k)) {
+      Prof pr(cat + kProf32, st, ((double)m * sizeof(Va) + (double)n * sizeof(Vb)) * k + 16.0 * m * n,
+              8.0 * m * n * (double)k);
+      pr.count(1);
+      if (cat == P_PROJ_HN && n > m) return tc_gemm_hn(b, ldb, a, lda, k, n, m, c, ldc, true, st, num_sms());
+      return tc_gemm_hn(a, lda, b, ldb, k, m, n, c, ldc, false, st, num_sms());
+    }
+  }
   // 48-row tiles when they pad m less than 32-row tiles (not for the square lower-triangle mode)
   const bool rm3 = !lower && (m + 47) / 48 * 48 < (m + 31) / 32 * 32;
   const int tmr = rm3 ? 48 : HN_T;
@@ -392,6 +405,8 @@ int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, dou
 
 int gram_f32(const float2* z, const float2* hz, int ld, int k, int m, double2* a, double2* s, cudaStream_t st) {
   if (m <= 0 || k <= 0) return DKS_OK;
+  if (tc_enabled(TC_GRAM) && tc_hn_supported(z, ld, hz, ld, k) && tc_hn_supported(z, ld, z, ld, k))
+    return tc_gram(z, hz, ld, k, m, a, s, st, num_sms());
   const int mt = (m + HN_T - 1) / HN_T;
   const int tiles = mt * (mt + 1) / 2;
   const int ktiles = (k + HN_T - 1) / HN_T;
@@ -636,6 +651,14 @@ template <typename Va, typename Vo>
 int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
             Vo* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
   if (k <= 0 || n <= 0) return DKS_OK;
+  if constexpr (std::is_same<Va, float2>::value && std::is_same<Vo, float2>::value) {
+    const int bit = cat == P_PROJ_NN ? TC_PROJ_NN : TC_ROTATE;
+    if (tc_enabled(bit) && tc_nn_supported(a, lda, k, m, n)) {
+      Prof pr(cat + kProf32, st, (double)m * k * sizeof(Va) + (beta != 0.0 ? 2.0 : 1.0) * n * k * sizeof(Vo) + 16.0 * m * n,
+              8.0 * (double)k * m * n);
+      return tc_gemm_nn(a, lda, k, m, w, ldw, wscale, n, out, ldo, beta, st, alpha, num_sms());
+    }
+  }
   const bool f32 = sizeof(Va) == sizeof(float2) && sizeof(Vo) == sizeof(float2);
   Prof pr(f32 && cat < P_RR ? cat + kProf32 : cat, st, (double)m * k * sizeof(Va) + (beta != 0.0 ? 2.0 : 1.0) * n * k * sizeof(Vo) + 16.0 * m * n,
           8.0 * (double)k * m * n);

@@ -1048,10 +1048,16 @@ __device__ __forceinline__ void stage_issue(void* dst, const void* src, uint32_t
   }
 }
 
+// polls allowed to the first wait for each staging copy (the wait whose give-up hands the step
+// to the single-CTA kernel).  1 << 24 in normal use; the failure-detection test hook sets it to
+// 0, so that every such wait gives up at once while the copy itself still lands (the second,
+// draining wait keeps the full limit)
+__device__ unsigned int g_rr_first_wait = 1u << 24;
+
 // every thread: bounded wait for the phase of the mbarrier
-__device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity) {
+__device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity, uint32_t limit = 1u << 24) {
   uint32_t done = 0;
-  for (uint32_t it = 0; it < (1u << 24) && !done; ++it)
+  for (uint32_t it = 0; it < limit && !done; ++it)
     asm volatile(
         "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
         : "=r"(done)
@@ -1066,8 +1072,8 @@ __device__ bool stage_block(void* dst, const void* src, uint32_t bytes, uint64_t
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier generic reads of dst
   __syncthreads();
   if (threadIdx.x == 0) stage_issue(dst, src, bytes, mbar);
-  const bool ok = __syncthreads_and(stage_wait(mbar, phase & 1) ? 1 : 0) != 0;
-  if (!ok) stage_wait(mbar, phase & 1);
+  const bool ok = __syncthreads_and(stage_wait(mbar, phase & 1, g_rr_first_wait) ? 1 : 0) != 0;
+  if (!ok) stage_wait(mbar, phase & 1);   // the copy in flight lands before the block goes on
   ++phase;
   return ok;
 }
@@ -1262,6 +1268,11 @@ __global__ void __launch_bounds__(128, 1) k_rr_backtr(double2* __restrict__ scr,
       info[2] = 0;
     }
   }
+}
+
+int rr_set_first_wait(unsigned polls) {
+  DKS_CUDA_TRY(cudaMemcpyToSymbol(g_rr_first_wait, &polls, sizeof(polls)));
+  return DKS_OK;
 }
 
 // byte offset of the hand-off flag inside the scratch layout above

@@ -681,6 +681,19 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
         const int nv = opts.nev_k ? opts.nev_k[ik] : nev;
         const int n = nv + opts.nbuf;
         const size_t elems = (size_t)n * ctx->ncomp * kp.npw;
+        // a start block with a NaN or infinite entry cannot be iterated (every Gram matrix would
+        // carry it): refuse it before any other work, naming the first such column
+        for (int j0 = 0; j0 < n; j0 += nmax) {
+          const int nc = std::min(nmax, n - j0);
+          const double2* xs = (const double2*)X[ik] + (size_t)j0 * ctx->ncomp * kp.npw;
+          DKS_TRY(col_stats<double2>(xs, xs, sm.lam, kp.ek, kp.npw, nc, sm.stats, ws, ctx->ncomp));
+          DKS_CUDA_TRY(cudaMemcpyAsync(pin.stats, sm.stats, 3 * (size_t)nc * sizeof(double), cudaMemcpyDeviceToHost, ws));
+          DKS_CUDA_TRY(cudaStreamSynchronize(ws));
+          for (int j = 0; j < nc; ++j)
+            if (!std::isfinite(pin.stats[3 * j + 1]))
+              return fail(DKS_ERR_INVALID_ARG, "start block column " + std::to_string(j0 + j) + " of k-point " +
+                                                   std::to_string(ik) + " is not finite");
+        }
         const double C = std::isnan(opts.C) ? kp.cshift : opts.C;
         const double om = std::isnan(opts.Omega) ? kp.omega : opts.Omega;
         std::vector<double>* h = ik == 0 ? &hist : nullptr;
@@ -828,6 +841,9 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
   int status = DKS_OK;
   for (int ik = 0; ik < ctx->nk && status == DKS_OK; ++ik)
     if (krc[ik] != DKS_OK) status = fail(krc[ik], "k-point " + std::to_string(ik) + ": " + kmsg[ik]);
+  // a tensor-core kernel that gave up a bounded wait left its results incomplete
+  if (status == DKS_OK && tc_mask() != 0 && tc_status_take() == DKS_ERR_TIMEOUT)
+    status = fail(DKS_ERR_TIMEOUT, "a tensor-core contraction gave up a bounded wait");
   for (int ik = 0; ik < ctx->nk && status == DKS_OK; ++ik) {
     if (o64s[ik].neg) status = fail(DKS_ERR_NEG_STATE, "a returned eigenvalue lies below the gap midpoint");
     else if (!o64s[ik].converged) status = fail(DKS_ERR_NOT_CONVERGED, "n_iter exhausted");

@@ -1,0 +1,997 @@
+// Tall-skinny complex contractions of Algorithm 1 on the fifth-generation tensor cores (tcgen05).
+//
+// Complex64 blocks are multiplied with FP32 accuracy through BF16 slices: every FP32 value x is
+// the exact sum x = h + m + l of three bfloat16 values (h = bf16(x), m = bf16(x - h),
+// l = x - h - m, each remainder exact in FP32), and a product a b is formed from the six slice
+// products h h' + h m' + m h' + h l' + l h' + m m'; the three that are left out are below
+// 2^-24 |a b| together.  Each slice product is an exact FP32 number, accumulated in FP32 in
+// tensor memory (TMEM).  Complex arithmetic is real arithmetic on interleaved (re, im) pairs:
+//
+//   nn  OUT (rows x n) = A (rows x m) W' (m x n) + beta OUT, W' = alpha diag(ws) W
+//       (rotations X <- Z V, P <- [0, Y, P] V, projector update x~ += B (D Z)):
+//       D[row][c] = sum_k A[row][k] B[c][k] over the interleaved inner index k = 2j + (re, im),
+//       with B[c] = (w_r, -w_i) pairs for the real part of column c and B[n + c] = (w_i, w_r)
+//       for its imaginary part; one MMA of N = 2 n columns gives both.
+//   hn  C (m x n) = A^H B over the tall index (Gram matrices S = Z^H Z, A = Z^H HZ, projector
+//       coefficients B^H x~): D_re = A B^T and D_im = A' B^T over interleaved pairs, with
+//       A' = i A = (-a_i, a_r) formed while the operand is converted.  The tall index is split
+//       across CTAs (chunks of at most kchunk rows, so each FP32 accumulation in TMEM is short);
+//       every CTA writes its FP32 partial tile and a second kernel adds the partials of each
+//       entry in FP64 in a fixed order (deterministic).
+//
+// Data movement: A (and, for hn, B) tiles are copied global -> shared memory by TMA
+// (cp.async.bulk.tensor.2d onto an mbarrier with expect-tx) through a 4-deep staging ring; all
+// 256 threads convert a staged tile into the three BF16 slices in the canonical no-swizzle
+// K-major layout (8-row x 16-byte core matrices); one thread issues the tcgen05.mma
+// instructions (kind::f16, BF16 inputs, FP32 accumulator in TMEM, M = 128) and tcgen05.commit
+// releases the operand buffers; the epilogue reads TMEM with tcgen05.ld.  Every mbarrier wait
+// is bounded: a wait that gives up records DKS_ERR_TIMEOUT in a device status word, the CTA
+// drains its own copies and MMAs in flight (bounded again), frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "dks_internal.h"
+
+namespace dks {
+namespace tc {
+
+constexpr uint32_t kWaitLimit = 1u << 24;   // mbarrier polls before a wait gives up
+constexpr int kM = 128;                     // MMA M (rows of a tile)
+constexpr int kOps = 2;                     // operand (BF16 slice) double buffer
+
+__device__ int g_tc_status = 0;             // DKS_ERR_TIMEOUT after a wait gave up
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+// wait for the phase with the given parity to complete; false when the wait gives up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* holder, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(holder)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// shared-memory writes of the threads -> visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// D[tmem] (+)= A[smem] B[smem]^T, BF16 inputs, FP32 accumulator
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on the mbarrier once every tcgen05 operation issued so far by this thread has completed
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (lane = thread's lane)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor (tcgen05 format): start address, leading-dimension byte
+// offset (next core matrix along K), stride byte offset (next 8-row group), version 1, no
+// swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// x = h + m + l exactly (three BF16 slices), for a pair of values (low half = first)
+__device__ __forceinline__ void split3(float a, float b, uint32_t& h, uint32_t& m, uint32_t& l) {
+  const __nv_bfloat162 hh = __floats2bfloat162_rn(a, b);
+  const float ra = a - __low2float(hh), rb = b - __high2float(hh);
+  const __nv_bfloat162 mm = __floats2bfloat162_rn(ra, rb);
+  const __nv_bfloat162 ll = __floats2bfloat162_rn(ra - __low2float(mm), rb - __high2float(mm));
+  h = *reinterpret_cast<const uint32_t*>(&hh);
+  m = *reinterpret_cast<const uint32_t*>(&mm);
+  l = *reinterpret_cast<const uint32_t*>(&ll);
+}
+// eight consecutive K values of one operand row -> one 16-byte core-matrix row in each slice
+__device__ __forceinline__ void store_slices(unsigned char* base, uint32_t slice_bytes, uint32_t off,
+                                             const float (&v)[8]) {
+  uint32_t h[4], m[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) split3(v[2 * q], v[2 * q + 1], h[q], m[q], l[q]);
+  *reinterpret_cast<uint4*>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(base + slice_bytes + off) = make_uint4(m[0], m[1], m[2], m[3]);
+  *reinterpret_cast<uint4*>(base + 2 * slice_bytes + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+// byte offset of (row r, core-matrix column kg) in a K-major no-swizzle tile with kgs core
+// matrices along K
+__device__ __forceinline__ uint32_t core_off(int r, int kg, int kgs) {
+  return (uint32_t)(((r >> 3) * kgs + kg) * 128 + (r & 7) * 16);
+}
+// slice pairs of the six products, largest first
+__constant__ int kPairA[6] = {0, 0, 1, 0, 2, 1};
+__constant__ int kPairB[6] = {0, 1, 0, 2, 0, 1};
+
+// ================================================================ nn: OUT = A W' (+ beta OUT)
+// W' is split once per call into BF16 slices laid out as the MMA's B operand (k_tc_split_w), per
+// column tile and 16-band chunk.  The main kernel is warp-specialised and persistent over 128-row
+// tiles of one column tile (grid row y: output columns [nt y, nt (y + 1)), nt <= 64):
+//   warp 0       producer: per stage one TMA copy of A (16 bands x 128 rows, FP32) and one bulk
+//                copy of the W' chunk into a staging slot
+//   warp 1       MMA issuer (one lane) and owner of the TMEM allocation
+//   warps 2-9    converters: staged A -> BF16 slices (two operand buffers)
+//   warps 10-17  fold and epilogue: per stage, the leading products h h' are read from TMEM
+//                and added into FP32 registers; at the end of a tile the set of the smaller
+//                products is added and the tile is written (+ beta OUT)
+// TMEM (512 columns): two buffers of the leading products (one per stage in flight, fresh each
+// stage), two buffers of the smaller products (one per tile in flight).  The leading products
+// thus take at most two accumulation steps in TMEM: the tensor core's FP32 accumulation is not
+// correctly rounded, and its error grows coherently when one accumulator takes many steps,
+// while the sums in registers are rounded to nearest.  Every hand-off is an mbarrier; every
+// wait is bounded.
+constexpr int NN_KT = 16;                           // complex inner indices per stage
+constexpr int NN_KR = 2 * NN_KT;                    // interleaved real K per stage (2 MMA K-steps)
+constexpr uint32_t NN_STG_A = kM * NN_KT * 8;       // FP32 staging of A: [16 j][128 rows] float2
+constexpr uint32_t NN_A_SLICE = kM * NN_KR * 2;     // one BF16 slice of A: 128 rows x 32 K
+constexpr int NN_STG_MAX = 8;                       // staging ring depth (chosen per launch)
+constexpr int NN_OPS = 2;                           // A operand buffers
+constexpr int NN_NTMAX = 64;                        // output columns of a CTA's column tile
+constexpr int NN_THREADS = 18 * 32;
+constexpr size_t NN_SMEM_LIMIT = 227 * 1024;
+
+struct NNArgs {
+  int k, m, n, nt, ldo, sw, nstg;
+  const unsigned char* wsl;            // [ytile][chunk][3 slices][2 nt rows][32 K] BF16
+  float2* out;
+  float beta;
+};
+
+__host__ __device__ inline uint32_t nn_b_slice(int nt) { return (uint32_t)(2 * nt) * NN_KR * 2; }
+__host__ inline size_t nn_slot(int nt) { return NN_STG_A + 3 * (size_t)nn_b_slice(nt); }
+__host__ inline size_t nn_fixed() { return 1024 + NN_OPS * 3 * (size_t)NN_A_SLICE + 512; }
+
+// W'[j][c] = alpha ws[j] w[c ldw + j] (rounded to FP32) -> BF16 slices of the B operand: row c of
+// a column tile holds (w_r, -w_i) pairs, row nt + c holds (w_i, w_r); bands j >= m and columns
+// c >= n are zero
+__global__ void k_tc_split_w(const double2* __restrict__ w, int ldw, const double* __restrict__ ws, double alpha,
+                             int m, int n, int nt, int nch, int ytiles, unsigned char* __restrict__ wsl) {
+  const uint32_t bslice = nn_b_slice(nt);
+  const int items = ytiles * nch * nt * 4;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+    const int g = it & 3, c = (it >> 2) % nt, tc_ = (it >> 2) / nt;
+    const int ch = tc_ % nch, yt = tc_ / nch;
+    const int col = yt * nt + c;
+    float re8[8], im8[8];
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+      const int j = ch * NN_KT + 4 * g + q4;
+      float wr = 0.f, wi = 0.f;
+      if (j < m && col < n) {
+        const double2 v = w[(size_t)col * ldw + j];
+        const double sc = (ws ? ws[j] : 1.0) * alpha;
+        wr = (float)(v.x * sc);
+        wi = (float)(v.y * sc);
+      }
+      re8[2 * q4] = wr;
+      re8[2 * q4 + 1] = -wi;
+      im8[2 * q4] = wi;
+      im8[2 * q4 + 1] = wr;
+    }
+    unsigned char* base = wsl + ((size_t)yt * nch + ch) * 3 * bslice;
+    store_slices(base, bslice, core_off(c, g, 4), re8);
+    store_slices(base, bslice, core_off(nt + c, g, 4), im8);
+  }
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(saddr(bar))
+               : "memory");
+}
+
+__global__ void __launch_bounds__(NN_THREADS, 1) k_tc_gemm_nn(const __grid_constant__ CUtensorMap tmap, NNArgs p) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nt = p.nt, nb2 = 2 * nt, n0 = (int)blockIdx.y * nt, nstg = p.nstg;
+  const uint32_t bslice = nn_b_slice(nt);
+  const uint32_t slot = NN_STG_A + 3 * bslice;
+  unsigned char* stg = sm;                                       // [nstg][A FP32 | W' slices]
+  unsigned char* opa = sm + (size_t)nstg * slot;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(opa + NN_OPS * 3 * NN_A_SLICE);
+  uint64_t* stg_full = bars;                        // [nstg] A and W' landed
+  uint64_t* stg_empty = stg_full + NN_STG_MAX;      // [nstg] the MMAs reading the slot completed
+  uint64_t* op_full = stg_empty + NN_STG_MAX;       // [NN_OPS] A slices written (8 converter warps)
+  uint64_t* op_empty = op_full + NN_OPS;            // [NN_OPS] MMAs that read them completed
+  uint64_t* acc_full = op_empty + NN_OPS;           // [2] leading products of a stage in TMEM
+  uint64_t* acc_empty = acc_full + 2;               // [2] read by the 8 fold warps
+  uint64_t* corr_full = acc_empty + 2;              // [2] smaller products of a tile in TMEM
+  uint64_t* corr_empty = corr_full + 2;             // [2] read by the 8 fold warps
+  uint64_t* drainb = corr_empty + 2;                // every MMA issued has completed
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drainb + 1);
+  volatile int* sflag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  const int rowtiles = (p.k + kM - 1) / kM;
+  const int nch = (p.m + NN_KT - 1) / NN_KT;
+  const int my_tiles = blockIdx.x < rowtiles ? (rowtiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int total = my_tiles * nch;
+  const unsigned char* wsl = p.wsl + (size_t)blockIdx.y * nch * 3 * bslice;
+
+  if (tid == 0) {
+    for (int i = 0; i < nstg; ++i) {
+      mbar_init(&stg_full[i], 1);
+      mbar_init(&stg_empty[i], 1);
+    }
+    for (int i = 0; i < NN_OPS; ++i) {
+      mbar_init(&op_full[i], 8);
+      mbar_init(&op_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 8);
+      mbar_init(&corr_full[i], 1);
+      mbar_init(&corr_empty[i], 8);
+    }
+    mbar_init(drainb, 1);
+    *sflag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_holder, 512u);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  const uint32_t hi_col[2] = {0u, (uint32_t)p.sw};
+  const uint32_t corr_col[2] = {(uint32_t)(2 * p.sw), (uint32_t)(3 * p.sw)};
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- producer
+    int issued = 0;
+    if (lane == 0) {
+      for (int q = 0; q < total && !*sflag; ++q) {
+        const int st = q % nstg;
+        if (q >= nstg && !mbar_wait(&stg_empty[st], (uint32_t)((q / nstg) - 1) & 1u)) {
+          *sflag = 1;
+          break;
+        }
+        const int t = blockIdx.x + (q / nch) * gridDim.x, ch = q % nch;
+        unsigned char* s = stg + (size_t)st * slot;
+        mbar_expect_tx(&stg_full[st], slot);
+        tma_load_2d(s, &tmap, 2 * kM * t, NN_KT * ch, &stg_full[st]);
+        bulk_load(s + NN_STG_A, wsl + (size_t)ch * 3 * bslice, 3 * bslice, &stg_full[st]);
+        issued = q + 1;
+      }
+      // copies still in flight land before the CTA exits (bounded)
+      for (int q = std::max(0, issued - nstg); q < issued; ++q)
+        mbar_wait(&stg_full[q % nstg], (uint32_t)(q / nstg) & 1u);
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kM, nb2);
+      const uint64_t da0 = sdesc(saddr(opa), 128, 512), db0 = sdesc(saddr(stg + NN_STG_A), 128, 512);
+      for (int q = 0; q < total && !*sflag; ++q) {
+        const int st = q % nstg, op = q % NN_OPS, b = q & 1, tt = q / nch, ch = q % nch, cb = tt & 1;
+        bool w = mbar_wait(&stg_full[st], (uint32_t)(q / nstg) & 1u);
+        if (w) w = mbar_wait(&op_full[op], (uint32_t)(q / NN_OPS) & 1u);
+        if (w && q >= 2) w = mbar_wait(&acc_empty[b], (uint32_t)((q >> 1) - 1) & 1u);
+        if (w && ch == 0 && tt >= 2) w = mbar_wait(&corr_empty[cb], (uint32_t)((tt >> 1) - 1) & 1u);
+        if (!w) {
+          *sflag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t da = da0 + ((uint64_t)(op * 3 * NN_A_SLICE) >> 4);
+        const uint64_t db = db0 + ((uint64_t)(st * slot) >> 4);
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          mma_bf16(tmem + hi_col[b], da + (uint64_t)(ks * 16), db + (uint64_t)(ks * 16), idesc, (uint32_t)ks);
+#pragma unroll
+          for (int pr = 1; pr < 6; ++pr) {
+            const uint64_t ad = da + ((uint64_t)(kPairA[pr] * NN_A_SLICE + ks * 256) >> 4);
+            const uint64_t bd = db + ((uint64_t)(kPairB[pr] * bslice + ks * 256) >> 4);
+            mma_bf16(tmem + corr_col[cb], ad, bd, idesc, (ch | ks | (pr - 1)) != 0);
+          }
+        }
+        mma_commit(&op_empty[op]);
+        mma_commit(&stg_empty[st]);
+        mma_commit(&acc_full[b]);
+        if (ch == nch - 1) mma_commit(&corr_full[cb]);
+      }
+      mma_commit(drainb);
+      mbar_wait(drainb, 0u);
+    }
+  } else if (warp < 10) {
+    // ---------------------------------------------------------------- converters
+    const int ct = tid - 64;                       // 0 .. 255
+    for (int q = 0; q < total && !*sflag; ++q) {
+      const int st = q % nstg, op = q % NN_OPS;
+      bool w = mbar_wait(&stg_full[st], (uint32_t)(q / nstg) & 1u);
+      if (w && q >= NN_OPS) w = mbar_wait(&op_empty[op], (uint32_t)((q / NN_OPS) - 1) & 1u);
+      if (!w) {
+        *sflag = 1;
+        break;
+      }
+      // A chunk: staging [16 j][128 rows] -> A slices, row r = (re, im) pairs of 16 bands
+      const float2* sg = reinterpret_cast<const float2*>(stg + (size_t)st * slot);
+      unsigned char* oa = opa + (size_t)op * 3 * NN_A_SLICE;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int it = ct + u * 256;
+        const int r = it & (kM - 1), g = it >> 7;
+        float v8[8];
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const float2 a = sg[(4 * g + q4) * kM + r];
+          v8[2 * q4] = a.x;
+          v8[2 * q4 + 1] = a.y;
+        }
+        store_slices(oa, NN_A_SLICE, core_off(r, g, 4), v8);
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&op_full[op]);
+    }
+  } else {
+    // ---------------------------------------------------------------- fold and epilogue
+    const int lq = warp & 3, half = (warp - 10) >> 2;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * lq) << 16);
+    float accr[2][16], acci[2][16];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int e = 0; e < 16; ++e) accr[u][e] = acci[u][e] = 0.f;
+    auto add_set = [&](uint32_t col0) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int c0 = 16 * (2 * u + half);
+        if (c0 < nt) {
+          float re[16], im[16];
+          tmem_ld16(lane_base + col0 + (uint32_t)c0, re);
+          tmem_ld16(lane_base + col0 + (uint32_t)(nt + c0), im);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            accr[u][e] += re[e];
+            acci[u][e] += im[e];
+          }
+        }
+      }
+    };
+    for (int q = 0; q < total && !*sflag; ++q) {
+      const int b = q & 1, tt = q / nch, ch = q % nch, cb = tt & 1;
+      if (!mbar_wait(&acc_full[b], (uint32_t)(q >> 1) & 1u)) {
+        *sflag = 1;
+        break;
+      }
+      tc_fence_after();
+      add_set(hi_col[b]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+      if (ch == nch - 1) {
+        if (!mbar_wait(&corr_full[cb], (uint32_t)(tt >> 1) & 1u)) {
+          *sflag = 1;
+          break;
+        }
+        tc_fence_after();
+        add_set(corr_col[cb]);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&corr_empty[cb]);
+        const int t = blockIdx.x + tt * gridDim.x;
+        const int row = t * kM + 32 * lq + lane;
+        float2* __restrict__ out = p.out;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int c0 = 16 * (2 * u + half);
+          if (c0 >= nt) continue;
+          // beta OUT: every old value of the chunk is loaded before the first store, so the
+          // loads overlap instead of waiting one by one behind possibly aliasing stores
+          if (p.beta != 0.f) {
+#pragma unroll
+            for (int h8 = 0; h8 < 16; h8 += 8) {
+              float2 old[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const int col = n0 + c0 + h8 + e;
+                old[e] = (row < p.k && c0 + h8 + e < nt && col < p.n) ? __ldg(out + (size_t)col * p.ldo + row)
+                                                                     : float2{0.f, 0.f};
+              }
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                accr[u][h8 + e] += p.beta * old[e].x;
+                acci[u][h8 + e] += p.beta * old[e].y;
+              }
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int col = n0 + c0 + e;
+            if (row < p.k && c0 + e < nt && col < p.n)
+              out[(size_t)col * p.ldo + row] = float2{accr[u][e], acci[u][e]};
+            accr[u][e] = acci[u][e] = 0.f;
+          }
+        }
+      }
+    }
+  }
+  if (*sflag && tid == 0) atomicExch(&g_tc_status, DKS_ERR_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512u);
+  }
+}
+
+// ================================================================ hn: C = A^H B (split over K)
+constexpr int HN_KT = 8;                            // complex rows per stage (16 real = one MMA K-step)
+constexpr int HN_KR = 2 * HN_KT;
+constexpr int HN_NB = 256;                          // largest N (B columns) of a tile
+constexpr uint32_t HN_STG_A = kM * HN_KR * 4;       // FP32 staging of A: [128 cols][16 floats]
+constexpr uint32_t HN_STG_B = 128 * HN_KR * 4;      // one B box: [128 cols][16 floats]
+constexpr uint32_t HN_STG_BYTES = HN_STG_A + 2 * HN_STG_B;
+constexpr uint32_t HN_A_SLICE = kM * HN_KR * 2;     // 128 rows x 16 K BF16
+constexpr uint32_t HN_B_SLICE = HN_NB * HN_KR * 2;  // 256 rows x 16 K BF16
+constexpr uint32_t HN_OP_BYTES = 6 * HN_A_SLICE + 3 * HN_B_SLICE;   // A, A' and B slices
+constexpr size_t HN_SMEM_FIXED = 1024 + kOps * (size_t)HN_OP_BYTES + 512;
+
+// One output tile: rows = A columns [ia0, ia0 + 128), columns = B1 columns [jb1, jb1 + nb1)
+// followed by B2 columns [jb2, jb2 + nb2).
+struct HNTile {
+  int ia0, jb1, nb1, jb2, nb2;
+};
+constexpr int kMaxTiles = 64;
+struct HNArgs {
+  int k, kchunk, ntiles, nstg;
+  HNTile tile[kMaxTiles];
+  float2* part;                          // [split][tile][HN_NB cols][128 rows]
+};
+
+// Warp-specialised: warp 0 issues the TMA copies of A and B into a ring of staging slots, warp 1
+// issues the MMAs and owns the TMEM allocation, warps 2-9 convert staged tiles into BF16 slices
+// (A, A' = i A and B; two operand buffers) and, after the last stage, read the partial tile out
+// of TMEM.  Every hand-off is an mbarrier; every wait is bounded.
+constexpr int HN_THREADS = 10 * 32;
+constexpr int HN_STG_MAX = 8;
+
+__global__ void __launch_bounds__(HN_THREADS, 1) k_tc_gemm_hn(const __grid_constant__ CUtensorMap ta,
+                                                             const __grid_constant__ CUtensorMap tb1,
+                                                             const __grid_constant__ CUtensorMap tb2, HNArgs p) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const HNTile tl = p.tile[blockIdx.x];
+  const int nbt = tl.nb1 + tl.nb2;
+  const int nmma = (nbt + 15) & ~15;                   // MMA N (multiple of 16)
+  const int nstg = p.nstg;
+  unsigned char* stg = sm;
+  unsigned char* ops = sm + (size_t)nstg * HN_STG_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ops + kOps * HN_OP_BYTES);
+  uint64_t* stg_full = bars;                           // [nstg] copies landed
+  uint64_t* stg_empty = stg_full + HN_STG_MAX;         // [nstg] converted (8 converter warps)
+  uint64_t* op_full = stg_empty + HN_STG_MAX;          // [kOps] slices written (8 converter warps)
+  uint64_t* op_empty = op_full + kOps;                 // [kOps] MMAs that read them completed
+  uint64_t* accf = op_empty + kOps;                    // every MMA of the CTA completed
+  uint64_t* drainb = accf + 1;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drainb + 1);
+  volatile int* sflag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  const int kb = blockIdx.y * p.kchunk;
+  const int ke = min(p.k, kb + p.kchunk);
+  const int total = ke > kb ? (ke - kb + HN_KT - 1) / HN_KT : 0;
+
+  if (tid == 0) {
+    for (int i = 0; i < nstg; ++i) {
+      mbar_init(&stg_full[i], 1);
+      mbar_init(&stg_empty[i], 8);
+    }
+    for (int i = 0; i < kOps; ++i) {
+      mbar_init(&op_full[i], 8);
+      mbar_init(&op_empty[i], 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(drainb, 1);
+    *sflag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_holder, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;                  // D_re at columns [0, 256), D_im at [256, 512)
+  const uint32_t stg_bytes = HN_STG_A + (tl.nb1 > 0 ? HN_STG_B : 0) + (tl.nb2 > 0 ? HN_STG_B : 0);
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int q = 0; q < total && !*sflag; ++q) {
+        const int st = q % nstg;
+        if (q >= nstg && !mbar_wait(&stg_empty[st], (uint32_t)((q / nstg) - 1) & 1u)) {
+          *sflag = 1;
+          break;
+        }
+        unsigned char* s = stg + (size_t)st * HN_STG_BYTES;
+        const int x = 2 * (kb + q * HN_KT);
+        mbar_expect_tx(&stg_full[st], stg_bytes);
+        tma_load_2d(s, &ta, x, tl.ia0, &stg_full[st]);
+        if (tl.nb1 > 0) tma_load_2d(s + HN_STG_A, &tb1, x, tl.jb1, &stg_full[st]);
+        if (tl.nb2 > 0) tma_load_2d(s + HN_STG_A + HN_STG_B, &tb2, x, tl.jb2, &stg_full[st]);
+        issued = q + 1;
+      }
+      for (int q = std::max(0, issued - nstg); q < issued; ++q)
+        mbar_wait(&stg_full[q % nstg], (uint32_t)(q / nstg) & 1u);
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kM, nmma);
+      const uint64_t d0 = sdesc(saddr(ops), 128, 256);
+      for (int q = 0; q < total && !*sflag; ++q) {
+        const int op = q % kOps;
+        if (!mbar_wait(&op_full[op], (uint32_t)(q / kOps) & 1u)) {
+          *sflag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t da = d0 + ((uint64_t)(op * HN_OP_BYTES) >> 4);
+        const uint64_t da2 = da + ((uint64_t)(3 * HN_A_SLICE) >> 4);
+        const uint64_t db = da + ((uint64_t)(6 * HN_A_SLICE) >> 4);
+#pragma unroll
+        for (int pr = 0; pr < 6; ++pr) {
+          const uint64_t bd = db + ((uint64_t)(kPairB[pr] * HN_B_SLICE) >> 4);
+          const uint64_t oa = (uint64_t)(kPairA[pr] * HN_A_SLICE) >> 4;
+          mma_bf16(tmem, da + oa, bd, idesc, (q | pr) != 0);
+          mma_bf16(tmem + 256, da2 + oa, bd, idesc, (q | pr) != 0);
+        }
+        mma_commit(&op_empty[op]);
+      }
+      mma_commit(accf);
+      mma_commit(drainb);
+      mbar_wait(drainb, 0u);
+    }
+  } else {
+    // ---------------------------------------------------------------- converters, then epilogue
+    const int ct = tid - 64;                          // 0 .. 255
+    for (int q = 0; q < total && !*sflag; ++q) {
+      const int st = q % nstg, op = q % kOps;
+      bool w = mbar_wait(&stg_full[st], (uint32_t)(q / nstg) & 1u);
+      if (w && q >= kOps) w = mbar_wait(&op_empty[op], (uint32_t)((q / kOps) - 1) & 1u);
+      if (!w) {
+        *sflag = 1;
+        break;
+      }
+      const float* sa = reinterpret_cast<const float*>(stg + (size_t)st * HN_STG_BYTES);
+      unsigned char* oa = ops + (size_t)op * HN_OP_BYTES;   // A slices, then A' slices, then B slices
+      unsigned char* oa2 = oa + 3 * HN_A_SLICE;
+      unsigned char* ob = oa + 6 * HN_A_SLICE;
+      {
+        // A and A' = i A: row r = column ia0 + r of A, 16 interleaved values = 8 complex rows
+        const int r = ct >> 1, g = ct & 1;
+        const float* src = sa + r * HN_KR + 8 * g;
+        float v8[8], w8[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v8[e] = src[e];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          w8[2 * e] = -v8[2 * e + 1];
+          w8[2 * e + 1] = v8[2 * e];
+        }
+        store_slices(oa, HN_A_SLICE, core_off(r, g, 2), v8);
+        store_slices(oa2, HN_A_SLICE, core_off(r, g, 2), w8);
+      }
+      // B: rows [0, nb1) from box 1, [nb1, nb1 + nb2) from box 2, zero up to nmma
+      for (int it = ct; it < nmma * 2; it += 256) {
+        const int r = it >> 1, g = it & 1;
+        float v8[8];
+        const float* src = nullptr;
+        if (r < tl.nb1) src = sa + (HN_STG_A / 4) + r * HN_KR + 8 * g;
+        else if (r < nbt) src = sa + ((HN_STG_A + HN_STG_B) / 4) + (r - tl.nb1) * HN_KR + 8 * g;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v8[e] = src ? src[e] : 0.f;
+        store_slices(ob, HN_B_SLICE, core_off(r, g, 2), v8);
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&op_full[op]);
+        mbar_arrive(&stg_empty[st]);
+      }
+    }
+    // epilogue: the partial tile part[split][tile][col][row] (FP32 re, im)
+    if (!*sflag && total > 0) {
+      if (!mbar_wait(accf, 0u)) {
+        *sflag = 1;
+      } else {
+        tc_fence_after();
+        float2* dst = p.part + ((size_t)blockIdx.y * p.ntiles + blockIdx.x) * (size_t)HN_NB * kM;
+        const int lq = warp & 3, half = (warp - 2) >> 2;
+        const int row = 32 * lq + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * lq) << 16);
+        for (int c0 = 16 * half; c0 < nbt; c0 += 32) {
+          float re[16], im[16];
+          tmem_ld16(lane_base + (uint32_t)c0, re);
+          tmem_ld16(lane_base + 256u + (uint32_t)c0, im);
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (c0 + e < nbt) dst[(size_t)(c0 + e) * kM + row] = float2{re[e], im[e]};
+        }
+      }
+    } else if (total == 0) {
+      float2* dst = p.part + ((size_t)blockIdx.y * p.ntiles + blockIdx.x) * (size_t)HN_NB * kM;
+      for (int e = ct; e < nbt * kM; e += 256) dst[e] = float2{0.f, 0.f};
+    }
+  }
+  if (*sflag && tid == 0) atomicExch(&g_tc_status, DKS_ERR_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// Sum of the partial tiles over the splits in FP64, fixed order; 32 entries (consecutive rows
+// of one column of a tile) per warp-slot, the splits spread over the 8 warps and added in warp
+// order.  mode 0: C[(jb + j) * ldc + ia0 + i] (= A^H B), mode 1: C[(ia0 + i) * ldc + jb + j] =
+// conj (= B^H A); gram: B1 columns go to C1, B2 columns to C2, lower triangle only.
+struct RedArgs {
+  int splits, ntiles, m, ldc, mode, gram;
+  HNTile tile[kMaxTiles];
+  const float2* part;
+  double2* c1;
+  double2* c2;
+};
+
+__global__ void __launch_bounds__(256) k_tc_reduce(RedArgs p) {
+  __shared__ double2 red[8][32];
+  const int tile = blockIdx.y;
+  const HNTile tl = p.tile[tile];
+  const int nbt = tl.nb1 + tl.nb2;
+  const int col = blockIdx.x >> 2, r0 = (blockIdx.x & 3) * 32;   // 4 slots of 32 rows per column
+  if (col >= nbt) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = r0 + lane;
+  double sx = 0.0, sy = 0.0;
+  const size_t stride = (size_t)p.ntiles * HN_NB * kM;
+  const float2* src = p.part + (size_t)tile * HN_NB * kM + (size_t)col * kM + row;
+  for (int s = warp; s < p.splits; s += 8) {
+    const float2 v = src[(size_t)s * stride];
+    sx += (double)v.x;
+    sy += (double)v.y;
+  }
+  red[warp][lane] = double2{sx, sy};
+  __syncthreads();
+  if (warp == 0) {
+    double2 t = red[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) {
+      t.x += red[w][lane].x;
+      t.y += red[w][lane].y;
+    }
+    const int i = tl.ia0 + row;
+    const bool second = col >= tl.nb1;
+    const int j = second ? tl.jb2 + (col - tl.nb1) : tl.jb1 + col;
+    if (i < p.m) {
+      if (p.gram) {
+        if (i >= j) (second ? p.c2 : p.c1)[(size_t)j * p.ldc + i] = t;
+      } else if (p.mode == 0) {
+        p.c1[(size_t)j * p.ldc + i] = t;
+      } else {
+        p.c1[(size_t)i * p.ldc + j] = double2{t.x, -t.y};
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host side
+std::mutex g_mu;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+int g_mask = -1;            // contractions on the tensor cores (TC_* bits); -1: not yet read
+int g_kchunk = 512;         // longest K range of one FP32 accumulation in the hn kernel
+bool g_attr_nn = false, g_attr_hn = false;
+
+int encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(DKS_ERR_CUDA, "tensor cores: cuTensorMapEncodeTiled is not available");
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  *out = g_encode;
+  return DKS_OK;
+}
+
+// 2D FP32 tensor map over complex columns: inner = 2 * rows floats, outer = ncols columns of
+// stride ld complex elements; box = (box_inner floats, box_rows columns)
+int make_map(CUtensorMap* map, const void* base, long long rows, int ncols, long long ld, int box_inner, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc;
+  DKS_TRY(encoder(&enc));
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * rows), (cuuint64_t)ncols};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ld * 8)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(DKS_ERR_CUDA, "tensor cores: cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return DKS_OK;
+}
+
+bool aligned_for_tma(const void* p, long long ld) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && (ld & 1) == 0 && ld > 0;
+}
+
+int device_ok() {
+  static int ok = -1;
+  std::lock_guard<std::mutex> g(g_mu);
+  if (ok < 0) {
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    ok = (major == 10 && minor == 3) ? 1 : 0;
+    if (ok) {
+      // the partial tiles are stream-ordered allocations: keep freed blocks in the device's
+      // default pool instead of returning them to the system at every synchronisation
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+    }
+  }
+  return ok;
+}
+
+}  // namespace tc
+
+int tc_mask() {
+  std::lock_guard<std::mutex> g(tc::g_mu);
+  if (tc::g_mask < 0) tc::g_mask = TC_DEFAULT;
+  return tc::g_mask;
+}
+
+bool tc_enabled(int bit) { return (tc_mask() & bit) != 0 && tc::device_ok() == 1; }
+
+int tc_set(int mask, int kchunk) {
+  std::lock_guard<std::mutex> g(tc::g_mu);
+  tc::g_mask = mask & TC_ALL;
+  if (kchunk > 0) tc::g_kchunk = std::max(tc::HN_KT, (kchunk / tc::HN_KT) * tc::HN_KT);
+  return DKS_OK;
+}
+
+int tc_get(int* mask, int* kchunk) {
+  if (mask) *mask = tc_mask();
+  std::lock_guard<std::mutex> g(tc::g_mu);
+  if (kchunk) *kchunk = tc::g_kchunk;
+  return DKS_OK;
+}
+
+int tc_status_take() {
+  int v = 0;
+  DKS_CUDA_TRY(cudaMemcpyFromSymbol(&v, tc::g_tc_status, sizeof(int)));
+  if (v) {
+    const int z = 0;
+    DKS_CUDA_TRY(cudaMemcpyToSymbol(tc::g_tc_status, &z, sizeof(int)));
+  }
+  return v;
+}
+
+bool tc_nn_supported(const float2* a, int lda, int k, int m, int n) {
+  return k > 0 && m > 0 && n > 0 && tc::aligned_for_tma(a, lda);
+}
+
+int tc_gemm_nn(const float2* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
+               float2* out, int ldo, double beta, cudaStream_t st, double alpha, int nsm) {
+  using namespace tc;
+  if (k <= 0 || n <= 0) return DKS_OK;
+  CUtensorMap map;
+  DKS_TRY(make_map(&map, a, k, m, lda, 2 * kM, NN_KT));
+  const int ytiles = (n + NN_NTMAX - 1) / NN_NTMAX;
+  const int nt = ((n + ytiles - 1) / ytiles + 7) & ~7;
+  const int sw = (nt + ((nt + 15) & ~15) + 31) & ~31;   // one accumulator buffer (<= 128 columns)
+  const int nch = (m + NN_KT - 1) / NN_KT;
+  const int nstg = (int)std::min<size_t>(NN_STG_MAX, (NN_SMEM_LIMIT - nn_fixed()) / nn_slot(nt));
+  const size_t smem = nn_fixed() + (size_t)nstg * nn_slot(nt);
+  {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!g_attr_nn) {
+      DKS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_tc_gemm_nn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)NN_SMEM_LIMIT));
+      g_attr_nn = true;
+    }
+  }
+  // W' in BF16 slices, per column tile and chunk (stream-ordered scratch)
+  const size_t wbytes = (size_t)ytiles * nch * 3 * nn_b_slice(nt);
+  unsigned char* wsl = nullptr;
+  DKS_CUDA_TRY(cudaMallocAsync((void**)&wsl, wbytes, st));
+  const int items = ytiles * nch * nt * 4;
+  k_tc_split_w<<<std::max(1, std::min(4 * nsm, (items + 255) / 256)), 256, 0, st>>>(w, ldw, wscale, alpha, m, n, nt,
+                                                                                 nch, ytiles, wsl);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    const int rowtiles = (k + kM - 1) / kM;
+    const int gx = std::max(1, std::min(rowtiles, nsm / ytiles));
+    NNArgs p;
+    p.k = k;
+    p.m = m;
+    p.n = n;
+    p.nt = nt;
+    p.ldo = ldo;
+    p.sw = sw;
+    p.nstg = nstg;
+    p.wsl = wsl;
+    p.out = out;
+    p.beta = (float)beta;
+    k_tc_gemm_nn<<<dim3(gx, ytiles), NN_THREADS, smem, st>>>(map, p);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(wsl, st);
+  if (e != cudaSuccess) return fail(DKS_ERR_CUDA, std::string("tensor-core OUT = A W launch: ") + cudaGetErrorString(e));
+  return DKS_OK;
+}
+
+bool tc_hn_supported(const float2* a, int lda, const float2* b, int ldb, int k) {
+  return k > 0 && tc::aligned_for_tma(a, lda) && tc::aligned_for_tma(b, ldb);
+}
+
+// C = A^H [B1 | B2] over k rows on the tensor cores.  gram: A = Z (m columns), B1 = HZ, B2 = Z,
+// lower triangles of c1 = Z^H HZ and c2 = Z^H Z (m x m, ldc = m).  Otherwise B2 is absent and
+// c1 (ldc) receives A^H B1 (mode 0) or its conjugate transpose B1^H A (mode 1).
+int tc_gemm_hn_impl(const float2* a, int lda, int m, const float2* b1, const float2* b2, int ldb, int n, int k,
+                    double2* c1, double2* c2, int ldc, int mode, bool gram, cudaStream_t st, int nsm) {
+  using namespace tc;
+  if (k <= 0 || m <= 0 || n <= 0) return DKS_OK;
+  RedArgs r{};
+  HNArgs p{};
+  int nt = 0;
+  const int mt = (m + kM - 1) / kM;
+  if (gram) {
+    // tiles (ib, jb), jb <= ib, of 128 rows and 128 + 128 columns (HZ, Z)
+    for (int ib = 0; ib < mt; ++ib)
+      for (int jb = 0; jb <= ib; ++jb) {
+        if (nt >= kMaxTiles) return fail(DKS_ERR_UNSUPPORTED, "tensor-core Gram: too many tiles");
+        const int nbj = std::min(kM, m - jb * kM);
+        p.tile[nt++] = HNTile{ib * kM, jb * kM, nbj, jb * kM, nbj};
+      }
+  } else {
+    // up to 256 B columns per tile: the first 128 through box 1, the rest through box 2 (the
+    // same tensor)
+    for (int ib = 0; ib < mt; ++ib)
+      for (int j0 = 0; j0 < n; j0 += HN_NB) {
+        if (nt >= kMaxTiles) return fail(DKS_ERR_UNSUPPORTED, "tensor-core A^H B: too many tiles");
+        const int cnt = std::min(HN_NB, n - j0), n1 = std::min(128, cnt);
+        p.tile[nt++] = HNTile{ib * kM, j0, n1, j0 + 128, cnt - n1};
+      }
+  }
+  int kchunk;
+  {
+    std::lock_guard<std::mutex> g(g_mu);
+    kchunk = g_kchunk;
+    if (!g_attr_hn) {
+      DKS_CUDA_TRY(cudaFuncSetAttribute((const void*)k_tc_gemm_hn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)NN_SMEM_LIMIT));
+      g_attr_hn = true;
+    }
+  }
+  // splits: each K range at most kchunk rows, rounded up to whole waves of one CTA per SM, and
+  // the partial tiles (256 KB per CTA) held to kPartBudget (longer ranges beyond that)
+  constexpr size_t kPartBudget = 256u << 20;
+  const size_t tile_bytes = (size_t)HN_NB * kM * sizeof(float2);
+  long long splits = (k + kchunk - 1) / kchunk;
+  const long long waves = (splits * nt + nsm - 1) / nsm;
+  splits = std::max(splits, waves * nsm / nt);
+  splits = std::max(1LL, std::min(splits, (long long)(kPartBudget / (tile_bytes * nt))));
+  const int kc = (int)(((k + splits - 1) / splits + HN_KT - 1) / HN_KT * HN_KT);
+  splits = (k + kc - 1) / kc;
+  CUtensorMap ta, tb1, tb2;
+  DKS_TRY(make_map(&ta, a, k, m, lda, HN_KR, kM));
+  DKS_TRY(make_map(&tb1, b1, k, gram ? m : n, ldb, HN_KR, 128));
+  DKS_TRY(make_map(&tb2, b2 ? b2 : b1, k, gram ? m : n, ldb, HN_KR, 128));
+  const size_t part_bytes = (size_t)splits * nt * tile_bytes;
+  float2* part = nullptr;
+  DKS_CUDA_TRY(cudaMallocAsync((void**)&part, part_bytes, st));
+  const int nstg = (int)std::min<size_t>(HN_STG_MAX, (NN_SMEM_LIMIT - HN_SMEM_FIXED) / HN_STG_BYTES);
+  p.k = k;
+  p.kchunk = kc;
+  p.ntiles = nt;
+  p.nstg = nstg;
+  p.part = part;
+  k_tc_gemm_hn<<<dim3(nt, (unsigned)splits), HN_THREADS, HN_SMEM_FIXED + (size_t)nstg * HN_STG_BYTES, st>>>(ta, tb1,
+                                                                                                           tb2, p);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    r.splits = (int)splits;
+    r.ntiles = nt;
+    r.m = m;
+    r.ldc = ldc;
+    r.mode = mode;
+    r.gram = gram ? 1 : 0;
+    for (int t = 0; t < nt; ++t) r.tile[t] = p.tile[t];
+    r.part = part;
+    r.c1 = c1;
+    r.c2 = c2;
+    k_tc_reduce<<<dim3(HN_NB * 4, nt), 256, 0, st>>>(r);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(part, st);
+  if (e != cudaSuccess) return fail(DKS_ERR_CUDA, std::string("tensor-core A^H B launch: ") + cudaGetErrorString(e));
+  return DKS_OK;
+}
+
+int tc_gram(const float2* z, const float2* hz, int ld, int k, int m, double2* a, double2* s, cudaStream_t st, int nsm) {
+  Prof pr(P_GRAM + kProf32, st, 2.0 * m * 8.0 * k + 32.0 * m * m, 8.0 * m * (m + 1.0) * (double)k);
+  pr.count(1);
+  return tc_gemm_hn_impl(z, ld, m, hz, z, ld, m, k, a, s, m, 0, true, st, nsm);
+}
+
+int tc_gemm_hn(const float2* a, int lda, const float2* b, int ldb, int k, int m, int n, double2* c, int ldc,
+               bool conj_transpose_out, cudaStream_t st, int nsm) {
+  return tc_gemm_hn_impl(a, lda, m, b, nullptr, ldb, n, k, c, nullptr, ldc, conj_transpose_out ? 1 : 0, false, st,
+                         nsm);
+}
+
+}  // namespace dks
