@@ -144,7 +144,7 @@ def cpu_oracle_sample(wl, nev, n_iter_ref, budget_s=20.0):
     full = max(t_init, 0.0) + per_it * n_iter_ref
     cores = len(os.sched_getaffinity(0))
     sample = (f"oracle Algorithm 1 on the same dimer: initial filtering + {len(marks) - 2} iterations "
-              f"({marks[-1] - t0:.1f} s), scaled to {n_iter_ref} iterations")
+              f"({marks[-1] - t0:.1f} s), extrapolated to {n_iter_ref} iterations")
     return nev / full, cores, sample, full
 
 
@@ -224,7 +224,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "mode": "fp64 oracle (numpy/scipy)"},
             "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "extrapolated": True},
             "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -834,7 +834,8 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, cores, sample, full = cpu_oracle_sample(wl, NEV, acc["iterations"])
-        cpu = {"value": v, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "extrapolated": True}
         try:
             cpu["other_configs"] = cpu_configs_section(acc["iterations"])
         except Exception as exc:                                  # a baseline must not cost the bench line
@@ -842,9 +843,15 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if mode == P.MODE_MIXED else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32+df64" if mode == P.MODE_MIXED else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "mode": args.mode, "parallelism": f"replicas x{ws}",
-                       "l2": "working set (>1 GB of blocks per solve) exceeds the 129 MB L2"},
+                       "l2": "working set (>1 GB of blocks per solve) exceeds the 129 MB L2",
+                       "dtype_note": ("FP32 phase (complex64; projector contractions on tcgen05 tensor cores "
+                                      "with three BF16 slices per FP32 value), then the FP64 refinement with "
+                                      "complex128 storage whose contractions and FFTs run in double-float "
+                                      "arithmetic (about 2^-48 per operation); Rayleigh-Ritz in FP64"
+                                      if mode == P.MODE_MIXED else "FP64"),
+                       "tensor_cores_mask": P.tensor_cores()[0]},
             "e2e": {"value": NEV * ws / (ms_e2e / 1e3), "unit": "eigenpairs/s",
                     "h2d_bytes_per_step": bytes_vec, "d2h_bytes_per_step": bytes_vec + 8 * NEV},
             "gpu_launches": launches, "clocks": clk, "roofline": roof,
