@@ -15,7 +15,9 @@ e2e    = the same through the public C ABI with the start block in pinned host m
 roofline = the kernel category with the largest device time inside the timed region, its
          algorithmic bytes (or flops) per launch divided by its mean CUDA-event duration.
 Multi-GPU (torchrun): every rank solves its own replica of the single-k-point dimer (weak
-scaling, no collective in the solve); the only collectives are the timing barrier and max.
+scaling, no collective in the solve); the only collectives are the timing barrier and max.  The
+layered-crystal section then splits its 16 k-points into contiguous cost-balanced shards, one per
+rank (no collective in the solve, one gather of the eigenvalues at the end).
 """
 from __future__ import annotations
 
@@ -488,6 +490,57 @@ def hx_rate(P, ctx, ik, nb, npw, nproj, ng, dtype, emulated, stream, hbm, reps=5
             "frac_of_hbm": alg / t / 1e9 / hbm}
 
 
+def layered_sharded(P, W, mode, stream, ws, rank, nbuf=8):
+    """The layered crystal on ws GPUs, one process each: the 16 k-points are split into contiguous
+    blocks balanced by (nev_k + nbuf) npw_k (paper_1211_1446_gb300.shard; npw_k taken as
+    proportional to Ecut_k^(3/2)), every rank solves its own k-points with no collective, and the
+    eigenvalues are gathered once at the end.  Time = the slowest rank's (max over ranks, after
+    a barrier); eigenpairs/s counts every rank's pairs."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1211_1446_gb300 import shard
+    wl = W.make("layered")
+    nev_all = [int(v) for v in wl.nev_k]
+    costs = [(nev_all[ik] + nbuf) * float(wl.ecut_k[ik]) ** 1.5 for ik in range(wl.nk)]
+    mine = shard.kpoint_shards(costs, ws)[rank]
+    out = {"ranks": ws, "kpoints_per_rank": [len(b) for b in shard.kpoint_shards(costs, ws)]}
+    lam, ms = {}, 0.0
+    if mine:
+        wk = dataclasses.replace(wl, kfrac=wl.kfrac[mine], ecut_k=wl.ecut_k[mine], nev_k=wl.nev_k[mine])
+        ctx = P.Context.from_workload(wk)
+        nev_k = [nev_all[ik] for ik in mine]
+        x0 = [torch.from_numpy(W.start_block(ctx.npw(i), nev_k[i] + nbuf, wl.seed, ik)).cuda()
+              for i, ik in enumerate(mine)]
+        xs = [t.clone() for t in x0]
+        ctx.solve(xs, 0, nev_k=nev_k, nbuf=nbuf, tol=TOL, mode=mode, n_iter=1, check=False)   # workspaces
+        for a, b in zip(xs, x0):
+            a.copy_(b)
+    torch.cuda.synchronize()
+    dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc = 0
+    if mine:
+        lk, rep, rc = ctx.solve(xs, 0, nev_k=nev_k, nbuf=nbuf, tol=TOL, mode=mode, check=False, stream=stream)
+        lam = {ik: lk[i] for i, ik in enumerate(mine)}
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = shard.max_over_ranks(e0.elapsed_time(e1))
+    allk = shard.gather_eigenvalues(lam)
+    worst = shard.max_over_ranks(float(-rc))                    # status codes are <= 0
+    out.update({"status": -int(worst), "ms": ms, "eigenpairs": sum(nev_all),
+                "eigenpairs_per_s": sum(nev_all) / (ms / 1e3), "kpoints_gathered": len(allk)})
+    gold = os.path.join(HERE, "tests", "golden", "layered_k0_eigs.txt")
+    if 0 in allk and os.path.exists(gold):
+        g = np.loadtxt(gold)
+        out["max_eig_err_vs_oracle_k0"] = float(np.abs(allk[0][:len(g)] - g).max())
+    return out
+
+
 def layered_section(P, W, mode, stream, hbm, nbuf=8, sample=(4, 9)):
     """The layered crystal (hexagonal a = 7.8, c = 28 bohr, 15 sites, 270 spin-orbit projector
     channels, 60 x 60 x 216 grid, 16 k-points with their own spheres of about 39,000-41,000
@@ -828,8 +881,13 @@ def main():
     dav = None if args.no_davidson else davidson_section(P, ctx, x0, lam, ms, mode, stream)
     scf = None if args.no_scf else scf_section(P, W, wl, ctx, mode, stream)
     sup = supercell_section(P, W, mode, stream) if args.supercell else None
-    lay = None if args.no_layered else layered_section(P, W, mode, stream, hbm)
-    sup_hx = None if args.no_supercell_hx else supercell_hx_section(P, W, stream, hbm)
+    if args.no_layered:
+        lay = None
+    elif ws > 1:
+        lay = layered_sharded(P, W, mode, stream, ws, rank)     # k-point shards, one per GPU
+    else:
+        lay = layered_section(P, W, mode, stream, hbm)
+    sup_hx = None if (args.no_supercell_hx or ws > 1) else supercell_hx_section(P, W, stream, hbm)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
