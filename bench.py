@@ -626,30 +626,49 @@ def supercell_hx_section(P, W, stream, hbm, nb=160):
     return out
 
 
-def supercell_section(P, W, mode, stream, block=128, nbuf=32, tol=1e-6):
+def supercell_section(P, W, mode, stream, kpoints=4, block=128, nbuf=32, tol=1e-6, nev=None):
     """The large-cell configuration (2 x 2 x 1 supercell of the layered crystal: 120 x 120 x 216
-    grid, about 158,000 planewaves per k, 1080 projector channels, 4 k-points, 480 pairs each),
-    solved in band blocks of `block` wanted + nbuf buffer columns with deflation.  Opt-in
-    (--supercell): it holds most of the GPU's memory and runs for minutes."""
+    grid, about 158,000 planewaves per k, 1080 projector channels, 480 pairs per k-point), solved
+    in band blocks of `block` wanted + nbuf buffer columns with deflation, k-point by k-point
+    (the first `kpoints` of the 2 x 2 x 1 mesh), each k-point's result printed to stderr as soon
+    as it is known.  Opt-in (--supercell): it holds most of the GPU's memory and runs for minutes
+    per k-point."""
+    import dataclasses
+
     import torch
     wl = W.make("supercell")
-    ctx = P.Context.from_workload(wl)
-    nev_k = [int(v) for v in wl.nev_k]
-    xs = [torch.from_numpy(W.start_block(ctx.npw(ik), nev_k[ik] + nbuf, wl.seed, ik)).cuda() for ik in range(wl.nk)]
-    torch.cuda.synchronize()
+    out = {"workload": "supercell 2x2x1 of the layered crystal: 120x120x216 grid, 1080 SO projector channels, "
+                       f"480 pairs per k in band blocks of {block} + {nbuf} buffer columns",
+           "kpoints": []}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    lam, rep, rc = ctx.solve(xs, 0, nev_k=nev_k, nbuf=nbuf, tol=tol, mode=mode, block=block, check=False,
-                             stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    out = {"status": int(rc), "message": rep["message"], "ms": ms, "eigenpairs": sum(nev_k),
-           "eigenpairs_per_s": sum(nev_k) / (ms / 1e3), "block": block, "nbuf": nbuf,
-           "npw": [ctx.npw(ik) for ik in range(wl.nk)], "iterations": rep["iterations"][:wl.nk],
-           "fp64_iterations": rep["fp64_iterations"][:wl.nk], "max_residual": rep["max_residual"][:wl.nk],
-           "tuning": ctx.tuning()}
-    ctx.close()
+    for ik in range(min(kpoints, wl.nk)):
+        wk = dataclasses.replace(wl, kfrac=wl.kfrac[ik:ik + 1], ecut_k=wl.ecut_k[ik:ik + 1], nev_k=wl.nev_k[ik:ik + 1])
+        ctx = P.Context.from_workload(wk)
+        nv = int(wl.nev_k[ik]) if nev is None else int(nev)
+        x = torch.from_numpy(W.start_block(ctx.npw(0), nv + nbuf, wl.seed, ik)).cuda()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lam, rep, rc = ctx.solve([x], nv, nbuf=nbuf, tol=tol, mode=mode, block=block if nv > block else 0,
+                                 check=False, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        row = {"k": ik, "status": int(rc), "message": rep["message"], "ms": ms, "eigenpairs": nv,
+               "eigenpairs_per_s": nv / (ms / 1e3), "npw": ctx.npw(0), "iterations": rep["iterations"][0],
+               "fp64_iterations": rep["fp64_iterations"][0], "max_residual": rep["max_residual"][0],
+               "h_applications": rep["h_applications"], "lowest_eigs": [float(v) for v in lam[0][:4]],
+               "residual_history": [float(f"{v:.3g}") for v in rep["history"]]}
+        if rc == 0:
+            row["kramers_max_split"] = float(abs(lam[0][0::2] - lam[0][1::2]).max()) if ik == 0 else None
+        out["kpoints"].append(row)
+        print(json.dumps({"supercell_kpoint": row}), file=sys.stderr, flush=True)
+        ctx.close()
+        del x
+        torch.cuda.empty_cache()
+    done = [r for r in out["kpoints"] if r["status"] == 0]
+    out["eigenpairs_per_s"] = (sum(r["eigenpairs"] for r in out["kpoints"]) /
+                               (sum(r["ms"] for r in out["kpoints"]) / 1e3)) if out["kpoints"] else None
+    out["all_converged"] = len(done) == len(out["kpoints"])
     return out
 
 
@@ -658,7 +677,9 @@ def tc_study(masks, reps):
     bench configuration) reps times for each DKS_TC_* mask, recording the FP32 phase's residual
     floor (lowest residual before the hand-off), the FP64-phase iterations and the solve time.
     The FP32 floor sets how many FP64 iterations remain, so a contraction belongs on the tensor
-    cores only if it leaves the floor where the CUDA-core kernels put it."""
+    cores only if it leaves the floor where the CUDA-core kernels put it.  Repeat r starts from
+    the seeded block of seed + r, the same starts for every mask (a deterministic path gives the
+    same trajectory every time from one start)."""
     import numpy as np
     import torch
 
@@ -666,8 +687,8 @@ def tc_study(masks, reps):
     import workloads as W
     wl = W.make("dimer")
     ctx = P.Context.from_workload(wl)
-    x0 = torch.from_numpy(W.start_block(ctx.npw(0), NEV + NBUF, wl.seed)).cuda()
-    x = torch.empty_like(x0)
+    x0s = [torch.from_numpy(W.start_block(ctx.npw(0), NEV + NBUF, wl.seed + r)).cuda() for r in range(reps)]
+    x = torch.empty_like(x0s[0])
     gold = np.loadtxt(os.path.join(HERE, "tests", "golden", "dimer_lobpcgf_eigs.txt"))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     old = P.tensor_cores()
@@ -675,8 +696,8 @@ def tc_study(masks, reps):
     for mask in masks:
         P.tensor_cores(mask)
         rows = []
-        for _ in range(reps):
-            x.copy_(x0)
+        for r in range(reps):
+            x.copy_(x0s[r])
             torch.cuda.synchronize()
             e0.record()
             lam, rep, rc = ctx.solve([x], NEV, tol=TOL, mode=P.MODE_MIXED, nbuf=NBUF, check=False)
@@ -708,8 +729,12 @@ def main():
     ap.add_argument("--no-ksso", action="store_true")
     ap.add_argument("--no-davidson", action="store_true")
     ap.add_argument("--no-scf", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch parameters instead of running dks_autotune before the timed solves")
     ap.add_argument("--no-layered", action="store_true", help="skip the layered-crystal (16 k-point) section")
     ap.add_argument("--no-supercell-hx", action="store_true", help="skip H' bandwidth at the supercell size")
+    ap.add_argument("--supercell-kpoints", type=int, default=4, help="k-points of the supercell solve (1-4)")
+    ap.add_argument("--supercell-nev", type=int, default=None, help="pairs per k-point of the supercell solve (480)")
     ap.add_argument("--supercell", action="store_true",
                     help="also solve the large-cell configuration in band blocks (minutes, most of the GPU memory)")
     ap.add_argument("--ref-iterations", type=int, default=60)
@@ -750,6 +775,12 @@ def main():
     ctx = P.Context.from_workload(wl)
     npw = ctx.npw(0)
     mode = P.MODE_MIXED if args.mode == "mixed" else P.MODE_FP64
+    # launch parameters and the projector contraction schedule from the autotuner (H' on the
+    # solve's block width, FP32: the phase that applies H' most often), before anything is timed
+    tune = None
+    if not args.no_tune:
+        tune = ctx.autotune(0, nb=NEV + NBUF, prec=P.PREC_FP32)
+        tune.pop("candidates", None)
     x0 = torch.from_numpy(W.start_block(npw, NEV + NBUF, wl.seed)).cuda()
     x = torch.empty_like(x0)
     stream = torch.cuda.current_stream()
@@ -852,6 +883,19 @@ def main():
         ach = d["flops"] / max(d["launches"], 1) / per_launch_s / 1e9
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "GFLOP/s", "frac": ach / pk,
                 "peak_source": psrc}
+    # the largest single kernel of the launch list: the double-float OUT = A W' kernel (k_gemm_nn_df4),
+    # which serves the refinement phase's rotations and projector updates (two categories)
+    if mode == P.MODE_MIXED:
+        cats = [c for c in ("rotate", "proj_b_dz") if prof.get(c, {}).get("launches")]
+        if cats:
+            f = sum(prof[c]["flops"] for c in cats)
+            t = sum(prof[c]["ms"] for c in cats) / 1e3
+            roof.update({"top_kernel": "k_gemm_nn_df4 (double-float rotations and projector updates)",
+                         "top_kernel_share_of_step": t * 1e3 / (ms * args.steps),
+                         "top_kernel_gflops": f / t / 1e9, "top_kernel_peak_gflops": df_peak,
+                         "top_kernel_frac": f / t / 1e9 / df_peak,
+                         "top_kernel_peak_source": "derived: FP64-equivalent rate of the double-float multiply-add "
+                                                   "(15 FP32 instructions) on 152 SMs x 128 FP32 lanes x 2070 MHz"})
     tr = NCU_TRAFFIC.get(dom)
     roof.update({"traffic": tr["bytes_per_launch"] if tr else None,
                  "traffic_note": tr["note"] if tr else "no ncu DRAM capture of this category's kernels",
@@ -880,7 +924,8 @@ def main():
     ksso = None if args.no_ksso else ksso_section(P, W, wl, ctx, x0, lam, ms, mode, stream)
     dav = None if args.no_davidson else davidson_section(P, ctx, x0, lam, ms, mode, stream)
     scf = None if args.no_scf else scf_section(P, W, wl, ctx, mode, stream)
-    sup = supercell_section(P, W, mode, stream) if args.supercell else None
+    sup = (supercell_section(P, W, mode, stream, kpoints=args.supercell_kpoints, nev=args.supercell_nev)
+           if args.supercell else None)
     if args.no_layered:
         lay = None
     elif ws > 1:
@@ -909,7 +954,7 @@ def main():
                                       "complex128 storage whose contractions and FFTs run in double-float "
                                       "arithmetic (about 2^-48 per operation); Rayleigh-Ritz in FP64"
                                       if mode == P.MODE_MIXED else "FP64"),
-                       "tensor_cores_mask": P.tensor_cores()[0]},
+                       "tensor_cores_mask": P.tensor_cores()[0], "tuning": tune or "defaults"},
             "e2e": {"value": NEV * ws / (ms_e2e / 1e3), "unit": "eigenpairs/s",
                     "h2d_bytes_per_step": bytes_vec, "d2h_bytes_per_step": bytes_vec + 8 * NEV},
             "gpu_launches": launches, "clocks": clk, "roofline": roof,

@@ -473,6 +473,10 @@ typedef struct {
   int plane_threads[32];
   int plane_split[32];
   double ms[32];              /* mean time of one H' application on the nb columns     */
+  int proj_tc;                /* contraction schedule chosen for the projector terms of
+                                 complex64 blocks: 0 CUDA cores, 1 tensor cores; -1 when not
+                                 tuned (prec other than FP32, no projectors, not a GB300)  */
+  double proj_ms[2];          /* H' time with each (at the chosen FFT parameters)       */
 } dks_tune_report;
 /* dks_autotune: times dks_apply_H on an nb-column scratch block of k-point ik in precision
  * prec (device memory allocated and freed on `stream`) for chunk budgets {16, 32, 64, 128} MB
@@ -485,6 +489,12 @@ int dks_autotune(dks_ctx* ctx, int ik, int nb, int prec, void* stream, dks_tune_
  * or a multiple of 32 in 64..512; plane_split 0 or 1.  Errors: INVALID_ARG. */
 int dks_tune_get(const dks_ctx* ctx, long long* fft_chunk_bytes, int* plane_threads, int* plane_split);
 int dks_tune_set(dks_ctx* ctx, long long fft_chunk_bytes, int plane_threads, int plane_split);
+/* The context's contraction schedule for the projector terms of complex64 blocks (Eq. HGH:
+ * B^H x~ and x~ += B D (B^H x~)): -1 follows the process-wide dks_tensor_cores mask (the
+ * default), 0 the CUDA-core kernels, 1 the tcgen05 tensor-core kernels.  dks_autotune with
+ * prec FP32 times both and sets it. */
+int dks_tune_contractions_get(const dks_ctx* ctx, int* proj_tc);
+int dks_tune_contractions_set(dks_ctx* ctx, int proj_tc);
 
 /* ------------------------------------------------ instrumentation (no counterpart in the paper;
  * the solve report's phase timers of a production code).  Every kernel launch of the library is

@@ -81,7 +81,8 @@ class ScfReport(C.Structure):
 
 class TuneReport(C.Structure):
     _fields_ = [("ncand", C.c_int), ("best", C.c_int), ("chunk_bytes", C.c_longlong * 32),
-                ("plane_threads", C.c_int * 32), ("plane_split", C.c_int * 32), ("ms", C.c_double * 32)]
+                ("plane_threads", C.c_int * 32), ("plane_split", C.c_int * 32), ("ms", C.c_double * 32),
+                ("proj_tc", C.c_int), ("proj_ms", C.c_double * 2)]
 
 
 EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dks_filter_constants",
@@ -92,7 +93,8 @@ EXPORTS = ["dks_create", "dks_destroy", "dks_npw", "dks_basis", "dks_nproj", "dk
            "dks_ncomp", "dks_density", "dks_hxc", "dks_set_potential", "dks_mixer_create", "dks_mix",
            "dks_mixer_destroy", "dks_scf_opts_default", "dks_scf", "dks_update_potential",
            "dks_density_residual", "dks_autotune", "dks_tune_get", "dks_tune_set", "dks_fft_plan",
-           "dks_debug_check", "dks_tensor_cores", "dks_tensor_cores_get", "dks_debug_rr_wait"]
+           "dks_debug_check", "dks_tensor_cores", "dks_tensor_cores_get", "dks_debug_rr_wait",
+           "dks_tune_contractions_get", "dks_tune_contractions_set"]
 
 _lib = None
 
@@ -156,6 +158,8 @@ def load_library(path: str = LIB_PATH):
     lib.dks_profile_enable.argtypes = [i]
     lib.dks_profile_read.argtypes = [i, vp, vp, vp, vp]
     lib.dks_tensor_cores.argtypes = [i, i]
+    lib.dks_tune_contractions_get.argtypes = [vp, C.POINTER(i)]
+    lib.dks_tune_contractions_set.argtypes = [vp, i]
     lib.dks_debug_rr_wait.argtypes = [C.c_uint, C.POINTER(C.c_uint)]
     lib.dks_tensor_cores_get.argtypes = [C.POINTER(i), C.POINTER(i)]
     _lib = lib
@@ -320,12 +324,17 @@ class Context:
 
     # ---- launch-parameter tuning (results never depend on it, only the time)
     def tuning(self):
-        chunk, threads, split = C.c_longlong(), C.c_int(), C.c_int()
+        """The context's launch parameters and projector contraction schedule."""
+        chunk, threads, split, ptc = C.c_longlong(), C.c_int(), C.c_int(), C.c_int()
         _check(_lib.dks_tune_get(self._h, C.byref(chunk), C.byref(threads), C.byref(split)))
-        return dict(chunk_bytes=chunk.value, plane_threads=threads.value, plane_split=split.value)
+        _check(_lib.dks_tune_contractions_get(self._h, C.byref(ptc)))
+        return dict(chunk_bytes=chunk.value, plane_threads=threads.value, plane_split=split.value,
+                    proj_tc=ptc.value)
 
-    def set_tuning(self, chunk_bytes, plane_threads=0, plane_split=0):
+    def set_tuning(self, chunk_bytes, plane_threads=0, plane_split=0, proj_tc=None):
         _check(_lib.dks_tune_set(self._h, int(chunk_bytes), int(plane_threads), int(plane_split)))
+        if proj_tc is not None:
+            _check(_lib.dks_tune_contractions_set(self._h, int(proj_tc)))
 
     def autotune(self, ik=0, nb=40, prec=PREC_FP32, cache=None, stream=None):
         """dks_autotune on an nb-column block of k-point ik; with `cache` (a JSON file path) a stored
@@ -337,12 +346,14 @@ class Context:
         if cache:
             hit = tuning_cache_lookup(cache, key)
             if hit is not None:
-                self.set_tuning(hit["chunk_bytes"], hit["plane_threads"], hit["plane_split"])
+                self.set_tuning(hit["chunk_bytes"], hit["plane_threads"], hit["plane_split"], hit.get("proj_tc"))
                 return dict(hit, cached=True)
         rep = TuneReport()
         _check(_lib.dks_autotune(self._h, int(ik), int(nb), int(prec), _stream(stream), C.byref(rep)))
         choice = dict(chunk_bytes=int(rep.chunk_bytes[rep.best]), plane_threads=int(rep.plane_threads[rep.best]),
                       plane_split=int(rep.plane_split[rep.best]))
+        if rep.proj_tc >= 0:
+            choice.update(proj_tc=int(rep.proj_tc), proj_ms=[float(rep.proj_ms[0]), float(rep.proj_ms[1])])
         if cache:
             tuning_cache_store(cache, key, choice)
         cands = [dict(chunk_bytes=int(rep.chunk_bytes[i]), plane_threads=int(rep.plane_threads[i]),
@@ -527,8 +538,11 @@ def tuning_cache_lookup(path, key):
         return None
     if not isinstance(entry, dict) or any(k not in entry for k in ("chunk_bytes", "plane_threads", "plane_split")):
         return None
-    return dict(chunk_bytes=int(entry["chunk_bytes"]), plane_threads=int(entry["plane_threads"]),
-                plane_split=int(entry["plane_split"]))
+    out = dict(chunk_bytes=int(entry["chunk_bytes"]), plane_threads=int(entry["plane_threads"]),
+               plane_split=int(entry["plane_split"]))
+    if "proj_tc" in entry:                     # the projector contraction schedule, when it was tuned
+        out["proj_tc"] = int(entry["proj_tc"])
+    return out
 
 
 def tuning_cache_store(path, key, choice):
@@ -544,6 +558,8 @@ def tuning_cache_store(path, key, choice):
         data = {}
     data[key] = dict(chunk_bytes=int(choice["chunk_bytes"]), plane_threads=int(choice["plane_threads"]),
                      plane_split=int(choice["plane_split"]))
+    if "proj_tc" in choice:
+        data[key]["proj_tc"] = int(choice["proj_tc"])
     tmp = f"{path}.tmp{os.getpid()}"
     with open(tmp, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)

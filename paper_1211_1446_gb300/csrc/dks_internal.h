@@ -119,6 +119,8 @@ struct dks_ctx {
   int plane_threads = 0;             // CTA size of the plane FFT kernel (0: from the FFT plan)
   int plane_split = 0;               // 1: pass B as row / column kernels even when a plane fits one CTA
   int ncomp = 4;                     // components per column: 4 (DKS, Eq. vDKS) or 2 (KSSO two-spinors)
+  int tc_proj = -1;                  // projector contractions of complex64 blocks: -1 follow the
+                                     // process-wide mask, 0 CUDA cores, 1 tensor cores (tuner's choice)
   int device = 0;
   int num_sms = 0;
 };
@@ -187,7 +189,9 @@ int density_accumulate(dks_ctx* ctx, int ik, const double2* x, int nb, const dou
 // kernels shared by the solver and the single-step entry points
 template <typename Va, typename Vb = Va, bool Acc64 = false>
 int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, double2* c,
-            cudaStream_t st, int cat = P_GRAM, int ldc = 0, bool lower = false);
+            cudaStream_t st, int cat = P_GRAM, int ldc = 0, bool lower = false, int tc = -1);
+// tc (complex64 operands only): -1 the process-wide tensor-core mask decides, 0 CUDA cores,
+// 1 tensor cores where the device and the operands allow them
 // c (m x n, col-major, leading dimension ldc or m) += a^H b, FP64 atomics; FP64 arithmetic when
 // either operand is complex128 or Acc64; lower: only the block lower triangle (square results)
 int mirror_lower(double2* c, int m, cudaStream_t st);   // upper triangle = conj of the lower
@@ -214,7 +218,7 @@ int gram_df(const float4* z, const float4* hz, int ld, int k, int m, double2* a,
 template <typename Va, typename Vo = Va>
 int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale,
             int n, Vo* out, int ldo, double beta, cudaStream_t st, double alpha = 1.0,
-            int cat = P_ROTATE);
+            int cat = P_ROTATE, int tc = -1);
 // out (k x n) = alpha * a (k x m) * (diag(wscale) w) + beta * out; wscale may be NULL;
 // FP64 arithmetic when a or out is complex128
 // columns of ncomp x npw elements (ncomp = 4: DKS four-spinors, 2: KSSO two-spinors)
@@ -244,6 +248,7 @@ int gather_cols(const double2* v, int ldv, int row0, int rows, const int* act, i
 constexpr int TC_ROTATE = DKS_TC_ROTATE, TC_GRAM = DKS_TC_GRAM, TC_PROJ_HN = DKS_TC_PROJ_HN,
               TC_PROJ_NN = DKS_TC_PROJ_NN, TC_ALL = DKS_TC_ALL, TC_DEFAULT = DKS_TC_DEFAULT;
 bool tc_enabled(int bit);            // bit selected and the device is a GB300 (sm_103)
+bool tc_device();                    // the device is a GB300 (sm_103)
 int tc_mask();
 int tc_set(int mask, int kchunk);
 int tc_get(int* mask, int* kchunk);

@@ -674,7 +674,8 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
       DKS_TRY(gemm_hn_df(kp.btdf, 2 * npw, (const double2*)x, 2 * npw, 2 * npw, ctx->nproj, ncol, zp, st,
                          P_PROJ_HN));
     else
-      DKS_TRY(gemm_hn<V>(bt, 2 * npw, x, 2 * npw, 2 * npw, ctx->nproj, ncol, zp, st, P_PROJ_HN));
+      DKS_TRY(gemm_hn<V>(bt, 2 * npw, x, 2 * npw, 2 * npw, ctx->nproj, ncol, zp, st, P_PROJ_HN, 0, false,
+                         ctx->tc_proj));
   }
   if (ctx->has_v) {
     bool done = false;
@@ -702,7 +703,7 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
                          (double2*)out, 2 * npw, 1.0, st, scale, P_PROJ_NN));
     else
       DKS_TRY(gemm_nn<V>(bt, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, ncol, out, 2 * npw,
-                         1.0, st, scale, P_PROJ_NN));
+                         1.0, st, scale, P_PROJ_NN, ctx->tc_proj));
   }
   return DKS_OK;
 }

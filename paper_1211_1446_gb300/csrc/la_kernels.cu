@@ -346,7 +346,7 @@ static int num_sms() {
 
 template <typename Va, typename Vb, bool Acc64>
 int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, double2* c, cudaStream_t st,
-            int cat, int ldc, bool lower) {
+            int cat, int ldc, bool lower, int tc) {
   if (m <= 0 || n <= 0 || k <= 0) return DKS_OK;
   if (ldc <= 0) ldc = m;
   if (lower && m != n) return fail(DKS_ERR_INVALID_ARG, "gemm_hn: lower-triangle mode needs a square result");
@@ -355,7 +355,8 @@ int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, dou
     // callers provide.  Projector coefficients are formed as (x~^H B)^H so that the wider block
     // x~ runs along the 128-row MMA dimension.
     const int bit = cat == P_PROJ_HN ? TC_PROJ_HN : TC_GRAM;
-    if (!lower && tc_enabled(bit) && tc_hn_supported(a, lda, b, ldb, k)) {
+    const bool use = tc < 0 ? tc_enabled(bit) : (tc == 1 && tc_device());
+    if (!lower && use && tc_hn_supported(a, lda, b, ldb, k)) {
       Prof pr(cat + kProf32, st, ((double)m * sizeof(Va) + (double)n * sizeof(Vb)) * k + 16.0 * m * n,
               8.0 * m * n * (double)k);
       pr.count(1);
@@ -649,11 +650,12 @@ static int col_groups(int n, int maxg) {
 
 template <typename Va, typename Vo>
 int gemm_nn(const Va* a, int lda, int k, int m, const double2* w, int ldw, const double* wscale, int n,
-            Vo* out, int ldo, double beta, cudaStream_t st, double alpha, int cat) {
+            Vo* out, int ldo, double beta, cudaStream_t st, double alpha, int cat, int tc) {
   if (k <= 0 || n <= 0) return DKS_OK;
   if constexpr (std::is_same<Va, float2>::value && std::is_same<Vo, float2>::value) {
     const int bit = cat == P_PROJ_NN ? TC_PROJ_NN : TC_ROTATE;
-    if (tc_enabled(bit) && tc_nn_supported(a, lda, k, m, n)) {
+    const bool use = tc < 0 ? tc_enabled(bit) : (tc == 1 && tc_device());
+    if (use && tc_nn_supported(a, lda, k, m, n)) {
       Prof pr(cat + kProf32, st, (double)m * k * sizeof(Va) + (beta != 0.0 ? 2.0 : 1.0) * n * k * sizeof(Vo) + 16.0 * m * n,
               8.0 * (double)k * m * n);
       return tc_gemm_nn(a, lda, k, m, w, ldw, wscale, n, out, ldo, beta, st, alpha, num_sms());
@@ -855,18 +857,18 @@ int gather_cols(const double2* v, int ldv, int row0, int rows, const int* act, i
 // explicit instantiations
 #define DKS_INST_HN(TA, TB, ACC)                                                                        \
   template int gemm_hn<TA, TB, ACC>(const TA*, int, const TB*, int, int, int, int, double2*, cudaStream_t, int, \
-                                    int, bool);
+                                    int, bool, int);
 DKS_INST_HN(double2, double2, false)
 DKS_INST_HN(float2, float2, false)
 DKS_INST_HN(float2, float2, true)
 DKS_INST_HN(double2, float2, false)
 DKS_INST_HN(float2, double2, false)
 template int gemm_nn<double2, double2>(const double2*, int, int, int, const double2*, int, const double*, int,
-                                       double2*, int, double, cudaStream_t, double, int);
+                                       double2*, int, double, cudaStream_t, double, int, int);
 template int gemm_nn<float2, float2>(const float2*, int, int, int, const double2*, int, const double*, int,
-                                     float2*, int, double, cudaStream_t, double, int);
+                                     float2*, int, double, cudaStream_t, double, int, int);
 template int gemm_nn<float2, double2>(const float2*, int, int, int, const double2*, int, const double*, int,
-                                      double2*, int, double, cudaStream_t, double, int);
+                                      double2*, int, double, cudaStream_t, double, int, int);
 template int col_stats<double2>(const double2*, const double2*, const double*, const double*, int, int, double*,
                                 cudaStream_t, int);
 template int col_stats<float2>(const float2*, const float2*, const double*, const double*, int, int, double*,

@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
+#include <vector>
 
 #include "dks_internal.h"
 
@@ -483,35 +484,38 @@ __global__ void __launch_bounds__(NN_THREADS, 1) k_tc_gemm_nn(const __grid_const
 }
 
 // ================================================================ hn: C = A^H B (split over K)
+// A tile is 128 columns of A (MMA M) against at most 64 columns of B (from B1 or B2; the Gram
+// form takes HZ through B1 and Z through B2).  Warp-specialised like the nn kernel: warp 0 TMA
+// producer, warp 1 MMA issuer and TMEM owner, warps 2-9 converters (A, A' = i A and B into BF16
+// slices), warps 10-17 fold.  Each 16-deep stage writes fresh TMEM accumulators (real and
+// imaginary part, double-buffered across stages): the five smaller slice products first, the
+// leading one last, so that at most one accumulation step at full magnitude enters each stage
+// sum; the fold warps add the stage sums into FP32 registers over the CTA's K chunk and write
+// the chunk's partial tile, which k_tc_reduce adds over the chunks in FP64 in a fixed order.
 constexpr int HN_KT = 8;                            // complex rows per stage (16 real = one MMA K-step)
 constexpr int HN_KR = 2 * HN_KT;
-constexpr int HN_NB = 256;                          // largest N (B columns) of a tile
+constexpr int HN_NB = 64;                           // largest N (B columns) of a tile
 constexpr uint32_t HN_STG_A = kM * HN_KR * 4;       // FP32 staging of A: [128 cols][16 floats]
-constexpr uint32_t HN_STG_B = 128 * HN_KR * 4;      // one B box: [128 cols][16 floats]
-constexpr uint32_t HN_STG_BYTES = HN_STG_A + 2 * HN_STG_B;
+constexpr uint32_t HN_STG_B = HN_NB * HN_KR * 4;    // B box: [64 cols][16 floats]
+constexpr uint32_t HN_STG_BYTES = HN_STG_A + HN_STG_B;
 constexpr uint32_t HN_A_SLICE = kM * HN_KR * 2;     // 128 rows x 16 K BF16
-constexpr uint32_t HN_B_SLICE = HN_NB * HN_KR * 2;  // 256 rows x 16 K BF16
+constexpr uint32_t HN_B_SLICE = HN_NB * HN_KR * 2;  // 64 rows x 16 K BF16
 constexpr uint32_t HN_OP_BYTES = 6 * HN_A_SLICE + 3 * HN_B_SLICE;   // A, A' and B slices
 constexpr size_t HN_SMEM_FIXED = 1024 + kOps * (size_t)HN_OP_BYTES + 512;
+constexpr int HN_THREADS = 18 * 32;
+constexpr int HN_STG_MAX = 8;
 
 // One output tile: rows = A columns [ia0, ia0 + 128), columns = B1 columns [jb1, jb1 + nb1)
-// followed by B2 columns [jb2, jb2 + nb2).
+// followed by B2 columns [jb2, jb2 + nb2), nb1 + nb2 <= 64.
 struct HNTile {
   int ia0, jb1, nb1, jb2, nb2;
 };
-constexpr int kMaxTiles = 64;
+constexpr int kMaxTiles = 256;
 struct HNArgs {
   int k, kchunk, ntiles, nstg;
-  HNTile tile[kMaxTiles];
+  const HNTile* tile;                    // device copy of the tile list
   float2* part;                          // [split][tile][HN_NB cols][128 rows]
 };
-
-// Warp-specialised: warp 0 issues the TMA copies of A and B into a ring of staging slots, warp 1
-// issues the MMAs and owns the TMEM allocation, warps 2-9 convert staged tiles into BF16 slices
-// (A, A' = i A and B; two operand buffers) and, after the last stage, read the partial tile out
-// of TMEM.  Every hand-off is an mbarrier; every wait is bounded.
-constexpr int HN_THREADS = 10 * 32;
-constexpr int HN_STG_MAX = 8;
 
 __global__ void __launch_bounds__(HN_THREADS, 1) k_tc_gemm_hn(const __grid_constant__ CUtensorMap ta,
                                                              const __grid_constant__ CUtensorMap tb1,
@@ -521,7 +525,7 @@ __global__ void __launch_bounds__(HN_THREADS, 1) k_tc_gemm_hn(const __grid_const
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const HNTile tl = p.tile[blockIdx.x];
   const int nbt = tl.nb1 + tl.nb2;
-  const int nmma = (nbt + 15) & ~15;                   // MMA N (multiple of 16)
+  const int nmma = (nbt + 15) & ~15;                   // MMA N (multiple of 16, <= 64)
   const int nstg = p.nstg;
   unsigned char* stg = sm;
   unsigned char* ops = sm + (size_t)nstg * HN_STG_BYTES;
@@ -530,8 +534,9 @@ __global__ void __launch_bounds__(HN_THREADS, 1) k_tc_gemm_hn(const __grid_const
   uint64_t* stg_empty = stg_full + HN_STG_MAX;         // [nstg] converted (8 converter warps)
   uint64_t* op_full = stg_empty + HN_STG_MAX;          // [kOps] slices written (8 converter warps)
   uint64_t* op_empty = op_full + kOps;                 // [kOps] MMAs that read them completed
-  uint64_t* accf = op_empty + kOps;                    // every MMA of the CTA completed
-  uint64_t* drainb = accf + 1;
+  uint64_t* acc_full = op_empty + kOps;                // [2] stage sums in TMEM
+  uint64_t* acc_empty = acc_full + 2;                  // [2] read by the 8 fold warps
+  uint64_t* drainb = acc_empty + 2;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drainb + 1);
   volatile int* sflag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
@@ -548,17 +553,20 @@ __global__ void __launch_bounds__(HN_THREADS, 1) k_tc_gemm_hn(const __grid_const
       mbar_init(&op_full[i], 8);
       mbar_init(&op_empty[i], 1);
     }
-    mbar_init(accf, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 8);
+    }
     mbar_init(drainb, 1);
     *sflag = 0;
     fence_barrier_init();
   }
-  if (warp == 1) tmem_alloc(tmem_holder, 512);
+  if (warp == 1) tmem_alloc(tmem_holder, 256);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tmem_holder;                  // D_re at columns [0, 256), D_im at [256, 512)
-  const uint32_t stg_bytes = HN_STG_A + (tl.nb1 > 0 ? HN_STG_B : 0) + (tl.nb2 > 0 ? HN_STG_B : 0);
+  const uint32_t tmem = *tmem_holder;   // buffer b: real part at columns [128 b, 128 b + 64), imaginary at +64
+  const uint32_t stg_bytes = HN_STG_A + HN_STG_B;
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
@@ -575,7 +583,7 @@ __global__ void __launch_bounds__(HN_THREADS, 1) k_tc_gemm_hn(const __grid_const
         mbar_expect_tx(&stg_full[st], stg_bytes);
         tma_load_2d(s, &ta, x, tl.ia0, &stg_full[st]);
         if (tl.nb1 > 0) tma_load_2d(s + HN_STG_A, &tb1, x, tl.jb1, &stg_full[st]);
-        if (tl.nb2 > 0) tma_load_2d(s + HN_STG_A + HN_STG_B, &tb2, x, tl.jb2, &stg_full[st]);
+        else tma_load_2d(s + HN_STG_A, &tb2, x, tl.jb2, &stg_full[st]);
         issued = q + 1;
       }
       for (int q = std::max(0, issued - nstg); q < issued; ++q)
@@ -587,8 +595,10 @@ __global__ void __launch_bounds__(HN_THREADS, 1) k_tc_gemm_hn(const __grid_const
       const uint32_t idesc = idesc_bf16(kM, nmma);
       const uint64_t d0 = sdesc(saddr(ops), 128, 256);
       for (int q = 0; q < total && !*sflag; ++q) {
-        const int op = q % kOps;
-        if (!mbar_wait(&op_full[op], (uint32_t)(q / kOps) & 1u)) {
+        const int op = q % kOps, b = q & 1;
+        bool w = mbar_wait(&op_full[op], (uint32_t)(q / kOps) & 1u);
+        if (w && q >= 2) w = mbar_wait(&acc_empty[b], (uint32_t)((q >> 1) - 1) & 1u);
+        if (!w) {
           *sflag = 1;
           break;
         }
@@ -596,21 +606,24 @@ __global__ void __launch_bounds__(HN_THREADS, 1) k_tc_gemm_hn(const __grid_const
         const uint64_t da = d0 + ((uint64_t)(op * HN_OP_BYTES) >> 4);
         const uint64_t da2 = da + ((uint64_t)(3 * HN_A_SLICE) >> 4);
         const uint64_t db = da + ((uint64_t)(6 * HN_A_SLICE) >> 4);
+        const uint32_t dre = tmem + 128u * (uint32_t)b, dim = dre + 64u;
+        // the smaller products first, the leading one (pair 0) last
 #pragma unroll
-        for (int pr = 0; pr < 6; ++pr) {
+        for (int k6 = 0; k6 < 6; ++k6) {
+          const int pr = (k6 + 1) % 6;
           const uint64_t bd = db + ((uint64_t)(kPairB[pr] * HN_B_SLICE) >> 4);
           const uint64_t oa = (uint64_t)(kPairA[pr] * HN_A_SLICE) >> 4;
-          mma_bf16(tmem, da + oa, bd, idesc, (q | pr) != 0);
-          mma_bf16(tmem + 256, da2 + oa, bd, idesc, (q | pr) != 0);
+          mma_bf16(dre, da + oa, bd, idesc, k6 != 0);
+          mma_bf16(dim, da2 + oa, bd, idesc, k6 != 0);
         }
         mma_commit(&op_empty[op]);
+        mma_commit(&acc_full[b]);
       }
-      mma_commit(accf);
       mma_commit(drainb);
       mbar_wait(drainb, 0u);
     }
-  } else {
-    // ---------------------------------------------------------------- converters, then epilogue
+  } else if (warp < 10) {
+    // ---------------------------------------------------------------- converters
     const int ct = tid - 64;                          // 0 .. 255
     for (int q = 0; q < total && !*sflag; ++q) {
       const int st = q % nstg, op = q % kOps;
@@ -639,15 +652,13 @@ __global__ void __launch_bounds__(HN_THREADS, 1) k_tc_gemm_hn(const __grid_const
         store_slices(oa, HN_A_SLICE, core_off(r, g, 2), v8);
         store_slices(oa2, HN_A_SLICE, core_off(r, g, 2), w8);
       }
-      // B: rows [0, nb1) from box 1, [nb1, nb1 + nb2) from box 2, zero up to nmma
-      for (int it = ct; it < nmma * 2; it += 256) {
-        const int r = it >> 1, g = it & 1;
+      if (ct < nmma * 2) {
+        // B: rows [0, nbt) from the staged box, zero up to nmma
+        const int r = ct >> 1, g = ct & 1;
         float v8[8];
-        const float* src = nullptr;
-        if (r < tl.nb1) src = sa + (HN_STG_A / 4) + r * HN_KR + 8 * g;
-        else if (r < nbt) src = sa + ((HN_STG_A + HN_STG_B) / 4) + (r - tl.nb1) * HN_KR + 8 * g;
+        const float* src = sa + (HN_STG_A / 4) + r * HN_KR + 8 * g;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v8[e] = src ? src[e] : 0.f;
+        for (int e = 0; e < 8; ++e) v8[e] = r < nbt ? src[e] : 0.f;
         store_slices(ob, HN_B_SLICE, core_off(r, g, 2), v8);
       }
       fence_async_smem();
@@ -657,28 +668,50 @@ __global__ void __launch_bounds__(HN_THREADS, 1) k_tc_gemm_hn(const __grid_const
         mbar_arrive(&stg_empty[st]);
       }
     }
-    // epilogue: the partial tile part[split][tile][col][row] (FP32 re, im)
-    if (!*sflag && total > 0) {
-      if (!mbar_wait(accf, 0u)) {
-        *sflag = 1;
-      } else {
-        tc_fence_after();
-        float2* dst = p.part + ((size_t)blockIdx.y * p.ntiles + blockIdx.x) * (size_t)HN_NB * kM;
-        const int lq = warp & 3, half = (warp - 2) >> 2;
-        const int row = 32 * lq + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(32 * lq) << 16);
-        for (int c0 = 16 * half; c0 < nbt; c0 += 32) {
-          float re[16], im[16];
-          tmem_ld16(lane_base + (uint32_t)c0, re);
-          tmem_ld16(lane_base + 256u + (uint32_t)c0, im);
+  } else {
+    // ---------------------------------------------------------------- fold, then the partial tile
+    const int lq = warp & 3, half = (warp - 10) >> 2;   // columns [32 half, 32 half + 32)
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * lq) << 16);
+    float accr[2][16], acci[2][16];
 #pragma unroll
-          for (int e = 0; e < 16; ++e)
-            if (c0 + e < nbt) dst[(size_t)(c0 + e) * kM + row] = float2{re[e], im[e]};
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int e = 0; e < 16; ++e) accr[u][e] = acci[u][e] = 0.f;
+    for (int q = 0; q < total && !*sflag; ++q) {
+      const int b = q & 1;
+      if (!mbar_wait(&acc_full[b], (uint32_t)(q >> 1) & 1u)) {
+        *sflag = 1;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int c0 = 32 * half + 16 * u;
+        if (c0 < nbt) {
+          float re[16], im[16];
+          tmem_ld16(lane_base + 128u * (uint32_t)b + (uint32_t)c0, re);
+          tmem_ld16(lane_base + 128u * (uint32_t)b + 64u + (uint32_t)c0, im);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            accr[u][e] += re[e];
+            acci[u][e] += im[e];
+          }
         }
       }
-    } else if (total == 0) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+    }
+    if (!*sflag) {
       float2* dst = p.part + ((size_t)blockIdx.y * p.ntiles + blockIdx.x) * (size_t)HN_NB * kM;
-      for (int e = ct; e < nbt * kM; e += 256) dst[e] = float2{0.f, 0.f};
+      const int row = 32 * lq + lane;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int c0 = 32 * half + 16 * u;
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          if (c0 + e < nbt) dst[(size_t)(c0 + e) * kM + row] = float2{accr[u][e], acci[u][e]};
+      }
     }
   }
   if (*sflag && tid == 0) atomicExch(&g_tc_status, DKS_ERR_TIMEOUT);
@@ -686,7 +719,7 @@ __global__ void __launch_bounds__(HN_THREADS, 1) k_tc_gemm_hn(const __grid_const
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, 512);
+    tmem_dealloc(tmem, 256);
   }
 }
 
@@ -696,7 +729,7 @@ __global__ void __launch_bounds__(HN_THREADS, 1) k_tc_gemm_hn(const __grid_const
 // conj (= B^H A); gram: B1 columns go to C1, B2 columns to C2, lower triangle only.
 struct RedArgs {
   int splits, ntiles, m, ldc, mode, gram;
-  HNTile tile[kMaxTiles];
+  const HNTile* tile;                    // device copy of the tile list
   const float2* part;
   double2* c1;
   double2* c2;
@@ -816,6 +849,8 @@ int tc_mask() {
 
 bool tc_enabled(int bit) { return (tc_mask() & bit) != 0 && tc::device_ok() == 1; }
 
+bool tc_device() { return tc::device_ok() == 1; }
+
 int tc_set(int mask, int kchunk) {
   std::lock_guard<std::mutex> g(tc::g_mu);
   tc::g_mask = mask & TC_ALL;
@@ -905,28 +940,25 @@ int tc_gemm_hn_impl(const float2* a, int lda, int m, const float2* b1, const flo
                     double2* c1, double2* c2, int ldc, int mode, bool gram, cudaStream_t st, int nsm) {
   using namespace tc;
   if (k <= 0 || m <= 0 || n <= 0) return DKS_OK;
-  RedArgs r{};
-  HNArgs p{};
-  int nt = 0;
+  std::vector<HNTile> tiles;
   const int mt = (m + kM - 1) / kM;
   if (gram) {
-    // tiles (ib, jb), jb <= ib, of 128 rows and 128 + 128 columns (HZ, Z)
+    // block (ib, jb), jb <= ib, of 128 rows: HZ columns of block jb through B1, then Z columns
+    // through B2, each in pieces of at most 64
     for (int ib = 0; ib < mt; ++ib)
       for (int jb = 0; jb <= ib; ++jb) {
-        if (nt >= kMaxTiles) return fail(DKS_ERR_UNSUPPORTED, "tensor-core Gram: too many tiles");
         const int nbj = std::min(kM, m - jb * kM);
-        p.tile[nt++] = HNTile{ib * kM, jb * kM, nbj, jb * kM, nbj};
+        const int pieces = (nbj + HN_NB - 1) / HN_NB, per = (nbj + pieces - 1) / pieces;
+        for (int j0 = 0; j0 < nbj; j0 += per) tiles.push_back(HNTile{ib * kM, jb * kM + j0, std::min(per, nbj - j0), 0, 0});
+        for (int j0 = 0; j0 < nbj; j0 += per) tiles.push_back(HNTile{ib * kM, 0, 0, jb * kM + j0, std::min(per, nbj - j0)});
       }
   } else {
-    // up to 256 B columns per tile: the first 128 through box 1, the rest through box 2 (the
-    // same tensor)
+    const int pieces = (n + HN_NB - 1) / HN_NB, per = (n + pieces - 1) / pieces;
     for (int ib = 0; ib < mt; ++ib)
-      for (int j0 = 0; j0 < n; j0 += HN_NB) {
-        if (nt >= kMaxTiles) return fail(DKS_ERR_UNSUPPORTED, "tensor-core A^H B: too many tiles");
-        const int cnt = std::min(HN_NB, n - j0), n1 = std::min(128, cnt);
-        p.tile[nt++] = HNTile{ib * kM, j0, n1, j0 + 128, cnt - n1};
-      }
+      for (int j0 = 0; j0 < n; j0 += per) tiles.push_back(HNTile{ib * kM, j0, std::min(per, n - j0), 0, 0});
   }
+  const int nt = (int)tiles.size();
+  if (nt > kMaxTiles) return fail(DKS_ERR_UNSUPPORTED, "tensor-core A^H B: too many tiles");
   int kchunk;
   {
     std::lock_guard<std::mutex> g(g_mu);
@@ -938,7 +970,7 @@ int tc_gemm_hn_impl(const float2* a, int lda, int m, const float2* b1, const flo
     }
   }
   // splits: each K range at most kchunk rows, rounded up to whole waves of one CTA per SM, and
-  // the partial tiles (256 KB per CTA) held to kPartBudget (longer ranges beyond that)
+  // the partial tiles (64 KB per CTA) held to kPartBudget (longer ranges beyond that)
   constexpr size_t kPartBudget = 256u << 20;
   const size_t tile_bytes = (size_t)HN_NB * kM * sizeof(float2);
   long long splits = (k + kchunk - 1) / kchunk;
@@ -949,35 +981,44 @@ int tc_gemm_hn_impl(const float2* a, int lda, int m, const float2* b1, const flo
   splits = (k + kc - 1) / kc;
   CUtensorMap ta, tb1, tb2;
   DKS_TRY(make_map(&ta, a, k, m, lda, HN_KR, kM));
-  DKS_TRY(make_map(&tb1, b1, k, gram ? m : n, ldb, HN_KR, 128));
-  DKS_TRY(make_map(&tb2, b2 ? b2 : b1, k, gram ? m : n, ldb, HN_KR, 128));
+  DKS_TRY(make_map(&tb1, b1, k, gram ? m : n, ldb, HN_KR, HN_NB));
+  DKS_TRY(make_map(&tb2, b2 ? b2 : b1, k, gram ? m : n, ldb, HN_KR, HN_NB));
   const size_t part_bytes = (size_t)splits * nt * tile_bytes;
-  float2* part = nullptr;
-  DKS_CUDA_TRY(cudaMallocAsync((void**)&part, part_bytes, st));
-  const int nstg = (int)std::min<size_t>(HN_STG_MAX, (NN_SMEM_LIMIT - HN_SMEM_FIXED) / HN_STG_BYTES);
-  p.k = k;
-  p.kchunk = kc;
-  p.ntiles = nt;
-  p.nstg = nstg;
-  p.part = part;
-  k_tc_gemm_hn<<<dim3(nt, (unsigned)splits), HN_THREADS, HN_SMEM_FIXED + (size_t)nstg * HN_STG_BYTES, st>>>(ta, tb1,
-                                                                                                           tb2, p);
-  cudaError_t e = cudaGetLastError();
+  const size_t tl_bytes = (tiles.size() * sizeof(HNTile) + 255) / 256 * 256;
+  unsigned char* buf = nullptr;
+  DKS_CUDA_TRY(cudaMallocAsync((void**)&buf, tl_bytes + part_bytes, st));
+  HNTile* dtiles = reinterpret_cast<HNTile*>(buf);
+  float2* part = reinterpret_cast<float2*>(buf + tl_bytes);
+  cudaError_t e = cudaMemcpyAsync(dtiles, tiles.data(), tiles.size() * sizeof(HNTile), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
+    const int nstg = (int)std::min<size_t>(HN_STG_MAX, (NN_SMEM_LIMIT - HN_SMEM_FIXED) / HN_STG_BYTES);
+    HNArgs p{};
+    p.k = k;
+    p.kchunk = kc;
+    p.ntiles = nt;
+    p.nstg = nstg;
+    p.tile = dtiles;
+    p.part = part;
+    k_tc_gemm_hn<<<dim3(nt, (unsigned)splits), HN_THREADS, HN_SMEM_FIXED + (size_t)nstg * HN_STG_BYTES, st>>>(
+        ta, tb1, tb2, p);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    RedArgs r{};
     r.splits = (int)splits;
     r.ntiles = nt;
     r.m = m;
     r.ldc = ldc;
     r.mode = mode;
     r.gram = gram ? 1 : 0;
-    for (int t = 0; t < nt; ++t) r.tile[t] = p.tile[t];
+    r.tile = dtiles;
     r.part = part;
     r.c1 = c1;
     r.c2 = c2;
     k_tc_reduce<<<dim3(HN_NB * 4, nt), 256, 0, st>>>(r);
     e = cudaGetLastError();
   }
-  cudaFreeAsync(part, st);
+  cudaFreeAsync(buf, st);
   if (e != cudaSuccess) return fail(DKS_ERR_CUDA, std::string("tensor-core A^H B launch: ") + cudaGetErrorString(e));
   return DKS_OK;
 }

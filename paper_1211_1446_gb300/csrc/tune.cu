@@ -1,8 +1,9 @@
-// Autotuning of the H' application's launch parameters.  The paper has no counterpart (its code
-// ran on CPUs); the parameters are this implementation's: the byte budget of one chunk of FFT
-// intermediates (how many bands' stick buffers share the L2-resident working set between the
-// three FFT passes), the CTA size of the one-kernel plane FFT, and whether the plane FFT runs as
-// one kernel or as row and column kernels.  dks_autotune times H' on a scratch block for every
+// Autotuning of the H' application's launch parameters and contraction schedule.  The paper has
+// no counterpart (its code ran on CPUs); the parameters are this implementation's: the byte budget
+// of one chunk of FFT intermediates (how many bands' stick buffers share the L2-resident working
+// set between the three FFT passes), the CTA size of the one-kernel plane FFT, whether the plane
+// FFT runs as one kernel or as row and column kernels, and (complex64 blocks) whether the
+// projector contractions run on the tensor cores or the CUDA cores.  dks_autotune times H' on a scratch block for every
 // candidate with CUDA events on the caller's stream and keeps the fastest; dks_tune_set applies
 // a stored choice (the Python layer caches choices per grid, basis size, block width, precision
 // and device).
@@ -41,6 +42,19 @@ int dks_tune_set(dks_ctx* ctx, long long fft_chunk_bytes, int plane_threads, int
   ctx->chunk_budget = (size_t)fft_chunk_bytes;
   ctx->plane_threads = plane_threads;
   ctx->plane_split = plane_split;
+  return DKS_OK;
+}
+
+int dks_tune_contractions_get(const dks_ctx* ctx, int* proj_tc) {
+  if (!ctx || !proj_tc) return fail(DKS_ERR_INVALID_ARG, "dks_tune_contractions_get: bad argument");
+  *proj_tc = ctx->tc_proj;
+  return DKS_OK;
+}
+
+int dks_tune_contractions_set(dks_ctx* ctx, int proj_tc) {
+  if (!ctx || proj_tc < -1 || proj_tc > 1)
+    return fail(DKS_ERR_INVALID_ARG, "dks_tune_contractions_set: proj_tc must be -1, 0 or 1");
+  ctx->tc_proj = proj_tc;
   return DKS_OK;
 }
 
@@ -99,6 +113,31 @@ int dks_autotune(dks_ctx* ctx, int ik, int nb, int prec, void* stream, dks_tune_
     return DKS_OK;
   };
   rc = body();
+  // contraction schedule of the projector terms (complex64 blocks on a GB300): both timed at the
+  // chosen FFT parameters
+  int proj_best = -1;
+  double proj_ms[2] = {0.0, 0.0};
+  if (rc == DKS_OK && best >= 0 && prec == DKS_PREC_FP32 && ctx->nproj > 0 && tc_device()) {
+    const int old_tc = ctx->tc_proj;
+    ctx->chunk_budget = (size_t)cc[best];
+    ctx->plane_threads = ct[best];
+    ctx->plane_split = cs[best];
+    void* x = buf;
+    void* hx = (char*)buf + elems * es;
+    for (int t = 0; t < 2 && rc == DKS_OK; ++t) {
+      ctx->tc_proj = t;
+      rc = dks_apply_H(ctx, ik, x, hx, nb, prec, st);
+      if (rc == DKS_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = fail(DKS_ERR_CUDA, "dks_autotune: event");
+      for (int r = 0; r < 3 && rc == DKS_OK; ++r) rc = dks_apply_H(ctx, ik, x, hx, nb, prec, st);
+      float ms = 0.0f;
+      if (rc == DKS_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = fail(DKS_ERR_CUDA, "dks_autotune: event timing");
+      proj_ms[t] = ms / 3.0;
+    }
+    ctx->tc_proj = old_tc;
+    if (rc == DKS_OK) proj_best = proj_ms[1] < proj_ms[0] ? 1 : 0;
+  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFreeAsync(buf, st);
@@ -112,7 +151,11 @@ int dks_autotune(dks_ctx* ctx, int ik, int nb, int prec, void* stream, dks_tune_
   ctx->chunk_budget = (size_t)cc[best];
   ctx->plane_threads = ct[best];
   ctx->plane_split = cs[best];
+  if (proj_best >= 0) ctx->tc_proj = proj_best;
   if (rep) {
+    rep->proj_tc = proj_best;
+    rep->proj_ms[0] = proj_ms[0];
+    rep->proj_ms[1] = proj_ms[1];
     rep->ncand = ncand;
     rep->best = best;
     for (int i = 0; i < ncand; ++i) {

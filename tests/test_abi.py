@@ -97,7 +97,10 @@ def test_tuning_entry_points_and_cache_without_gpu(tmp_path):
     chunk, thr, spl = C.c_longlong(), C.c_int(), C.c_int()
     assert lib.dks_tune_get(None, C.byref(chunk), C.byref(thr), C.byref(spl)) == -1
     rep = P.TuneReport()
-    assert C.sizeof(rep) == 8 + 32 * 8 + 32 * 4 + 32 * 4 + 32 * 8
+    # ncand, best, the 32 candidates, then proj_tc (padded to 8 bytes) and proj_ms[2]
+    assert C.sizeof(rep) == 8 + 32 * 8 + 32 * 4 + 32 * 4 + 32 * 8 + 8 + 2 * 8
+    assert lib.dks_tune_contractions_set(None, 1) == -1
+    assert lib.dks_tune_contractions_get(None, C.byref(thr)) == -1
     path = str(tmp_path / "tune.json")
     k1 = P.tuning_key((48, 48, 56), 57419, 4, 40, 1, "GB300")
     k2 = P.tuning_key((48, 48, 56), 57419, 4, 40, 0, "GB300")
@@ -110,6 +113,9 @@ def test_tuning_entry_points_and_cache_without_gpu(tmp_path):
     assert P.tuning_cache_lookup(path, k1) is None
     P.tuning_cache_store(path, k1, dict(chunk_bytes=16 << 20, plane_threads=128, plane_split=0))
     assert P.tuning_cache_lookup(path, k1) == dict(chunk_bytes=16 << 20, plane_threads=128, plane_split=0)
+    # the projector contraction schedule round-trips when present
+    P.tuning_cache_store(path, k2, dict(chunk_bytes=32 << 20, plane_threads=0, plane_split=0, proj_tc=1, proj_ms=[1, 2]))
+    assert P.tuning_cache_lookup(path, k2) == dict(chunk_bytes=32 << 20, plane_threads=0, plane_split=0, proj_tc=1)
 
 
 def _min_passes(n, memo={1: 0}):

