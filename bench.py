@@ -883,19 +883,31 @@ def main():
         ach = d["flops"] / max(d["launches"], 1) / per_launch_s / 1e9
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "GFLOP/s", "frac": ach / pk,
                 "peak_source": psrc}
-    # the largest single kernel of the launch list: the double-float OUT = A W' kernel (k_gemm_nn_df4),
-    # which serves the refinement phase's rotations and projector updates (two categories)
+    # the refinement phase's Gram matrices and rotations: with DKS_TC_FP64 (default) on the tcgen05
+    # tensor cores from exact integer slices (28 BF16 slice products per real multiply-add, so the
+    # FP64-equivalent ceiling is the BF16 tensor peak / 28), else double-float on the FP32 lanes
     if mode == P.MODE_MIXED:
-        cats = [c for c in ("rotate", "proj_b_dz") if prof.get(c, {}).get("launches")]
+        slices = bool(P.tensor_cores()[0] & P.TC_FP64)
+        cats = [c for c in ("gram", "rotate") if prof.get(c, {}).get("launches")]
         if cats:
             f = sum(prof[c]["flops"] for c in cats)
             t = sum(prof[c]["ms"] for c in cats) / 1e3
-            roof.update({"top_kernel": "k_gemm_nn_df4 (double-float rotations and projector updates)",
+            pk = bf16 * 1e3 / 28.0 if slices else df_peak
+            roof.update({"top_kernel": ("k_oz_gram + k_oz_rot (refinement-phase Gram matrices and rotations, "
+                                        "tcgen05, exact integer slices)" if slices else
+                                        "k_gram_df + k_gemm_nn_df4 (refinement-phase Gram matrices and rotations, "
+                                        "double-float)"),
                          "top_kernel_share_of_step": t * 1e3 / (ms * args.steps),
-                         "top_kernel_gflops": f / t / 1e9, "top_kernel_peak_gflops": df_peak,
-                         "top_kernel_frac": f / t / 1e9 / df_peak,
-                         "top_kernel_peak_source": "derived: FP64-equivalent rate of the double-float multiply-add "
-                                                   "(15 FP32 instructions) on 152 SMs x 128 FP32 lanes x 2070 MHz"})
+                         "top_kernel_gflops": f / t / 1e9, "top_kernel_peak_gflops": pk,
+                         "top_kernel_frac": f / t / 1e9 / pk,
+                         "top_kernel_peak_source": (f"{src} BF16 tensor peak / 28 slice products per multiply-add"
+                                                    if slices else
+                                                    "derived: FP64-equivalent rate of the double-float multiply-add "
+                                                    "(15 FP32 instructions) on 152 SMs x 128 FP32 lanes x 2070 MHz")})
+            if slices and prof.get("rotate", {}).get("launches"):
+                r = prof["rotate"]
+                roof["top_kernel_rotate_gbs"] = r["bytes"] / (r["ms"] / 1e3) / 1e9
+                roof["top_kernel_rotate_frac_hbm"] = roof["top_kernel_rotate_gbs"] / hbm
     tr = NCU_TRAFFIC.get(dom)
     roof.update({"traffic": tr["bytes_per_launch"] if tr else None,
                  "traffic_note": tr["note"] if tr else "no ncu DRAM capture of this category's kernels",
@@ -949,10 +961,17 @@ def main():
             "vs_baseline": None, "dtype": "f32+df64" if mode == P.MODE_MIXED else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "mode": args.mode, "parallelism": f"replicas x{ws}",
                        "l2": "working set (>1 GB of blocks per solve) exceeds the 129 MB L2",
-                       "dtype_note": ("FP32 phase (complex64; projector contractions on tcgen05 tensor cores "
-                                      "with three BF16 slices per FP32 value), then the FP64 refinement with "
-                                      "complex128 storage whose contractions and FFTs run in double-float "
-                                      "arithmetic (about 2^-48 per operation); Rayleigh-Ritz in FP64"
+                       "dtype_note": (("FP32 phase (complex64; projector contractions on tcgen05 tensor cores "
+                                       "with three BF16 slices per FP32 value), then the FP64 refinement with "
+                                       "complex128 storage: Gram matrices and rotations on tcgen05 tensor cores "
+                                       "from exact integer slices (seven 8-bit digits per value, exact FP32 "
+                                       "level sums), projector contractions and FFTs in double-float arithmetic "
+                                       "(about 2^-48 per operation); Rayleigh-Ritz in FP64"
+                                       if P.tensor_cores()[0] & P.TC_FP64 else
+                                       "FP32 phase (complex64; projector contractions on tcgen05 tensor cores "
+                                       "with three BF16 slices per FP32 value), then the FP64 refinement with "
+                                       "complex128 storage whose contractions and FFTs run in double-float "
+                                       "arithmetic (about 2^-48 per operation); Rayleigh-Ritz in FP64")
                                       if mode == P.MODE_MIXED else "FP64"),
                        "tensor_cores_mask": P.tensor_cores()[0], "tuning": tune or "defaults"},
             "e2e": {"value": NEV * ws / (ms_e2e / 1e3), "unit": "eigenpairs/s",

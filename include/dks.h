@@ -329,12 +329,23 @@ int dks_debug_rr_wait(unsigned first_wait_polls, unsigned* redone);
 #define DKS_TC_GRAM 2     /* S = Z^H Z, A = Z^H HZ (and the other FP32 A^H B Gram forms)    */
 #define DKS_TC_PROJ_HN 4  /* projector coefficients B^H x~                                  */
 #define DKS_TC_PROJ_NN 8  /* projector update x~ += B (D B^H x~)                            */
-#define DKS_TC_ALL 15
-/* default: the projector contractions.  Rotations and Gram matrices stay on the CUDA cores: on
- * the tensor cores they raise the residual floor of the FP32 phase (the residual H X - X Lambda
- * is formed from separately rotated X and HX blocks and the negative continuum amplifies what
+/* complex128 blocks in double-float precision (the FP64 refinement phase of the mixed mode,
+ * DKS_PREC_FP64_EMULATED): the Gram matrices A = Z^H HZ, S = Z^H Z and the rotations X <- Z V,
+ * P <- [0, Y, P] V from exact integer slices -- per 128-row window and column an exponent E with
+ * |Re|, |Im| < 2^(E-1), every value rounded to 56 fractional bits of 2^E and cut into seven
+ * 8-bit digits held as bfloat16; the 28 digit products of levels 0..6 accumulate on the tensor
+ * cores level by level, exactly in FP32 for levels 0..3, and the window sums are added in
+ * double-float and FP64 (error near 2^-50 of the window maxima per product, deterministic).
+ * The blocks are sliced once per iteration and the slices serve both the Gram matrices and the
+ * rotations. */
+#define DKS_TC_FP64 16
+#define DKS_TC_ALL 31
+/* default: the projector contractions of complex64 blocks and the refinement phase's
+ * contractions.  The complex64 rotations and Gram matrices stay on the CUDA cores: on the
+ * tensor cores they raise the residual floor of the FP32 phase (the residual H X - X Lambda is
+ * formed from separately rotated X and HX blocks and the negative continuum amplifies what
  * their rounding leaves), which costs more FP64 iterations than the contraction saves. */
-#define DKS_TC_DEFAULT (DKS_TC_PROJ_HN | DKS_TC_PROJ_NN)
+#define DKS_TC_DEFAULT (DKS_TC_PROJ_HN | DKS_TC_PROJ_NN | DKS_TC_FP64)
 int dks_tensor_cores(int mask, int kchunk);
 /* the current mask and chunk length */
 int dks_tensor_cores_get(int* mask, int* kchunk);

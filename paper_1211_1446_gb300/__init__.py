@@ -591,13 +591,14 @@ class Mixer:
             pass
 
 
-TC_ROTATE, TC_GRAM, TC_PROJ_HN, TC_PROJ_NN, TC_ALL = 1, 2, 4, 8, 15
+TC_ROTATE, TC_GRAM, TC_PROJ_HN, TC_PROJ_NN, TC_FP64, TC_ALL = 1, 2, 4, 8, 16, 31
 
 
 def tensor_cores(mask=None, kchunk=0):
-    """dks_tensor_cores: select which complex64 contractions run on the tcgen05 tensor cores
-    (TC_* bits; None leaves the mask) and the longest FP32 accumulation of the Gram forms
-    (kchunk rows, 0 = unchanged).  Returns the previous (mask, kchunk)."""
+    """dks_tensor_cores: select which contractions run on the tcgen05 tensor cores (TC_* bits;
+    TC_FP64: the complex128 Gram matrices and rotations of the double-float refinement phase
+    from exact integer slices; None leaves the mask) and the longest FP32 accumulation of the
+    complex64 Gram forms (kchunk rows, 0 = unchanged).  Returns the previous (mask, kchunk)."""
     lib = load_library()
     m, k = C.c_int(), C.c_int()
     _check(lib.dks_tensor_cores_get(C.byref(m), C.byref(k)))

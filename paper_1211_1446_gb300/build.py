@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdks.so")
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libdks_debug.so")
-SOURCES = ["dks_api.cu", "dks_prof.cu", "hx_kernels.cu", "la_kernels.cu", "df_kernels.cu", "rr_kernels.cu", "rr_cluster.cu", "rr_static.cu", "solver.cu", "scf.cu", "tune.cu", "tc_gemm.cu"]
+SOURCES = ["dks_api.cu", "dks_prof.cu", "hx_kernels.cu", "la_kernels.cu", "df_kernels.cu", "rr_kernels.cu", "rr_cluster.cu", "rr_static.cu", "solver.cu", "scf.cu", "tune.cu", "tc_gemm.cu", "oz_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]

@@ -633,7 +633,23 @@ int dks_gram_hermitian(const void* Z, const void* HZ, int rows, int nz, void* A,
   cudaStream_t st = (cudaStream_t)stream;
   DKS_CUDA_TRY(cudaMemsetAsync(A, 0, (size_t)nz * nz * sizeof(double2), st));
   DKS_CUDA_TRY(cudaMemsetAsync(S, 0, (size_t)nz * nz * sizeof(double2), st));
-  if (prec == DKS_PREC_FP64_EMULATED) {
+  if (prec == DKS_PREC_FP64_EMULATED && tc_enabled(TC_FP64)) {
+    // exact integer slices of Z and HZ on the tensor cores
+    const size_t ob = (oz_bytes(rows, nz) + 255) / 256 * 256;
+    unsigned char* buf = nullptr;
+    if (cudaMallocAsync((void**)&buf, 2 * ob, st) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DKS_ERR_OOM, "dks_gram_hermitian: no device memory for the slices");
+    }
+    OzBlock oz, ozh;
+    oz_layout(buf, rows, nz, &oz);
+    oz_layout(buf + ob, rows, nz, &ozh);
+    int rc = oz_split((const double2*)Z, rows, nz, oz, st);
+    if (!rc) rc = oz_split((const double2*)HZ, rows, nz, ozh, st);
+    if (!rc) rc = oz_gram(oz, ozh, nz, (double2*)A, (double2*)S, st);
+    cudaFreeAsync(buf, st);
+    DKS_TRY(rc);
+  } else if (prec == DKS_PREC_FP64_EMULATED) {
     const size_t n = (size_t)nz * rows;
     float4* zs = nullptr;
     if (cudaMallocAsync((void**)&zs, 2 * n * sizeof(float4), st) != cudaSuccess) {
@@ -674,6 +690,20 @@ int dks_rotate(const void* Z, int rows, int nz, const void* W, int ldw, int n, v
   if (rows <= 0 || nz <= 0 || n <= 0 || ldw < nz || !Z || !W || !OUT)
     return fail(DKS_ERR_INVALID_ARG, "dks_rotate: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
+  if (prec == DKS_PREC_FP64_EMULATED && tc_enabled(TC_FP64)) {
+    // exact integer slices of Z on the tensor cores
+    void* buf = nullptr;
+    if (cudaMallocAsync(&buf, oz_bytes(rows, nz), st) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DKS_ERR_OOM, "dks_rotate: no device memory for the slices");
+    }
+    OzBlock oz;
+    oz_layout(buf, rows, nz, &oz);
+    int rc = oz_split((const double2*)Z, rows, nz, oz, st);
+    if (!rc) rc = oz_rotate(oz, 0, nz, (const double2*)W, ldw, n, (double2*)OUT, rows, beta, st);
+    cudaFreeAsync(buf, st);
+    return rc;
+  }
   if (prec == DKS_PREC_FP64_EMULATED)
     return gemm_nn_df((const double2*)Z, rows, rows, nz, (const double2*)W, ldw, nullptr, n, (double2*)OUT, rows,
                       beta, st);

@@ -246,7 +246,8 @@ int gather_cols(const double2* v, int ldv, int row0, int rows, const int* act, i
 // complex64 contractions on tcgen05 with three BF16 slices per FP32 value (tc_gemm.cu); the
 // bits select which of the FP32 contractions take that path (dks_tensor_cores)
 constexpr int TC_ROTATE = DKS_TC_ROTATE, TC_GRAM = DKS_TC_GRAM, TC_PROJ_HN = DKS_TC_PROJ_HN,
-              TC_PROJ_NN = DKS_TC_PROJ_NN, TC_ALL = DKS_TC_ALL, TC_DEFAULT = DKS_TC_DEFAULT;
+              TC_PROJ_NN = DKS_TC_PROJ_NN, TC_FP64 = DKS_TC_FP64, TC_ALL = DKS_TC_ALL,
+              TC_DEFAULT = DKS_TC_DEFAULT;
 bool tc_enabled(int bit);            // bit selected and the device is a GB300 (sm_103)
 bool tc_device();                    // the device is a GB300 (sm_103)
 int tc_mask();
@@ -263,5 +264,23 @@ int tc_gram(const float2* z, const float2* hz, int ld, int k, int m, double2* a,
 // c = a^H b (m x n, ldc), or with conj_transpose_out c = b^H a (n x m, ldc), written
 int tc_gemm_hn(const float2* a, int lda, const float2* b, int ldb, int k, int m, int n, double2* c, int ldc,
                bool conj_transpose_out, cudaStream_t st, int nsm);
+
+// complex128 contractions on tcgen05 from exact integer slices (oz_gemm.cu): a block is sliced
+// once (oz_split) into a buffer of oz_bytes(rows, ncol) bytes laid out by oz_layout
+struct OzBlock {
+  uint16_t* sl = nullptr;            // [6 slices][re, im][ncolp / 8][rowsp / 8][8 x 8] BF16
+  int* ex = nullptr;                 // [rowsp / 128][ncolp] window exponents
+  int rows = 0, rowsp = 0, ncol = 0, ncolp = 0;
+};
+size_t oz_bytes(int rows, int ncol);
+int oz_layout(void* buf, int rows, int ncol, OzBlock* out);
+// slices of the first ncol columns of a (rows x ncol, lda); ncol <= the block's capacity
+int oz_split(const double2* a, long long lda, int ncol, const OzBlock& z, cudaStream_t st);
+// lower triangles of A = Z^H HZ and S = Z^H Z over the first m columns (m x m, written)
+int oz_gram(const OzBlock& z, const OzBlock& hz, int m, double2* a, double2* s, cudaStream_t st);
+// out (rows x n, ldo) = alpha Z[:, c0 : c0 + m] W (+ beta out), W m x n complex128 (ldw)
+int oz_rotate(const OzBlock& z, int c0, int m, const double2* w, int ldw, int n, double2* out, int ldo, double beta,
+              cudaStream_t st, double alpha = 1.0);
+int oz_status_take();                // DKS_ERR_TIMEOUT when such a kernel gave up a wait (then cleared)
 
 }  // namespace dks

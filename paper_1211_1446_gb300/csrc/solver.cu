@@ -45,6 +45,11 @@ struct Blocks {
   // the Gram matrices and all four rotations
   float4* zdf = nullptr;
   float4* hzdf = nullptr;
+  // or exact integer slices of Z and HZ for the tensor cores (DKS_TC_FP64): split once per
+  // iteration, read by the Gram matrices and all four rotations
+  void* ozz = nullptr;
+  void* ozh = nullptr;
+  int ozcols = 0;      // column capacity of the slice buffers
   // FP32 phase: copy of the X with the lowest residual so far (the FP64 phase starts from it)
   V* best = nullptr;
 };
@@ -191,8 +196,21 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
   DKS_TRY(apply_h<V>(ctx, ex, ik, b.z[cur], b.hz[cur], n, 0.0, 1.0, st));
   happ += n;
   // Gram matrices and rotations of nz columns of Z, HZ (from double-float copies when present)
-  const bool split = df && b.zdf && b.hzdf;
+  const bool slices = df && b.ozz && b.ozh;
+  const bool split = df && !slices && b.zdf && b.hzdf;
+  OzBlock ozz, ozh;
+  if (slices) {
+    DKS_TRY(oz_layout(b.ozz, rows, b.ozcols, &ozz));
+    DKS_TRY(oz_layout(b.ozh, rows, b.ozcols, &ozh));
+  }
   auto gram_z = [&](int nzc) -> int {
+    if (slices) {
+      DKS_TRY(oz_split((const double2*)b.z[cur], rows, nzc, ozz, st));
+      DKS_TRY(oz_split((const double2*)b.hz[cur], rows, nzc, ozh, st));
+      DKS_TRY(oz_gram(ozz, ozh, nzc, sm.a, sm.s, st));
+      DKS_TRY(mirror_lower(sm.a, nzc, st));
+      return mirror_lower(sm.s, nzc, st);
+    }
     if (!split) return gram<V>(b.z[cur], b.hz[cur], rows, nzc, sm, st, df);
     DKS_TRY(split_df((const double2*)b.z[cur], b.zdf, (size_t)nzc * colsz, st));
     DKS_TRY(split_df((const double2*)b.hz[cur], b.hzdf, (size_t)nzc * colsz, st));
@@ -200,6 +218,7 @@ static int phase(dks_ctx* ctx, Exec& ex, int ik, Blocks<V>& b, Small& sm, Pinned
   };
   // out <- Z[c0:c0+m] W (h: from HZ instead of Z)
   auto rotate = [&](bool h, size_t c0, int m, const double2* w, int ldw, int ncol, V* outp) -> int {
+    if (slices) return oz_rotate(h ? ozh : ozz, (int)c0, m, w, ldw, ncol, (double2*)outp, rows, 0.0, st);
     if (split)
       return gemm_nn_df((h ? b.hzdf : b.zdf) + c0 * colsz, rows, rows, m, w, ldw, nullptr, ncol, (double2*)outp,
                         rows, 0.0, st);
@@ -562,13 +581,16 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
   const size_t small = (2 * nz * nz + 2 * nz * nmax + rr_scratch_elems((int)nz)) * sizeof(double2) +
                        (nmax + 3 * nmax) * sizeof(double) + (nmax + 4) * sizeof(int) + 16 * 256;
   const bool split_copies = mixed && opts.emulate_fp64 != 0 && !davidson;
+  // FP64-phase contractions on the tensor cores: exact integer slices instead of double-float copies
+  const bool oz_slices = split_copies && tc_enabled(TC_FP64);
+  const size_t ozb = oz_slices ? (oz_bytes(rowsmax, (int)cols) + 255) / 256 * 256 : 0;
   // band blocks: FP32 copy of the locked vectors (mixed mode) and the projection coefficients
   const size_t lock32 = mixed ? (size_t)nlockmax * rowsmax * sizeof(float2) : 0;
   const size_t lockcoef = (size_t)nlockmax * nmax * sizeof(double2);
   const size_t dcols64 = (size_t)2 * mmax + 4 * (size_t)nmax, dcols32 = mixed ? (size_t)2 * mmax + 5 * (size_t)nmax : 0;
   const size_t total =
       davidson ? (dcols64 * sizeof(double2) + dcols32 * sizeof(float2)) * rowsmax + small + 32 * 256
-               : 4 * big64 + tmp64 + 4 * big32 + 2 * tmp32 + small + (split_copies ? 2 * big64 : 0) + lock32 +
+               : 4 * big64 + tmp64 + 4 * big32 + 2 * tmp32 + small + (split_copies ? (oz_slices ? 2 * ozb : 2 * big64) : 0) + lock32 +
                      lockcoef + 18 * 256;
   // concurrent k-point workers, each with its own stream and workspace (bounded by free memory)
   int nworkers = opts.concurrency > 0 ? opts.concurrency : std::min(ctx->nk, 4);
@@ -639,7 +661,11 @@ int dks_lobpcgf_solve(dks_ctx* ctx, int nev, double tol, const dks_solve_opts* o
       b64.hz[0] = (double2*)take(big64);
       b64.hz[1] = (double2*)take(big64);
       b64.tmp = (double2*)take(tmp64);
-      if (split_copies) {
+      if (oz_slices) {
+        b64.ozz = take(ozb);
+        b64.ozh = take(ozb);
+        b64.ozcols = (int)cols;
+      } else if (split_copies) {
         b64.zdf = (float4*)take(big64);
         b64.hzdf = (float4*)take(big64);
       }
