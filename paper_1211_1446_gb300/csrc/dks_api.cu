@@ -293,10 +293,12 @@ static void free_ctx(dks_ctx* ctx) {
     cudaFree(kp.bt64);
     cudaFree(kp.bt32);
     cudaFree(kp.btdf);
+    if (kp.btoz) cudaFree(kp.btoz);
   }
   for (Exec* e : ctx->exec) {
     release(e->ws_h);
     release(e->ws_solve);
+    release(e->ws_oz);
     if (e->own) cudaStreamDestroy(e->own);
     delete e;
   }

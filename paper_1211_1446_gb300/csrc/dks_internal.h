@@ -65,6 +65,10 @@ struct KPoint {
   double2* bt64 = nullptr;      // nproj x (2 npw) projector rows (beta, spin-major)
   float2* bt32 = nullptr;
   float4* btdf = nullptr;       // the same rows as double-float (re hi, re lo, im hi, im lo)
+  // exact integer slices of bt64 for the refinement phase's projector contractions on the
+  // tensor cores (oz_gemm.cu layout), made on first use; btoz_state 1 ready, -1 not held
+  void* btoz = nullptr;
+  int btoz_state = 0;
   double cshift = 0, omega = 1; // default filter constants
 };
 
@@ -78,6 +82,7 @@ struct Workspace {
 struct Exec {
   Workspace ws_h;               // H' intermediates + projector coefficients
   Workspace ws_solve;           // solver blocks
+  Workspace ws_oz;              // exact integer slices of x~ for the projector contractions
   bool df_gemm = false;         // complex128 projector contractions in double-float arithmetic
   cudaStream_t own = nullptr;   // stream created for a concurrent solve worker
 };
@@ -268,7 +273,7 @@ int tc_gemm_hn(const float2* a, int lda, const float2* b, int ldb, int k, int m,
 // complex128 contractions on tcgen05 from exact integer slices (oz_gemm.cu): a block is sliced
 // once (oz_split) into a buffer of oz_bytes(rows, ncol) bytes laid out by oz_layout
 struct OzBlock {
-  uint16_t* sl = nullptr;            // [6 slices][re, im][ncolp / 8][rowsp / 8][8 x 8] BF16
+  uint16_t* sl = nullptr;            // [7 slices][re, im][ncolp / 8][rowsp / 8][8 x 8] BF16
   int* ex = nullptr;                 // [rowsp / 128][ncolp] window exponents
   int rows = 0, rowsp = 0, ncol = 0, ncolp = 0;
 };
@@ -280,7 +285,13 @@ int oz_split(const double2* a, long long lda, int ncol, const OzBlock& z, cudaSt
 int oz_gram(const OzBlock& z, const OzBlock& hz, int m, double2* a, double2* s, cudaStream_t st);
 // out (rows x n, ldo) = alpha Z[:, c0 : c0 + m] W (+ beta out), W m x n complex128 (ldw)
 int oz_rotate(const OzBlock& z, int c0, int m, const double2* w, int ldw, int n, double2* out, int ldo, double beta,
-              cudaStream_t st, double alpha = 1.0);
+              cudaStream_t st, double alpha = 1.0, const double* wscale = nullptr, int cat = P_ROTATE);
+// C = A^H B (m x n, ldc) over the first m columns of a and n of b, or with conj_transpose_out
+// C = B^H A (n x m, ldc); written
+int oz_gemm_hn(const OzBlock& a, int m, const OzBlock& b, int n, double2* c, int ldc, bool conj_transpose_out,
+               cudaStream_t st, int cat = P_GRAM);
+// the slices of a k-point's projector table (created on first use; false when they cannot be held)
+bool projector_slices(dks_ctx* ctx, int ik, cudaStream_t st);
 int oz_status_take();                // DKS_ERR_TIMEOUT when such a kernel gave up a wait (then cleared)
 
 }  // namespace dks

@@ -666,11 +666,23 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
   V* tbuf = reinterpret_cast<V*>(reinterpret_cast<char*>(ex.ws_h.ptr) + zp_bytes);
   void* pbuf = p_bytes ? reinterpret_cast<char*>(ex.ws_h.ptr) + zp_bytes + t_bytes : nullptr;
   const V* bt = nullptr;
+  // refinement phase with DKS_TC_FP64: both projector contractions from exact integer slices of
+  // x~ (made here) and of the projector table (made once per k-point)
+  const bool ozp = fp64 && ex.df_gemm && ctx->nproj && tc_enabled(TC_FP64) && projector_slices(ctx, ik, st);
+  OzBlock bto;
+  if (ozp) DKS_TRY(oz_layout(kp.btoz, 2 * npw, ctx->nproj, &bto));
   if (ctx->nproj) {
     bt = fp64 ? reinterpret_cast<const V*>(kp.bt64) : reinterpret_cast<const V*>(kp.bt32);
     DKS_CUDA_TRY(cudaMemsetAsync(zp, 0, zp_elems * sizeof(double2), st));
     // Z = B^H x~ : (nproj x 2npw) (2npw x 2nb)
-    if (fp64 && ex.df_gemm)
+    if (ozp) {
+      // x~ (2 npw x ncol) as the A operand, the table as B: Z = (x~^H B)^H
+      DKS_TRY(grow(ex.ws_oz, oz_bytes(2 * npw, ncol)));
+      OzBlock xo;
+      DKS_TRY(oz_layout(ex.ws_oz.ptr, 2 * npw, ncol, &xo));
+      DKS_TRY(oz_split((const double2*)x, 2 * npw, ncol, xo, st));
+      DKS_TRY(oz_gemm_hn(xo, ncol, bto, ctx->nproj, zp, ctx->nproj, true, st, P_PROJ_HN));
+    } else if (fp64 && ex.df_gemm)
       DKS_TRY(gemm_hn_df(kp.btdf, 2 * npw, (const double2*)x, 2 * npw, 2 * npw, ctx->nproj, ncol, zp, st,
                          P_PROJ_HN));
     else
@@ -698,7 +710,10 @@ int apply_h(dks_ctx* ctx, Exec& ex, int ik, const V* x, V* out, int nb, double s
   DKS_CUDA_TRY(cudaGetLastError());
   if (ctx->nproj) {
     // out~ += B (scale D Z)
-    if (fp64 && ex.df_gemm)
+    if (ozp)
+      DKS_TRY(oz_rotate(bto, 0, ctx->nproj, zp, ctx->nproj, ncol, (double2*)out, 2 * npw, 1.0, st, scale,
+                        ctx->dvec_dev, P_PROJ_NN));
+    else if (fp64 && ex.df_gemm)
       DKS_TRY(gemm_nn_df(kp.btdf, 2 * npw, 2 * npw, ctx->nproj, zp, ctx->nproj, ctx->dvec_dev, ncol,
                          (double2*)out, 2 * npw, 1.0, st, scale, P_PROJ_NN));
     else

@@ -86,17 +86,21 @@ __device__ __forceinline__ long long fixed56(unsigned long long bits, int E) {
   const long long f = sh <= 0 ? (long long)(m53 << (-sh)) : (long long)((m53 + (1ull << (sh - 1))) >> sh);
   return (bits >> 63) ? -f : f;
 }
-// seven balanced base-256 digits of F, as the BF16 bit patterns of d_s 2^(-8s)
+// seven balanced base-256 digits of F (F = sum_s d_s 256^(6-s), -128 <= d_s <= 127 for s >= 1), as
+// the BF16 bit patterns of d_s 2^(-8s).  Adding 128 to each of the six low bytes makes them plain
+// bytes of G = F + 0x808080808080: d_s = byte - 128 for s >= 1 and d_0 = G >> 48 (the unique
+// balanced representation, without a carry chain).
 __device__ __forceinline__ void digits7(long long f, uint16_t (&out)[kS]) {
+  const long long g = f + 0x0000808080808080LL;
+  const uint32_t lo = (uint32_t)g, hi = (uint32_t)((unsigned long long)g >> 32);
   int d[kS];
-#pragma unroll
-  for (int s = kS - 1; s >= 1; --s) {
-    int lo = (int)(f & 255);
-    lo -= (lo >= 128) ? 256 : 0;
-    d[s] = lo;
-    f = (f - lo) >> 8;
-  }
-  d[0] = (int)f;
+  d[0] = (int)(g >> 48);
+  d[1] = (int)((hi >> 8) & 255u) - 128;
+  d[2] = (int)(hi & 255u) - 128;
+  d[3] = (int)(lo >> 24) - 128;
+  d[4] = (int)((lo >> 16) & 255u) - 128;
+  d[5] = (int)((lo >> 8) & 255u) - 128;
+  d[6] = (int)(lo & 255u) - 128;
 #pragma unroll
   for (int s = 0; s < kS; ++s) {
     const float x = (float)d[s] * __int_as_float((127 - 8 * s) << 23);   // d_s 2^(-8s), exact
@@ -178,32 +182,37 @@ __device__ __forceinline__ void df_add2(float& h, float& l, float h2, float l2) 
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }   // -126 <= k <= 127
 
 // ================================================================ Gram: A = Z^H HZ, S = Z^H Z
-// A tile is 128 columns of Z (MMA M) against 32 columns of HZ (A) or of Z (S), over a chunk of
-// whole windows.  Warp 0: TMA producer (one 5-D copy of the A slices and one of the B slices per
-// 16-row stage); warp 1: MMA issuer and TMEM owner; warps 2-17: fold.  TMEM: five accumulators
-// x (re 32 | im 32) columns.  Per pair (s, t) three MMAs: A_re(s) [B_re(t) | B_im(t)] (N = 64,
-// the two parts of a B slice are adjacent in shared memory) into (re | im), A_im(s) B_im(t) into
-// re and A_im(s) (-B_re(t)) into im.  At the end of a window the fold warps read the five
-// accumulators (the MMAs of the next window wait only for that read), add them in double-float,
-// scale by 2^(E_a + E_b - 16) and add into double-float registers.
-constexpr int G_N = 32;
-constexpr uint32_t G_A_BYTES = kS * 2 * 16 * 2 * kCore;    // [s][p][16 column groups][2 row groups]
-constexpr uint32_t G_B_BYTES = kS * 2 * 4 * 2 * kCore;     // [s][p][4 column groups][2 row groups]
-constexpr uint32_t G_STG = G_A_BYTES + G_B_BYTES;
-constexpr int G_NSTG = 3;
-constexpr int G_THREADS = 18 * 32;
+// A tile is 128 columns of Z (MMA M) against 48 columns of HZ (A) or of Z (S), over a chunk of
+// whole windows.  Warp 0: TMA producer (per 16-row stage one 5-D copy of the A slices and one
+// copy per slice of the B slices); warp 1: MMA issuer and TMEM owner; warps 2-17: fold; warp 18:
+// writes -B_re next to each slice's B_im.  Per slice t the stage then holds [B_re | B_im | -B_re]
+// (48 rows each), and per pair (s, t) two MMAs of N = 96, A_re(s) [B_re | B_im] and A_im(s)
+// [B_im | -B_re], add the real and imaginary parts into one accumulator (the N = 96 operands keep
+// the tensor core's shared-memory reads per multiply-add low).  TMEM: five accumulators x
+// (re 48 | im 48) columns.  At the end of a window the fold warps read the five accumulators
+// (the MMAs of the next window wait only for that read), scale by 2^(E_a + E_b - 16) and add
+// into double-float registers.
+constexpr int G_N = 48;
+constexpr uint32_t G_A_BYTES = kS * 2 * 16 * 2 * kCore;     // [s][p][16 column groups][2 row groups]
+constexpr uint32_t G_BP_BYTES = (G_N / 8) * 2 * kCore;      // one part of one B slice: 6 groups x 2
+constexpr uint32_t G_BS_BYTES = 3 * G_BP_BYTES;             // [B_re | B_im | -B_re] of one slice
+constexpr uint32_t G_STG = G_A_BYTES + kS * G_BS_BYTES;
+constexpr uint32_t G_TX = G_A_BYTES + kS * 2 * G_BP_BYTES;   // bytes landed by TMA per stage
+constexpr int G_NSTG = 2;
+constexpr int G_THREADS = 19 * 32;
 constexpr size_t G_SMEM = 1024 + G_NSTG * (size_t)G_STG + 256;
-constexpr int G_STEPS = kWin / 16;                         // 16-row stages per window
+constexpr int G_STEPS = kWin / 16;                          // 16-row stages per window
+constexpr uint32_t G_REG = 2 * G_N;                         // TMEM columns per accumulator
 
 struct GTile {
-  int ia0, jb, src;   // Z columns [ia0, ia0 + 128) against columns [jb, jb + 32) of HZ (src 0) or Z (src 1)
+  int ia0, jb, src;   // Z columns [ia0, ia0 + 128) against columns [jb, jb + 48) of HZ (src 0) or Z (src 1)
 };
 struct GramArgs {
-  int nwin, wpc, ntiles, ncolp;
+  int nwin, wpc, ntiles, ncolp, ncolpb;   // column capacities of A (Z) and of the B operand
   const GTile* tile;
   const int* exz;     // [window][ncolp] exponents of Z
   const int* exh;     // of HZ
-  double2* part;      // [split][tile][32 columns][128 rows]
+  double2* part;      // [split][tile][48 columns][128 rows]
 };
 
 __global__ void __launch_bounds__(G_THREADS, 1) k_oz_gram(const __grid_constant__ CUtensorMap tz,
@@ -214,8 +223,9 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_oz_gram(const __grid_constant_
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const GTile tl = p.tile[blockIdx.x];
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + G_NSTG * (size_t)G_STG);
-  uint64_t* stg_full = bars;               // [G_NSTG]
-  uint64_t* stg_empty = stg_full + G_NSTG; // [G_NSTG]
+  uint64_t* stg_full = bars;               // [G_NSTG] copies landed
+  uint64_t* neg_full = stg_full + G_NSTG;  // [G_NSTG] -B_re written
+  uint64_t* stg_empty = neg_full + G_NSTG; // [G_NSTG] MMAs done with the stage
   uint64_t* acc_full = stg_empty + G_NSTG; // window sums in TMEM
   uint64_t* acc_empty = acc_full + 1;      // read by the 16 fold warps
   uint64_t* drainb = acc_empty + 1;
@@ -229,6 +239,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_oz_gram(const __grid_constant_
   if (tid == 0) {
     for (int i = 0; i < G_NSTG; ++i) {
       mbar_init(&stg_full[i], 1);
+      mbar_init(&neg_full[i], 1);
       mbar_init(&stg_empty[i], 1);
     }
     mbar_init(acc_full, 1);
@@ -247,7 +258,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_oz_gram(const __grid_constant_
     // ---------------------------------------------------------------- producer
     if (lane == 0) {
       int issued = 0;
-      const CUtensorMap* mb = tl.src ? &tzb : &th;   // B boxes: 4 column groups
+      const CUtensorMap* mb = tl.src ? &tzb : &th;   // B boxes: 6 column groups, one slice
       for (int q = 0; q < total && !*sflag; ++q) {
         const int st = q % G_NSTG;
         if (q >= G_NSTG && !mbar_wait(&stg_empty[st], (uint32_t)((q / G_NSTG) - 1) & 1u)) {
@@ -256,20 +267,40 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_oz_gram(const __grid_constant_
         }
         unsigned char* s = sm + (size_t)st * G_STG;
         const int rgc = (w0 + q / G_STEPS) * (kWin / 8) + (q % G_STEPS) * 2;
-        mbar_expect_tx(&stg_full[st], G_STG);
+        mbar_expect_tx(&stg_full[st], G_TX);
         tma_load_5d(s, &tz, 0, rgc, tl.ia0 / 8, 0, 0, &stg_full[st]);
-        tma_load_5d(s + G_A_BYTES, mb, 0, rgc, tl.jb / 8, 0, 0, &stg_full[st]);
+        for (int t = 0; t < kS; ++t)
+          tma_load_5d(s + G_A_BYTES + t * G_BS_BYTES, mb, 0, rgc, tl.jb / 8, 0, t, &stg_full[st]);
         issued = q + 1;
       }
       for (int q = max(0, issued - G_NSTG); q < issued; ++q) mbar_wait(&stg_full[q % G_NSTG], (uint32_t)(q / G_NSTG) & 1u);
     }
+  } else if (warp == 18) {
+    // ---------------------------------------------------------------- -B_re next to B_im
+    for (int q = 0; q < total && !*sflag; ++q) {
+      const int st = q % G_NSTG;
+      if (!mbar_wait(&stg_full[st], (uint32_t)(q / G_NSTG) & 1u)) {
+        *sflag = 1;
+        break;
+      }
+      unsigned char* b = sm + (size_t)st * G_STG + G_A_BYTES;
+      for (int i = lane; i < kS * (int)(G_BP_BYTES / 16); i += 32) {
+        const int t = i / (G_BP_BYTES / 16), o = (i % (G_BP_BYTES / 16)) * 16;
+        const uint4 v = *reinterpret_cast<const uint4*>(b + t * G_BS_BYTES + o);
+        *reinterpret_cast<uint4*>(b + t * G_BS_BYTES + 2 * G_BP_BYTES + o) =
+            make_uint4(v.x ^ 0x80008000u, v.y ^ 0x80008000u, v.z ^ 0x80008000u, v.w ^ 0x80008000u);
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&neg_full[st]);
+    }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const uint32_t id64 = idesc_bf16(128, 2 * G_N), id32 = idesc_bf16(128, G_N), id32n = id32 | kNegateB;
+      const uint32_t id96 = idesc_bf16(128, 2 * G_N);
       for (int q = 0; q < total && !*sflag; ++q) {
         const int st = q % G_NSTG, wl = q / G_STEPS, ks = q % G_STEPS;
-        bool ok = mbar_wait(&stg_full[st], (uint32_t)(q / G_NSTG) & 1u);
+        bool ok = mbar_wait(&neg_full[st], (uint32_t)(q / G_NSTG) & 1u);
         if (ok && ks == 0 && wl >= 1) ok = mbar_wait(acc_empty, (uint32_t)(wl - 1) & 1u);
         if (!ok) {
           *sflag = 1;
@@ -283,12 +314,11 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_oz_gram(const __grid_constant_
           const uint32_t acc = (ks == 0 && pair_first(pr)) ? 0u : 1u;
           const uint64_t are = sdesc(sa + (uint32_t)(2 * s) * 4096u, 128, 256);
           const uint64_t aim = sdesc(sa + (uint32_t)(2 * s + 1) * 4096u, 128, 256);
-          const uint64_t bre = sdesc(sb + (uint32_t)(2 * t) * 1024u, 128, 256);       // [B_re | B_im]
-          const uint64_t bim = sdesc(sb + (uint32_t)(2 * t + 1) * 1024u, 128, 256);
-          const uint32_t dre = tmem + 64u * (uint32_t)reg, dim = dre + 32u;
-          mma_bf16(dre, are, bre, id64, acc);      // (re | im) += A_re (B_re | B_im)
-          mma_bf16(dre, aim, bim, id32, 1u);       // re += A_im B_im
-          mma_bf16(dim, aim, bre, id32n, 1u);      // im -= A_im B_re
+          const uint64_t p1 = sdesc(sb + (uint32_t)t * G_BS_BYTES, 128, 256);               // [B_re | B_im]
+          const uint64_t p2 = sdesc(sb + (uint32_t)t * G_BS_BYTES + G_BP_BYTES, 128, 256);  // [B_im | -B_re]
+          const uint32_t d = tmem + G_REG * (uint32_t)reg;
+          mma_bf16(d, are, p1, id96, acc);
+          mma_bf16(d, aim, p2, id96, 1u);
         }
         mma_commit(&stg_empty[st]);
         if (ks == G_STEPS - 1) mma_commit(acc_full);
@@ -298,75 +328,71 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_oz_gram(const __grid_constant_
     }
   } else {
     // ---------------------------------------------------------------- fold, then the partial tile
-    const int lq = warp & 3, cq = (warp - 2) >> 2;     // lanes [32 lq, +32), columns [8 cq, 8 cq + 8)
+    const int lq = warp & 3, cq = (warp - 2) >> 2;     // lanes [32 lq, +32), columns [12 cq, 12 cq + 12)
     const int row = 32 * lq + lane;
     const int ia = tl.ia0 + row;
     const int* exb = tl.src ? p.exz : p.exh;
-    float ah[16], al[16];                              // re: 0..7, im: 8..15
-    int eref[8];
+    float ah[24], al[24];                              // re: 0..11, im: 12..23
+    int eref[12];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) ah[e] = al[e] = 0.f;
+    for (int e = 0; e < 24; ++e) ah[e] = al[e] = 0.f;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) eref[e] = INT_MIN;
+    for (int e = 0; e < 12; ++e) eref[e] = INT_MIN;
     for (int wl = 0; wl < nw && !*sflag; ++wl) {
+      // scales of this window (loaded while the window's MMAs run)
+      const int w = w0 + wl;
+      const int ea = ia < p.ncolp ? p.exz[(size_t)w * p.ncolp + ia] : 0;
+      float sc[12];
+#pragma unroll
+      for (int e = 0; e < 12; ++e) {
+        const int j = tl.jb + 12 * cq + e;
+        const int k = ea + (j < p.ncolpb ? exb[(size_t)w * p.ncolpb + j] : 0) - 16;
+        if (eref[e] == INT_MIN) eref[e] = k;
+        int d = k - eref[e];
+        if (d > 60) {   // a window far larger than the reference: rescale the running sums
+          const float r = d > 126 ? 0.f : pow2f(-d);
+          ah[e] *= r;
+          al[e] *= r;
+          ah[12 + e] *= r;
+          al[12 + e] *= r;
+          eref[e] = k;
+          d = 0;
+        }
+        sc[e] = d < -100 ? 0.f : pow2f(d);   // below 2^-100 of the running sums: dropped
+      }
       if (!mbar_wait(acc_full, (uint32_t)wl & 1u)) {
         *sflag = 1;
         break;
       }
       tc_fence_after();
-      const uint32_t base = tmem + ((uint32_t)(32 * lq) << 16) + 8u * (uint32_t)cq;
-      float h[16], l[16];
+      const uint32_t base = tmem + ((uint32_t)(32 * lq) << 16) + 12u * (uint32_t)cq;
 #pragma unroll
       for (int reg = 0; reg < kRegs; ++reg) {
-        float re[8], im[8];
-        tmem_ld8(base + 64u * (uint32_t)reg, re);
-        tmem_ld8(base + 64u * (uint32_t)reg + 32u, im);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          if (reg == 0) {
-            h[e] = re[e];
-            h[8 + e] = im[e];
-            l[e] = l[8 + e] = 0.f;
-          } else {
-            df_add1(h[e], l[e], re[e]);
-            df_add1(h[8 + e], l[8 + e], im[e]);
+        for (int c4 = 0; c4 < 3; ++c4) {
+          float re[4], im[4];
+          tmem_ld4(base + G_REG * (uint32_t)reg + 4u * c4, re);
+          tmem_ld4(base + G_REG * (uint32_t)reg + G_N + 4u * c4, im);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = 4 * c4 + e;
+            df_add2(ah[k], al[k], re[e] * sc[k], 0.f);
+            df_add2(ah[12 + k], al[12 + k], im[e] * sc[k], 0.f);
           }
         }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
-      const int w = w0 + wl;
-      const int ea = ia < p.ncolp ? p.exz[(size_t)w * p.ncolp + ia] : 0;
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int j = tl.jb + 8 * cq + e;
-        const int k = ea + (j < p.ncolp ? exb[(size_t)w * p.ncolp + j] : 0) - 16;
-        if (eref[e] == INT_MIN) eref[e] = k;
-        int d = k - eref[e];
-        if (d > 60) {   // a window far larger than the reference: rescale the running sums
-          const float sc = d > 126 ? 0.f : pow2f(-d);
-          ah[e] *= sc;
-          al[e] *= sc;
-          ah[8 + e] *= sc;
-          al[8 + e] *= sc;
-          eref[e] = k;
-          d = 0;
-        }
-        if (d < -100) continue;   // below 2^-100 of the running sums
-        const float sc = pow2f(d);
-        df_add2(ah[e], al[e], h[e] * sc, l[e] * sc);
-        df_add2(ah[8 + e], al[8 + e], h[8 + e] * sc, l[8 + e] * sc);
-      }
     }
     if (!*sflag) {
       double2* dst = p.part + ((size_t)blockIdx.y * p.ntiles + blockIdx.x) * (size_t)G_N * 128;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int col = 8 * cq + e;
+      for (int e = 0; e < 12; ++e) {
+        const int col = 12 * cq + e;
         const int k = eref[e] == INT_MIN ? 0 : eref[e];
         dst[(size_t)col * 128 + row] = double2{ldexp((double)ah[e] + (double)al[e], k),
-                                               ldexp((double)ah[8 + e] + (double)al[8 + e], k)};
+                                               ldexp((double)ah[12 + e] + (double)al[12 + e], k)};
       }
     }
   }
@@ -379,10 +405,11 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_oz_gram(const __grid_constant_
   }
 }
 
-// Sum of the partial tiles over the chunks in FP64, fixed order (warp order of strided sums);
-// lower triangles of A (tiles of HZ) and S (tiles of Z), column-major with ldc.
+// Sum of the partial tiles over the chunks in FP64, fixed order (warp order of strided sums).
+// mode 0 (Gram): lower triangles of A (tiles of HZ) and S (tiles of Z), column-major with ldc;
+// mode 1: C[j ldc + i] = (A^H B)_ij for i < m, j < n; mode 2: C[i ldc + j] = conj (= B^H A).
 struct GRedArgs {
-  int splits, ntiles, m, ldc;
+  int splits, ntiles, m, n, ldc, mode;
   const GTile* tile;
   const double2* part;
   double2* a;
@@ -413,8 +440,23 @@ __global__ void __launch_bounds__(256) k_oz_gram_reduce(GRedArgs p) {
       t.y += red[w][lane].y;
     }
     const int i = tl.ia0 + row, j = tl.jb + col;
-    if (i < p.m && j <= i) (tl.src ? p.s : p.a)[(size_t)j * p.ldc + i] = t;
+    if (p.mode == 0) {
+      if (i < p.m && j <= i) (tl.src ? p.s : p.a)[(size_t)j * p.ldc + i] = t;
+    } else if (i < p.m && j < p.n) {
+      if (p.mode == 1) p.a[(size_t)j * p.ldc + i] = t;
+      else p.a[(size_t)i * p.ldc + j] = double2{t.x, -t.y};
+    }
   }
+}
+
+// W'[j][c] = w[j ldw + c] ws[c] (projector update: the channel weights D)
+__global__ void k_oz_scale_w(const double2* __restrict__ w, int ldw, const double* __restrict__ ws, int m, int n,
+                             double2* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m * n) return;
+  const int c = i % m, j = i / m;
+  const double2 v = w[(size_t)j * ldw + c];
+  out[i] = double2{v.x * ws[c], v.y * ws[c]};
 }
 
 // ================================================================ rotation: OUT = alpha Z W (+ beta OUT)
@@ -619,19 +661,23 @@ __global__ void __launch_bounds__(R_THREADS, 1) k_oz_rot(const __grid_constant__
           unsigned char* dstb = sbw + (size_t)ob * bbytes;
           // core-matrix row of B row r (of 2 nt) for the 8 columns of half kg
           auto off = [&](int r) { return (uint32_t)(((r >> 3) * 2 + kg) * kCore + (r & 7) * 16); };
+          // the eight W values of this lane first (independent read-only loads, one latency),
+          // then their digits
+          double2 wv[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int wc = p.cg0 * 8 + ch * R_KC + kg * 8 + e - p.c0, j = n0 + jl;
+            wv[e] = (wc >= 0 && wc < p.m && j < p.n) ? __ldg(p.w + (size_t)j * p.ldw + wc) : double2{0.0, 0.0};
+          }
 #pragma unroll
           for (int pp = 0; pp < 2; ++pp) {
             uint32_t wd[kS][4];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const int cl = ch * R_KC + kg * 8 + e;
-              const int wc = p.cg0 * 8 + cl - p.c0, j = n0 + jl;
-              long long f = 0;
-              if (wc >= 0 && wc < p.m && j < p.n) {
-                const double* x = reinterpret_cast<const double*>(p.w + (size_t)j * p.ldw + wc);
-                // W' = 2^E(t, c) W relative to 2^F_j: the window exponent enters the shift
-                f = fixed56((unsigned long long)__double_as_longlong(x[pp]), fjv - etw[cl]);
-              }
+              // W' = 2^E(t, c) W relative to 2^F_j: the window exponent enters the shift
+              const double x = pp ? wv[e].y : wv[e].x;
+              const long long f = fixed56((unsigned long long)__double_as_longlong(x), fjv - etw[cl]);
               uint16_t dg[kS];
               digits7(f, dg);
 #pragma unroll
@@ -708,19 +754,33 @@ __global__ void __launch_bounds__(R_THREADS, 1) k_oz_rot(const __grid_constant__
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
+      // FP64 is slow on this part: scale the double-float pair in FP32 (exact power of two while
+      // in range), then one FP64 add per value (and one FMA for beta)
       const int r = t * kWin + 32 * lq + lane;
       if (r < p.rows) {
 #pragma unroll
         for (int e = 0; e < 12; ++e) {
           const int j = n0 + cq * ncw + e;
           if (e < ncw && j < p.n) {
-            double2 v = double2{ldexp((double)h[e] + (double)l[e], fcol[e] - 16) * p.alpha,
-                                ldexp((double)h[12 + e] + (double)l[12 + e], fcol[e] - 16) * p.alpha};
+            const int k = fcol[e] - 16;
+            double2 v;
+            if (k >= -60 && k <= 60) {   // the low parts stay normal unless far below 2^-53 of the sum
+              const float sc = pow2f(k);
+              v.x = (double)(h[e] * sc) + (double)(l[e] * sc);
+              v.y = (double)(h[12 + e] * sc) + (double)(l[12 + e] * sc);
+            } else {
+              v.x = ldexp((double)h[e] + (double)l[e], k);
+              v.y = ldexp((double)h[12 + e] + (double)l[12 + e], k);
+            }
+            if (p.alpha != 1.0) {
+              v.x *= p.alpha;
+              v.y *= p.alpha;
+            }
             double2* o = p.out + (size_t)j * p.ldo + r;
             if (p.beta != 0.0) {
               const double2 old = *o;
-              v.x += p.beta * old.x;
-              v.y += p.beta * old.y;
+              v.x = fma(p.beta, old.x, v.x);
+              v.y = fma(p.beta, old.y, v.y);
             }
             *o = v;
           }
@@ -751,13 +811,13 @@ bool g_attr = false;
 constexpr uint32_t g_a_lbo = OZ_A_LBO, g_a_sbo = OZ_A_SBO;
 
 // 5-D map over a slice buffer: (64 core elements, row groups, column groups, part, slice)
-int make_map5(CUtensorMap* map, const OzBlock& z, int box_rg, int box_cg) {
+int make_map5(CUtensorMap* map, const OzBlock& z, int box_rg, int box_cg, int box_s = kS) {
   PFN_cuTensorMapEncodeTiled_v12000 enc;
   DKS_TRY(tc::encoder(&enc));
   const cuuint64_t R = (cuuint64_t)(z.rowsp / 8), G = (cuuint64_t)(z.ncolp / 8);
   const cuuint64_t dims[5] = {64, R, G, 2, (cuuint64_t)kS};
   const cuuint64_t strides[4] = {kCore, R * kCore, G * R * kCore, 2 * G * R * kCore};
-  const cuuint32_t box[5] = {64, (cuuint32_t)box_rg, (cuuint32_t)box_cg, 2, (cuuint32_t)kS};
+  const cuuint32_t box[5] = {64, (cuuint32_t)box_rg, (cuuint32_t)box_cg, 2, (cuuint32_t)box_s};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, z.sl, dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -821,20 +881,12 @@ int oz_split(const double2* a, long long lda, int ncol, const OzBlock& z, cudaSt
   return DKS_OK;
 }
 
-// lower triangles of A = Z^H HZ and S = Z^H Z over the first m columns (ldc = m)
-int oz_gram(const OzBlock& z, const OzBlock& hz, int m, double2* a, double2* s, cudaStream_t st) {
-  using namespace oz;
-  if (m <= 0) return DKS_OK;
-  if (z.rowsp != hz.rowsp || z.ncolp != hz.ncolp || m > z.ncol)
-    return fail(DKS_ERR_INVALID_ARG, "exact-slice Gram: mismatched blocks");
+namespace oz {
+// A^H B over tiles: A (tz, 128-column boxes), B from hz (src 0) or z (src 1), partial tiles per
+// chunk of windows, then the fixed-order reduction in the given mode.
+int hn_tiles(const OzBlock& z, const OzBlock& hz, const std::vector<GTile>& tiles, int m, int n, double2* a,
+             double2* s, int ldc, int mode, cudaStream_t st) {
   DKS_TRY(set_attrs());
-  std::vector<GTile> tiles;
-  const int mt = (m + 127) / 128;
-  for (int ib = 0; ib < mt; ++ib) {
-    const int jmax = std::min(m, ib * 128 + 128);   // lower triangle: columns j <= i
-    for (int src = 0; src < 2; ++src)
-      for (int jb = 0; jb < jmax; jb += G_N) tiles.push_back(GTile{ib * 128, jb, src});
-  }
   const int nt = (int)tiles.size();
   const int nwin = z.rowsp / kWin;
   const int nsm = sm_count();
@@ -842,12 +894,12 @@ int oz_gram(const OzBlock& z, const OzBlock& hz, int m, double2* a, double2* s, 
   int splits = std::max(1, std::min(nwin, (2 * nsm + nt - 1) / nt));
   const int wpc = (nwin + splits - 1) / splits;
   splits = (nwin + wpc - 1) / wpc;
-  Prof pr(P_GRAM, st, 2.0 * 28.0 * z.rowsp * ((m + 7) / 8 * 8) + 32.0 * m * m, 8.0 * m * (m + 1.0) * (double)z.rows);
   CUtensorMap tz, th;
   DKS_TRY(make_map5(&tz, z, 2, 16));
-  DKS_TRY(make_map5(&th, hz, 2, 4));
-  CUtensorMap tzb;   // Z as the B operand: boxes of 4 column groups
-  DKS_TRY(make_map5(&tzb, z, 2, 4));
+  DKS_TRY(make_map5(&th, hz, 2, G_N / 8, 1));
+  CUtensorMap tzb;   // Z as the B operand: boxes of 6 column groups, one slice
+  DKS_TRY(make_map5(&tzb, z, 2, G_N / 8, 1));
+  if (nt > 65535) return fail(DKS_ERR_UNSUPPORTED, "exact-slice A^H B: too many tiles");
   const size_t tl_bytes = (tiles.size() * sizeof(GTile) + 255) / 256 * 256;
   const size_t part_bytes = (size_t)splits * nt * G_N * 128 * sizeof(double2);
   unsigned char* buf = nullptr;
@@ -861,6 +913,7 @@ int oz_gram(const OzBlock& z, const OzBlock& hz, int m, double2* a, double2* s, 
     p.wpc = wpc;
     p.ntiles = nt;
     p.ncolp = z.ncolp;
+    p.ncolpb = hz.ncolp;   // tiles of src 1 (B from Z) occur only in the Gram form, where both agree
     p.tile = dtiles;
     p.exz = z.ex;
     p.exh = hz.ex;
@@ -873,7 +926,9 @@ int oz_gram(const OzBlock& z, const OzBlock& hz, int m, double2* a, double2* s, 
     r.splits = splits;
     r.ntiles = nt;
     r.m = m;
-    r.ldc = m;
+    r.n = n;
+    r.ldc = ldc;
+    r.mode = mode;
     r.tile = dtiles;
     r.part = part;
     r.a = a;
@@ -882,18 +937,60 @@ int oz_gram(const OzBlock& z, const OzBlock& hz, int m, double2* a, double2* s, 
     e = cudaGetLastError();
   }
   cudaFreeAsync(buf, st);
-  if (e != cudaSuccess) return fail(DKS_ERR_CUDA, std::string("exact-slice Gram launch: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(DKS_ERR_CUDA, std::string("exact-slice A^H B launch: ") + cudaGetErrorString(e));
   return DKS_OK;
+}
+}  // namespace oz
+
+// lower triangles of A = Z^H HZ and S = Z^H Z over the first m columns (ldc = m)
+int oz_gram(const OzBlock& z, const OzBlock& hz, int m, double2* a, double2* s, cudaStream_t st) {
+  using namespace oz;
+  if (m <= 0) return DKS_OK;
+  if (z.rowsp != hz.rowsp || z.ncolp != hz.ncolp || m > z.ncol)
+    return fail(DKS_ERR_INVALID_ARG, "exact-slice Gram: mismatched blocks");
+  std::vector<GTile> tiles;
+  const int mt = (m + 127) / 128;
+  for (int ib = 0; ib < mt; ++ib) {
+    const int jmax = std::min(m, ib * 128 + 128);   // lower triangle: columns j <= i
+    for (int src = 0; src < 2; ++src)
+      for (int jb = 0; jb < jmax; jb += G_N) tiles.push_back(GTile{ib * 128, jb, src});
+  }
+  Prof pr(P_GRAM, st, 2.0 * 28.0 * z.rowsp * ((m + 7) / 8 * 8) + 32.0 * m * m, 8.0 * m * (m + 1.0) * (double)z.rows);
+  return hn_tiles(z, hz, tiles, m, m, a, s, m, 0, st);
+}
+
+// C = A^H B (m x n, ldc), or with conj_transpose_out C = B^H A (n x m, ldc)
+int oz_gemm_hn(const OzBlock& a, int m, const OzBlock& b, int n, double2* c, int ldc, bool conj_transpose_out,
+               cudaStream_t st, int cat) {
+  using namespace oz;
+  if (m <= 0 || n <= 0) return DKS_OK;
+  if (a.rowsp != b.rowsp || m > a.ncol || n > b.ncol)
+    return fail(DKS_ERR_INVALID_ARG, "exact-slice A^H B: mismatched blocks");
+  std::vector<GTile> tiles;
+  for (int ib = 0; ib < (m + 127) / 128; ++ib)
+    for (int jb = 0; jb < n; jb += G_N) tiles.push_back(GTile{ib * 128, jb, 0});
+  Prof pr(cat, st, 28.0 * a.rowsp * ((m + 7) / 8 * 8 + (n + 7) / 8 * 8) + 16.0 * m * n, 8.0 * m * n * (double)a.rows);
+  return hn_tiles(a, b, tiles, m, n, c, nullptr, ldc, conj_transpose_out ? 2 : 1, st);
 }
 
 // OUT (rows x n, ldo) = alpha Z[:, c0 : c0 + m] W (+ beta OUT), W: m x n complex128 (ldw)
 int oz_rotate(const OzBlock& z, int c0, int m, const double2* w, int ldw, int n, double2* out, int ldo, double beta,
-              cudaStream_t st, double alpha) {
+              cudaStream_t st, double alpha, const double* wscale, int cat) {
   using namespace oz;
   if (m <= 0 || n <= 0 || z.rows <= 0) return DKS_OK;
   if (c0 < 0 || c0 + m > z.ncol) return fail(DKS_ERR_INVALID_ARG, "exact-slice rotation: columns outside the block");
+  if (wscale) {
+    // W' = W diag-scaled by ws along its rows, then the plain rotation
+    double2* ws2 = nullptr;
+    DKS_CUDA_TRY(cudaMallocAsync((void**)&ws2, (size_t)m * n * sizeof(double2), st));
+    k_oz_scale_w<<<(m * n + 255) / 256, 256, 0, st>>>(w, ldw, wscale, m, n, ws2);
+    int rc = cudaGetLastError() == cudaSuccess ? DKS_OK : fail(DKS_ERR_CUDA, "exact-slice rotation: scaling launch");
+    if (!rc) rc = oz_rotate(z, c0, m, ws2, m, n, out, ldo, beta, st, alpha, nullptr, cat);
+    cudaFreeAsync(ws2, st);
+    return rc;
+  }
   DKS_TRY(set_attrs());
-  Prof pr(P_ROTATE, st, 28.0 * z.rowsp * ((m + 7) / 8 * 8) + (beta != 0.0 ? 2.0 : 1.0) * 16.0 * n * z.rows,
+  Prof pr(cat, st, 28.0 * z.rowsp * ((m + 7) / 8 * 8) + (beta != 0.0 ? 2.0 : 1.0) * 16.0 * n * z.rows,
           8.0 * (double)z.rows * m * n);
   const int ytiles = (n + R_NTMAX - 1) / R_NTMAX;
   const int nt = (((n + ytiles - 1) / ytiles) + 15) / 16 * 16;
@@ -931,6 +1028,38 @@ int oz_rotate(const OzBlock& z, int c0, int m, const double2* w, int ldw, int n,
     DKS_CUDA_TRY(cudaGetLastError());
   }
   return DKS_OK;
+}
+
+bool projector_slices(dks_ctx* ctx, int ik, cudaStream_t st) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> g(mu);
+  KPoint& kp = ctx->k[ik];
+  if (kp.btoz_state) return kp.btoz_state > 0;
+  kp.btoz_state = -1;
+  if (!ctx->nproj || !kp.bt64) return false;
+  // the slices are a speed-up (the double-float contractions remain): held only with room to spare
+  const size_t bytes = oz_bytes(2 * kp.npw, ctx->nproj);
+  size_t freeb = 0, totalb = 0;
+  if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess || bytes > freeb / 4) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaMalloc(&kp.btoz, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    kp.btoz = nullptr;
+    return false;
+  }
+  OzBlock b;
+  oz_layout(kp.btoz, 2 * kp.npw, ctx->nproj, &b);
+  // made once on this stream, then read from any stream of the context
+  if (oz_split(kp.bt64, 2 * kp.npw, ctx->nproj, b, st) != DKS_OK || cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(kp.btoz);
+    kp.btoz = nullptr;
+    return false;
+  }
+  kp.btoz_state = 1;
+  return true;
 }
 
 int oz_status_take() {
