@@ -180,6 +180,30 @@ __device__ __forceinline__ void df_add2(float& h, float& l, float h2, float l2) 
   l = e - (h - s);
 }
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }   // -126 <= k <= 127
+// (h + l) 2^k as a double, from a normalised double-float pair (|l| <= ulp(h) / 2), with integer
+// operations only (FP64 instructions, conversions included, are slow on this part): the
+// significands are aligned in a 64-bit integer; exact up to a truncation below 2^-52 of h.
+// The caller keeps the result's exponent in range (|k| <= 60 and h a normal FP32 number).
+__device__ __forceinline__ double df_to_double(float h, float l, int k) {
+  const uint32_t hb = __float_as_uint(h), lb = __float_as_uint(l);
+  const int eh = (int)((hb >> 23) & 255u);
+  if (eh == 0) return 0.0;
+  long long m = (long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;   // implicit bit at position 52
+  const int el = (int)((lb >> 23) & 255u);
+  if (el) {
+    const int d = eh - el;                                          // >= 24 for a normalised pair
+    if (d < 53) {
+      const long long ml = ((long long)((lb & 0x7FFFFFu) | 0x800000u) << 29) >> d;
+      m += ((hb ^ lb) >> 31) ? -ml : ml;
+    }
+  }
+  long long e = (long long)(eh - 127 + 1023 + k);
+  if (m < (1LL << 52)) {   // a borrow took the leading bit
+    m <<= 1;
+    --e;
+  }
+  return __longlong_as_double(((long long)(hb >> 31) << 63) | (e << 52) | (m & ((1LL << 52) - 1)));
+}
 
 // ================================================================ Gram: A = Z^H HZ, S = Z^H Z
 // A tile is 128 columns of Z (MMA M) against 48 columns of HZ (A) or of Z (S), over a chunk of
@@ -449,14 +473,15 @@ __global__ void __launch_bounds__(256) k_oz_gram_reduce(GRedArgs p) {
   }
 }
 
-// W'[j][c] = w[j ldw + c] ws[c] (projector update: the channel weights D)
-__global__ void k_oz_scale_w(const double2* __restrict__ w, int ldw, const double* __restrict__ ws, int m, int n,
-                             double2* __restrict__ out) {
+// W'[j][c] = alpha ws[c] w[j ldw + c] (projector update: the channel weights D and the filter scale)
+__global__ void k_oz_scale_w(const double2* __restrict__ w, int ldw, const double* __restrict__ ws, double alpha,
+                             int m, int n, double2* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m * n) return;
   const int c = i % m, j = i / m;
   const double2 v = w[(size_t)j * ldw + c];
-  out[i] = double2{v.x * ws[c], v.y * ws[c]};
+  const double f = ws ? alpha * ws[c] : alpha;
+  out[i] = double2{v.x * f, v.y * f};
 }
 
 // ================================================================ rotation: OUT = alpha Z W (+ beta OUT)
@@ -498,7 +523,7 @@ struct RotArgs {
   const double2* w;
   const int* ex;         // [window][ncolp]
   double2* out;
-  double alpha, beta;
+  double beta;
 };
 
 __global__ void __launch_bounds__(R_THREADS, 1) k_oz_rot(const __grid_constant__ CUtensorMap tz, RotArgs p) {
@@ -764,17 +789,12 @@ __global__ void __launch_bounds__(R_THREADS, 1) k_oz_rot(const __grid_constant__
           if (e < ncw && j < p.n) {
             const int k = fcol[e] - 16;
             double2 v;
-            if (k >= -60 && k <= 60) {   // the low parts stay normal unless far below 2^-53 of the sum
-              const float sc = pow2f(k);
-              v.x = (double)(h[e] * sc) + (double)(l[e] * sc);
-              v.y = (double)(h[12 + e] * sc) + (double)(l[12 + e] * sc);
+            if (k >= -60 && k <= 60) {
+              v.x = df_to_double(h[e], l[e], k);
+              v.y = df_to_double(h[12 + e], l[12 + e], k);
             } else {
               v.x = ldexp((double)h[e] + (double)l[e], k);
               v.y = ldexp((double)h[12 + e] + (double)l[12 + e], k);
-            }
-            if (p.alpha != 1.0) {
-              v.x *= p.alpha;
-              v.y *= p.alpha;
             }
             double2* o = p.out + (size_t)j * p.ldo + r;
             if (p.beta != 0.0) {
@@ -979,13 +999,13 @@ int oz_rotate(const OzBlock& z, int c0, int m, const double2* w, int ldw, int n,
   using namespace oz;
   if (m <= 0 || n <= 0 || z.rows <= 0) return DKS_OK;
   if (c0 < 0 || c0 + m > z.ncol) return fail(DKS_ERR_INVALID_ARG, "exact-slice rotation: columns outside the block");
-  if (wscale) {
-    // W' = W diag-scaled by ws along its rows, then the plain rotation
+  if (wscale || alpha != 1.0) {
+    // W' = alpha diag(ws) W (a small FP64 pass), then the plain rotation
     double2* ws2 = nullptr;
     DKS_CUDA_TRY(cudaMallocAsync((void**)&ws2, (size_t)m * n * sizeof(double2), st));
-    k_oz_scale_w<<<(m * n + 255) / 256, 256, 0, st>>>(w, ldw, wscale, m, n, ws2);
+    k_oz_scale_w<<<(m * n + 255) / 256, 256, 0, st>>>(w, ldw, wscale, alpha, m, n, ws2);
     int rc = cudaGetLastError() == cudaSuccess ? DKS_OK : fail(DKS_ERR_CUDA, "exact-slice rotation: scaling launch");
-    if (!rc) rc = oz_rotate(z, c0, m, ws2, m, n, out, ldo, beta, st, alpha, nullptr, cat);
+    if (!rc) rc = oz_rotate(z, c0, m, ws2, m, n, out, ldo, beta, st, 1.0, nullptr, cat);
     cudaFreeAsync(ws2, st);
     return rc;
   }
@@ -1021,7 +1041,6 @@ int oz_rotate(const OzBlock& z, int c0, int m, const double2* w, int ldw, int n,
     p.w = w + cs;
     p.ex = z.ex;
     p.out = out;
-    p.alpha = alpha;
     p.beta = cs == 0 ? beta : 1.0;
     if (p.kch * R_KC > R_CMAX) return fail(DKS_ERR_UNSUPPORTED, "exact-slice rotation: chunk bound");
     k_oz_rot<<<dim3(grid_x, ytiles), R_THREADS, R_SMEM, st>>>(tz, p);
