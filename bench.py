@@ -234,13 +234,14 @@ def run_reference(args):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per kernel launch from ncu captures of
 # the current kernels at the dimer's sizes, one kernel and one launch per capture, e.g.
-#   ncu --set full --clock-control none -k regex:k_gram_df -c 1 -o prof python bench.py --kernel-case gramdf
+#   ncu --set full --clock-control none -k regex:k_oz_gram -c 1 -o prof python bench.py --kernel-case gramdf
 NCU_TRAFFIC = {
     "rayleigh_ritz": {"bytes_per_launch": (526.3e3 + 2 * 469.2e3 + 425.5e3 + 539.9e3) / 5,
                       "note": "kernel case rr (m = 120, n = 40): mean over the five kernels of a step, "
                               "each captured cold (the pencil is 537 KB)"},
-    "gram": {"bytes_per_launch": 922.6e6 + 4.5e6,
-             "note": "kernel case gramdf (k_gram_df, 120 columns of 229,676 rows)"},
+    "gram": {"bytes_per_launch": 1561.8e6 + 20.7e6,
+             "note": "kernel case gramdf (k_oz_gram, exact integer slices of 120 columns of 229,676 rows: "
+                     "one DRAM pass over the Z and HZ slices)"},
     "gram_fp32": {"bytes_per_launch": 223.3e6 + 3.3e6,
                   "note": "kernel case gram32 (k_gram_f32, 120 columns of 229,676 rows)"},
 }
