@@ -76,11 +76,10 @@ __global__ void __launch_bounds__(256) k_stick_inverse(
 // pass B: one plane of one field: 2D inverse FFT, x V/Ng, 2D forward FFT
 // ---------------------------------------------------------------------------
 template <typename Vg, typename V>
-__global__ void __launch_bounds__(512) k_plane(Vg* __restrict__ t, int nsticks,
-                                               const int* __restrict__ stick_plane, AxisPlan p1,
-                                               AxisPlan p2, int ld, int n3, const V* __restrict__ tw1,
-                                               const V* __restrict__ tw2,
-                                               const typename RealOf<V>::T* __restrict__ vperm) {
+__device__ __forceinline__ void plane_body(Vg* __restrict__ t, int nsticks, const int* __restrict__ stick_plane,
+                                           const AxisPlan& p1, const AxisPlan& p2, int ld, int n3,
+                                           const V* __restrict__ tw1, const V* __restrict__ tw2,
+                                           const typename RealOf<V>::T* __restrict__ vperm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* plane = reinterpret_cast<V*>(smem_raw);   // n1 rows of stride ld (odd), position i1*ld + i2
   const int n1 = p1.n, n2 = p2.n, np = n1 * ld;
@@ -102,6 +101,25 @@ __global__ void __launch_bounds__(512) k_plane(Vg* __restrict__ t, int nsticks,
   for (int s = threadIdx.x; s < nsticks; s += blockDim.x)
     if (dks_ok(stick_plane[s] >= 0 && stick_plane[s] < np, kChkPlane | (s & 0xffffff)))
       row[s] = to_g(plane[stick_plane[s]]);
+}
+template <typename Vg, typename V>
+__global__ void __launch_bounds__(512) k_plane(Vg* __restrict__ t, int nsticks,
+                                               const int* __restrict__ stick_plane, AxisPlan p1,
+                                               AxisPlan p2, int ld, int n3, const V* __restrict__ tw1,
+                                               const V* __restrict__ tw2,
+                                               const typename RealOf<V>::T* __restrict__ vperm) {
+  plane_body<Vg, V>(t, nsticks, stick_plane, p1, p2, ld, n3, tw1, tw2, vperm);
+}
+// the same for 128-thread CTAs of complex64 planes, compiled for ten resident CTAs per SM: the
+// plane passes are latency-bound, and the register budget of the general form (one CTA of up
+// to 512 threads) leaves eight
+template <typename Vg, typename V>
+__global__ void __launch_bounds__(128, 10) k_plane128(Vg* __restrict__ t, int nsticks,
+                                                      const int* __restrict__ stick_plane, AxisPlan p1,
+                                                      AxisPlan p2, int ld, int n3, const V* __restrict__ tw1,
+                                                      const V* __restrict__ tw2,
+                                                      const typename RealOf<V>::T* __restrict__ vperm) {
+  plane_body<Vg, V>(t, nsticks, stick_plane, p1, p2, ld, n3, tw1, tw2, vperm);
 }
 
 // ---------------------------------------------------------------------------
@@ -587,6 +605,7 @@ static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int n
     DKS_TRY(set_smem<Vs>((const void*)k_plane_rows_fwd<Vg, Vs>, sm_r));
   } else {
     DKS_TRY(set_smem<Vs>((const void*)k_plane<Vg, Vs>, sm_b));
+    if constexpr (std::is_same<Vs, float2>::value) DKS_TRY(set_smem<Vs>((const void*)k_plane128<Vg, Vs>, sm_b));
   }
   DKS_TRY(set_smem<Vs>(nc == 4 ? (const void*)k_stick_forward<Vg, Vs> : (const void*)k_stick_forward_ks<Vg, Vs>,
                        sm_c));
@@ -618,8 +637,17 @@ static int fft_local(dks_ctx* ctx, const KPoint& kp, const Vg* x, Vg* out, int n
                                                         n3, tw2, rpb);
       } else {
         dim3 gb(n3, nc * nbc);
-        k_plane<Vg, Vs><<<gb, tb_plane, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0], ctx->plan[1],
-                                                    ld, n3, tw1, tw2, vp);
+        bool launched = false;
+        if constexpr (std::is_same<Vs, float2>::value) {
+          if (tb_plane == 128) {
+            k_plane128<Vg, Vs><<<gb, 128, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0],
+                                                      ctx->plan[1], ld, n3, tw1, tw2, vp);
+            launched = true;
+          }
+        }
+        if (!launched)
+          k_plane<Vg, Vs><<<gb, tb_plane, sm_b, st>>>(tbuf, kp.nsticks, kp.stick_plane, ctx->plan[0],
+                                                      ctx->plan[1], ld, n3, tw1, tw2, vp);
       }
     }
     {
