@@ -627,13 +627,14 @@ def supercell_hx_section(P, W, stream, hbm, nb=160):
     return out
 
 
-def supercell_section(P, W, mode, stream, kpoints=4, block=128, nbuf=32, tol=1e-6, nev=None):
+def supercell_section(P, W, mode, stream, kpoints=4, block=128, nbuf=32, tol=1e-6, nev=None, fp64=False):
     """The large-cell configuration (2 x 2 x 1 supercell of the layered crystal: 120 x 120 x 216
     grid, about 158,000 planewaves per k, 1080 projector channels, 480 pairs per k-point), solved
     in band blocks of `block` wanted + nbuf buffer columns with deflation, k-point by k-point
     (the first `kpoints` of the 2 x 2 x 1 mesh), each k-point's result printed to stderr as soon
     as it is known.  Opt-in (--supercell): it holds most of the GPU's memory and runs for minutes
-    per k-point."""
+    per k-point.  fp64: each k-point is solved again from the same start block in the plain FP64
+    form, for the speedup and the eigenvalue difference."""
     import dataclasses
 
     import torch
@@ -661,6 +662,19 @@ def supercell_section(P, W, mode, stream, kpoints=4, block=128, nbuf=32, tol=1e-
                "residual_history": [float(f"{v:.3g}") for v in rep["history"]]}
         if rc == 0:
             row["kramers_max_split"] = float(abs(lam[0][0::2] - lam[0][1::2]).max()) if ik == 0 else None
+        if fp64 and mode != P.MODE_FP64:
+            x.copy_(torch.from_numpy(W.start_block(ctx.npw(0), nv + nbuf, wl.seed, ik)))
+            torch.cuda.synchronize()
+            e0.record(stream)
+            lam64, rep64, rc64 = ctx.solve([x], nv, nbuf=nbuf, tol=tol, mode=P.MODE_FP64,
+                                           block=block if nv > block else 0, check=False, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = e0.elapsed_time(e1)
+            row.update({"fp64_form_status": int(rc64), "fp64_form_ms": ms64,
+                        "fp64_form_iterations": rep64["iterations"][0],
+                        "speedup_mixed_vs_fp64": ms64 / ms,
+                        "max_eig_diff_vs_fp64": float(abs(lam64[0] - lam[0]).max()) if rc == 0 and rc64 == 0 else None})
         out["kpoints"].append(row)
         print(json.dumps({"supercell_kpoint": row}), file=sys.stderr, flush=True)
         ctx.close()
@@ -736,6 +750,9 @@ def main():
     ap.add_argument("--no-supercell-hx", action="store_true", help="skip H' bandwidth at the supercell size")
     ap.add_argument("--supercell-kpoints", type=int, default=4, help="k-points of the supercell solve (1-4)")
     ap.add_argument("--supercell-nev", type=int, default=None, help="pairs per k-point of the supercell solve (480)")
+    ap.add_argument("--supercell-nbuf", type=int, default=32, help="buffer columns of the supercell solves")
+    ap.add_argument("--supercell-fp64", action="store_true",
+                    help="also solve each supercell k-point in the plain FP64 form (speedup)")
     ap.add_argument("--supercell", action="store_true",
                     help="also solve the large-cell configuration in band blocks (minutes, most of the GPU memory)")
     ap.add_argument("--ref-iterations", type=int, default=60)
@@ -937,7 +954,8 @@ def main():
     ksso = None if args.no_ksso else ksso_section(P, W, wl, ctx, x0, lam, ms, mode, stream)
     dav = None if args.no_davidson else davidson_section(P, ctx, x0, lam, ms, mode, stream)
     scf = None if args.no_scf else scf_section(P, W, wl, ctx, mode, stream)
-    sup = (supercell_section(P, W, mode, stream, kpoints=args.supercell_kpoints, nev=args.supercell_nev)
+    sup = (supercell_section(P, W, mode, stream, kpoints=args.supercell_kpoints, nev=args.supercell_nev,
+                             nbuf=args.supercell_nbuf, fp64=args.supercell_fp64)
            if args.supercell else None)
     if args.no_layered:
         lay = None
