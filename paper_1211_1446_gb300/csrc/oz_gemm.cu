@@ -107,6 +107,12 @@ __device__ __forceinline__ void digits7(long long f, uint16_t (&out)[kS]) {
     out[s] = (uint16_t)(__float_as_uint(x) >> 16);                       // exact in BF16
   }
 }
+// A NaN or an infinity of a sliced block becomes seven BF16 NaN digits, so that every
+// tensor-core product that uses it is NaN (as in IEEE arithmetic) and a non-finite block still
+// fails the solver's finiteness checks.  (W of a rotation is sliced without that check: in the
+// solver it comes from the Rayleigh-Ritz step, whose non-finite results show in its eigenvalues.)
+__device__ __forceinline__ bool non_finite(unsigned long long bits) { return ((bits >> 52) & 0x7FF) == 0x7FF; }
+
 // biased exponent field of the larger of |re|, |im| (0 for zero and subnormal values)
 __device__ __forceinline__ int exp_field(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
@@ -147,7 +153,12 @@ __global__ void __launch_bounds__(256) k_oz_split(const double2* __restrict__ z,
   for (int p = 0; p < 2; ++p) {
     uint16_t dg[4][kS];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) digits7(fixed56(bits[2 * i + p], E), dg[i]);
+    for (int i = 0; i < 4; ++i) {
+      const bool nf = non_finite(bits[2 * i + p]);
+      digits7(nf ? 0LL : fixed56(bits[2 * i + p], E), dg[i]);
+#pragma unroll
+      for (int s = 0; s < kS; ++s) dg[i][s] = nf ? (uint16_t)0x7FC0 : dg[i][s];
+    }
 #pragma unroll
     for (int s = 0; s < kS; ++s) {
       const uint2 v = make_uint2((uint32_t)dg[0][s] | ((uint32_t)dg[1][s] << 16),
@@ -188,6 +199,7 @@ __device__ __forceinline__ double df_to_double(float h, float l, int k) {
   const uint32_t hb = __float_as_uint(h), lb = __float_as_uint(l);
   const int eh = (int)((hb >> 23) & 255u);
   if (eh == 0) return 0.0;
+  if (eh == 255) return __longlong_as_double(0x7FF8000000000000LL);   // NaN or infinity
   long long m = (long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;   // implicit bit at position 52
   const int el = (int)((lb >> 23) & 255u);
   if (el) {

@@ -188,3 +188,41 @@ def test_dimer_full_size_refinement_on_slices(slices):
           f"{rep['seconds'] * 1e3:.0f} ms max err {np.abs(lam[0] - ref).max():.2e}")
     assert rc == 0, rep["message"]
     assert np.abs(lam[0] - ref).max() < 1e-8
+
+
+def test_non_finite_inputs_come_out_nan(slices):
+    """A NaN or an infinity in a block gives NaN wherever it enters a product (its slices are
+    BF16 NaNs, which the tensor cores propagate), so that the solver's finiteness checks still
+    see it: Gram entries of the poisoned columns are NaN and the others exact-slice accurate; in
+    a rotation the output row of a non-finite Z entry is NaN and every other output is finite."""
+    import torch
+    P = slices
+    rng = np.random.default_rng(9)
+    rows, nz, n = 1000, 12, 5
+    z = rng.standard_normal((nz, rows)) + 1j * rng.standard_normal((nz, rows))
+    hz = rng.standard_normal((nz, rows)) + 1j * rng.standard_normal((nz, rows))
+    zb = z.copy()
+    zb[3, 700] = np.nan
+    zb[5, 10] = np.inf
+    a = torch.empty((nz, nz), dtype=torch.complex128, device="cuda")
+    s = torch.empty_like(a)
+    P.gram_hermitian(to_dev(zb, torch.complex128), to_dev(hz, torch.complex128), a, s, emulated=True)
+    torch.cuda.synchronize()
+    ga, gs = a.cpu().numpy().T, s.cpu().numpy().T
+    lo = np.tril(np.ones((nz, nz), dtype=bool))
+    poisoned = np.isin(np.arange(nz), [3, 5])
+    bad = poisoned[:, None] | poisoned[None, :]
+    assert np.all(np.isnan(gs[lo & bad])) and np.all(np.isfinite(gs[lo & ~bad]))
+    assert np.all(np.isnan(ga[lo & poisoned[:, None]])) and np.all(np.isfinite(ga[lo & ~poisoned[:, None]]))
+    want_s = z.conj() @ z.T
+    scale = np.abs(z) @ np.abs(z).T
+    assert _scaled(gs[lo & ~bad], want_s[lo & ~bad], scale[lo & ~bad]) < 1e-13
+    # rotation: NaN in Z row 700 of column 3
+    w = rng.standard_normal((n, nz)) + 1j * rng.standard_normal((n, nz))   # columns of W
+    zr = z.copy()
+    zr[3, 700] = np.nan
+    out = torch.zeros((n, rows), dtype=torch.complex128, device="cuda")
+    P.rotate(to_dev(zr, torch.complex128), to_dev(w, torch.complex128), n, out, emulated=True)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    assert np.all(np.isnan(o[:, 700])) and np.all(np.isfinite(np.delete(o, 700, axis=1)))
