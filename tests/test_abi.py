@@ -203,3 +203,25 @@ def test_rayleigh_ritz_binding_rejects_short_info_and_bad_shapes():
             fn(a, a, n, v[:2], lam, torch.zeros(3, dtype=torch.int32))
         with pytest.raises(ValueError, match="device of A"):
             fn(a, a, n, v, lam, torch.zeros(3, dtype=torch.int32))
+
+
+def test_tensor_core_mask_without_gpu():
+    """The TC_* bits match include/dks.h, the default mask holds the projector contractions and
+    the refinement phase's exact slices, DKS_TC_ALL is accepted and a bit above it rejected."""
+    import paper_1211_1446_gb300 as P
+    src = open(os.path.join(ROOT, "include", "dks.h")).read()
+    bits = {k: int(v) for k, v in re.findall(r"#define DKS_TC_(\w+)\s+(\d+)", src)}
+    assert bits["ROTATE"] == P.TC_ROTATE and bits["GRAM"] == P.TC_GRAM
+    assert bits["PROJ_HN"] == P.TC_PROJ_HN and bits["PROJ_NN"] == P.TC_PROJ_NN
+    assert bits["FP64"] == P.TC_FP64 and bits["ALL"] == P.TC_ALL
+    assert P.TC_ALL == P.TC_ROTATE | P.TC_GRAM | P.TC_PROJ_HN | P.TC_PROJ_NN | P.TC_FP64
+    old = P.tensor_cores()
+    try:
+        P.tensor_cores(P.TC_ALL)
+        assert P.tensor_cores()[0] == P.TC_ALL
+        with pytest.raises(Exception):
+            P.tensor_cores(P.TC_ALL + 1)
+        assert P.tensor_cores()[0] == P.TC_ALL
+    finally:
+        P.tensor_cores(old[0])
+    assert P.tensor_cores()[0] == old[0]
