@@ -352,15 +352,17 @@ int gemm_hn(const Va* a, int lda, const Vb* b, int ldb, int k, int m, int n, dou
   if (lower && m != n) return fail(DKS_ERR_INVALID_ARG, "gemm_hn: lower-triangle mode needs a square result");
   if constexpr (std::is_same<Va, float2>::value && std::is_same<Vb, float2>::value && !Acc64) {
     // tensor cores: the result is written, which equals the accumulation into the zeroed c the
-    // callers provide.  Projector coefficients are formed as (x~^H B)^H so that the wider block
-    // x~ runs along the 128-row MMA dimension.
+    // callers provide.  Projector coefficients: a side of at most 64 columns goes along the MMA's
+    // 128 rows in the packed form (A and i A together); otherwise the wider block runs along
+    // them, forming (x~^H B)^H when x~ is the wider one.
     const int bit = cat == P_PROJ_HN ? TC_PROJ_HN : TC_GRAM;
     const bool use = tc < 0 ? tc_enabled(bit) : (tc == 1 && tc_device());
     if (!lower && use && tc_hn_supported(a, lda, b, ldb, k)) {
       Prof pr(cat + kProf32, st, ((double)m * sizeof(Va) + (double)n * sizeof(Vb)) * k + 16.0 * m * n,
               8.0 * m * n * (double)k);
       pr.count(1);
-      if (cat == P_PROJ_HN && n > m) return tc_gemm_hn(b, ldb, a, lda, k, n, m, c, ldc, true, st, num_sms());
+      if (cat == P_PROJ_HN && m > 64 && (n <= 64 || n > m))
+        return tc_gemm_hn(b, ldb, a, lda, k, n, m, c, ldc, true, st, num_sms());
       return tc_gemm_hn(a, lda, b, ldb, k, m, n, c, ldc, false, st, num_sms());
     }
   }

@@ -404,17 +404,12 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_oz_gram(const __grid_constant_
       const uint32_t base = tmem + ((uint32_t)(32 * lq) << 16) + 12u * (uint32_t)cq;
 #pragma unroll
       for (int reg = 0; reg < kRegs; ++reg) {
+        float re[12], im[12];
+        tmem_ld12x2(base + G_REG * (uint32_t)reg, base + G_REG * (uint32_t)reg + G_N, re, im);
 #pragma unroll
-        for (int c4 = 0; c4 < 3; ++c4) {
-          float re[4], im[4];
-          tmem_ld4(base + G_REG * (uint32_t)reg + 4u * c4, re);
-          tmem_ld4(base + G_REG * (uint32_t)reg + G_N + 4u * c4, im);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int k = 4 * c4 + e;
-            df_add2(ah[k], al[k], re[e] * sc[k], 0.f);
-            df_add2(ah[12 + k], al[12 + k], im[e] * sc[k], 0.f);
-          }
+        for (int k = 0; k < 12; ++k) {
+          df_add2(ah[k], al[k], re[k] * sc[k], 0.f);
+          df_add2(ah[12 + k], al[12 + k], im[k] * sc[k], 0.f);
         }
       }
       tc_fence_before();
@@ -767,24 +762,19 @@ __global__ void __launch_bounds__(R_THREADS, 1) k_oz_rot(const __grid_constant__
       const uint32_t base = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(cq * ncw);
 #pragma unroll
       for (int reg = 0; reg < kRegs; ++reg) {
+        // 12 columns from the warp's first: those past its ncw belong to the next warp's columns
+        // of the same accumulators (read, not used)
+        float re[12], im[12];
+        tmem_ld12x2(base + (uint32_t)(2 * nt * reg), base + (uint32_t)(2 * nt * reg + nt), re, im);
 #pragma unroll
-        for (int c4 = 0; c4 < 3; ++c4) {
-          if (4 * c4 < ncw) {
-            float re[4], im[4];
-            tmem_ld4(base + (uint32_t)(2 * nt * reg + 4 * c4), re);
-            tmem_ld4(base + (uint32_t)(2 * nt * reg + nt + 4 * c4), im);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int k = 4 * c4 + e;
-              if (reg == 0) {
-                h[k] = re[e];
-                h[12 + k] = im[e];
-                l[k] = l[12 + k] = 0.f;
-              } else {
-                df_add1(h[k], l[k], re[e]);
-                df_add1(h[12 + k], l[12 + k], im[e]);
-              }
-            }
+        for (int k = 0; k < 12; ++k) {
+          if (reg == 0) {
+            h[k] = re[k];
+            h[12 + k] = im[k];
+            l[k] = l[12 + k] = 0.f;
+          } else {
+            df_add1(h[k], l[k], re[k]);
+            df_add1(h[12 + k], l[12 + k], im[k]);
           }
         }
       }
