@@ -228,15 +228,17 @@ __global__ void __launch_bounds__(256) k_gemm_hn_f32p(const float2* __restrict__
 }
 
 // Both Gram matrices of Algorithm 1 from FP32 blocks in one pass: S = Z^H Z and A = Z^H HZ, block
-// lower triangles of 32 x 32 tiles.  The Z tile of the row block serves both products and each
-// thread reuses its two Z row values for four outputs of S and four of A; FP32 within a
-// 32-deep k-tile, folded into double-float totals.
+// lower triangles of 32 x 32 tiles.  The Z tile of the row block serves both products; each of
+// the 128 threads holds 4 x 2 outputs of S and of A, so per k step its 8 shared-memory loads
+// (four Z row values, two Z and two HZ column values) feed 16 complex multiply-adds; FP32 within
+// a 32-deep k-tile, folded into double-float totals.
 // two shared-memory stages of (Z rows of the tile's row block, Z and HZ rows of its column block):
 // the next 32-deep k-tile is copied with cp.async while the current one is multiplied
 constexpr int GF_TILE = HN_T * (HN_T + 1);   // one padded 32 x 33 tile, float2
 constexpr size_t GF_SMEM = 2 * 3 * (size_t)GF_TILE * sizeof(float2);
+constexpr int GF_THREADS = 128;
 
-__global__ void __launch_bounds__(256) k_gram_f32(const float2* __restrict__ z, const float2* __restrict__ hz,
+__global__ void __launch_bounds__(GF_THREADS, 4) k_gram_f32(const float2* __restrict__ z, const float2* __restrict__ hz,
                                                   int ld, int k, int m, int kchunk, double2* __restrict__ a,
                                                   double2* __restrict__ s) {
   extern __shared__ __align__(16) unsigned char gf_smem[];
@@ -249,18 +251,18 @@ __global__ void __launch_bounds__(256) k_gram_f32(const float2* __restrict__ z, 
   const int m0 = tm * HN_T, n0 = tn * HN_T;
   const int kb = blockIdx.y * kchunk;
   const int ke = min(k, kb + kchunk);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float2 as_[2][2], aa[2][2];
-  dfl ts[2][2][2] = {}, ta[2][2][2] = {};
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // rows ty + 8 i, columns tx + 16 j
+  float2 as_[4][2], aa[4][2];
+  dfl ts[4][2][2] = {}, ta[4][2][2] = {};
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) as_[i][j] = aa[i][j] = float2{0.f, 0.f};
   auto load = [&](int buf, int k0) {
     float2* zs = stage + (size_t)buf * 3 * GF_TILE;
     float2* zb = zs + GF_TILE;
     float2* hb = zb + GF_TILE;
-    for (int e = threadIdx.x; e < HN_T * HN_T; e += 256) {
+    for (int e = threadIdx.x; e < HN_T * HN_T; e += GF_THREADS) {
       const int kq = e & (HN_T - 1), q = e >> 5;
       const int gk = k0 + kq;
       const int o = kq * (HN_T + 1) + q;
@@ -295,20 +297,20 @@ __global__ void __launch_bounds__(256) k_gram_f32(const float2* __restrict__ z, 
       const float2* zr = zs + kq * (HN_T + 1);
       const float2* br = zb + kq * (HN_T + 1);
       const float2* hr = hb + kq * (HN_T + 1);
-      const float2 a0 = zr[ty], a1 = zr[ty + 16];
-      const float2 b0 = br[tx], b1 = br[tx + 16];
-      const float2 h0 = hr[tx], h1 = hr[tx + 16];
-      as_[0][0] = cfmac(a0, b0, as_[0][0]);
-      as_[0][1] = cfmac(a0, b1, as_[0][1]);
-      as_[1][0] = cfmac(a1, b0, as_[1][0]);
-      as_[1][1] = cfmac(a1, b1, as_[1][1]);
-      aa[0][0] = cfmac(a0, h0, aa[0][0]);
-      aa[0][1] = cfmac(a0, h1, aa[0][1]);
-      aa[1][0] = cfmac(a1, h0, aa[1][0]);
-      aa[1][1] = cfmac(a1, h1, aa[1][1]);
+      const float2 b[2] = {br[tx], br[tx + 16]};
+      const float2 h[2] = {hr[tx], hr[tx + 16]};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float2 ai = zr[ty + 8 * i];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          as_[i][j] = cfmac(ai, b[j], as_[i][j]);
+          aa[i][j] = cfmac(ai, h[j], aa[i][j]);
+        }
+      }
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         ts[i][j][0] = df_add_f(ts[i][j][0], as_[i][j].x);
@@ -320,10 +322,10 @@ __global__ void __launch_bounds__(256) k_gram_f32(const float2* __restrict__ z, 
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      const int mm = m0 + ty + 16 * i, nn = n0 + tx + 16 * j;
+      const int mm = m0 + ty + 8 * i, nn = n0 + tx + 16 * j;
       if (mm < m && nn < m) {
         atomicAdd(&s[(size_t)nn * m + mm].x, df_val(ts[i][j][0]));
         atomicAdd(&s[(size_t)nn * m + mm].y, df_val(ts[i][j][1]));
@@ -423,7 +425,7 @@ int gram_f32(const float2* z, const float2* hz, int ld, int k, int m, double2* a
                                       (int)GF_SMEM));
     attr = true;
   }
-  k_gram_f32<<<dim3(tiles, splits), 256, GF_SMEM, st>>>(z, hz, ld, k, m, kchunk, a, s);
+  k_gram_f32<<<dim3(tiles, splits), GF_THREADS, GF_SMEM, st>>>(z, hz, ld, k, m, kchunk, a, s);
   DKS_CUDA_TRY(cudaGetLastError());
   return DKS_OK;
 }
