@@ -242,8 +242,6 @@ NCU_TRAFFIC = {
     "gram": {"bytes_per_launch": 1561.8e6 + 20.7e6,
              "note": "kernel case gramdf (k_oz_gram, exact integer slices of 120 columns of 229,676 rows: "
                      "one DRAM pass over the Z and HZ slices)"},
-    "gram_fp32": {"bytes_per_launch": 223.3e6 + 3.3e6,
-                  "note": "kernel case gram32 (k_gram_f32, 120 columns of 229,676 rows)"},
 }
 
 
