@@ -20,9 +20,10 @@
 //       entry in FP64 in a fixed order (deterministic).
 //
 // Data movement: A (and, for hn, B) tiles are copied global -> shared memory by TMA
-// (cp.async.bulk.tensor.2d onto an mbarrier with expect-tx) through a 4-deep staging ring; all
-// 256 threads convert a staged tile into the three BF16 slices in the canonical no-swizzle
-// K-major layout (8-row x 16-byte core matrices); one thread issues the tcgen05.mma
+// (cp.async.bulk.tensor.2d onto an mbarrier with expect-tx) through a staging ring as deep as
+// shared memory allows (up to 8 stages); eight converter warps turn a staged tile into the three
+// BF16 slices in the canonical no-swizzle K-major layout (8-row x 16-byte core matrices); one
+// thread issues the tcgen05.mma
 // instructions (kind::f16, BF16 inputs, FP32 accumulator in TMEM, M = 128) and tcgen05.commit
 // releases the operand buffers; the epilogue reads TMEM with tcgen05.ld.  Every mbarrier wait
 // is bounded: a wait that gives up records DKS_ERR_TIMEOUT in a device status word, the CTA
